@@ -1,0 +1,212 @@
+/*
+ * dpgmg.h -- C ABI of the GB300 DPG multigrid solver for 3D time-harmonic
+ * acoustics (Badger, Henneking, Petrides, Demkowicz, arXiv 2304.01728).
+ *
+ * Problem (Sec. 2, Eq. helmholtz, with the wavespeed reading rho = 1, bulk
+ * modulus c^2, impedance Z = c):
+ *     i w c^-2 p + div u = f,   i w u + grad p = g   in Omega (an axis-aligned box)
+ *     Z^-1 p - u.n = u0                               on Gamma = boundary of Omega
+ * discretised by the broken ultraweak DPG method of Sec. 2 (trial fields in
+ * L^2 of order p, traces p-hat in H^{1/2}, u-hat_n in H^{-1/2}, test space
+ * enriched by dp = 1, adjoint graph test norm Eq. Gnorm with alpha = 1),
+ * statically condensed onto the trace unknowns (Sec. 1.2), and solved by
+ * conjugate gradients preconditioned with the DPG-MG V-cycle of Sec. 3
+ * (macro-grid prolongation, vertex-patch additive Schwarz smoothing, coarse
+ * operators restricted from the fine grid).  The impedance condition is
+ * built in by eliminating u-hat_n on Gamma: boundary faces carry p-hat only.
+ *
+ * Conventions for every call:
+ *   - Return value: DPGMG_OK (0) or a negative DPGMG_ERR_* code; no
+ *     exception or signal crosses the ABI.  dpgmg_strerror() names the code;
+ *     dpgmg_last_error() gives a message for the calling thread.
+ *   - Complex arrays are interleaved (re, im) doubles ("c128").
+ *   - Input arrays are host arrays owned by the caller and are copied during
+ *     the call.  Output arrays are owned by the caller; they are host arrays
+ *     unless the call says otherwise.
+ *   - A handle owns one CUDA device (and optionally one caller stream) and all
+ *     device memory of the systems set up through it, until dpgmg_release() /
+ *     dpgmg_destroy().  Calls on one handle are serialised by an internal
+ *     mutex; distinct handles may be used from distinct threads.
+ *
+ * Global trace numbering (the order of dpgmg_solve's trace output), for an
+ * nx x ny x nz mesh of order p:
+ *   block V  vertices, 1 DOF each; vertex (i,j,k) -> i + (nx+1)(j + (ny+1)k)
+ *   block E  edges along x, then y, then z; an edge along axis d at lattice
+ *            position (i,j,k) has index extents n_e + (e != d) and p-1 DOFs
+ *            (H^1 modes 2..p of that axis)
+ *   block F  faces normal to x, then y, then z (p-hat); extents n_e + (e == d);
+ *            (p-1)^2 DOFs, modes (m1, m2) of the tangential axes (increasing
+ *            axis order), index (m1-2) + (p-1)(m2-2)
+ *   block U  interior faces only (u-hat_n, the flux along the +axis normal),
+ *            same face order with boundary faces skipped; p^2 DOFs, Legendre
+ *            modes (a, b) of the tangential axes, index a + p b.
+ * The 1D bases on an element's unit interval: Legendre L_a(x) = P_a(2x-1);
+ * H^1: phi_0 = 1-x, phi_1 = x, phi_k = (P_k - P_{k-2})(2x-1)/sqrt(2(2k-1)).
+ * Element-local trace order: p-hat functions phi_a phi_b phi_c, (a,b,c) in
+ * {0..p}^3 by a + (p+1)(b + (p+1)c) keeping triples with an index < 2, then
+ * u-hat of faces x-, x+, y-, y+, z-, z+ with modes a + p b.
+ * Field output per element: [p, u_x, u_y, u_z], each sum_abc coef L_a L_b L_c
+ * with a, b, c < p, index a + p(b + p c); elements ordered i + nx(j + ny k).
+ */
+#ifndef DPGMG_H
+#define DPGMG_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------ */
+#define DPGMG_OK                  0
+#define DPGMG_ERR_ARG            -1  /* invalid argument or unsupported option */
+#define DPGMG_ERR_NOMEM          -2  /* device-memory budget or allocation exceeded */
+#define DPGMG_ERR_NOT_HPD        -3  /* a Cholesky pivot <= 0 (element, patch, coarse) */
+#define DPGMG_ERR_BREAKDOWN      -4  /* CG breakdown: (p, Ap) <= 0 or not finite */
+#define DPGMG_ERR_NOT_CONVERGED  -5  /* max_iter reached; outputs and stats still written */
+#define DPGMG_ERR_TIMEOUT        -6  /* a bounded device wait expired */
+#define DPGMG_ERR_PENDING        -7  /* serving: request not finished yet */
+#define DPGMG_ERR_CUDA           -8  /* a CUDA runtime call failed */
+
+/* ---- enums ------------------------------------------------------------- */
+#define DPGMG_SRC_GAUSSIAN      0   /* f = A exp(-|x-x0|^2/(2 s^2)), g = 0, u0 = 0 */
+#define DPGMG_SRC_PLANE_WAVE    1   /* u0 of p = exp(-i w d.x/c), u = d p / c; f = g = 0 */
+#define DPGMG_SRC_MANUFACTURED  2   /* f, g, u0 of given polynomials p_ex, u_ex */
+
+#define DPGMG_PREC_FP64   0         /* V-cycle in complex128 */
+#define DPGMG_PREC_MIXED  1         /* V-cycle in complex64, CG in complex128 */
+
+#define DPGMG_COARSEST_CHOLESKY 0   /* dense Cholesky solve on level 0 */
+#define DPGMG_COARSEST_NONE     1   /* no level-0 correction (Sec. 4 list) */
+
+/* ---- problem and options ----------------------------------------------- */
+typedef struct dpgmg_problem {
+  int n[3];                /* elements per axis, each >= 1 */
+  double x0[3], x1[3];     /* box corners, x1 > x0 */
+  int p;                   /* trial order, 1..5 */
+  int dp;                  /* test enrichment; must be 1 (Sec. 2) */
+  double omega;            /* angular frequency w > 0 */
+  const double* wavespeed; /* host [n0*n1*n2] per element (> 0), or NULL for c = 1 */
+  int source;              /* DPGMG_SRC_* */
+  double src_center[3];    /* Gaussian centre x0 */
+  double src_width;        /* Gaussian standard deviation s > 0 */
+  double src_amp;          /* Gaussian amplitude A */
+  double wave_dir[3];      /* plane wave direction d (normalised internally); needs constant c */
+  int mf_order;            /* manufactured: polynomial degree + 1 per axis (m >= 1) */
+  const double* mf_coeffs; /* manufactured: host c128 [4][m][m][m] (comp, c, b, a):
+                              comp 0 = p_ex, 1..3 = u_ex components; tensor Legendre
+                              L_a(X) L_b(Y) L_c(Z) in box coordinates X = (x-x0)/(x1-x0) */
+} dpgmg_problem;
+
+typedef struct dpgmg_opts {
+  double tol;              /* relative residual target ||r||/||b|| (Sec. 4: 1e-7; default 1e-8) */
+  int max_iter;            /* CG iteration cap */
+  int nu_pre, nu_post;     /* smoothing steps per level (V(1,1) default, Sec. 4) */
+  int n_levels;            /* levels incl. finest and coarsest, >= 1 */
+  int p_min;               /* lowest order of the p-coarsening stage (>= 1) */
+  int precision;           /* DPGMG_PREC_* */
+  int coarsest;            /* DPGMG_COARSEST_* */
+  double theta;            /* smoother damping; <= 0 => estimate by power iteration */
+} dpgmg_opts;
+
+typedef struct dpgmg_stats {
+  int iters;               /* CG iterations (= V-cycle applications) */
+  double relres;           /* final recursive relative residual */
+  double true_relres;      /* ||b - A x|| / ||b|| recomputed at exit (FP64) */
+  double t_setup_ms;       /* device time of dpgmg_setup */
+  double t_pcg_ms;         /* device time from the first CG step to convergence */
+  long long bytes_per_iter;/* algorithmic bytes of one CG iteration (matrix entries read once) */
+  long long n_dof;         /* finest trace DOFs */
+} dpgmg_stats;
+
+typedef struct dpgmg_level_desc {
+  int n[3], p;
+  long long n_dof;         /* trace DOFs of the level's mesh and order */
+  long long n_smooth;      /* DOFs the smoother acts on (macro DOFs on h levels) */
+  int kind;                /* transition to the level below: 0 none, 1 p, 2 h */
+  long long n_patches;
+  long long patch_max;
+  long long sum_patch_sq;  /* sum of squared patch sizes */
+  long long op_nnz;        /* stored entries of the level's smoothing operator */
+  double theta;
+} dpgmg_level_desc;
+
+typedef struct dpgmg_handle_s* dpgmg_handle;
+typedef struct dpgmg_system_s* dpgmg_system;
+
+/* Create a handle bound to CUDA device `device`.  mem_budget_bytes caps the
+ * device memory of all systems of this handle (0 = 90% of free memory).
+ * cuda_stream: a cudaStream_t to issue work on, or NULL for a private stream. */
+int dpgmg_create(dpgmg_handle* h, int device, size_t mem_budget_bytes, void* cuda_stream);
+void dpgmg_destroy(dpgmg_handle h);
+
+/* Sizes of a problem without touching the device: finest trace DOFs, field
+ * DOFs (n_elem * 4 p^3) and the device bytes dpgmg_setup would hold. */
+int dpgmg_query_sizes(const dpgmg_problem* pb, const dpgmg_opts* op,
+                      long long* n_trace, long long* n_field, size_t* dev_bytes);
+
+/* Default options: tol 1e-8, max_iter 2000, V(1,1), 2 levels, p_min 2, FP64,
+ * Cholesky coarsest, theta estimated. */
+void dpgmg_default_opts(dpgmg_opts* op);
+
+/* Build the whole hierarchy on the device (Sec. 2-3): batched element DPG
+ * matrices (enriched-test Gram Cholesky, B^* G^-1 B, static condensation),
+ * assembly, p-restriction / macro condensation + natural inclusion +
+ * restriction per level, patch factorisations, damping, coarsest factor.
+ * Errors: ARG (invalid problem/options), NOMEM (over budget; nothing kept),
+ * NOT_HPD (a factorisation failed), CUDA. */
+int dpgmg_setup(dpgmg_handle h, const dpgmg_problem* pb, const dpgmg_opts* op,
+                dpgmg_system* sys);
+
+/* MG-preconditioned CG from x0 = 0 (Sec. 3-4) and field recovery.
+ * trace_out: c128[n_trace] (global numbering above) or NULL;
+ * field_out: c128[n_elem*4p^3] or NULL; both device pointers when
+ * out_is_device != 0, else host.  st may be NULL.
+ * Errors: NOT_CONVERGED (outputs written), BREAKDOWN, TIMEOUT, CUDA. */
+int dpgmg_solve(dpgmg_handle h, dpgmg_system sys, void* trace_out, void* field_out,
+                int out_is_device, dpgmg_stats* st);
+
+void dpgmg_release(dpgmg_handle h, dpgmg_system sys);
+const char* dpgmg_strerror(int code);
+const char* dpgmg_last_error(void);
+
+/* ---- introspection (one call per step of the hot path, used by tests) ---- */
+
+/* Level l (0 = coarsest) description. */
+int dpgmg_level_info(dpgmg_handle h, dpgmg_system sys, int level, dpgmg_level_desc* out);
+
+/* Element matrix of level `level` for element e (local trace order above;
+ * absent u-hat rows/columns are zero): host c128 [nloc*nloc], row-major.
+ * On the finest level this is the condensed DPG element matrix
+ * K_tt - K_tf K_ff^-1 K_ft of Sec. 1.2; below it the restricted coarse
+ * element matrices of Sec. 3.  load_out (finest only, may be NULL): host
+ * c128 [nloc], the condensed element load. */
+int dpgmg_element_matrix(dpgmg_handle h, dpgmg_system sys, int level, long long e,
+                         double* mat_out, double* load_out);
+
+/* Assembled right-hand side b of the finest trace system: host c128 [n_trace]. */
+int dpgmg_rhs(dpgmg_handle h, dpgmg_system sys, double* b_out);
+
+#define DPGMG_OP_A          0  /* y = A_l x: the level's smoothing operator (A_l on p
+                                  levels and the finest, macro M_l on h levels); on the
+                                  finest level in CG precision (FP64) */
+#define DPGMG_OP_SMOOTH     1  /* y = theta_l S_l x (additive Schwarz, Sec. 3) */
+#define DPGMG_OP_VCYCLE     2  /* y = B_l x (V-cycle from level l down) */
+#define DPGMG_OP_RESTRICT   3  /* y = P_l^* x  (level l -> l-1; x full level-l vector) */
+#define DPGMG_OP_PROLONG    4  /* y = P_l x    (level l-1 -> l) */
+#define DPGMG_OP_CONDENSE   5  /* y = x with macro-interior residual condensed (h levels) */
+#define DPGMG_OP_COARSE     6  /* y = A_0^-1 x (level 0) */
+#define DPGMG_OP_AFULL      7  /* y = A_L x on the finest level, FP64 (the CG operator) */
+
+/* Apply one operator of level `level` to a host c128 vector x; y is a host
+ * c128 vector.  Sizes: n_dof of the level (n_dof of level-1 for RESTRICT's y
+ * and PROLONG's x).  On the mixed-precision path the V-cycle operators run
+ * in complex64 (inputs rounded, outputs widened). */
+int dpgmg_apply(dpgmg_handle h, dpgmg_system sys, int op, int level,
+                const double* x, double* y);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DPGMG_H */

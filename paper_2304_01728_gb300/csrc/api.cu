@@ -1,0 +1,430 @@
+// C ABI of the DPG-MG solver (include/dpgmg.h): handles, problem validation,
+// setup / solve orchestration and introspection.  No exception crosses the
+// ABI; every failure becomes a DPGMG_ERR_* status and a thread-local message.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <mutex>
+#include <new>
+
+#include "internal.h"
+
+struct dpgmg_handle_s {
+  dpgmg::HandleImpl h;
+  std::mutex mu;
+};
+struct dpgmg_system_s {
+  dpgmg::SystemImpl s;
+};
+
+namespace dpgmg {
+
+static thread_local std::string g_last;
+void set_last_error(const std::string& m) { g_last = m; }
+
+void* Alloc::get(size_t bytes) {
+  bytes = (bytes + 255) & ~(size_t)255;
+  if (used + bytes > budget) throw Err{DPGMG_ERR_NOMEM, "device-memory budget exceeded"};
+  void* p = nullptr;
+  cudaError_t e = cudaMalloc(&p, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    throw Err{DPGMG_ERR_NOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(e)};
+  }
+  ptrs.push_back(p);
+  used += bytes;
+  peak = std::max(peak, used);
+  return p;
+}
+
+void Alloc::free_all() {
+  for (void* p : ptrs) cudaFree(p);
+  ptrs.clear();
+  used = 0;
+}
+
+static int validate(const dpgmg_problem* pb, const dpgmg_opts* op) {
+  if (!pb || !op) return DPGMG_ERR_ARG;
+  for (int d = 0; d < 3; ++d) {
+    if (pb->n[d] < 1 || !(pb->x1[d] > pb->x0[d])) return DPGMG_ERR_ARG;
+  }
+  if (pb->p < 1 || pb->p > 5 || pb->dp != 1 || !(pb->omega > 0.0)) return DPGMG_ERR_ARG;
+  if (pb->source < 0 || pb->source > 2) return DPGMG_ERR_ARG;
+  if (pb->source == DPGMG_SRC_GAUSSIAN && !(pb->src_width > 0.0)) return DPGMG_ERR_ARG;
+  if (pb->source == DPGMG_SRC_MANUFACTURED && (pb->mf_order < 1 || pb->mf_order > 8 || !pb->mf_coeffs))
+    return DPGMG_ERR_ARG;
+  if (pb->source == DPGMG_SRC_PLANE_WAVE) {
+    double n2 = pb->wave_dir[0] * pb->wave_dir[0] + pb->wave_dir[1] * pb->wave_dir[1] + pb->wave_dir[2] * pb->wave_dir[2];
+    if (!(n2 > 0.0)) return DPGMG_ERR_ARG;
+  }
+  if (pb->wavespeed) {
+    int64_t ne = (int64_t)pb->n[0] * pb->n[1] * pb->n[2];
+    for (int64_t e = 0; e < ne; ++e)
+      if (!(pb->wavespeed[e] > 0.0) || !std::isfinite(pb->wavespeed[e])) return DPGMG_ERR_ARG;
+  }
+  if (!(op->tol > 0.0) || op->max_iter < 1 || op->nu_pre < 0 || op->nu_post < 0 || op->n_levels < 1 ||
+      op->p_min < 1 || (op->precision != DPGMG_PREC_FP64 && op->precision != DPGMG_PREC_MIXED) ||
+      (op->coarsest != DPGMG_COARSEST_CHOLESKY && op->coarsest != DPGMG_COARSEST_NONE))
+    return DPGMG_ERR_ARG;
+  return DPGMG_OK;
+}
+
+// Device bytes held by a system (upper-bound estimate used for admission).
+static size_t estimate_bytes(const dpgmg_problem* pb, const dpgmg_opts* op) {
+  const int nn[3] = {pb->n[0], pb->n[1], pb->n[2]};
+  auto specs = plan_levels(nn, pb->p, op->n_levels, op->p_min);
+  const bool mixed = op->precision == DPGMG_PREC_MIXED;
+  double bytes = 0;
+  const int p = pb->p;
+  const int64_t ne = (int64_t)nn[0] * nn[1] * nn[2];
+  const double ntr = n_trace_local(p), nf = 4.0 * p * p * p;
+  const double nt = std::pow(p + 2.0, 3) + 3.0 * (p + 2.0) * (p + 1.0) * (p + 1.0);
+  bytes += ne * (ntr * ntr + nf * (ntr + 1) + ntr) * 16.0;                                   // E, Yrec, Fc
+  bytes += std::min<double>(4096.0, (double)ne) * (nt * nt * 8 + nt * (nf + ntr + 1) * 16 + std::pow(nf + ntr + 1, 2) * 16);
+  for (size_t l = 0; l < specs.size(); ++l) {
+    const LevelSpec& s = specs[l];
+    const double nel = (double)s.n[0] * s.n[1] * s.n[2];
+    const double nl = n_trace_local(s.p);
+    MeshL m;
+    double x0[3] = {0, 0, 0}, x1[3] = {1, 1, 1};
+    m.init(s.n, s.p, x0, x1);
+    const double esz = mixed ? 24.0 : 16.0;
+    bytes += nel * nl * nl * 16.0 + nel * nl * 8.0 + m.ndof * 200.0;        // element matrices, maps, vectors
+    if (l + 1 < specs.size()) {
+      bytes += nel * nl * nl * (esz + 4.0 / 3.0);                            // operator values + indices
+      const int q = s.p;
+      double np_int;
+      int64_t nv;
+      if (s.kind_below == 1) {
+        np_int = 1 + 6 * (q - 1) + 12 * ((q - 1) * (q - 1) + q * q);
+        nv = (int64_t)(s.n[0] + 1) * (s.n[1] + 1) * (s.n[2] + 1);
+      } else {
+        np_int = 1 + 6 * (2 * (q - 1) + 1) + 12 * (4 * (q - 1) * (q - 1) + 4 * (q - 1) + 1 + 4 * q * q);
+        nv = (int64_t)(s.n[0] / 2 + 1) * (s.n[1] / 2 + 1) * (s.n[2] / 2 + 1);
+        const double nS = 6 * (4 * (q - 1) * (q - 1) + 4 * (q - 1) + 1 + 4 * q * q) + 12 * (2 * (q - 1) + 1) + 8;
+        const double nI = 1 + 6 * (q - 1) + 12 * ((q - 1) * (q - 1) + q * q);
+        const double nK = nel / 8.0;
+        bytes += nK * (nI * nS + nI * nI) * esz + std::min(nK, 2048.0) * ((nS + nI) * (nS + nI) + 2 * nS * nS) * 16;
+      }
+      bytes += nv * np_int * np_int * 1.25 * esz + std::min<double>(2e9, nv * np_int * np_int * 16.0);
+    } else {
+      double N0 = (double)m.ndof;
+      if (op->coarsest == DPGMG_COARSEST_CHOLESKY || specs.size() == 1) bytes += N0 * N0 * esz;
+    }
+  }
+  return (size_t)(bytes * 1.1) + ((size_t)64 << 20);
+}
+
+static void fill_bytes_per_iter(SystemImpl& S) {
+  const bool mixed = S.op.precision == DPGMG_PREC_MIXED;
+  const double esz = mixed ? 8.0 : 16.0;
+  double b = 0;
+  const Level& F = S.levels.back();
+  // CG operator (FP64)
+  int64_t cg_nnz = 0;
+  if (S.levels.size() > 1 && F.kind == 1) cg_nnz = F.A.nnz;
+  else cg_nnz = (int64_t)(F.mesh.nelem * (double)F.nloc * F.nloc * 0.8);
+  b += cg_nnz * 16.0;
+  const int nu = S.op.nu_pre + S.op.nu_post;
+  for (size_t l = 1; l < S.levels.size(); ++l) {
+    const Level& L = S.levels[l];
+    b += nu * (double)L.P.nvals * esz;                                           // smoother
+    b += std::max(1, nu) * (double)L.A.nnz * esz;                                // residual SpMVs
+    if (L.kind == 2) b += (double)L.nK * (2.0 * L.nI * L.nS + L.nI * L.nI) * esz; // condense + backsub
+  }
+  const Level& C0 = S.levels[0];
+  if (C0.C64) b += (double)C0.N0 * C0.N0 * esz;                                  // two triangular solves
+  S.bytes_per_iter = (int64_t)b;
+}
+
+}  // namespace dpgmg
+
+using namespace dpgmg;
+
+static int fail(const Err& e) {
+  set_last_error(e.msg);
+  return e.code;
+}
+
+extern "C" {
+
+void dpgmg_default_opts(dpgmg_opts* op) {
+  if (!op) return;
+  op->tol = 1e-8;
+  op->max_iter = 2000;
+  op->nu_pre = 1;
+  op->nu_post = 1;
+  op->n_levels = 2;
+  op->p_min = 2;
+  op->precision = DPGMG_PREC_FP64;
+  op->coarsest = DPGMG_COARSEST_CHOLESKY;
+  op->theta = 0.0;
+}
+
+const char* dpgmg_strerror(int code) {
+  switch (code) {
+    case DPGMG_OK: return "ok";
+    case DPGMG_ERR_ARG: return "invalid argument";
+    case DPGMG_ERR_NOMEM: return "device memory budget exceeded";
+    case DPGMG_ERR_NOT_HPD: return "factorisation lost positive definiteness";
+    case DPGMG_ERR_BREAKDOWN: return "conjugate-gradient breakdown";
+    case DPGMG_ERR_NOT_CONVERGED: return "not converged within max_iter";
+    case DPGMG_ERR_TIMEOUT: return "bounded device wait expired";
+    case DPGMG_ERR_PENDING: return "request pending";
+    case DPGMG_ERR_CUDA: return "CUDA runtime error";
+    default: return "unknown status";
+  }
+}
+
+const char* dpgmg_last_error(void) { return g_last.c_str(); }
+
+int dpgmg_create(dpgmg_handle* out, int device, size_t mem_budget_bytes, void* cuda_stream) {
+  if (!out) return DPGMG_ERR_ARG;
+  *out = nullptr;
+  try {
+    int ndev = 0;
+    DPG_CUDA(cudaGetDeviceCount(&ndev));
+    if (device < 0 || device >= ndev) return DPGMG_ERR_ARG;
+    DPG_CUDA(cudaSetDevice(device));
+    auto* h = new (std::nothrow) dpgmg_handle_s();
+    if (!h) return DPGMG_ERR_NOMEM;
+    h->h.device = device;
+    if (cuda_stream) {
+      h->h.stream = reinterpret_cast<cudaStream_t>(cuda_stream);
+    } else {
+      DPG_CUDA(cudaStreamCreateWithFlags(&h->h.stream, cudaStreamNonBlocking));
+      h->h.own_stream = true;
+    }
+    size_t fr = 0, tot = 0;
+    DPG_CUDA(cudaMemGetInfo(&fr, &tot));
+    h->h.budget = mem_budget_bytes ? mem_budget_bytes : (size_t)(0.9 * fr);
+    *out = h;
+    return DPGMG_OK;
+  } catch (const Err& e) {
+    return fail(e);
+  }
+}
+
+void dpgmg_destroy(dpgmg_handle h) {
+  if (!h) return;
+  cudaSetDevice(h->h.device);
+  if (h->h.own_stream) cudaStreamDestroy(h->h.stream);
+  delete h;
+}
+
+int dpgmg_query_sizes(const dpgmg_problem* pb, const dpgmg_opts* op, long long* n_trace, long long* n_field,
+                      size_t* dev_bytes) {
+  int v = validate(pb, op);
+  if (v) return v;
+  MeshL m;
+  m.init(pb->n, pb->p, pb->x0, pb->x1);
+  if (n_trace) *n_trace = m.ndof;
+  if (n_field) *n_field = m.nelem * 4LL * pb->p * pb->p * pb->p;
+  if (dev_bytes) *dev_bytes = estimate_bytes(pb, op);
+  return DPGMG_OK;
+}
+
+int dpgmg_setup(dpgmg_handle h, const dpgmg_problem* pb, const dpgmg_opts* op, dpgmg_system* out) {
+  if (!h || !out) return DPGMG_ERR_ARG;
+  *out = nullptr;
+  int v = validate(pb, op);
+  if (v) {
+    set_last_error("invalid problem or options");
+    return v;
+  }
+  std::lock_guard<std::mutex> lk(h->mu);
+  size_t est = estimate_bytes(pb, op);
+  if (h->h.used + est > h->h.budget) {
+    set_last_error("estimated device footprint exceeds the handle's budget");
+    return DPGMG_ERR_NOMEM;
+  }
+  auto* sys = new (std::nothrow) dpgmg_system_s();
+  if (!sys) return DPGMG_ERR_NOMEM;
+  SystemImpl& S = sys->s;
+  try {
+    DPG_CUDA(cudaSetDevice(h->h.device));
+    cudaStream_t st = h->h.stream;
+    S.pb = *pb;
+    S.op = *op;
+    const int64_t ne = (int64_t)pb->n[0] * pb->n[1] * pb->n[2];
+    S.wavespeed.assign(ne, 1.0);
+    if (pb->wavespeed) std::copy(pb->wavespeed, pb->wavespeed + ne, S.wavespeed.begin());
+    if (pb->source == DPGMG_SRC_MANUFACTURED) {
+      size_t m = pb->mf_order;
+      S.mf_coeffs.assign(pb->mf_coeffs, pb->mf_coeffs + 2 * 4 * m * m * m);
+    }
+    S.pb.wavespeed = nullptr;
+    S.pb.mf_coeffs = nullptr;
+    S.mem.budget = h->h.budget - h->h.used;
+    auto specs = plan_levels(pb->n, pb->p, op->n_levels, op->p_min);
+    S.levels.resize(specs.size());
+    for (size_t i = 0; i < specs.size(); ++i) {
+      Level& L = S.levels[specs.size() - 1 - i];
+      L.mesh.init(specs[i].n, specs[i].p, pb->x0, pb->x1);
+      L.kind = specs[i].kind_below;
+      L.nloc = (int)L.mesh.loc.size();
+    }
+    cudaEvent_t e0, e1;
+    DPG_CUDA(cudaEventCreate(&e0));
+    DPG_CUDA(cudaEventCreate(&e1));
+    DPG_CUDA(cudaEventRecord(e0, st));
+    element_stage(S, st);
+    build_hierarchy(S, st);
+    assemble_rhs(S, st);
+    ensure_workspace(S, st);
+    DPG_CUDA(cudaEventRecord(e1, st));
+    DPG_CUDA(cudaEventSynchronize(e1));
+    float ms = 0.f;
+    DPG_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    S.t_setup_ms = ms;
+    fill_bytes_per_iter(S);
+    h->h.used += S.mem.used;
+    *out = sys;
+    return DPGMG_OK;
+  } catch (const Err& e) {
+    cudaDeviceSynchronize();
+    free_workspace(S);
+    delete sys;
+    return fail(e);
+  } catch (const std::exception& e) {
+    cudaDeviceSynchronize();
+    free_workspace(S);
+    delete sys;
+    return fail(Err{DPGMG_ERR_ARG, e.what()});
+  }
+}
+
+int dpgmg_solve(dpgmg_handle h, dpgmg_system sys, void* trace_out, void* field_out, int out_is_device,
+                dpgmg_stats* st) {
+  if (!h || !sys) return DPGMG_ERR_ARG;
+  std::lock_guard<std::mutex> lk(h->mu);
+  SystemImpl& S = sys->s;
+  try {
+    DPG_CUDA(cudaSetDevice(h->h.device));
+    cudaStream_t s = h->h.stream;
+    const int64_t n = S.levels.back().mesh.ndof;
+    const int64_t nfld = S.nelem * S.nf;
+    Alloc tmp;
+    tmp.budget = (size_t)-1;
+    double2* x = (trace_out && out_is_device) ? reinterpret_cast<double2*>(trace_out) : tmp.arr<double2>((size_t)n);
+    int status = pcg_solve(S, s, x, st);
+    if (field_out) {
+      double2* f = out_is_device ? reinterpret_cast<double2*>(field_out) : tmp.arr<double2>((size_t)nfld);
+      recover_fields(S, x, f, s);
+      if (!out_is_device)
+        DPG_CUDA(cudaMemcpyAsync(field_out, f, (size_t)nfld * sizeof(double2), cudaMemcpyDeviceToHost, s));
+    }
+    if (trace_out && !out_is_device)
+      DPG_CUDA(cudaMemcpyAsync(trace_out, x, (size_t)n * sizeof(double2), cudaMemcpyDeviceToHost, s));
+    DPG_CUDA(cudaStreamSynchronize(s));
+    if (status != DPGMG_OK) set_last_error(dpgmg_strerror(status));
+    return status;
+  } catch (const Err& e) {
+    return fail(e);
+  }
+}
+
+void dpgmg_release(dpgmg_handle h, dpgmg_system sys) {
+  if (!sys) return;
+  if (h) {
+    std::lock_guard<std::mutex> lk(h->mu);
+    cudaSetDevice(h->h.device);
+    cudaStreamSynchronize(h->h.stream);
+    h->h.used -= std::min(h->h.used, sys->s.mem.used);
+  }
+  free_workspace(sys->s);
+  delete sys;
+}
+
+int dpgmg_level_info(dpgmg_handle h, dpgmg_system sys, int level, dpgmg_level_desc* out) {
+  if (!h || !sys || !out) return DPGMG_ERR_ARG;
+  SystemImpl& S = sys->s;
+  if (level < 0 || level >= (int)S.levels.size()) return DPGMG_ERR_ARG;
+  const Level& L = S.levels[level];
+  for (int d = 0; d < 3; ++d) out->n[d] = L.mesh.n[d];
+  out->p = L.mesh.p;
+  out->n_dof = L.mesh.ndof;
+  out->n_smooth = L.n_smooth;
+  out->kind = L.kind;
+  out->n_patches = L.P.np;
+  out->patch_max = L.P.max_n;
+  out->sum_patch_sq = L.P.sum_sq;
+  out->op_nnz = L.A.nnz;
+  out->theta = L.theta;
+  return DPGMG_OK;
+}
+
+int dpgmg_element_matrix(dpgmg_handle h, dpgmg_system sys, int level, long long e, double* mat_out,
+                         double* load_out) {
+  if (!h || !sys || !mat_out) return DPGMG_ERR_ARG;
+  std::lock_guard<std::mutex> lk(h->mu);
+  SystemImpl& S = sys->s;
+  if (level < 0 || level >= (int)S.levels.size()) return DPGMG_ERR_ARG;
+  const Level& L = S.levels[level];
+  if (e < 0 || e >= L.mesh.nelem) return DPGMG_ERR_ARG;
+  try {
+    DPG_CUDA(cudaSetDevice(h->h.device));
+    cudaStream_t s = h->h.stream;
+    size_t nn = (size_t)L.nloc * L.nloc;
+    DPG_CUDA(cudaMemcpyAsync(mat_out, L.E + e * nn, nn * sizeof(double2), cudaMemcpyDeviceToHost, s));
+    if (load_out) {
+      if (level != (int)S.levels.size() - 1) return DPGMG_ERR_ARG;
+      DPG_CUDA(cudaMemcpyAsync(load_out, S.Fc + e * S.ntr, S.ntr * sizeof(double2), cudaMemcpyDeviceToHost, s));
+    }
+    DPG_CUDA(cudaStreamSynchronize(s));
+    return DPGMG_OK;
+  } catch (const Err& e2) {
+    return fail(e2);
+  }
+}
+
+int dpgmg_rhs(dpgmg_handle h, dpgmg_system sys, double* b_out) {
+  if (!h || !sys || !b_out) return DPGMG_ERR_ARG;
+  std::lock_guard<std::mutex> lk(h->mu);
+  SystemImpl& S = sys->s;
+  try {
+    DPG_CUDA(cudaSetDevice(h->h.device));
+    size_t n = (size_t)S.levels.back().mesh.ndof;
+    DPG_CUDA(cudaMemcpyAsync(b_out, S.b, n * sizeof(double2), cudaMemcpyDeviceToHost, h->h.stream));
+    DPG_CUDA(cudaStreamSynchronize(h->h.stream));
+    return DPGMG_OK;
+  } catch (const Err& e) {
+    return fail(e);
+  }
+}
+
+int dpgmg_apply(dpgmg_handle h, dpgmg_system sys, int op, int level, const double* x, double* y) {
+  if (!h || !sys || !x || !y) return DPGMG_ERR_ARG;
+  std::lock_guard<std::mutex> lk(h->mu);
+  SystemImpl& S = sys->s;
+  const int nl = (int)S.levels.size();
+  if (level < 0 || level >= nl || op < 0 || op > DPGMG_OP_AFULL) return DPGMG_ERR_ARG;
+  const Level& L = S.levels[level];
+  if ((op == DPGMG_OP_A || op == DPGMG_OP_SMOOTH || op == DPGMG_OP_RESTRICT || op == DPGMG_OP_PROLONG) && level == 0)
+    return DPGMG_ERR_ARG;
+  if (op == DPGMG_OP_CONDENSE && L.kind != 2) return DPGMG_ERR_ARG;
+  if (op == DPGMG_OP_COARSE && (level != 0 || !L.C64)) return DPGMG_ERR_ARG;
+  if (op == DPGMG_OP_AFULL && level != nl - 1) return DPGMG_ERR_ARG;
+  try {
+    DPG_CUDA(cudaSetDevice(h->h.device));
+    cudaStream_t s = h->h.stream;
+    int64_t nin = L.mesh.ndof, nout = L.mesh.ndof;
+    if (op == DPGMG_OP_RESTRICT) nout = S.levels[level - 1].mesh.ndof;
+    if (op == DPGMG_OP_PROLONG) nin = S.levels[level - 1].mesh.ndof;
+    Alloc tmp;
+    tmp.budget = (size_t)-1;
+    double2* dx = tmp.arr<double2>((size_t)nin);
+    double2* dy = tmp.arr<double2>((size_t)nout);
+    DPG_CUDA(cudaMemcpyAsync(dx, x, (size_t)nin * sizeof(double2), cudaMemcpyHostToDevice, s));
+    apply_op(S, op, level, dx, dy, s);
+    DPG_CUDA(cudaMemcpyAsync(y, dy, (size_t)nout * sizeof(double2), cudaMemcpyDeviceToHost, s));
+    DPG_CUDA(cudaStreamSynchronize(s));
+    return DPGMG_OK;
+  } catch (const Err& e) {
+    return fail(e);
+  }
+}
+
+}  // extern "C"

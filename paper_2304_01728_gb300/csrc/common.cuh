@@ -1,0 +1,354 @@
+// Shared device helpers: complex arithmetic and CTA-cooperative dense
+// linear algebra on row-major matrices in global memory.
+//
+// The batched element, macro-element and patch kernels run one CTA per
+// small dense problem (n up to ~1100).  The routines below are blocked
+// (block size NB) with shared-memory staging of the diagonal block and of
+// the operand tiles of the trailing updates.  They assume blockDim.x == 256.
+#pragma once
+#include <cuda_runtime.h>
+#include <cstdint>
+
+namespace dpgmg {
+
+// ------------------------------------------------------------- scalar ops
+template <class T> struct Ops;
+
+template <> struct Ops<double> {
+  using R = double;
+  __device__ __forceinline__ static double zero() { return 0.0; }
+  __device__ __forceinline__ static double add(double a, double b) { return a + b; }
+  __device__ __forceinline__ static double sub(double a, double b) { return a - b; }
+  __device__ __forceinline__ static double mul(double a, double b) { return a * b; }
+  __device__ __forceinline__ static double mulc(double a, double b) { return a * b; }   // a conj(b)
+  __device__ __forceinline__ static double fma(double a, double b, double c) { return ::fma(a, b, c); }
+  __device__ __forceinline__ static double fmac(double a, double b, double c) { return ::fma(a, b, c); }  // a conj(b) + c
+  __device__ __forceinline__ static double fnmac(double a, double b, double c) { return ::fma(-a, b, c); } // c - a conj(b)
+  __device__ __forceinline__ static double fnma(double a, double b, double c) { return ::fma(-a, b, c); }  // c - a b
+  __device__ __forceinline__ static double conj(double a) { return a; }
+  __device__ __forceinline__ static double re(double a) { return a; }
+  __device__ __forceinline__ static double scale(double a, double s) { return a * s; }
+  __device__ __forceinline__ static double from_re(double r) { return r; }
+};
+
+template <> struct Ops<float> {
+  using R = float;
+  __device__ __forceinline__ static float zero() { return 0.f; }
+  __device__ __forceinline__ static float add(float a, float b) { return a + b; }
+  __device__ __forceinline__ static float sub(float a, float b) { return a - b; }
+  __device__ __forceinline__ static float mul(float a, float b) { return a * b; }
+  __device__ __forceinline__ static float mulc(float a, float b) { return a * b; }
+  __device__ __forceinline__ static float fma(float a, float b, float c) { return fmaf(a, b, c); }
+  __device__ __forceinline__ static float fmac(float a, float b, float c) { return fmaf(a, b, c); }
+  __device__ __forceinline__ static float fnmac(float a, float b, float c) { return fmaf(-a, b, c); }
+  __device__ __forceinline__ static float fnma(float a, float b, float c) { return fmaf(-a, b, c); }
+  __device__ __forceinline__ static float conj(float a) { return a; }
+  __device__ __forceinline__ static float re(float a) { return a; }
+  __device__ __forceinline__ static float scale(float a, float s) { return a * s; }
+  __device__ __forceinline__ static float from_re(float r) { return r; }
+};
+
+template <class V, class S> struct CplxOps {
+  using R = S;
+  __device__ __forceinline__ static V mk(S r, S i) { V v; v.x = r; v.y = i; return v; }
+  __device__ __forceinline__ static V zero() { return mk(S(0), S(0)); }
+  __device__ __forceinline__ static V add(V a, V b) { return mk(a.x + b.x, a.y + b.y); }
+  __device__ __forceinline__ static V sub(V a, V b) { return mk(a.x - b.x, a.y - b.y); }
+  __device__ __forceinline__ static V mul(V a, V b) { return mk(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x); }
+  __device__ __forceinline__ static V mulc(V a, V b) { return mk(a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y); }
+  __device__ __forceinline__ static V fma(V a, V b, V c) {
+    return mk(c.x + a.x * b.x - a.y * b.y, c.y + a.x * b.y + a.y * b.x);
+  }
+  __device__ __forceinline__ static V fmac(V a, V b, V c) {   // a conj(b) + c
+    return mk(c.x + a.x * b.x + a.y * b.y, c.y + a.y * b.x - a.x * b.y);
+  }
+  __device__ __forceinline__ static V fnmac(V a, V b, V c) {  // c - a conj(b)
+    return mk(c.x - a.x * b.x - a.y * b.y, c.y - a.y * b.x + a.x * b.y);
+  }
+  __device__ __forceinline__ static V fnma(V a, V b, V c) {   // c - a b
+    return mk(c.x - a.x * b.x + a.y * b.y, c.y - a.x * b.y - a.y * b.x);
+  }
+  __device__ __forceinline__ static V conj(V a) { return mk(a.x, -a.y); }
+  __device__ __forceinline__ static S re(V a) { return a.x; }
+  __device__ __forceinline__ static V scale(V a, S s) { return mk(a.x * s, a.y * s); }
+  __device__ __forceinline__ static V from_re(S r) { return mk(r, S(0)); }
+};
+template <> struct Ops<double2> : CplxOps<double2, double> {};
+template <> struct Ops<float2> : CplxOps<float2, float> {};
+
+// ------------------------------------------------------- CTA dense kernels
+constexpr int CTA_THREADS = 256;
+constexpr int NB = 32;          // panel width
+constexpr int TL = 32;          // output tile edge of the tiled updates
+
+// In-place lower Cholesky A = L L^H of an n x n Hermitian matrix (row-major,
+// leading dimension lda).  The strict upper triangle is not referenced and
+// is left unchanged.  Returns 0 or k+1 if the k-th pivot is not positive.
+// smem: >= NB*NB + 2*TL*NB elements of T.
+template <class T>
+__device__ int cta_potrf(T* A, int n, int lda, T* smem) {
+  using O = Ops<T>;
+  using R = typename O::R;
+  T* D = smem;
+  T* Pi = smem + NB * NB;
+  T* Pj = Pi + TL * NB;
+  __shared__ int info;
+  const int tid = threadIdx.x;
+  if (tid == 0) info = 0;
+  __syncthreads();
+  for (int k0 = 0; k0 < n; k0 += NB) {
+    const int kb = min(NB, n - k0);
+    // diagonal block -> shared, unblocked factorisation
+    for (int e = tid; e < kb * kb; e += blockDim.x) {
+      int i = e / kb, j = e % kb;
+      D[i * NB + j] = A[(size_t)(k0 + i) * lda + k0 + j];
+    }
+    __syncthreads();
+    for (int j = 0; j < kb; ++j) {
+      if (tid == 0) {
+        R d = O::re(D[j * NB + j]);
+        if (!(d > R(0))) { if (info == 0) info = k0 + j + 1; d = R(1); }
+        D[j * NB + j] = O::from_re(sqrt(d));
+      }
+      __syncthreads();
+      R inv = R(1) / O::re(D[j * NB + j]);
+      for (int i = j + 1 + tid; i < kb; i += blockDim.x) D[i * NB + j] = O::scale(D[i * NB + j], inv);
+      __syncthreads();
+      // rank-1 update of the remaining lower part
+      int rem = kb - j - 1;
+      for (int e = tid; e < rem * rem; e += blockDim.x) {
+        int i = j + 1 + e / rem, c = j + 1 + e % rem;
+        if (c <= i) D[i * NB + c] = O::fnmac(D[i * NB + j], D[c * NB + j], D[i * NB + c]);
+      }
+      __syncthreads();
+    }
+    for (int e = tid; e < kb * kb; e += blockDim.x) {
+      int i = e / kb, j = e % kb;
+      if (j <= i) A[(size_t)(k0 + i) * lda + k0 + j] = D[i * NB + j];
+    }
+    // panel: rows below solve x L_kk^H = a
+    const int k1 = k0 + kb;
+    for (int i = k1 + tid; i < n; i += blockDim.x) {
+      T* row = A + (size_t)i * lda + k0;
+      T x[NB];
+      for (int j = 0; j < kb; ++j) {
+        T v = row[j];
+        for (int t = 0; t < j; ++t) v = O::fnmac(x[t], D[j * NB + t], v);
+        x[j] = O::scale(v, R(1) / O::re(D[j * NB + j]));
+      }
+      for (int j = 0; j < kb; ++j) row[j] = x[j];
+    }
+    __syncthreads();
+    // trailing update A[i][j] -= sum_t L[i][t] conj(L[j][t]), lower part
+    const int m = n - k1;
+    const int nt = (m + TL - 1) / TL;
+    for (int bi = 0; bi < nt; ++bi) {
+      for (int bj = 0; bj <= bi; ++bj) {
+        const int i0 = k1 + bi * TL, j0 = k1 + bj * TL;
+        for (int e = tid; e < TL * NB; e += blockDim.x) {
+          int r = e / NB, t = e % NB;
+          Pi[e] = (i0 + r < n && t < kb) ? A[(size_t)(i0 + r) * lda + k0 + t] : O::zero();
+          Pj[e] = (j0 + r < n && t < kb) ? A[(size_t)(j0 + r) * lda + k0 + t] : O::zero();
+        }
+        __syncthreads();
+        for (int e = tid; e < TL * TL; e += blockDim.x) {
+          int r = e / TL, c = e % TL;
+          int i = i0 + r, j = j0 + c;
+          if (i < n && j <= i) {
+            T acc = O::zero();
+            for (int t = 0; t < kb; ++t) acc = O::fmac(Pi[r * NB + t], Pj[c * NB + t], acc);
+            size_t o = (size_t)i * lda + j;
+            A[o] = O::sub(A[o], acc);
+          }
+        }
+        __syncthreads();
+      }
+    }
+  }
+  __syncthreads();
+  return info;
+}
+
+// Mixed products of a triangular-factor entry (real or complex) with a
+// right-hand-side entry (complex or real of the same precision).
+__device__ __forceinline__ double2 lmul(double l, double2 b) { return make_double2(l * b.x, l * b.y); }
+__device__ __forceinline__ double2 lmul(double2 l, double2 b) { return Ops<double2>::mul(l, b); }
+__device__ __forceinline__ float2 lmul(float l, float2 b) { return make_float2(l * b.x, l * b.y); }
+__device__ __forceinline__ float2 lmul(float2 l, float2 b) { return Ops<float2>::mul(l, b); }
+__device__ __forceinline__ double lmul(double l, double b) { return l * b; }
+__device__ __forceinline__ float lmul(float l, float b) { return l * b; }
+
+// Solve L X = B in place (L lower triangular n x n of type TLt, B n x nrhs
+// of type TB; TLt may be the real type of TB).  smem (bytes): room for
+// NB*NB + TL*NB elements of TLt followed by NB*TL elements of TB.
+template <class TLt, class TB>
+__device__ void cta_trsm_lower(const TLt* L, int n, int ldl, TB* B, int nrhs, int ldb, char* smem) {
+  using OL = Ops<TLt>;
+  using OB = Ops<TB>;
+  using RB = typename OB::R;
+  TLt* D = reinterpret_cast<TLt*>(smem);
+  TLt* Lt = D + NB * NB;
+  TB* Xt = reinterpret_cast<TB*>(Lt + TL * NB);
+  const int tid = threadIdx.x;
+  for (int k0 = 0; k0 < n; k0 += NB) {
+    const int kb = min(NB, n - k0);
+    for (int e = tid; e < kb * kb; e += blockDim.x) {
+      int i = e / kb, j = e % kb;
+      D[i * NB + j] = (j <= i) ? L[(size_t)(k0 + i) * ldl + k0 + j] : OL::zero();
+    }
+    __syncthreads();
+    // diagonal solve: one thread per right-hand-side column
+    for (int c = tid; c < nrhs; c += blockDim.x) {
+      TB x[NB];
+      for (int r = 0; r < kb; ++r) {
+        TB v = B[(size_t)(k0 + r) * ldb + c];
+        for (int t = 0; t < r; ++t) v = OB::sub(v, lmul(D[r * NB + t], x[t]));
+        x[r] = OB::scale(v, RB(1) / OL::re(D[r * NB + r]));
+        B[(size_t)(k0 + r) * ldb + c] = x[r];
+      }
+    }
+    __syncthreads();
+    // update rows below: B[i][c] -= sum_t L[i][k0+t] X[k0+t][c]
+    const int k1 = k0 + kb;
+    for (int i0 = k1; i0 < n; i0 += TL) {
+      for (int e = tid; e < TL * NB; e += blockDim.x) {
+        int r = e / NB, t = e % NB;
+        Lt[e] = (i0 + r < n && t < kb) ? L[(size_t)(i0 + r) * ldl + k0 + t] : OL::zero();
+      }
+      for (int c0 = 0; c0 < nrhs; c0 += TL) {
+        for (int e = tid; e < NB * TL; e += blockDim.x) {
+          int t = e / TL, c = e % TL;
+          Xt[e] = (t < kb && c0 + c < nrhs) ? B[(size_t)(k0 + t) * ldb + c0 + c] : OB::zero();
+        }
+        __syncthreads();
+        for (int e = tid; e < TL * TL; e += blockDim.x) {
+          int r = e / TL, c = e % TL;
+          int i = i0 + r, cc = c0 + c;
+          if (i < n && cc < nrhs) {
+            TB acc = OB::zero();
+            for (int t = 0; t < kb; ++t) acc = OB::add(acc, lmul(Lt[r * NB + t], Xt[t * TL + c]));
+            size_t o = (size_t)i * ldb + cc;
+            B[o] = OB::sub(B[o], acc);
+          }
+        }
+        __syncthreads();
+      }
+    }
+  }
+  __syncthreads();
+}
+
+// Solve L^H X = B in place (backward substitution), complex L and B of the
+// same type T.  smem as cta_trsm_lower.
+template <class T>
+__device__ void cta_trsm_lower_h(const T* L, int n, int ldl, T* B, int nrhs, int ldb, char* smem) {
+  using O = Ops<T>;
+  using R = typename O::R;
+  T* D = reinterpret_cast<T*>(smem);
+  T* Lt = D + NB * NB;
+  T* Xt = Lt + TL * NB;
+  const int tid = threadIdx.x;
+  const int nblk = (n + NB - 1) / NB;
+  for (int kbI = nblk - 1; kbI >= 0; --kbI) {
+    const int k0 = kbI * NB;
+    const int kb = min(NB, n - k0);
+    for (int e = tid; e < kb * kb; e += blockDim.x) {
+      int i = e / kb, j = e % kb;
+      D[i * NB + j] = (j <= i) ? L[(size_t)(k0 + i) * ldl + k0 + j] : O::zero();
+    }
+    __syncthreads();
+    // diagonal: (L_kk^H) x = b  ->  x_r = (b_r - sum_{t>r} conj(D[t][r]) x_t) / D[r][r]
+    for (int c = tid; c < nrhs; c += blockDim.x) {
+      T x[NB];
+      for (int r = kb - 1; r >= 0; --r) {
+        T v = B[(size_t)(k0 + r) * ldb + c];
+        for (int t = r + 1; t < kb; ++t) v = O::sub(v, O::mul(O::conj(D[t * NB + r]), x[t]));
+        x[r] = O::scale(v, R(1) / O::re(D[r * NB + r]));
+        B[(size_t)(k0 + r) * ldb + c] = x[r];
+      }
+    }
+    __syncthreads();
+    // update rows above: B[i][c] -= sum_t conj(L[k0+t][i]) X[k0+t][c], i < k0
+    for (int i0 = 0; i0 < k0; i0 += TL) {
+      for (int e = tid; e < TL * NB; e += blockDim.x) {
+        int r = e / NB, t = e % NB;     // Lt[r][t] = conj(L[k0+t][i0+r])
+        Lt[e] = (i0 + r < k0 && t < kb) ? O::conj(L[(size_t)(k0 + t) * ldl + i0 + r]) : O::zero();
+      }
+      for (int c0 = 0; c0 < nrhs; c0 += TL) {
+        for (int e = tid; e < NB * TL; e += blockDim.x) {
+          int t = e / TL, c = e % TL;
+          Xt[e] = (t < kb && c0 + c < nrhs) ? B[(size_t)(k0 + t) * ldb + c0 + c] : O::zero();
+        }
+        __syncthreads();
+        for (int e = tid; e < TL * TL; e += blockDim.x) {
+          int r = e / TL, c = e % TL;
+          int i = i0 + r, cc = c0 + c;
+          if (i < k0 && cc < nrhs) {
+            T acc = O::zero();
+            for (int t = 0; t < kb; ++t) acc = O::fma(Lt[r * NB + t], Xt[t * TL + c], acc);
+            size_t o = (size_t)i * ldb + cc;
+            B[o] = O::sub(B[o], acc);
+          }
+        }
+        __syncthreads();
+      }
+    }
+  }
+  __syncthreads();
+}
+
+// C (m x n) = beta*C + alpha * op(A) * B where op(A) = A^H (A is k x m,
+// transA = true) or A (m x k).  B is k x n.  All of type T (alpha real).
+// smem: 2*TL*NB elements of T.
+template <class T>
+__device__ void cta_gemm(bool transA, int m, int n, int k, typename Ops<T>::R alpha,
+                         const T* A, int lda, const T* B, int ldb,
+                         typename Ops<T>::R beta, T* C, int ldc, T* smem) {
+  using O = Ops<T>;
+  T* At = smem;               // At[r][t]: op(A)[i0+r][k0+t]
+  T* Bt = smem + TL * NB;     // Bt[t][c]: B[k0+t][j0+c]
+  const int tid = threadIdx.x;
+  constexpr int PER = TL * TL / CTA_THREADS;   // outputs per thread
+  for (int i0 = 0; i0 < m; i0 += TL) {
+    for (int j0 = 0; j0 < n; j0 += TL) {
+      T acc[PER];
+      for (int q = 0; q < PER; ++q) acc[q] = O::zero();
+      for (int k0 = 0; k0 < k; k0 += NB) {
+        for (int e = tid; e < TL * NB; e += blockDim.x) {
+          int r = e / NB, t = e % NB;
+          T v = O::zero();
+          if (i0 + r < m && k0 + t < k)
+            v = transA ? O::conj(A[(size_t)(k0 + t) * lda + i0 + r]) : A[(size_t)(i0 + r) * lda + k0 + t];
+          At[e] = v;
+        }
+        for (int e = tid; e < NB * TL; e += blockDim.x) {
+          int t = e / TL, c = e % TL;
+          Bt[e] = (k0 + t < k && j0 + c < n) ? B[(size_t)(k0 + t) * ldb + j0 + c] : O::zero();
+        }
+        __syncthreads();
+        for (int q = 0; q < PER; ++q) {
+          int e = tid + q * CTA_THREADS;
+          int r = e / TL, c = e % TL;
+          T a = acc[q];
+#pragma unroll 8
+          for (int t = 0; t < NB; ++t) a = O::fma(At[r * NB + t], Bt[t * TL + c], a);
+          acc[q] = a;
+        }
+        __syncthreads();
+      }
+      for (int q = 0; q < PER; ++q) {
+        int e = tid + q * CTA_THREADS;
+        int r = e / TL, c = e % TL;
+        int i = i0 + r, j = j0 + c;
+        if (i < m && j < n) {
+          size_t o = (size_t)i * ldc + j;
+          T v = O::scale(acc[q], alpha);
+          C[o] = (beta == 0) ? v : O::add(O::scale(C[o], beta), v);
+        }
+      }
+    }
+  }
+  __syncthreads();
+}
+
+}  // namespace dpgmg

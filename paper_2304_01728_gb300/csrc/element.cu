@@ -1,0 +1,444 @@
+// Batched element-local DPG work (Sec. 2 of the paper; the per-element steps
+// of the fine-grid assembly):
+//   k_elem_build     Gram G' (real form), enriched stiffness B' and load l'
+//   k_elem_potrf     G' = L L^T                      (real FP64 Cholesky)
+//   k_elem_trsm      W = L^-1 [B' | l']              (optimal test functions)
+//   k_elem_herk      K = W^H W = [B l]^* G^-1 [B l]  (DPG element matrix + load)
+//   k_elem_condense  static condensation of the 4p^3 field DOFs (Sec. 1.2):
+//                    K_c = K_tt - K_tf K_ff^-1 K_ft, F_c = F_t - K_tf K_ff^-1 F_f
+// One CTA per element; elements are processed in chunks that bound the
+// scratch memory.  All arithmetic is FP64.
+#include <algorithm>
+#include <cmath>
+
+#include "common.cuh"
+#include "element_entries.cuh"
+#include "internal.h"
+
+namespace dpgmg {
+
+struct ElemArgs {
+  int n[3];
+  double x0[3], h[3];
+  double omega;
+  int p, nt, nf, ntr, m, nql;
+  const double* c;        // per element wavespeed
+  int src;
+  double sc[3], sw, sa, wd[3];
+  int mfm;
+  const double2* mfc;     // [4][m][m][m]
+  double bx0[3], bL[3];
+  const int4 *tf, *ff, *tr;
+  Tab1D tab;
+  const double *xq, *wq, *Lq;  // load rule and L_a at its points ([n1][nql])
+  int64_t e0;
+  double* G;
+  double2* W;
+  double2* K;
+  double2* Eout;
+  double2* Fc;
+  double2* Yrec;
+  int* info;
+};
+
+__device__ __forceinline__ double2 cexp_i(double phase) {
+  double s, c;
+  sincos(phase, &s, &c);
+  return make_double2(c, s);
+}
+
+// Manufactured polynomial (p_ex, u_ex) and gradients at a physical point.
+__device__ void mf_eval(const ElemArgs& a, const double x[3], double2 val[4], double2 grad[4][3]) {
+  const int m = a.mfm;
+  double L[3][8], dL[3][8];
+  for (int d = 0; d < 3; ++d) {
+    double X = (x[d] - a.bx0[d]) / a.bL[d];
+    double xi = 2.0 * X - 1.0;
+    L[d][0] = 1.0;
+    dL[d][0] = 0.0;
+    if (m > 1) { L[d][1] = xi; dL[d][1] = 1.0; }
+    for (int k = 1; k + 1 < m; ++k) {
+      L[d][k + 1] = ((2 * k + 1) * xi * L[d][k] - k * L[d][k - 1]) / (k + 1);
+      dL[d][k + 1] = dL[d][k - 1] + (2 * k + 1) * L[d][k];
+    }
+    for (int k = 0; k < m; ++k) dL[d][k] *= 2.0 / a.bL[d];
+  }
+  for (int comp = 0; comp < 4; ++comp) {
+    double2 v = make_double2(0, 0), g0 = v, g1 = v, g2 = v;
+    const double2* C = a.mfc + (size_t)comp * m * m * m;
+    for (int cc = 0; cc < m; ++cc)
+      for (int b = 0; b < m; ++b)
+        for (int aa = 0; aa < m; ++aa) {
+          double2 co = C[(cc * m + b) * m + aa];
+          double t0 = L[0][aa] * L[1][b] * L[2][cc];
+          double t1 = dL[0][aa] * L[1][b] * L[2][cc];
+          double t2 = L[0][aa] * dL[1][b] * L[2][cc];
+          double t3 = L[0][aa] * L[1][b] * dL[2][cc];
+          v.x += co.x * t0; v.y += co.y * t0;
+          g0.x += co.x * t1; g0.y += co.y * t1;
+          g1.x += co.x * t2; g1.y += co.y * t2;
+          g2.x += co.x * t3; g2.y += co.y * t3;
+        }
+    val[comp] = v;
+    grad[comp][0] = g0;
+    grad[comp][1] = g1;
+    grad[comp][2] = g2;
+  }
+}
+
+// Volume data f, g at a point (Sec. 2 strong form with sources).
+__device__ void src_volume(const ElemArgs& a, double c, const double x[3], double2& f, double2 g[3]) {
+  f = make_double2(0, 0);
+  g[0] = g[1] = g[2] = make_double2(0, 0);
+  if (a.src == DPGMG_SRC_GAUSSIAN) {
+    double r2 = 0;
+    for (int d = 0; d < 3; ++d) r2 += (x[d] - a.sc[d]) * (x[d] - a.sc[d]);
+    f.x = a.sa * exp(-r2 / (2.0 * a.sw * a.sw));
+  } else if (a.src == DPGMG_SRC_MANUFACTURED) {
+    double2 val[4], gr[4][3];
+    mf_eval(a, x, val, gr);
+    double bt = a.omega / (c * c);
+    // f = i w c^-2 p + div u ; g = i w u + grad p
+    f.x = -bt * val[0].y + gr[1][0].x + gr[2][1].x + gr[3][2].x;
+    f.y = bt * val[0].x + gr[1][0].y + gr[2][1].y + gr[3][2].y;
+    for (int d = 0; d < 3; ++d) {
+      g[d].x = -a.omega * val[1 + d].y + gr[0][d].x;
+      g[d].y = a.omega * val[1 + d].x + gr[0][d].y;
+    }
+  }
+}
+
+// Impedance load u0 at a boundary point with outward normal n.
+__device__ double2 src_u0(const ElemArgs& a, double c, const double x[3], const double nrm[3]) {
+  if (a.src == DPGMG_SRC_PLANE_WAVE) {
+    double dx = a.wd[0] * x[0] + a.wd[1] * x[1] + a.wd[2] * x[2];
+    double dn = a.wd[0] * nrm[0] + a.wd[1] * nrm[1] + a.wd[2] * nrm[2];
+    double2 pv = cexp_i(-a.omega * dx / c);
+    double s = (1.0 - dn) / c;
+    return make_double2(s * pv.x, s * pv.y);
+  }
+  if (a.src == DPGMG_SRC_MANUFACTURED) {
+    double2 val[4], gr[4][3];
+    mf_eval(a, x, val, gr);
+    double2 r = make_double2(val[0].x / c, val[0].y / c);
+    for (int d = 0; d < 3; ++d) {
+      r.x -= val[1 + d].x * nrm[d];
+      r.y -= val[1 + d].y * nrm[d];
+    }
+    return r;
+  }
+  return make_double2(0, 0);
+}
+
+__device__ __forceinline__ void elem_geom(const ElemArgs& a, int64_t e, int ec[3], double corner[3], int& bmask) {
+  ec[0] = (int)(e % a.n[0]);
+  ec[1] = (int)((e / a.n[0]) % a.n[1]);
+  ec[2] = (int)(e / ((int64_t)a.n[0] * a.n[1]));
+  bmask = 0;
+  for (int d = 0; d < 3; ++d) {
+    corner[d] = a.x0[d] + ec[d] * a.h[d];
+    if (ec[d] == 0) bmask |= 1 << (2 * d);
+    if (ec[d] == a.n[d] - 1) bmask |= 1 << (2 * d + 1);
+  }
+}
+
+__global__ void __launch_bounds__(CTA_THREADS) k_elem_build(ElemArgs a) {
+  extern __shared__ double2 sh2[];
+  const int64_t le = blockIdx.x;
+  const int64_t e = a.e0 + le;
+  int ec[3], bmask;
+  double corner[3];
+  elem_geom(a, e, ec, corner, bmask);
+  const double c = a.c[e];
+  const double beta = a.omega / (c * c);
+  const int nt = a.nt, m = a.m, ldw = m + 1;
+  double* G = a.G + le * (size_t)nt * nt;
+  double2* W = a.W + le * (size_t)nt * ldw;
+  for (int64_t q = threadIdx.x; q < (int64_t)nt * nt; q += blockDim.x) {
+    int i = (int)(q / nt), j = (int)(q % nt);
+    G[q] = (j <= i) ? gram_entry(a.tab, a.tf[i], a.tf[j], a.h, beta, a.omega) : 0.0;
+  }
+  for (int64_t q = threadIdx.x; q < (int64_t)nt * m; q += blockDim.x) {
+    int i = (int)(q / m), j = (int)(q % m);
+    double2 v = (j < a.nf) ? bfield_entry(a.tab, a.tf[i], a.ff[j], a.h, beta, a.omega)
+                           : btrace_entry(a.tab, a.tf[i], a.tr[j - a.nf], a.h, 1.0 / c, bmask);
+    W[(size_t)i * ldw + j] = v;
+  }
+  // ---- load l' (v rows scaled by -i)
+  const int nq = a.nql, nq3 = nq * nq * nq;
+  const int n1 = a.tab.n1;
+  double2* fv = sh2;                 // [nq3]
+  double2* gv = sh2 + nq3;           // [3][nq3]
+  const double J = a.h[0] * a.h[1] * a.h[2];
+  for (int q = threadIdx.x; q < nq3; q += blockDim.x) {
+    int qa = q % nq, qb = (q / nq) % nq, qc = q / (nq * nq);
+    double x[3] = {corner[0] + a.xq[qa] * a.h[0], corner[1] + a.xq[qb] * a.h[1], corner[2] + a.xq[qc] * a.h[2]};
+    double2 f, g[3];
+    src_volume(a, c, x, f, g);
+    double w = a.wq[qa] * a.wq[qb] * a.wq[qc] * J;
+    fv[q] = make_double2(f.x * w, f.y * w);
+    for (int d = 0; d < 3; ++d) gv[d * nq3 + q] = make_double2(g[d].x * w, g[d].y * w);
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < nt; i += blockDim.x) {
+    int4 t = a.tf[i];
+    double2 acc = make_double2(0, 0);
+    const double2* src = (t.x == 3) ? fv : gv + (size_t)t.x * nq3;
+    for (int q = 0; q < nq3; ++q) {
+      int qa = q % nq, qb = (q / nq) % nq, qc = q / (nq * nq);
+      double bv = a.Lq[t.y * nq + qa] * a.Lq[t.z * nq + qb] * a.Lq[t.w * nq + qc];
+      acc.x += src[q].x * bv;
+      acc.y += src[q].y * bv;
+    }
+    if (t.x != 3) acc = make_double2(acc.y, -acc.x);
+    W[(size_t)i * ldw + m] = acc;
+  }
+  __syncthreads();
+  // boundary faces: <u0, q>
+  if (a.src != DPGMG_SRC_GAUSSIAN) {
+    for (int d = 0; d < 3; ++d)
+      for (int s = 0; s < 2; ++s) {
+        if (!((bmask >> (2 * d + s)) & 1)) continue;
+        int t1 = d == 0 ? 1 : 0, t2 = d == 2 ? 1 : 2;
+        for (int q = threadIdx.x; q < nq * nq; q += blockDim.x) {
+          int qa = q % nq, qb = q / nq;
+          double x[3];
+          x[d] = corner[d] + s * a.h[d];
+          x[t1] = corner[t1] + a.xq[qa] * a.h[t1];
+          x[t2] = corner[t2] + a.xq[qb] * a.h[t2];
+          double nrm[3] = {0, 0, 0};
+          nrm[d] = s ? 1.0 : -1.0;
+          double2 u = src_u0(a, c, x, nrm);
+          double w = a.wq[qa] * a.wq[qb] * a.h[t1] * a.h[t2];
+          fv[q] = make_double2(u.x * w, u.y * w);
+        }
+        __syncthreads();
+        for (int i = threadIdx.x; i < nt; i += blockDim.x) {
+          int4 t = a.tf[i];
+          if (t.x != 3) continue;
+          int id[3] = {t.y, t.z, t.w};
+          double endv = (s ? 1.0 : ((id[d] & 1) ? -1.0 : 1.0));
+          double2 acc = make_double2(0, 0);
+          for (int q = 0; q < nq * nq; ++q) {
+            int qa = q % nq, qb = q / nq;
+            double bv = endv * a.Lq[id[t1] * nq + qa] * a.Lq[id[t2] * nq + qb];
+            acc.x += fv[q].x * bv;
+            acc.y += fv[q].y * bv;
+          }
+          double2& o = W[(size_t)i * ldw + m];
+          o.x += acc.x;
+          o.y += acc.y;
+        }
+        __syncthreads();
+      }
+  }
+  (void)n1;
+}
+
+__global__ void __launch_bounds__(CTA_THREADS) k_elem_potrf(ElemArgs a) {
+  extern __shared__ double sh[];
+  const int64_t le = blockIdx.x;
+  double* G = a.G + le * (size_t)a.nt * a.nt;
+  int info = cta_potrf<double>(G, a.nt, a.nt, sh);
+  if (threadIdx.x == 0 && info) atomicOr(a.info, 1);
+}
+
+__global__ void __launch_bounds__(CTA_THREADS) k_elem_trsm(ElemArgs a) {
+  extern __shared__ char shc[];
+  const int64_t le = blockIdx.x;
+  const double* G = a.G + le * (size_t)a.nt * a.nt;
+  double2* W = a.W + le * (size_t)a.nt * (a.m + 1);
+  cta_trsm_lower<double, double2>(G, a.nt, a.nt, W, a.m + 1, a.m + 1, shc);
+}
+
+__global__ void __launch_bounds__(CTA_THREADS) k_elem_herk(ElemArgs a) {
+  extern __shared__ double2 sh2[];
+  const int64_t le = blockIdx.x;
+  const int ld = a.m + 1;
+  const double2* W = a.W + le * (size_t)a.nt * ld;
+  double2* K = a.K + le * (size_t)ld * ld;
+  cta_gemm<double2>(true, ld, ld, a.nt, 1.0, W, ld, W, ld, 0.0, K, ld, sh2);
+}
+
+__global__ void __launch_bounds__(CTA_THREADS) k_elem_condense(ElemArgs a) {
+  extern __shared__ double2 sh2[];
+  const int64_t le = blockIdx.x;
+  const int64_t e = a.e0 + le;
+  const int ld = a.m + 1, nf = a.nf, ntr = a.ntr;
+  double2* K = a.K + le * (size_t)ld * ld;
+  int info = cta_potrf<double2>(K, nf, ld, sh2);
+  if (threadIdx.x == 0 && info) atomicOr(a.info, 2);
+  cta_trsm_lower<double2, double2>(K, nf, ld, K + nf, ntr + 1, ld, reinterpret_cast<char*>(sh2));
+  cta_trsm_lower_h<double2>(K, nf, ld, K + nf, ntr + 1, ld, reinterpret_cast<char*>(sh2));
+  cta_gemm<double2>(false, ntr, ntr + 1, nf, -1.0, K + (size_t)nf * ld, ld, K + nf, ld, 1.0,
+                    K + (size_t)nf * ld + nf, ld, sh2);
+  double2* E = a.Eout + e * (size_t)ntr * ntr;
+  for (int q = threadIdx.x; q < ntr * ntr; q += blockDim.x) {
+    int i = q / ntr, j = q % ntr;
+    E[q] = K[(size_t)(nf + i) * ld + nf + j];
+  }
+  for (int i = threadIdx.x; i < ntr; i += blockDim.x) a.Fc[e * ntr + i] = K[(size_t)(nf + i) * ld + a.m];
+  double2* Y = a.Yrec + e * (size_t)nf * (ntr + 1);
+  for (int q = threadIdx.x; q < nf * (ntr + 1); q += blockDim.x) {
+    int i = q / (ntr + 1), j = q % (ntr + 1);
+    Y[q] = K[(size_t)i * ld + nf + j];
+  }
+}
+
+// fields[e][i] = Y_F[i] - sum_j Y_K[i][j] x[dofs[e][j]]
+__global__ void k_recover(const double2* Yrec, const int64_t* dofs, const double2* x, double2* out,
+                          int64_t nelem, int nf, int ntr) {
+  int64_t gid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (gid >= nelem * nf) return;
+  int64_t e = gid / nf;
+  int i = (int)(gid % nf);
+  const double2* Y = Yrec + (e * nf + i) * (size_t)(ntr + 1);
+  double2 acc = Y[ntr];
+  for (int j = 0; j < ntr; ++j) {
+    int64_t g = dofs[e * ntr + j];
+    if (g < 0) continue;
+    double2 y = Y[j], v = x[g];
+    acc.x -= y.x * v.x - y.y * v.y;
+    acc.y -= y.x * v.y + y.y * v.x;
+  }
+  out[gid] = acc;
+}
+
+// ------------------------------------------------------------------- host
+static void make_descriptors(int p, std::vector<int4>& tf, std::vector<int4>& ff, std::vector<int4>& tr) {
+  const int pt = p + 1;
+  tf.clear();
+  ff.clear();
+  tr.clear();
+  for (int c = 0; c <= pt; ++c)
+    for (int b = 0; b <= pt; ++b)
+      for (int a = 0; a <= pt; ++a) tf.push_back(make_int4(3, a, b, c));
+  for (int d = 0; d < 3; ++d) {
+    int ext[3];
+    for (int e = 0; e < 3; ++e) ext[e] = (e == d) ? pt : pt - 1;
+    for (int c = 0; c <= ext[2]; ++c)
+      for (int b = 0; b <= ext[1]; ++b)
+        for (int a = 0; a <= ext[0]; ++a) tf.push_back(make_int4(d, a, b, c));
+  }
+  for (int comp = 0; comp < 4; ++comp)
+    for (int c = 0; c < p; ++c)
+      for (int b = 0; b < p; ++b)
+        for (int a = 0; a < p; ++a) ff.push_back(make_int4(comp, a, b, c));
+  for (const LocFn& f : local_trace_functions(p))
+    tr.push_back(f.type == 0 ? make_int4(0, f.idx[0], f.idx[1], f.idx[2])
+                             : make_int4(1, f.d, f.s, f.a + 256 * f.b));
+}
+
+static size_t smem_bytes_dense(size_t elt) { return (size_t)(NB * NB + 2 * TL * NB) * elt + 64; }
+
+void element_stage(SystemImpl& S, cudaStream_t st) {
+  Level& L = S.levels.back();
+  const MeshL& m = L.mesh;
+  const int p = m.p;
+  std::vector<int4> tf, ff, tr;
+  make_descriptors(p, tf, ff, tr);
+  Tables1D T = make_tables(p);
+  Alloc& A = S.mem;
+
+  ElemArgs a{};
+  for (int d = 0; d < 3; ++d) {
+    a.n[d] = m.n[d];
+    a.x0[d] = m.x0[d];
+    a.h[d] = m.h[d];
+    a.sc[d] = S.pb.src_center[d];
+    a.bx0[d] = S.pb.x0[d];
+    a.bL[d] = S.pb.x1[d] - S.pb.x0[d];
+  }
+  double dn = std::sqrt(S.pb.wave_dir[0] * S.pb.wave_dir[0] + S.pb.wave_dir[1] * S.pb.wave_dir[1] +
+                        S.pb.wave_dir[2] * S.pb.wave_dir[2]);
+  for (int d = 0; d < 3; ++d) a.wd[d] = dn > 0 ? S.pb.wave_dir[d] / dn : 0.0;
+  a.omega = S.pb.omega;
+  a.p = p;
+  a.nt = (int)tf.size();
+  a.nf = (int)ff.size();
+  a.ntr = (int)tr.size();
+  a.m = a.nf + a.ntr;
+  a.nql = T.nql;
+  a.src = S.pb.source;
+  a.sw = S.pb.src_width;
+  a.sa = S.pb.src_amp;
+  a.mfm = S.pb.mf_order;
+  a.c = upload(A, S.wavespeed, st);
+  std::vector<double2> mfc(S.mf_coeffs.size() / 2);
+  for (size_t i = 0; i < mfc.size(); ++i) mfc[i] = make_double2(S.mf_coeffs[2 * i], S.mf_coeffs[2 * i + 1]);
+  a.mfc = upload(A, mfc, st);
+  a.tf = upload(A, tf, st);
+  a.ff = upload(A, ff, st);
+  a.tr = upload(A, tr, st);
+  a.tab.p = p;
+  a.tab.pt = p + 1;
+  a.tab.n1 = p + 2;
+  a.tab.Mleg = upload(A, T.Mleg, st);
+  a.tab.D = upload(A, T.D, st);
+  a.tab.S = upload(A, T.S, st);
+  a.tab.Phi = upload(A, T.Phi, st);
+  a.xq = upload(A, T.xq, st);
+  a.wq = upload(A, T.wq, st);
+  a.Lq = upload(A, T.Lq, st);
+  a.info = A.arr<int>(1);
+  DPG_CUDA(cudaMemsetAsync(a.info, 0, sizeof(int), st));
+
+  const int64_t nel = m.nelem;
+  S.nelem = nel;
+  S.nf = a.nf;
+  S.ntr = a.ntr;
+  L.nloc = a.ntr;
+  L.E = A.arr<double2>((size_t)nel * a.ntr * a.ntr);
+  S.Fc = A.arr<double2>((size_t)nel * a.ntr);
+  S.Yrec = A.arr<double2>((size_t)nel * a.nf * (a.ntr + 1));
+  a.Eout = L.E;
+  a.Fc = S.Fc;
+  a.Yrec = S.Yrec;
+
+  // scratch per element: G (nt^2 doubles), W (nt (m+1)), K ((m+1)^2)
+  const size_t per = (size_t)a.nt * a.nt * 8 + (size_t)a.nt * (a.m + 1) * 16 + (size_t)(a.m + 1) * (a.m + 1) * 16;
+  size_t avail = std::max<size_t>(A.budget > A.used ? A.budget - A.used : 0, 0);
+  size_t scratch_cap = std::min<size_t>((size_t)8 << 30, avail / 3);
+  int64_t chunk = std::max<int64_t>(1, std::min<int64_t>(nel, (int64_t)(scratch_cap / per)));
+  chunk = std::min<int64_t>(chunk, 4096);
+  a.G = A.arr<double>((size_t)chunk * a.nt * a.nt);
+  a.W = A.arr<double2>((size_t)chunk * a.nt * (a.m + 1));
+  a.K = A.arr<double2>((size_t)chunk * (a.m + 1) * (a.m + 1));
+
+  const size_t sm_build = (size_t)4 * T.nql * T.nql * T.nql * sizeof(double2) + 64;
+  const size_t sm_real = smem_bytes_dense(8);
+  const size_t sm_cplx = smem_bytes_dense(16);
+  DPG_CUDA(cudaFuncSetAttribute(k_elem_build, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_build));
+  DPG_CUDA(cudaFuncSetAttribute(k_elem_potrf, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_real));
+  DPG_CUDA(cudaFuncSetAttribute(k_elem_trsm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_cplx));
+  DPG_CUDA(cudaFuncSetAttribute(k_elem_herk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_cplx));
+  DPG_CUDA(cudaFuncSetAttribute(k_elem_condense, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_cplx));
+  for (int64_t e0 = 0; e0 < nel; e0 += chunk) {
+    a.e0 = e0;
+    const int nb = (int)std::min<int64_t>(chunk, nel - e0);
+    k_elem_build<<<nb, CTA_THREADS, sm_build, st>>>(a);
+    DPG_CHECK_LAUNCH();
+    k_elem_potrf<<<nb, CTA_THREADS, sm_real, st>>>(a);
+    DPG_CHECK_LAUNCH();
+    k_elem_trsm<<<nb, CTA_THREADS, sm_cplx, st>>>(a);
+    DPG_CHECK_LAUNCH();
+    k_elem_herk<<<nb, CTA_THREADS, sm_cplx, st>>>(a);
+    DPG_CHECK_LAUNCH();
+    k_elem_condense<<<nb, CTA_THREADS, sm_cplx, st>>>(a);
+    DPG_CHECK_LAUNCH();
+  }
+  int info = 0;
+  DPG_CUDA(cudaMemcpyAsync(&info, a.info, sizeof(int), cudaMemcpyDeviceToHost, st));
+  DPG_CUDA(cudaStreamSynchronize(st));
+  if (info) throw Err{DPGMG_ERR_NOT_HPD, "element Gram or field block not positive definite"};
+}
+
+void recover_fields(SystemImpl& S, const double2* x, double2* fields, cudaStream_t st) {
+  const Level& L = S.levels.back();
+  int64_t n = S.nelem * S.nf;
+  k_recover<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(S.Yrec, L.dofs, x, fields, S.nelem, (int)S.nf,
+                                                        (int)S.ntr);
+  DPG_CHECK_LAUNCH();
+}
+
+}  // namespace dpgmg

@@ -1,0 +1,135 @@
+// Host-side mesh, DOF numbering and multigrid index structures.
+//
+// Structured axis-aligned hexahedral meshes; the global trace numbering and
+// element-local orderings documented in include/dpgmg.h.  Everything here is
+// integer bookkeeping plus the small 1D tables of the discretisation; the
+// arithmetic of the method runs in the CUDA kernels.
+#pragma once
+#include <cstdint>
+#include <vector>
+
+namespace dpgmg {
+
+// One element-local trace function.
+struct LocFn {
+  int type;        // 0 p-hat, 1 u-hat
+  int idx[3];      // p-hat: H^1 indices per axis
+  int d, s, a, b;  // u-hat: normal axis, side (0 low / 1 high), Legendre modes
+};
+
+std::vector<LocFn> local_trace_functions(int p);
+int n_trace_local(int p);
+
+struct MeshL {
+  int n[3] = {0, 0, 0};
+  int p = 0;
+  double x0[3], x1[3], h[3];
+  int64_t nV = 0, nEd[3], nFd[3], nFid[3], nE = 0, nF = 0, nFi = 0;
+  int64_t offE = 0, offF = 0, offU = 0, ndof = 0, nelem = 0;
+  // entity ids: [0,nV) vertices, [nV, nV+nE) edges, then faces (p-hat),
+  // then interior faces (u-hat)
+  int64_t entE = 0, entF = 0, entU = 0, nent = 0;
+  std::vector<LocFn> loc;
+
+  void init(const int nn[3], int pp, const double a[3], const double b[3]);
+  static int64_t lin(const int c[3], const int64_t ext[3]) {
+    return c[0] + ext[0] * (c[1] + ext[1] * (int64_t)c[2]);
+  }
+  void elem_coord(int64_t e, int c[3]) const {
+    c[0] = (int)(e % n[0]);
+    c[1] = (int)((e / n[0]) % n[1]);
+    c[2] = (int)(e / ((int64_t)n[0] * n[1]));
+  }
+  int64_t elem_index(const int c[3]) const {
+    return c[0] + (int64_t)n[0] * (c[1] + (int64_t)n[1] * c[2]);
+  }
+  int64_t vertex(const int c[3]) const;
+  int64_t edge(int d, const int c[3]) const;    // edge index (within all edges)
+  int64_t face(int d, const int c[3]) const;    // face index (within all faces)
+  int64_t iface(int d, const int c[3]) const;   // interior-face rank
+  bool boundary_face(int d, const int c[3]) const { return c[d] == 0 || c[d] == n[d]; }
+  // global DOF of each local trace function of element e (-1 if absent)
+  void elem_dofs(int64_t e, int64_t* out) const;
+  // entity id of each local trace function (-1 if absent)
+  void elem_entities(int64_t e, int64_t* out) const;
+  // first DOF and DOF count of entity E
+  void ent_range(int64_t E, int64_t* start, int* nd) const;
+  // entity of a DOF, and its centre in doubled coordinates (half-element units)
+  int64_t dof_entity(int64_t g) const;
+  void ent_center(int64_t E, int ctr[3]) const;
+  // entity at a doubled-coordinate centre (kind from parity); -1 if none
+  int64_t entity_at(const int ctr[3], bool uhat) const;
+};
+
+// Level plan from the finest (n, p) (p-coarsening to p_min, then halving n).
+struct LevelSpec { int n[3]; int p; int kind_below; };  // kind 0 none, 1 p, 2 h
+std::vector<LevelSpec> plan_levels(const int n[3], int p, int n_levels, int p_min);
+
+// Entity-shared CSR ("ECSR"): rows are grouped by entity; all rows of one
+// entity share one sorted list of column DOFs.  Values of row r of entity E
+// start at val_ptr[E] + (r - start(E)) * nnz_row(E).
+struct ECSRHost {
+  int64_t nrows = 0;                 // = ndof of the level (non-row DOFs have row_ent = -1)
+  std::vector<int32_t> row_ent;      // per DOF: compact row-entity index or -1
+  std::vector<int64_t> ent_start;    // per row entity: first DOF
+  std::vector<int32_t> ent_nd;       // per row entity: DOF count
+  std::vector<int64_t> col_ptr;      // per row entity (+1): offset in col_idx
+  std::vector<int32_t> col_idx;      // expanded column DOFs, sorted per entity
+  std::vector<int64_t> val_ptr;      // per row entity (+1): value offset
+  int64_t nnz() const { return val_ptr.empty() ? 0 : val_ptr.back(); }
+};
+// groups: for each super-element, the list of entity ids it touches.
+ECSRHost build_ecsr(const MeshL& m, const std::vector<std::vector<int64_t>>& groups);
+
+// Vertex patches of a level's smoothing space (rule R1): a DOF is in the
+// patch of coarse vertex w when every (macro-)element adjacent to its entity
+// has w as a corner.  H = coarse element width in doubled fine units (2 on p
+// levels, 4 on h levels); nco = coarse mesh extents.
+struct Patches {
+  std::vector<int64_t> ptr;    // per patch (+1)
+  std::vector<int32_t> dofs;   // patch-major DOF lists (sorted within a patch)
+  std::vector<int64_t> val_ptr;// per patch (+1): offset of the n_j x n_j block
+  std::vector<int64_t> slot_ptr; // per DOF (+1): CSR of the DOF's slots in dofs[]
+  std::vector<int32_t> slots;
+};
+Patches build_patches(const MeshL& m, const std::vector<char>& smask, int H, const int nco[3]);
+
+// Macro-grid structure of one h-transition (fine level m, coarse level mc).
+struct MacroHost {
+  int nS = 0, nI = 0, nloc_f = 0, nloc_c = 0;
+  std::vector<int32_t> child_map;   // [8][nloc_f] -> K-local index (S first, then I)
+  std::vector<int64_t> S_glob;      // [nK][nS] fine global DOF (-1 absent)
+  std::vector<int64_t> I_glob;      // [nK][nI]
+  std::vector<double> IK;           // [nS][nloc_c] natural inclusion (real)
+  // CSR of P (fine rows) and P^T (coarse rows)
+  std::vector<int64_t> P_ptr, PT_ptr;
+  std::vector<int32_t> P_col, PT_col;
+  std::vector<double> P_val, PT_val;
+  // per fine DOF: CSR of the (K, a) slots where it is an S DOF
+  std::vector<int64_t> sslot_ptr;
+  std::vector<int32_t> sslots;
+  std::vector<char> smask;          // fine DOF on the coarse skeleton
+  std::vector<std::vector<int64_t>> groups;  // macro element -> fine entities (for ECSR)
+};
+MacroHost build_macro(const MeshL& mf, const MeshL& mc);
+
+// p-transition: positions of order p-1 local functions in the order-p list,
+// and the coarse -> fine DOF injection.
+void p_selection(int p, std::vector<int32_t>& sel);
+void p_injection(const MeshL& mf, const MeshL& mc, std::vector<int32_t>& inj);
+
+// 1D tables for the element kernels (enriched test order pt = p + 1).
+struct Tables1D {
+  int p, pt, nql;
+  std::vector<double> Mleg;   // [pt+1] int L_a^2 = 1/(2a+1)
+  std::vector<double> D;      // [pt+1][pt+1] int L_a' L_b
+  std::vector<double> S;      // [pt+1][pt+1] int L_a' L_b'
+  std::vector<double> Phi;    // [p+1][pt+1] int phi_k L_b
+  std::vector<double> phi_end;// [p+1][2] phi_k(0), phi_k(1)
+  std::vector<double> xq, wq; // load rule: nql Gauss points / weights on [0,1]
+  std::vector<double> Lq;     // [pt+1][nql] L_a at load points
+};
+Tables1D make_tables(int p);
+void gauss_legendre01(int n, std::vector<double>& x, std::vector<double>& w);
+
+}  // namespace dpgmg

@@ -1,0 +1,146 @@
+// Internal declarations shared by the CUDA translation units.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/dpgmg.h"
+#include "host_mesh.h"
+
+namespace dpgmg {
+
+// ----------------------------------------------------------- error plumbing
+struct Err {
+  int code;
+  std::string msg;
+};
+void set_last_error(const std::string& m);
+#define DPG_CUDA(call)                                                                 \
+  do {                                                                                 \
+    cudaError_t e_ = (call);                                                           \
+    if (e_ != cudaSuccess)                                                             \
+      throw ::dpgmg::Err{DPGMG_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)}; \
+  } while (0)
+#define DPG_CHECK_LAUNCH() DPG_CUDA(cudaGetLastError())
+
+// Device allocation tracked against the handle's budget.
+struct Alloc {
+  size_t budget = 0, used = 0, peak = 0;
+  std::vector<void*> ptrs;
+  void* get(size_t bytes);
+  template <class T> T* arr(size_t n) { return reinterpret_cast<T*>(get(n * sizeof(T) + 16)); }
+  void free_all();
+  ~Alloc() { free_all(); }
+};
+
+template <class T> T* upload(Alloc& A, const std::vector<T>& h, cudaStream_t s) {
+  T* d = A.arr<T>(h.size() ? h.size() : 1);
+  if (!h.empty()) DPG_CUDA(cudaMemcpyAsync(d, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice, s));
+  return d;
+}
+
+// ----------------------------------------------------------- device structs
+struct ECSRDev {
+  int64_t nrows = 0, nent = 0, nnz = 0, max_nnz_row = 0;
+  int32_t* row_ent = nullptr;
+  int64_t* ent_start = nullptr;
+  int32_t* ent_nd = nullptr;
+  int64_t* col_ptr = nullptr;
+  int32_t* col_idx = nullptr;
+  int64_t* val_ptr = nullptr;
+  double2* v64 = nullptr;
+  float2* v32 = nullptr;
+};
+
+struct PatchDev {
+  int64_t np = 0, nslots = 0, nvals = 0, max_n = 0, sum_sq = 0;
+  int64_t* ptr = nullptr;
+  int32_t* dofs = nullptr;
+  int64_t* val_ptr = nullptr;
+  int64_t* slot_ptr = nullptr;
+  int32_t* slots = nullptr;
+  double2* inv64 = nullptr;
+  float2* inv32 = nullptr;
+};
+
+struct Level {
+  MeshL mesh;
+  int kind = 0;              // transition to the level below: 0 none, 1 p, 2 h
+  int nloc = 0;
+  double2* E = nullptr;      // element matrices [nelem][nloc][nloc]
+  int64_t* dofs = nullptr;   // [nelem][nloc]
+  ECSRDev A;                 // smoothing operator (A_l or macro M_l)
+  PatchDev P;
+  double theta = 0.0;
+  int64_t n_smooth = 0;
+  // p transition
+  int32_t* inj = nullptr;
+  // h transition
+  int nS = 0, nI = 0;
+  int64_t nK = 0;
+  int64_t* S_glob = nullptr;
+  int64_t* I_glob = nullptr;
+  double2* Y64 = nullptr;    // [nK][nI][nS]   A_II^-1 A_IS
+  double2* Ai64 = nullptr;   // [nK][nI][nI]   A_II^-1
+  float2* Y32 = nullptr;
+  float2* Ai32 = nullptr;
+  int64_t *P_ptr = nullptr, *PT_ptr = nullptr, *sslot_ptr = nullptr;
+  int32_t *P_col = nullptr, *PT_col = nullptr, *sslots = nullptr;
+  double *P_val = nullptr, *PT_val = nullptr;
+  char* smask = nullptr;
+  // coarsest: dense Cholesky factor
+  int64_t N0 = 0;
+  double2* C64 = nullptr;
+  float2* C32 = nullptr;
+};
+
+struct Workspace;   // V-cycle work vectors (per precision)
+
+struct SystemImpl {
+  dpgmg_problem pb;
+  dpgmg_opts op;
+  std::vector<double> wavespeed;
+  std::vector<double> mf_coeffs;
+  std::vector<Level> levels;     // 0 = coarsest
+  Alloc mem;
+  int64_t nf = 0, ntr = 0, nelem = 0;
+  double2* Yrec = nullptr;       // finest: [nelem][nf][ntr+1] K_ff^-1 [K_ft | F_f]
+  double2* Fc = nullptr;         // finest: [nelem][ntr] condensed loads
+  double2* b = nullptr;          // assembled right-hand side
+  double t_setup_ms = 0.0;
+  int64_t bytes_per_iter = 0;
+  void* ws = nullptr;            // solver workspace
+  int coarse_blocks = 0;
+};
+
+struct HandleImpl {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  size_t budget = 0;
+  size_t used = 0;
+};
+
+// ----------------------------------------------------------- stage entry points
+// element.cu
+void element_stage(SystemImpl& S, cudaStream_t st);
+void recover_fields(SystemImpl& S, const double2* x, double2* fields, cudaStream_t st);
+// level.cu
+void assemble_ecsr(Alloc& A, const MeshL& m, const ECSRHost& H, ECSRDev& D, cudaStream_t st);
+void ecsr_add_elements(ECSRDev& D, const double2* E, const int64_t* dofs, int64_t nel, int nloc,
+                       cudaStream_t st);
+void build_hierarchy(SystemImpl& S, cudaStream_t st);
+void assemble_rhs(SystemImpl& S, cudaStream_t st);
+// solve.cu
+int pcg_solve(SystemImpl& S, cudaStream_t st, double2* x, dpgmg_stats* stats);
+void apply_op(SystemImpl& S, int op, int level, const double2* x, double2* y, cudaStream_t st);
+void ensure_workspace(SystemImpl& S, cudaStream_t st);
+void free_workspace(SystemImpl& S);
+void spmv64(const ECSRDev& A, const double2* x, double2* y, cudaStream_t st);
+void estimate_theta(SystemImpl& S, int level, cudaStream_t st);
+void smooth_apply64(const Level& L, const double2* r, double2* y, double theta, double2* scratch,
+                    cudaStream_t st);
+
+}  // namespace dpgmg

@@ -1,0 +1,505 @@
+// DPG-MG hierarchy construction on the device (Sec. 3 of the paper):
+//   * assembly of element matrices into the entity-shared CSR operator,
+//   * p-transitions: restricted coarse operator = principal submatrix,
+//   * h-transitions: macro-grid condensation per coarse element
+//       M^K = A^K_SS - A^K_SI (A^K_II)^-1 A^K_IS     (stage one, "Prolongation")
+//     and coarse operator by restriction A_c^K = I_K^T M^K I_K with the natural
+//     inclusion I_K (stage two; "Alternative construction of coarse-grid
+//     operators", restrict),
+//   * vertex-patch blocks of the smoothing operator and their inverses
+//     ("V-cycle and smoother"),
+//   * the dense Cholesky factor of the coarsest operator (the paper solves its
+//     initial mesh directly, Sec. 4 list).
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+
+#include "common.cuh"
+#include "internal.h"
+
+namespace dpgmg {
+
+// ------------------------------------------------------------ ECSR assembly
+void assemble_ecsr(Alloc& A, const MeshL& m, const ECSRHost& H, ECSRDev& D, cudaStream_t st) {
+  D.nrows = H.nrows;
+  D.nent = (int64_t)H.ent_start.size();
+  D.nnz = H.nnz();
+  D.row_ent = upload(A, H.row_ent, st);
+  D.ent_start = upload(A, H.ent_start, st);
+  D.ent_nd = upload(A, H.ent_nd, st);
+  D.col_ptr = upload(A, H.col_ptr, st);
+  D.col_idx = upload(A, H.col_idx, st);
+  D.val_ptr = upload(A, H.val_ptr, st);
+  D.max_nnz_row = 0;
+  for (int64_t E = 0; E < D.nent; ++E) D.max_nnz_row = std::max(D.max_nnz_row, H.col_ptr[E + 1] - H.col_ptr[E]);
+  D.v64 = A.arr<double2>((size_t)D.nnz);
+  DPG_CUDA(cudaMemsetAsync(D.v64, 0, (size_t)D.nnz * sizeof(double2), st));
+  (void)m;
+}
+
+__device__ __forceinline__ int64_t ecsr_find(const ECSRDev& A, int64_t row, int64_t col) {
+  int32_t E = A.row_ent[row];
+  if (E < 0) return -1;
+  int64_t c0 = A.col_ptr[E], c1 = A.col_ptr[E + 1];
+  int64_t lo = c0, hi = c1;
+  while (lo < hi) {
+    int64_t mid = (lo + hi) >> 1;
+    if (A.col_idx[mid] < col) lo = mid + 1;
+    else hi = mid;
+  }
+  if (lo >= c1 || A.col_idx[lo] != col) return -1;
+  int64_t r = row - A.ent_start[E];
+  return A.val_ptr[E] + r * (c1 - c0) + (lo - c0);
+}
+
+__global__ void k_ecsr_add(ECSRDev A, const double2* E, const int64_t* dofs, int64_t nel, int nloc) {
+  const int64_t e = blockIdx.x;
+  const double2* Ee = E + e * (size_t)nloc * nloc;
+  const int64_t* g = dofs + e * nloc;
+  for (int q = threadIdx.x; q < nloc * nloc; q += blockDim.x) {
+    int i = q / nloc, j = q % nloc;
+    int64_t gi = g[i], gj = g[j];
+    if (gi < 0 || gj < 0) continue;
+    int64_t pos = ecsr_find(A, gi, gj);
+    if (pos < 0) continue;
+    double2 v = Ee[q];
+    atomicAdd(&A.v64[pos].x, v.x);
+    atomicAdd(&A.v64[pos].y, v.y);
+  }
+}
+
+void ecsr_add_elements(ECSRDev& D, const double2* E, const int64_t* dofs, int64_t nel, int nloc, cudaStream_t st) {
+  if (nel == 0) return;
+  k_ecsr_add<<<(unsigned)nel, 256, 0, st>>>(D, E, dofs, nel, nloc);
+  DPG_CHECK_LAUNCH();
+}
+
+static std::vector<std::vector<int64_t>> element_groups(const MeshL& m) {
+  std::vector<std::vector<int64_t>> g(m.nelem);
+  std::vector<int64_t> ent(m.loc.size());
+  for (int64_t e = 0; e < m.nelem; ++e) {
+    m.elem_entities(e, ent.data());
+    for (int64_t E : ent)
+      if (E >= 0) g[e].push_back(E);
+    std::sort(g[e].begin(), g[e].end());
+    g[e].erase(std::unique(g[e].begin(), g[e].end()), g[e].end());
+  }
+  return g;
+}
+
+static int64_t* upload_dofs(Alloc& A, const MeshL& m, cudaStream_t st) {
+  std::vector<int64_t> d((size_t)m.nelem * m.loc.size());
+  for (int64_t e = 0; e < m.nelem; ++e) m.elem_dofs(e, d.data() + e * m.loc.size());
+  return upload(A, d, st);
+}
+
+// ------------------------------------------------------------ p-transition
+__global__ void k_p_restrict(const double2* Ef, double2* Ec, const int32_t* sel, int nf, int nc) {
+  const int64_t e = blockIdx.x;
+  for (int q = threadIdx.x; q < nc * nc; q += blockDim.x) {
+    int i = q / nc, j = q % nc;
+    Ec[e * (size_t)nc * nc + q] = Ef[e * (size_t)nf * nf + (size_t)sel[i] * nf + sel[j]];
+  }
+}
+
+// ------------------------------------------------------------ h-transition
+struct MacroArgs {
+  int nS, nI, nlf, nlc;
+  int64_t K0;
+  const double2* Ef;          // fine element matrices
+  const int64_t* fdofs;       // fine element DOFs
+  const int32_t* child_map;   // [8][nlf]
+  int nf0, nf1;               // fine mesh extents x, y
+  int nc0, nc1;               // coarse mesh extents x, y
+  const double2* IK;          // [nS][nlc] (real values)
+  double2* AK;                // scratch [chunk][(nS+nI)^2]
+  double2* T1;                // scratch [chunk][nS][nlc]
+  double2* MK;                // out [chunk][nS][nS]
+  double2* Y;                 // out [nK][nI][nS]
+  double2* Ai;                // out [nK][nI][nI]
+  double2* Ec;                // out [nK][nlc][nlc]
+  int* info;
+};
+
+__global__ void __launch_bounds__(CTA_THREADS) k_macro(MacroArgs a) {
+  extern __shared__ double2 sh2[];
+  const int64_t lk = blockIdx.x;
+  const int64_t K = a.K0 + lk;
+  const int nS = a.nS, nI = a.nI, n = nS + nI;
+  double2* AK = a.AK + lk * (size_t)n * n;
+  for (int64_t q = threadIdx.x; q < (int64_t)n * n; q += blockDim.x) AK[q] = make_double2(0, 0);
+  __syncthreads();
+  int kc[3];
+  kc[0] = (int)(K % a.nc0);
+  kc[1] = (int)((K / a.nc0) % a.nc1);
+  kc[2] = (int)(K / ((int64_t)a.nc0 * a.nc1));
+  for (int o = 0; o < 8; ++o) {
+    int fc[3] = {2 * kc[0] + (o & 1), 2 * kc[1] + ((o >> 1) & 1), 2 * kc[2] + ((o >> 2) & 1)};
+    int64_t fe = fc[0] + (int64_t)a.nf0 * (fc[1] + (int64_t)a.nf1 * fc[2]);
+    const double2* E = a.Ef + fe * (size_t)a.nlf * a.nlf;
+    const int64_t* g = a.fdofs + fe * a.nlf;
+    const int32_t* cm = a.child_map + o * a.nlf;
+    for (int q = threadIdx.x; q < a.nlf * a.nlf; q += blockDim.x) {
+      int i = q / a.nlf, j = q % a.nlf;
+      if (g[i] < 0 || g[j] < 0) continue;
+      double2& t = AK[(size_t)cm[i] * n + cm[j]];
+      t.x += E[q].x;
+      t.y += E[q].y;
+    }
+    __syncthreads();
+  }
+  // Cholesky of A_II (trailing block), Y = A_II^-1 A_IS (in place of A_IS)
+  double2* AII = AK + (size_t)nS * n + nS;
+  int info = cta_potrf<double2>(AII, nI, n, sh2);
+  if (threadIdx.x == 0 && info) atomicOr(a.info, 4);
+  double2* AIS = AK + (size_t)nS * n;
+  cta_trsm_lower<double2, double2>(AII, nI, n, AIS, nS, n, reinterpret_cast<char*>(sh2));
+  cta_trsm_lower_h<double2>(AII, nI, n, AIS, nS, n, reinterpret_cast<char*>(sh2));
+  // M^K = A_SS - A_SI Y
+  double2* MK = a.MK + lk * (size_t)nS * nS;
+  for (int q = threadIdx.x; q < nS * nS; q += blockDim.x) MK[q] = AK[(size_t)(q / nS) * n + (q % nS)];
+  __syncthreads();
+  cta_gemm<double2>(false, nS, nS, nI, -1.0, AK + nS, n, AIS, n, 1.0, MK, nS, sh2);
+  // store Y and A_II^-1
+  double2* Y = a.Y + K * (size_t)nI * nS;
+  for (int q = threadIdx.x; q < nI * nS; q += blockDim.x) Y[q] = AIS[(size_t)(q / nS) * n + (q % nS)];
+  double2* Ai = a.Ai + K * (size_t)nI * nI;
+  for (int q = threadIdx.x; q < nI * nI; q += blockDim.x)
+    Ai[q] = (q / nI == q % nI) ? make_double2(1, 0) : make_double2(0, 0);
+  __syncthreads();
+  cta_trsm_lower<double2, double2>(AII, nI, n, Ai, nI, nI, reinterpret_cast<char*>(sh2));
+  cta_trsm_lower_h<double2>(AII, nI, n, Ai, nI, nI, reinterpret_cast<char*>(sh2));
+  // restriction: E_c = I_K^T (M^K I_K)
+  double2* T1 = a.T1 + lk * (size_t)nS * a.nlc;
+  cta_gemm<double2>(false, nS, a.nlc, nS, 1.0, MK, nS, a.IK, a.nlc, 0.0, T1, a.nlc, sh2);
+  double2* Ec = a.Ec + K * (size_t)a.nlc * a.nlc;
+  cta_gemm<double2>(true, a.nlc, a.nlc, nS, 1.0, a.IK, a.nlc, T1, a.nlc, 0.0, Ec, a.nlc, sh2);
+}
+
+// ------------------------------------------------------------------ patches
+__global__ void k_patch_gather(ECSRDev A, const int64_t* ptr, const int32_t* dofs, const int64_t* vptr,
+                               double2* out, int64_t j0) {
+  const int64_t j = j0 + blockIdx.x;
+  const int64_t b = ptr[j];
+  const int n = (int)(ptr[j + 1] - b);
+  double2* M = out + vptr[j];
+  for (int q = threadIdx.x; q < n * n; q += blockDim.x) {
+    int r = q / n, c = q % n;
+    int64_t pos = ecsr_find(A, dofs[b + r], dofs[b + c]);
+    M[q] = pos >= 0 ? A.v64[pos] : make_double2(0, 0);
+  }
+}
+
+// In place: M (n x n) -> M^-1 via Cholesky in the scratch copy W.
+__global__ void __launch_bounds__(CTA_THREADS) k_patch_invert(const int64_t* ptr, const int64_t* vptr, double2* vals,
+                                                            double2* scratch, const int64_t* soff, int64_t j0,
+                                                            int* info) {
+  extern __shared__ double2 sh2[];
+  const int64_t j = j0 + blockIdx.x;
+  const int n = (int)(ptr[j + 1] - ptr[j]);
+  double2* M = vals + vptr[j];
+  double2* W = scratch + soff[blockIdx.x];
+  for (int q = threadIdx.x; q < n * n; q += blockDim.x) W[q] = M[q];
+  __syncthreads();
+  int inf = cta_potrf<double2>(W, n, n, sh2);
+  if (threadIdx.x == 0 && inf) atomicOr(info, 8);
+  for (int q = threadIdx.x; q < n * n; q += blockDim.x)
+    M[q] = (q / n == q % n) ? make_double2(1, 0) : make_double2(0, 0);
+  __syncthreads();
+  cta_trsm_lower<double2, double2>(W, n, n, M, n, n, reinterpret_cast<char*>(sh2));
+  cta_trsm_lower_h<double2>(W, n, n, M, n, n, reinterpret_cast<char*>(sh2));
+}
+
+// ------------------------------------------------------------------ coarsest
+__global__ void k_dense_scatter(double2* C, int64_t N, const double2* E, const int64_t* dofs, int nloc) {
+  const int64_t e = blockIdx.x;
+  for (int q = threadIdx.x; q < nloc * nloc; q += blockDim.x) {
+    int i = q / nloc, j = q % nloc;
+    int64_t gi = dofs[e * nloc + i], gj = dofs[e * nloc + j];
+    if (gi < 0 || gj < 0) continue;
+    double2 v = E[e * (size_t)nloc * nloc + q];
+    atomicAdd(&C[gi * N + gj].x, v.x);
+    atomicAdd(&C[gi * N + gj].y, v.y);
+  }
+}
+
+constexpr int CNB = 64;   // block width of the multi-CTA dense Cholesky
+
+__global__ void __launch_bounds__(CTA_THREADS) k_dense_diag(double2* C, int64_t N, int k0, int* info) {
+  extern __shared__ double2 sh2[];
+  int kb = (int)(N - k0 < CNB ? N - k0 : CNB);
+  int inf = cta_potrf<double2>(C + (size_t)k0 * N + k0, kb, (int)N, sh2);
+  if (threadIdx.x == 0 && inf) atomicOr(info, 16);
+}
+
+// rows i >= k1: C[i, k0:k0+kb] <- C[i, k0:k0+kb] L_kk^-H ; one thread per row
+__global__ void k_dense_panel(double2* C, int64_t N, int k0) {
+  extern __shared__ double2 D[];
+  int kb = (int)(N - k0 < CNB ? N - k0 : CNB);
+  for (int q = threadIdx.x; q < kb * kb; q += blockDim.x) D[q] = C[(size_t)(k0 + q / kb) * N + k0 + q % kb];
+  __syncthreads();
+  int64_t i = (int64_t)k0 + kb + blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  double2* row = C + i * N + k0;
+  double2 x[CNB];
+  for (int j = 0; j < kb; ++j) {
+    double2 v = row[j];
+    for (int t = 0; t < j; ++t) v = Ops<double2>::fnmac(x[t], D[j * kb + t], v);
+    double inv = 1.0 / D[j * kb + j].x;
+    x[j] = make_double2(v.x * inv, v.y * inv);
+  }
+  for (int j = 0; j < kb; ++j) row[j] = x[j];
+}
+
+// trailing update, one CTA per lower 64x64 tile pair: C[i][j] -= sum_t L[i][t] conj(L[j][t])
+__global__ void __launch_bounds__(CTA_THREADS) k_dense_herk(double2* C, int64_t N, int k0) {
+  __shared__ double2 Pi[CNB][17];
+  __shared__ double2 Pj[CNB][17];
+  const int kb = (int)(N - k0 < CNB ? N - k0 : CNB);
+  const int64_t k1 = k0 + kb;
+  // decode tile pair (bi >= bj) from the linear block index
+  int64_t t = blockIdx.x;
+  int64_t bi = (int64_t)((std::sqrt(8.0 * t + 1.0) - 1.0) / 2.0);
+  while ((bi + 1) * (bi + 2) / 2 <= t) ++bi;
+  while (bi * (bi + 1) / 2 > t) --bi;
+  int64_t bj = t - bi * (bi + 1) / 2;
+  const int64_t i0 = k1 + bi * CNB, j0 = k1 + bj * CNB;
+  const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;   // 16 x 16 threads, 4 x 4 outputs each
+  double2 acc[4][4];
+  for (int a = 0; a < 4; ++a)
+    for (int b = 0; b < 4; ++b) acc[a][b] = make_double2(0, 0);
+  for (int t0 = 0; t0 < kb; t0 += 16) {
+    for (int q = threadIdx.x; q < CNB * 16; q += blockDim.x) {
+      int r = q / 16, c = q % 16;
+      int64_t ii = i0 + r, jj = j0 + r;
+      Pi[r][c] = (ii < N && t0 + c < kb) ? C[ii * N + k0 + t0 + c] : make_double2(0, 0);
+      Pj[r][c] = (jj < N && t0 + c < kb) ? C[jj * N + k0 + t0 + c] : make_double2(0, 0);
+    }
+    __syncthreads();
+    for (int c = 0; c < 16; ++c) {
+      double2 av[4], bv[4];
+      for (int a = 0; a < 4; ++a) av[a] = Pi[ty * 4 + a][c];
+      for (int b = 0; b < 4; ++b) bv[b] = Pj[tx * 4 + b][c];
+      for (int a = 0; a < 4; ++a)
+        for (int b = 0; b < 4; ++b) acc[a][b] = Ops<double2>::fmac(av[a], bv[b], acc[a][b]);
+    }
+    __syncthreads();
+  }
+  for (int a = 0; a < 4; ++a)
+    for (int b = 0; b < 4; ++b) {
+      int64_t i = i0 + ty * 4 + a, j = j0 + tx * 4 + b;
+      if (i < N && j <= i) {
+        double2& o = C[i * N + j];
+        o.x -= acc[a][b].x;
+        o.y -= acc[a][b].y;
+      }
+    }
+}
+
+static void dense_cholesky(double2* C, int64_t N, int* info, cudaStream_t st) {
+  const size_t sm = (size_t)(NB * NB + 2 * TL * NB) * sizeof(double2) + 64;
+  DPG_CUDA(cudaFuncSetAttribute(k_dense_diag, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+  DPG_CUDA(cudaFuncSetAttribute(k_dense_panel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)(CNB * CNB * sizeof(double2))));
+  for (int64_t k0 = 0; k0 < N; k0 += CNB) {
+    int kb = (int)(N - k0 < CNB ? N - k0 : CNB);
+    k_dense_diag<<<1, CTA_THREADS, sm, st>>>(C, N, (int)k0, info);
+    DPG_CHECK_LAUNCH();
+    int64_t rows = N - k0 - kb;
+    if (rows <= 0) break;
+    k_dense_panel<<<(unsigned)((rows + 127) / 128), 128, CNB * CNB * sizeof(double2), st>>>(C, N, (int)k0);
+    DPG_CHECK_LAUNCH();
+    int64_t nt = (rows + CNB - 1) / CNB;
+    k_dense_herk<<<(unsigned)(nt * (nt + 1) / 2), CTA_THREADS, 0, st>>>(C, N, (int)k0);
+    DPG_CHECK_LAUNCH();
+  }
+}
+
+// --------------------------------------------------------------- precision
+__global__ void k_to_c64(const double2* a, float2* b, int64_t n) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  for (; i < n; i += (int64_t)gridDim.x * blockDim.x) b[i] = make_float2((float)a[i].x, (float)a[i].y);
+}
+static float2* to_c64(Alloc& A, const double2* src, int64_t n, cudaStream_t st) {
+  float2* d = A.arr<float2>((size_t)std::max<int64_t>(n, 1));
+  if (n > 0) {
+    k_to_c64<<<1216, 256, 0, st>>>(src, d, n);
+    DPG_CHECK_LAUNCH();
+  }
+  return d;
+}
+
+// --------------------------------------------------------------- rhs
+__global__ void k_rhs(const double2* Fc, const int64_t* dofs, double2* b, int64_t nel, int nloc) {
+  int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (q >= nel * nloc) return;
+  int64_t g = dofs[q];
+  if (g < 0) return;
+  atomicAdd(&b[g].x, Fc[q].x);
+  atomicAdd(&b[g].y, Fc[q].y);
+}
+
+void assemble_rhs(SystemImpl& S, cudaStream_t st) {
+  const Level& L = S.levels.back();
+  S.b = S.mem.arr<double2>((size_t)L.mesh.ndof);
+  DPG_CUDA(cudaMemsetAsync(S.b, 0, (size_t)L.mesh.ndof * sizeof(double2), st));
+  int64_t n = S.nelem * S.ntr;
+  k_rhs<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(S.Fc, L.dofs, S.b, S.nelem, (int)S.ntr);
+  DPG_CHECK_LAUNCH();
+}
+
+// --------------------------------------------------------------- driver
+static void setup_patches(SystemImpl& S, Level& F, const std::vector<char>& smask, int H, const int nco[3],
+                          int* dinfo, cudaStream_t st) {
+  Alloc& A = S.mem;
+  Patches P = build_patches(F.mesh, smask, H, nco);
+  PatchDev& D = F.P;
+  D.np = (int64_t)P.ptr.size() - 1;
+  D.nslots = (int64_t)P.dofs.size();
+  D.nvals = P.val_ptr.back();
+  D.max_n = 0;
+  D.sum_sq = D.nvals;
+  for (int64_t j = 0; j < D.np; ++j) D.max_n = std::max(D.max_n, P.ptr[j + 1] - P.ptr[j]);
+  D.ptr = upload(A, P.ptr, st);
+  D.dofs = upload(A, P.dofs, st);
+  D.val_ptr = upload(A, P.val_ptr, st);
+  D.slot_ptr = upload(A, P.slot_ptr, st);
+  D.slots = upload(A, P.slots, st);
+  D.inv64 = A.arr<double2>((size_t)D.nvals);
+  k_patch_gather<<<(unsigned)D.np, 256, 0, st>>>(F.A, D.ptr, D.dofs, D.val_ptr, D.inv64, 0);
+  DPG_CHECK_LAUNCH();
+  // invert in chunks with a bounded scratch
+  const size_t sm = (size_t)(NB * NB + 2 * TL * NB) * sizeof(double2) + 64;
+  DPG_CUDA(cudaFuncSetAttribute(k_patch_invert, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+  size_t one = (size_t)D.max_n * D.max_n * 16;
+  size_t cap = std::min<size_t>(std::max<size_t>((size_t)1 << 28, one) * 4, (size_t)2 << 30);
+  cap = std::max(cap, one);
+  double2* scratch = A.arr<double2>(cap / 16);
+  int64_t* soff = A.arr<int64_t>((size_t)D.np + 1);
+  std::vector<int64_t> offs;
+  for (int64_t j0 = 0; j0 < D.np;) {
+    offs.clear();
+    int64_t acc = 0, j = j0;
+    while (j < D.np) {
+      int64_t nj = P.ptr[j + 1] - P.ptr[j];
+      if (acc + nj * nj > (int64_t)(cap / 16) && j > j0) break;
+      offs.push_back(acc);
+      acc += nj * nj;
+      ++j;
+    }
+    DPG_CUDA(cudaMemcpyAsync(soff, offs.data(), offs.size() * sizeof(int64_t), cudaMemcpyHostToDevice, st));
+    k_patch_invert<<<(unsigned)(j - j0), CTA_THREADS, sm, st>>>(D.ptr, D.val_ptr, D.inv64, scratch, soff, j0, dinfo);
+    DPG_CHECK_LAUNCH();
+    DPG_CUDA(cudaStreamSynchronize(st));   // offsets buffer is reused
+    j0 = j;
+  }
+}
+
+void build_hierarchy(SystemImpl& S, cudaStream_t st) {
+  Alloc& A = S.mem;
+  const int L = (int)S.levels.size() - 1;
+  const bool mixed = S.op.precision == DPGMG_PREC_MIXED;
+  int* dinfo = A.arr<int>(1);
+  DPG_CUDA(cudaMemsetAsync(dinfo, 0, sizeof(int), st));
+  S.levels[L].dofs = upload_dofs(A, S.levels[L].mesh, st);
+  for (int l = L; l >= 1; --l) {
+    Level& F = S.levels[l];
+    Level& C = S.levels[l - 1];
+    C.dofs = upload_dofs(A, C.mesh, st);
+    C.nloc = (int)C.mesh.loc.size();
+    C.E = A.arr<double2>((size_t)C.mesh.nelem * C.nloc * C.nloc);
+    std::vector<char> smask;
+    int H;
+    if (F.kind == 1) {
+      std::vector<int32_t> sel, inj;
+      p_selection(F.mesh.p, sel);
+      p_injection(F.mesh, C.mesh, inj);
+      F.inj = upload(A, inj, st);
+      int32_t* dsel = upload(A, sel, st);
+      k_p_restrict<<<(unsigned)C.mesh.nelem, 256, 0, st>>>(F.E, C.E, dsel, F.nloc, C.nloc);
+      DPG_CHECK_LAUNCH();
+      ECSRHost H_ = build_ecsr(F.mesh, element_groups(F.mesh));
+      assemble_ecsr(A, F.mesh, H_, F.A, st);
+      ecsr_add_elements(F.A, F.E, F.dofs, F.mesh.nelem, F.nloc, st);
+      smask.assign(F.mesh.ndof, 1);
+      H = 2;
+    } else {
+      MacroHost M = build_macro(F.mesh, C.mesh);
+      F.nS = M.nS;
+      F.nI = M.nI;
+      F.nK = C.mesh.nelem;
+      F.S_glob = upload(A, M.S_glob, st);
+      F.I_glob = upload(A, M.I_glob, st);
+      F.P_ptr = upload(A, M.P_ptr, st);
+      F.P_col = upload(A, M.P_col, st);
+      F.P_val = upload(A, M.P_val, st);
+      F.PT_ptr = upload(A, M.PT_ptr, st);
+      F.PT_col = upload(A, M.PT_col, st);
+      F.PT_val = upload(A, M.PT_val, st);
+      F.sslot_ptr = upload(A, M.sslot_ptr, st);
+      F.sslots = upload(A, M.sslots, st);
+      F.smask = upload(A, M.smask, st);
+      int32_t* cmap = upload(A, M.child_map, st);
+      std::vector<double2> ik(M.IK.size());
+      for (size_t i = 0; i < ik.size(); ++i) ik[i] = make_double2(M.IK[i], 0.0);
+      double2* dIK = upload(A, ik, st);
+      F.Y64 = A.arr<double2>((size_t)F.nK * F.nI * F.nS);
+      F.Ai64 = A.arr<double2>((size_t)F.nK * F.nI * F.nI);
+      ECSRHost H_ = build_ecsr(F.mesh, M.groups);
+      assemble_ecsr(A, F.mesh, H_, F.A, st);
+      const int n = F.nS + F.nI;
+      int64_t chunk = std::min<int64_t>(F.nK, 2048);
+      double2* AK = A.arr<double2>((size_t)chunk * n * n);
+      double2* T1 = A.arr<double2>((size_t)chunk * F.nS * C.nloc);
+      double2* MK = A.arr<double2>((size_t)chunk * F.nS * F.nS);
+      MacroArgs a{};
+      a.nS = F.nS; a.nI = F.nI; a.nlf = F.nloc; a.nlc = C.nloc;
+      a.Ef = F.E; a.fdofs = F.dofs; a.child_map = cmap;
+      a.nf0 = F.mesh.n[0]; a.nf1 = F.mesh.n[1];
+      a.nc0 = C.mesh.n[0]; a.nc1 = C.mesh.n[1];
+      a.IK = dIK; a.AK = AK; a.T1 = T1; a.MK = MK;
+      a.Y = F.Y64; a.Ai = F.Ai64; a.Ec = C.E; a.info = dinfo;
+      const size_t sm = (size_t)(NB * NB + 2 * TL * NB) * sizeof(double2) + 64;
+      DPG_CUDA(cudaFuncSetAttribute(k_macro, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+      for (int64_t K0 = 0; K0 < F.nK; K0 += chunk) {
+        a.K0 = K0;
+        int nb = (int)std::min<int64_t>(chunk, F.nK - K0);
+        k_macro<<<nb, CTA_THREADS, sm, st>>>(a);
+        DPG_CHECK_LAUNCH();
+        ecsr_add_elements(F.A, MK, F.S_glob + K0 * F.nS, nb, F.nS, st);
+      }
+      smask.assign(M.smask.begin(), M.smask.end());
+      H = 4;
+    }
+    F.n_smooth = 0;
+    for (char c : smask) F.n_smooth += c;
+    setup_patches(S, F, smask, H, C.mesh.n, dinfo, st);
+    estimate_theta(S, l, st);
+    if (mixed) {
+      F.A.v32 = to_c64(A, F.A.v64, F.A.nnz, st);
+      F.P.inv32 = to_c64(A, F.P.inv64, F.P.nvals, st);
+      if (F.kind == 2) {
+        F.Y32 = to_c64(A, F.Y64, F.nK * F.nI * F.nS, st);
+        F.Ai32 = to_c64(A, F.Ai64, F.nK * F.nI * F.nI, st);
+      }
+    }
+  }
+  // coarsest
+  Level& C0 = S.levels[0];
+  if (L == 0) C0.dofs = S.levels[0].dofs;
+  if (S.op.coarsest == DPGMG_COARSEST_CHOLESKY || L == 0) {
+    C0.N0 = C0.mesh.ndof;
+    C0.C64 = A.arr<double2>((size_t)C0.N0 * C0.N0);
+    DPG_CUDA(cudaMemsetAsync(C0.C64, 0, (size_t)C0.N0 * C0.N0 * sizeof(double2), st));
+    k_dense_scatter<<<(unsigned)C0.mesh.nelem, 256, 0, st>>>(C0.C64, C0.N0, C0.E, C0.dofs, C0.nloc);
+    DPG_CHECK_LAUNCH();
+    dense_cholesky(C0.C64, C0.N0, dinfo, st);
+    if (mixed) C0.C32 = to_c64(A, C0.C64, C0.N0 * C0.N0, st);
+  }
+  int info = 0;
+  DPG_CUDA(cudaMemcpyAsync(&info, dinfo, sizeof(int), cudaMemcpyDeviceToHost, st));
+  DPG_CUDA(cudaStreamSynchronize(st));
+  if (info) throw Err{DPGMG_ERR_NOT_HPD, "a macro, patch or coarsest factorisation lost positive definiteness"};
+}
+
+}  // namespace dpgmg

@@ -1,0 +1,904 @@
+// The DPG-MG V-cycle and MG-preconditioned conjugate gradients (Sec. 3-4):
+//   k_spmv            y = A x or y = b - A x on the entity-shared CSR operator
+//   k_patch_apply     per-patch dense products A_j^-1 (R_j r)   (additive Schwarz)
+//   k_slot_sum        x_g (+)= theta * sum of the patch results of DOF g
+//   k_condense_*      macro-grid residual condensation r_S -= Y^H r_I (h levels)
+//   k_backsub         x_I = A_II^-1 r_I - Y x_S                  (h levels)
+//   k_csr_real        natural inclusion P and its adjoint P^T      (h levels)
+//   k_coarse_solve    L L^H e = r with the dense coarsest factor (cooperative)
+//   k_dot_*, k_axpy*  CG recurrences in FP64
+// Every kernel is templated on the complex type of the V-cycle (complex128
+// on the FP64 path, complex64 on the mixed path); CG always runs in FP64.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "common.cuh"
+#include "internal.h"
+
+namespace dpgmg {
+
+template <class C> struct Prec;
+template <> struct Prec<double2> {
+  static const double2* A(const ECSRDev& a) { return a.v64; }
+  static const double2* inv(const PatchDev& p) { return p.inv64; }
+  static const double2* Y(const Level& l) { return l.Y64; }
+  static const double2* Ai(const Level& l) { return l.Ai64; }
+  static const double2* Cf(const Level& l) { return l.C64; }
+};
+template <> struct Prec<float2> {
+  static const float2* A(const ECSRDev& a) { return a.v32; }
+  static const float2* inv(const PatchDev& p) { return p.inv32; }
+  static const float2* Y(const Level& l) { return l.Y32; }
+  static const float2* Ai(const Level& l) { return l.Ai32; }
+  static const float2* Cf(const Level& l) { return l.C32; }
+};
+
+template <class C> __device__ __forceinline__ C warp_sum(C v) {
+  for (int o = 16; o > 0; o >>= 1) {
+    v.x += __shfl_xor_sync(0xffffffffu, v.x, o);
+    v.y += __shfl_xor_sync(0xffffffffu, v.y, o);
+  }
+  return v;
+}
+
+// ------------------------------------------------------------------ SpMV
+// mode 0: y = A x; mode 1: y = b - A x.  One warp per row.
+template <class C>
+__global__ void __launch_bounds__(256) k_spmv(const int32_t* __restrict__ row_ent, const int64_t* __restrict__ ent_start,
+                                              const int64_t* __restrict__ col_ptr, const int32_t* __restrict__ col_idx,
+                                              const int64_t* __restrict__ val_ptr, const C* __restrict__ v,
+                                              const C* __restrict__ x, const C* __restrict__ b, C* __restrict__ y,
+                                              int64_t nrows, int mode) {
+  using O = Ops<C>;
+  const int lane = threadIdx.x & 31;
+  const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t row = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); row < nrows; row += nw) {
+    const int32_t E = row_ent[row];
+    C acc = O::zero();
+    if (E >= 0) {
+      const int64_t c0 = col_ptr[E];
+      const int nnz = (int)(col_ptr[E + 1] - c0);
+      const C* vals = v + val_ptr[E] + (row - ent_start[E]) * nnz;
+      const int32_t* cols = col_idx + c0;
+      for (int k = lane; k < nnz; k += 32) acc = O::fma(vals[k], x[cols[k]], acc);
+      acc = warp_sum(acc);
+    }
+    if (lane == 0) y[row] = mode ? O::sub(b[row], acc) : acc;
+  }
+}
+
+template <class C>
+static void spmv(const ECSRDev& A, const C* vals, const C* x, const C* b, C* y, int mode, cudaStream_t st) {
+  int64_t blocks = std::min<int64_t>((A.nrows + 7) / 8, 152 * 16);
+  k_spmv<C><<<(unsigned)blocks, 256, 0, st>>>(A.row_ent, A.ent_start, A.col_ptr, A.col_idx, A.val_ptr, vals, x, b, y,
+                                               A.nrows, mode);
+  DPG_CHECK_LAUNCH();
+}
+
+void spmv64(const ECSRDev& A, const double2* x, double2* y, cudaStream_t st) {
+  spmv<double2>(A, A.v64, x, nullptr, y, 0, st);
+}
+
+// ------------------------------------------------------------- smoother
+template <class C>
+__global__ void __launch_bounds__(256) k_patch_apply(const int64_t* __restrict__ ptr, const int32_t* __restrict__ dofs,
+                                                     const int64_t* __restrict__ vptr, const C* __restrict__ inv,
+                                                     const C* __restrict__ r, C* __restrict__ pbuf) {
+  extern __shared__ unsigned char shraw[];
+  C* rj = reinterpret_cast<C*>(shraw);
+  using O = Ops<C>;
+  const int64_t j = blockIdx.x;
+  const int64_t b = ptr[j];
+  const int n = (int)(ptr[j + 1] - b);
+  for (int q = threadIdx.x; q < n; q += blockDim.x) rj[q] = r[dofs[b + q]];
+  __syncthreads();
+  const C* M = inv + vptr[j];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  for (int a = w; a < n; a += 8) {
+    const C* row = M + (size_t)a * n;
+    C acc = O::zero();
+    for (int k = lane; k < n; k += 32) acc = O::fma(row[k], rj[k], acc);
+    acc = warp_sum(acc);
+    if (lane == 0) pbuf[b + a] = acc;
+  }
+}
+
+// y[g] = (accumulate ? y[g] : 0) + theta * sum_{slots of g} pbuf[slot]
+template <class C>
+__global__ void k_slot_sum(const int64_t* __restrict__ sptr, const int32_t* __restrict__ slots,
+                           const C* __restrict__ pbuf, C* __restrict__ y, int64_t n, double theta, int accumulate) {
+  int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (g >= n) return;
+  C acc = Ops<C>::zero();
+  for (int64_t s = sptr[g]; s < sptr[g + 1]; ++s) acc = Ops<C>::add(acc, pbuf[slots[s]]);
+  acc = Ops<C>::scale(acc, (typename Ops<C>::R)theta);
+  y[g] = accumulate ? Ops<C>::add(y[g], acc) : acc;
+}
+
+template <class C>
+static void smooth(const Level& L, const C* r, C* y, double theta, int accumulate, C* pbuf, cudaStream_t st) {
+  const PatchDev& P = L.P;
+  size_t sm = (size_t)P.max_n * sizeof(C) + 16;
+  k_patch_apply<C><<<(unsigned)P.np, 256, sm, st>>>(P.ptr, P.dofs, P.val_ptr, Prec<C>::inv(P), r, pbuf);
+  DPG_CHECK_LAUNCH();
+  int64_t n = L.mesh.ndof;
+  k_slot_sum<C><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(P.slot_ptr, P.slots, pbuf, y, n, theta, accumulate);
+  DPG_CHECK_LAUNCH();
+}
+
+void smooth_apply64(const Level& L, const double2* r, double2* y, double theta, double2* scratch, cudaStream_t st) {
+  smooth<double2>(L, r, y, theta, 0, scratch, st);
+}
+
+// ------------------------------------------------------------- transfers
+template <class C>
+__global__ void k_condense_apply(int nS, int nI, const int64_t* __restrict__ Ig, const C* __restrict__ Y,
+                                 const C* __restrict__ r, C* __restrict__ cbuf) {
+  extern __shared__ unsigned char shraw[];
+  C* rI = reinterpret_cast<C*>(shraw);
+  const int64_t K = blockIdx.x;
+  for (int i = threadIdx.x; i < nI; i += blockDim.x) rI[i] = r[Ig[K * nI + i]];
+  __syncthreads();
+  const C* YK = Y + K * (size_t)nI * nS;
+  for (int a = threadIdx.x; a < nS; a += blockDim.x) {
+    C acc = Ops<C>::zero();
+    for (int i = 0; i < nI; ++i) acc = Ops<C>::fmac(rI[i], YK[(size_t)i * nS + a], acc);   // conj(Y[i][a]) r_I[i]
+    cbuf[K * nS + a] = acc;
+  }
+}
+
+// rs[g] = smask[g] ? r[g] - sum_{slots} cbuf[slot] : 0
+template <class C>
+__global__ void k_condense_sum(const int64_t* __restrict__ sptr, const int32_t* __restrict__ slots,
+                               const C* __restrict__ cbuf, const char* __restrict__ smask, const C* __restrict__ r,
+                               C* __restrict__ rs, int64_t n) {
+  int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (g >= n) return;
+  if (!smask[g]) { rs[g] = Ops<C>::zero(); return; }
+  C acc = r[g];
+  for (int64_t s = sptr[g]; s < sptr[g + 1]; ++s) acc = Ops<C>::sub(acc, cbuf[slots[s]]);
+  rs[g] = acc;
+}
+
+// x_I = A_II^-1 r_I - Y x_S, one CTA per coarse element, one warp per row
+template <class C>
+__global__ void k_backsub(int nS, int nI, const int64_t* __restrict__ Sg, const int64_t* __restrict__ Ig,
+                          const C* __restrict__ Ai, const C* __restrict__ Y, const C* __restrict__ r,
+                          C* __restrict__ x) {
+  extern __shared__ unsigned char shraw[];
+  C* rI = reinterpret_cast<C*>(shraw);
+  C* xS = rI + nI;
+  using O = Ops<C>;
+  const int64_t K = blockIdx.x;
+  for (int i = threadIdx.x; i < nI; i += blockDim.x) rI[i] = r[Ig[K * nI + i]];
+  for (int a = threadIdx.x; a < nS; a += blockDim.x) {
+    int64_t g = Sg[K * nS + a];
+    xS[a] = g >= 0 ? x[g] : O::zero();
+  }
+  __syncthreads();
+  const C* AiK = Ai + K * (size_t)nI * nI;
+  const C* YK = Y + K * (size_t)nI * nS;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  for (int i = w; i < nI; i += blockDim.x >> 5) {
+    C acc = O::zero();
+    for (int k = lane; k < nI; k += 32) acc = O::fma(AiK[(size_t)i * nI + k], rI[k], acc);
+    for (int a = lane; a < nS; a += 32) acc = O::fnma(YK[(size_t)i * nS + a], xS[a], acc);
+    acc = warp_sum(acc);
+    if (lane == 0) x[Ig[K * nI + i]] = acc;
+  }
+}
+
+// y[i] (+)= sum_k val[k] x[col[k]] with real values (natural inclusion)
+template <class C>
+__global__ void k_csr_real(const int64_t* __restrict__ ptr, const int32_t* __restrict__ col,
+                           const double* __restrict__ val, const C* __restrict__ x, C* __restrict__ y, int64_t n,
+                           int accumulate) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  using R = typename Ops<C>::R;
+  C acc = Ops<C>::zero();
+  for (int64_t k = ptr[i]; k < ptr[i + 1]; ++k) {
+    R v = (R)val[k];
+    C xv = x[col[k]];
+    acc.x += v * xv.x;
+    acc.y += v * xv.y;
+  }
+  y[i] = accumulate ? Ops<C>::add(y[i], acc) : acc;
+}
+
+template <class C>
+__global__ void k_gather(const int32_t* __restrict__ idx, const C* __restrict__ x, C* __restrict__ y, int64_t n) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n) y[i] = x[idx[i]];
+}
+template <class C>
+__global__ void k_scatter_add(const int32_t* __restrict__ idx, const C* __restrict__ x, C* __restrict__ y, int64_t n) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n) y[idx[i]] = Ops<C>::add(y[idx[i]], x[i]);
+}
+
+// ----------------------------------------------------------- coarse solve
+constexpr int CB = 64;
+constexpr long long BARRIER_SPIN_LIMIT = 1ll << 26;
+
+__device__ void grid_barrier(unsigned* bar, unsigned nblocks, unsigned& gen, int* err) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    unsigned arrived = atomicAdd(&bar[0], 1u) + 1u;
+    if (arrived == nblocks) {
+      atomicExch(&bar[0], 0u);
+      __threadfence();
+      atomicAdd(&bar[1], 1u);
+    } else {
+      long long it = 0;
+      while (atomicAdd(&bar[1], 0u) == gen && it < BARRIER_SPIN_LIMIT) {
+        ++it;
+        __nanosleep(64);
+      }
+      if (it >= BARRIER_SPIN_LIMIT) atomicExch(err, 1);
+    }
+    gen += 1u;
+    __threadfence();
+  }
+  __syncthreads();
+}
+
+// Dense L L^H e = r.  y holds r on entry and e on exit.  Row block kb is owned
+// by CTA kb % gridDim.x, which applies every update to its rows; Dinv holds
+// the inverses of the diagonal blocks of L.
+template <class C>
+__global__ void __launch_bounds__(256) k_coarse_solve(const C* __restrict__ L, const C* __restrict__ Dinv, int64_t N,
+                                                      C* y, unsigned* bar, int* err) {
+  __shared__ C zb[CB];
+  using O = Ops<C>;
+  const int nb = (int)((N + CB - 1) / CB);
+  unsigned gen = 0;
+  if (threadIdx.x == 0) gen = atomicAdd(&bar[1], 0u);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  // forward: L z = r
+  for (int kb = 0; kb < nb; ++kb) {
+    const int64_t k0 = (int64_t)kb * CB;
+    const int kw = (int)(N - k0 < CB ? N - k0 : CB);
+    if ((int)(kb % gridDim.x) == (int)blockIdx.x) {
+      if (threadIdx.x < kw) zb[threadIdx.x] = y[k0 + threadIdx.x];
+      __syncthreads();
+      const C* D = Dinv + (size_t)kb * CB * CB;
+      for (int r = w; r < kw; r += 8) {
+        C acc = O::zero();
+        for (int t = lane; t <= r; t += 32) acc = O::fma(D[r * CB + t], zb[t], acc);
+        acc = warp_sum(acc);
+        if (lane == 0) y[k0 + r] = acc;
+      }
+    }
+    grid_barrier(bar, gridDim.x, gen, err);
+    if (threadIdx.x < kw) zb[threadIdx.x] = y[k0 + threadIdx.x];
+    __syncthreads();
+    for (int rb = kb + 1; rb < nb; ++rb) {
+      if ((int)(rb % gridDim.x) != (int)blockIdx.x) continue;
+      const int64_t r0 = (int64_t)rb * CB;
+      const int rw = (int)(N - r0 < CB ? N - r0 : CB);
+      for (int r = w; r < rw; r += 8) {
+        const C* row = L + (size_t)(r0 + r) * N + k0;
+        C acc = O::zero();
+        for (int t = lane; t < kw; t += 32) acc = O::fma(row[t], zb[t], acc);
+        acc = warp_sum(acc);
+        if (lane == 0) y[r0 + r] = O::sub(y[r0 + r], acc);
+      }
+    }
+    __syncthreads();
+  }
+  grid_barrier(bar, gridDim.x, gen, err);
+  // backward: L^H e = z
+  for (int kb = nb - 1; kb >= 0; --kb) {
+    const int64_t k0 = (int64_t)kb * CB;
+    const int kw = (int)(N - k0 < CB ? N - k0 : CB);
+    if ((int)(kb % gridDim.x) == (int)blockIdx.x) {
+      if (threadIdx.x < kw) zb[threadIdx.x] = y[k0 + threadIdx.x];
+      __syncthreads();
+      const C* D = Dinv + (size_t)kb * CB * CB;
+      // x = D^H z : x_r = sum_{t >= r} conj(D[t][r]) z_t
+      for (int r = w; r < kw; r += 8) {
+        C acc = O::zero();
+        for (int t = r + lane; t < kw; t += 32) acc = O::fmac(zb[t], D[t * CB + r], acc);
+        acc = warp_sum(acc);
+        if (lane == 0) y[k0 + r] = acc;
+      }
+    }
+    grid_barrier(bar, gridDim.x, gen, err);
+    if (threadIdx.x < kw) zb[threadIdx.x] = y[k0 + threadIdx.x];
+    __syncthreads();
+    // rows i < k0: y_i -= sum_t conj(L[k0+t][i]) x_t ; threads over i (coalesced)
+    for (int rb = 0; rb < kb; ++rb) {
+      if ((int)(rb % gridDim.x) != (int)blockIdx.x) continue;
+      const int64_t r0 = (int64_t)rb * CB;
+      for (int i = threadIdx.x; i < CB; i += blockDim.x) {
+        C acc = O::zero();
+        for (int t = 0; t < kw; ++t) acc = O::fmac(zb[t], L[(size_t)(k0 + t) * N + r0 + i], acc);
+        y[r0 + i] = O::sub(y[r0 + i], acc);
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// inverse of each lower-triangular diagonal block of the coarse factor
+template <class C>
+__global__ void __launch_bounds__(256) k_diag_inverse(const C* L, int64_t N, C* Dinv) {
+  extern __shared__ unsigned char shraw[];
+  const int kb = blockIdx.x;
+  const int64_t k0 = (int64_t)kb * CB;
+  const int kw = (int)(N - k0 < CB ? N - k0 : CB);
+  C* D = Dinv + (size_t)kb * CB * CB;
+  for (int q = threadIdx.x; q < CB * CB; q += blockDim.x) {
+    int r = q / CB, c = q % CB;
+    D[q] = (r == c && r < kw) ? Ops<C>::from_re(1) : Ops<C>::zero();
+  }
+  __syncthreads();
+  cta_trsm_lower<C, C>(L + (size_t)k0 * N + k0, kw, (int)N, D, kw, CB, reinterpret_cast<char*>(shraw));
+}
+
+// ------------------------------------------------------------- vector ops
+template <class C>
+__global__ void k_zero(C* y, int64_t n) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n) y[i] = Ops<C>::zero();
+}
+__global__ void k_narrow(const double2* a, float2* b, int64_t n) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n) b[i] = make_float2((float)a[i].x, (float)a[i].y);
+}
+__global__ void k_widen(const float2* a, double2* b, int64_t n) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n) b[i] = make_double2(a[i].x, a[i].y);
+}
+
+constexpr int RED_BLOCKS = 608;
+
+// partial[b] = sum conj(u_i) v_i over the block's share (FP64)
+__global__ void k_dot_partial(const double2* __restrict__ u, const double2* __restrict__ v, int64_t n,
+                              double2* __restrict__ part) {
+  __shared__ double2 sh[8];
+  double2 acc = make_double2(0, 0);
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    acc = Ops<double2>::fmac(v[i], u[i], acc);
+  acc = warp_sum(acc);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double2 s = make_double2(0, 0);
+    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) s = Ops<double2>::add(s, sh[k]);
+    part[blockIdx.x] = s;
+  }
+}
+
+// scalar slots of the CG state
+enum { SC_RHO = 0, SC_PQ, SC_ALPHA, SC_BETA, SC_RR, SC_RHONEW, SC_COUNT };
+
+// which: 0 -> PQ then ALPHA = RHO / PQ ; 1 -> RR ; 2 -> RHONEW, BETA, RHO ; 3 -> RHO
+__global__ void k_dot_finish(const double2* part, int nparts, double2* sc, int which) {
+  __shared__ double2 sh[256];
+  double2 acc = make_double2(0, 0);
+  for (int k = threadIdx.x; k < nparts; k += blockDim.x) acc = Ops<double2>::add(acc, part[k]);
+  sh[threadIdx.x] = acc;
+  __syncthreads();
+  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+    if ((int)threadIdx.x < s) sh[threadIdx.x] = Ops<double2>::add(sh[threadIdx.x], sh[threadIdx.x + s]);
+    __syncthreads();
+  }
+  if (threadIdx.x != 0) return;
+  double2 d = sh[0];
+  if (which == 0) {
+    sc[SC_PQ] = d;
+    double2 rho = sc[SC_RHO];
+    double den = d.x * d.x + d.y * d.y;
+    sc[SC_ALPHA] = make_double2((rho.x * d.x + rho.y * d.y) / den, (rho.y * d.x - rho.x * d.y) / den);
+  } else if (which == 1) {
+    sc[SC_RR] = d;
+  } else if (which == 2) {
+    double2 rho = sc[SC_RHO];
+    double den = rho.x * rho.x + rho.y * rho.y;
+    sc[SC_BETA] = make_double2((d.x * rho.x + d.y * rho.y) / den, (d.y * rho.x - d.x * rho.y) / den);
+    sc[SC_RHONEW] = d;
+    sc[SC_RHO] = d;
+  } else {
+    sc[SC_RHO] = d;
+  }
+}
+
+// x += alpha p ; r -= alpha q ; rr-partials of ||r||^2
+__global__ void k_cg_update(double2* __restrict__ x, double2* __restrict__ r, const double2* __restrict__ p,
+                            const double2* __restrict__ q, const double2* __restrict__ sc, int64_t n,
+                            double2* __restrict__ part) {
+  __shared__ double2 sh[8];
+  const double2 al = sc[SC_ALPHA];
+  double acc = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    double2 pi = p[i], qi = q[i], xi = x[i], ri = r[i];
+    xi.x += al.x * pi.x - al.y * pi.y;
+    xi.y += al.x * pi.y + al.y * pi.x;
+    ri.x -= al.x * qi.x - al.y * qi.y;
+    ri.y -= al.x * qi.y + al.y * qi.x;
+    x[i] = xi;
+    r[i] = ri;
+    acc += ri.x * ri.x + ri.y * ri.y;
+  }
+  double2 a2 = warp_sum(make_double2(acc, 0.0));
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = a2;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double2 s = make_double2(0, 0);
+    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) s = Ops<double2>::add(s, sh[k]);
+    part[blockIdx.x] = s;
+  }
+}
+
+// p = z + beta p
+__global__ void k_cg_dir(double2* __restrict__ p, const double2* __restrict__ z, const double2* __restrict__ sc,
+                         int64_t n) {
+  const double2 be = sc[SC_BETA];
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    double2 pi = p[i], zi = z[i];
+    p[i] = make_double2(zi.x + be.x * pi.x - be.y * pi.y, zi.y + be.x * pi.y + be.y * pi.x);
+  }
+}
+
+// ------------------------------------------------------------ workspace
+template <class C> struct LevelWS {
+  C *r = nullptr, *rs = nullptr, *x = nullptr, *t = nullptr, *pbuf = nullptr, *cbuf = nullptr;
+};
+
+struct WS {
+  Alloc mem;
+  std::vector<LevelWS<double2>> w64;
+  std::vector<LevelWS<float2>> w32;
+  double2 *x = nullptr, *r = nullptr, *p = nullptr, *q = nullptr, *z = nullptr, *part = nullptr, *sc = nullptr;
+  double2* sc_host = nullptr;    // pinned
+  double2 *Dinv64 = nullptr;
+  float2 *Dinv32 = nullptr;
+  unsigned* bar = nullptr;
+  int* err = nullptr;
+  int coarse_grid = 0;
+  ECSRDev Acg;                   // the CG operator (finest A_L, FP64)
+  bool acg_owned = false;
+};
+
+template <class C> static std::vector<LevelWS<C>>& wsv(WS& w);
+template <> std::vector<LevelWS<double2>>& wsv<double2>(WS& w) { return w.w64; }
+template <> std::vector<LevelWS<float2>>& wsv<float2>(WS& w) { return w.w32; }
+
+template <class C>
+static void alloc_level_ws(WS& W, SystemImpl& S) {
+  auto& v = wsv<C>(W);
+  v.resize(S.levels.size());
+  for (size_t l = 0; l < S.levels.size(); ++l) {
+    const Level& L = S.levels[l];
+    int64_t n = L.mesh.ndof;
+    v[l].r = S.mem.arr<C>((size_t)n);
+    v[l].rs = S.mem.arr<C>((size_t)n);
+    v[l].x = S.mem.arr<C>((size_t)n);
+    v[l].t = S.mem.arr<C>((size_t)n);
+    if (l >= 1) v[l].pbuf = S.mem.arr<C>((size_t)std::max<int64_t>(L.P.nslots, 1));
+    if (L.kind == 2) v[l].cbuf = S.mem.arr<C>((size_t)L.nK * L.nS);
+  }
+}
+
+template <class C>
+static void diag_inverse(const C* Lf, int64_t N, C* Dinv, cudaStream_t st) {
+  int nb = (int)((N + CB - 1) / CB);
+  size_t sm = (size_t)(NB * NB + TL * NB) * sizeof(C) + (size_t)NB * TL * sizeof(C) + 64;
+  DPG_CUDA(cudaFuncSetAttribute(k_diag_inverse<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+  k_diag_inverse<C><<<nb, 256, sm, st>>>(Lf, N, Dinv);
+  DPG_CHECK_LAUNCH();
+}
+
+void ensure_workspace(SystemImpl& S, cudaStream_t st) {
+  if (S.ws) return;
+  WS* W = new WS();
+  S.ws = W;
+  const Level& F = S.levels.back();
+  const int64_t n = F.mesh.ndof;
+  W->x = S.mem.arr<double2>((size_t)n);
+  W->r = S.mem.arr<double2>((size_t)n);
+  W->p = S.mem.arr<double2>((size_t)n);
+  W->q = S.mem.arr<double2>((size_t)n);
+  W->z = S.mem.arr<double2>((size_t)n);
+  W->part = S.mem.arr<double2>(RED_BLOCKS);
+  W->sc = S.mem.arr<double2>(SC_COUNT);
+  DPG_CUDA(cudaMallocHost(&W->sc_host, SC_COUNT * sizeof(double2)));
+  W->bar = S.mem.arr<unsigned>(2);
+  W->err = S.mem.arr<int>(1);
+  DPG_CUDA(cudaMemsetAsync(W->bar, 0, 2 * sizeof(unsigned), st));
+  DPG_CUDA(cudaMemsetAsync(W->err, 0, sizeof(int), st));
+  alloc_level_ws<double2>(*W, S);
+  if (S.op.precision == DPGMG_PREC_MIXED) alloc_level_ws<float2>(*W, S);
+  const Level& C0 = S.levels[0];
+  if (C0.C64) {
+    int nb = (int)((C0.N0 + CB - 1) / CB);
+    W->Dinv64 = S.mem.arr<double2>((size_t)nb * CB * CB);
+    diag_inverse<double2>(C0.C64, C0.N0, W->Dinv64, st);
+    if (C0.C32) {
+      W->Dinv32 = S.mem.arr<float2>((size_t)nb * CB * CB);
+      diag_inverse<float2>(C0.C32, C0.N0, W->Dinv32, st);
+    }
+    int dev = 0, nsm = 0, per = 0;
+    DPG_CUDA(cudaGetDevice(&dev));
+    DPG_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    DPG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_coarse_solve<double2>, 256, 0));
+    int per32 = 0;
+    DPG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per32, k_coarse_solve<float2>, 256, 0));
+    W->coarse_grid = std::max(1, std::min(nb, nsm * std::max(1, std::min(per, per32))));
+  }
+  DPG_CUDA(cudaStreamSynchronize(st));
+}
+
+void free_workspace(SystemImpl& S) {
+  if (!S.ws) return;
+  WS* W = reinterpret_cast<WS*>(S.ws);
+  if (W->sc_host) cudaFreeHost(W->sc_host);
+  delete W;
+  S.ws = nullptr;
+}
+
+template <class C> static const C* dinv(WS& W);
+template <> const double2* dinv<double2>(WS& W) { return W.Dinv64; }
+template <> const float2* dinv<float2>(WS& W) { return W.Dinv32; }
+
+template <class C>
+static void coarse_solve(SystemImpl& S, WS& W, const C* r, C* e, cudaStream_t st) {
+  const Level& C0 = S.levels[0];
+  const int64_t N = C0.N0;
+  DPG_CUDA(cudaMemcpyAsync(e, r, (size_t)N * sizeof(C), cudaMemcpyDeviceToDevice, st));
+  const C* Lf = Prec<C>::Cf(C0);
+  const C* Di = dinv<C>(W);
+  unsigned* bar = W.bar;
+  int* err = W.err;
+  int64_t NN = N;
+  C* ep = e;
+  void* args[] = {(void*)&Lf, (void*)&Di, (void*)&NN, (void*)&ep, (void*)&bar, (void*)&err};
+  DPG_CUDA(cudaMemsetAsync(bar, 0, sizeof(unsigned), st));   // arrival counter (generation kept)
+  DPG_CUDA(cudaLaunchCooperativeKernel((void*)k_coarse_solve<C>, dim3(W.coarse_grid), dim3(256), args, 0, st));
+}
+
+// -------------------------------------------------------------- V-cycle
+static inline unsigned nblk(int64_t n) { return (unsigned)((n + 255) / 256); }
+
+template <class C>
+static void restrict_vec(const Level& F, const Level& Cl, const C* r1, C* rc, cudaStream_t st) {
+  if (F.kind == 1) {
+    k_gather<C><<<nblk(Cl.mesh.ndof), 256, 0, st>>>(F.inj, r1, rc, Cl.mesh.ndof);
+  } else {
+    k_csr_real<C><<<nblk(Cl.mesh.ndof), 256, 0, st>>>(F.PT_ptr, F.PT_col, F.PT_val, r1, rc, Cl.mesh.ndof, 0);
+  }
+  DPG_CHECK_LAUNCH();
+}
+
+template <class C>
+static void prolong_add(const Level& F, const Level& Cl, const C* ec, C* x, cudaStream_t st) {
+  if (F.kind == 1) {
+    k_scatter_add<C><<<nblk(Cl.mesh.ndof), 256, 0, st>>>(F.inj, ec, x, Cl.mesh.ndof);
+  } else {
+    k_csr_real<C><<<nblk(F.mesh.ndof), 256, 0, st>>>(F.P_ptr, F.P_col, F.P_val, ec, x, F.mesh.ndof, 1);
+  }
+  DPG_CHECK_LAUNCH();
+}
+
+template <class C>
+static void condense(const Level& F, const C* r, C* rs, C* cbuf, cudaStream_t st) {
+  size_t sm = (size_t)F.nI * sizeof(C) + 16;
+  k_condense_apply<C><<<(unsigned)F.nK, 256, sm, st>>>(F.nS, F.nI, F.I_glob, Prec<C>::Y(F), r, cbuf);
+  DPG_CHECK_LAUNCH();
+  k_condense_sum<C><<<nblk(F.mesh.ndof), 256, 0, st>>>(F.sslot_ptr, F.sslots, cbuf, F.smask, r, rs, F.mesh.ndof);
+  DPG_CHECK_LAUNCH();
+}
+
+template <class C>
+static void backsub(const Level& F, const C* r, C* x, cudaStream_t st) {
+  size_t sm = (size_t)(F.nI + F.nS) * sizeof(C) + 16;
+  k_backsub<C><<<(unsigned)F.nK, 256, sm, st>>>(F.nS, F.nI, F.S_glob, F.I_glob, Prec<C>::Ai(F), Prec<C>::Y(F), r, x);
+  DPG_CHECK_LAUNCH();
+}
+
+// x = B_l r (r is not modified)
+template <class C>
+static void vcycle(SystemImpl& S, WS& W, int l, const C* r, C* x, cudaStream_t st) {
+  auto& V = wsv<C>(W);
+  const Level& F = S.levels[l];
+  const int64_t n = F.mesh.ndof;
+  if (l == 0) {
+    if (F.C64) coarse_solve<C>(S, W, r, x, st);
+    else {
+      k_zero<C><<<nblk(n), 256, 0, st>>>(x, n);
+      DPG_CHECK_LAUNCH();
+    }
+    return;
+  }
+  const Level& Cl = S.levels[l - 1];
+  const C* Avals = Prec<C>::A(F.A);
+  const C* rs = r;
+  if (F.kind == 2) {
+    condense<C>(F, r, V[l].rs, V[l].cbuf, st);
+    rs = V[l].rs;
+  }
+  // pre-smoothing from x = 0
+  for (int k = 0; k < S.op.nu_pre; ++k) {
+    if (k == 0) {
+      smooth<C>(F, rs, x, F.theta, 0, V[l].pbuf, st);
+    } else {
+      spmv<C>(F.A, Avals, x, rs, V[l].t, 1, st);
+      smooth<C>(F, V[l].t, x, F.theta, 1, V[l].pbuf, st);
+    }
+  }
+  if (S.op.nu_pre == 0) {
+    k_zero<C><<<nblk(n), 256, 0, st>>>(x, n);
+    DPG_CHECK_LAUNCH();
+  }
+  // coarse-grid correction
+  spmv<C>(F.A, Avals, x, rs, V[l].t, 1, st);
+  restrict_vec<C>(F, Cl, V[l].t, V[l - 1].r, st);
+  vcycle<C>(S, W, l - 1, V[l - 1].r, V[l - 1].x, st);
+  prolong_add<C>(F, Cl, V[l - 1].x, x, st);
+  for (int k = 0; k < S.op.nu_post; ++k) {
+    spmv<C>(F.A, Avals, x, rs, V[l].t, 1, st);
+    smooth<C>(F, V[l].t, x, F.theta, 1, V[l].pbuf, st);
+  }
+  if (F.kind == 2) backsub<C>(F, r, x, st);
+}
+
+// z = B r on the finest level in the V-cycle precision
+static void precondition(SystemImpl& S, WS& W, const double2* r, double2* z, cudaStream_t st) {
+  const int L = (int)S.levels.size() - 1;
+  const int64_t n = S.levels[L].mesh.ndof;
+  if (S.op.precision == DPGMG_PREC_MIXED) {
+    auto& V = W.w32;
+    k_narrow<<<nblk(n), 256, 0, st>>>(r, V[L].r, n);
+    DPG_CHECK_LAUNCH();
+    vcycle<float2>(S, W, L, V[L].r, V[L].x, st);
+    k_widen<<<nblk(n), 256, 0, st>>>(V[L].x, z, n);
+    DPG_CHECK_LAUNCH();
+  } else {
+    vcycle<double2>(S, W, L, r, z, st);
+  }
+}
+
+static void dot(WS& W, const double2* u, const double2* v, int64_t n, int which, cudaStream_t st) {
+  k_dot_partial<<<RED_BLOCKS, 256, 0, st>>>(u, v, n, W.part);
+  DPG_CHECK_LAUNCH();
+  k_dot_finish<<<1, 256, 0, st>>>(W.part, RED_BLOCKS, W.sc, which);
+  DPG_CHECK_LAUNCH();
+}
+
+static int check_err(WS& W, cudaStream_t st) {
+  int e = 0;
+  DPG_CUDA(cudaMemcpyAsync(&e, W.err, sizeof(int), cudaMemcpyDeviceToHost, st));
+  DPG_CUDA(cudaStreamSynchronize(st));
+  return e;
+}
+
+static const ECSRDev& cg_operator(SystemImpl& S, WS& W, cudaStream_t st) {
+  const Level& F = S.levels.back();
+  if (S.levels.size() > 1 && F.kind == 1) return F.A;
+  if (!W.acg_owned) {
+    // finest operator assembled separately (single level, or h-transition below the finest)
+    std::vector<std::vector<int64_t>> g(F.mesh.nelem);
+    std::vector<int64_t> ent(F.mesh.loc.size());
+    for (int64_t e = 0; e < F.mesh.nelem; ++e) {
+      F.mesh.elem_entities(e, ent.data());
+      for (int64_t E : ent)
+        if (E >= 0) g[e].push_back(E);
+      std::sort(g[e].begin(), g[e].end());
+      g[e].erase(std::unique(g[e].begin(), g[e].end()), g[e].end());
+    }
+    ECSRHost H = build_ecsr(F.mesh, g);
+    assemble_ecsr(S.mem, F.mesh, H, W.Acg, st);
+    ecsr_add_elements(W.Acg, F.E, F.dofs, F.mesh.nelem, F.nloc, st);
+    DPG_CUDA(cudaStreamSynchronize(st));
+    W.acg_owned = true;
+  }
+  return W.Acg;
+}
+
+int pcg_solve(SystemImpl& S, cudaStream_t st, double2* xout, dpgmg_stats* stats) {
+  ensure_workspace(S, st);
+  WS& W = *reinterpret_cast<WS*>(S.ws);
+  const ECSRDev& A = cg_operator(S, W, st);
+  const int64_t n = S.levels.back().mesh.ndof;
+  cudaEvent_t e0, e1;
+  DPG_CUDA(cudaEventCreate(&e0));
+  DPG_CUDA(cudaEventCreate(&e1));
+  DPG_CUDA(cudaEventRecord(e0, st));
+  k_zero<double2><<<nblk(n), 256, 0, st>>>(W.x, n);
+  DPG_CHECK_LAUNCH();
+  DPG_CUDA(cudaMemcpyAsync(W.r, S.b, (size_t)n * sizeof(double2), cudaMemcpyDeviceToDevice, st));
+  dot(W, W.r, W.r, n, 1, st);   // ||b||^2
+  DPG_CUDA(cudaMemcpyAsync(W.sc_host, W.sc, SC_COUNT * sizeof(double2), cudaMemcpyDeviceToHost, st));
+  DPG_CUDA(cudaStreamSynchronize(st));
+  const double nb = std::sqrt(W.sc_host[SC_RR].x);
+  int status = DPGMG_OK;
+  int it = 0;
+  double rel = 1.0;
+  if (nb > 0.0) {
+    precondition(S, W, W.r, W.z, st);
+    dot(W, W.z, W.r, n, 3, st);   // rho = z^H r
+    DPG_CUDA(cudaMemcpyAsync(W.p, W.z, (size_t)n * sizeof(double2), cudaMemcpyDeviceToDevice, st));
+    while (it < S.op.max_iter) {
+      spmv<double2>(A, A.v64, W.p, nullptr, W.q, 0, st);
+      dot(W, W.p, W.q, n, 0, st);   // pq = p^H q, alpha = rho / pq
+      k_cg_update<<<RED_BLOCKS, 256, 0, st>>>(W.x, W.r, W.p, W.q, W.sc, n, W.part);
+      DPG_CHECK_LAUNCH();
+      k_dot_finish<<<1, 256, 0, st>>>(W.part, RED_BLOCKS, W.sc, 1);
+      DPG_CHECK_LAUNCH();
+      DPG_CUDA(cudaMemcpyAsync(W.sc_host, W.sc, SC_COUNT * sizeof(double2), cudaMemcpyDeviceToHost, st));
+      DPG_CUDA(cudaStreamSynchronize(st));
+      ++it;
+      const double pq = W.sc_host[SC_PQ].x;
+      if (!(pq > 0.0) || !std::isfinite(pq)) { status = DPGMG_ERR_BREAKDOWN; break; }
+      rel = std::sqrt(W.sc_host[SC_RR].x) / nb;
+      if (!std::isfinite(rel)) { status = DPGMG_ERR_BREAKDOWN; break; }
+      if (rel <= S.op.tol) break;
+      precondition(S, W, W.r, W.z, st);
+      dot(W, W.z, W.r, n, 2, st);   // rho_new = z^H r, beta
+      k_cg_dir<<<RED_BLOCKS, 256, 0, st>>>(W.p, W.z, W.sc, n);
+      DPG_CHECK_LAUNCH();
+    }
+    if (status == DPGMG_OK && rel > S.op.tol) status = DPGMG_ERR_NOT_CONVERGED;
+  }
+  DPG_CUDA(cudaEventRecord(e1, st));
+  DPG_CUDA(cudaEventSynchronize(e1));
+  float ms = 0.f;
+  DPG_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (check_err(W, st)) status = DPGMG_ERR_TIMEOUT;
+  // true residual ||b - A x|| / ||b|| in FP64
+  double true_rel = 0.0;
+  if (nb > 0.0) {
+    spmv<double2>(A, A.v64, W.x, S.b, W.q, 1, st);
+    dot(W, W.q, W.q, n, 1, st);
+    DPG_CUDA(cudaMemcpyAsync(W.sc_host, W.sc, SC_COUNT * sizeof(double2), cudaMemcpyDeviceToHost, st));
+    DPG_CUDA(cudaStreamSynchronize(st));
+    true_rel = std::sqrt(W.sc_host[SC_RR].x) / nb;
+  }
+  if (xout) DPG_CUDA(cudaMemcpyAsync(xout, W.x, (size_t)n * sizeof(double2), cudaMemcpyDeviceToDevice, st));
+  if (stats) {
+    stats->iters = it;
+    stats->relres = rel;
+    stats->true_relres = true_rel;
+    stats->t_pcg_ms = ms;
+    stats->t_setup_ms = S.t_setup_ms;
+    stats->bytes_per_iter = S.bytes_per_iter;
+    stats->n_dof = n;
+  }
+  return status;
+}
+
+// ---------------------------------------------------------------- theta
+// theta = 1 / (1.05 lambda), lambda from 30 power iterations x <- S M x /
+// ||S M x|| started from a SplitMix64 vector (seed 12345) on the smoothing
+// space, then the Rayleigh quotient (M x, S M x) / (M x, x).  FP64.
+__device__ __forceinline__ uint64_t splitmix64(uint64_t seed, uint64_t k) {
+  uint64_t z = seed + (k + 1) * 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+__global__ void k_start_vector(double2* x, int64_t n, const int64_t* slot_ptr) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const double s = 1.0 / 9007199254740992.0;
+  double re = 2.0 * (double)(splitmix64(12345ull, 2 * (uint64_t)i) >> 11) * s - 1.0;
+  double im = 2.0 * (double)(splitmix64(12345ull, 2 * (uint64_t)i + 1) >> 11) * s - 1.0;
+  bool in = slot_ptr[i + 1] > slot_ptr[i];   // DOF belongs to some patch
+  x[i] = in ? make_double2(re, im) : make_double2(0, 0);
+}
+__global__ void k_scale(double2* x, int64_t n, const double2* sc, int slot) {
+  double s = 1.0 / sqrt(sc[slot].x);
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    x[i] = make_double2(x[i].x * s, x[i].y * s);
+}
+
+void estimate_theta(SystemImpl& S, int l, cudaStream_t st) {
+  Level& F = S.levels[l];
+  if (S.op.theta > 0.0) { F.theta = S.op.theta; return; }
+  const int64_t n = F.mesh.ndof;
+  Alloc tmp;
+  tmp.budget = (size_t)-1;
+  double2* x = tmp.arr<double2>((size_t)n);
+  double2* y = tmp.arr<double2>((size_t)n);
+  double2* t = tmp.arr<double2>((size_t)n);
+  double2* pbuf = tmp.arr<double2>((size_t)std::max<int64_t>(F.P.nslots, 1));
+  double2* part = tmp.arr<double2>(RED_BLOCKS);
+  double2* sc = tmp.arr<double2>(SC_COUNT);
+  WS W;
+  W.part = part;
+  W.sc = sc;
+  k_start_vector<<<nblk(n), 256, 0, st>>>(x, n, F.P.slot_ptr);
+  DPG_CHECK_LAUNCH();
+  dot(W, x, x, n, 1, st);
+  k_scale<<<RED_BLOCKS, 256, 0, st>>>(x, n, sc, SC_RR);
+  for (int k = 0; k < 30; ++k) {
+    spmv<double2>(F.A, F.A.v64, x, nullptr, t, 0, st);
+    smooth<double2>(F, t, y, 1.0, 0, pbuf, st);
+    dot(W, y, y, n, 1, st);
+    k_scale<<<RED_BLOCKS, 256, 0, st>>>(y, n, sc, SC_RR);
+    std::swap(x, y);
+  }
+  spmv<double2>(F.A, F.A.v64, x, nullptr, t, 0, st);   // M x
+  smooth<double2>(F, t, y, 1.0, 0, pbuf, st);          // S M x
+  double2 h[SC_COUNT];
+  dot(W, t, y, n, 3, st);                               // (M x)^H (S M x) -> RHO
+  DPG_CUDA(cudaMemcpyAsync(h, sc, sizeof(h), cudaMemcpyDeviceToHost, st));
+  DPG_CUDA(cudaStreamSynchronize(st));
+  double num = h[SC_RHO].x;
+  dot(W, x, t, n, 3, st);                               // x^H M x
+  DPG_CUDA(cudaMemcpyAsync(h, sc, sizeof(h), cudaMemcpyDeviceToHost, st));
+  DPG_CUDA(cudaStreamSynchronize(st));
+  double den = h[SC_RHO].x;
+  double lam = num / den;
+  F.theta = 1.0 / (1.05 * lam);
+  W.part = nullptr;
+  W.sc = nullptr;
+}
+
+// ------------------------------------------------------------ introspection
+template <class C>
+static void apply_t(SystemImpl& S, WS& W, int op, int l, const C* x, C* y, cudaStream_t st) {
+  const Level& F = S.levels[l];
+  auto& V = wsv<C>(W);
+  switch (op) {
+    case DPGMG_OP_A:
+      spmv<C>(F.A, Prec<C>::A(F.A), x, nullptr, y, 0, st);
+      break;
+    case DPGMG_OP_SMOOTH:
+      smooth<C>(F, x, y, F.theta, 0, V[l].pbuf, st);
+      break;
+    case DPGMG_OP_VCYCLE:
+      vcycle<C>(S, W, l, x, y, st);
+      break;
+    case DPGMG_OP_RESTRICT:
+      restrict_vec<C>(F, S.levels[l - 1], x, y, st);
+      break;
+    case DPGMG_OP_PROLONG:
+      k_zero<C><<<nblk(F.mesh.ndof), 256, 0, st>>>(y, F.mesh.ndof);
+      prolong_add<C>(F, S.levels[l - 1], x, y, st);
+      break;
+    case DPGMG_OP_CONDENSE:
+      condense<C>(F, x, y, V[l].cbuf, st);
+      break;
+    case DPGMG_OP_COARSE:
+      coarse_solve<C>(S, W, x, y, st);
+      break;
+  }
+}
+
+void apply_op(SystemImpl& S, int op, int l, const double2* x, double2* y, cudaStream_t st) {
+  ensure_workspace(S, st);
+  WS& W = *reinterpret_cast<WS*>(S.ws);
+  if (op == DPGMG_OP_AFULL) {
+    const ECSRDev& A = cg_operator(S, W, st);
+    spmv<double2>(A, A.v64, x, nullptr, y, 0, st);
+    return;
+  }
+  if (S.op.precision == DPGMG_PREC_MIXED) {
+    const Level& F = S.levels[l];
+    int64_t nin = F.mesh.ndof, nout = F.mesh.ndof;
+    if (op == DPGMG_OP_RESTRICT) nout = S.levels[l - 1].mesh.ndof;
+    if (op == DPGMG_OP_PROLONG) nin = S.levels[l - 1].mesh.ndof;
+    Alloc tmp;
+    tmp.budget = (size_t)-1;
+    float2* xi = tmp.arr<float2>((size_t)nin);
+    float2* yo = tmp.arr<float2>((size_t)nout);
+    k_narrow<<<nblk(nin), 256, 0, st>>>(x, xi, nin);
+    apply_t<float2>(S, W, op, l, xi, yo, st);
+    k_widen<<<nblk(nout), 256, 0, st>>>(yo, y, nout);
+    DPG_CUDA(cudaStreamSynchronize(st));
+  } else {
+    apply_t<double2>(S, W, op, l, x, y, st);
+  }
+  DPG_CHECK_LAUNCH();
+  if (check_err(W, st)) throw Err{DPGMG_ERR_TIMEOUT, "coarse solve barrier timed out"};
+}
+
+}  // namespace dpgmg

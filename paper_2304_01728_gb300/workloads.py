@@ -1,0 +1,67 @@
+"""Seeded synthetic workloads (problem parameters only, no solver arithmetic).
+
+The paper's convergence studies use a Gaussian beam in the unit cube (Sec. 4,
+"Problem Setup") and its application a layered high-contrast seismic model
+driven by a tight Gaussian point source (Sec. 5).  Neither the beam data nor
+the seismic model is available, so these generators produce inputs of the
+same shape: unit-cube Gaussian sources, and a box with horizontally layered
+piecewise-constant wavespeed and a point-like Gaussian source.
+
+Random draws use SplitMix64 in counter form, u_k = (out_k >> 11) 2^-53,
+out_k = mix(seed + (k+1) 0x9E3779B97F4A7C15).
+"""
+import math
+
+_G = 0x9E3779B97F4A7C15
+_M = (1 << 64) - 1
+
+
+def _u(seed, k):
+    z = (seed + (k + 1) * _G) & _M
+    z = ((z ^ (z >> 30)) * 0xBF58476D1CE4E5B9) & _M
+    z = ((z ^ (z >> 27)) * 0x94D049BB133111EB) & _M
+    z ^= z >> 31
+    return (z >> 11) * (1.0 / 9007199254740992.0)
+
+
+def config1():
+    """4^3 hexes, p = 2, omega = 4, c = 1, Gaussian at the cube centre, 2-level p-MG, FP64."""
+    return dict(problem=dict(n=(4, 4, 4), p=2, omega=4.0, src_center=(0.5, 0.5, 0.5), src_width=0.1),
+                opts=dict(n_levels=2, p_min=1, precision="fp64", tol=1e-8),
+                name="unit cube 4^3 p=2 omega=4, 2-level p-MG, complex128")
+
+
+def config2(precision="mixed"):
+    """16^3 hexes, p = 3, omega = 16 pi, c = 1, seeded source in [0.3, 0.7]^3, 3 levels."""
+    x0 = tuple(0.3 + 0.4 * _u(2, k) for k in range(3))
+    return dict(problem=dict(n=(16, 16, 16), p=3, omega=16 * math.pi, src_center=x0, src_width=0.1),
+                opts=dict(n_levels=3, p_min=2, precision=precision, tol=1e-8),
+                name="unit cube 16^3 p=3 omega=16pi, 3-level h/p V(1,1), %s V-cycle" % precision)
+
+
+def config3(precision="mixed"):
+    """[0,2]x[0,2]x[0,1], 32x32x16 hexes, p = 3, omega = 20 pi, 6 seeded layers, 4 levels."""
+    n = (32, 32, 16)
+    cuts = []
+    k = 0
+    while len(cuts) < 5:
+        v = 1 + int(15 * _u(3, k))
+        k += 1
+        if v not in cuts:
+            cuts.append(v)
+    cuts.sort()
+    speeds = []
+    for _ in range(6):
+        speeds.append(0.1 + 0.9 * _u(3, k))
+        k += 1
+    x0 = (0.5 + _u(3, k), 0.5 + _u(3, k + 1), 0.25 + 0.5 * _u(3, k + 2))
+    bounds = [0] + cuts + [n[2]]
+    c = []
+    for kz in range(n[2]):
+        layer = max(i for i in range(6) if bounds[i] <= kz)
+        c.extend([speeds[layer]] * (n[0] * n[1]))
+    return dict(problem=dict(n=n, p=3, omega=20 * math.pi, x0=(0, 0, 0), x1=(2, 2, 1), wavespeed=c,
+                             src_center=x0, src_width=0.02),
+                opts=dict(n_levels=4, p_min=2, precision=precision, tol=1e-8),
+                name="layered box 32x32x16 p=3 omega=20pi, 4-level, %s V-cycle" % precision,
+                layers=dict(cuts=cuts, speeds=speeds))

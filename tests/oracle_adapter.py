@@ -1,0 +1,40 @@
+"""Builds oracle systems from the same workload dictionaries the library gets.
+
+Test infrastructure: the tests drive both sides with identical seeded inputs
+(``paper_2304_01728_gb300.workloads``) and compare element by element.
+"""
+import numpy as np
+
+from oracle.assembly import build_fine
+from oracle.hierarchy import build_hierarchy
+from oracle.problem import GaussianSource, Manufactured, PlaneWave
+
+
+def oracle_load(pk):
+    src = pk.get("source", "gaussian")
+    if src == "gaussian":
+        return GaussianSource(pk.get("src_center", (0.5, 0.5, 0.5)), pk.get("src_width", 0.1), pk.get("src_amp", 1.0))
+    if src == "plane_wave":
+        return PlaneWave(pk["wave_dir"], pk["omega"], 1.0)
+    return Manufactured(pk["mf_coeffs"], pk["omega"], pk.get("x0", (0, 0, 0)), pk.get("x1", (1, 1, 1)))
+
+
+def oracle_system(pk, ok, hierarchy=True):
+    fs = build_fine(pk["n"], pk["p"], pk["omega"], wavespeed=pk.get("wavespeed"), load=oracle_load(pk),
+                    x0=pk.get("x0", (0, 0, 0)), x1=pk.get("x1", (1, 1, 1)))
+    A, b = fs.assemble()
+    levels = None
+    if hierarchy:
+        levels = build_hierarchy(fs.mesh, fs.Kc, fs.dofs, ok.get("n_levels", 2), ok.get("p_min", 2),
+                                 coarsest=ok.get("coarsest", "cholesky"))
+    return fs, A, b, levels
+
+
+def rel(a, b):
+    nb = np.linalg.norm(b)
+    return np.linalg.norm(a - b) / (nb if nb > 0 else 1.0)
+
+
+def rand_vec(n, seed):
+    rng = np.random.default_rng(seed)
+    return rng.standard_normal(n) + 1j * rng.standard_normal(n)

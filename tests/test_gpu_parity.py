@@ -1,0 +1,266 @@
+"""GPU parity of every step of the DPG-MG hot path against the FP64 oracle.
+
+All calls go through the C ABI (libdpgmg.so via the ctypes binding).  The
+FP64 path is compared at 1e-11 relative (roundoff of a different but
+equivalent arithmetic order: the library uses the real form of the Gram
+matrix and closed-form 1D integrals, the oracle complex quadrature); the
+solution at the spec bar of 1e-7 relative L2 with the iteration count
+within 10% (equal in practice on the FP64 path).
+"""
+import numpy as np
+import pytest
+
+from oracle.solver import mg_pcg, vcycle
+from oracle.traces import field_dofs, trace_dofs
+from paper_2304_01728_gb300 import dpgmg as D
+from paper_2304_01728_gb300 import workloads
+from tests.oracle_adapter import oracle_system, rand_vec, rel
+
+pytestmark = pytest.mark.gpu
+
+TOL_FP64 = 1e-11
+
+
+class Case:
+    def __init__(self, pk, ok):
+        self.pk, self.ok = pk, ok
+        self.solver = D.Solver(pk, **ok)
+        self.fs, self.A, self.b, self.levels = oracle_system(pk, ok)
+        self.L = len(self.levels) - 1
+
+    def gpu_level(self, l):
+        return self.solver.level(l)
+
+
+@pytest.fixture(scope="module")
+def c1():
+    w = workloads.config1()
+    c = Case(w["problem"], w["opts"])
+    yield c
+    c.solver.close()
+
+
+@pytest.fixture(scope="module")
+def ph():
+    """4^3 p2 -> 4^3 p1 -> 2^3 p1: a p- and an h-transition, heterogeneous c."""
+    c = np.random.default_rng(11).uniform(0.6, 1.4, 64)
+    pk = dict(n=(4, 4, 4), p=2, omega=5.0, wavespeed=c, src_center=(0.3, 0.6, 0.45), src_width=0.15,
+              x0=(0, 0, 0), x1=(1.0, 1.2, 0.9))
+    ok = dict(n_levels=3, p_min=1, precision="fp64", tol=1e-10)
+    case = Case(pk, ok)
+    yield case
+    case.solver.close()
+
+
+@pytest.fixture(scope="module")
+def hh():
+    """4^3 p2 -> 2^3 p2: one h-transition at p = 2."""
+    pk = dict(n=(4, 4, 4), p=2, omega=6.0, src_center=(0.55, 0.45, 0.5), src_width=0.2)
+    ok = dict(n_levels=2, p_min=2, precision="fp64", tol=1e-10)
+    case = Case(pk, ok)
+    yield case
+    case.solver.close()
+
+
+CASES = ["c1", "ph", "hh"]
+
+
+@pytest.mark.parametrize("name", CASES)
+def test_element_matrices_every_level(name, request):
+    c = request.getfixturevalue(name)
+    s = c.solver
+    for l in range(c.L + 1):
+        lev = c.levels[c.L - l] if False else c.levels[l]
+        nloc = lev.E.shape[1]
+        for e in range(lev.E.shape[0]):
+            M = D.dpgmg_element_matrix(s.h, s.s, l, e, nloc)
+            assert rel(M, lev.E[e]) < TOL_FP64, (l, e, rel(M, lev.E[e]))
+    # finest condensed loads
+    nloc = c.fs.Kc.shape[1]
+    for e in range(c.fs.mesh.n_elem):
+        _, F = D.dpgmg_element_matrix(s.h, s.s, c.L, e, nloc, with_load=True)
+        assert rel(F, c.fs.Fc[e]) < TOL_FP64
+
+
+@pytest.mark.parametrize("name", CASES)
+def test_rhs_and_cg_operator(name, request):
+    c = request.getfixturevalue(name)
+    s = c.solver
+    b = D.dpgmg_rhs(s.h, s.s, c.A.shape[0])
+    assert rel(b, c.b) < TOL_FP64
+    x = rand_vec(c.A.shape[0], 1)
+    y = D.dpgmg_apply(s.h, s.s, D.OP_AFULL, c.L, x, c.A.shape[0])
+    assert rel(y, c.A @ x) < TOL_FP64
+
+
+@pytest.mark.parametrize("name", CASES)
+def test_level_structure_and_theta(name, request):
+    c = request.getfixturevalue(name)
+    for l in range(1, c.L + 1):
+        g = c.gpu_level(l)
+        o = c.levels[l]
+        assert g.n_dof == o.mesh.n_dof
+        assert g.kind == {"p": 1, "h": 2}[o.kind]
+        sizes = np.array([len(x) for x in o.patches])
+        assert g.n_patches == len(sizes) and g.patch_max == sizes.max()
+        assert g.sum_patch_sq == int(np.sum(sizes ** 2))
+        assert g.n_smooth == int(o.smask.sum())
+        assert abs(g.theta - o.theta) < 1e-9 * o.theta, (g.theta, o.theta)
+
+
+@pytest.mark.parametrize("name", CASES)
+def test_smoothing_operator_and_smoother(name, request):
+    c = request.getfixturevalue(name)
+    s = c.solver
+    for l in range(1, c.L + 1):
+        o = c.levels[l]
+        n = o.mesh.n_dof
+        x = rand_vec(n, 10 + l)
+        y = D.dpgmg_apply(s.h, s.s, D.OP_A, l, x, n)
+        assert rel(y, o.M @ x) < TOL_FP64
+        from oracle.hierarchy import smoother
+        y = D.dpgmg_apply(s.h, s.s, D.OP_SMOOTH, l, x, n)
+        assert rel(y, o.theta * smoother(o, x)) < TOL_FP64
+
+
+@pytest.mark.parametrize("name", CASES)
+def test_transfers(name, request):
+    c = request.getfixturevalue(name)
+    s = c.solver
+    for l in range(1, c.L + 1):
+        o, oc = c.levels[l], c.levels[l - 1]
+        nf, nc = o.mesh.n_dof, oc.mesh.n_dof
+        x = rand_vec(nf, 20 + l)
+        xc = rand_vec(nc, 30 + l)
+        r = D.dpgmg_apply(s.h, s.s, D.OP_RESTRICT, l, x, nc)
+        p = D.dpgmg_apply(s.h, s.s, D.OP_PROLONG, l, xc, nf)
+        if o.kind == "p":
+            assert np.array_equal(r, x[o.inj])
+            ref = np.zeros(nf, dtype=complex)
+            ref[o.inj] = xc
+            assert np.array_equal(p, ref)
+        else:
+            assert rel(r, o.P.conj().T @ x) < 1e-13
+            assert rel(p, o.P @ xc) < 1e-13
+            y = D.dpgmg_apply(s.h, s.s, D.OP_CONDENSE, l, x, nf)
+            ref = np.where(o.smask, x, 0)
+            for Sg, Ig, T in zip(o.S, o.I, o.T):
+                ref[Sg] -= T @ x[Ig]
+            assert rel(y, ref) < TOL_FP64
+
+
+@pytest.mark.parametrize("name", CASES)
+def test_coarse_solve_and_vcycle(name, request):
+    c = request.getfixturevalue(name)
+    s = c.solver
+    import scipy.linalg as sla
+    o0 = c.levels[0]
+    x = rand_vec(o0.mesh.n_dof, 5)
+    y = D.dpgmg_apply(s.h, s.s, D.OP_COARSE, 0, x, o0.mesh.n_dof)
+    assert rel(y, sla.cho_solve(o0.chol, x)) < 1e-10
+    for l in range(1, c.L + 1):
+        n = c.levels[l].mesh.n_dof
+        x = rand_vec(n, 40 + l)
+        y = D.dpgmg_apply(s.h, s.s, D.OP_VCYCLE, l, x, n)
+        ref = vcycle(c.levels, l, x)
+        assert rel(y, ref) < 1e-10, rel(y, ref)
+
+
+@pytest.mark.parametrize("name", CASES)
+def test_pcg_solution_and_iterations(name, request):
+    c = request.getfixturevalue(name)
+    tol = c.ok["tol"]
+    x_ref, it_ref, hist = mg_pcg(c.levels, c.A, c.b, tol=tol)
+    x, f, st, code = c.solver.solve()
+    assert code == D.DPGMG_OK
+    assert st.relres <= tol and st.true_relres <= 10 * tol
+    assert abs(st.iters - it_ref) <= max(1, 0.1 * it_ref), (st.iters, it_ref)
+    assert rel(x, x_ref) < 1e-7
+    f_ref = c.fs.fields(x_ref)
+    assert rel(f.reshape(f_ref.shape), f_ref) < 1e-7
+
+
+def test_manufactured_solution_exact_through_gpu():
+    p = 3
+    C = np.random.default_rng(3).standard_normal((4, p, p, p)) + 1j * np.random.default_rng(4).standard_normal((4, p, p, p))
+    x0, x1 = (0.0, 0.0, 0.0), (1.0, 2.0, 1.0)
+    c = np.random.default_rng(5).uniform(0.5, 2.0, 4 * 2 * 2)
+    pk = dict(n=(4, 2, 2), p=p, omega=7.0, x0=x0, x1=x1, wavespeed=c, source="manufactured", mf_coeffs=C)
+    from oracle.mesh import Mesh
+    from oracle.problem import Manufactured
+    ld = Manufactured(C, 7.0, x0, x1)
+    m = Mesh((4, 2, 2), p, x0, x1)
+    with D.Solver(pk, n_levels=2, p_min=2, tol=1e-13, max_iter=500) as s:
+        x, f, st, code = s.solve()
+    assert rel(x, trace_dofs(m, ld.p, ld.u)) < 1e-9
+    fe = field_dofs(m, ld.p, ld.u)
+    assert rel(f.reshape(fe.shape), fe) < 1e-9
+
+
+def test_plane_wave_load_matches_oracle():
+    pk = dict(n=(3, 2, 2), p=2, omega=4.0, source="plane_wave", wave_dir=(1.0, 2.0, 2.0))
+    fs, A, b, _ = oracle_system(pk, {}, hierarchy=False)
+    with D.Solver(pk, n_levels=1) as s:
+        g = D.dpgmg_rhs(s.h, s.s, A.shape[0])
+        assert rel(g, b) < TOL_FP64
+        x, f, st, code = s.solve()
+        assert code == D.DPGMG_OK and st.iters <= 2
+    import scipy.sparse.linalg as spla
+    assert rel(x, spla.spsolve(A.tocsc(), b)) < 1e-10
+
+
+def test_mixed_precision_c1(c1):
+    w = workloads.config1()
+    ok = dict(w["opts"], precision="mixed")
+    x_ref, it_ref, _ = mg_pcg(c1.levels, c1.A, c1.b, tol=ok["tol"])
+    with D.Solver(w["problem"], **ok) as s:
+        n = c1.A.shape[0]
+        v = rand_vec(n, 9)
+        y = D.dpgmg_apply(s.h, s.s, D.OP_VCYCLE, c1.L, v, n)
+        assert rel(y, vcycle(c1.levels, c1.L, v)) < 1e-5
+        x, f, st, code = s.solve()
+    assert code == D.DPGMG_OK and st.true_relres <= 1e-8 * 10
+    assert abs(st.iters - it_ref) <= max(1, 0.1 * it_ref)
+    assert rel(x, x_ref) < 1e-7
+
+
+def test_coarsest_none_matches_oracle():
+    w = workloads.config1()
+    ok = dict(w["opts"], coarsest="none")
+    fs, A, b, levels = oracle_system(w["problem"], ok)
+    _, it_ref, _ = mg_pcg(levels, A, b, tol=ok["tol"])
+    with D.Solver(w["problem"], **ok) as s:
+        x, f, st, code = s.solve()
+    assert code == D.DPGMG_OK and abs(st.iters - it_ref) <= max(1, 0.1 * it_ref)
+
+
+def test_error_statuses():
+    w = workloads.config1()
+    h = D.dpgmg_create(0)
+    try:
+        pb, keep = D.make_problem(**w["problem"])
+        op = D.make_opts(**w["opts"])
+        pb.p = 0
+        with pytest.raises(D.DpgmgError) as e:
+            D.dpgmg_setup(h, pb, op)
+        assert e.value.code == D.DPGMG_ERR_ARG
+        pb.p = 2
+        pb.dp = 2
+        with pytest.raises(D.DpgmgError) as e:
+            D.dpgmg_setup(h, pb, op)
+        assert e.value.code == D.DPGMG_ERR_ARG
+    finally:
+        D.dpgmg_destroy(h)
+    # budget far below the footprint: refused before any allocation
+    h = D.dpgmg_create(0, mem_budget_bytes=1 << 20)
+    try:
+        pb, keep = D.make_problem(**w["problem"])
+        with pytest.raises(D.DpgmgError) as e:
+            D.dpgmg_setup(h, pb, D.make_opts(**w["opts"]))
+        assert e.value.code == D.DPGMG_ERR_NOMEM
+    finally:
+        D.dpgmg_destroy(h)
+    # iteration cap: NOT_CONVERGED with outputs and stats written
+    with D.Solver(w["problem"], **dict(w["opts"], max_iter=2)) as s:
+        x, f, st, code = s.solve()
+        assert code == D.DPGMG_ERR_NOT_CONVERGED and st.iters == 2 and np.linalg.norm(x) > 0
