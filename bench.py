@@ -1,0 +1,386 @@
+#!/usr/bin/env python3
+"""Benchmark of the DPG-MG solver (MG-preconditioned CG on the condensed DPG trace system).
+
+One step = one pass of the whole hot path through the C ABI: dpgmg_setup
+(batched element DPG work, assembly, hierarchy, patch factorisations,
+coarsest factor) + dpgmg_solve (PCG to relative residual 1e-8, field
+recovery) + dpgmg_release, on the 16^3, p = 3, omega = 16 pi unit-cube
+workload with a 3-level h/p V(1,1)-cycle.
+
+value  = DOF-iterations per second of the PCG phase (N_dof * iterations /
+         PCG device time), summed over ranks; ms_per_step is the whole step.
+e2e    = the same metric with the end-to-end time of setup + solve through the
+         public API with host input and output buffers (copies included).
+roofline: the finest-level smoother product kernel, timed live with CUDA
+         events on the library's stream inside the timed steps.
+cpu_baseline: the FP64 oracle (test infrastructure) on a bounded sample of
+         the same workload (a 4^3-element sub-box of the 16^3 mesh around the
+         source, same h, p, omega, 3 levels), PCG phase only, one core.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
+       [--config 2] [--precision mixed|fp64]
+"""
+import argparse
+import ctypes
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "DOF-iters/s of MG-PCG to rel. residual 1e-8"
+UNIT = "DOF-iter/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--config", type=int, default=2, choices=[1, 2, 3])
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp64-compare", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--oracle-sample", action="store_true", help=argparse.SUPPRESS)
+    ap.add_argument("--oracle-steps", type=int, default=1, help=argparse.SUPPRESS)
+    return ap.parse_args()
+
+
+def workload(cfg, precision):
+    from paper_2304_01728_gb300 import workloads
+    return {1: workloads.config1, 2: lambda: workloads.config2(precision),
+            3: lambda: workloads.config3(precision)}[cfg]()
+
+
+# ------------------------------------------------------------------ oracle
+def oracle_sample_problem(w):
+    """A 4^3-element sub-box of the workload mesh that contains the source."""
+    pk = dict(w["problem"])
+    n = pk["n"]
+    x0 = pk.get("x0", (0, 0, 0))
+    x1 = pk.get("x1", (1, 1, 1))
+    h = [(x1[d] - x0[d]) / n[d] for d in range(3)]
+    sub = [min(4, n[d]) for d in range(3)]
+    lo, hi = [], []
+    for d in range(3):
+        c = int(round((pk["src_center"][d] - x0[d]) / h[d])) - sub[d] // 2
+        c = max(0, min(n[d] - sub[d], c))
+        lo.append(x0[d] + c * h[d])
+        hi.append(x0[d] + (c + sub[d]) * h[d])
+    ws = pk.get("wavespeed")
+    wsub = None
+    if ws is not None:
+        wsub = []
+        for kz in range(sub[2]):
+            for ky in range(sub[1]):
+                for kx in range(sub[0]):
+                    ix = int(round((lo[0] - x0[0]) / h[0])) + kx
+                    iy = int(round((lo[1] - x0[1]) / h[1])) + ky
+                    iz = int(round((lo[2] - x0[2]) / h[2])) + kz
+                    wsub.append(ws[ix + n[0] * (iy + n[1] * iz)])
+    levels = w["opts"]["n_levels"]
+    return dict(n=tuple(sub), p=pk["p"], omega=pk["omega"], x0=tuple(lo), x1=tuple(hi), wavespeed=wsub,
+                src_center=pk["src_center"], src_width=pk["src_width"]), dict(w["opts"], n_levels=min(levels, 3))
+
+
+def oracle_sample_run(args):
+    """Runs in a fresh single-threaded process: oracle setup (untimed), PCG (timed)."""
+    import numpy as np  # noqa: F401
+    from oracle.assembly import build_fine
+    from oracle.hierarchy import build_hierarchy
+    from oracle.problem import GaussianSource
+    from oracle.solver import mg_pcg
+    w = workload(args.config, "fp64")
+    pk, ok = oracle_sample_problem(w)
+    t0 = time.perf_counter()
+    fs = build_fine(pk["n"], pk["p"], pk["omega"], wavespeed=pk["wavespeed"],
+                    load=GaussianSource(pk["src_center"], pk["src_width"]), x0=pk["x0"], x1=pk["x1"])
+    A, b = fs.assemble()
+    levels = build_hierarchy(fs.mesh, fs.Kc, fs.dofs, ok["n_levels"], ok["p_min"])
+    t_setup = time.perf_counter() - t0
+    res = []
+    for _ in range(args.oracle_steps):
+        t1 = time.perf_counter()
+        x, it, hist = mg_pcg(levels, A, b, tol=ok["tol"])
+        res.append((time.perf_counter() - t1, it))
+    n = A.shape[0]
+    tot_t = sum(r[0] for r in res)
+    tot_di = sum(n * r[1] for r in res)
+    print(json.dumps(dict(value=tot_di / tot_t, n_dof=n, iters=res[-1][1], pcg_s=[r[0] for r in res],
+                          setup_s=t_setup, sample="%dx%dx%d-element sub-box [%s]-[%s] of the %s mesh (same h, p=%d, "
+                          "omega, source), %d levels, PCG phase only" % (
+                              pk["n"][0], pk["n"][1], pk["n"][2], ",".join("%.4g" % v for v in pk["x0"]),
+                              ",".join("%.4g" % v for v in pk["x1"]), "x".join(map(str, w["problem"]["n"])),
+                              pk["p"], ok["n_levels"]))))
+
+
+def oracle_subprocess(args, steps=1, timeout=600):
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
+               CUDA_VISIBLE_DEVICES="")
+    cmd = [sys.executable, os.path.abspath(__file__), "--oracle-sample", "--config", str(args.config),
+           "--oracle-steps", str(steps)]
+    r = subprocess.run(cmd, capture_output=True, text=True, env=env, timeout=timeout)
+    if r.returncode != 0:
+        raise RuntimeError("oracle sample failed: " + r.stderr[-2000:])
+    return json.loads(r.stdout.strip().splitlines()[-1])
+
+
+# ------------------------------------------------------------------ clocks
+class Clocks:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device):
+        self.device = device
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.p = None
+
+    def start(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.device), "--query-gpu=" + self.Q,
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return None
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.p.kill()
+        self.f.flush()
+        self.f.seek(0)
+        rows = [l.strip().split(", ") for l in self.f.read().splitlines() if l.strip()]
+        os.unlink(self.f.name)
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            if len(r) < 9:
+                continue
+            try:
+                sm.append(float(r[1]))
+                mx = float(r[2])
+            except ValueError:
+                continue
+            for k, nm in enumerate(names):
+                if r[5 + k].strip().lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ gb300
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return d.get("hbm_gbs", 6800.0), "measured"
+    except OSError:
+        return 6800.0, "fallback"
+
+
+def traffic_for(kernel):
+    """Per-launch DRAM bytes from the committed ncu summary, if the kernel source is unchanged."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(p) as f:
+            d = json.load(f)
+    except OSError:
+        return None
+    src = os.path.join(ROOT, "paper_2304_01728_gb300", "csrc", "solve.cu")
+    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    e = d.get(kernel)
+    if not e or e.get("solve_cu_sha") != sha:
+        return None
+    return e.get("traffic_bytes_per_launch")
+
+
+def run_gb300(args, rank, world, local_rank):
+    import numpy as np
+    import torch
+    from paper_2304_01728_gb300 import build as B
+    B.build()
+    from paper_2304_01728_gb300 import dpgmg as D
+
+    torch.cuda.set_device(local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    w = workload(args.config, args.precision)
+    stream = torch.cuda.Stream()
+    h = D.dpgmg_create(local_rank, 0, ctypes.c_void_p(stream.cuda_stream))
+    pb, keep = D.make_problem(**w["problem"])
+    op = D.make_opts(**w["opts"])
+    n_dof, n_field, dev_bytes = D.dpgmg_query_sizes(pb, op)
+    trace = torch.empty(2 * n_dof, dtype=torch.float64, device="cuda")
+    fields = torch.empty(2 * n_field, dtype=torch.float64, device="cuda")
+
+    def step(prof=D.PROF_OFF):
+        s = D.dpgmg_setup(h, pb, op)
+        try:
+            if prof:
+                D.dpgmg_profile(h, s, prof)
+            code, st = D.dpgmg_solve(h, s, trace.data_ptr(), fields.data_ptr(), out_is_device=True)
+            if code != D.DPGMG_OK:
+                raise RuntimeError("solve status %s" % D.strerror(code))
+            pr = D.dpgmg_profile_read(h, s) if prof else None
+            return st, pr
+        finally:
+            D.dpgmg_release(h, s)
+
+    for _ in range(args.warmup):
+        step()
+    clocks = Clocks(local_rank)
+    clocks.start()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    l0 = D.dpgmg_launch_count()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    stats, prof_ms, prof_n, prof_b = [], 0.0, 0, 0
+    for _ in range(args.steps):
+        st, pr = step(D.PROF_SMOOTH_FINE)
+        stats.append((st.iters, st.t_pcg_ms, st.t_setup_ms, st.true_relres, st.relres, st.bytes_per_iter))
+        prof_ms += pr[0]
+        prof_n += pr[1]
+        prof_b = pr[2]
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    launches = D.dpgmg_launch_count() - l0
+    clk = clocks.stop()
+    total_ms = e0.elapsed_time(e1)
+    dof_iters = float(sum(n_dof * s[0] for s in stats))
+    pcg_ms = float(sum(s[1] for s in stats))
+    if dist:
+        t = torch.tensor([dof_iters, pcg_ms, total_ms], dtype=torch.float64, device="cuda")
+        tmax = t.clone()
+        dist.all_reduce(t, op=dist.ReduceOp.SUM)
+        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
+        dof_iters, pcg_ms, total_ms = float(t[0]), float(tmax[1]), float(tmax[2])
+    value = dof_iters / (pcg_ms / 1e3)
+
+    # ---- end to end through the public API with host buffers
+    e2e = None
+    nelem = int(np.prod(w["problem"]["n"]))
+    steps_e2e = 0 if args.no_e2e else args.steps
+    c_host = np.ascontiguousarray(w["problem"].get("wavespeed") or np.ones(nelem), dtype=np.float64)
+    c_pin = torch.from_numpy(c_host).pin_memory()
+    pk2 = dict(w["problem"], wavespeed=None)
+    pb2, keep2 = D.make_problem(**pk2)
+    pb2.wavespeed = ctypes.cast(ctypes.c_void_p(c_pin.data_ptr()), ctypes.POINTER(ctypes.c_double))
+    tr_h = torch.empty(2 * n_dof, dtype=torch.float64).pin_memory()
+    fl_h = torch.empty(2 * n_field, dtype=torch.float64).pin_memory()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    e2e_di = 0.0
+    for _ in range(steps_e2e):
+        s = D.dpgmg_setup(h, pb2, op)
+        code, st = D.dpgmg_solve(h, s, tr_h.data_ptr(), fl_h.data_ptr(), out_is_device=False)
+        D.dpgmg_release(h, s)
+        e2e_di += n_dof * st.iters
+    torch.cuda.synchronize()
+    t_e2e = time.perf_counter() - t0
+    if steps_e2e:
+        e2e = {"value": e2e_di / t_e2e, "unit": UNIT, "h2d_bytes_per_step": int(c_host.nbytes),
+               "d2h_bytes_per_step": int(16 * (n_dof + n_field)), "ms_per_step": 1e3 * t_e2e / steps_e2e}
+
+    # ---- FP64 V-cycle path on the same workload (one step, reported beside)
+    fp64 = None
+    if args.precision == "mixed" and not args.no_fp64_compare:
+        op64 = D.make_opts(**dict(w["opts"], precision="fp64"))
+        s = D.dpgmg_setup(h, pb, op64)
+        code, st = D.dpgmg_solve(h, s, trace.data_ptr(), fields.data_ptr(), out_is_device=True)
+        D.dpgmg_release(h, s)
+        fp64 = {"value": n_dof * st.iters / (st.t_pcg_ms / 1e3), "iters": st.iters, "pcg_ms": st.t_pcg_ms,
+                "setup_ms": st.t_setup_ms, "true_relres": st.true_relres}
+    D.dpgmg_destroy(h)
+
+    if rank != 0:
+        return None
+    peak, peak_kind = peaks()
+    per_launch_ms = prof_ms / max(prof_n, 1)
+    achieved = prof_b / (per_launch_ms / 1e3) / 1e9
+    it_last = stats[-1]
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "c64 V-cycle / c128 CG" if args.precision == "mixed" else "c128",
+        "data": "synthetic (seeded Gaussian source; no dataset)",
+        "config": {"workload": w["name"], "n": list(w["problem"]["n"]), "p": w["problem"]["p"],
+                   "omega": w["problem"]["omega"], "levels": w["opts"]["n_levels"], "precision": args.precision,
+                   "n_dof": n_dof, "parallelism": "replicas" if world > 1 else "single GPU",
+                   "l2": "operators (GBs) exceed L2; no flush needed"},
+        "iters": it_last[0], "pcg_ms": pcg_ms / args.steps, "setup_ms": sum(s[2] for s in stats) / args.steps,
+        "true_relres": it_last[3], "relres": it_last[4], "bytes_per_iter": it_last[5],
+        "pcg_GBps": it_last[5] * it_last[0] / (stats[-1][1] / 1e3) / 1e9,
+        "gpu_launches": int(launches),
+        "roofline": {"kernel": "k_patch_apply (finest smoother)", "bound": "hbm", "achieved": achieved,
+                     "peak": peak, "unit": "GB/s", "frac": achieved / peak, "peak_source": peak_kind,
+                     "bytes_per_launch": prof_b, "launches": prof_n, "avg_launch_ms": per_launch_ms,
+                     "traffic": traffic_for("k_patch_apply")},
+        "clocks": clk, "e2e": e2e, "fp64_path": fp64,
+    }
+    return out
+
+
+# ------------------------------------------------------------------ main
+def main():
+    args = parse()
+    if args.oracle_sample:
+        oracle_sample_run(args)
+        return
+    rank = int(os.environ.get("RANK", 0))
+    world = int(os.environ.get("WORLD_SIZE", 1))
+    local_rank = int(os.environ.get("LOCAL_RANK", 0))
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        # the reference arm is the FP64 oracle (no reference implementation exists)
+        t0 = time.perf_counter()
+        r = oracle_subprocess(args, steps=args.warmup + args.steps, timeout=1800)
+        pcg = r["pcg_s"][args.warmup:]
+        value = r["n_dof"] * r["iters"] * len(pcg) / sum(pcg)
+        print(json.dumps({
+            "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(pcg) / len(pcg),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c128",
+            "data": "synthetic", "config": {"workload": workload(args.config, args.precision)["name"]},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": r["sample"]},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "wall_s": time.perf_counter() - t0}))
+        return
+    out = run_gb300(args, rank, world, local_rank)
+    if out is None:
+        return
+    if not args.no_cpu_baseline and world == 1 or (not args.no_cpu_baseline and rank == 0):
+        try:
+            r = oracle_subprocess(args, steps=1)
+            out["cpu_baseline"] = {"value": r["value"], "unit": UNIT, "cores": 1, "kind": "oracle",
+                                   "sample": r["sample"], "n_dof": r["n_dof"], "iters": r["iters"]}
+        except Exception as e:  # reported, never silently replaced
+            out["cpu_baseline"] = {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                   "sample": "failed: %s" % str(e)[:200]}
+    print(json.dumps(out))
+
+
+if __name__ == "__main__":
+    main()

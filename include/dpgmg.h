@@ -205,6 +205,26 @@ int dpgmg_rhs(dpgmg_handle h, dpgmg_system sys, double* b_out);
 int dpgmg_apply(dpgmg_handle h, dpgmg_system sys, int op, int level,
                 const double* x, double* y);
 
+/* ---- measurement hooks --------------------------------------------------- */
+
+/* Number of CUDA kernels this library has launched in this process (all
+ * handles), for counting the launches inside a timed region. */
+long long dpgmg_launch_count(void);
+
+#define DPGMG_PROF_OFF         0
+#define DPGMG_PROF_SMOOTH_FINE 1  /* patch products of the finest smoother */
+#define DPGMG_PROF_SPMV_FINE   2  /* residual SpMVs of the finest V-cycle level */
+#define DPGMG_PROF_SPMV_CG     3  /* the FP64 CG operator application */
+
+/* Bracket every launch of one kernel with CUDA events on the launching
+ * stream during subsequent dpgmg_solve calls (which = DPGMG_PROF_*; OFF
+ * clears).  dpgmg_profile_read() synchronises, returns the summed device
+ * time, the launch count and the algorithmic bytes per launch (stored
+ * matrix entries read once), and resets the accumulators. */
+int dpgmg_profile(dpgmg_handle h, dpgmg_system sys, int which);
+int dpgmg_profile_read(dpgmg_handle h, dpgmg_system sys, double* total_ms, long long* launches,
+                       long long* bytes_per_launch);
+
 #ifdef __cplusplus
 }
 #endif

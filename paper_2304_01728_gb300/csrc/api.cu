@@ -4,6 +4,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <atomic>
 #include <mutex>
 #include <new>
 
@@ -21,6 +22,9 @@ namespace dpgmg {
 
 static thread_local std::string g_last;
 void set_last_error(const std::string& m) { g_last = m; }
+
+static std::atomic<long long> g_launches{0};
+void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
 void* Alloc::get(size_t bytes) {
   bytes = (bytes + 255) & ~(size_t)255;
@@ -285,6 +289,7 @@ int dpgmg_setup(dpgmg_handle h, const dpgmg_problem* pb, const dpgmg_opts* op, d
     return DPGMG_OK;
   } catch (const Err& e) {
     cudaDeviceSynchronize();
+    profile_clear(S);
     free_workspace(S);
     delete sys;
     return fail(e);
@@ -334,8 +339,32 @@ void dpgmg_release(dpgmg_handle h, dpgmg_system sys) {
     cudaStreamSynchronize(h->h.stream);
     h->h.used -= std::min(h->h.used, sys->s.mem.used);
   }
+  profile_clear(sys->s);
   free_workspace(sys->s);
   delete sys;
+}
+
+long long dpgmg_launch_count(void) { return g_launches.load(); }
+
+int dpgmg_profile(dpgmg_handle h, dpgmg_system sys, int which) {
+  if (!h || !sys || which < DPGMG_PROF_OFF || which > DPGMG_PROF_SPMV_CG) return DPGMG_ERR_ARG;
+  std::lock_guard<std::mutex> lk(h->mu);
+  sys->s.prof_which = which;
+  profile_clear(sys->s);
+  return DPGMG_OK;
+}
+
+int dpgmg_profile_read(dpgmg_handle h, dpgmg_system sys, double* total_ms, long long* launches,
+                       long long* bytes_per_launch) {
+  if (!h || !sys) return DPGMG_ERR_ARG;
+  std::lock_guard<std::mutex> lk(h->mu);
+  try {
+    DPG_CUDA(cudaSetDevice(h->h.device));
+    profile_read(sys->s, total_ms, launches, bytes_per_launch);
+    return DPGMG_OK;
+  } catch (const Err& e) {
+    return fail(e);
+  }
 }
 
 int dpgmg_level_info(dpgmg_handle h, dpgmg_system sys, int level, dpgmg_level_desc* out) {

@@ -23,7 +23,12 @@ void set_last_error(const std::string& m);
     if (e_ != cudaSuccess)                                                             \
       throw ::dpgmg::Err{DPGMG_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)}; \
   } while (0)
-#define DPG_CHECK_LAUNCH() DPG_CUDA(cudaGetLastError())
+void count_launch();
+#define DPG_CHECK_LAUNCH()            \
+  do {                                \
+    ::dpgmg::count_launch();          \
+    DPG_CUDA(cudaGetLastError());     \
+  } while (0)
 
 // Device allocation tracked against the handle's budget.
 struct Alloc {
@@ -112,6 +117,9 @@ struct SystemImpl {
   double t_setup_ms = 0.0;
   int64_t bytes_per_iter = 0;
   void* ws = nullptr;            // solver workspace
+  int prof_which = 0;            // DPGMG_PROF_* being bracketed with events
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> prof_events;
+  int64_t prof_bytes = 0;
   int coarse_blocks = 0;
 };
 
@@ -140,6 +148,8 @@ void ensure_workspace(SystemImpl& S, cudaStream_t st);
 void free_workspace(SystemImpl& S);
 void spmv64(const ECSRDev& A, const double2* x, double2* y, cudaStream_t st);
 void estimate_theta(SystemImpl& S, int level, cudaStream_t st);
+void profile_read(SystemImpl& S, double* ms, long long* launches, long long* bytes);
+void profile_clear(SystemImpl& S);
 void smooth_apply64(const Level& L, const double2* r, double2* y, double theta, double2* scratch,
                     cudaStream_t st);
 

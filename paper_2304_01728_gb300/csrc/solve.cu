@@ -35,6 +35,44 @@ template <> struct Prec<float2> {
   static const float2* Cf(const Level& l) { return l.C32; }
 };
 
+// ------------------------------------------------------------ profiling
+// Events bracketing one chosen kernel (DPGMG_PROF_*) on the launching stream.
+static int prof_begin(SystemImpl* S, cudaStream_t st) {
+  if (!S) return -1;
+  cudaEvent_t a, b;
+  DPG_CUDA(cudaEventCreate(&a));
+  DPG_CUDA(cudaEventCreate(&b));
+  DPG_CUDA(cudaEventRecord(a, st));
+  S->prof_events.emplace_back(a, b);
+  return (int)S->prof_events.size() - 1;
+}
+static void prof_end(SystemImpl* S, int idx, cudaStream_t st) {
+  if (!S || idx < 0) return;
+  DPG_CUDA(cudaEventRecord(S->prof_events[idx].second, st));
+}
+
+void profile_clear(SystemImpl& S) {
+  for (auto& e : S.prof_events) {
+    cudaEventDestroy(e.first);
+    cudaEventDestroy(e.second);
+  }
+  S.prof_events.clear();
+}
+
+void profile_read(SystemImpl& S, double* ms, long long* launches, long long* bytes) {
+  double tot = 0.0;
+  for (auto& e : S.prof_events) {
+    DPG_CUDA(cudaEventSynchronize(e.second));
+    float t = 0.f;
+    DPG_CUDA(cudaEventElapsedTime(&t, e.first, e.second));
+    tot += t;
+  }
+  if (ms) *ms = tot;
+  if (launches) *launches = (long long)S.prof_events.size();
+  if (bytes) *bytes = S.prof_bytes;
+  profile_clear(S);
+}
+
 template <class C> __device__ __forceinline__ C warp_sum(C v) {
   for (int o = 16; o > 0; o >>= 1) {
     v.x += __shfl_xor_sync(0xffffffffu, v.x, o);
@@ -70,11 +108,14 @@ __global__ void __launch_bounds__(256) k_spmv(const int32_t* __restrict__ row_en
 }
 
 template <class C>
-static void spmv(const ECSRDev& A, const C* vals, const C* x, const C* b, C* y, int mode, cudaStream_t st) {
+static void spmv(const ECSRDev& A, const C* vals, const C* x, const C* b, C* y, int mode, cudaStream_t st,
+                 SystemImpl* prof = nullptr) {
   int64_t blocks = std::min<int64_t>((A.nrows + 7) / 8, 152 * 16);
+  int pe = prof_begin(prof, st);
   k_spmv<C><<<(unsigned)blocks, 256, 0, st>>>(A.row_ent, A.ent_start, A.col_ptr, A.col_idx, A.val_ptr, vals, x, b, y,
                                                A.nrows, mode);
   DPG_CHECK_LAUNCH();
+  prof_end(prof, pe, st);
 }
 
 void spmv64(const ECSRDev& A, const double2* x, double2* y, cudaStream_t st) {
@@ -118,11 +159,14 @@ __global__ void k_slot_sum(const int64_t* __restrict__ sptr, const int32_t* __re
 }
 
 template <class C>
-static void smooth(const Level& L, const C* r, C* y, double theta, int accumulate, C* pbuf, cudaStream_t st) {
+static void smooth(const Level& L, const C* r, C* y, double theta, int accumulate, C* pbuf, cudaStream_t st,
+                   SystemImpl* prof = nullptr) {
   const PatchDev& P = L.P;
   size_t sm = (size_t)P.max_n * sizeof(C) + 16;
+  int pe = prof_begin(prof, st);
   k_patch_apply<C><<<(unsigned)P.np, 256, sm, st>>>(P.ptr, P.dofs, P.val_ptr, Prec<C>::inv(P), r, pbuf);
   DPG_CHECK_LAUNCH();
+  prof_end(prof, pe, st);
   int64_t n = L.mesh.ndof;
   k_slot_sum<C><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(P.slot_ptr, P.slots, pbuf, y, n, theta, accumulate);
   DPG_CHECK_LAUNCH();
@@ -618,6 +662,9 @@ static void vcycle(SystemImpl& S, WS& W, int l, const C* r, C* x, cudaStream_t s
   const Level& Cl = S.levels[l - 1];
   const C* Avals = Prec<C>::A(F.A);
   const C* rs = r;
+  const bool fine = l == (int)S.levels.size() - 1;
+  SystemImpl* psm = (fine && S.prof_which == DPGMG_PROF_SMOOTH_FINE) ? &S : nullptr;
+  SystemImpl* psp = (fine && S.prof_which == DPGMG_PROF_SPMV_FINE) ? &S : nullptr;
   if (F.kind == 2) {
     condense<C>(F, r, V[l].rs, V[l].cbuf, st);
     rs = V[l].rs;
@@ -625,10 +672,10 @@ static void vcycle(SystemImpl& S, WS& W, int l, const C* r, C* x, cudaStream_t s
   // pre-smoothing from x = 0
   for (int k = 0; k < S.op.nu_pre; ++k) {
     if (k == 0) {
-      smooth<C>(F, rs, x, F.theta, 0, V[l].pbuf, st);
+      smooth<C>(F, rs, x, F.theta, 0, V[l].pbuf, st, psm);
     } else {
-      spmv<C>(F.A, Avals, x, rs, V[l].t, 1, st);
-      smooth<C>(F, V[l].t, x, F.theta, 1, V[l].pbuf, st);
+      spmv<C>(F.A, Avals, x, rs, V[l].t, 1, st, psp);
+      smooth<C>(F, V[l].t, x, F.theta, 1, V[l].pbuf, st, psm);
     }
   }
   if (S.op.nu_pre == 0) {
@@ -636,13 +683,13 @@ static void vcycle(SystemImpl& S, WS& W, int l, const C* r, C* x, cudaStream_t s
     DPG_CHECK_LAUNCH();
   }
   // coarse-grid correction
-  spmv<C>(F.A, Avals, x, rs, V[l].t, 1, st);
+  spmv<C>(F.A, Avals, x, rs, V[l].t, 1, st, psp);
   restrict_vec<C>(F, Cl, V[l].t, V[l - 1].r, st);
   vcycle<C>(S, W, l - 1, V[l - 1].r, V[l - 1].x, st);
   prolong_add<C>(F, Cl, V[l - 1].x, x, st);
   for (int k = 0; k < S.op.nu_post; ++k) {
-    spmv<C>(F.A, Avals, x, rs, V[l].t, 1, st);
-    smooth<C>(F, V[l].t, x, F.theta, 1, V[l].pbuf, st);
+    spmv<C>(F.A, Avals, x, rs, V[l].t, 1, st, psp);
+    smooth<C>(F, V[l].t, x, F.theta, 1, V[l].pbuf, st, psm);
   }
   if (F.kind == 2) backsub<C>(F, r, x, st);
 }
@@ -704,6 +751,13 @@ int pcg_solve(SystemImpl& S, cudaStream_t st, double2* xout, dpgmg_stats* stats)
   ensure_workspace(S, st);
   WS& W = *reinterpret_cast<WS*>(S.ws);
   const ECSRDev& A = cg_operator(S, W, st);
+  {
+    const Level& Ff = S.levels.back();
+    const int64_t esz = S.op.precision == DPGMG_PREC_MIXED ? 8 : 16;
+    if (S.prof_which == DPGMG_PROF_SMOOTH_FINE) S.prof_bytes = Ff.P.nvals * esz;
+    else if (S.prof_which == DPGMG_PROF_SPMV_FINE) S.prof_bytes = Ff.A.nnz * esz;
+    else if (S.prof_which == DPGMG_PROF_SPMV_CG) S.prof_bytes = A.nnz * 16;
+  }
   const int64_t n = S.levels.back().mesh.ndof;
   cudaEvent_t e0, e1;
   DPG_CUDA(cudaEventCreate(&e0));
@@ -723,8 +777,9 @@ int pcg_solve(SystemImpl& S, cudaStream_t st, double2* xout, dpgmg_stats* stats)
     precondition(S, W, W.r, W.z, st);
     dot(W, W.z, W.r, n, 3, st);   // rho = z^H r
     DPG_CUDA(cudaMemcpyAsync(W.p, W.z, (size_t)n * sizeof(double2), cudaMemcpyDeviceToDevice, st));
+    SystemImpl* pcg_prof = S.prof_which == DPGMG_PROF_SPMV_CG ? &S : nullptr;
     while (it < S.op.max_iter) {
-      spmv<double2>(A, A.v64, W.p, nullptr, W.q, 0, st);
+      spmv<double2>(A, A.v64, W.p, nullptr, W.q, 0, st, pcg_prof);
       dot(W, W.p, W.q, n, 0, st);   // pq = p^H q, alpha = rho / pq
       k_cg_update<<<RED_BLOCKS, 256, 0, st>>>(W.x, W.r, W.p, W.q, W.sc, n, W.part);
       DPG_CHECK_LAUNCH();

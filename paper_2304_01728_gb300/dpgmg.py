@@ -61,7 +61,9 @@ class dpgmg_level_desc(ctypes.Structure):
 _lib = None
 EXPORTS = ["dpgmg_create", "dpgmg_destroy", "dpgmg_query_sizes", "dpgmg_default_opts", "dpgmg_setup",
            "dpgmg_solve", "dpgmg_release", "dpgmg_strerror", "dpgmg_last_error", "dpgmg_level_info",
-           "dpgmg_element_matrix", "dpgmg_rhs", "dpgmg_apply"]
+           "dpgmg_element_matrix", "dpgmg_rhs", "dpgmg_apply", "dpgmg_launch_count", "dpgmg_profile",
+           "dpgmg_profile_read"]
+PROF_OFF, PROF_SMOOTH_FINE, PROF_SPMV_FINE, PROF_SPMV_CG = 0, 1, 2, 3
 
 
 def lib():
@@ -93,8 +95,12 @@ def lib():
     L.dpgmg_element_matrix.argtypes = [vp, vp, i, ll, dptr, dptr]
     L.dpgmg_rhs.argtypes = [vp, vp, dptr]
     L.dpgmg_apply.argtypes = [vp, vp, i, i, dptr, dptr]
+    L.dpgmg_launch_count.argtypes = []
+    L.dpgmg_launch_count.restype = ll
+    L.dpgmg_profile.argtypes = [vp, vp, i]
+    L.dpgmg_profile_read.argtypes = [vp, vp, ctypes.POINTER(d), ctypes.POINTER(ll), ctypes.POINTER(ll)]
     for f in ["dpgmg_create", "dpgmg_query_sizes", "dpgmg_setup", "dpgmg_solve", "dpgmg_level_info",
-              "dpgmg_element_matrix", "dpgmg_rhs", "dpgmg_apply"]:
+              "dpgmg_element_matrix", "dpgmg_rhs", "dpgmg_apply", "dpgmg_profile", "dpgmg_profile_read"]:
         getattr(L, f).restype = i
     _lib = L
     return L
@@ -212,6 +218,21 @@ def dpgmg_apply(h, s, op, level, x, nout):
     y = np.zeros(nout, dtype=np.complex128)
     _check(lib().dpgmg_apply(h, s, int(op), int(level), _dptr(x), _dptr(y)), "dpgmg_apply")
     return y
+
+
+def dpgmg_launch_count():
+    return int(lib().dpgmg_launch_count())
+
+
+def dpgmg_profile(h, s, which):
+    _check(lib().dpgmg_profile(h, s, int(which)), "dpgmg_profile")
+
+
+def dpgmg_profile_read(h, s):
+    """(summed device ms, launches, algorithmic bytes per launch) since the last read."""
+    ms, n, b = ctypes.c_double(), ctypes.c_longlong(), ctypes.c_longlong()
+    _check(lib().dpgmg_profile_read(h, s, ctypes.byref(ms), ctypes.byref(n), ctypes.byref(b)), "dpgmg_profile_read")
+    return ms.value, n.value, b.value
 
 
 def strerror(code):
