@@ -36,14 +36,27 @@ void* Alloc::get(size_t bytes) {
     throw Err{DPGMG_ERR_NOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(e)};
   }
   ptrs.push_back(p);
+  sizes.push_back(bytes);
   used += bytes;
   peak = std::max(peak, used);
   return p;
 }
 
+void Alloc::release(void* p) {
+  for (size_t i = 0; i < ptrs.size(); ++i)
+    if (ptrs[i] == p) {
+      cudaFree(p);
+      used -= sizes[i];
+      ptrs.erase(ptrs.begin() + i);
+      sizes.erase(sizes.begin() + i);
+      return;
+    }
+}
+
 void Alloc::free_all() {
   for (void* p : ptrs) cudaFree(p);
   ptrs.clear();
+  sizes.clear();
   used = 0;
 }
 
@@ -113,7 +126,7 @@ static size_t estimate_bytes(const dpgmg_problem* pb, const dpgmg_opts* op) {
       bytes += nv * np_int * np_int * 1.25 * esz + std::min<double>(2e9, nv * np_int * np_int * 16.0);
     } else {
       double N0 = (double)m.ndof;
-      if (op->coarsest == DPGMG_COARSEST_CHOLESKY || specs.size() == 1) bytes += N0 * N0 * esz;
+      if (op->coarsest == DPGMG_COARSEST_CHOLESKY || specs.size() == 1) bytes += N0 * N0 * (16.0 + 2 * esz);
     }
   }
   return (size_t)(bytes * 1.1) + ((size_t)64 << 20);
@@ -137,7 +150,7 @@ static void fill_bytes_per_iter(SystemImpl& S) {
     if (L.kind == 2) b += (double)L.nK * (2.0 * L.nI * L.nS + L.nI * L.nI) * esz; // condense + backsub
   }
   const Level& C0 = S.levels[0];
-  if (C0.C64) b += (double)C0.N0 * C0.N0 * esz;                                  // two triangular solves
+  if (C0.has_coarse) b += (double)C0.N0 * (C0.N0 + 1) * esz;                     // L^-1 and L^-H (packed)
   S.bytes_per_iter = (int64_t)b;
 }
 
@@ -434,7 +447,7 @@ int dpgmg_apply(dpgmg_handle h, dpgmg_system sys, int op, int level, const doubl
   if ((op == DPGMG_OP_A || op == DPGMG_OP_SMOOTH || op == DPGMG_OP_RESTRICT || op == DPGMG_OP_PROLONG) && level == 0)
     return DPGMG_ERR_ARG;
   if (op == DPGMG_OP_CONDENSE && L.kind != 2) return DPGMG_ERR_ARG;
-  if (op == DPGMG_OP_COARSE && (level != 0 || !L.C64)) return DPGMG_ERR_ARG;
+  if (op == DPGMG_OP_COARSE && (level != 0 || !L.has_coarse)) return DPGMG_ERR_ARG;
   if (op == DPGMG_OP_AFULL && level != nl - 1) return DPGMG_ERR_ARG;
   try {
     DPG_CUDA(cudaSetDevice(h->h.device));

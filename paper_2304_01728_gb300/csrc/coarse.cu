@@ -1,0 +1,366 @@
+// Coarsest level of the V-cycle: direct solve with the dense operator A_0
+// (the paper solves its initial mesh directly, Sec. 4 list).
+//
+// Setup (in the V-cycle precision: complex128 on the FP64 path, complex64 on
+// the mixed path):
+//   A_0 = sum of the level-0 element matrices      (dense, N0 x N0)
+//   A_0 = L L^H                                    (blocked right-looking Cholesky)
+//   X   = L^-1                                     (blocked forward substitution, B = I)
+// X is stored packed twice: its lower triangle by rows and its conjugate
+// transpose (upper triangle of L^-H) by rows, so each V-cycle application
+//   e = L^-H (L^-1 r)
+// is two dense triangular matrix-vector products with no sequential
+// dependency between rows (one warp per row, coalesced row reads).
+#include <algorithm>
+#include <cmath>
+
+#include "common.cuh"
+#include "internal.h"
+
+namespace dpgmg {
+
+constexpr int CNB = 64;   // block width of the dense kernels
+
+template <class C> __device__ __forceinline__ C warp_sum_c(C v) {
+  for (int o = 16; o > 0; o >>= 1) {
+    v.x += __shfl_xor_sync(0xffffffffu, v.x, o);
+    v.y += __shfl_xor_sync(0xffffffffu, v.y, o);
+  }
+  return v;
+}
+
+__global__ void k_dense_scatter(double2* A, int64_t N, const double2* E, const int64_t* dofs, int nloc) {
+  const int64_t e = blockIdx.x;
+  for (int q = threadIdx.x; q < nloc * nloc; q += blockDim.x) {
+    int i = q / nloc, j = q % nloc;
+    int64_t gi = dofs[e * nloc + i], gj = dofs[e * nloc + j];
+    if (gi < 0 || gj < 0) continue;
+    double2 v = E[e * (size_t)nloc * nloc + q];
+    atomicAdd(&A[gi * N + gj].x, v.x);
+    atomicAdd(&A[gi * N + gj].y, v.y);
+  }
+}
+
+__global__ void k_narrow_mat(const double2* a, float2* b, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    b[i] = make_float2((float)a[i].x, (float)a[i].y);
+}
+
+// ---------------------------------------------------------------- Cholesky
+template <class C>
+__global__ void __launch_bounds__(CTA_THREADS) k_dense_diag(C* A, int64_t N, int k0, int* info) {
+  extern __shared__ unsigned char shraw[];
+  int kb = (int)(N - k0 < CNB ? N - k0 : CNB);
+  int inf = cta_potrf<C>(A + (size_t)k0 * N + k0, kb, (int)N, reinterpret_cast<C*>(shraw));
+  if (threadIdx.x == 0 && inf) atomicOr(info, 16);
+}
+
+// rows i >= k0 + kb: A[i, k0:k0+kb] <- A[i, k0:k0+kb] L_kk^-H ; one thread per row
+template <class C>
+__global__ void k_dense_panel(C* A, int64_t N, int k0) {
+  extern __shared__ unsigned char shraw[];
+  C* D = reinterpret_cast<C*>(shraw);
+  using O = Ops<C>;
+  using R = typename O::R;
+  const int kb = (int)(N - k0 < CNB ? N - k0 : CNB);
+  for (int q = threadIdx.x; q < kb * kb; q += blockDim.x) D[q] = A[(size_t)(k0 + q / kb) * N + k0 + q % kb];
+  __syncthreads();
+  int64_t i = (int64_t)k0 + kb + blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  C* row = A + i * N + k0;
+  C x[CNB];
+  for (int j = 0; j < kb; ++j) {
+    C v = row[j];
+    for (int t = 0; t < j; ++t) v = O::fnmac(x[t], D[j * kb + t], v);
+    x[j] = O::scale(v, R(1) / O::re(D[j * kb + j]));
+  }
+  for (int j = 0; j < kb; ++j) row[j] = x[j];
+}
+
+// trailing update of one lower 64x64 tile pair: A[i][j] -= sum_t L[i][t] conj(L[j][t])
+template <class C>
+__global__ void __launch_bounds__(CTA_THREADS) k_dense_herk(C* A, int64_t N, int k0) {
+  __shared__ C Pi[CNB][17];
+  __shared__ C Pj[CNB][17];
+  using O = Ops<C>;
+  const int kb = (int)(N - k0 < CNB ? N - k0 : CNB);
+  const int64_t k1 = k0 + kb;
+  int64_t t = blockIdx.x;
+  int64_t bi = (int64_t)((sqrt(8.0 * (double)t + 1.0) - 1.0) / 2.0);
+  while ((bi + 1) * (bi + 2) / 2 <= t) ++bi;
+  while (bi * (bi + 1) / 2 > t) --bi;
+  const int64_t bj = t - bi * (bi + 1) / 2;
+  const int64_t i0 = k1 + bi * CNB, j0 = k1 + bj * CNB;
+  const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+  C acc[4][4];
+  for (int a = 0; a < 4; ++a)
+    for (int b = 0; b < 4; ++b) acc[a][b] = O::zero();
+  for (int t0 = 0; t0 < kb; t0 += 16) {
+    for (int q = threadIdx.x; q < CNB * 16; q += blockDim.x) {
+      int r = q / 16, c = q % 16;
+      int64_t ii = i0 + r, jj = j0 + r;
+      Pi[r][c] = (ii < N && t0 + c < kb) ? A[ii * N + k0 + t0 + c] : O::zero();
+      Pj[r][c] = (jj < N && t0 + c < kb) ? A[jj * N + k0 + t0 + c] : O::zero();
+    }
+    __syncthreads();
+    for (int c = 0; c < 16; ++c) {
+      C av[4], bv[4];
+      for (int a = 0; a < 4; ++a) av[a] = Pi[ty * 4 + a][c];
+      for (int b = 0; b < 4; ++b) bv[b] = Pj[tx * 4 + b][c];
+      for (int a = 0; a < 4; ++a)
+        for (int b = 0; b < 4; ++b) acc[a][b] = O::fmac(av[a], bv[b], acc[a][b]);
+    }
+    __syncthreads();
+  }
+  for (int a = 0; a < 4; ++a)
+    for (int b = 0; b < 4; ++b) {
+      int64_t i = i0 + ty * 4 + a, j = j0 + tx * 4 + b;
+      if (i < N && j <= i) {
+        C& o = A[i * N + j];
+        o = O::sub(o, acc[a][b]);
+      }
+    }
+}
+
+template <class C>
+static void dense_cholesky(C* A, int64_t N, int* info, cudaStream_t st) {
+  const size_t sm = (size_t)(NB * NB + 2 * TL * NB) * sizeof(C) + 64;
+  const size_t smp = (size_t)CNB * CNB * sizeof(C);
+  DPG_CUDA(cudaFuncSetAttribute(k_dense_diag<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+  DPG_CUDA(cudaFuncSetAttribute(k_dense_panel<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smp));
+  for (int64_t k0 = 0; k0 < N; k0 += CNB) {
+    int kb = (int)std::min<int64_t>(CNB, N - k0);
+    k_dense_diag<C><<<1, CTA_THREADS, sm, st>>>(A, N, (int)k0, info);
+    DPG_CHECK_LAUNCH();
+    int64_t rows = N - k0 - kb;
+    if (rows <= 0) break;
+    k_dense_panel<C><<<(unsigned)((rows + 127) / 128), 128, smp, st>>>(A, N, (int)k0);
+    DPG_CHECK_LAUNCH();
+    int64_t nt = (rows + CNB - 1) / CNB;
+    k_dense_herk<C><<<(unsigned)(nt * (nt + 1) / 2), CTA_THREADS, 0, st>>>(A, N, (int)k0);
+    DPG_CHECK_LAUNCH();
+  }
+}
+
+// ---------------------------------------------------------- L^-1 (blocked)
+// Dinv[kb] = L_kk^-1 for every diagonal block.
+template <class C>
+__global__ void __launch_bounds__(CTA_THREADS) k_diag_inverse(const C* L, int64_t N, C* Dinv) {
+  extern __shared__ unsigned char shraw[];
+  const int kb = blockIdx.x;
+  const int64_t k0 = (int64_t)kb * CNB;
+  const int kw = (int)(N - k0 < CNB ? N - k0 : CNB);
+  C* D = Dinv + (size_t)kb * CNB * CNB;
+  for (int q = threadIdx.x; q < CNB * CNB; q += blockDim.x) {
+    int r = q / CNB, c = q % CNB;
+    D[q] = (r == c && r < kw) ? Ops<C>::from_re(1) : Ops<C>::zero();
+  }
+  __syncthreads();
+  cta_trsm_lower<C, C>(L + (size_t)k0 * N + k0, kw, (int)N, D, kw, CNB, reinterpret_cast<char*>(shraw));
+}
+
+// X[kb rows, tile cols] <- Dinv_kb * X[kb rows, tile cols], one CTA per 64-column tile
+template <class C>
+__global__ void __launch_bounds__(CTA_THREADS) k_trinv_scale(C* X, const C* Dinv, int64_t N, int kb) {
+  extern __shared__ unsigned char shraw[];
+  C* D = reinterpret_cast<C*>(shraw);
+  C* T = D + CNB * CNB;
+  using O = Ops<C>;
+  const int64_t k0 = (int64_t)kb * CNB;
+  const int kw = (int)(N - k0 < CNB ? N - k0 : CNB);
+  const int64_t c0 = (int64_t)blockIdx.x * CNB;
+  const int cw = (int)(N - c0 < CNB ? N - c0 : CNB);
+  const C* Dk = Dinv + (size_t)kb * CNB * CNB;
+  for (int q = threadIdx.x; q < CNB * CNB; q += blockDim.x) {
+    D[q] = Dk[q];
+    int r = q / CNB, c = q % CNB;
+    T[q] = (r < kw && c < cw) ? X[(k0 + r) * N + c0 + c] : O::zero();
+  }
+  __syncthreads();
+  for (int q = threadIdx.x; q < CNB * CNB; q += blockDim.x) {
+    int r = q / CNB, c = q % CNB;
+    if (r >= kw || c >= cw) continue;
+    C acc = O::zero();
+    for (int t = 0; t <= r; ++t) acc = O::fma(D[r * CNB + t], T[t * CNB + c], acc);
+    X[(k0 + r) * N + c0 + c] = acc;
+  }
+}
+
+// X[ib, jb] -= L[ib, kb] X[kb, jb] for ib > kb, jb <= kb (64x64 tiles)
+template <class C>
+__global__ void __launch_bounds__(CTA_THREADS) k_trinv_update(C* X, const C* L, int64_t N, int kb) {
+  __shared__ C La[CNB][17];
+  __shared__ C Xb[16][CNB + 1];
+  using O = Ops<C>;
+  const int64_t k0 = (int64_t)kb * CNB;
+  const int kw = (int)(N - k0 < CNB ? N - k0 : CNB);
+  const int ncol = kb + 1;
+  const int64_t ib = kb + 1 + blockIdx.x / ncol;
+  const int64_t jb = blockIdx.x % ncol;
+  const int64_t i0 = ib * CNB, j0 = jb * CNB;
+  const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+  C acc[4][4];
+  for (int a = 0; a < 4; ++a)
+    for (int b = 0; b < 4; ++b) acc[a][b] = O::zero();
+  for (int t0 = 0; t0 < kw; t0 += 16) {
+    for (int q = threadIdx.x; q < CNB * 16; q += blockDim.x) {
+      int r = q / 16, c = q % 16;
+      La[r][c] = (i0 + r < N && t0 + c < kw) ? L[(i0 + r) * N + k0 + t0 + c] : O::zero();
+      int t = q / CNB, cc = q % CNB;
+      Xb[t][cc] = (t0 + t < kw && j0 + cc < N) ? X[(k0 + t0 + t) * N + j0 + cc] : O::zero();
+    }
+    __syncthreads();
+    for (int c = 0; c < 16; ++c) {
+      C av[4], bv[4];
+      for (int a = 0; a < 4; ++a) av[a] = La[ty * 4 + a][c];
+      for (int b = 0; b < 4; ++b) bv[b] = Xb[c][tx * 4 + b];
+      for (int a = 0; a < 4; ++a)
+        for (int b = 0; b < 4; ++b) acc[a][b] = O::fma(av[a], bv[b], acc[a][b]);
+    }
+    __syncthreads();
+  }
+  for (int a = 0; a < 4; ++a)
+    for (int b = 0; b < 4; ++b) {
+      int64_t i = i0 + ty * 4 + a, j = j0 + tx * 4 + b;
+      if (i < N && j < N) {
+        C& o = X[i * N + j];
+        o = O::sub(o, acc[a][b]);
+      }
+    }
+}
+
+template <class C>
+__global__ void k_identity_lower(C* X, int64_t N) {
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < N * N; q += (int64_t)gridDim.x * blockDim.x)
+    X[q] = (q / N == q % N) ? Ops<C>::from_re(1) : Ops<C>::zero();
+}
+
+// Lp: rows of the lower triangle of X; Up: rows of X^H (upper triangle)
+template <class C>
+__global__ void k_pack(const C* X, int64_t N, C* Lp, C* Up) {
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < N * N; q += (int64_t)gridDim.x * blockDim.x) {
+    int64_t i = q / N, j = q % N;
+    if (j > i) continue;
+    C v = X[q];
+    Lp[i * (i + 1) / 2 + j] = v;
+    // X^H[j][i] = conj(X[i][j]) goes to row j of the upper packing at column i
+    Up[j * N - j * (j - 1) / 2 + (i - j)] = Ops<C>::conj(v);
+  }
+}
+
+template <class C>
+static void coarse_factor(Alloc& A, C* dense, int64_t N, C** Lp, C** Up, int* info, cudaStream_t st) {
+  dense_cholesky<C>(dense, N, info, st);
+  const int nb = (int)((N + CNB - 1) / CNB);
+  C* Dinv = A.arr<C>((size_t)nb * CNB * CNB);
+  const size_t smd = (size_t)(NB * NB + TL * NB) * sizeof(C) + (size_t)NB * TL * sizeof(C) + 64;
+  DPG_CUDA(cudaFuncSetAttribute(k_diag_inverse<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smd));
+  k_diag_inverse<C><<<nb, CTA_THREADS, smd, st>>>(dense, N, Dinv);
+  DPG_CHECK_LAUNCH();
+  C* X = A.arr<C>((size_t)N * N);
+  k_identity_lower<C><<<1216, 256, 0, st>>>(X, N);
+  DPG_CHECK_LAUNCH();
+  const size_t sms = (size_t)2 * CNB * CNB * sizeof(C);
+  DPG_CUDA(cudaFuncSetAttribute(k_trinv_scale<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sms));
+  for (int kb = 0; kb < nb; ++kb) {
+    k_trinv_scale<C><<<kb + 1, CTA_THREADS, sms, st>>>(X, Dinv, N, kb);
+    DPG_CHECK_LAUNCH();
+    const int rows = nb - kb - 1;
+    if (rows > 0) {
+      k_trinv_update<C><<<(unsigned)(rows * (kb + 1)), CTA_THREADS, 0, st>>>(X, dense, N, kb);
+      DPG_CHECK_LAUNCH();
+    }
+  }
+  const int64_t np = N * (N + 1) / 2;
+  *Lp = A.arr<C>((size_t)np);
+  *Up = A.arr<C>((size_t)np);
+  k_pack<C><<<1216, 256, 0, st>>>(X, N, *Lp, *Up);
+  DPG_CHECK_LAUNCH();
+  DPG_CUDA(cudaStreamSynchronize(st));
+  A.release(X);
+  A.release(Dinv);
+}
+
+void coarse_setup(SystemImpl& S, Level& C0, int* info, cudaStream_t st) {
+  Alloc& A = S.mem;
+  const int64_t N = C0.mesh.ndof;
+  C0.N0 = N;
+  double2* dense = A.arr<double2>((size_t)N * N);
+  DPG_CUDA(cudaMemsetAsync(dense, 0, (size_t)N * N * sizeof(double2), st));
+  k_dense_scatter<<<(unsigned)C0.mesh.nelem, 256, 0, st>>>(dense, N, C0.E, C0.dofs, C0.nloc);
+  DPG_CHECK_LAUNCH();
+  if (S.op.precision == DPGMG_PREC_MIXED) {
+    float2* d32 = A.arr<float2>((size_t)N * N);
+    k_narrow_mat<<<1216, 256, 0, st>>>(dense, d32, N * N);
+    DPG_CHECK_LAUNCH();
+    DPG_CUDA(cudaStreamSynchronize(st));
+    A.release(dense);
+    coarse_factor<float2>(A, d32, N, &C0.Lp32, &C0.Up32, info, st);
+    A.release(d32);
+  } else {
+    coarse_factor<double2>(A, dense, N, &C0.Lp64, &C0.Up64, info, st);
+    A.release(dense);
+  }
+  C0.has_coarse = true;
+}
+
+// ------------------------------------------------------------------ apply
+template <class C>
+__global__ void __launch_bounds__(256) k_trmv_lower(const C* __restrict__ Lp, int64_t N, const C* __restrict__ r,
+                                                    C* __restrict__ y) {
+  using O = Ops<C>;
+  const int lane = threadIdx.x & 31;
+  const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t i = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); i < N; i += nw) {
+    const C* row = Lp + i * (i + 1) / 2;
+    C a0 = O::zero(), a1 = O::zero();
+    int64_t j = lane;
+    for (; j + 32 <= i; j += 64) {
+      a0 = O::fma(row[j], r[j], a0);
+      a1 = O::fma(row[j + 32], r[j + 32], a1);
+    }
+    for (; j <= i; j += 32) a0 = O::fma(row[j], r[j], a0);
+    a0 = warp_sum_c(O::add(a0, a1));
+    if (lane == 0) y[i] = a0;
+  }
+}
+
+template <class C>
+__global__ void __launch_bounds__(256) k_trmv_upper(const C* __restrict__ Up, int64_t N, const C* __restrict__ y,
+                                                    C* __restrict__ e) {
+  using O = Ops<C>;
+  const int lane = threadIdx.x & 31;
+  const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t j = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); j < N; j += nw) {
+    const C* row = Up + j * N - j * (j - 1) / 2;
+    const int64_t len = N - j;
+    const C* yy = y + j;
+    C a0 = O::zero(), a1 = O::zero();
+    int64_t t = lane;
+    for (; t + 32 < len; t += 64) {
+      a0 = O::fma(row[t], yy[t], a0);
+      a1 = O::fma(row[t + 32], yy[t + 32], a1);
+    }
+    for (; t < len; t += 32) a0 = O::fma(row[t], yy[t], a0);
+    a0 = warp_sum_c(O::add(a0, a1));
+    if (lane == 0) e[j] = a0;
+  }
+}
+
+template <class C>
+static void coarse_apply_t(const C* Lp, const C* Up, int64_t N, const C* r, C* e, C* tmp, cudaStream_t st) {
+  unsigned blocks = (unsigned)std::min<int64_t>((N + 7) / 8, 152 * 16);
+  k_trmv_lower<C><<<blocks, 256, 0, st>>>(Lp, N, r, tmp);
+  DPG_CHECK_LAUNCH();
+  k_trmv_upper<C><<<blocks, 256, 0, st>>>(Up, N, tmp, e);
+  DPG_CHECK_LAUNCH();
+}
+
+void coarse_apply64(const Level& C0, const double2* r, double2* e, double2* tmp, cudaStream_t st) {
+  coarse_apply_t<double2>(C0.Lp64, C0.Up64, C0.N0, r, e, tmp, st);
+}
+void coarse_apply32(const Level& C0, const float2* r, float2* e, float2* tmp, cudaStream_t st) {
+  coarse_apply_t<float2>(C0.Lp32, C0.Up32, C0.N0, r, e, tmp, st);
+}
+
+}  // namespace dpgmg

@@ -34,7 +34,9 @@ void count_launch();
 struct Alloc {
   size_t budget = 0, used = 0, peak = 0;
   std::vector<void*> ptrs;
+  std::vector<size_t> sizes;
   void* get(size_t bytes);
+  void release(void* p);     // free one allocation early (stream work using it must be done)
   template <class T> T* arr(size_t n) { return reinterpret_cast<T*>(get(n * sizeof(T) + 16)); }
   void free_all();
   ~Alloc() { free_all(); }
@@ -95,10 +97,11 @@ struct Level {
   int32_t *P_col = nullptr, *PT_col = nullptr, *sslots = nullptr;
   double *P_val = nullptr, *PT_val = nullptr;
   char* smask = nullptr;
-  // coarsest: dense Cholesky factor
+  // coarsest: packed L^-1 (rows of its lower triangle) and L^-H (rows of its upper triangle)
   int64_t N0 = 0;
-  double2* C64 = nullptr;
-  float2* C32 = nullptr;
+  bool has_coarse = false;
+  double2 *Lp64 = nullptr, *Up64 = nullptr;
+  float2 *Lp32 = nullptr, *Up32 = nullptr;
 };
 
 struct Workspace;   // V-cycle work vectors (per precision)
@@ -141,6 +144,10 @@ void ecsr_add_elements(ECSRDev& D, const double2* E, const int64_t* dofs, int64_
                        cudaStream_t st);
 void build_hierarchy(SystemImpl& S, cudaStream_t st);
 void assemble_rhs(SystemImpl& S, cudaStream_t st);
+// coarse.cu
+void coarse_setup(SystemImpl& S, Level& C0, int* info, cudaStream_t st);
+void coarse_apply64(const Level& C0, const double2* r, double2* e, double2* tmp, cudaStream_t st);
+void coarse_apply32(const Level& C0, const float2* r, float2* e, float2* tmp, cudaStream_t st);
 // solve.cu
 int pcg_solve(SystemImpl& S, cudaStream_t st, double2* x, dpgmg_stats* stats);
 void apply_op(SystemImpl& S, int op, int level, const double2* x, double2* y, cudaStream_t st);

@@ -8,8 +8,7 @@
 //     operators", restrict),
 //   * vertex-patch blocks of the smoothing operator and their inverses
 //     ("V-cycle and smoother"),
-//   * the dense Cholesky factor of the coarsest operator (the paper solves its
-//     initial mesh directly, Sec. 4 list).
+//   * the coarsest level (coarse.cu).
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -210,111 +209,6 @@ __global__ void __launch_bounds__(CTA_THREADS) k_patch_invert(const int64_t* ptr
   cta_trsm_lower_h<double2>(W, n, n, M, n, n, reinterpret_cast<char*>(sh2));
 }
 
-// ------------------------------------------------------------------ coarsest
-__global__ void k_dense_scatter(double2* C, int64_t N, const double2* E, const int64_t* dofs, int nloc) {
-  const int64_t e = blockIdx.x;
-  for (int q = threadIdx.x; q < nloc * nloc; q += blockDim.x) {
-    int i = q / nloc, j = q % nloc;
-    int64_t gi = dofs[e * nloc + i], gj = dofs[e * nloc + j];
-    if (gi < 0 || gj < 0) continue;
-    double2 v = E[e * (size_t)nloc * nloc + q];
-    atomicAdd(&C[gi * N + gj].x, v.x);
-    atomicAdd(&C[gi * N + gj].y, v.y);
-  }
-}
-
-constexpr int CNB = 64;   // block width of the multi-CTA dense Cholesky
-
-__global__ void __launch_bounds__(CTA_THREADS) k_dense_diag(double2* C, int64_t N, int k0, int* info) {
-  extern __shared__ double2 sh2[];
-  int kb = (int)(N - k0 < CNB ? N - k0 : CNB);
-  int inf = cta_potrf<double2>(C + (size_t)k0 * N + k0, kb, (int)N, sh2);
-  if (threadIdx.x == 0 && inf) atomicOr(info, 16);
-}
-
-// rows i >= k1: C[i, k0:k0+kb] <- C[i, k0:k0+kb] L_kk^-H ; one thread per row
-__global__ void k_dense_panel(double2* C, int64_t N, int k0) {
-  extern __shared__ double2 D[];
-  int kb = (int)(N - k0 < CNB ? N - k0 : CNB);
-  for (int q = threadIdx.x; q < kb * kb; q += blockDim.x) D[q] = C[(size_t)(k0 + q / kb) * N + k0 + q % kb];
-  __syncthreads();
-  int64_t i = (int64_t)k0 + kb + blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (i >= N) return;
-  double2* row = C + i * N + k0;
-  double2 x[CNB];
-  for (int j = 0; j < kb; ++j) {
-    double2 v = row[j];
-    for (int t = 0; t < j; ++t) v = Ops<double2>::fnmac(x[t], D[j * kb + t], v);
-    double inv = 1.0 / D[j * kb + j].x;
-    x[j] = make_double2(v.x * inv, v.y * inv);
-  }
-  for (int j = 0; j < kb; ++j) row[j] = x[j];
-}
-
-// trailing update, one CTA per lower 64x64 tile pair: C[i][j] -= sum_t L[i][t] conj(L[j][t])
-__global__ void __launch_bounds__(CTA_THREADS) k_dense_herk(double2* C, int64_t N, int k0) {
-  __shared__ double2 Pi[CNB][17];
-  __shared__ double2 Pj[CNB][17];
-  const int kb = (int)(N - k0 < CNB ? N - k0 : CNB);
-  const int64_t k1 = k0 + kb;
-  // decode tile pair (bi >= bj) from the linear block index
-  int64_t t = blockIdx.x;
-  int64_t bi = (int64_t)((std::sqrt(8.0 * t + 1.0) - 1.0) / 2.0);
-  while ((bi + 1) * (bi + 2) / 2 <= t) ++bi;
-  while (bi * (bi + 1) / 2 > t) --bi;
-  int64_t bj = t - bi * (bi + 1) / 2;
-  const int64_t i0 = k1 + bi * CNB, j0 = k1 + bj * CNB;
-  const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;   // 16 x 16 threads, 4 x 4 outputs each
-  double2 acc[4][4];
-  for (int a = 0; a < 4; ++a)
-    for (int b = 0; b < 4; ++b) acc[a][b] = make_double2(0, 0);
-  for (int t0 = 0; t0 < kb; t0 += 16) {
-    for (int q = threadIdx.x; q < CNB * 16; q += blockDim.x) {
-      int r = q / 16, c = q % 16;
-      int64_t ii = i0 + r, jj = j0 + r;
-      Pi[r][c] = (ii < N && t0 + c < kb) ? C[ii * N + k0 + t0 + c] : make_double2(0, 0);
-      Pj[r][c] = (jj < N && t0 + c < kb) ? C[jj * N + k0 + t0 + c] : make_double2(0, 0);
-    }
-    __syncthreads();
-    for (int c = 0; c < 16; ++c) {
-      double2 av[4], bv[4];
-      for (int a = 0; a < 4; ++a) av[a] = Pi[ty * 4 + a][c];
-      for (int b = 0; b < 4; ++b) bv[b] = Pj[tx * 4 + b][c];
-      for (int a = 0; a < 4; ++a)
-        for (int b = 0; b < 4; ++b) acc[a][b] = Ops<double2>::fmac(av[a], bv[b], acc[a][b]);
-    }
-    __syncthreads();
-  }
-  for (int a = 0; a < 4; ++a)
-    for (int b = 0; b < 4; ++b) {
-      int64_t i = i0 + ty * 4 + a, j = j0 + tx * 4 + b;
-      if (i < N && j <= i) {
-        double2& o = C[i * N + j];
-        o.x -= acc[a][b].x;
-        o.y -= acc[a][b].y;
-      }
-    }
-}
-
-static void dense_cholesky(double2* C, int64_t N, int* info, cudaStream_t st) {
-  const size_t sm = (size_t)(NB * NB + 2 * TL * NB) * sizeof(double2) + 64;
-  DPG_CUDA(cudaFuncSetAttribute(k_dense_diag, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-  DPG_CUDA(cudaFuncSetAttribute(k_dense_panel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)(CNB * CNB * sizeof(double2))));
-  for (int64_t k0 = 0; k0 < N; k0 += CNB) {
-    int kb = (int)(N - k0 < CNB ? N - k0 : CNB);
-    k_dense_diag<<<1, CTA_THREADS, sm, st>>>(C, N, (int)k0, info);
-    DPG_CHECK_LAUNCH();
-    int64_t rows = N - k0 - kb;
-    if (rows <= 0) break;
-    k_dense_panel<<<(unsigned)((rows + 127) / 128), 128, CNB * CNB * sizeof(double2), st>>>(C, N, (int)k0);
-    DPG_CHECK_LAUNCH();
-    int64_t nt = (rows + CNB - 1) / CNB;
-    k_dense_herk<<<(unsigned)(nt * (nt + 1) / 2), CTA_THREADS, 0, st>>>(C, N, (int)k0);
-    DPG_CHECK_LAUNCH();
-  }
-}
-
 // --------------------------------------------------------------- precision
 __global__ void k_to_c64(const double2* a, float2* b, int64_t n) {
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -487,15 +381,7 @@ void build_hierarchy(SystemImpl& S, cudaStream_t st) {
   // coarsest
   Level& C0 = S.levels[0];
   if (L == 0) C0.dofs = S.levels[0].dofs;
-  if (S.op.coarsest == DPGMG_COARSEST_CHOLESKY || L == 0) {
-    C0.N0 = C0.mesh.ndof;
-    C0.C64 = A.arr<double2>((size_t)C0.N0 * C0.N0);
-    DPG_CUDA(cudaMemsetAsync(C0.C64, 0, (size_t)C0.N0 * C0.N0 * sizeof(double2), st));
-    k_dense_scatter<<<(unsigned)C0.mesh.nelem, 256, 0, st>>>(C0.C64, C0.N0, C0.E, C0.dofs, C0.nloc);
-    DPG_CHECK_LAUNCH();
-    dense_cholesky(C0.C64, C0.N0, dinfo, st);
-    if (mixed) C0.C32 = to_c64(A, C0.C64, C0.N0 * C0.N0, st);
-  }
+  if (S.op.coarsest == DPGMG_COARSEST_CHOLESKY || L == 0) coarse_setup(S, C0, dinfo, st);
   int info = 0;
   DPG_CUDA(cudaMemcpyAsync(&info, dinfo, sizeof(int), cudaMemcpyDeviceToHost, st));
   DPG_CUDA(cudaStreamSynchronize(st));

@@ -5,7 +5,7 @@
 //   k_condense_*      macro-grid residual condensation r_S -= Y^H r_I (h levels)
 //   k_backsub         x_I = A_II^-1 r_I - Y x_S                  (h levels)
 //   k_csr_real        natural inclusion P and its adjoint P^T      (h levels)
-//   k_coarse_solve    L L^H e = r with the dense coarsest factor (cooperative)
+//   (coarsest solve: coarse.cu)
 //   k_dot_*, k_axpy*  CG recurrences in FP64
 // Every kernel is templated on the complex type of the V-cycle (complex128
 // on the FP64 path, complex64 on the mixed path); CG always runs in FP64.
@@ -25,14 +25,12 @@ template <> struct Prec<double2> {
   static const double2* inv(const PatchDev& p) { return p.inv64; }
   static const double2* Y(const Level& l) { return l.Y64; }
   static const double2* Ai(const Level& l) { return l.Ai64; }
-  static const double2* Cf(const Level& l) { return l.C64; }
 };
 template <> struct Prec<float2> {
   static const float2* A(const ECSRDev& a) { return a.v32; }
   static const float2* inv(const PatchDev& p) { return p.inv32; }
   static const float2* Y(const Level& l) { return l.Y32; }
   static const float2* Ai(const Level& l) { return l.Ai32; }
-  static const float2* Cf(const Level& l) { return l.C32; }
 };
 
 // ------------------------------------------------------------ profiling
@@ -123,6 +121,9 @@ void spmv64(const ECSRDev& A, const double2* x, double2* y, cudaStream_t st) {
 }
 
 // ------------------------------------------------------------- smoother
+// Patch product y_j = A_j^-1 (R_j r).  A_j^-1 is Hermitian, so row a of the
+// product is sum_k conj(M[k][a]) r_k: thread a walks down column a of the
+// row-major block, and consecutive threads read consecutive addresses.
 template <class C>
 __global__ void __launch_bounds__(256) k_patch_apply(const int64_t* __restrict__ ptr, const int32_t* __restrict__ dofs,
                                                      const int64_t* __restrict__ vptr, const C* __restrict__ inv,
@@ -136,13 +137,17 @@ __global__ void __launch_bounds__(256) k_patch_apply(const int64_t* __restrict__
   for (int q = threadIdx.x; q < n; q += blockDim.x) rj[q] = r[dofs[b + q]];
   __syncthreads();
   const C* M = inv + vptr[j];
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  for (int a = w; a < n; a += 8) {
-    const C* row = M + (size_t)a * n;
-    C acc = O::zero();
-    for (int k = lane; k < n; k += 32) acc = O::fma(row[k], rj[k], acc);
-    acc = warp_sum(acc);
-    if (lane == 0) pbuf[b + a] = acc;
+  for (int a = threadIdx.x; a < n; a += blockDim.x) {
+    C a0 = O::zero(), a1 = O::zero(), a2 = O::zero(), a3 = O::zero();
+    int k = 0;
+    for (; k + 4 <= n; k += 4) {
+      a0 = O::fmac(rj[k], M[(size_t)k * n + a], a0);
+      a1 = O::fmac(rj[k + 1], M[(size_t)(k + 1) * n + a], a1);
+      a2 = O::fmac(rj[k + 2], M[(size_t)(k + 2) * n + a], a2);
+      a3 = O::fmac(rj[k + 3], M[(size_t)(k + 3) * n + a], a3);
+    }
+    for (; k < n; ++k) a0 = O::fmac(rj[k], M[(size_t)k * n + a], a0);
+    pbuf[b + a] = O::add(O::add(a0, a1), O::add(a2, a3));
   }
 }
 
@@ -263,127 +268,6 @@ __global__ void k_scatter_add(const int32_t* __restrict__ idx, const C* __restri
   if (i < n) y[idx[i]] = Ops<C>::add(y[idx[i]], x[i]);
 }
 
-// ----------------------------------------------------------- coarse solve
-constexpr int CB = 64;
-constexpr long long BARRIER_SPIN_LIMIT = 1ll << 26;
-
-__device__ void grid_barrier(unsigned* bar, unsigned nblocks, unsigned& gen, int* err) {
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    __threadfence();
-    unsigned arrived = atomicAdd(&bar[0], 1u) + 1u;
-    if (arrived == nblocks) {
-      atomicExch(&bar[0], 0u);
-      __threadfence();
-      atomicAdd(&bar[1], 1u);
-    } else {
-      long long it = 0;
-      while (atomicAdd(&bar[1], 0u) == gen && it < BARRIER_SPIN_LIMIT) {
-        ++it;
-        __nanosleep(64);
-      }
-      if (it >= BARRIER_SPIN_LIMIT) atomicExch(err, 1);
-    }
-    gen += 1u;
-    __threadfence();
-  }
-  __syncthreads();
-}
-
-// Dense L L^H e = r.  y holds r on entry and e on exit.  Row block kb is owned
-// by CTA kb % gridDim.x, which applies every update to its rows; Dinv holds
-// the inverses of the diagonal blocks of L.
-template <class C>
-__global__ void __launch_bounds__(256) k_coarse_solve(const C* __restrict__ L, const C* __restrict__ Dinv, int64_t N,
-                                                      C* y, unsigned* bar, int* err) {
-  __shared__ C zb[CB];
-  using O = Ops<C>;
-  const int nb = (int)((N + CB - 1) / CB);
-  unsigned gen = 0;
-  if (threadIdx.x == 0) gen = atomicAdd(&bar[1], 0u);
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  // forward: L z = r
-  for (int kb = 0; kb < nb; ++kb) {
-    const int64_t k0 = (int64_t)kb * CB;
-    const int kw = (int)(N - k0 < CB ? N - k0 : CB);
-    if ((int)(kb % gridDim.x) == (int)blockIdx.x) {
-      if (threadIdx.x < kw) zb[threadIdx.x] = y[k0 + threadIdx.x];
-      __syncthreads();
-      const C* D = Dinv + (size_t)kb * CB * CB;
-      for (int r = w; r < kw; r += 8) {
-        C acc = O::zero();
-        for (int t = lane; t <= r; t += 32) acc = O::fma(D[r * CB + t], zb[t], acc);
-        acc = warp_sum(acc);
-        if (lane == 0) y[k0 + r] = acc;
-      }
-    }
-    grid_barrier(bar, gridDim.x, gen, err);
-    if (threadIdx.x < kw) zb[threadIdx.x] = y[k0 + threadIdx.x];
-    __syncthreads();
-    for (int rb = kb + 1; rb < nb; ++rb) {
-      if ((int)(rb % gridDim.x) != (int)blockIdx.x) continue;
-      const int64_t r0 = (int64_t)rb * CB;
-      const int rw = (int)(N - r0 < CB ? N - r0 : CB);
-      for (int r = w; r < rw; r += 8) {
-        const C* row = L + (size_t)(r0 + r) * N + k0;
-        C acc = O::zero();
-        for (int t = lane; t < kw; t += 32) acc = O::fma(row[t], zb[t], acc);
-        acc = warp_sum(acc);
-        if (lane == 0) y[r0 + r] = O::sub(y[r0 + r], acc);
-      }
-    }
-    __syncthreads();
-  }
-  grid_barrier(bar, gridDim.x, gen, err);
-  // backward: L^H e = z
-  for (int kb = nb - 1; kb >= 0; --kb) {
-    const int64_t k0 = (int64_t)kb * CB;
-    const int kw = (int)(N - k0 < CB ? N - k0 : CB);
-    if ((int)(kb % gridDim.x) == (int)blockIdx.x) {
-      if (threadIdx.x < kw) zb[threadIdx.x] = y[k0 + threadIdx.x];
-      __syncthreads();
-      const C* D = Dinv + (size_t)kb * CB * CB;
-      // x = D^H z : x_r = sum_{t >= r} conj(D[t][r]) z_t
-      for (int r = w; r < kw; r += 8) {
-        C acc = O::zero();
-        for (int t = r + lane; t < kw; t += 32) acc = O::fmac(zb[t], D[t * CB + r], acc);
-        acc = warp_sum(acc);
-        if (lane == 0) y[k0 + r] = acc;
-      }
-    }
-    grid_barrier(bar, gridDim.x, gen, err);
-    if (threadIdx.x < kw) zb[threadIdx.x] = y[k0 + threadIdx.x];
-    __syncthreads();
-    // rows i < k0: y_i -= sum_t conj(L[k0+t][i]) x_t ; threads over i (coalesced)
-    for (int rb = 0; rb < kb; ++rb) {
-      if ((int)(rb % gridDim.x) != (int)blockIdx.x) continue;
-      const int64_t r0 = (int64_t)rb * CB;
-      for (int i = threadIdx.x; i < CB; i += blockDim.x) {
-        C acc = O::zero();
-        for (int t = 0; t < kw; ++t) acc = O::fmac(zb[t], L[(size_t)(k0 + t) * N + r0 + i], acc);
-        y[r0 + i] = O::sub(y[r0 + i], acc);
-      }
-    }
-    __syncthreads();
-  }
-}
-
-// inverse of each lower-triangular diagonal block of the coarse factor
-template <class C>
-__global__ void __launch_bounds__(256) k_diag_inverse(const C* L, int64_t N, C* Dinv) {
-  extern __shared__ unsigned char shraw[];
-  const int kb = blockIdx.x;
-  const int64_t k0 = (int64_t)kb * CB;
-  const int kw = (int)(N - k0 < CB ? N - k0 : CB);
-  C* D = Dinv + (size_t)kb * CB * CB;
-  for (int q = threadIdx.x; q < CB * CB; q += blockDim.x) {
-    int r = q / CB, c = q % CB;
-    D[q] = (r == c && r < kw) ? Ops<C>::from_re(1) : Ops<C>::zero();
-  }
-  __syncthreads();
-  cta_trsm_lower<C, C>(L + (size_t)k0 * N + k0, kw, (int)N, D, kw, CB, reinterpret_cast<char*>(shraw));
-}
-
 // ------------------------------------------------------------- vector ops
 template <class C>
 __global__ void k_zero(C* y, int64_t n) {
@@ -500,11 +384,7 @@ struct WS {
   std::vector<LevelWS<float2>> w32;
   double2 *x = nullptr, *r = nullptr, *p = nullptr, *q = nullptr, *z = nullptr, *part = nullptr, *sc = nullptr;
   double2* sc_host = nullptr;    // pinned
-  double2 *Dinv64 = nullptr;
-  float2 *Dinv32 = nullptr;
-  unsigned* bar = nullptr;
   int* err = nullptr;
-  int coarse_grid = 0;
   ECSRDev Acg;                   // the CG operator (finest A_L, FP64)
   bool acg_owned = false;
 };
@@ -529,15 +409,6 @@ static void alloc_level_ws(WS& W, SystemImpl& S) {
   }
 }
 
-template <class C>
-static void diag_inverse(const C* Lf, int64_t N, C* Dinv, cudaStream_t st) {
-  int nb = (int)((N + CB - 1) / CB);
-  size_t sm = (size_t)(NB * NB + TL * NB) * sizeof(C) + (size_t)NB * TL * sizeof(C) + 64;
-  DPG_CUDA(cudaFuncSetAttribute(k_diag_inverse<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-  k_diag_inverse<C><<<nb, 256, sm, st>>>(Lf, N, Dinv);
-  DPG_CHECK_LAUNCH();
-}
-
 void ensure_workspace(SystemImpl& S, cudaStream_t st) {
   if (S.ws) return;
   WS* W = new WS();
@@ -552,29 +423,10 @@ void ensure_workspace(SystemImpl& S, cudaStream_t st) {
   W->part = S.mem.arr<double2>(RED_BLOCKS);
   W->sc = S.mem.arr<double2>(SC_COUNT);
   DPG_CUDA(cudaMallocHost(&W->sc_host, SC_COUNT * sizeof(double2)));
-  W->bar = S.mem.arr<unsigned>(2);
   W->err = S.mem.arr<int>(1);
-  DPG_CUDA(cudaMemsetAsync(W->bar, 0, 2 * sizeof(unsigned), st));
   DPG_CUDA(cudaMemsetAsync(W->err, 0, sizeof(int), st));
   alloc_level_ws<double2>(*W, S);
   if (S.op.precision == DPGMG_PREC_MIXED) alloc_level_ws<float2>(*W, S);
-  const Level& C0 = S.levels[0];
-  if (C0.C64) {
-    int nb = (int)((C0.N0 + CB - 1) / CB);
-    W->Dinv64 = S.mem.arr<double2>((size_t)nb * CB * CB);
-    diag_inverse<double2>(C0.C64, C0.N0, W->Dinv64, st);
-    if (C0.C32) {
-      W->Dinv32 = S.mem.arr<float2>((size_t)nb * CB * CB);
-      diag_inverse<float2>(C0.C32, C0.N0, W->Dinv32, st);
-    }
-    int dev = 0, nsm = 0, per = 0;
-    DPG_CUDA(cudaGetDevice(&dev));
-    DPG_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
-    DPG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_coarse_solve<double2>, 256, 0));
-    int per32 = 0;
-    DPG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per32, k_coarse_solve<float2>, 256, 0));
-    W->coarse_grid = std::max(1, std::min(nb, nsm * std::max(1, std::min(per, per32))));
-  }
   DPG_CUDA(cudaStreamSynchronize(st));
 }
 
@@ -586,24 +438,12 @@ void free_workspace(SystemImpl& S) {
   S.ws = nullptr;
 }
 
-template <class C> static const C* dinv(WS& W);
-template <> const double2* dinv<double2>(WS& W) { return W.Dinv64; }
-template <> const float2* dinv<float2>(WS& W) { return W.Dinv32; }
-
-template <class C>
-static void coarse_solve(SystemImpl& S, WS& W, const C* r, C* e, cudaStream_t st) {
-  const Level& C0 = S.levels[0];
-  const int64_t N = C0.N0;
-  DPG_CUDA(cudaMemcpyAsync(e, r, (size_t)N * sizeof(C), cudaMemcpyDeviceToDevice, st));
-  const C* Lf = Prec<C>::Cf(C0);
-  const C* Di = dinv<C>(W);
-  unsigned* bar = W.bar;
-  int* err = W.err;
-  int64_t NN = N;
-  C* ep = e;
-  void* args[] = {(void*)&Lf, (void*)&Di, (void*)&NN, (void*)&ep, (void*)&bar, (void*)&err};
-  DPG_CUDA(cudaMemsetAsync(bar, 0, sizeof(unsigned), st));   // arrival counter (generation kept)
-  DPG_CUDA(cudaLaunchCooperativeKernel((void*)k_coarse_solve<C>, dim3(W.coarse_grid), dim3(256), args, 0, st));
+template <class C> static void coarse_solve(SystemImpl& S, WS& W, const C* r, C* e, cudaStream_t st);
+template <> void coarse_solve<double2>(SystemImpl& S, WS& W, const double2* r, double2* e, cudaStream_t st) {
+  coarse_apply64(S.levels[0], r, e, W.w64[0].t, st);
+}
+template <> void coarse_solve<float2>(SystemImpl& S, WS& W, const float2* r, float2* e, cudaStream_t st) {
+  coarse_apply32(S.levels[0], r, e, W.w32[0].t, st);
 }
 
 // -------------------------------------------------------------- V-cycle
@@ -652,7 +492,7 @@ static void vcycle(SystemImpl& S, WS& W, int l, const C* r, C* x, cudaStream_t s
   const Level& F = S.levels[l];
   const int64_t n = F.mesh.ndof;
   if (l == 0) {
-    if (F.C64) coarse_solve<C>(S, W, r, x, st);
+    if (F.has_coarse) coarse_solve<C>(S, W, r, x, st);
     else {
       k_zero<C><<<nblk(n), 256, 0, st>>>(x, n);
       DPG_CHECK_LAUNCH();
