@@ -305,51 +305,57 @@ void coarse_setup(SystemImpl& S, Level& C0, int* info, cudaStream_t st) {
 }
 
 // ------------------------------------------------------------------ apply
+// One warp per row pair (i, N-1-i): every warp reads N+1 entries.
+template <class C>
+__device__ __forceinline__ C dot_row(const C* __restrict__ row, const C* __restrict__ v, int64_t len, int lane) {
+  using O = Ops<C>;
+  C a0 = O::zero(), a1 = O::zero();
+  int64_t t = lane;
+  for (; t + 32 < len; t += 64) {
+    a0 = O::fma(row[t], v[t], a0);
+    a1 = O::fma(row[t + 32], v[t + 32], a1);
+  }
+  if (t < len) a0 = O::fma(row[t], v[t], a0);
+  return warp_sum_c(O::add(a0, a1));
+}
+
 template <class C>
 __global__ void __launch_bounds__(256) k_trmv_lower(const C* __restrict__ Lp, int64_t N, const C* __restrict__ r,
                                                     C* __restrict__ y) {
-  using O = Ops<C>;
   const int lane = threadIdx.x & 31;
+  const int64_t half = (N + 1) / 2;
   const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
-  for (int64_t i = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); i < N; i += nw) {
-    const C* row = Lp + i * (i + 1) / 2;
-    C a0 = O::zero(), a1 = O::zero();
-    int64_t j = lane;
-    for (; j + 32 <= i; j += 64) {
-      a0 = O::fma(row[j], r[j], a0);
-      a1 = O::fma(row[j + 32], r[j + 32], a1);
+  for (int64_t w = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); w < half; w += nw) {
+    const int64_t i1 = w, i2 = N - 1 - w;
+    C s1 = dot_row<C>(Lp + i1 * (i1 + 1) / 2, r, i1 + 1, lane);
+    if (lane == 0) y[i1] = s1;
+    if (i2 != i1) {
+      C s2 = dot_row<C>(Lp + i2 * (i2 + 1) / 2, r, i2 + 1, lane);
+      if (lane == 0) y[i2] = s2;
     }
-    for (; j <= i; j += 32) a0 = O::fma(row[j], r[j], a0);
-    a0 = warp_sum_c(O::add(a0, a1));
-    if (lane == 0) y[i] = a0;
   }
 }
 
 template <class C>
 __global__ void __launch_bounds__(256) k_trmv_upper(const C* __restrict__ Up, int64_t N, const C* __restrict__ y,
                                                     C* __restrict__ e) {
-  using O = Ops<C>;
   const int lane = threadIdx.x & 31;
+  const int64_t half = (N + 1) / 2;
   const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
-  for (int64_t j = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); j < N; j += nw) {
-    const C* row = Up + j * N - j * (j - 1) / 2;
-    const int64_t len = N - j;
-    const C* yy = y + j;
-    C a0 = O::zero(), a1 = O::zero();
-    int64_t t = lane;
-    for (; t + 32 < len; t += 64) {
-      a0 = O::fma(row[t], yy[t], a0);
-      a1 = O::fma(row[t + 32], yy[t + 32], a1);
+  for (int64_t w = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); w < half; w += nw) {
+    const int64_t j1 = w, j2 = N - 1 - w;
+    C s1 = dot_row<C>(Up + j1 * N - j1 * (j1 - 1) / 2, y + j1, N - j1, lane);
+    if (lane == 0) e[j1] = s1;
+    if (j2 != j1) {
+      C s2 = dot_row<C>(Up + j2 * N - j2 * (j2 - 1) / 2, y + j2, N - j2, lane);
+      if (lane == 0) e[j2] = s2;
     }
-    for (; t < len; t += 32) a0 = O::fma(row[t], yy[t], a0);
-    a0 = warp_sum_c(O::add(a0, a1));
-    if (lane == 0) e[j] = a0;
   }
 }
 
 template <class C>
 static void coarse_apply_t(const C* Lp, const C* Up, int64_t N, const C* r, C* e, C* tmp, cudaStream_t st) {
-  unsigned blocks = (unsigned)std::min<int64_t>((N + 7) / 8, 152 * 16);
+  unsigned blocks = (unsigned)std::min<int64_t>(((N + 1) / 2 + 7) / 8, 152 * 16);
   k_trmv_lower<C><<<blocks, 256, 0, st>>>(Lp, N, r, tmp);
   DPG_CHECK_LAUNCH();
   k_trmv_upper<C><<<blocks, 256, 0, st>>>(Up, N, tmp, e);

@@ -58,7 +58,8 @@ struct ECSRDev {
   int32_t* col_idx = nullptr;
   int64_t* val_ptr = nullptr;
   double2* v64 = nullptr;
-  float2* v32 = nullptr;
+  float2* v32 = nullptr;   // complex64 values (= high parts of the double-float split)
+  float2* vlo = nullptr;   // low parts: v64 ~ v32 + vlo (CG operator only)
 };
 
 struct PatchDev {
@@ -70,6 +71,8 @@ struct PatchDev {
   int32_t* slots = nullptr;
   double2* inv64 = nullptr;
   float2* inv32 = nullptr;
+  int2* chunks = nullptr;      // (patch, first row) of each 32-row work item
+  int64_t nchunks = 0;
 };
 
 struct Level {

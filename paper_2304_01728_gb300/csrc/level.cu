@@ -259,6 +259,13 @@ static void setup_patches(SystemImpl& S, Level& F, const std::vector<char>& smas
   D.val_ptr = upload(A, P.val_ptr, st);
   D.slot_ptr = upload(A, P.slot_ptr, st);
   D.slots = upload(A, P.slots, st);
+  {
+    std::vector<int2> ch;
+    for (int64_t j = 0; j < D.np; ++j)
+      for (int64_t a0 = 0; a0 < P.ptr[j + 1] - P.ptr[j]; a0 += 32) ch.push_back(make_int2((int)j, (int)a0));
+    D.nchunks = (int64_t)ch.size();
+    D.chunks = upload(A, ch, st);
+  }
   D.inv64 = A.arr<double2>((size_t)D.nvals);
   k_patch_gather<<<(unsigned)D.np, 256, 0, st>>>(F.A, D.ptr, D.dofs, D.val_ptr, D.inv64, 0);
   DPG_CHECK_LAUNCH();

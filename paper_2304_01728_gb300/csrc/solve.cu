@@ -116,38 +116,152 @@ static void spmv(const ECSRDev& A, const C* vals, const C* x, const C* b, C* y, 
   prof_end(prof, pe, st);
 }
 
+// ------------------------------------------------- double-float CG operator
+// The CG operator is stored as complex64 high and low parts (a = a_hi + a_lo,
+// exact to ~2^-48) and applied with error-free FP32 transformations
+// (TwoProduct by fma, TwoSum; Ogita, Rump and Oishi, "Accurate sum and dot
+// product", SIAM J. Sci. Comput. 2005): products a_hi x_hi are kept exactly,
+// the cross terms a_hi x_lo + a_lo x_hi are added to the low accumulator.
+// The result carries ~48 significant bits, enough for the FP64 CG recurrence,
+// without the FP64 pipe that bounds a complex128 SpMV on this GPU.
+__device__ __forceinline__ void df_add(float& sh, float& sl, float p, float q) {
+  const float s = sh + p;
+  const float bb = s - sh;
+  const float e = (sh - (s - bb)) + (p - bb);
+  sh = s;
+  sl += e + q;
+}
+__device__ __forceinline__ void df_mul(float ah, float al, float xh, float xl, float& p, float& q) {
+  p = ah * xh;
+  q = fmaf(ah, xh, -p);
+  q = fmaf(ah, xl, q);
+  q = fmaf(al, xh, q);
+}
+
+__global__ void __launch_bounds__(256) k_spmv_df(const int32_t* __restrict__ row_ent, const int64_t* __restrict__ ent_start,
+                                                 const int64_t* __restrict__ col_ptr, const int32_t* __restrict__ col_idx,
+                                                 const int64_t* __restrict__ val_ptr, const float2* __restrict__ vh,
+                                                 const float2* __restrict__ vl, const float2* __restrict__ xh,
+                                                 const float2* __restrict__ xl, const double2* __restrict__ b,
+                                                 double2* __restrict__ y, int64_t nrows, int mode) {
+  const int lane = threadIdx.x & 31;
+  const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t row = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); row < nrows; row += nw) {
+    const int32_t E = row_ent[row];
+    float rh = 0.f, rl = 0.f, ih = 0.f, il = 0.f;
+    if (E >= 0) {
+      const int64_t c0 = col_ptr[E];
+      const int nnz = (int)(col_ptr[E + 1] - c0);
+      const int64_t off = val_ptr[E] + (row - ent_start[E]) * nnz;
+      const int32_t* cols = col_idx + c0;
+      for (int k = lane; k < nnz; k += 32) {
+        const float2 ah = vh[off + k], al = vl[off + k];
+        const int c = cols[k];
+        const float2 uh = xh[c], ul = xl[c];
+        float p, q;
+        df_mul(ah.x, al.x, uh.x, ul.x, p, q);
+        df_add(rh, rl, p, q);
+        df_mul(ah.y, al.y, uh.y, ul.y, p, q);
+        df_add(rh, rl, -p, -q);
+        df_mul(ah.x, al.x, uh.y, ul.y, p, q);
+        df_add(ih, il, p, q);
+        df_mul(ah.y, al.y, uh.x, ul.x, p, q);
+        df_add(ih, il, p, q);
+      }
+    }
+    double re = (double)rh + (double)rl, im = (double)ih + (double)il;
+    for (int o = 16; o > 0; o >>= 1) {
+      re += __shfl_xor_sync(0xffffffffu, re, o);
+      im += __shfl_xor_sync(0xffffffffu, im, o);
+    }
+    if (lane == 0) y[row] = mode ? make_double2(b[row].x - re, b[row].y - im) : make_double2(re, im);
+  }
+}
+
+__global__ void k_split_vec(const double2* __restrict__ x, float2* __restrict__ xh, float2* __restrict__ xl,
+                            int64_t n) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const double2 v = x[i];
+  const float hx = (float)v.x, hy = (float)v.y;
+  xh[i] = make_float2(hx, hy);
+  xl[i] = make_float2((float)(v.x - (double)hx), (float)(v.y - (double)hy));
+}
+
+__global__ void k_split_vals(const double2* __restrict__ v, float2* __restrict__ vh, float2* __restrict__ vl,
+                             int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const double2 a = v[i];
+    const float hx = (float)a.x, hy = (float)a.y;
+    vh[i] = make_float2(hx, hy);
+    vl[i] = make_float2((float)(a.x - (double)hx), (float)(a.y - (double)hy));
+  }
+}
+
+// y = A x (mode 0) or b - A x (mode 1) with the double-float operator; xh/xl scratch
+static void spmv_df(const ECSRDev& A, const double2* x, const double2* b, double2* y, int mode, float2* xh,
+                    float2* xl, cudaStream_t st, SystemImpl* prof = nullptr) {
+  const int64_t n = A.nrows;
+  k_split_vec<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(x, xh, xl, n);
+  DPG_CHECK_LAUNCH();
+  int64_t blocks = std::min<int64_t>((n + 7) / 8, 152 * 16);
+  int pe = prof_begin(prof, st);
+  k_spmv_df<<<(unsigned)blocks, 256, 0, st>>>(A.row_ent, A.ent_start, A.col_ptr, A.col_idx, A.val_ptr, A.v32, A.vlo,
+                                             xh, xl, b, y, n, mode);
+  DPG_CHECK_LAUNCH();
+  prof_end(prof, pe, st);
+}
+
+void split_operator(Alloc& M, ECSRDev& A, cudaStream_t st) {
+  if (!A.v32) A.v32 = M.arr<float2>((size_t)std::max<int64_t>(A.nnz, 1));
+  A.vlo = M.arr<float2>((size_t)std::max<int64_t>(A.nnz, 1));
+  k_split_vals<<<1216, 256, 0, st>>>(A.v64, A.v32, A.vlo, A.nnz);
+  DPG_CHECK_LAUNCH();
+}
+
 void spmv64(const ECSRDev& A, const double2* x, double2* y, cudaStream_t st) {
   spmv<double2>(A, A.v64, x, nullptr, y, 0, st);
 }
 
 // ------------------------------------------------------------- smoother
-// Patch product y_j = A_j^-1 (R_j r).  A_j^-1 is Hermitian, so row a of the
-// product is sum_k conj(M[k][a]) r_k: thread a walks down column a of the
-// row-major block, and consecutive threads read consecutive addresses.
+// Patch product y_j = A_j^-1 (R_j r), one CTA per 32-row chunk of a patch.
+// A_j^-1 is Hermitian, so y_a = sum_k conj(M[k][a]) r_k: lane a of warp w
+// reads M[k][a0 + lane] for k = w, w + 8, ... (256-byte coalesced rows), and
+// the 8 warp partials are summed in shared memory.
 template <class C>
 __global__ void __launch_bounds__(256) k_patch_apply(const int64_t* __restrict__ ptr, const int32_t* __restrict__ dofs,
-                                                     const int64_t* __restrict__ vptr, const C* __restrict__ inv,
-                                                     const C* __restrict__ r, C* __restrict__ pbuf) {
+                                                     const int64_t* __restrict__ vptr, const int2* __restrict__ chunks,
+                                                     const C* __restrict__ inv, const C* __restrict__ r,
+                                                     C* __restrict__ pbuf) {
   extern __shared__ unsigned char shraw[];
+  __shared__ C part[8][33];
   C* rj = reinterpret_cast<C*>(shraw);
   using O = Ops<C>;
-  const int64_t j = blockIdx.x;
+  const int2 ch = chunks[blockIdx.x];
+  const int64_t j = ch.x;
   const int64_t b = ptr[j];
   const int n = (int)(ptr[j + 1] - b);
   for (int q = threadIdx.x; q < n; q += blockDim.x) rj[q] = r[dofs[b + q]];
   __syncthreads();
-  const C* M = inv + vptr[j];
-  for (int a = threadIdx.x; a < n; a += blockDim.x) {
-    C a0 = O::zero(), a1 = O::zero(), a2 = O::zero(), a3 = O::zero();
-    int k = 0;
-    for (; k + 4 <= n; k += 4) {
-      a0 = O::fmac(rj[k], M[(size_t)k * n + a], a0);
-      a1 = O::fmac(rj[k + 1], M[(size_t)(k + 1) * n + a], a1);
-      a2 = O::fmac(rj[k + 2], M[(size_t)(k + 2) * n + a], a2);
-      a3 = O::fmac(rj[k + 3], M[(size_t)(k + 3) * n + a], a3);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int a = ch.y + lane;
+  const C* M = inv + vptr[j] + a;
+  C a0 = O::zero(), a1 = O::zero();
+  if (a < n) {
+    int k = w;
+    for (; k + 8 < n; k += 16) {
+      a0 = O::fmac(rj[k], M[(size_t)k * n], a0);
+      a1 = O::fmac(rj[k + 8], M[(size_t)(k + 8) * n], a1);
     }
-    for (; k < n; ++k) a0 = O::fmac(rj[k], M[(size_t)k * n + a], a0);
-    pbuf[b + a] = O::add(O::add(a0, a1), O::add(a2, a3));
+    if (k < n) a0 = O::fmac(rj[k], M[(size_t)k * n], a0);
+  }
+  part[w][lane] = O::add(a0, a1);
+  __syncthreads();
+  if (w == 0 && a < n) {
+    C s = part[0][lane];
+#pragma unroll
+    for (int q = 1; q < 8; ++q) s = O::add(s, part[q][lane]);
+    pbuf[b + a] = s;
   }
 }
 
@@ -169,7 +283,8 @@ static void smooth(const Level& L, const C* r, C* y, double theta, int accumulat
   const PatchDev& P = L.P;
   size_t sm = (size_t)P.max_n * sizeof(C) + 16;
   int pe = prof_begin(prof, st);
-  k_patch_apply<C><<<(unsigned)P.np, 256, sm, st>>>(P.ptr, P.dofs, P.val_ptr, Prec<C>::inv(P), r, pbuf);
+  k_patch_apply<C><<<(unsigned)P.nchunks, 256, sm, st>>>(P.ptr, P.dofs, P.val_ptr, P.chunks, Prec<C>::inv(P), r,
+                                                        pbuf);
   DPG_CHECK_LAUNCH();
   prof_end(prof, pe, st);
   int64_t n = L.mesh.ndof;
@@ -383,6 +498,7 @@ struct WS {
   std::vector<LevelWS<double2>> w64;
   std::vector<LevelWS<float2>> w32;
   double2 *x = nullptr, *r = nullptr, *p = nullptr, *q = nullptr, *z = nullptr, *part = nullptr, *sc = nullptr;
+  float2 *xh = nullptr, *xl = nullptr;     // double-float split of the CG operand
   double2* sc_host = nullptr;    // pinned
   int* err = nullptr;
   ECSRDev Acg;                   // the CG operator (finest A_L, FP64)
@@ -421,6 +537,8 @@ void ensure_workspace(SystemImpl& S, cudaStream_t st) {
   W->q = S.mem.arr<double2>((size_t)n);
   W->z = S.mem.arr<double2>((size_t)n);
   W->part = S.mem.arr<double2>(RED_BLOCKS);
+  W->xh = S.mem.arr<float2>((size_t)n);
+  W->xl = S.mem.arr<float2>((size_t)n);
   W->sc = S.mem.arr<double2>(SC_COUNT);
   DPG_CUDA(cudaMallocHost(&W->sc_host, SC_COUNT * sizeof(double2)));
   W->err = S.mem.arr<int>(1);
@@ -565,8 +683,11 @@ static int check_err(WS& W, cudaStream_t st) {
 }
 
 static const ECSRDev& cg_operator(SystemImpl& S, WS& W, cudaStream_t st) {
-  const Level& F = S.levels.back();
-  if (S.levels.size() > 1 && F.kind == 1) return F.A;
+  Level& F = S.levels.back();
+  if (S.levels.size() > 1 && F.kind == 1) {
+    if (!F.A.vlo) split_operator(S.mem, F.A, st);
+    return F.A;
+  }
   if (!W.acg_owned) {
     // finest operator assembled separately (single level, or h-transition below the finest)
     std::vector<std::vector<int64_t>> g(F.mesh.nelem);
@@ -581,6 +702,7 @@ static const ECSRDev& cg_operator(SystemImpl& S, WS& W, cudaStream_t st) {
     ECSRHost H = build_ecsr(F.mesh, g);
     assemble_ecsr(S.mem, F.mesh, H, W.Acg, st);
     ecsr_add_elements(W.Acg, F.E, F.dofs, F.mesh.nelem, F.nloc, st);
+    split_operator(S.mem, W.Acg, st);
     DPG_CUDA(cudaStreamSynchronize(st));
     W.acg_owned = true;
   }
@@ -596,7 +718,7 @@ int pcg_solve(SystemImpl& S, cudaStream_t st, double2* xout, dpgmg_stats* stats)
     const int64_t esz = S.op.precision == DPGMG_PREC_MIXED ? 8 : 16;
     if (S.prof_which == DPGMG_PROF_SMOOTH_FINE) S.prof_bytes = Ff.P.nvals * esz;
     else if (S.prof_which == DPGMG_PROF_SPMV_FINE) S.prof_bytes = Ff.A.nnz * esz;
-    else if (S.prof_which == DPGMG_PROF_SPMV_CG) S.prof_bytes = A.nnz * 16;
+    else if (S.prof_which == DPGMG_PROF_SPMV_CG) S.prof_bytes = A.nnz * 16;   // hi + lo complex64
   }
   const int64_t n = S.levels.back().mesh.ndof;
   cudaEvent_t e0, e1;
@@ -619,7 +741,7 @@ int pcg_solve(SystemImpl& S, cudaStream_t st, double2* xout, dpgmg_stats* stats)
     DPG_CUDA(cudaMemcpyAsync(W.p, W.z, (size_t)n * sizeof(double2), cudaMemcpyDeviceToDevice, st));
     SystemImpl* pcg_prof = S.prof_which == DPGMG_PROF_SPMV_CG ? &S : nullptr;
     while (it < S.op.max_iter) {
-      spmv<double2>(A, A.v64, W.p, nullptr, W.q, 0, st, pcg_prof);
+      spmv_df(A, W.p, nullptr, W.q, 0, W.xh, W.xl, st, pcg_prof);
       dot(W, W.p, W.q, n, 0, st);   // pq = p^H q, alpha = rho / pq
       k_cg_update<<<RED_BLOCKS, 256, 0, st>>>(W.x, W.r, W.p, W.q, W.sc, n, W.part);
       DPG_CHECK_LAUNCH();
@@ -650,7 +772,7 @@ int pcg_solve(SystemImpl& S, cudaStream_t st, double2* xout, dpgmg_stats* stats)
   // true residual ||b - A x|| / ||b|| in FP64
   double true_rel = 0.0;
   if (nb > 0.0) {
-    spmv<double2>(A, A.v64, W.x, S.b, W.q, 1, st);
+    spmv_df(A, W.x, S.b, W.q, 1, W.xh, W.xl, st);
     dot(W, W.q, W.q, n, 1, st);
     DPG_CUDA(cudaMemcpyAsync(W.sc_host, W.sc, SC_COUNT * sizeof(double2), cudaMemcpyDeviceToHost, st));
     DPG_CUDA(cudaStreamSynchronize(st));
@@ -773,7 +895,7 @@ void apply_op(SystemImpl& S, int op, int l, const double2* x, double2* y, cudaSt
   WS& W = *reinterpret_cast<WS*>(S.ws);
   if (op == DPGMG_OP_AFULL) {
     const ECSRDev& A = cg_operator(S, W, st);
-    spmv<double2>(A, A.v64, x, nullptr, y, 0, st);
+    spmv_df(A, x, nullptr, y, 0, W.xh, W.xl, st);
     return;
   }
   if (S.op.precision == DPGMG_PREC_MIXED) {
