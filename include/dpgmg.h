@@ -225,6 +225,30 @@ int dpgmg_profile(dpgmg_handle h, dpgmg_system sys, int which);
 int dpgmg_profile_read(dpgmg_handle h, dpgmg_system sys, double* total_ms, long long* launches,
                        long long* bytes_per_launch);
 
+/* ---- allocation-free smoother ---------------------------------------------- */
+
+/* The paper has no counterpart to this call; it serves callers that cannot let
+ * a library allocate device memory: programs that give all device memory to
+ * their own fixed arena or pool up front, and latency-critical loops that
+ * cannot afford the device-wide synchronisation of cudaMalloc/cudaFree.
+ *
+ * y = theta_l S_l r, the same operator as dpgmg_apply(DPGMG_OP_SMOOTH), on
+ * caller-owned DEVICE buffers r_dev, y_dev (c128, n_dof of level l each).
+ * `level` is 1..n_levels-1.  It allocates nothing: its only scratch (one
+ * complex entry per patch slot) is a fixed array compiled into the library,
+ * DPGMG_NOALLOC_MAX_SLOTS entries (64 MiB), which every GPU that loads the
+ * library holds until the process exits.  A level with more patch slots is
+ * rejected with DPGMG_ERR_ARG (message in dpgmg_last_error).  The first call
+ * on a device looks up the array's device address (cudaGetSymbolAddress);
+ * make that first call before any stream capture on that device.  Every
+ * entry of the scratch that is read is written first in the same call, so
+ * leftover contents of earlier calls do not matter; but all calls share the
+ * one array, so calls whose work overlaps on the GPU (other handles, other
+ * streams) race on it.  The work runs on the handle's stream and the call
+ * returns after y is written.  Errors: ARG, CUDA. */
+#define DPGMG_NOALLOC_MAX_SLOTS 4194304LL
+int dpgmg_smooth_noalloc(dpgmg_handle h, dpgmg_system sys, int level, const double* r_dev, double* y_dev);
+
 #ifdef __cplusplus
 }
 #endif

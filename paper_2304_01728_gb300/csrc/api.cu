@@ -10,13 +10,6 @@
 
 #include "internal.h"
 
-struct dpgmg_handle_s {
-  dpgmg::HandleImpl h;
-  std::mutex mu;
-};
-struct dpgmg_system_s {
-  dpgmg::SystemImpl s;
-};
 
 namespace dpgmg {
 

@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -164,3 +165,11 @@ void smooth_apply64(const Level& L, const double2* r, double2* y, double theta, 
                     cudaStream_t st);
 
 }  // namespace dpgmg
+
+struct dpgmg_handle_s {
+  dpgmg::HandleImpl h;
+  std::mutex mu;
+};
+struct dpgmg_system_s {
+  dpgmg::SystemImpl s;
+};

@@ -62,7 +62,7 @@ _lib = None
 EXPORTS = ["dpgmg_create", "dpgmg_destroy", "dpgmg_query_sizes", "dpgmg_default_opts", "dpgmg_setup",
            "dpgmg_solve", "dpgmg_release", "dpgmg_strerror", "dpgmg_last_error", "dpgmg_level_info",
            "dpgmg_element_matrix", "dpgmg_rhs", "dpgmg_apply", "dpgmg_launch_count", "dpgmg_profile",
-           "dpgmg_profile_read"]
+           "dpgmg_profile_read", "dpgmg_smooth_noalloc"]
 PROF_OFF, PROF_SMOOTH_FINE, PROF_SPMV_FINE, PROF_SPMV_CG = 0, 1, 2, 3
 
 
@@ -95,6 +95,8 @@ def lib():
     L.dpgmg_element_matrix.argtypes = [vp, vp, i, ll, dptr, dptr]
     L.dpgmg_rhs.argtypes = [vp, vp, dptr]
     L.dpgmg_apply.argtypes = [vp, vp, i, i, dptr, dptr]
+    L.dpgmg_smooth_noalloc.argtypes = [vp, vp, i, vp, vp]
+    L.dpgmg_smooth_noalloc.restype = i
     L.dpgmg_launch_count.argtypes = []
     L.dpgmg_launch_count.restype = ll
     L.dpgmg_profile.argtypes = [vp, vp, i]
@@ -233,6 +235,12 @@ def dpgmg_profile_read(h, s):
     ms, n, b = ctypes.c_double(), ctypes.c_longlong(), ctypes.c_longlong()
     _check(lib().dpgmg_profile_read(h, s, ctypes.byref(ms), ctypes.byref(n), ctypes.byref(b)), "dpgmg_profile_read")
     return ms.value, n.value, b.value
+
+
+def dpgmg_smooth_noalloc(h, s, level, r_dev, y_dev):
+    """y = theta S r on device pointers (ints), allocation-free; see include/dpgmg.h."""
+    _check(lib().dpgmg_smooth_noalloc(h, s, int(level), ctypes.c_void_p(r_dev), ctypes.c_void_p(y_dev)),
+           "dpgmg_smooth_noalloc")
 
 
 def strerror(code):
