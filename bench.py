@@ -50,6 +50,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64-compare", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--n", type=int, default=0, help="override the mesh size n^3 (profiling of a smaller case)")
     ap.add_argument("--oracle-sample", action="store_true", help=argparse.SUPPRESS)
     ap.add_argument("--oracle-steps", type=int, default=1, help=argparse.SUPPRESS)
     return ap.parse_args()
@@ -223,6 +224,9 @@ def run_gb300(args, rank, world, local_rank):
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
     w = workload(args.config, args.precision)
+    if args.n:
+        w["problem"]["n"] = (args.n,) * 3
+        w["name"] += " (mesh overridden to %d^3)" % args.n
     stream = torch.cuda.Stream()
     h = D.dpgmg_create(local_rank, 0, ctypes.c_void_p(stream.cuda_stream))
     pb, keep = D.make_problem(**w["problem"])

@@ -189,24 +189,25 @@ __global__ void k_patch_gather(ECSRDev A, const int64_t* ptr, const int32_t* dof
   }
 }
 
-// In place: M (n x n) -> M^-1 via Cholesky in the scratch copy W.
-__global__ void __launch_bounds__(CTA_THREADS) k_patch_invert(const int64_t* ptr, const int64_t* vptr, double2* vals,
-                                                            double2* scratch, const int64_t* soff, int64_t j0,
-                                                            int* info) {
-  extern __shared__ double2 sh2[];
+// In place: M (n x n) -> M^-1 via Cholesky in the scratch copy W (precision C).
+template <class C>
+__global__ void __launch_bounds__(CTA_THREADS) k_patch_invert(const int64_t* ptr, const int64_t* vptr, C* vals,
+                                                            C* scratch, const int64_t* soff, int64_t j0, int* info) {
+  extern __shared__ unsigned char shraw[];
+  C* sh = reinterpret_cast<C*>(shraw);
   const int64_t j = j0 + blockIdx.x;
   const int n = (int)(ptr[j + 1] - ptr[j]);
-  double2* M = vals + vptr[j];
-  double2* W = scratch + soff[blockIdx.x];
+  C* M = vals + vptr[j];
+  C* W = scratch + soff[blockIdx.x];
   for (int q = threadIdx.x; q < n * n; q += blockDim.x) W[q] = M[q];
   __syncthreads();
-  int inf = cta_potrf<double2>(W, n, n, sh2);
+  int inf = cta_potrf<C>(W, n, n, sh);
   if (threadIdx.x == 0 && inf) atomicOr(info, 8);
   for (int q = threadIdx.x; q < n * n; q += blockDim.x)
-    M[q] = (q / n == q % n) ? make_double2(1, 0) : make_double2(0, 0);
+    M[q] = (q / n == q % n) ? Ops<C>::from_re(1) : Ops<C>::zero();
   __syncthreads();
-  cta_trsm_lower<double2, double2>(W, n, n, M, n, n, reinterpret_cast<char*>(sh2));
-  cta_trsm_lower_h<double2>(W, n, n, M, n, n, reinterpret_cast<char*>(sh2));
+  cta_trsm_lower<C, C>(W, n, n, M, n, n, reinterpret_cast<char*>(sh));
+  cta_trsm_lower_h<C>(W, n, n, M, n, n, reinterpret_cast<char*>(sh));
 }
 
 // --------------------------------------------------------------- precision
@@ -243,8 +244,39 @@ void assemble_rhs(SystemImpl& S, cudaStream_t st) {
 }
 
 // --------------------------------------------------------------- driver
+// Invert all patch blocks in place, in chunks that bound the scratch copy.
+template <class C>
+static void invert_patches(Alloc& A, PatchDev& D, const Patches& P, C* vals, int* dinfo, cudaStream_t st) {
+  const size_t sm = (size_t)(NB * NB + 2 * TL * NB) * sizeof(C) + 64;
+  DPG_CUDA(cudaFuncSetAttribute(k_patch_invert<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+  const size_t one = (size_t)D.max_n * D.max_n;
+  size_t cap = std::min<size_t>(std::max<size_t>(((size_t)1 << 28) / sizeof(C), one) * 4, ((size_t)2 << 30) / sizeof(C));
+  cap = std::max(cap, one);
+  C* scratch = A.arr<C>(cap);
+  int64_t* soff = A.arr<int64_t>((size_t)D.np + 1);
+  std::vector<int64_t> offs;
+  for (int64_t j0 = 0; j0 < D.np;) {
+    offs.clear();
+    int64_t acc = 0, j = j0;
+    while (j < D.np) {
+      int64_t nj = P.ptr[j + 1] - P.ptr[j];
+      if (acc + nj * nj > (int64_t)cap && j > j0) break;
+      offs.push_back(acc);
+      acc += nj * nj;
+      ++j;
+    }
+    DPG_CUDA(cudaMemcpyAsync(soff, offs.data(), offs.size() * sizeof(int64_t), cudaMemcpyHostToDevice, st));
+    k_patch_invert<C><<<(unsigned)(j - j0), CTA_THREADS, sm, st>>>(D.ptr, D.val_ptr, vals, scratch, soff, j0, dinfo);
+    DPG_CHECK_LAUNCH();
+    DPG_CUDA(cudaStreamSynchronize(st));   // the offsets buffer is reused
+    j0 = j;
+  }
+  A.release(soff);
+  A.release(scratch);
+}
+
 static void setup_patches(SystemImpl& S, Level& F, const std::vector<char>& smask, int H, const int nco[3],
-                          int* dinfo, cudaStream_t st) {
+                          int* dinfo, cudaStream_t st, bool mixed) {
   Alloc& A = S.mem;
   Patches P = build_patches(F.mesh, smask, H, nco);
   PatchDev& D = F.P;
@@ -269,31 +301,11 @@ static void setup_patches(SystemImpl& S, Level& F, const std::vector<char>& smas
   D.inv64 = A.arr<double2>((size_t)D.nvals);
   k_patch_gather<<<(unsigned)D.np, 256, 0, st>>>(F.A, D.ptr, D.dofs, D.val_ptr, D.inv64, 0);
   DPG_CHECK_LAUNCH();
-  // invert in chunks with a bounded scratch
-  const size_t sm = (size_t)(NB * NB + 2 * TL * NB) * sizeof(double2) + 64;
-  DPG_CUDA(cudaFuncSetAttribute(k_patch_invert, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-  size_t one = (size_t)D.max_n * D.max_n * 16;
-  size_t cap = std::min<size_t>(std::max<size_t>((size_t)1 << 28, one) * 4, (size_t)2 << 30);
-  cap = std::max(cap, one);
-  double2* scratch = A.arr<double2>(cap / 16);
-  int64_t* soff = A.arr<int64_t>((size_t)D.np + 1);
-  std::vector<int64_t> offs;
-  for (int64_t j0 = 0; j0 < D.np;) {
-    offs.clear();
-    int64_t acc = 0, j = j0;
-    while (j < D.np) {
-      int64_t nj = P.ptr[j + 1] - P.ptr[j];
-      if (acc + nj * nj > (int64_t)(cap / 16) && j > j0) break;
-      offs.push_back(acc);
-      acc += nj * nj;
-      ++j;
-    }
-    DPG_CUDA(cudaMemcpyAsync(soff, offs.data(), offs.size() * sizeof(int64_t), cudaMemcpyHostToDevice, st));
-    k_patch_invert<<<(unsigned)(j - j0), CTA_THREADS, sm, st>>>(D.ptr, D.val_ptr, D.inv64, scratch, soff, j0, dinfo);
-    DPG_CHECK_LAUNCH();
-    DPG_CUDA(cudaStreamSynchronize(st));   // offsets buffer is reused
-    j0 = j;
-  }
+  // Patch inverses are computed in FP64 on both paths; the mixed path rounds
+  // them to complex64 after theta is estimated (a complex64 factorisation of
+  // blocks with condition numbers up to ~5e4 perturbs the smoother by ~1e-3).
+  invert_patches<double2>(A, D, P, D.inv64, dinfo, st);
+  (void)mixed;
 }
 
 void build_hierarchy(SystemImpl& S, cudaStream_t st) {
@@ -374,11 +386,14 @@ void build_hierarchy(SystemImpl& S, cudaStream_t st) {
     }
     F.n_smooth = 0;
     for (char c : smask) F.n_smooth += c;
-    setup_patches(S, F, smask, H, C.mesh.n, dinfo, st);
+    setup_patches(S, F, smask, H, C.mesh.n, dinfo, st, mixed);
     estimate_theta(S, l, st);
     if (mixed) {
       F.A.v32 = to_c64(A, F.A.v64, F.A.nnz, st);
       F.P.inv32 = to_c64(A, F.P.inv64, F.P.nvals, st);
+      DPG_CUDA(cudaStreamSynchronize(st));
+      A.release(F.P.inv64);     // the mixed V-cycle only reads the complex64 copy
+      F.P.inv64 = nullptr;
       if (F.kind == 2) {
         F.Y32 = to_c64(A, F.Y64, F.nK * F.nI * F.nS, st);
         F.Ai32 = to_c64(A, F.Ai64, F.nK * F.nI * F.nI, st);

@@ -246,16 +246,20 @@ __global__ void __launch_bounds__(256) k_patch_apply(const int64_t* __restrict__
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int a = ch.y + lane;
   const C* M = inv + vptr[j] + a;
-  C a0 = O::zero(), a1 = O::zero();
+  C a0 = O::zero(), a1 = O::zero(), a2 = O::zero(), a3 = O::zero();
   if (a < n) {
     int k = w;
-    for (; k + 8 < n; k += 16) {
-      a0 = O::fmac(rj[k], M[(size_t)k * n], a0);
-      a1 = O::fmac(rj[k + 8], M[(size_t)(k + 8) * n], a1);
+    for (; k + 24 < n; k += 32) {
+      const C m0 = M[(size_t)k * n], m1 = M[(size_t)(k + 8) * n];
+      const C m2 = M[(size_t)(k + 16) * n], m3 = M[(size_t)(k + 24) * n];
+      a0 = O::fmac(rj[k], m0, a0);
+      a1 = O::fmac(rj[k + 8], m1, a1);
+      a2 = O::fmac(rj[k + 16], m2, a2);
+      a3 = O::fmac(rj[k + 24], m3, a3);
     }
-    if (k < n) a0 = O::fmac(rj[k], M[(size_t)k * n], a0);
+    for (; k < n; k += 8) a0 = O::fmac(rj[k], M[(size_t)k * n], a0);
   }
-  part[w][lane] = O::add(a0, a1);
+  part[w][lane] = O::add(O::add(a0, a1), O::add(a2, a3));
   __syncthreads();
   if (w == 0 && a < n) {
     C s = part[0][lane];
@@ -801,62 +805,105 @@ __device__ __forceinline__ uint64_t splitmix64(uint64_t seed, uint64_t k) {
   z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
   return z ^ (z >> 31);
 }
-__global__ void k_start_vector(double2* x, int64_t n, const int64_t* slot_ptr) {
+template <class C>
+__global__ void k_start_vector(C* x, int64_t n, const int64_t* slot_ptr) {
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= n) return;
   const double s = 1.0 / 9007199254740992.0;
   double re = 2.0 * (double)(splitmix64(12345ull, 2 * (uint64_t)i) >> 11) * s - 1.0;
   double im = 2.0 * (double)(splitmix64(12345ull, 2 * (uint64_t)i + 1) >> 11) * s - 1.0;
   bool in = slot_ptr[i + 1] > slot_ptr[i];   // DOF belongs to some patch
-  x[i] = in ? make_double2(re, im) : make_double2(0, 0);
+  using R = typename Ops<C>::R;
+  x[i] = in ? Ops<C>::mk((R)re, (R)im) : Ops<C>::zero();
 }
-__global__ void k_scale(double2* x, int64_t n, const double2* sc, int slot) {
-  double s = 1.0 / sqrt(sc[slot].x);
+
+// partial[b] = sum conj(u_i) v_i (accumulated in FP64 whatever the vector precision)
+template <class C>
+__global__ void k_dot_partial_t(const C* __restrict__ u, const C* __restrict__ v, int64_t n, double2* __restrict__ part) {
+  __shared__ double2 sh[8];
+  double2 acc = make_double2(0, 0);
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const double ux = u[i].x, uy = u[i].y, vx = v[i].x, vy = v[i].y;
+    acc.x += ux * vx + uy * vy;
+    acc.y += ux * vy - uy * vx;
+  }
+  acc = warp_sum(acc);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double2 s2 = make_double2(0, 0);
+    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) s2 = Ops<double2>::add(s2, sh[k]);
+    part[blockIdx.x] = s2;
+  }
+}
+
+template <class C>
+__global__ void k_scale(C* x, int64_t n, const double2* sc, int slot) {
+  using R = typename Ops<C>::R;
+  const R s = (R)(1.0 / sqrt(sc[slot].x));
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    x[i] = make_double2(x[i].x * s, x[i].y * s);
+    x[i] = Ops<C>::scale(x[i], s);
+}
+
+template <class C>
+static void dot_t(WS& W, const C* u, const C* v, int64_t n, int which, cudaStream_t st) {
+  k_dot_partial_t<C><<<RED_BLOCKS, 256, 0, st>>>(u, v, n, W.part);
+  DPG_CHECK_LAUNCH();
+  k_dot_finish<<<1, 256, 0, st>>>(W.part, RED_BLOCKS, W.sc, which);
+  DPG_CHECK_LAUNCH();
+}
+
+// theta = 1 / (1.05 lambda) with the smoother and operator of the V-cycle precision C.
+template <class C>
+static double estimate_theta_t(SystemImpl& S, Level& F, cudaStream_t st) {
+  const int64_t n = F.mesh.ndof;
+  Alloc tmp;
+  tmp.budget = (size_t)-1;
+  C* x = tmp.arr<C>((size_t)n);
+  C* y = tmp.arr<C>((size_t)n);
+  C* t = tmp.arr<C>((size_t)n);
+  C* pbuf = tmp.arr<C>((size_t)std::max<int64_t>(F.P.nslots, 1));
+  WS W;
+  W.part = tmp.arr<double2>(RED_BLOCKS);
+  W.sc = tmp.arr<double2>(SC_COUNT);
+  const C* Av = Prec<C>::A(F.A);
+  k_start_vector<C><<<nblk(n), 256, 0, st>>>(x, n, F.P.slot_ptr);
+  DPG_CHECK_LAUNCH();
+  dot_t<C>(W, x, x, n, 1, st);
+  k_scale<C><<<RED_BLOCKS, 256, 0, st>>>(x, n, W.sc, SC_RR);
+  DPG_CHECK_LAUNCH();
+  for (int k = 0; k < 30; ++k) {
+    spmv<C>(F.A, Av, x, nullptr, t, 0, st);
+    smooth<C>(F, t, y, 1.0, 0, pbuf, st);
+    dot_t<C>(W, y, y, n, 1, st);
+    k_scale<C><<<RED_BLOCKS, 256, 0, st>>>(y, n, W.sc, SC_RR);
+    DPG_CHECK_LAUNCH();
+    std::swap(x, y);
+  }
+  spmv<C>(F.A, Av, x, nullptr, t, 0, st);   // M x
+  smooth<C>(F, t, y, 1.0, 0, pbuf, st);     // S M x
+  double2 h[SC_COUNT];
+  dot_t<C>(W, t, y, n, 3, st);               // (M x)^H (S M x)
+  DPG_CUDA(cudaMemcpyAsync(h, W.sc, sizeof(h), cudaMemcpyDeviceToHost, st));
+  DPG_CUDA(cudaStreamSynchronize(st));
+  const double num = h[SC_RHO].x;
+  dot_t<C>(W, x, t, n, 3, st);               // x^H M x
+  DPG_CUDA(cudaMemcpyAsync(h, W.sc, sizeof(h), cudaMemcpyDeviceToHost, st));
+  DPG_CUDA(cudaStreamSynchronize(st));
+  const double den = h[SC_RHO].x;
+  W.part = nullptr;
+  W.sc = nullptr;
+  return 1.0 / (1.05 * (num / den));
 }
 
 void estimate_theta(SystemImpl& S, int l, cudaStream_t st) {
   Level& F = S.levels[l];
-  if (S.op.theta > 0.0) { F.theta = S.op.theta; return; }
-  const int64_t n = F.mesh.ndof;
-  Alloc tmp;
-  tmp.budget = (size_t)-1;
-  double2* x = tmp.arr<double2>((size_t)n);
-  double2* y = tmp.arr<double2>((size_t)n);
-  double2* t = tmp.arr<double2>((size_t)n);
-  double2* pbuf = tmp.arr<double2>((size_t)std::max<int64_t>(F.P.nslots, 1));
-  double2* part = tmp.arr<double2>(RED_BLOCKS);
-  double2* sc = tmp.arr<double2>(SC_COUNT);
-  WS W;
-  W.part = part;
-  W.sc = sc;
-  k_start_vector<<<nblk(n), 256, 0, st>>>(x, n, F.P.slot_ptr);
-  DPG_CHECK_LAUNCH();
-  dot(W, x, x, n, 1, st);
-  k_scale<<<RED_BLOCKS, 256, 0, st>>>(x, n, sc, SC_RR);
-  for (int k = 0; k < 30; ++k) {
-    spmv<double2>(F.A, F.A.v64, x, nullptr, t, 0, st);
-    smooth<double2>(F, t, y, 1.0, 0, pbuf, st);
-    dot(W, y, y, n, 1, st);
-    k_scale<<<RED_BLOCKS, 256, 0, st>>>(y, n, sc, SC_RR);
-    std::swap(x, y);
+  if (S.op.theta > 0.0) {
+    F.theta = S.op.theta;
+    return;
   }
-  spmv<double2>(F.A, F.A.v64, x, nullptr, t, 0, st);   // M x
-  smooth<double2>(F, t, y, 1.0, 0, pbuf, st);          // S M x
-  double2 h[SC_COUNT];
-  dot(W, t, y, n, 3, st);                               // (M x)^H (S M x) -> RHO
-  DPG_CUDA(cudaMemcpyAsync(h, sc, sizeof(h), cudaMemcpyDeviceToHost, st));
-  DPG_CUDA(cudaStreamSynchronize(st));
-  double num = h[SC_RHO].x;
-  dot(W, x, t, n, 3, st);                               // x^H M x
-  DPG_CUDA(cudaMemcpyAsync(h, sc, sizeof(h), cudaMemcpyDeviceToHost, st));
-  DPG_CUDA(cudaStreamSynchronize(st));
-  double den = h[SC_RHO].x;
-  double lam = num / den;
-  F.theta = 1.0 / (1.05 * lam);
-  W.part = nullptr;
-  W.sc = nullptr;
+  // FP64 on both paths (the mixed path's complex64 operators are made after)
+  F.theta = estimate_theta_t<double2>(S, F, st);
 }
 
 // ------------------------------------------------------------ introspection

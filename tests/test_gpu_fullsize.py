@@ -1,0 +1,55 @@
+"""Full-size parity on the 16^3, p = 3, omega = 16 pi workload (the bench configuration).
+
+Reference values come from tests/golden/c2_oracle.json, written by
+tests/golden/make_c2_golden.py from a full oracle run (FP64, same seeds).
+Sampled element matrices are recomputed by the oracle on the spot; the
+solution is compared on 64 sampled trace DOFs; theta per level and the
+iteration count against the oracle's.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+from oracle.element import boundary_faces, condense, dpg_element
+from oracle.mesh import Mesh
+from oracle.problem import GaussianSource
+from paper_2304_01728_gb300 import dpgmg as D
+from paper_2304_01728_gb300 import workloads
+
+pytestmark = pytest.mark.gpu
+GOLD = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "c2_oracle.json")))
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_c2_full_size(precision):
+    w = workloads.config2(precision)
+    pk, ok = w["problem"], w["opts"]
+    with D.Solver(pk, **ok) as s:
+        # sampled condensed element matrices (corner, edge, face, interior, source region)
+        m = Mesh(pk["n"], pk["p"])
+        ld = GaussianSource(pk["src_center"], pk["src_width"])
+        for e in [0, 15, 8 * 16 + 7, 16 * 16 * 8 + 16 * 8 + 8, 4095, 16 * 16 * 9 + 16 * 9 + 9]:
+            bf = boundary_faces(m, e)
+            corner = m.x0 + np.asarray(m.elem_coord(e)) * m.h
+            K, F = dpg_element(m.p, m.h, corner, 1.0, pk["omega"], bf, ld)
+            Kc, Fc = condense(m.p, K, F, bf)
+            G, Fg = D.dpgmg_element_matrix(s.h, s.s, 2, e, Kc.shape[0], with_load=True)
+            assert np.linalg.norm(G - Kc) / np.linalg.norm(Kc) < 1e-11
+            assert np.linalg.norm(Fg - Fc) / max(np.linalg.norm(Fc), 1e-300) < 1e-10
+        # hierarchy: theta per level (FP64 power iteration on both sides)
+        for l, th in enumerate(GOLD["theta"], start=1):
+            assert abs(s.level(l).theta - th) < 1e-8 * th
+        b = D.dpgmg_rhs(s.h, s.s, s.n_trace)
+        assert abs(np.linalg.norm(b) - GOLD["norm_b"]) < 1e-11 * GOLD["norm_b"]
+        x, f, st, code = s.solve()
+    assert code == D.DPGMG_OK
+    assert st.relres <= 1e-8 and st.true_relres <= 1e-8
+    assert abs(st.iters - GOLD["iters"]) <= max(1, round(0.1 * GOLD["iters"]))
+    idx = np.array(GOLD["sample_idx"])
+    xr = np.array([complex(*v) for v in GOLD["sample_x"]])
+    err = np.linalg.norm(x[idx] - xr) / np.linalg.norm(xr)
+    print("sampled solution error vs oracle (%s): %.3e, iterations %d" % (precision, err, st.iters))
+    assert err < (1e-9 if precision == "fp64" else 1e-7), err
+    assert abs(np.linalg.norm(x) - GOLD["norm_x"]) < 1e-7 * GOLD["norm_x"]
