@@ -117,6 +117,7 @@ typedef struct dpgmg_stats {
   double t_pcg_ms;         /* device time from the first CG step to convergence */
   long long bytes_per_iter;/* algorithmic bytes of one CG iteration (matrix entries read once) */
   long long n_dof;         /* finest trace DOFs */
+  long long dev_bytes_peak;/* peak device bytes held by the system */
 } dpgmg_stats;
 
 typedef struct dpgmg_level_desc {
@@ -133,6 +134,7 @@ typedef struct dpgmg_level_desc {
 
 typedef struct dpgmg_handle_s* dpgmg_handle;
 typedef struct dpgmg_system_s* dpgmg_system;
+typedef long long dpgmg_ticket;
 
 /* Create a handle bound to CUDA device `device`.  mem_budget_bytes caps the
  * device memory of all systems of this handle (0 = 90% of free memory).
@@ -168,6 +170,34 @@ int dpgmg_solve(dpgmg_handle h, dpgmg_system sys, void* trace_out, void* field_o
 
 void dpgmg_release(dpgmg_handle h, dpgmg_system sys);
 const char* dpgmg_strerror(int code);
+
+/* ---- serving (continuous batching) ---------------------------------------- */
+
+/* Start the serving loop of a handle with `slots` concurrent solves (1..64);
+ * optional, the first dpgmg_submit starts it with 4 slots.  Each slot owns a
+ * CUDA stream; the serving memory budget is the handle's budget not held by
+ * systems set up with dpgmg_setup at that moment.  Errors: ARG (bad count,
+ * or already started with another count). */
+int dpgmg_serve_start(dpgmg_handle h, int slots);
+
+/* Queue one solve (the same problem and options as dpgmg_setup + dpgmg_solve,
+ * copied during the call) and return its ticket without waiting.  Requests
+ * are admitted first-fit as a slot is free and their footprint estimate
+ * (dpgmg_query_sizes) fits the serving memory not held by running requests,
+ * so requests arriving while others run start as memory frees up and their
+ * work overlaps on the device.  Errors: ARG; NOMEM if the footprint exceeds
+ * the whole serving budget (the request is refused, not queued). */
+int dpgmg_submit(dpgmg_handle h, const dpgmg_problem* pb, const dpgmg_opts* op, dpgmg_ticket* ticket);
+
+/* Collect a finished request: DPGMG_ERR_PENDING while it is queued or running;
+ * otherwise copies the trace (c128[n_trace]) and fields (c128[n_elem*4p^3])
+ * into the host buffers (either may be NULL), fills st and latency_ms
+ * (completion minus submission, host clock) and returns the request's status
+ * (OK, NOT_CONVERGED, NOMEM, NOT_HPD, ...).  A collected ticket is forgotten;
+ * polling it again returns ARG.  dpgmg_destroy stops the loop and drops
+ * requests not yet collected. */
+int dpgmg_poll(dpgmg_handle h, dpgmg_ticket ticket, void* trace_out, void* field_out, dpgmg_stats* st,
+               double* latency_ms);
 const char* dpgmg_last_error(void);
 
 /* ---- introspection (one call per step of the hot path, used by tests) ---- */

@@ -23,10 +23,10 @@ void* Alloc::get(size_t bytes) {
   bytes = (bytes + 255) & ~(size_t)255;
   if (used + bytes > budget) throw Err{DPGMG_ERR_NOMEM, "device-memory budget exceeded"};
   void* p = nullptr;
-  cudaError_t e = cudaMalloc(&p, bytes);
+  cudaError_t e = cudaMallocAsync(&p, bytes, stream);
   if (e != cudaSuccess) {
     cudaGetLastError();
-    throw Err{DPGMG_ERR_NOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(e)};
+    throw Err{DPGMG_ERR_NOMEM, std::string("cudaMallocAsync: ") + cudaGetErrorString(e)};
   }
   ptrs.push_back(p);
   sizes.push_back(bytes);
@@ -38,7 +38,7 @@ void* Alloc::get(size_t bytes) {
 void Alloc::release(void* p) {
   for (size_t i = 0; i < ptrs.size(); ++i)
     if (ptrs[i] == p) {
-      cudaFree(p);
+      cudaFreeAsync(p, stream);
       used -= sizes[i];
       ptrs.erase(ptrs.begin() + i);
       sizes.erase(sizes.begin() + i);
@@ -47,13 +47,13 @@ void Alloc::release(void* p) {
 }
 
 void Alloc::free_all() {
-  for (void* p : ptrs) cudaFree(p);
+  for (void* p : ptrs) cudaFreeAsync(p, stream);
   ptrs.clear();
   sizes.clear();
   used = 0;
 }
 
-static int validate(const dpgmg_problem* pb, const dpgmg_opts* op) {
+int validate_problem(const dpgmg_problem* pb, const dpgmg_opts* op) {
   if (!pb || !op) return DPGMG_ERR_ARG;
   for (int d = 0; d < 3; ++d) {
     if (pb->n[d] < 1 || !(pb->x1[d] > pb->x0[d])) return DPGMG_ERR_ARG;
@@ -79,50 +79,69 @@ static int validate(const dpgmg_problem* pb, const dpgmg_opts* op) {
   return DPGMG_OK;
 }
 
-// Device bytes held by a system (upper-bound estimate used for admission).
-static size_t estimate_bytes(const dpgmg_problem* pb, const dpgmg_opts* op) {
+// Device bytes a system needs (upper bound used for admission): everything
+// resident after setup plus the largest scratch of any setup phase (the
+// phases run one after another and release their scratch).
+size_t estimate_bytes(const dpgmg_problem* pb, const dpgmg_opts* op) {
   const int nn[3] = {pb->n[0], pb->n[1], pb->n[2]};
   auto specs = plan_levels(nn, pb->p, op->n_levels, op->p_min);
   const bool mixed = op->precision == DPGMG_PREC_MIXED;
-  double bytes = 0;
+  const double vsz = mixed ? 8.0 : 16.0;       // V-cycle complex size
+  const double x32 = mixed ? 8.0 : 0.0;        // extra complex64 copies on the mixed path
+  double resident = 0.0, transient = 0.0;
   const int p = pb->p;
-  const int64_t ne = (int64_t)nn[0] * nn[1] * nn[2];
+  const double ne = (double)nn[0] * nn[1] * nn[2];
   const double ntr = n_trace_local(p), nf = 4.0 * p * p * p;
   const double nt = std::pow(p + 2.0, 3) + 3.0 * (p + 2.0) * (p + 1.0) * (p + 1.0);
-  bytes += ne * (ntr * ntr + nf * (ntr + 1) + ntr) * 16.0;                                   // E, Yrec, Fc
-  bytes += std::min<double>(4096.0, (double)ne) * (nt * nt * 8 + nt * (nf + ntr + 1) * 16 + std::pow(nf + ntr + 1, 2) * 16);
-  for (size_t l = 0; l < specs.size(); ++l) {
-    const LevelSpec& s = specs[l];
-    const double nel = (double)s.n[0] * s.n[1] * s.n[2];
-    const double nl = n_trace_local(s.p);
+  const double m1 = nf + ntr + 1.0;
+  resident += ne * (ntr * ntr + nf * (ntr + 1.0) + ntr) * 16.0;     // finest E, Yrec, Fc
+  const double per = nt * nt * 8.0 + nt * m1 * 16.0 + m1 * m1 * 16.0;
+  transient = std::max(transient, (double)element_chunk((int64_t)ne, (size_t)per) * per);
+  double xdofs = 0.0;
+  for (size_t i = 0; i < specs.size(); ++i) {
+    const LevelSpec& s = specs[i];
     MeshL m;
-    double x0[3] = {0, 0, 0}, x1[3] = {1, 1, 1};
-    m.init(s.n, s.p, x0, x1);
-    const double esz = mixed ? 24.0 : 16.0;
-    bytes += nel * nl * nl * 16.0 + nel * nl * 8.0 + m.ndof * 200.0;        // element matrices, maps, vectors
-    if (l + 1 < specs.size()) {
-      bytes += nel * nl * nl * (esz + 4.0 / 3.0);                            // operator values + indices
+    double a0[3] = {0, 0, 0}, a1[3] = {1, 1, 1};
+    m.init(s.n, s.p, a0, a1);
+    const double nel = (double)m.nelem, nl = n_trace_local(s.p), nd = (double)m.ndof;
+    if (i == 0) xdofs = nd;
+    if (i > 0) resident += nel * nl * nl * 16.0;                      // restricted element matrices
+    resident += nel * nl * 8.0 + nd * 4.0 * (16.0 + x32) + nd * 64.0; // maps, work vectors, row indices
+    if (s.kind_below != 0) {
       const int q = s.p;
-      double np_int;
-      int64_t nv;
-      if (s.kind_below == 1) {
-        np_int = 1 + 6 * (q - 1) + 12 * ((q - 1) * (q - 1) + q * q);
-        nv = (int64_t)(s.n[0] + 1) * (s.n[1] + 1) * (s.n[2] + 1);
-      } else {
-        np_int = 1 + 6 * (2 * (q - 1) + 1) + 12 * (4 * (q - 1) * (q - 1) + 4 * (q - 1) + 1 + 4 * q * q);
-        nv = (int64_t)(s.n[0] / 2 + 1) * (s.n[1] / 2 + 1) * (s.n[2] / 2 + 1);
-        const double nS = 6 * (4 * (q - 1) * (q - 1) + 4 * (q - 1) + 1 + 4 * q * q) + 12 * (2 * (q - 1) + 1) + 8;
-        const double nI = 1 + 6 * (q - 1) + 12 * ((q - 1) * (q - 1) + q * q);
-        const double nK = nel / 8.0;
-        bytes += nK * (nI * nS + nI * nI) * esz + std::min(nK, 2048.0) * ((nS + nI) * (nS + nI) + 2 * nS * nS) * 16;
+      const bool hlev = s.kind_below == 2;
+      const double nS = 6.0 * (4.0 * (q - 1) * (q - 1) + 4.0 * (q - 1) + 1.0 + 4.0 * q * q) + 12.0 * (2.0 * (q - 1) + 1.0) + 8.0;
+      const double nI = 1.0 + 6.0 * (q - 1) + 12.0 * ((q - 1.0) * (q - 1.0) + q * q);
+      const double nK = nel / 8.0;
+      const double nnz = hlev ? nK * nS * nS : nel * nl * nl;         // bound on stored entries
+      resident += nnz * (16.0 + x32 + 4.0);                           // values (+complex64) and columns
+      if (i == 0) resident += nnz * (mixed ? 8.0 : 16.0);             // double-float split of the CG operator
+      int nco[3];
+      for (int d = 0; d < 3; ++d) nco[d] = hlev ? s.n[d] / 2 : s.n[d];
+      auto ps = patch_sizes(m, hlev, hlev ? 4 : 2, nco);
+      double nvals = 0.0, nslots = 0.0, nmax = 0.0;
+      for (int64_t v : ps) {
+        nvals += (double)v * v;
+        nslots += (double)v;
+        nmax = std::max(nmax, (double)v);
       }
-      bytes += nv * np_int * np_int * 1.25 * esz + std::min<double>(2e9, nv * np_int * np_int * 16.0);
-    } else {
-      double N0 = (double)m.ndof;
-      if (op->coarsest == DPGMG_COARSEST_CHOLESKY || specs.size() == 1) bytes += N0 * N0 * (16.0 + 2 * esz);
+      resident += nvals * vsz + nslots * (8.0 + 16.0 + x32) + nslots / 32.0 * 8.0;
+      const double one = nmax * nmax * 16.0;
+      const double cap = std::max(std::min(std::min(std::max((double)(1 << 28), one) * 4.0, (double)(2ull << 30)),
+                                           nvals * 16.0), one);
+      transient = std::max(transient, nvals * (16.0 + x32) + cap + nd * 48.0 + nslots * 16.0);
+      if (hlev) {
+        resident += nK * (nI * nS + nI * nI) * (16.0 + x32) + nK * (nS + nI) * 8.0 + nK * nS * (16.0 + x32 + 4.0);
+        const double nlc = n_trace_local(q);
+        transient = std::max(transient, std::min(nK, 2048.0) * ((nS + nI) * (nS + nI) + nS * nlc + nS * nS) * 16.0);
+      }
+    } else if (op->coarsest == DPGMG_COARSEST_CHOLESKY || specs.size() == 1) {
+      resident += nd * (nd + 1.0) * vsz;                              // packed L^-1 and L^-H
+      transient = std::max(transient, nd * nd * (mixed ? 24.0 : 32.0) + nd * 64.0 * 16.0);
     }
   }
-  return (size_t)(bytes * 1.1) + ((size_t)64 << 20);
+  resident += (xdofs + ne * nf) * 16.0;                              // solution outputs
+  return (size_t)((resident + transient) * 1.05) + ((size_t)64 << 20);
 }
 
 static void fill_bytes_per_iter(SystemImpl& S) {
@@ -145,6 +164,46 @@ static void fill_bytes_per_iter(SystemImpl& S) {
   const Level& C0 = S.levels[0];
   if (C0.has_coarse) b += (double)C0.N0 * (C0.N0 + 1) * esz;                     // L^-1 and L^-H (packed)
   S.bytes_per_iter = (int64_t)b;
+}
+
+void setup_system(SystemImpl& S, const dpgmg_problem* pb, const dpgmg_opts* op, size_t budget, cudaStream_t st) {
+  S.pb = *pb;
+  S.op = *op;
+  const int64_t ne = (int64_t)pb->n[0] * pb->n[1] * pb->n[2];
+  S.wavespeed.assign(ne, 1.0);
+  if (pb->wavespeed) std::copy(pb->wavespeed, pb->wavespeed + ne, S.wavespeed.begin());
+  if (pb->source == DPGMG_SRC_MANUFACTURED) {
+    size_t m = pb->mf_order;
+    S.mf_coeffs.assign(pb->mf_coeffs, pb->mf_coeffs + 2 * 4 * m * m * m);
+  }
+  S.pb.wavespeed = nullptr;
+  S.pb.mf_coeffs = nullptr;
+  S.mem.budget = budget;
+  S.mem.stream = st;
+  auto specs = plan_levels(pb->n, pb->p, op->n_levels, op->p_min);
+  S.levels.resize(specs.size());
+  for (size_t i = 0; i < specs.size(); ++i) {
+    Level& L = S.levels[specs.size() - 1 - i];
+    L.mesh.init(specs[i].n, specs[i].p, pb->x0, pb->x1);
+    L.kind = specs[i].kind_below;
+    L.nloc = (int)L.mesh.loc.size();
+  }
+  cudaEvent_t e0, e1;
+  DPG_CUDA(cudaEventCreate(&e0));
+  DPG_CUDA(cudaEventCreate(&e1));
+  DPG_CUDA(cudaEventRecord(e0, st));
+  element_stage(S, st);
+  build_hierarchy(S, st);
+  assemble_rhs(S, st);
+  ensure_workspace(S, st);
+  DPG_CUDA(cudaEventRecord(e1, st));
+  DPG_CUDA(cudaEventSynchronize(e1));
+  float ms = 0.f;
+  DPG_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  S.t_setup_ms = ms;
+  fill_bytes_per_iter(S);
 }
 
 }  // namespace dpgmg
@@ -205,6 +264,12 @@ int dpgmg_create(dpgmg_handle* out, int device, size_t mem_budget_bytes, void* c
       DPG_CUDA(cudaStreamCreateWithFlags(&h->h.stream, cudaStreamNonBlocking));
       h->h.own_stream = true;
     }
+    // keep freed stream-ordered memory in the process's pool between setups
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, device) == cudaSuccess) {
+      uint64_t thr = UINT64_MAX;
+      cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+    }
     size_t fr = 0, tot = 0;
     DPG_CUDA(cudaMemGetInfo(&fr, &tot));
     h->h.budget = mem_budget_bytes ? mem_budget_bytes : (size_t)(0.9 * fr);
@@ -217,6 +282,7 @@ int dpgmg_create(dpgmg_handle* out, int device, size_t mem_budget_bytes, void* c
 
 void dpgmg_destroy(dpgmg_handle h) {
   if (!h) return;
+  server_shutdown(h);
   cudaSetDevice(h->h.device);
   if (h->h.own_stream) cudaStreamDestroy(h->h.stream);
   delete h;
@@ -224,7 +290,7 @@ void dpgmg_destroy(dpgmg_handle h) {
 
 int dpgmg_query_sizes(const dpgmg_problem* pb, const dpgmg_opts* op, long long* n_trace, long long* n_field,
                       size_t* dev_bytes) {
-  int v = validate(pb, op);
+  int v = validate_problem(pb, op);
   if (v) return v;
   MeshL m;
   m.init(pb->n, pb->p, pb->x0, pb->x1);
@@ -237,7 +303,7 @@ int dpgmg_query_sizes(const dpgmg_problem* pb, const dpgmg_opts* op, long long* 
 int dpgmg_setup(dpgmg_handle h, const dpgmg_problem* pb, const dpgmg_opts* op, dpgmg_system* out) {
   if (!h || !out) return DPGMG_ERR_ARG;
   *out = nullptr;
-  int v = validate(pb, op);
+  int v = validate_problem(pb, op);
   if (v) {
     set_last_error("invalid problem or options");
     return v;
@@ -253,54 +319,18 @@ int dpgmg_setup(dpgmg_handle h, const dpgmg_problem* pb, const dpgmg_opts* op, d
   SystemImpl& S = sys->s;
   try {
     DPG_CUDA(cudaSetDevice(h->h.device));
-    cudaStream_t st = h->h.stream;
-    S.pb = *pb;
-    S.op = *op;
-    const int64_t ne = (int64_t)pb->n[0] * pb->n[1] * pb->n[2];
-    S.wavespeed.assign(ne, 1.0);
-    if (pb->wavespeed) std::copy(pb->wavespeed, pb->wavespeed + ne, S.wavespeed.begin());
-    if (pb->source == DPGMG_SRC_MANUFACTURED) {
-      size_t m = pb->mf_order;
-      S.mf_coeffs.assign(pb->mf_coeffs, pb->mf_coeffs + 2 * 4 * m * m * m);
-    }
-    S.pb.wavespeed = nullptr;
-    S.pb.mf_coeffs = nullptr;
-    S.mem.budget = h->h.budget - h->h.used;
-    auto specs = plan_levels(pb->n, pb->p, op->n_levels, op->p_min);
-    S.levels.resize(specs.size());
-    for (size_t i = 0; i < specs.size(); ++i) {
-      Level& L = S.levels[specs.size() - 1 - i];
-      L.mesh.init(specs[i].n, specs[i].p, pb->x0, pb->x1);
-      L.kind = specs[i].kind_below;
-      L.nloc = (int)L.mesh.loc.size();
-    }
-    cudaEvent_t e0, e1;
-    DPG_CUDA(cudaEventCreate(&e0));
-    DPG_CUDA(cudaEventCreate(&e1));
-    DPG_CUDA(cudaEventRecord(e0, st));
-    element_stage(S, st);
-    build_hierarchy(S, st);
-    assemble_rhs(S, st);
-    ensure_workspace(S, st);
-    DPG_CUDA(cudaEventRecord(e1, st));
-    DPG_CUDA(cudaEventSynchronize(e1));
-    float ms = 0.f;
-    DPG_CUDA(cudaEventElapsedTime(&ms, e0, e1));
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
-    S.t_setup_ms = ms;
-    fill_bytes_per_iter(S);
+    setup_system(S, pb, op, h->h.budget - h->h.used, h->h.stream);
     h->h.used += S.mem.used;
     *out = sys;
     return DPGMG_OK;
   } catch (const Err& e) {
-    cudaDeviceSynchronize();
+    cudaStreamSynchronize(h->h.stream);
     profile_clear(S);
     free_workspace(S);
     delete sys;
     return fail(e);
   } catch (const std::exception& e) {
-    cudaDeviceSynchronize();
+    cudaStreamSynchronize(h->h.stream);
     free_workspace(S);
     delete sys;
     return fail(Err{DPGMG_ERR_ARG, e.what()});
@@ -319,6 +349,7 @@ int dpgmg_solve(dpgmg_handle h, dpgmg_system sys, void* trace_out, void* field_o
     const int64_t nfld = S.nelem * S.nf;
     Alloc tmp;
     tmp.budget = (size_t)-1;
+    tmp.stream = s;
     double2* x = (trace_out && out_is_device) ? reinterpret_cast<double2*>(trace_out) : tmp.arr<double2>((size_t)n);
     int status = pcg_solve(S, s, x, st);
     if (field_out) {
@@ -450,6 +481,7 @@ int dpgmg_apply(dpgmg_handle h, dpgmg_system sys, int op, int level, const doubl
     if (op == DPGMG_OP_PROLONG) nin = S.levels[level - 1].mesh.ndof;
     Alloc tmp;
     tmp.budget = (size_t)-1;
+    tmp.stream = s;
     double2* dx = tmp.arr<double2>((size_t)nin);
     double2* dy = tmp.arr<double2>((size_t)nout);
     DPG_CUDA(cudaMemcpyAsync(dx, x, (size_t)nin * sizeof(double2), cudaMemcpyHostToDevice, s));

@@ -329,6 +329,12 @@ static void make_descriptors(int p, std::vector<int4>& tf, std::vector<int4>& ff
                              : make_int4(1, f.d, f.s, f.a + 256 * f.b));
 }
 
+// Elements per batch of the element stage: at most 4096 and at most 8 GiB of scratch.
+int64_t element_chunk(int64_t nel, size_t per_elem) {
+  int64_t c = (int64_t)(((size_t)8 << 30) / per_elem);
+  return std::max<int64_t>(1, std::min<int64_t>(std::min<int64_t>(nel, 4096), c));
+}
+
 static size_t smem_bytes_dense(size_t elt) { return (size_t)(NB * NB + 2 * TL * NB) * elt + 64; }
 
 void element_stage(SystemImpl& S, cudaStream_t st) {
@@ -397,18 +403,18 @@ void element_stage(SystemImpl& S, cudaStream_t st) {
 
   // scratch per element: G (nt^2 doubles), W (nt (m+1)), K ((m+1)^2)
   const size_t per = (size_t)a.nt * a.nt * 8 + (size_t)a.nt * (a.m + 1) * 16 + (size_t)(a.m + 1) * (a.m + 1) * 16;
-  size_t avail = std::max<size_t>(A.budget > A.used ? A.budget - A.used : 0, 0);
-  size_t scratch_cap = std::min<size_t>((size_t)8 << 30, avail / 3);
-  int64_t chunk = std::max<int64_t>(1, std::min<int64_t>(nel, (int64_t)(scratch_cap / per)));
-  chunk = std::min<int64_t>(chunk, 4096);
+  int64_t chunk = element_chunk(nel, per);
   a.G = A.arr<double>((size_t)chunk * a.nt * a.nt);
   a.W = A.arr<double2>((size_t)chunk * a.nt * (a.m + 1));
   a.K = A.arr<double2>((size_t)chunk * (a.m + 1) * (a.m + 1));
 
   const size_t sm_build = (size_t)4 * T.nql * T.nql * T.nql * sizeof(double2) + 64;
+  // Function attributes are process-wide and systems may be set up concurrently
+  // (serving slots), so the limit is the largest any order p <= 5 needs.
+  const size_t sm_build_max = (size_t)4 * 10 * 10 * 10 * sizeof(double2) + 64;
   const size_t sm_real = smem_bytes_dense(8);
   const size_t sm_cplx = smem_bytes_dense(16);
-  DPG_CUDA(cudaFuncSetAttribute(k_elem_build, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_build));
+  DPG_CUDA(cudaFuncSetAttribute(k_elem_build, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_build_max));
   DPG_CUDA(cudaFuncSetAttribute(k_elem_potrf, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_real));
   DPG_CUDA(cudaFuncSetAttribute(k_elem_trsm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_cplx));
   DPG_CUDA(cudaFuncSetAttribute(k_elem_herk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_cplx));
@@ -430,6 +436,9 @@ void element_stage(SystemImpl& S, cudaStream_t st) {
   int info = 0;
   DPG_CUDA(cudaMemcpyAsync(&info, a.info, sizeof(int), cudaMemcpyDeviceToHost, st));
   DPG_CUDA(cudaStreamSynchronize(st));
+  A.release(a.G);
+  A.release(a.W);
+  A.release(a.K);
   if (info) throw Err{DPGMG_ERR_NOT_HPD, "element Gram or field block not positive definite"};
 }
 

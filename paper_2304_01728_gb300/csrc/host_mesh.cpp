@@ -460,6 +460,42 @@ Patches build_patches(const MeshL& m, const std::vector<char>& smask, int H, con
   return P;
 }
 
+std::vector<int64_t> patch_sizes(const MeshL& m, bool macro, int H, const int nco[3]) {
+  std::vector<int64_t> cnt((size_t)(nco[0] + 1) * (nco[1] + 1) * (nco[2] + 1), 0);
+  for (int64_t E = 0; E < m.nent; ++E) {
+    int64_t st;
+    int nd;
+    m.ent_range(E, &st, &nd);
+    if (nd == 0) continue;
+    int ctr[3];
+    m.ent_center(E, ctr);
+    if (macro) {   // entity on the skeleton of the coarse mesh (a flat coordinate on a coarse plane)
+      bool on = false;
+      for (int d = 0; d < 3; ++d)
+        if (!(ctr[d] & 1) && ctr[d] % 4 == 0) on = true;
+      if (!on) continue;
+    }
+    int W[3][2], c[3];
+    for (int d = 0; d < 3; ++d) {
+      int top = H * nco[d];
+      if (ctr[d] % H == 0) {
+        if (ctr[d] == 0) { W[d][0] = 0; W[d][1] = 1; c[d] = 2; }
+        else if (ctr[d] == top) { W[d][0] = nco[d] - 1; W[d][1] = nco[d]; c[d] = 2; }
+        else { W[d][0] = ctr[d] / H; c[d] = 1; }
+      } else {
+        W[d][0] = ctr[d] / H;
+        W[d][1] = ctr[d] / H + 1;
+        c[d] = 2;
+      }
+    }
+    for (int a = 0; a < c[0]; ++a)
+      for (int b = 0; b < c[1]; ++b)
+        for (int q = 0; q < c[2]; ++q)
+          cnt[W[0][a] + (int64_t)(nco[0] + 1) * (W[1][b] + (int64_t)(nco[1] + 1) * W[2][q])] += nd;
+  }
+  return cnt;
+}
+
 // ----------------------------------------------------------- transitions
 void p_selection(int p, std::vector<int32_t>& sel) {
   auto fine = local_trace_functions(p);

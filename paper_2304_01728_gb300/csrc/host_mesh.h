@@ -93,6 +93,9 @@ struct Patches {
   std::vector<int32_t> slots;
 };
 Patches build_patches(const MeshL& m, const std::vector<char>& smask, int H, const int nco[3]);
+// Patch sizes only (same rule), for memory estimates: n_j per coarse vertex.
+// macro = true selects the h-level smoothing space (fine DOFs on the coarse skeleton).
+std::vector<int64_t> patch_sizes(const MeshL& m, bool macro, int H, const int nco[3]);
 
 // Macro-grid structure of one h-transition (fine level m, coarse level mc).
 struct MacroHost {

@@ -32,8 +32,11 @@ void count_launch();
   } while (0)
 
 // Device allocation tracked against the handle's budget.
+// Stream-ordered (cudaMallocAsync / cudaFreeAsync on `stream`), so freeing
+// one system never synchronises work of other streams.
 struct Alloc {
   size_t budget = 0, used = 0, peak = 0;
+  cudaStream_t stream = nullptr;
   std::vector<void*> ptrs;
   std::vector<size_t> sizes;
   void* get(size_t bytes);
@@ -109,6 +112,7 @@ struct Level {
 };
 
 struct Workspace;   // V-cycle work vectors (per precision)
+struct Server;      // serving loop (server.cu)
 
 struct SystemImpl {
   dpgmg_problem pb;
@@ -140,6 +144,7 @@ struct HandleImpl {
 
 // ----------------------------------------------------------- stage entry points
 // element.cu
+int64_t element_chunk(int64_t nel, size_t per_elem);
 void element_stage(SystemImpl& S, cudaStream_t st);
 void recover_fields(SystemImpl& S, const double2* x, double2* fields, cudaStream_t st);
 // level.cu
@@ -160,6 +165,10 @@ void free_workspace(SystemImpl& S);
 void spmv64(const ECSRDev& A, const double2* x, double2* y, cudaStream_t st);
 void estimate_theta(SystemImpl& S, int level, cudaStream_t st);
 void profile_read(SystemImpl& S, double* ms, long long* launches, long long* bytes);
+// api.cu: validation, footprint estimate and the whole setup of one system
+int validate_problem(const dpgmg_problem* pb, const dpgmg_opts* op);
+size_t estimate_bytes(const dpgmg_problem* pb, const dpgmg_opts* op);
+void setup_system(SystemImpl& S, const dpgmg_problem* pb, const dpgmg_opts* op, size_t budget, cudaStream_t st);
 void profile_clear(SystemImpl& S);
 void smooth_apply64(const Level& L, const double2* r, double2* y, double theta, double2* scratch,
                     cudaStream_t st);
@@ -169,7 +178,11 @@ void smooth_apply64(const Level& L, const double2* r, double2* y, double theta, 
 struct dpgmg_handle_s {
   dpgmg::HandleImpl h;
   std::mutex mu;
+  dpgmg::Server* server = nullptr;
 };
+namespace dpgmg {
+void server_shutdown(dpgmg_handle h);
+}
 struct dpgmg_system_s {
   dpgmg::SystemImpl s;
 };

@@ -251,7 +251,7 @@ static void invert_patches(Alloc& A, PatchDev& D, const Patches& P, C* vals, int
   DPG_CUDA(cudaFuncSetAttribute(k_patch_invert<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
   const size_t one = (size_t)D.max_n * D.max_n;
   size_t cap = std::min<size_t>(std::max<size_t>(((size_t)1 << 28) / sizeof(C), one) * 4, ((size_t)2 << 30) / sizeof(C));
-  cap = std::max(cap, one);
+  cap = std::max(std::min<size_t>(cap, (size_t)D.nvals), one);
   C* scratch = A.arr<C>(cap);
   int64_t* soff = A.arr<int64_t>((size_t)D.np + 1);
   std::vector<int64_t> offs;
@@ -381,6 +381,10 @@ void build_hierarchy(SystemImpl& S, cudaStream_t st) {
         DPG_CHECK_LAUNCH();
         ecsr_add_elements(F.A, MK, F.S_glob + K0 * F.nS, nb, F.nS, st);
       }
+      DPG_CUDA(cudaStreamSynchronize(st));
+      A.release(AK);
+      A.release(T1);
+      A.release(MK);
       smask.assign(M.smask.begin(), M.smask.end());
       H = 4;
     }

@@ -503,7 +503,7 @@ struct WS {
   std::vector<LevelWS<float2>> w32;
   double2 *x = nullptr, *r = nullptr, *p = nullptr, *q = nullptr, *z = nullptr, *part = nullptr, *sc = nullptr;
   float2 *xh = nullptr, *xl = nullptr;     // double-float split of the CG operand
-  double2* sc_host = nullptr;    // pinned
+  double2 sc_host[SC_COUNT];     // scalar read-back (a few bytes per CG step)
   int* err = nullptr;
   ECSRDev Acg;                   // the CG operator (finest A_L, FP64)
   bool acg_owned = false;
@@ -544,7 +544,6 @@ void ensure_workspace(SystemImpl& S, cudaStream_t st) {
   W->xh = S.mem.arr<float2>((size_t)n);
   W->xl = S.mem.arr<float2>((size_t)n);
   W->sc = S.mem.arr<double2>(SC_COUNT);
-  DPG_CUDA(cudaMallocHost(&W->sc_host, SC_COUNT * sizeof(double2)));
   W->err = S.mem.arr<int>(1);
   DPG_CUDA(cudaMemsetAsync(W->err, 0, sizeof(int), st));
   alloc_level_ws<double2>(*W, S);
@@ -555,7 +554,6 @@ void ensure_workspace(SystemImpl& S, cudaStream_t st) {
 void free_workspace(SystemImpl& S) {
   if (!S.ws) return;
   WS* W = reinterpret_cast<WS*>(S.ws);
-  if (W->sc_host) cudaFreeHost(W->sc_host);
   delete W;
   S.ws = nullptr;
 }
@@ -791,6 +789,7 @@ int pcg_solve(SystemImpl& S, cudaStream_t st, double2* xout, dpgmg_stats* stats)
     stats->t_setup_ms = S.t_setup_ms;
     stats->bytes_per_iter = S.bytes_per_iter;
     stats->n_dof = n;
+    stats->dev_bytes_peak = (long long)S.mem.peak;
   }
   return status;
 }
@@ -859,6 +858,7 @@ static double estimate_theta_t(SystemImpl& S, Level& F, cudaStream_t st) {
   const int64_t n = F.mesh.ndof;
   Alloc tmp;
   tmp.budget = (size_t)-1;
+  tmp.stream = st;
   C* x = tmp.arr<C>((size_t)n);
   C* y = tmp.arr<C>((size_t)n);
   C* t = tmp.arr<C>((size_t)n);
@@ -952,6 +952,7 @@ void apply_op(SystemImpl& S, int op, int l, const double2* x, double2* y, cudaSt
     if (op == DPGMG_OP_PROLONG) nin = S.levels[l - 1].mesh.ndof;
     Alloc tmp;
     tmp.budget = (size_t)-1;
+    tmp.stream = st;
     float2* xi = tmp.arr<float2>((size_t)nin);
     float2* yo = tmp.arr<float2>((size_t)nout);
     k_narrow<<<nblk(nin), 256, 0, st>>>(x, xi, nin);

@@ -48,7 +48,8 @@ class dpgmg_opts(ctypes.Structure):
 class dpgmg_stats(ctypes.Structure):
     _fields_ = [("iters", ctypes.c_int), ("relres", ctypes.c_double), ("true_relres", ctypes.c_double),
                 ("t_setup_ms", ctypes.c_double), ("t_pcg_ms", ctypes.c_double),
-                ("bytes_per_iter", ctypes.c_longlong), ("n_dof", ctypes.c_longlong)]
+                ("bytes_per_iter", ctypes.c_longlong), ("n_dof", ctypes.c_longlong),
+                ("dev_bytes_peak", ctypes.c_longlong)]
 
 
 class dpgmg_level_desc(ctypes.Structure):
@@ -62,7 +63,7 @@ _lib = None
 EXPORTS = ["dpgmg_create", "dpgmg_destroy", "dpgmg_query_sizes", "dpgmg_default_opts", "dpgmg_setup",
            "dpgmg_solve", "dpgmg_release", "dpgmg_strerror", "dpgmg_last_error", "dpgmg_level_info",
            "dpgmg_element_matrix", "dpgmg_rhs", "dpgmg_apply", "dpgmg_launch_count", "dpgmg_profile",
-           "dpgmg_profile_read", "dpgmg_smooth_noalloc"]
+           "dpgmg_profile_read", "dpgmg_smooth_noalloc", "dpgmg_serve_start", "dpgmg_submit", "dpgmg_poll"]
 PROF_OFF, PROF_SMOOTH_FINE, PROF_SPMV_FINE, PROF_SPMV_CG = 0, 1, 2, 3
 
 
@@ -95,6 +96,12 @@ def lib():
     L.dpgmg_element_matrix.argtypes = [vp, vp, i, ll, dptr, dptr]
     L.dpgmg_rhs.argtypes = [vp, vp, dptr]
     L.dpgmg_apply.argtypes = [vp, vp, i, i, dptr, dptr]
+    L.dpgmg_serve_start.argtypes = [vp, i]
+    L.dpgmg_serve_start.restype = i
+    L.dpgmg_submit.argtypes = [vp, ctypes.POINTER(dpgmg_problem), ctypes.POINTER(dpgmg_opts), ctypes.POINTER(ll)]
+    L.dpgmg_submit.restype = i
+    L.dpgmg_poll.argtypes = [vp, ll, vp, vp, ctypes.POINTER(dpgmg_stats), ctypes.POINTER(d)]
+    L.dpgmg_poll.restype = i
     L.dpgmg_smooth_noalloc.argtypes = [vp, vp, i, vp, vp]
     L.dpgmg_smooth_noalloc.restype = i
     L.dpgmg_launch_count.argtypes = []
@@ -220,6 +227,27 @@ def dpgmg_apply(h, s, op, level, x, nout):
     y = np.zeros(nout, dtype=np.complex128)
     _check(lib().dpgmg_apply(h, s, int(op), int(level), _dptr(x), _dptr(y)), "dpgmg_apply")
     return y
+
+
+def dpgmg_serve_start(h, slots):
+    _check(lib().dpgmg_serve_start(h, int(slots)), "dpgmg_serve_start")
+
+
+def dpgmg_submit(h, pb, op):
+    """Queue a solve; returns the ticket (raises DpgmgError with NOMEM when refused)."""
+    t = ctypes.c_longlong()
+    _check(lib().dpgmg_submit(h, ctypes.byref(pb), ctypes.byref(op), ctypes.byref(t)), "dpgmg_submit")
+    return t.value
+
+
+def dpgmg_poll(h, ticket, trace_out=None, field_out=None):
+    """(status, stats, latency_ms); status DPGMG_ERR_PENDING while not finished."""
+    st = dpgmg_stats()
+    lat = ctypes.c_double()
+    tp = trace_out.ctypes.data if isinstance(trace_out, np.ndarray) else trace_out
+    fp = field_out.ctypes.data if isinstance(field_out, np.ndarray) else field_out
+    code = lib().dpgmg_poll(h, ctypes.c_longlong(ticket), tp, fp, ctypes.byref(st), ctypes.byref(lat))
+    return code, st, lat.value
 
 
 def dpgmg_launch_count():
