@@ -185,6 +185,17 @@ class Clocks:
                 "samples": len(sm)}
 
 
+# ------------------------------------------------------------------ ranks
+def reduce_ranks(dist, dof_iters, pcg_ms, total_ms, device):
+    """Replicas only: work adds up over ranks, time is the slowest rank's."""
+    import torch
+    s = torch.tensor([dof_iters], dtype=torch.float64, device=device)
+    m = torch.tensor([pcg_ms, total_ms], dtype=torch.float64, device=device)
+    dist.all_reduce(s, op=dist.ReduceOp.SUM)
+    dist.all_reduce(m, op=dist.ReduceOp.MAX)
+    return float(s[0]), float(m[0]), float(m[1])
+
+
 # ------------------------------------------------------------------ gb300
 def peaks():
     try:
@@ -275,11 +286,7 @@ def run_gb300(args, rank, world, local_rank):
     dof_iters = float(sum(n_dof * s[0] for s in stats))
     pcg_ms = float(sum(s[1] for s in stats))
     if dist:
-        t = torch.tensor([dof_iters, pcg_ms, total_ms], dtype=torch.float64, device="cuda")
-        tmax = t.clone()
-        dist.all_reduce(t, op=dist.ReduceOp.SUM)
-        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
-        dof_iters, pcg_ms, total_ms = float(t[0]), float(tmax[1]), float(tmax[2])
+        dof_iters, pcg_ms, total_ms = reduce_ranks(dist, dof_iters, pcg_ms, total_ms, "cuda")
     value = dof_iters / (pcg_ms / 1e3)
 
     # ---- end to end through the public API with host buffers

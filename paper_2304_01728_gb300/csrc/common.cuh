@@ -351,4 +351,110 @@ __device__ void cta_gemm(bool transA, int m, int n, int k, typename Ops<T>::R al
   __syncthreads();
 }
 
+// X = L^-1 in place of X = I (L lower triangular, n x n).  Blocks of X above
+// the diagonal stay zero and are skipped: n^3/6 multiply-adds.
+// smem: as cta_trsm_lower<T, T>.
+template <class T>
+__device__ void cta_trinv_lower(const T* L, int n, int ldl, T* X, int ldx, char* smem) {
+  using O = Ops<T>;
+  using R = typename O::R;
+  T* D = reinterpret_cast<T*>(smem);
+  T* Lt = D + NB * NB;
+  T* Xt = Lt + TL * NB;
+  const int tid = threadIdx.x;
+  for (int k0 = 0; k0 < n; k0 += NB) {
+    const int kb = min(NB, n - k0);
+    const int k1 = k0 + kb;
+    for (int e = tid; e < kb * kb; e += blockDim.x) {
+      int i = e / kb, j = e % kb;
+      D[i * NB + j] = (j <= i) ? L[(size_t)(k0 + i) * ldl + k0 + j] : O::zero();
+    }
+    __syncthreads();
+    for (int c = tid; c < k1; c += blockDim.x) {
+      T x[NB];
+      for (int r = 0; r < kb; ++r) {
+        T v = X[(size_t)(k0 + r) * ldx + c];
+        for (int t = 0; t < r; ++t) v = O::fnma(D[r * NB + t], x[t], v);
+        x[r] = O::scale(v, R(1) / O::re(D[r * NB + r]));
+        X[(size_t)(k0 + r) * ldx + c] = x[r];
+      }
+    }
+    __syncthreads();
+    for (int i0 = k1; i0 < n; i0 += TL) {
+      for (int e = tid; e < TL * NB; e += blockDim.x) {
+        int r = e / NB, t = e % NB;
+        Lt[e] = (i0 + r < n && t < kb) ? L[(size_t)(i0 + r) * ldl + k0 + t] : O::zero();
+      }
+      for (int c0 = 0; c0 < k1; c0 += TL) {
+        for (int e = tid; e < NB * TL; e += blockDim.x) {
+          int t = e / TL, c = e % TL;
+          Xt[e] = (t < kb && c0 + c < k1) ? X[(size_t)(k0 + t) * ldx + c0 + c] : O::zero();
+        }
+        __syncthreads();
+        for (int e = tid; e < TL * TL; e += blockDim.x) {
+          int r = e / TL, c = e % TL;
+          int i = i0 + r, cc = c0 + c;
+          if (i < n && cc < k1) {
+            T acc = O::zero();
+            for (int t = 0; t < kb; ++t) acc = O::fma(Lt[r * NB + t], Xt[t * TL + c], acc);
+            size_t o = (size_t)i * ldx + cc;
+            X[o] = O::sub(X[o], acc);
+          }
+        }
+        __syncthreads();
+      }
+    }
+  }
+  __syncthreads();
+}
+
+// M = X^H X for lower-triangular X (n x n): each lower tile sums only over
+// rows k >= its first row (X[k][i] = 0 for k < i); the strictly upper tiles
+// are written as the conjugate mirror.  n^3/6 multiply-adds.
+// smem: 2*TL*NB elements of T.
+template <class T>
+__device__ void cta_herk_lower_tri(const T* X, int n, int ldx, T* M, int ldm, T* smem) {
+  using O = Ops<T>;
+  T* At = smem;
+  T* Bt = smem + TL * NB;
+  const int tid = threadIdx.x;
+  constexpr int PER = TL * TL / CTA_THREADS;
+  for (int i0 = 0; i0 < n; i0 += TL) {
+    for (int j0 = 0; j0 <= i0; j0 += TL) {
+      T acc[PER];
+      for (int q = 0; q < PER; ++q) acc[q] = O::zero();
+      for (int k0 = i0; k0 < n; k0 += NB) {
+        for (int e = tid; e < TL * NB; e += blockDim.x) {
+          int r = e / NB, t = e % NB;
+          At[e] = (i0 + r < n && k0 + t < n) ? O::conj(X[(size_t)(k0 + t) * ldx + i0 + r]) : O::zero();
+        }
+        for (int e = tid; e < NB * TL; e += blockDim.x) {
+          int t = e / TL, c = e % TL;
+          Bt[e] = (k0 + t < n && j0 + c < n) ? X[(size_t)(k0 + t) * ldx + j0 + c] : O::zero();
+        }
+        __syncthreads();
+        for (int q = 0; q < PER; ++q) {
+          int e = tid + q * CTA_THREADS;
+          int r = e / TL, c = e % TL;
+          T a = acc[q];
+#pragma unroll 8
+          for (int t = 0; t < NB; ++t) a = O::fma(At[r * NB + t], Bt[t * TL + c], a);
+          acc[q] = a;
+        }
+        __syncthreads();
+      }
+      for (int q = 0; q < PER; ++q) {
+        int e = tid + q * CTA_THREADS;
+        int r = e / TL, c = e % TL;
+        int i = i0 + r, j = j0 + c;
+        if (i < n && j < n) {
+          M[(size_t)i * ldm + j] = acc[q];
+          if (j0 < i0) M[(size_t)j * ldm + i] = O::conj(acc[q]);
+        }
+      }
+    }
+  }
+  __syncthreads();
+}
+
 }  // namespace dpgmg

@@ -8,6 +8,14 @@
 //                    K_c = K_tt - K_tf K_ff^-1 K_ft, F_c = F_t - K_tf K_ff^-1 F_f
 // One CTA per element; elements are processed in chunks that bound the
 // scratch memory.  All arithmetic is FP64.
+//
+// Real path.  Scaling the trial functions p and p-hat by i (u, u-hat by 1)
+// on top of the test scaling v -> i v makes B' and the load real on every
+// element without impedance boundary faces when the source is real (the
+// impedance term <p-hat, Z^-1 q> is the only complex entry).  Such elements
+// run TRSM, K = W^T W and the condensation in real arithmetic (a quarter of
+// the complex flops); the unit phases are put back on the outputs:
+// K_c[i][j] = beta_i conj(beta_j) K'_c[i][j], F_c[i] = beta_i F'_c[i].
 #include <algorithm>
 #include <cmath>
 
@@ -31,10 +39,11 @@ struct ElemArgs {
   const int4 *tf, *ff, *tr;
   Tab1D tab;
   const double *xq, *wq, *Lq;  // load rule and L_a at its points ([n1][nql])
+  const int64_t* elist;    // element ids of the batch list
   int64_t e0;
   double* G;
-  double2* W;
-  double2* K;
+  void* W;                 // [chunk][nt][m+1] of the path's scalar type
+  void* K;                 // [chunk][m+1][m+1]
   double2* Eout;
   double2* Fc;
   double2* Yrec;
@@ -142,10 +151,17 @@ __device__ __forceinline__ void elem_geom(const ElemArgs& a, int64_t e, int ec[3
   }
 }
 
+// scalar of the path from a complex (test-scaled) entry; rot = the trial
+// function carries the phase i
+template <class T> __device__ __forceinline__ T to_path(double2 v, bool rot);
+template <> __device__ __forceinline__ double2 to_path<double2>(double2 v, bool) { return v; }
+template <> __device__ __forceinline__ double to_path<double>(double2 v, bool rot) { return rot ? -v.y : v.x; }
+
+template <class T>
 __global__ void __launch_bounds__(CTA_THREADS) k_elem_build(ElemArgs a) {
   extern __shared__ double2 sh2[];
   const int64_t le = blockIdx.x;
-  const int64_t e = a.e0 + le;
+  const int64_t e = a.elist[a.e0 + le];
   int ec[3], bmask;
   double corner[3];
   elem_geom(a, e, ec, corner, bmask);
@@ -153,7 +169,7 @@ __global__ void __launch_bounds__(CTA_THREADS) k_elem_build(ElemArgs a) {
   const double beta = a.omega / (c * c);
   const int nt = a.nt, m = a.m, ldw = m + 1;
   double* G = a.G + le * (size_t)nt * nt;
-  double2* W = a.W + le * (size_t)nt * ldw;
+  T* W = reinterpret_cast<T*>(a.W) + le * (size_t)nt * ldw;
   for (int64_t q = threadIdx.x; q < (int64_t)nt * nt; q += blockDim.x) {
     int i = (int)(q / nt), j = (int)(q % nt);
     G[q] = (j <= i) ? gram_entry(a.tab, a.tf[i], a.tf[j], a.h, beta, a.omega) : 0.0;
@@ -162,7 +178,8 @@ __global__ void __launch_bounds__(CTA_THREADS) k_elem_build(ElemArgs a) {
     int i = (int)(q / m), j = (int)(q % m);
     double2 v = (j < a.nf) ? bfield_entry(a.tab, a.tf[i], a.ff[j], a.h, beta, a.omega)
                            : btrace_entry(a.tab, a.tf[i], a.tr[j - a.nf], a.h, 1.0 / c, bmask);
-    W[(size_t)i * ldw + j] = v;
+    const bool rot = (j < a.nf) ? a.ff[j].x == 0 : a.tr[j - a.nf].x == 0;
+    W[(size_t)i * ldw + j] = to_path<T>(v, rot);
   }
   // ---- load l' (v rows scaled by -i)
   const int nq = a.nql, nq3 = nq * nq * nq;
@@ -191,7 +208,7 @@ __global__ void __launch_bounds__(CTA_THREADS) k_elem_build(ElemArgs a) {
       acc.y += src[q].y * bv;
     }
     if (t.x != 3) acc = make_double2(acc.y, -acc.x);
-    W[(size_t)i * ldw + m] = acc;
+    W[(size_t)i * ldw + m] = to_path<T>(acc, false);
   }
   __syncthreads();
   // boundary faces: <u0, q>
@@ -225,9 +242,10 @@ __global__ void __launch_bounds__(CTA_THREADS) k_elem_build(ElemArgs a) {
             acc.x += fv[q].x * bv;
             acc.y += fv[q].y * bv;
           }
-          double2& o = W[(size_t)i * ldw + m];
-          o.x += acc.x;
-          o.y += acc.y;
+          // boundary loads only occur on the complex path
+          double2* o = reinterpret_cast<double2*>(&W[(size_t)i * ldw + m]);
+          o->x += acc.x;
+          o->y += acc.y;
         }
         __syncthreads();
       }
@@ -243,45 +261,60 @@ __global__ void __launch_bounds__(CTA_THREADS) k_elem_potrf(ElemArgs a) {
   if (threadIdx.x == 0 && info) atomicOr(a.info, 1);
 }
 
+template <class T>
 __global__ void __launch_bounds__(CTA_THREADS) k_elem_trsm(ElemArgs a) {
   extern __shared__ char shc[];
   const int64_t le = blockIdx.x;
   const double* G = a.G + le * (size_t)a.nt * a.nt;
-  double2* W = a.W + le * (size_t)a.nt * (a.m + 1);
-  cta_trsm_lower<double, double2>(G, a.nt, a.nt, W, a.m + 1, a.m + 1, shc);
+  T* W = reinterpret_cast<T*>(a.W) + le * (size_t)a.nt * (a.m + 1);
+  cta_trsm_lower<double, T>(G, a.nt, a.nt, W, a.m + 1, a.m + 1, shc);
 }
 
+template <class T>
 __global__ void __launch_bounds__(CTA_THREADS) k_elem_herk(ElemArgs a) {
-  extern __shared__ double2 sh2[];
+  extern __shared__ unsigned char shraw[];
   const int64_t le = blockIdx.x;
   const int ld = a.m + 1;
-  const double2* W = a.W + le * (size_t)a.nt * ld;
-  double2* K = a.K + le * (size_t)ld * ld;
-  cta_gemm<double2>(true, ld, ld, a.nt, 1.0, W, ld, W, ld, 0.0, K, ld, sh2);
+  const T* W = reinterpret_cast<const T*>(a.W) + le * (size_t)a.nt * ld;
+  T* K = reinterpret_cast<T*>(a.K) + le * (size_t)ld * ld;
+  cta_gemm<T>(true, ld, ld, a.nt, 1.0, W, ld, W, ld, 0.0, K, ld, reinterpret_cast<T*>(shraw));
 }
 
+// complex output of the path's value; ph = 0: x1, 1: x i, 2: x (-i)
+template <class T> __device__ __forceinline__ double2 phased(T v, int ph);
+template <> __device__ __forceinline__ double2 phased<double2>(double2 v, int) { return v; }
+template <> __device__ __forceinline__ double2 phased<double>(double v, int ph) {
+  return ph == 0 ? make_double2(v, 0.0) : (ph == 1 ? make_double2(0.0, v) : make_double2(0.0, -v));
+}
+__device__ __forceinline__ int phase_of(bool a_i, bool b_i) { return (a_i && !b_i) ? 1 : ((!a_i && b_i) ? 2 : 0); }
+
+template <class T>
 __global__ void __launch_bounds__(CTA_THREADS) k_elem_condense(ElemArgs a) {
-  extern __shared__ double2 sh2[];
+  extern __shared__ unsigned char shraw[];
+  T* sh = reinterpret_cast<T*>(shraw);
   const int64_t le = blockIdx.x;
-  const int64_t e = a.e0 + le;
+  const int64_t e = a.elist[a.e0 + le];
   const int ld = a.m + 1, nf = a.nf, ntr = a.ntr;
-  double2* K = a.K + le * (size_t)ld * ld;
-  int info = cta_potrf<double2>(K, nf, ld, sh2);
+  T* K = reinterpret_cast<T*>(a.K) + le * (size_t)ld * ld;
+  int info = cta_potrf<T>(K, nf, ld, sh);
   if (threadIdx.x == 0 && info) atomicOr(a.info, 2);
-  cta_trsm_lower<double2, double2>(K, nf, ld, K + nf, ntr + 1, ld, reinterpret_cast<char*>(sh2));
-  cta_trsm_lower_h<double2>(K, nf, ld, K + nf, ntr + 1, ld, reinterpret_cast<char*>(sh2));
-  cta_gemm<double2>(false, ntr, ntr + 1, nf, -1.0, K + (size_t)nf * ld, ld, K + nf, ld, 1.0,
-                    K + (size_t)nf * ld + nf, ld, sh2);
+  cta_trsm_lower<T, T>(K, nf, ld, K + nf, ntr + 1, ld, reinterpret_cast<char*>(sh));
+  cta_trsm_lower_h<T>(K, nf, ld, K + nf, ntr + 1, ld, reinterpret_cast<char*>(sh));
+  cta_gemm<T>(false, ntr, ntr + 1, nf, -1.0, K + (size_t)nf * ld, ld, K + nf, ld, 1.0, K + (size_t)nf * ld + nf, ld,
+              sh);
   double2* E = a.Eout + e * (size_t)ntr * ntr;
   for (int q = threadIdx.x; q < ntr * ntr; q += blockDim.x) {
     int i = q / ntr, j = q % ntr;
-    E[q] = K[(size_t)(nf + i) * ld + nf + j];
+    E[q] = phased<T>(K[(size_t)(nf + i) * ld + nf + j], phase_of(a.tr[i].x == 0, a.tr[j].x == 0));
   }
-  for (int i = threadIdx.x; i < ntr; i += blockDim.x) a.Fc[e * ntr + i] = K[(size_t)(nf + i) * ld + a.m];
+  for (int i = threadIdx.x; i < ntr; i += blockDim.x)
+    a.Fc[e * ntr + i] = phased<T>(K[(size_t)(nf + i) * ld + a.m], a.tr[i].x == 0 ? 1 : 0);
   double2* Y = a.Yrec + e * (size_t)nf * (ntr + 1);
   for (int q = threadIdx.x; q < nf * (ntr + 1); q += blockDim.x) {
     int i = q / (ntr + 1), j = q % (ntr + 1);
-    Y[q] = K[(size_t)i * ld + nf + j];
+    const bool fi = a.ff[i].x == 0;
+    const int ph = (j < ntr) ? phase_of(fi, a.tr[j].x == 0) : (fi ? 1 : 0);
+    Y[q] = phased<T>(K[(size_t)i * ld + nf + j], ph);
   }
 }
 
@@ -414,31 +447,59 @@ void element_stage(SystemImpl& S, cudaStream_t st) {
   const size_t sm_build_max = (size_t)4 * 10 * 10 * 10 * sizeof(double2) + 64;
   const size_t sm_real = smem_bytes_dense(8);
   const size_t sm_cplx = smem_bytes_dense(16);
-  DPG_CUDA(cudaFuncSetAttribute(k_elem_build, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_build_max));
+  DPG_CUDA(cudaFuncSetAttribute(k_elem_build<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_build_max));
+  DPG_CUDA(cudaFuncSetAttribute(k_elem_build<double2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_build_max));
   DPG_CUDA(cudaFuncSetAttribute(k_elem_potrf, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_real));
-  DPG_CUDA(cudaFuncSetAttribute(k_elem_trsm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_cplx));
-  DPG_CUDA(cudaFuncSetAttribute(k_elem_herk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_cplx));
-  DPG_CUDA(cudaFuncSetAttribute(k_elem_condense, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_cplx));
-  for (int64_t e0 = 0; e0 < nel; e0 += chunk) {
-    a.e0 = e0;
-    const int nb = (int)std::min<int64_t>(chunk, nel - e0);
-    k_elem_build<<<nb, CTA_THREADS, sm_build, st>>>(a);
-    DPG_CHECK_LAUNCH();
-    k_elem_potrf<<<nb, CTA_THREADS, sm_real, st>>>(a);
-    DPG_CHECK_LAUNCH();
-    k_elem_trsm<<<nb, CTA_THREADS, sm_cplx, st>>>(a);
-    DPG_CHECK_LAUNCH();
-    k_elem_herk<<<nb, CTA_THREADS, sm_cplx, st>>>(a);
-    DPG_CHECK_LAUNCH();
-    k_elem_condense<<<nb, CTA_THREADS, sm_cplx, st>>>(a);
-    DPG_CHECK_LAUNCH();
+  DPG_CUDA(cudaFuncSetAttribute(k_elem_trsm<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_cplx));
+  DPG_CUDA(cudaFuncSetAttribute(k_elem_trsm<double2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_cplx));
+  DPG_CUDA(cudaFuncSetAttribute(k_elem_herk<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_cplx));
+  DPG_CUDA(cudaFuncSetAttribute(k_elem_herk<double2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_cplx));
+  DPG_CUDA(cudaFuncSetAttribute(k_elem_condense<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_cplx));
+  DPG_CUDA(cudaFuncSetAttribute(k_elem_condense<double2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_cplx));
+  // element lists: real path (no impedance face, real source) and complex path
+  std::vector<int64_t> lreal, lcplx;
+  const bool real_src = S.pb.source != DPGMG_SRC_MANUFACTURED;
+  for (int64_t e = 0; e < nel; ++e) {
+    int ec[3];
+    m.elem_coord(e, ec);
+    bool interior = true;
+    for (int d = 0; d < 3; ++d)
+      if (ec[d] == 0 || ec[d] == m.n[d] - 1) interior = false;
+    (interior && real_src ? lreal : lcplx).push_back(e);
   }
+  int64_t* dreal = upload(A, lreal, st);
+  int64_t* dcplx = upload(A, lcplx, st);
+  auto run_list = [&](const int64_t* dl, int64_t cnt, bool real) {
+    a.elist = dl;
+    for (int64_t e0 = 0; e0 < cnt; e0 += chunk) {
+      a.e0 = e0;
+      const int nb = (int)std::min<int64_t>(chunk, cnt - e0);
+      if (real) k_elem_build<double><<<nb, CTA_THREADS, sm_build, st>>>(a);
+      else k_elem_build<double2><<<nb, CTA_THREADS, sm_build, st>>>(a);
+      DPG_CHECK_LAUNCH();
+      k_elem_potrf<<<nb, CTA_THREADS, sm_real, st>>>(a);
+      DPG_CHECK_LAUNCH();
+      if (real) k_elem_trsm<double><<<nb, CTA_THREADS, sm_cplx, st>>>(a);
+      else k_elem_trsm<double2><<<nb, CTA_THREADS, sm_cplx, st>>>(a);
+      DPG_CHECK_LAUNCH();
+      if (real) k_elem_herk<double><<<nb, CTA_THREADS, sm_cplx, st>>>(a);
+      else k_elem_herk<double2><<<nb, CTA_THREADS, sm_cplx, st>>>(a);
+      DPG_CHECK_LAUNCH();
+      if (real) k_elem_condense<double><<<nb, CTA_THREADS, sm_cplx, st>>>(a);
+      else k_elem_condense<double2><<<nb, CTA_THREADS, sm_cplx, st>>>(a);
+      DPG_CHECK_LAUNCH();
+    }
+  };
+  run_list(dreal, (int64_t)lreal.size(), true);
+  run_list(dcplx, (int64_t)lcplx.size(), false);
   int info = 0;
   DPG_CUDA(cudaMemcpyAsync(&info, a.info, sizeof(int), cudaMemcpyDeviceToHost, st));
   DPG_CUDA(cudaStreamSynchronize(st));
   A.release(a.G);
   A.release(a.W);
   A.release(a.K);
+  A.release(dreal);
+  A.release(dcplx);
   if (info) throw Err{DPGMG_ERR_NOT_HPD, "element Gram or field block not positive definite"};
 }
 

@@ -203,11 +203,13 @@ __global__ void __launch_bounds__(CTA_THREADS) k_patch_invert(const int64_t* ptr
   __syncthreads();
   int inf = cta_potrf<C>(W, n, n, sh);
   if (threadIdx.x == 0 && inf) atomicOr(info, 8);
+  // M = L^-1 (lower), then W = L^-H L^-1 = A^-1, copied back into M
   for (int q = threadIdx.x; q < n * n; q += blockDim.x)
     M[q] = (q / n == q % n) ? Ops<C>::from_re(1) : Ops<C>::zero();
   __syncthreads();
-  cta_trsm_lower<C, C>(W, n, n, M, n, n, reinterpret_cast<char*>(sh));
-  cta_trsm_lower_h<C>(W, n, n, M, n, n, reinterpret_cast<char*>(sh));
+  cta_trinv_lower<C>(W, n, n, M, n, reinterpret_cast<char*>(sh));
+  cta_herk_lower_tri<C>(M, n, n, W, n, sh);
+  for (int q = threadIdx.x; q < n * n; q += blockDim.x) M[q] = W[q];
 }
 
 // --------------------------------------------------------------- precision
