@@ -130,6 +130,8 @@ typedef struct dpgmg_level_desc {
   long long sum_patch_sq;  /* sum of squared patch sizes */
   long long op_nnz;        /* stored entries of the level's smoothing operator */
   double theta;
+  long long patch_stored;  /* stored patch-inverse entries (sum n_j^2, or sum n_j(n_j+1)/2 in
+                              Hermitian half storage) */
 } dpgmg_level_desc;
 
 typedef struct dpgmg_handle_s* dpgmg_handle;

@@ -419,6 +419,7 @@ int dpgmg_level_info(dpgmg_handle h, dpgmg_system sys, int level, dpgmg_level_de
   out->sum_patch_sq = L.P.sum_sq;
   out->op_nnz = L.A.nnz;
   out->theta = L.theta;
+  out->patch_stored = L.P.half ? L.P.nhvals : L.P.nvals;
   return DPGMG_OK;
 }
 

@@ -77,6 +77,13 @@ struct PatchDev {
   float2* inv32 = nullptr;
   int2* chunks = nullptr;      // (patch, first row) of each 32-row work item
   int64_t nchunks = 0;
+  // Hermitian half storage (lower triangles packed by rows), used for the
+  // complex64 operators of the mixed path
+  bool half = false;
+  int64_t nhvals = 0;
+  int64_t* hptr = nullptr;     // per patch (+1): offset of its packed triangle
+  float2* h32 = nullptr;
+  int64_t scratch_entries() const { return nslots; }
 };
 
 struct Level {

@@ -19,6 +19,7 @@
 
 #include "common.cuh"
 #include "internal.h"
+#include "smoother.cuh"
 
 namespace dpgmg {
 
@@ -46,71 +47,25 @@ static void* noalloc_scratch(int dev) {
   return g_noalloc_addr[dev];
 }
 
-template <class C> __device__ __forceinline__ C from_c128(double2 v);
-template <> __device__ __forceinline__ double2 from_c128<double2>(double2 v) { return v; }
-template <> __device__ __forceinline__ float2 from_c128<float2>(double2 v) {
-  return make_float2((float)v.x, (float)v.y);
-}
-
-// Patch products for one 32-row chunk (same work split as the solver's
-// smoother); r is complex128 and is rounded to the operator precision C.
+// The same smoother kernels as the solver (smoother.cuh), reading and
+// writing complex128 vectors; scratch = the static array.
 template <class C>
-__global__ void __launch_bounds__(256) k_na_patch(const int64_t* __restrict__ ptr, const int32_t* __restrict__ dofs,
-                                                  const int64_t* __restrict__ vptr, const int2* __restrict__ chunks,
-                                                  const C* __restrict__ inv, const double2* __restrict__ r,
-                                                  C* __restrict__ pbuf) {
-  extern __shared__ unsigned char shraw[];
-  __shared__ C part[8][33];
-  C* rj = reinterpret_cast<C*>(shraw);
-  using O = Ops<C>;
-  const int2 ch = chunks[blockIdx.x];
-  const int64_t j = ch.x;
-  const int64_t b = ptr[j];
-  const int n = (int)(ptr[j + 1] - b);
-  for (int q = threadIdx.x; q < n; q += blockDim.x) rj[q] = from_c128<C>(r[dofs[b + q]]);
-  __syncthreads();
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  const int a = ch.y + lane;
-  const C* M = inv + vptr[j] + a;
-  C a0 = O::zero(), a1 = O::zero();
-  if (a < n) {
-    int k = w;
-    for (; k + 8 < n; k += 16) {
-      a0 = O::fmac(rj[k], M[(size_t)k * n], a0);
-      a1 = O::fmac(rj[k + 8], M[(size_t)(k + 8) * n], a1);
-    }
-    if (k < n) a0 = O::fmac(rj[k], M[(size_t)k * n], a0);
-  }
-  part[w][lane] = O::add(a0, a1);
-  __syncthreads();
-  if (w == 0 && a < n) {
-    C s = part[0][lane];
-#pragma unroll
-    for (int q = 1; q < 8; ++q) s = O::add(s, part[q][lane]);
-    pbuf[b + a] = s;
-  }
-}
-
-// y[g] = theta * sum of the patch products of DOF g (complex128 output)
-template <class C>
-__global__ void k_na_sum(const int64_t* __restrict__ sptr, const int32_t* __restrict__ slots,
-                         const C* __restrict__ pbuf, double2* __restrict__ y, int64_t n, double theta) {
-  int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (g >= n) return;
-  C acc = Ops<C>::zero();
-  for (int64_t s = sptr[g]; s < sptr[g + 1]; ++s) acc = Ops<C>::add(acc, pbuf[slots[s]]);
-  acc = Ops<C>::scale(acc, (typename Ops<C>::R)theta);
-  y[g] = make_double2((double)acc.x, (double)acc.y);
-}
-
-template <class C>
-static void na_smooth(const Level& L, const C* inv, const double2* r, double2* y, C* pbuf, cudaStream_t st) {
+static void na_smooth(const Level& L, const C* inv_full, const C* inv_half, const double2* r, double2* y, C* scratch,
+                      cudaStream_t st) {
   const PatchDev& P = L.P;
-  const size_t sm = (size_t)P.max_n * sizeof(C) + 16;
-  k_na_patch<C><<<(unsigned)P.nchunks, 256, sm, st>>>(P.ptr, P.dofs, P.val_ptr, P.chunks, inv, r, pbuf);
-  DPG_CHECK_LAUNCH();
   const int64_t n = L.mesh.ndof;
-  k_na_sum<C><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(P.slot_ptr, P.slots, pbuf, y, n, L.theta);
+  if (P.half && inv_half) {
+    const int mx = 9 * HALF_MAX_N * (int)sizeof(C) + 16;
+    DPG_CUDA(cudaFuncSetAttribute(k_patch_apply_h<C, double2>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
+    const size_t sm = (size_t)9 * P.max_n * sizeof(C) + 16;
+    k_patch_apply_h<C, double2><<<(unsigned)P.np, 256, sm, st>>>(P.ptr, P.dofs, P.hptr, inv_half, r, scratch);
+  } else {
+    const size_t sm = (size_t)P.max_n * sizeof(C) + 16;
+    k_patch_apply<C, double2><<<(unsigned)P.nchunks, 256, sm, st>>>(P.ptr, P.dofs, P.val_ptr, P.chunks, inv_full, r,
+                                                                     scratch);
+  }
+  DPG_CHECK_LAUNCH();
+  k_slot_sum<C, double2><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(P.slot_ptr, P.slots, scratch, y, n, L.theta, 0);
   DPG_CHECK_LAUNCH();
 }
 
@@ -128,9 +83,9 @@ extern "C" int dpgmg_smooth_noalloc(dpgmg_handle h, dpgmg_system sys, int level,
     return DPGMG_ERR_ARG;
   }
   const Level& L = S.levels[level];
-  if (L.P.nslots > NOALLOC_MAX_SLOTS) {
-    set_last_error("dpgmg_smooth_noalloc: level has " + std::to_string(L.P.nslots) +
-                   " patch slots, above the fixed scratch of " + std::to_string(NOALLOC_MAX_SLOTS));
+  if (L.P.scratch_entries() > NOALLOC_MAX_SLOTS) {
+    set_last_error("dpgmg_smooth_noalloc: level needs " + std::to_string(L.P.scratch_entries()) +
+                   " scratch entries, above the fixed scratch of " + std::to_string(NOALLOC_MAX_SLOTS));
     return DPGMG_ERR_ARG;
   }
   try {
@@ -140,9 +95,9 @@ extern "C" int dpgmg_smooth_noalloc(dpgmg_handle h, dpgmg_system sys, int level,
     const double2* r = reinterpret_cast<const double2*>(r_dev);
     double2* y = reinterpret_cast<double2*>(y_dev);
     if (S.op.precision == DPGMG_PREC_MIXED)
-      na_smooth<float2>(L, L.P.inv32, r, y, reinterpret_cast<float2*>(scratch), st);
+      na_smooth<float2>(L, L.P.inv32, L.P.h32, r, y, reinterpret_cast<float2*>(scratch), st);
     else
-      na_smooth<double2>(L, L.P.inv64, r, y, reinterpret_cast<double2*>(scratch), st);
+      na_smooth<double2>(L, L.P.inv64, nullptr, r, y, reinterpret_cast<double2*>(scratch), st);
     DPG_CUDA(cudaStreamSynchronize(st));
     return DPGMG_OK;
   } catch (const Err& e) {

@@ -1,0 +1,180 @@
+// Additive Schwarz smoother kernels (Sec. 3, "V-cycle and smoother"):
+//   y = theta * sum_j R_j^T A_jj^-1 R_j r
+// over the vertex patches of a level.  A_jj^-1 is Hermitian.
+//
+// Full storage (n_j x n_j blocks): one CTA per 32-row chunk of a patch; lane a
+// of warp w reads M[k][a0 + a] for k = w, w + 8, ... (coalesced), the 8 warp
+// partials are summed in shared memory; y_a = sum_k conj(M[k][a]) r_k.
+//
+// Half storage (lower triangle packed by rows, n_j (n_j + 1) / 2 entries):
+// every stored entry is read once and used twice (row sum and mirrored
+// column sum), see k_patch_apply_h.  Used for complex64 operators; patches
+// up to HALF_MAX_N DOFs (the shared-memory buffers scale with n_j).
+#pragma once
+#include "common.cuh"
+
+namespace dpgmg {
+
+constexpr int HALF_MAX_N = 1024;
+
+template <class C> __device__ __forceinline__ C warp_sum_s(C v) {
+  for (int o = 16; o > 0; o >>= 1) {
+    v.x += __shfl_xor_sync(0xffffffffu, v.x, o);
+    v.y += __shfl_xor_sync(0xffffffffu, v.y, o);
+  }
+  return v;
+}
+
+// conversions between the operator precision C and the vectors' type
+template <class C, class V> __device__ __forceinline__ C cvt_in(V v) {
+  return Ops<C>::mk((typename Ops<C>::R)v.x, (typename Ops<C>::R)v.y);
+}
+
+template <class C, class TIN>
+__global__ void __launch_bounds__(256) k_patch_apply(const int64_t* __restrict__ ptr, const int32_t* __restrict__ dofs,
+                                                     const int64_t* __restrict__ vptr, const int2* __restrict__ chunks,
+                                                     const C* __restrict__ inv, const TIN* __restrict__ r,
+                                                     C* __restrict__ pbuf) {
+  extern __shared__ unsigned char shraw[];
+  __shared__ C part[8][33];
+  C* rj = reinterpret_cast<C*>(shraw);
+  using O = Ops<C>;
+  const int2 ch = chunks[blockIdx.x];
+  const int64_t j = ch.x;
+  const int64_t b = ptr[j];
+  const int n = (int)(ptr[j + 1] - b);
+  for (int q = threadIdx.x; q < n; q += blockDim.x) rj[q] = cvt_in<C>(r[dofs[b + q]]);
+  __syncthreads();
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int a = ch.y + lane;
+  const C* M = inv + vptr[j] + a;
+  C a0 = O::zero(), a1 = O::zero(), a2 = O::zero(), a3 = O::zero();
+  if (a < n) {
+    int k = w;
+    for (; k + 24 < n; k += 32) {
+      const C m0 = M[(size_t)k * n], m1 = M[(size_t)(k + 8) * n];
+      const C m2 = M[(size_t)(k + 16) * n], m3 = M[(size_t)(k + 24) * n];
+      a0 = O::fmac(rj[k], m0, a0);
+      a1 = O::fmac(rj[k + 8], m1, a1);
+      a2 = O::fmac(rj[k + 16], m2, a2);
+      a3 = O::fmac(rj[k + 24], m3, a3);
+    }
+    for (; k < n; k += 8) a0 = O::fmac(rj[k], M[(size_t)k * n], a0);
+  }
+  part[w][lane] = O::add(O::add(a0, a1), O::add(a2, a3));
+  __syncthreads();
+  if (w == 0 && a < n) {
+    C s = part[0][lane];
+#pragma unroll
+    for (int q = 1; q < 8; ++q) s = O::add(s, part[q][lane]);
+    pbuf[b + a] = s;
+  }
+}
+
+// y[g] = (accumulate ? y[g] : 0) + theta * sum_{slots of g} pbuf[slot]
+template <class C, class TOUT>
+__global__ void k_slot_sum(const int64_t* __restrict__ sptr, const int32_t* __restrict__ slots,
+                           const C* __restrict__ pbuf, TOUT* __restrict__ y, int64_t n, double theta, int accumulate) {
+  int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (g >= n) return;
+  C acc = Ops<C>::zero();
+  for (int64_t s = sptr[g]; s < sptr[g + 1]; ++s) acc = Ops<C>::add(acc, pbuf[slots[s]]);
+  acc = Ops<C>::scale(acc, (typename Ops<C>::R)theta);
+  TOUT o = cvt_in<TOUT>(acc);
+  y[g] = accumulate ? Ops<TOUT>::add(y[g], o) : o;
+}
+
+// ---------------------------------------------------------------- half storage
+// One CTA per patch.  The packed lower triangle is cut into 32 x 32 tiles
+// (I, K), K <= I; warp w takes tiles w, w + 8, ... of the list.  A tile is
+// loaded with 32 coalesced row-segment loads (lane k holds column 32K + k of
+// the tile's 32 rows), then
+//   columns: lane k adds sum_r conj(T[r][k]) r_{32I+r} to y_{32K+k}
+//            (strictly below the diagonal);
+//   rows:    the 32 products T[r][k] r_{32K+k} are summed over the lanes by a
+//            recursive-halving transpose-reduce (31 shuffles), after which
+//            lane r holds the tile's contribution to y_{32I+r}.
+// Contributions go to the warp's own shared buffer; the 8 buffers are summed
+// in a fixed order, so the result is deterministic.
+template <class C, class TIN>
+__global__ void __launch_bounds__(256) k_patch_apply_h(const int64_t* __restrict__ ptr, const int32_t* __restrict__ dofs,
+                                                       const int64_t* __restrict__ hptr, const C* __restrict__ H,
+                                                       const TIN* __restrict__ r, C* __restrict__ pbuf) {
+  extern __shared__ unsigned char shraw[];
+  using O = Ops<C>;
+  const int64_t j = blockIdx.x;
+  const int64_t b = ptr[j];
+  const int n = (int)(ptr[j + 1] - b);
+  C* rj = reinterpret_cast<C*>(shraw);   // [n]
+  C* wb = rj + n;                        // [8][n]
+  for (int q = threadIdx.x; q < n; q += blockDim.x) rj[q] = cvt_in<C>(r[dofs[b + q]]);
+  for (int q = threadIdx.x; q < 8 * n; q += blockDim.x) wb[q] = O::zero();
+  __syncthreads();
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  C* my = wb + w * n;
+  const C* Hj = H + hptr[j];
+  const int T = (n + 31) >> 5;
+  const int ntiles = T * (T + 1) / 2;
+  for (int t = w; t < ntiles; t += 8) {
+    int I = (int)((sqrtf(8.0f * t + 1.0f) - 1.0f) * 0.5f);
+    while ((I + 1) * (I + 2) / 2 <= t) ++I;
+    while (I * (I + 1) / 2 > t) --I;
+    const int K = t - I * (I + 1) / 2;
+    const int k = 32 * K + lane;
+    C v[32];
+#pragma unroll
+    for (int q = 0; q < 32; ++q) {
+      const int a = 32 * I + q;
+      v[q] = (a < n && k <= a) ? Hj[(int64_t)a * (a + 1) / 2 + k] : O::zero();
+    }
+    // mirrored upper triangle: y_k += sum_r conj(M[a][k]) r_a, a = 32I + r > k
+    C cacc = O::zero();
+#pragma unroll
+    for (int q = 0; q < 32; ++q)
+      if (32 * I + q > k) cacc = O::fmac(rj[min(32 * I + q, n - 1)], v[q], cacc);
+    if (k < n) my[k] = O::add(my[k], cacc);
+    // row sums: v[q] <- M[a][k] r_k, then transpose-reduce over the lanes
+    const C rk = (k < n) ? rj[k] : O::zero();
+#pragma unroll
+    for (int q = 0; q < 32; ++q) v[q] = O::mul(v[q], rk);
+#pragma unroll
+    for (int s = 16; s >= 1; s >>= 1) {
+      const bool up = (lane & s) != 0;
+#pragma unroll
+      for (int i = 0; i < s; ++i) {
+        const C send = up ? v[i] : v[i + s];
+        C recv;
+        recv.x = __shfl_xor_sync(0xffffffffu, send.x, s);
+        recv.y = __shfl_xor_sync(0xffffffffu, send.y, s);
+        v[i] = O::add(up ? v[i + s] : v[i], recv);
+      }
+    }
+    const int a = 32 * I + lane;
+    __syncwarp();
+    if (a < n) my[a] = O::add(my[a], v[0]);
+    __syncwarp();
+  }
+  __syncthreads();
+  for (int q = threadIdx.x; q < n; q += blockDim.x) {
+    C s = wb[q];
+#pragma unroll
+    for (int ww = 1; ww < 8; ++ww) s = O::add(s, wb[ww * n + q]);
+    pbuf[b + q] = s;
+  }
+}
+
+// packs the lower triangle of every full block into half storage
+template <class CF, class CH>
+__global__ void k_pack_half(const int64_t* __restrict__ ptr, const int64_t* __restrict__ vptr,
+                            const int64_t* __restrict__ hptr, const CF* __restrict__ full, CH* __restrict__ half) {
+  const int64_t j = blockIdx.x;
+  const int n = (int)(ptr[j + 1] - ptr[j]);
+  const CF* M = full + vptr[j];
+  CH* Hj = half + hptr[j];
+  for (int64_t q = threadIdx.x; q < (int64_t)n * n; q += blockDim.x) {
+    const int a = (int)(q / n), k = (int)(q % n);
+    if (k <= a) Hj[(int64_t)a * (a + 1) / 2 + k] = cvt_in<CH>(M[q]);
+  }
+}
+
+}  // namespace dpgmg

@@ -16,6 +16,7 @@
 
 #include "common.cuh"
 #include "internal.h"
+#include "smoother.cuh"
 
 namespace dpgmg {
 
@@ -23,12 +24,14 @@ template <class C> struct Prec;
 template <> struct Prec<double2> {
   static const double2* A(const ECSRDev& a) { return a.v64; }
   static const double2* inv(const PatchDev& p) { return p.inv64; }
+  static const double2* half(const PatchDev&) { return nullptr; }
   static const double2* Y(const Level& l) { return l.Y64; }
   static const double2* Ai(const Level& l) { return l.Ai64; }
 };
 template <> struct Prec<float2> {
   static const float2* A(const ECSRDev& a) { return a.v32; }
   static const float2* inv(const PatchDev& p) { return p.inv32; }
+  static const float2* half(const PatchDev& p) { return p.h32; }
   static const float2* Y(const Level& l) { return l.Y32; }
   static const float2* Ai(const Level& l) { return l.Ai32; }
 };
@@ -224,75 +227,35 @@ void spmv64(const ECSRDev& A, const double2* x, double2* y, cudaStream_t st) {
 }
 
 // ------------------------------------------------------------- smoother
-// Patch product y_j = A_j^-1 (R_j r), one CTA per 32-row chunk of a patch.
-// A_j^-1 is Hermitian, so y_a = sum_k conj(M[k][a]) r_k: lane a of warp w
-// reads M[k][a0 + lane] for k = w, w + 8, ... (256-byte coalesced rows), and
-// the 8 warp partials are summed in shared memory.
-template <class C>
-__global__ void __launch_bounds__(256) k_patch_apply(const int64_t* __restrict__ ptr, const int32_t* __restrict__ dofs,
-                                                     const int64_t* __restrict__ vptr, const int2* __restrict__ chunks,
-                                                     const C* __restrict__ inv, const C* __restrict__ r,
-                                                     C* __restrict__ pbuf) {
-  extern __shared__ unsigned char shraw[];
-  __shared__ C part[8][33];
-  C* rj = reinterpret_cast<C*>(shraw);
-  using O = Ops<C>;
-  const int2 ch = chunks[blockIdx.x];
-  const int64_t j = ch.x;
-  const int64_t b = ptr[j];
-  const int n = (int)(ptr[j + 1] - b);
-  for (int q = threadIdx.x; q < n; q += blockDim.x) rj[q] = r[dofs[b + q]];
-  __syncthreads();
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  const int a = ch.y + lane;
-  const C* M = inv + vptr[j] + a;
-  C a0 = O::zero(), a1 = O::zero(), a2 = O::zero(), a3 = O::zero();
-  if (a < n) {
-    int k = w;
-    for (; k + 24 < n; k += 32) {
-      const C m0 = M[(size_t)k * n], m1 = M[(size_t)(k + 8) * n];
-      const C m2 = M[(size_t)(k + 16) * n], m3 = M[(size_t)(k + 24) * n];
-      a0 = O::fmac(rj[k], m0, a0);
-      a1 = O::fmac(rj[k + 8], m1, a1);
-      a2 = O::fmac(rj[k + 16], m2, a2);
-      a3 = O::fmac(rj[k + 24], m3, a3);
-    }
-    for (; k < n; k += 8) a0 = O::fmac(rj[k], M[(size_t)k * n], a0);
-  }
-  part[w][lane] = O::add(O::add(a0, a1), O::add(a2, a3));
-  __syncthreads();
-  if (w == 0 && a < n) {
-    C s = part[0][lane];
-#pragma unroll
-    for (int q = 1; q < 8; ++q) s = O::add(s, part[q][lane]);
-    pbuf[b + a] = s;
-  }
-}
-
-// y[g] = (accumulate ? y[g] : 0) + theta * sum_{slots of g} pbuf[slot]
-template <class C>
-__global__ void k_slot_sum(const int64_t* __restrict__ sptr, const int32_t* __restrict__ slots,
-                           const C* __restrict__ pbuf, C* __restrict__ y, int64_t n, double theta, int accumulate) {
-  int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (g >= n) return;
-  C acc = Ops<C>::zero();
-  for (int64_t s = sptr[g]; s < sptr[g + 1]; ++s) acc = Ops<C>::add(acc, pbuf[slots[s]]);
-  acc = Ops<C>::scale(acc, (typename Ops<C>::R)theta);
-  y[g] = accumulate ? Ops<C>::add(y[g], acc) : acc;
+// Dynamic shared memory of the half-storage product can exceed the default
+// 48 KiB; the limit is set to the largest size any level needs.
+static void configure_smoother_kernels() {
+  const int mx = 9 * HALF_MAX_N * (int)sizeof(float2) + 16;
+  DPG_CUDA(cudaFuncSetAttribute(k_patch_apply_h<float2, float2>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
 }
 
 template <class C>
 static void smooth(const Level& L, const C* r, C* y, double theta, int accumulate, C* pbuf, cudaStream_t st,
                    SystemImpl* prof = nullptr) {
   const PatchDev& P = L.P;
+  const int64_t n = L.mesh.ndof;
+  if (P.half && Prec<C>::half(P)) {
+    const size_t sm = (size_t)9 * P.max_n * sizeof(C) + 16;
+    int pe = prof_begin(prof, st);
+    k_patch_apply_h<C, C><<<(unsigned)P.np, 256, sm, st>>>(P.ptr, P.dofs, P.hptr, Prec<C>::half(P), r, pbuf);
+    DPG_CHECK_LAUNCH();
+    prof_end(prof, pe, st);
+    k_slot_sum<C, C><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(P.slot_ptr, P.slots, pbuf, y, n, theta, accumulate);
+    DPG_CHECK_LAUNCH();
+    return;
+  }
   size_t sm = (size_t)P.max_n * sizeof(C) + 16;
   int pe = prof_begin(prof, st);
-  k_patch_apply<C><<<(unsigned)P.nchunks, 256, sm, st>>>(P.ptr, P.dofs, P.val_ptr, P.chunks, Prec<C>::inv(P), r,
-                                                        pbuf);
+  k_patch_apply<C, C><<<(unsigned)P.nchunks, 256, sm, st>>>(P.ptr, P.dofs, P.val_ptr, P.chunks, Prec<C>::inv(P), r,
+                                                            pbuf);
   DPG_CHECK_LAUNCH();
   prof_end(prof, pe, st);
-  int64_t n = L.mesh.ndof;
-  k_slot_sum<C><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(P.slot_ptr, P.slots, pbuf, y, n, theta, accumulate);
+  k_slot_sum<C, C><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(P.slot_ptr, P.slots, pbuf, y, n, theta, accumulate);
   DPG_CHECK_LAUNCH();
 }
 
@@ -524,13 +487,14 @@ static void alloc_level_ws(WS& W, SystemImpl& S) {
     v[l].rs = S.mem.arr<C>((size_t)n);
     v[l].x = S.mem.arr<C>((size_t)n);
     v[l].t = S.mem.arr<C>((size_t)n);
-    if (l >= 1) v[l].pbuf = S.mem.arr<C>((size_t)std::max<int64_t>(L.P.nslots, 1));
+    if (l >= 1) v[l].pbuf = S.mem.arr<C>((size_t)std::max<int64_t>(L.P.scratch_entries(), 1));
     if (L.kind == 2) v[l].cbuf = S.mem.arr<C>((size_t)L.nK * L.nS);
   }
 }
 
 void ensure_workspace(SystemImpl& S, cudaStream_t st) {
   if (S.ws) return;
+  configure_smoother_kernels();
   WS* W = new WS();
   S.ws = W;
   const Level& F = S.levels.back();
@@ -718,7 +682,7 @@ int pcg_solve(SystemImpl& S, cudaStream_t st, double2* xout, dpgmg_stats* stats)
   {
     const Level& Ff = S.levels.back();
     const int64_t esz = S.op.precision == DPGMG_PREC_MIXED ? 8 : 16;
-    if (S.prof_which == DPGMG_PROF_SMOOTH_FINE) S.prof_bytes = Ff.P.nvals * esz;
+    if (S.prof_which == DPGMG_PROF_SMOOTH_FINE) S.prof_bytes = Ff.P.nvals * esz;   // full-storage algorithmic bytes
     else if (S.prof_which == DPGMG_PROF_SPMV_FINE) S.prof_bytes = Ff.A.nnz * esz;
     else if (S.prof_which == DPGMG_PROF_SPMV_CG) S.prof_bytes = A.nnz * 16;   // hi + lo complex64
   }
@@ -862,7 +826,7 @@ static double estimate_theta_t(SystemImpl& S, Level& F, cudaStream_t st) {
   C* x = tmp.arr<C>((size_t)n);
   C* y = tmp.arr<C>((size_t)n);
   C* t = tmp.arr<C>((size_t)n);
-  C* pbuf = tmp.arr<C>((size_t)std::max<int64_t>(F.P.nslots, 1));
+  C* pbuf = tmp.arr<C>((size_t)std::max<int64_t>(F.P.scratch_entries(), 1));
   WS W;
   W.part = tmp.arr<double2>(RED_BLOCKS);
   W.sc = tmp.arr<double2>(SC_COUNT);
@@ -898,6 +862,7 @@ static double estimate_theta_t(SystemImpl& S, Level& F, cudaStream_t st) {
 
 void estimate_theta(SystemImpl& S, int l, cudaStream_t st) {
   Level& F = S.levels[l];
+  configure_smoother_kernels();
   if (S.op.theta > 0.0) {
     F.theta = S.op.theta;
     return;

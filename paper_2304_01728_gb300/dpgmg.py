@@ -56,7 +56,7 @@ class dpgmg_level_desc(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int * 3), ("p", ctypes.c_int), ("n_dof", ctypes.c_longlong),
                 ("n_smooth", ctypes.c_longlong), ("kind", ctypes.c_int), ("n_patches", ctypes.c_longlong),
                 ("patch_max", ctypes.c_longlong), ("sum_patch_sq", ctypes.c_longlong),
-                ("op_nnz", ctypes.c_longlong), ("theta", ctypes.c_double)]
+                ("op_nnz", ctypes.c_longlong), ("theta", ctypes.c_double), ("patch_stored", ctypes.c_longlong)]
 
 
 _lib = None

@@ -59,4 +59,4 @@ def test_struct_layouts_match_header(libpath):
     assert ctypes.sizeof(dpgmg.dpgmg_problem) == 176
     assert ctypes.sizeof(dpgmg.dpgmg_opts) == 48
     assert ctypes.sizeof(dpgmg.dpgmg_stats) == 64
-    assert ctypes.sizeof(dpgmg.dpgmg_level_desc) == 80
+    assert ctypes.sizeof(dpgmg.dpgmg_level_desc) == 88
