@@ -51,6 +51,12 @@ def parse():
     ap.add_argument("--no-fp64-compare", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--n", type=int, default=0, help="override the mesh size n^3 (profiling of a smaller case)")
+    ap.add_argument("--mode", default="step", choices=["step", "batch", "serve"],
+                    help="step: the bench line; batch: independent uneven problems; serve: Poisson request stream")
+    ap.add_argument("--count", type=int, default=16, help="batch/serve: problems drawn from the seeded stream")
+    ap.add_argument("--max-dofs", type=float, default=2.5e5, help="batch/serve: sample only problems up to this size")
+    ap.add_argument("--slots", type=int, default=4, help="batch/serve: concurrent serving slots")
+    ap.add_argument("--rate", type=float, default=0.0, help="serve: arrival rate in requests/s (0: all at t = 0)")
     ap.add_argument("--oracle-sample", action="store_true", help=argparse.SUPPRESS)
     ap.add_argument("--oracle-steps", type=int, default=1, help=argparse.SUPPRESS)
     return ap.parse_args()
@@ -214,10 +220,12 @@ def traffic_for(kernel):
             d = json.load(f)
     except OSError:
         return None
-    src = os.path.join(ROOT, "paper_2304_01728_gb300", "csrc", "solve.cu")
-    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
     e = d.get(kernel)
-    if not e or e.get("solve_cu_sha") != sha:
+    if not e:
+        return None
+    src = os.path.join(ROOT, e["source"])
+    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    if e.get("source_sha") != sha:
         return None
     return e.get("traffic_bytes_per_launch")
 
@@ -289,6 +297,16 @@ def run_gb300(args, rank, world, local_rank):
         dof_iters, pcg_ms, total_ms = reduce_ranks(dist, dof_iters, pcg_ms, total_ms, "cuda")
     value = dof_iters / (pcg_ms / 1e3)
 
+    # ---- the other HBM-bound kernels of the iteration, one profiled step each
+    kernels = []
+    for prof, name in ((D.PROF_SPMV_FINE, "k_spmv (finest V-cycle SpMV, c64 values)"),
+                       (D.PROF_SPMV_CG, "k_spmv_df (CG operator, c64 hi + lo values)")):
+        _, pr = step(prof)
+        ms = pr[0] / max(pr[1], 1)
+        gbs = pr[2] / (ms / 1e3) / 1e9
+        kernels.append({"kernel": name, "bytes_per_launch": pr[2], "launches": pr[1], "avg_launch_ms": ms,
+                        "achieved": gbs, "unit": "GB/s"})
+
     # ---- end to end through the public API with host buffers
     e2e = None
     nelem = int(np.prod(w["problem"]["n"]))
@@ -349,8 +367,83 @@ def run_gb300(args, rank, world, local_rank):
                      "bytes_per_launch": prof_b, "launches": prof_n, "avg_launch_ms": per_launch_ms,
                      "traffic": traffic_for("k_patch_apply")},
         "clocks": clk, "e2e": e2e, "fp64_path": fp64,
+        "kernels": [dict(k, frac=k["achieved"] / peak) for k in kernels],
     }
     return out
+
+
+# ------------------------------------------------------------------ batch / serve
+def run_stream(args):
+    """Independent problems through the serving loop (continuous batching).
+
+    batch: the first --count problems of the seeded uneven batch stream, all
+    submitted at t = 0.  serve: the first --count requests of the seeded
+    serving stream, submitted at Poisson arrival times (--rate requests/s).
+    Problems above --max-dofs are left out of the sample (stated in the output);
+    requests whose footprint exceeds the memory budget are refused (NOMEM).
+    """
+    import numpy as np
+    from paper_2304_01728_gb300 import build as B
+    B.build()
+    from paper_2304_01728_gb300 import dpgmg as D
+    from paper_2304_01728_gb300 import workloads as WL
+    prec = args.precision
+    stream = WL.config4(64, prec) if args.mode == "batch" else WL.config5(max(args.count, 1), prec)
+    drawn = stream[:args.count]
+    h = D.dpgmg_create(0)
+    D.dpgmg_serve_start(h, args.slots)
+    sample, skipped = [], 0
+    for it in drawn:
+        pb, keep = D.make_problem(**it["problem"])
+        op = D.make_opts(**it["opts"])
+        nt, nf, est = D.dpgmg_query_sizes(pb, op)
+        if nt > args.max_dofs:
+            skipped += 1
+            continue
+        sample.append((it, pb, op, keep, nt, nf))
+    t_arr, t = [], 0.0
+    for it, *_ in sample:
+        t += (it.get("gap", 0.0) / args.rate) if (args.mode == "serve" and args.rate > 0) else 0.0
+        t_arr.append(t)
+    tickets, refused = [], 0
+    t0 = time.perf_counter()
+    for (it, pb, op, keep, nt, nf), ta in zip(sample, t_arr):
+        while time.perf_counter() - t0 < ta:
+            time.sleep(0.0005)
+        try:
+            tickets.append((D.dpgmg_submit(h, pb, op), nt, nf))
+        except D.DpgmgError as e:
+            if e.code != D.DPGMG_ERR_NOMEM:
+                raise
+            refused += 1
+    lat, dof_iters, iters, fails = [], 0.0, [], 0
+    for tk, nt, nf in tickets:
+        x = np.zeros(nt, dtype=np.complex128)
+        f = np.zeros(nf, dtype=np.complex128)
+        while True:
+            code, st, l = D.dpgmg_poll(h, tk, x, f)
+            if code != D.DPGMG_ERR_PENDING:
+                break
+            time.sleep(0.001)
+        if code != D.DPGMG_OK:
+            fails += 1
+            continue
+        lat.append(l)
+        dof_iters += nt * st.iters
+        iters.append(st.iters)
+    wall = time.perf_counter() - t0
+    D.dpgmg_destroy(h)
+    done = len(lat)
+    out = {"mode": args.mode, "metric": "solves/s", "value": done / wall, "unit": "solve/s",
+           "dof_iters_per_s": dof_iters / wall, "p50_ms": float(np.percentile(lat, 50)) if lat else None,
+           "p99_ms": float(np.percentile(lat, 99)) if lat else None, "completed": done, "failed": fails,
+           "refused_nomem": refused, "drawn": len(drawn), "left_out_above_max_dofs": skipped,
+           "max_dofs": args.max_dofs, "slots": args.slots, "rate_per_s": args.rate, "precision": prec,
+           "wall_s": wall, "iters_mean": float(np.mean(iters)) if iters else None,
+           "sample": "first %d problems of the seeded %s stream, those with <= %g trace DOFs" % (
+               len(drawn), "batch (n~U{8..24}, p~U{2,3,4})" if args.mode == "batch" else
+               "serving (n~U{8..48}, p~U{2..5})", args.max_dofs)}
+    print(json.dumps(out))
 
 
 # ------------------------------------------------------------------ main
@@ -378,6 +471,10 @@ def main():
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": r["sample"]},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
             "wall_s": time.perf_counter() - t0}))
+        return
+    if args.mode != "step":
+        if rank == 0:
+            run_stream(args)
         return
     out = run_gb300(args, rank, world, local_rank)
     if out is None:

@@ -78,6 +78,7 @@ extern "C" {
 
 #define DPGMG_COARSEST_CHOLESKY 0   /* dense Cholesky solve on level 0 */
 #define DPGMG_COARSEST_NONE     1   /* no level-0 correction (Sec. 4 list) */
+#define DPGMG_COARSEST_AUTO     2   /* CHOLESKY if level 0 has at most 20,000 DOFs, else NONE */
 
 /* ---- problem and options ----------------------------------------------- */
 typedef struct dpgmg_problem {

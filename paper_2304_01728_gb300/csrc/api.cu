@@ -74,10 +74,14 @@ int validate_problem(const dpgmg_problem* pb, const dpgmg_opts* op) {
   }
   if (!(op->tol > 0.0) || op->max_iter < 1 || op->nu_pre < 0 || op->nu_post < 0 || op->n_levels < 1 ||
       op->p_min < 1 || (op->precision != DPGMG_PREC_FP64 && op->precision != DPGMG_PREC_MIXED) ||
-      (op->coarsest != DPGMG_COARSEST_CHOLESKY && op->coarsest != DPGMG_COARSEST_NONE))
+      (op->coarsest != DPGMG_COARSEST_CHOLESKY && op->coarsest != DPGMG_COARSEST_NONE &&
+       op->coarsest != DPGMG_COARSEST_AUTO))
     return DPGMG_ERR_ARG;
   return DPGMG_OK;
 }
+
+// DPGMG_COARSEST_AUTO: the dense coarsest solve is used up to this size.
+constexpr double kAutoCoarsestMax = 20000.0;
 
 // Device bytes a system needs (upper bound used for admission): everything
 // resident after setup plus the largest scratch of any setup phase (the
@@ -135,7 +139,8 @@ size_t estimate_bytes(const dpgmg_problem* pb, const dpgmg_opts* op) {
         const double nlc = n_trace_local(q);
         transient = std::max(transient, std::min(nK, 2048.0) * ((nS + nI) * (nS + nI) + nS * nlc + nS * nS) * 16.0);
       }
-    } else if (op->coarsest == DPGMG_COARSEST_CHOLESKY || specs.size() == 1) {
+    } else if (op->coarsest == DPGMG_COARSEST_CHOLESKY || specs.size() == 1 ||
+               (op->coarsest == DPGMG_COARSEST_AUTO && nd <= kAutoCoarsestMax)) {
       resident += nd * (nd + 1.0) * vsz;                              // packed L^-1 and L^-H
       transient = std::max(transient, nd * nd * (mixed ? 24.0 : 32.0) + nd * 64.0 * 16.0);
     }

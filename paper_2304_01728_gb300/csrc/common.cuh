@@ -408,12 +408,13 @@ __device__ void cta_trinv_lower(const T* L, int n, int ldl, T* X, int ldx, char*
   __syncthreads();
 }
 
-// M = X^H X for lower-triangular X (n x n): each lower tile sums only over
-// rows k >= its first row (X[k][i] = 0 for k < i); the strictly upper tiles
-// are written as the conjugate mirror.  n^3/6 multiply-adds.
-// smem: 2*TL*NB elements of T.
+// M = X^H X (M n x n, X kdim x n): only the lower tiles are computed, the
+// strictly upper tiles are written as their conjugate mirror (half the flops
+// of a full product).  With `tri` X is lower triangular (kdim = n) and each
+// tile sums only over rows k >= its first row (X[k][i] = 0 for k < i):
+// n^3/6 multiply-adds.  smem: 2*TL*NB elements of T.
 template <class T>
-__device__ void cta_herk_lower_tri(const T* X, int n, int ldx, T* M, int ldm, T* smem) {
+__device__ void cta_herk_lower(const T* X, int kdim, int n, int ldx, T* M, int ldm, T* smem, bool tri) {
   using O = Ops<T>;
   T* At = smem;
   T* Bt = smem + TL * NB;
@@ -423,14 +424,14 @@ __device__ void cta_herk_lower_tri(const T* X, int n, int ldx, T* M, int ldm, T*
     for (int j0 = 0; j0 <= i0; j0 += TL) {
       T acc[PER];
       for (int q = 0; q < PER; ++q) acc[q] = O::zero();
-      for (int k0 = i0; k0 < n; k0 += NB) {
+      for (int k0 = tri ? i0 : 0; k0 < kdim; k0 += NB) {
         for (int e = tid; e < TL * NB; e += blockDim.x) {
           int r = e / NB, t = e % NB;
-          At[e] = (i0 + r < n && k0 + t < n) ? O::conj(X[(size_t)(k0 + t) * ldx + i0 + r]) : O::zero();
+          At[e] = (i0 + r < n && k0 + t < kdim) ? O::conj(X[(size_t)(k0 + t) * ldx + i0 + r]) : O::zero();
         }
         for (int e = tid; e < NB * TL; e += blockDim.x) {
           int t = e / TL, c = e % TL;
-          Bt[e] = (k0 + t < n && j0 + c < n) ? X[(size_t)(k0 + t) * ldx + j0 + c] : O::zero();
+          Bt[e] = (k0 + t < kdim && j0 + c < n) ? X[(size_t)(k0 + t) * ldx + j0 + c] : O::zero();
         }
         __syncthreads();
         for (int q = 0; q < PER; ++q) {
@@ -455,6 +456,11 @@ __device__ void cta_herk_lower_tri(const T* X, int n, int ldx, T* M, int ldm, T*
     }
   }
   __syncthreads();
+}
+
+template <class T>
+__device__ void cta_herk_lower_tri(const T* X, int n, int ldx, T* M, int ldm, T* smem) {
+  cta_herk_lower<T>(X, n, n, ldx, M, ldm, smem, true);
 }
 
 }  // namespace dpgmg

@@ -277,7 +277,8 @@ __global__ void __launch_bounds__(CTA_THREADS) k_elem_herk(ElemArgs a) {
   const int ld = a.m + 1;
   const T* W = reinterpret_cast<const T*>(a.W) + le * (size_t)a.nt * ld;
   T* K = reinterpret_cast<T*>(a.K) + le * (size_t)ld * ld;
-  cta_gemm<T>(true, ld, ld, a.nt, 1.0, W, ld, W, ld, 0.0, K, ld, reinterpret_cast<T*>(shraw));
+  // K = W^H W is Hermitian: lower tiles plus their mirror
+  cta_herk_lower<T>(W, a.nt, ld, ld, K, ld, reinterpret_cast<T*>(shraw), false);
 }
 
 // complex output of the path's value; ph = 0: x1, 1: x i, 2: x (-i)

@@ -304,6 +304,10 @@ static void setup_patches(SystemImpl& S, Level& F, const std::vector<char>& smas
     std::vector<int2> ch;
     for (int64_t j = 0; j < D.np; ++j)
       for (int64_t a0 = 0; a0 < P.ptr[j + 1] - P.ptr[j]; a0 += 32) ch.push_back(make_int2((int)j, (int)a0));
+    // largest patches first: the short work items of small patches end the launch
+    std::stable_sort(ch.begin(), ch.end(), [&](const int2& u, const int2& v) {
+      return P.ptr[u.x + 1] - P.ptr[u.x] > P.ptr[v.x + 1] - P.ptr[v.x];
+    });
     D.nchunks = (int64_t)ch.size();
     D.chunks = upload(A, ch, st);
   }
@@ -434,7 +438,9 @@ void build_hierarchy(SystemImpl& S, cudaStream_t st) {
   // coarsest
   Level& C0 = S.levels[0];
   if (L == 0) C0.dofs = S.levels[0].dofs;
-  if (S.op.coarsest == DPGMG_COARSEST_CHOLESKY || L == 0) coarse_setup(S, C0, dinfo, st);
+  const bool dense = S.op.coarsest == DPGMG_COARSEST_CHOLESKY || L == 0 ||
+                     (S.op.coarsest == DPGMG_COARSEST_AUTO && C0.mesh.ndof <= 20000);
+  if (dense) coarse_setup(S, C0, dinfo, st);
   int info = 0;
   DPG_CUDA(cudaMemcpyAsync(&info, dinfo, sizeof(int), cudaMemcpyDeviceToHost, st));
   DPG_CUDA(cudaStreamSynchronize(st));

@@ -101,8 +101,16 @@ __global__ void __launch_bounds__(256) k_spmv(const int32_t* __restrict__ row_en
       const int nnz = (int)(col_ptr[E + 1] - c0);
       const C* vals = v + val_ptr[E] + (row - ent_start[E]) * nnz;
       const int32_t* cols = col_idx + c0;
-      for (int k = lane; k < nnz; k += 32) acc = O::fma(vals[k], x[cols[k]], acc);
-      acc = warp_sum(acc);
+      C acc1 = O::zero();
+      int k = lane;
+      for (; k + 32 < nnz; k += 64) {   // two independent loads per lane per step
+        const C v0 = vals[k], v1 = vals[k + 32];
+        const int cA = cols[k], cB = cols[k + 32];
+        acc = O::fma(v0, x[cA], acc);
+        acc1 = O::fma(v1, x[cB], acc1);
+      }
+      if (k < nnz) acc = O::fma(vals[k], x[cols[k]], acc);
+      acc = warp_sum(O::add(acc, acc1));
     }
     if (lane == 0) y[row] = mode ? O::sub(b[row], acc) : acc;
   }
@@ -141,43 +149,83 @@ __device__ __forceinline__ void df_mul(float ah, float al, float xh, float xl, f
   q = fmaf(al, xh, q);
 }
 
+// Warp sum of double-float values (h, l) with TwoSum on the high parts; every
+// lane ends with the same (h, l) (the exact error of a + b does not depend on
+// the order of the operands).
+__device__ __forceinline__ void df_warp_sum(float& h, float& l) {
+  for (int o = 16; o > 0; o >>= 1) {
+    const float oh = __shfl_xor_sync(0xffffffffu, h, o), ol = __shfl_xor_sync(0xffffffffu, l, o);
+    const float s = h + oh;
+    const float bb = s - h;
+    const float e = (h - (s - bb)) + (oh - bb);
+    h = s;
+    l = l + ol + e;
+  }
+}
+
+// One CTA per 32 consecutive rows (4 per warp).  The row sums stay in FP32
+// pairs up to the end; one warp then turns the 32 results into complex128 with
+// full-warp instructions (the FP64 pipe of this GPU runs at 1/64 of FP32).
+constexpr int DF_ROWS = 32;
 __global__ void __launch_bounds__(256) k_spmv_df(const int32_t* __restrict__ row_ent, const int64_t* __restrict__ ent_start,
                                                  const int64_t* __restrict__ col_ptr, const int32_t* __restrict__ col_idx,
                                                  const int64_t* __restrict__ val_ptr, const float2* __restrict__ vh,
                                                  const float2* __restrict__ vl, const float2* __restrict__ xh,
                                                  const float2* __restrict__ xl, const double2* __restrict__ b,
                                                  double2* __restrict__ y, int64_t nrows, int mode) {
-  const int lane = threadIdx.x & 31;
-  const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
-  for (int64_t row = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); row < nrows; row += nw) {
-    const int32_t E = row_ent[row];
+  __shared__ float4 res[DF_ROWS];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int64_t base = (int64_t)blockIdx.x * DF_ROWS;
+#pragma unroll 1
+  for (int i = 0; i < DF_ROWS / 8; ++i) {
+    const int64_t row = base + w * (DF_ROWS / 8) + i;
     float rh = 0.f, rl = 0.f, ih = 0.f, il = 0.f;
+    const int32_t E = row < nrows ? row_ent[row] : -1;
     if (E >= 0) {
       const int64_t c0 = col_ptr[E];
       const int nnz = (int)(col_ptr[E + 1] - c0);
       const int64_t off = val_ptr[E] + (row - ent_start[E]) * nnz;
       const int32_t* cols = col_idx + c0;
-      for (int k = lane; k < nnz; k += 32) {
-        const float2 ah = vh[off + k], al = vl[off + k];
-        const int c = cols[k];
-        const float2 uh = xh[c], ul = xl[c];
+      for (int k = lane; k < nnz; k += 64) {
+        // two columns per lane per step, all loads issued before the arithmetic
+        const bool two = k + 32 < nnz;
+        const float2 ah0 = vh[off + k], al0 = vl[off + k];
+        const int cA = cols[k];
+        const float2 ah1 = two ? vh[off + k + 32] : make_float2(0.f, 0.f);
+        const float2 al1 = two ? vl[off + k + 32] : make_float2(0.f, 0.f);
+        const int cB = two ? cols[k + 32] : cA;
+        const float2 uh0 = xh[cA], ul0 = xl[cA], uh1 = xh[cB], ul1 = xl[cB];
         float p, q;
-        df_mul(ah.x, al.x, uh.x, ul.x, p, q);
+        df_mul(ah0.x, al0.x, uh0.x, ul0.x, p, q);
         df_add(rh, rl, p, q);
-        df_mul(ah.y, al.y, uh.y, ul.y, p, q);
+        df_mul(ah0.y, al0.y, uh0.y, ul0.y, p, q);
         df_add(rh, rl, -p, -q);
-        df_mul(ah.x, al.x, uh.y, ul.y, p, q);
+        df_mul(ah0.x, al0.x, uh0.y, ul0.y, p, q);
         df_add(ih, il, p, q);
-        df_mul(ah.y, al.y, uh.x, ul.x, p, q);
+        df_mul(ah0.y, al0.y, uh0.x, ul0.x, p, q);
+        df_add(ih, il, p, q);
+        df_mul(ah1.x, al1.x, uh1.x, ul1.x, p, q);
+        df_add(rh, rl, p, q);
+        df_mul(ah1.y, al1.y, uh1.y, ul1.y, p, q);
+        df_add(rh, rl, -p, -q);
+        df_mul(ah1.x, al1.x, uh1.y, ul1.y, p, q);
+        df_add(ih, il, p, q);
+        df_mul(ah1.y, al1.y, uh1.x, ul1.x, p, q);
         df_add(ih, il, p, q);
       }
+      df_warp_sum(rh, rl);
+      df_warp_sum(ih, il);
     }
-    double re = (double)rh + (double)rl, im = (double)ih + (double)il;
-    for (int o = 16; o > 0; o >>= 1) {
-      re += __shfl_xor_sync(0xffffffffu, re, o);
-      im += __shfl_xor_sync(0xffffffffu, im, o);
+    if (lane == 0) res[w * (DF_ROWS / 8) + i] = make_float4(rh, rl, ih, il);
+  }
+  __syncthreads();
+  if (w == 0) {
+    const int64_t row = base + lane;
+    if (row < nrows) {
+      const float4 v = res[lane];
+      const double re = (double)v.x + (double)v.y, im = (double)v.z + (double)v.w;
+      y[row] = mode ? make_double2(b[row].x - re, b[row].y - im) : make_double2(re, im);
     }
-    if (lane == 0) y[row] = mode ? make_double2(b[row].x - re, b[row].y - im) : make_double2(re, im);
   }
 }
 
@@ -207,7 +255,7 @@ static void spmv_df(const ECSRDev& A, const double2* x, const double2* b, double
   const int64_t n = A.nrows;
   k_split_vec<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(x, xh, xl, n);
   DPG_CHECK_LAUNCH();
-  int64_t blocks = std::min<int64_t>((n + 7) / 8, 152 * 16);
+  const int64_t blocks = (n + DF_ROWS - 1) / DF_ROWS;
   int pe = prof_begin(prof, st);
   k_spmv_df<<<(unsigned)blocks, 256, 0, st>>>(A.row_ent, A.ent_start, A.col_ptr, A.col_idx, A.val_ptr, A.v32, A.vlo,
                                              xh, xl, b, y, n, mode);

@@ -20,7 +20,7 @@ DPGMG_ERR_ARG, DPGMG_ERR_NOMEM, DPGMG_ERR_NOT_HPD, DPGMG_ERR_BREAKDOWN = -1, -2,
 DPGMG_ERR_NOT_CONVERGED, DPGMG_ERR_TIMEOUT, DPGMG_ERR_PENDING, DPGMG_ERR_CUDA = -5, -6, -7, -8
 SRC_GAUSSIAN, SRC_PLANE_WAVE, SRC_MANUFACTURED = 0, 1, 2
 PREC_FP64, PREC_MIXED = 0, 1
-COARSEST_CHOLESKY, COARSEST_NONE = 0, 1
+COARSEST_CHOLESKY, COARSEST_NONE, COARSEST_AUTO = 0, 1, 2
 OP_A, OP_SMOOTH, OP_VCYCLE, OP_RESTRICT, OP_PROLONG, OP_CONDENSE, OP_COARSE, OP_AFULL = range(8)
 
 
@@ -159,7 +159,7 @@ def make_opts(**kw):
         if k == "precision" and isinstance(v, str):
             v = {"fp64": PREC_FP64, "mixed": PREC_MIXED}[v]
         if k == "coarsest" and isinstance(v, str):
-            v = {"cholesky": COARSEST_CHOLESKY, "none": COARSEST_NONE}[v]
+            v = {"cholesky": COARSEST_CHOLESKY, "none": COARSEST_NONE, "auto": COARSEST_AUTO}[v]
         setattr(op, k, v)
     return op
 

@@ -65,3 +65,51 @@ def config3(precision="mixed"):
                 opts=dict(n_levels=4, p_min=2, precision=precision, tol=1e-8),
                 name="layered box 32x32x16 p=3 omega=20pi, 4-level, %s V-cycle" % precision,
                 layers=dict(cuts=cuts, speeds=speeds))
+
+
+def _stream_opts(n, precision):
+    return dict(n_levels=4, p_min=2 if n % 2 == 0 else 1, precision=precision, tol=1e-8, coarsest="auto")
+
+
+def config4(count=64, precision="mixed"):
+    """64 independent problems (seed 4): n^3 with n ~ U{8..24}, p ~ U{2,3,4},
+    omega ~ U[4, 12 pi], c = 1, Gaussian source x0 ~ U[0.3, 0.7]^3, sigma 0.1.
+    Hierarchy: p-coarsening to 2, then halving n while it is even, at most 4
+    levels.  Odd n stops h-coarsening; there p is coarsened down to 1 instead,
+    so that no such problem is left with a single level.  The options ask for
+    the dense coarsest solve only where level 0 is small ("auto")."""
+    out = []
+    k = 0
+    for _ in range(count):
+        n = 8 + int(17 * _u(4, k))
+        p = 2 + int(3 * _u(4, k + 1))
+        om = 4.0 + (12 * math.pi - 4.0) * _u(4, k + 2)
+        x0 = tuple(0.3 + 0.4 * _u(4, k + 3 + d) for d in range(3))
+        k += 6
+        out.append(dict(problem=dict(n=(n, n, n), p=p, omega=om, src_center=x0, src_width=0.1),
+                        opts=_stream_opts(n, precision)))
+    return out
+
+
+def config5(count=2000, precision="mixed"):
+    """Serving stream (seed 5): n^3 with n ~ U{8..48}, p ~ U{2..5},
+    omega ~ U[4, 32 pi], wavespeed constant (prob. 0.5) or 4 seeded layers in
+    U[0.1, 1], Gaussian source; inter-arrival times are drawn separately
+    (unit-rate exponentials, scaled by the caller's rate).  Hierarchy options
+    as in config4."""
+    out = []
+    k = 0
+    for _ in range(count):
+        n = 8 + int(41 * _u(5, k))
+        p = 2 + int(4 * _u(5, k + 1))
+        om = 4.0 + (32 * math.pi - 4.0) * _u(5, k + 2)
+        x0 = tuple(0.3 + 0.4 * _u(5, k + 3 + d) for d in range(3))
+        layered = _u(5, k + 6) >= 0.5
+        speeds = [0.1 + 0.9 * _u(5, k + 7 + i) for i in range(4)]
+        gap = -math.log(1.0 - _u(5, k + 11))
+        k += 12
+        pk = dict(n=(n, n, n), p=p, omega=om, src_center=x0, src_width=0.1)
+        if layered:
+            pk["wavespeed"] = [speeds[min(3, (4 * kz) // n)] for kz in range(n) for _ in range(n * n)]
+        out.append(dict(problem=pk, opts=_stream_opts(n, precision), gap=gap))
+    return out

@@ -234,6 +234,27 @@ def test_coarsest_none_matches_oracle():
     assert code == D.DPGMG_OK and abs(st.iters - it_ref) <= max(1, 0.1 * it_ref)
 
 
+@pytest.mark.parametrize("n,expect", [(10, "cholesky"), (11, "none")])
+def test_coarsest_auto_rule(n, expect):
+    """AUTO takes the dense coarsest solve when level 0 holds at most 20,000
+    DOFs (10^3 elements of order 2: 19,061) and none above (11^3: 25,356):
+    it allocates exactly what the explicit choice allocates and gives its
+    result (assembly sums with FP64 atomics, so equal to rounding)."""
+    pk = dict(n=(n, n, n), p=3, omega=10.0, src_center=(0.4, 0.5, 0.6), src_width=0.15)
+    ok = dict(n_levels=2, p_min=2, precision="mixed", tol=1e-8)
+    out = {}
+    for c in ("auto", expect):
+        with D.Solver(pk, **dict(ok, coarsest=c)) as s:
+            x, f, st, code = s.solve()
+            nd0 = D.dpgmg_level_info(s.h, s.s, 0).n_dof
+        assert code == D.DPGMG_OK
+        out[c] = (x, st.iters, st.dev_bytes_peak)
+    assert (nd0 <= 20000) == (expect == "cholesky")
+    assert out["auto"][1] == out[expect][1]
+    assert out["auto"][2] == out[expect][2]
+    assert rel(out["auto"][0], out[expect][0]) < 1e-6
+
+
 def test_error_statuses():
     w = workloads.config1()
     h = D.dpgmg_create(0)
