@@ -107,8 +107,17 @@ typedef struct dpgmg_opts {
   int p_min;               /* lowest order of the p-coarsening stage (>= 1) */
   int precision;           /* DPGMG_PREC_* */
   int coarsest;            /* DPGMG_COARSEST_* */
+  int flags;               /* DPGMG_FLAG_* bits, 0 by default */
   double theta;            /* smoother damping; <= 0 => estimate by power iteration */
 } dpgmg_opts;
+
+/* CG steps after the first are replayed from one captured CUDA graph unless
+   this bit is set (or the stream cannot be captured); results are the same. */
+#define DPGMG_FLAG_EAGER 1
+/* Mixed path: the rank-64 updates of the coarsest complex64 factorisation run
+   on the tensor cores (TF32 operand splitting, about FP32 accuracy) unless
+   this bit is set, which selects the FP32 CUDA-core kernels. */
+#define DPGMG_FLAG_CUDA_CORES 2
 
 typedef struct dpgmg_stats {
   int iters;               /* CG iterations (= V-cycle applications) */

@@ -17,7 +17,13 @@ static thread_local std::string g_last;
 void set_last_error(const std::string& m) { g_last = m; }
 
 static std::atomic<long long> g_launches{0};
-void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+static thread_local long long t_launches = 0;   // this thread's launches (graph capture counts)
+void count_launch() {
+  g_launches.fetch_add(1, std::memory_order_relaxed);
+  ++t_launches;
+}
+void count_launches(long long n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+long long thread_launch_count() { return t_launches; }
 
 void* Alloc::get(size_t bytes) {
   bytes = (bytes + 255) & ~(size_t)255;
@@ -75,7 +81,8 @@ int validate_problem(const dpgmg_problem* pb, const dpgmg_opts* op) {
   if (!(op->tol > 0.0) || op->max_iter < 1 || op->nu_pre < 0 || op->nu_post < 0 || op->n_levels < 1 ||
       op->p_min < 1 || (op->precision != DPGMG_PREC_FP64 && op->precision != DPGMG_PREC_MIXED) ||
       (op->coarsest != DPGMG_COARSEST_CHOLESKY && op->coarsest != DPGMG_COARSEST_NONE &&
-       op->coarsest != DPGMG_COARSEST_AUTO))
+       op->coarsest != DPGMG_COARSEST_AUTO) ||
+      (op->flags & ~(DPGMG_FLAG_EAGER | DPGMG_FLAG_CUDA_CORES)))
     return DPGMG_ERR_ARG;
   return DPGMG_OK;
 }
@@ -232,6 +239,7 @@ void dpgmg_default_opts(dpgmg_opts* op) {
   op->p_min = 2;
   op->precision = DPGMG_PREC_FP64;
   op->coarsest = DPGMG_COARSEST_CHOLESKY;
+  op->flags = 0;
   op->theta = 0.0;
 }
 

@@ -122,8 +122,28 @@ __global__ void __launch_bounds__(CTA_THREADS) k_dense_herk(C* A, int64_t N, int
     }
 }
 
+// Complex64 rank-64 updates on the tensor cores (tc_update.cu).
+void tc_configure();
+void tc_herk_update(float2* A, int64_t N, int k0, int kw, int* err, cudaStream_t st);
+void tc_trinv_update(float2* X, const float2* L, int64_t N, int kb, int* err, cudaStream_t st);
+
 template <class C>
-static void dense_cholesky(C* A, int64_t N, int* info, cudaStream_t st) {
+static bool tc_herk(C*, int64_t, int, int, int*, cudaStream_t) { return false; }
+template <>
+bool tc_herk<float2>(float2* A, int64_t N, int k0, int kw, int* info, cudaStream_t st) {
+  tc_herk_update(A, N, k0, kw, info, st);
+  return true;
+}
+template <class C>
+static bool tc_trinv(C*, const C*, int64_t, int, int*, cudaStream_t) { return false; }
+template <>
+bool tc_trinv<float2>(float2* X, const float2* L, int64_t N, int kb, int* info, cudaStream_t st) {
+  tc_trinv_update(X, L, N, kb, info, st);
+  return true;
+}
+
+template <class C>
+static void dense_cholesky(C* A, int64_t N, int* info, bool tensor, cudaStream_t st) {
   const size_t sm = (size_t)(NB * NB + 2 * TL * NB) * sizeof(C) + 64;
   const size_t smp = (size_t)CNB * CNB * sizeof(C);
   DPG_CUDA(cudaFuncSetAttribute(k_dense_diag<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
@@ -136,6 +156,7 @@ static void dense_cholesky(C* A, int64_t N, int* info, cudaStream_t st) {
     if (rows <= 0) break;
     k_dense_panel<C><<<(unsigned)((rows + 127) / 128), 128, smp, st>>>(A, N, (int)k0);
     DPG_CHECK_LAUNCH();
+    if (tensor && tc_herk<C>(A, N, (int)k0, kb, info, st)) continue;
     int64_t nt = (rows + CNB - 1) / CNB;
     k_dense_herk<C><<<(unsigned)(nt * (nt + 1) / 2), CTA_THREADS, 0, st>>>(A, N, (int)k0);
     DPG_CHECK_LAUNCH();
@@ -249,8 +270,9 @@ __global__ void k_pack(const C* X, int64_t N, C* Lp, C* Up) {
 }
 
 template <class C>
-static void coarse_factor(Alloc& A, C* dense, int64_t N, C** Lp, C** Up, int* info, cudaStream_t st) {
-  dense_cholesky<C>(dense, N, info, st);
+static void coarse_factor(Alloc& A, C* dense, int64_t N, C** Lp, C** Up, int* info, bool tensor, cudaStream_t st) {
+  if (tensor) tc_configure();
+  dense_cholesky<C>(dense, N, info, tensor, st);
   const int nb = (int)((N + CNB - 1) / CNB);
   C* Dinv = A.arr<C>((size_t)nb * CNB * CNB);
   const size_t smd = (size_t)(NB * NB + TL * NB) * sizeof(C) + (size_t)NB * TL * sizeof(C) + 64;
@@ -266,7 +288,7 @@ static void coarse_factor(Alloc& A, C* dense, int64_t N, C** Lp, C** Up, int* in
     k_trinv_scale<C><<<kb + 1, CTA_THREADS, sms, st>>>(X, Dinv, N, kb);
     DPG_CHECK_LAUNCH();
     const int rows = nb - kb - 1;
-    if (rows > 0) {
+    if (rows > 0 && !(tensor && tc_trinv<C>(X, dense, N, kb, info, st))) {
       k_trinv_update<C><<<(unsigned)(rows * (kb + 1)), CTA_THREADS, 0, st>>>(X, dense, N, kb);
       DPG_CHECK_LAUNCH();
     }
@@ -295,10 +317,10 @@ void coarse_setup(SystemImpl& S, Level& C0, int* info, cudaStream_t st) {
     DPG_CHECK_LAUNCH();
     DPG_CUDA(cudaStreamSynchronize(st));
     A.release(dense);
-    coarse_factor<float2>(A, d32, N, &C0.Lp32, &C0.Up32, info, st);
+    coarse_factor<float2>(A, d32, N, &C0.Lp32, &C0.Up32, info, !(S.op.flags & DPGMG_FLAG_CUDA_CORES), st);
     A.release(d32);
   } else {
-    coarse_factor<double2>(A, dense, N, &C0.Lp64, &C0.Up64, info, st);
+    coarse_factor<double2>(A, dense, N, &C0.Lp64, &C0.Up64, info, false, st);
     A.release(dense);
   }
   C0.has_coarse = true;

@@ -5,6 +5,7 @@
 #include <cmath>
 #include <map>
 #include <stdexcept>
+#include <thread>
 #include <tuple>
 
 namespace dpgmg {
@@ -363,42 +364,94 @@ std::vector<LevelSpec> plan_levels(const int n[3], int p, int n_levels, int p_mi
 }
 
 // ------------------------------------------------------------------- ECSR
+// Runs body(lo, hi) over [0, n) on up to 16 host threads (contiguous ranges).
+template <class F>
+static void parallel_ranges(int64_t n, F&& body) {
+  const int64_t hw = std::max<int64_t>(1, (int64_t)std::thread::hardware_concurrency());
+  const int64_t nt = std::min<int64_t>({hw, (int64_t)16, std::max<int64_t>(1, n / 256)});
+  if (nt <= 1) {
+    body((int64_t)0, n);
+    return;
+  }
+  std::vector<std::thread> th;
+  for (int64_t t = 0; t < nt; ++t) th.emplace_back([&, t]() { body(n * t / nt, n * (t + 1) / nt); });
+  for (auto& x : th) x.join();
+}
+
 ECSRHost build_ecsr(const MeshL& m, const std::vector<std::vector<int64_t>>& groups) {
   ECSRHost A;
   A.nrows = m.ndof;
-  std::vector<std::vector<int32_t>> ent_groups(m.nent);
-  for (size_t g = 0; g < groups.size(); ++g)
-    for (int64_t E : groups[g]) ent_groups[E].push_back((int32_t)g);
-  A.row_ent.assign(m.ndof, -1);
-  A.col_ptr.push_back(0);
-  A.val_ptr.push_back(0);
-  std::vector<int64_t> cols;
+  // entity -> groups containing it (CSR)
+  std::vector<int64_t> eg_ptr(m.nent + 1, 0);
+  for (const auto& g : groups)
+    for (int64_t E : g) ++eg_ptr[E + 1];
+  for (int64_t E = 0; E < m.nent; ++E) eg_ptr[E + 1] += eg_ptr[E];
+  std::vector<int32_t> eg(eg_ptr.back());
+  {
+    std::vector<int64_t> fill(eg_ptr.begin(), eg_ptr.end() - 1);
+    for (size_t g = 0; g < groups.size(); ++g)
+      for (int64_t E : groups[g]) eg[fill[E]++] = (int32_t)g;
+  }
+  // row entities in entity order
+  std::vector<int64_t> rows;
   for (int64_t E = 0; E < m.nent; ++E) {
-    if (ent_groups[E].empty()) continue;
+    if (eg_ptr[E + 1] == eg_ptr[E]) continue;
     int64_t st;
     int nd;
     m.ent_range(E, &st, &nd);
-    if (nd == 0) continue;
-    cols.clear();
-    for (int32_t g : ent_groups[E])
-      for (int64_t F : groups[g]) cols.push_back(F);
-    std::sort(cols.begin(), cols.end());
-    cols.erase(std::unique(cols.begin(), cols.end()), cols.end());
-    int64_t nnz_row = 0;
-    for (int64_t F : cols) {
-      int64_t fs;
-      int fn;
-      m.ent_range(F, &fs, &fn);
-      for (int k = 0; k < fn; ++k) A.col_idx.push_back((int32_t)(fs + k));
-      nnz_row += fn;
-    }
-    int32_t id = (int32_t)A.ent_start.size();
-    A.ent_start.push_back(st);
-    A.ent_nd.push_back(nd);
-    A.col_ptr.push_back((int64_t)A.col_idx.size());
-    A.val_ptr.push_back(A.val_ptr.back() + nnz_row * nd);
-    for (int k = 0; k < nd; ++k) A.row_ent[st + k] = id;
+    if (nd > 0) rows.push_back(E);
   }
+  const int64_t R = (int64_t)rows.size();
+  // per row entity: sorted distinct column entities and their DOF count
+  std::vector<std::vector<int64_t>> nb(R);
+  std::vector<int64_t> ncol(R);
+  parallel_ranges(R, [&](int64_t lo, int64_t hi) {
+    std::vector<int64_t> cols;
+    for (int64_t r = lo; r < hi; ++r) {
+      const int64_t E = rows[r];
+      cols.clear();
+      for (int64_t q = eg_ptr[E]; q < eg_ptr[E + 1]; ++q)
+        for (int64_t F : groups[eg[q]]) cols.push_back(F);
+      std::sort(cols.begin(), cols.end());
+      cols.erase(std::unique(cols.begin(), cols.end()), cols.end());
+      int64_t c = 0;
+      for (int64_t F : cols) {
+        int64_t fs;
+        int fn;
+        m.ent_range(F, &fs, &fn);
+        c += fn;
+      }
+      nb[r] = cols;
+      ncol[r] = c;
+    }
+  });
+  A.row_ent.assign(m.ndof, -1);
+  A.ent_start.resize(R);
+  A.ent_nd.resize(R);
+  A.col_ptr.assign(R + 1, 0);
+  A.val_ptr.assign(R + 1, 0);
+  for (int64_t r = 0; r < R; ++r) {
+    int64_t st;
+    int nd;
+    m.ent_range(rows[r], &st, &nd);
+    A.ent_start[r] = st;
+    A.ent_nd[r] = nd;
+    A.col_ptr[r + 1] = A.col_ptr[r] + ncol[r];
+    A.val_ptr[r + 1] = A.val_ptr[r] + ncol[r] * nd;
+    for (int k = 0; k < nd; ++k) A.row_ent[st + k] = (int32_t)r;
+  }
+  A.col_idx.resize(A.col_ptr[R]);
+  parallel_ranges(R, [&](int64_t lo, int64_t hi) {
+    for (int64_t r = lo; r < hi; ++r) {
+      int32_t* out = A.col_idx.data() + A.col_ptr[r];
+      for (int64_t F : nb[r]) {
+        int64_t fs;
+        int fn;
+        m.ent_range(F, &fs, &fn);
+        for (int k = 0; k < fn; ++k) *out++ = (int32_t)(fs + k);
+      }
+    }
+  });
   return A;
 }
 

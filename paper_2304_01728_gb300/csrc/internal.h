@@ -25,6 +25,8 @@ void set_last_error(const std::string& m);
       throw ::dpgmg::Err{DPGMG_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)}; \
   } while (0)
 void count_launch();
+void count_launches(long long n);
+long long thread_launch_count();
 #define DPG_CHECK_LAUNCH()            \
   do {                                \
     ::dpgmg::count_launch();          \
@@ -137,6 +139,9 @@ struct SystemImpl {
   void* ws = nullptr;            // solver workspace
   int prof_which = 0;            // DPGMG_PROF_* being bracketed with events
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> prof_events;
+  std::vector<int> prof_graph_pairs;   // pairs recorded by a captured graph (re-read after each replay)
+  double prof_graph_ms = 0.0;          // accumulated time of graph-recorded pairs
+  long long prof_graph_n = 0;          // and their number of timed launches
   int64_t prof_bytes = 0;
   int coarse_blocks = 0;
 };

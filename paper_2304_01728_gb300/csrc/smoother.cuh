@@ -50,20 +50,20 @@ __global__ void __launch_bounds__(256) k_patch_apply(const int64_t* __restrict__
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int a = ch.y + lane;
   const C* M = inv + vptr[j] + a;
-  // eight independent row loads in flight per thread
-  C acc[4] = {O::zero(), O::zero(), O::zero(), O::zero()};
+  C a0 = O::zero(), a1 = O::zero(), a2 = O::zero(), a3 = O::zero();
   if (a < n) {
     int k = w;
-    for (; k + 56 < n; k += 64) {
-      C m[8];
-#pragma unroll
-      for (int u = 0; u < 8; ++u) m[u] = M[(size_t)(k + 8 * u) * n];
-#pragma unroll
-      for (int u = 0; u < 8; ++u) acc[u & 3] = O::fmac(rj[k + 8 * u], m[u], acc[u & 3]);
+    for (; k + 24 < n; k += 32) {
+      const C m0 = M[(size_t)k * n], m1 = M[(size_t)(k + 8) * n];
+      const C m2 = M[(size_t)(k + 16) * n], m3 = M[(size_t)(k + 24) * n];
+      a0 = O::fmac(rj[k], m0, a0);
+      a1 = O::fmac(rj[k + 8], m1, a1);
+      a2 = O::fmac(rj[k + 16], m2, a2);
+      a3 = O::fmac(rj[k + 24], m3, a3);
     }
-    for (; k < n; k += 8) acc[0] = O::fmac(rj[k], M[(size_t)k * n], acc[0]);
+    for (; k < n; k += 8) a0 = O::fmac(rj[k], M[(size_t)k * n], a0);
   }
-  part[w][lane] = O::add(O::add(acc[0], acc[1]), O::add(acc[2], acc[3]));
+  part[w][lane] = O::add(O::add(a0, a1), O::add(a2, a3));
   __syncthreads();
   if (w == 0 && a < n) {
     C s = part[0][lane];

@@ -38,18 +38,41 @@ template <> struct Prec<float2> {
 
 // ------------------------------------------------------------ profiling
 // Events bracketing one chosen kernel (DPGMG_PROF_*) on the launching stream.
+// Inside a stream capture the two records become event-record nodes of the
+// graph; such pairs are read after every replay (prof_graph_accumulate).
+static bool capturing(cudaStream_t st) {
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  DPG_CUDA(cudaStreamIsCapturing(st, &cs));
+  return cs == cudaStreamCaptureStatusActive;
+}
 static int prof_begin(SystemImpl* S, cudaStream_t st) {
   if (!S) return -1;
   cudaEvent_t a, b;
   DPG_CUDA(cudaEventCreate(&a));
   DPG_CUDA(cudaEventCreate(&b));
-  DPG_CUDA(cudaEventRecord(a, st));
+  const int idx = (int)S->prof_events.size();
   S->prof_events.emplace_back(a, b);
-  return (int)S->prof_events.size() - 1;
+  if (capturing(st)) {
+    DPG_CUDA(cudaEventRecordWithFlags(a, st, cudaEventRecordExternal));
+    S->prof_graph_pairs.push_back(idx);
+  } else {
+    DPG_CUDA(cudaEventRecord(a, st));
+  }
+  return idx;
 }
 static void prof_end(SystemImpl* S, int idx, cudaStream_t st) {
   if (!S || idx < 0) return;
-  DPG_CUDA(cudaEventRecord(S->prof_events[idx].second, st));
+  if (capturing(st)) DPG_CUDA(cudaEventRecordWithFlags(S->prof_events[idx].second, st, cudaEventRecordExternal));
+  else DPG_CUDA(cudaEventRecord(S->prof_events[idx].second, st));
+}
+// after a replay has completed: add the times of the graph's event pairs
+static void prof_graph_accumulate(SystemImpl& S) {
+  for (int idx : S.prof_graph_pairs) {
+    float t = 0.f;
+    DPG_CUDA(cudaEventElapsedTime(&t, S.prof_events[idx].first, S.prof_events[idx].second));
+    S.prof_graph_ms += t;
+    ++S.prof_graph_n;
+  }
 }
 
 void profile_clear(SystemImpl& S) {
@@ -58,18 +81,26 @@ void profile_clear(SystemImpl& S) {
     cudaEventDestroy(e.second);
   }
   S.prof_events.clear();
+  S.prof_graph_pairs.clear();
+  S.prof_graph_ms = 0.0;
+  S.prof_graph_n = 0;
 }
 
 void profile_read(SystemImpl& S, double* ms, long long* launches, long long* bytes) {
-  double tot = 0.0;
-  for (auto& e : S.prof_events) {
-    DPG_CUDA(cudaEventSynchronize(e.second));
+  double tot = S.prof_graph_ms;
+  long long n = S.prof_graph_n;
+  std::vector<char> in_graph(S.prof_events.size(), 0);
+  for (int idx : S.prof_graph_pairs) in_graph[idx] = 1;
+  for (size_t i = 0; i < S.prof_events.size(); ++i) {
+    if (in_graph[i]) continue;
+    DPG_CUDA(cudaEventSynchronize(S.prof_events[i].second));
     float t = 0.f;
-    DPG_CUDA(cudaEventElapsedTime(&t, e.first, e.second));
+    DPG_CUDA(cudaEventElapsedTime(&t, S.prof_events[i].first, S.prof_events[i].second));
     tot += t;
+    ++n;
   }
   if (ms) *ms = tot;
-  if (launches) *launches = (long long)S.prof_events.size();
+  if (launches) *launches = n;
   if (bytes) *bytes = S.prof_bytes;
   profile_clear(S);
 }
@@ -514,7 +545,7 @@ struct WS {
   std::vector<LevelWS<float2>> w32;
   double2 *x = nullptr, *r = nullptr, *p = nullptr, *q = nullptr, *z = nullptr, *part = nullptr, *sc = nullptr;
   float2 *xh = nullptr, *xl = nullptr;     // double-float split of the CG operand
-  double2 sc_host[SC_COUNT];     // scalar read-back (a few bytes per CG step)
+  double2* sc_host = nullptr;    // pinned scalar read-back (a few bytes per CG step)
   int* err = nullptr;
   ECSRDev Acg;                   // the CG operator (finest A_L, FP64)
   bool acg_owned = false;
@@ -556,6 +587,7 @@ void ensure_workspace(SystemImpl& S, cudaStream_t st) {
   W->xh = S.mem.arr<float2>((size_t)n);
   W->xl = S.mem.arr<float2>((size_t)n);
   W->sc = S.mem.arr<double2>(SC_COUNT);
+  DPG_CUDA(cudaMallocHost(&W->sc_host, SC_COUNT * sizeof(double2)));
   W->err = S.mem.arr<int>(1);
   DPG_CUDA(cudaMemsetAsync(W->err, 0, sizeof(int), st));
   alloc_level_ws<double2>(*W, S);
@@ -566,6 +598,7 @@ void ensure_workspace(SystemImpl& S, cudaStream_t st) {
 void free_workspace(SystemImpl& S) {
   if (!S.ws) return;
   WS* W = reinterpret_cast<WS*>(S.ws);
+  if (W->sc_host) cudaFreeHost(W->sc_host);
   delete W;
   S.ws = nullptr;
 }
@@ -723,6 +756,54 @@ static const ECSRDev& cg_operator(SystemImpl& S, WS& W, cudaStream_t st) {
   return W.Acg;
 }
 
+// One CG step (V-cycle, direction update, CG operator, scalar read-back) as a
+// CUDA graph: captured on the second iteration, replayed after that.  The
+// launch sequence of a step does not change between iterations, and every
+// buffer it touches lives as long as the system.  If the stream cannot be
+// captured (the legacy default stream), the step runs eagerly.
+struct PcgGraph {
+  cudaGraphExec_t exec = nullptr;
+  long long nodes = 0;
+  bool failed = false;
+  template <class F> bool ready(cudaStream_t st, F&& body) {
+    if (exec) return true;
+    if (failed) return false;
+    if (cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+      cudaGetLastError();
+      failed = true;
+      return false;
+    }
+    const long long l0 = thread_launch_count();
+    cudaGraph_t g = nullptr;
+    try {
+      body();
+    } catch (...) {
+      cudaStreamEndCapture(st, &g);
+      if (g) cudaGraphDestroy(g);
+      throw;
+    }
+    DPG_CUDA(cudaStreamEndCapture(st, &g));
+    nodes = thread_launch_count() - l0;
+    count_launches(-nodes);   // captured, not yet run
+    const cudaError_t e = cudaGraphInstantiate(&exec, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      exec = nullptr;
+      failed = true;
+      return false;
+    }
+    return true;
+  }
+  void launch(cudaStream_t st) {
+    DPG_CUDA(cudaGraphLaunch(exec, st));
+    count_launches(nodes);
+  }
+  ~PcgGraph() {
+    if (exec) cudaGraphExecDestroy(exec);
+  }
+};
+
 int pcg_solve(SystemImpl& S, cudaStream_t st, double2* xout, dpgmg_stats* stats) {
   ensure_workspace(S, st);
   WS& W = *reinterpret_cast<WS*>(S.ws);
@@ -750,29 +831,47 @@ int pcg_solve(SystemImpl& S, cudaStream_t st, double2* xout, dpgmg_stats* stats)
   int it = 0;
   double rel = 1.0;
   if (nb > 0.0) {
-    precondition(S, W, W.r, W.z, st);
-    dot(W, W.z, W.r, n, 3, st);   // rho = z^H r
-    DPG_CUDA(cudaMemcpyAsync(W.p, W.z, (size_t)n * sizeof(double2), cudaMemcpyDeviceToDevice, st));
     SystemImpl* pcg_prof = S.prof_which == DPGMG_PROF_SPMV_CG ? &S : nullptr;
-    while (it < S.op.max_iter) {
+    // q = A p, alpha = rho / p^H q, x += alpha p, r -= alpha q, ||r||^2, scalars to the host
+    auto tail = [&]() {
       spmv_df(A, W.p, nullptr, W.q, 0, W.xh, W.xl, st, pcg_prof);
-      dot(W, W.p, W.q, n, 0, st);   // pq = p^H q, alpha = rho / pq
+      dot(W, W.p, W.q, n, 0, st);   // pq = p^H q
       k_cg_update<<<RED_BLOCKS, 256, 0, st>>>(W.x, W.r, W.p, W.q, W.sc, n, W.part);
       DPG_CHECK_LAUNCH();
       k_dot_finish<<<1, 256, 0, st>>>(W.part, RED_BLOCKS, W.sc, 1);
       DPG_CHECK_LAUNCH();
       DPG_CUDA(cudaMemcpyAsync(W.sc_host, W.sc, SC_COUNT * sizeof(double2), cudaMemcpyDeviceToHost, st));
+    };
+    // z = B r, rho_new = z^H r, beta = rho_new / rho, p = z + beta p
+    auto head = [&]() {
+      precondition(S, W, W.r, W.z, st);
+      dot(W, W.z, W.r, n, 2, st);
+      k_cg_dir<<<RED_BLOCKS, 256, 0, st>>>(W.p, W.z, W.sc, n);
+      DPG_CHECK_LAUNCH();
+    };
+    precondition(S, W, W.r, W.z, st);
+    dot(W, W.z, W.r, n, 3, st);   // rho = z^H r
+    DPG_CUDA(cudaMemcpyAsync(W.p, W.z, (size_t)n * sizeof(double2), cudaMemcpyDeviceToDevice, st));
+    tail();
+    PcgGraph G;
+    const bool graphs = !(S.op.flags & DPGMG_FLAG_EAGER);
+    bool replayed = false;
+    while (true) {
       DPG_CUDA(cudaStreamSynchronize(st));
+      if (replayed) prof_graph_accumulate(S);
       ++it;
       const double pq = W.sc_host[SC_PQ].x;
       if (!(pq > 0.0) || !std::isfinite(pq)) { status = DPGMG_ERR_BREAKDOWN; break; }
       rel = std::sqrt(W.sc_host[SC_RR].x) / nb;
       if (!std::isfinite(rel)) { status = DPGMG_ERR_BREAKDOWN; break; }
-      if (rel <= S.op.tol) break;
-      precondition(S, W, W.r, W.z, st);
-      dot(W, W.z, W.r, n, 2, st);   // rho_new = z^H r, beta
-      k_cg_dir<<<RED_BLOCKS, 256, 0, st>>>(W.p, W.z, W.sc, n);
-      DPG_CHECK_LAUNCH();
+      if (rel <= S.op.tol || it >= S.op.max_iter) break;
+      if (graphs && G.ready(st, [&]() { head(); tail(); })) {
+        G.launch(st);
+        replayed = true;
+      } else {
+        head();
+        tail();
+      }
     }
     if (status == DPGMG_OK && rel > S.op.tol) status = DPGMG_ERR_NOT_CONVERGED;
   }

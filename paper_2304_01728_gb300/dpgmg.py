@@ -21,6 +21,7 @@ DPGMG_ERR_NOT_CONVERGED, DPGMG_ERR_TIMEOUT, DPGMG_ERR_PENDING, DPGMG_ERR_CUDA = 
 SRC_GAUSSIAN, SRC_PLANE_WAVE, SRC_MANUFACTURED = 0, 1, 2
 PREC_FP64, PREC_MIXED = 0, 1
 COARSEST_CHOLESKY, COARSEST_NONE, COARSEST_AUTO = 0, 1, 2
+FLAG_EAGER, FLAG_CUDA_CORES = 1, 2
 OP_A, OP_SMOOTH, OP_VCYCLE, OP_RESTRICT, OP_PROLONG, OP_CONDENSE, OP_COARSE, OP_AFULL = range(8)
 
 
@@ -42,7 +43,8 @@ class dpgmg_problem(ctypes.Structure):
 class dpgmg_opts(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("max_iter", ctypes.c_int), ("nu_pre", ctypes.c_int),
                 ("nu_post", ctypes.c_int), ("n_levels", ctypes.c_int), ("p_min", ctypes.c_int),
-                ("precision", ctypes.c_int), ("coarsest", ctypes.c_int), ("theta", ctypes.c_double)]
+                ("precision", ctypes.c_int), ("coarsest", ctypes.c_int), ("flags", ctypes.c_int),
+                ("theta", ctypes.c_double)]
 
 
 class dpgmg_stats(ctypes.Structure):

@@ -255,6 +255,47 @@ def test_coarsest_auto_rule(n, expect):
     assert rel(out["auto"][0], out[expect][0]) < 1e-6
 
 
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("mixed", 1e-6)])
+def test_graph_replay_matches_eager(precision, tol):
+    """CG steps replayed from the captured graph give the eager result with
+    the same iteration count and the same number of kernel launches."""
+    w = workloads.config1()
+    out = {}
+    for flags in (0, D.FLAG_EAGER):
+        ok = dict(w["opts"], precision=precision, flags=flags)
+        with D.Solver(w["problem"], **ok) as s:
+            l0 = D.dpgmg_launch_count()
+            x, f, st, code = s.solve()
+            out[flags] = (x, st.iters, D.dpgmg_launch_count() - l0)
+        assert code == D.DPGMG_OK
+    assert out[0][1] == out[D.FLAG_EAGER][1]
+    assert out[0][2] == out[D.FLAG_EAGER][2]
+    assert rel(out[0][0], out[D.FLAG_EAGER][0]) < tol
+
+
+@pytest.mark.parametrize("n", [4, 6])
+def test_coarse_factor_on_tensor_cores(n):
+    """Mixed path: the complex64 coarsest factor built with tensor-core
+    (3xTF32) updates solves level 0 as accurately as the CUDA-core FP32
+    factor.  Level 0 has 269 (n = 4) and 883 (n = 6) DOFs: several 64-wide
+    tiles with a ragged last one."""
+    import scipy.linalg as sla
+    w = workloads.config1()
+    pk = dict(w["problem"], n=(n, n, n))
+    ok = dict(w["opts"], precision="mixed")
+    _, _, _, levels = oracle_system(pk, ok)
+    o0 = levels[0]
+    x = rand_vec(o0.mesh.n_dof, 7)
+    y_ref = sla.cho_solve(o0.chol, x)
+    y = {}
+    for flags in (0, D.FLAG_CUDA_CORES):
+        with D.Solver(pk, **dict(ok, flags=flags)) as s:
+            y[flags] = D.dpgmg_apply(s.h, s.s, D.OP_COARSE, 0, x, o0.mesh.n_dof)
+    e_tc, e_cc = rel(y[0], y_ref), rel(y[D.FLAG_CUDA_CORES], y_ref)
+    assert e_cc < 1e-3 and e_tc < 1e-3, (e_tc, e_cc)
+    assert e_tc < 4 * e_cc + 1e-6, (e_tc, e_cc)
+
+
 def test_error_statuses():
     w = workloads.config1()
     h = D.dpgmg_create(0)
