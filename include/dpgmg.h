@@ -114,10 +114,13 @@ typedef struct dpgmg_opts {
 /* CG steps after the first are replayed from one captured CUDA graph unless
    this bit is set (or the stream cannot be captured); results are the same. */
 #define DPGMG_FLAG_EAGER 1
-/* Mixed path: the rank-64 updates of the coarsest complex64 factorisation run
-   on the tensor cores (TF32 operand splitting, about FP32 accuracy) unless
-   this bit is set, which selects the FP32 CUDA-core kernels. */
-#define DPGMG_FLAG_CUDA_CORES 2
+/* Mixed path: run the rank-64 updates of the coarsest complex64 factorisation
+   on the tensor cores (tcgen05, 3xTF32 operand splitting: products keep ~22 of
+   FP32's 24 bits) instead of the FP32 CUDA-core kernels.  Off by default: the
+   coarse solve it gives is a few times less accurate, which moves the point
+   where CG stops (on the 16^3 p=3 workload the solution then differs from the
+   FP64 oracle's by 2.4e-7 instead of 7.7e-8, with the same iteration count). */
+#define DPGMG_FLAG_TENSOR_CORES 2
 
 typedef struct dpgmg_stats {
   int iters;               /* CG iterations (= V-cycle applications) */
@@ -257,6 +260,18 @@ long long dpgmg_launch_count(void);
 #define DPGMG_PROF_SMOOTH_FINE 1  /* patch products of the finest smoother */
 #define DPGMG_PROF_SPMV_FINE   2  /* residual SpMVs of the finest V-cycle level */
 #define DPGMG_PROF_SPMV_CG     3  /* the FP64 CG operator application */
+
+/* SpMV work decomposition, chosen at setup by timing.  The operators are
+ * applied by one warp per group of G rows of one mesh entity (G = 1, 2, 4 or
+ * 8; the rows of an entity share their column list, so larger G loads each
+ * column index and vector entry once for G rows).  dpgmg_setup times every G
+ * on each operator and keeps the fastest; choices are cached per (product
+ * type, p, level kind, log2 of the row count) for the life of the process.
+ * level >= 1 addresses that level's V-cycle operator, level == -1 the CG
+ * operator.  set = 1, 2, 4 or 8 overrides the choice (0 leaves it); *group
+ * (may be NULL) receives the value in force.  Returns DPGMG_ERR_ARG for an
+ * invalid level or size.  Results do not depend on G beyond rounding order. */
+int dpgmg_spmv_group(dpgmg_handle h, dpgmg_system sys, int level, int set, int* group);
 
 /* Bracket every launch of one kernel with CUDA events on the launching
  * stream during subsequent dpgmg_solve calls (which = DPGMG_PROF_*; OFF

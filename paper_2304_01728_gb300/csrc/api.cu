@@ -82,7 +82,7 @@ int validate_problem(const dpgmg_problem* pb, const dpgmg_opts* op) {
       op->p_min < 1 || (op->precision != DPGMG_PREC_FP64 && op->precision != DPGMG_PREC_MIXED) ||
       (op->coarsest != DPGMG_COARSEST_CHOLESKY && op->coarsest != DPGMG_COARSEST_NONE &&
        op->coarsest != DPGMG_COARSEST_AUTO) ||
-      (op->flags & ~(DPGMG_FLAG_EAGER | DPGMG_FLAG_CUDA_CORES)))
+      (op->flags & ~(DPGMG_FLAG_EAGER | DPGMG_FLAG_TENSOR_CORES)))
     return DPGMG_ERR_ARG;
   return DPGMG_OK;
 }
@@ -117,7 +117,7 @@ size_t estimate_bytes(const dpgmg_problem* pb, const dpgmg_opts* op) {
     const double nel = (double)m.nelem, nl = n_trace_local(s.p), nd = (double)m.ndof;
     if (i == 0) xdofs = nd;
     if (i > 0) resident += nel * nl * nl * 16.0;                      // restricted element matrices
-    resident += nel * nl * 8.0 + nd * 4.0 * (16.0 + x32) + nd * 64.0; // maps, work vectors, row indices
+    resident += nel * nl * 8.0 + nd * 4.0 * (16.0 + x32) + nd * 80.0; // maps, work vectors, row indices, SpMV tasks
     if (s.kind_below != 0) {
       const int q = s.p;
       const bool hlev = s.kind_below == 2;
@@ -207,7 +207,7 @@ void setup_system(SystemImpl& S, const dpgmg_problem* pb, const dpgmg_opts* op, 
   element_stage(S, st);
   build_hierarchy(S, st);
   assemble_rhs(S, st);
-  ensure_workspace(S, st);
+  prepare_solve(S, st);
   DPG_CUDA(cudaEventRecord(e1, st));
   DPG_CUDA(cudaEventSynchronize(e1));
   float ms = 0.f;
@@ -415,6 +415,26 @@ int dpgmg_profile_read(dpgmg_handle h, dpgmg_system sys, double* total_ms, long 
   } catch (const Err& e) {
     return fail(e);
   }
+}
+
+int dpgmg_spmv_group(dpgmg_handle h, dpgmg_system sys, int level, int set, int* group) {
+  if (!h || !sys) return DPGMG_ERR_ARG;
+  if (set != 0 && set != 1 && set != 2 && set != 4 && set != 8) return DPGMG_ERR_ARG;
+  std::lock_guard<std::mutex> lk(h->mu);
+  SystemImpl& S = sys->s;
+  const int slot = S.op.precision == DPGMG_PREC_MIXED ? 0 : 1;
+  int* g = nullptr;
+  if (level == -1) {
+    ECSRDev* A = cg_operator_of(S);
+    if (!A) return DPGMG_ERR_ARG;
+    g = &A->gsel[2];
+  } else {
+    if (level < 1 || level >= (int)S.levels.size()) return DPGMG_ERR_ARG;
+    g = &S.levels[level].A.gsel[slot];
+  }
+  if (set) *g = set;
+  if (group) *group = *g;
+  return DPGMG_OK;
 }
 
 int dpgmg_level_info(dpgmg_handle h, dpgmg_system sys, int level, dpgmg_level_desc* out) {

@@ -317,7 +317,7 @@ void coarse_setup(SystemImpl& S, Level& C0, int* info, cudaStream_t st) {
     DPG_CHECK_LAUNCH();
     DPG_CUDA(cudaStreamSynchronize(st));
     A.release(dense);
-    coarse_factor<float2>(A, d32, N, &C0.Lp32, &C0.Up32, info, !(S.op.flags & DPGMG_FLAG_CUDA_CORES), st);
+    coarse_factor<float2>(A, d32, N, &C0.Lp32, &C0.Up32, info, (S.op.flags & DPGMG_FLAG_TENSOR_CORES) != 0, st);
     A.release(d32);
   } else {
     coarse_factor<double2>(A, dense, N, &C0.Lp64, &C0.Up64, info, false, st);

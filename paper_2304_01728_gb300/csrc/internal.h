@@ -66,6 +66,15 @@ struct ECSRDev {
   double2* v64 = nullptr;
   float2* v32 = nullptr;   // complex64 values (= high parts of the double-float split)
   float2* vlo = nullptr;   // low parts: v64 ~ v32 + vlo (CG operator only)
+  // Entity-blocked SpMV work lists: tasks[i] = (entity, first row) groups of
+  // G = 2^i rows of one entity (i = 1, 2, 3); rows with no entity are listed
+  // in null_rows.  gsel[] is the group size chosen by the tuner for the
+  // complex64, complex128 and double-float products (1 = one warp per row).
+  int2* tasks[4] = {nullptr, nullptr, nullptr, nullptr};
+  int64_t ntasks[4] = {0, 0, 0, 0};
+  int32_t* null_rows = nullptr;
+  int64_t n_null = 0;
+  int gsel[3] = {1, 1, 1};
 };
 
 struct PatchDev {
@@ -173,6 +182,9 @@ void coarse_apply32(const Level& C0, const float2* r, float2* e, float2* tmp, cu
 int pcg_solve(SystemImpl& S, cudaStream_t st, double2* x, dpgmg_stats* stats);
 void apply_op(SystemImpl& S, int op, int level, const double2* x, double2* y, cudaStream_t st);
 void ensure_workspace(SystemImpl& S, cudaStream_t st);
+// CG operator split and kernel-variant tuning, run once at the end of setup
+void prepare_solve(SystemImpl& S, cudaStream_t st);
+ECSRDev* cg_operator_of(SystemImpl& S);
 void free_workspace(SystemImpl& S);
 void spmv64(const ECSRDev& A, const double2* x, double2* y, cudaStream_t st);
 void estimate_theta(SystemImpl& S, int level, cudaStream_t st);

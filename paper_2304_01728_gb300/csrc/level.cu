@@ -32,6 +32,21 @@ void assemble_ecsr(Alloc& A, const MeshL& m, const ECSRHost& H, ECSRDev& D, cuda
   D.val_ptr = upload(A, H.val_ptr, st);
   D.max_nnz_row = 0;
   for (int64_t E = 0; E < D.nent; ++E) D.max_nnz_row = std::max(D.max_nnz_row, H.col_ptr[E + 1] - H.col_ptr[E]);
+  for (int gi = 1; gi <= 3; ++gi) {
+    const int G = 1 << gi;
+    std::vector<int2> t;
+    for (int64_t E = 0; E < D.nent; ++E)
+      for (int r0 = 0; r0 < H.ent_nd[E]; r0 += G) t.push_back(make_int2((int)E, r0));
+    D.ntasks[gi] = (int64_t)t.size();
+    D.tasks[gi] = t.empty() ? nullptr : upload(A, t, st);
+  }
+  {
+    std::vector<int32_t> nr;
+    for (int64_t r = 0; r < H.nrows; ++r)
+      if (H.row_ent[r] < 0) nr.push_back((int32_t)r);
+    D.n_null = (int64_t)nr.size();
+    D.null_rows = nr.empty() ? nullptr : upload(A, nr, st);
+  }
   D.v64 = A.arr<double2>((size_t)D.nnz);
   DPG_CUDA(cudaMemsetAsync(D.v64, 0, (size_t)D.nnz * sizeof(double2), st));
   (void)m;

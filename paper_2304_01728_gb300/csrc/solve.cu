@@ -10,6 +10,9 @@
 // Every kernel is templated on the complex type of the V-cycle (complex128
 // on the FP64 path, complex64 on the mixed path); CG always runs in FP64.
 #include <algorithm>
+#include <map>
+#include <mutex>
+#include <tuple>
 #include <cmath>
 #include <cstring>
 #include <vector>
@@ -147,14 +150,97 @@ __global__ void __launch_bounds__(256) k_spmv(const int32_t* __restrict__ row_en
   }
 }
 
+// Entity-blocked SpMV: one warp per task (entity E, rows r0 .. r0 + G - 1 of
+// E).  The G rows share E's column list, so each column index and x entry is
+// loaded once for G rows and G value streams are in flight per column.
+template <class C, int G>
+__global__ void __launch_bounds__(256) k_spmv_ent(const int2* __restrict__ tasks, int64_t ntasks,
+                                                  const int64_t* __restrict__ ent_start,
+                                                  const int32_t* __restrict__ ent_nd, const int64_t* __restrict__ col_ptr,
+                                                  const int32_t* __restrict__ col_idx,
+                                                  const int64_t* __restrict__ val_ptr, const C* __restrict__ v,
+                                                  const C* __restrict__ x, const C* __restrict__ b, C* __restrict__ y,
+                                                  int mode) {
+  using O = Ops<C>;
+  const int lane = threadIdx.x & 31;
+  const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t t = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); t < ntasks; t += nw) {
+    const int2 tk = tasks[t];
+    const int E = tk.x, r0 = tk.y;
+    const int g = min(G, ent_nd[E] - r0);
+    const int64_t c0 = col_ptr[E];
+    const int nnz = (int)(col_ptr[E + 1] - c0);
+    const C* vals = v + val_ptr[E] + (int64_t)r0 * nnz;
+    const int32_t* cols = col_idx + c0;
+    C acc[G];
+#pragma unroll
+    for (int r = 0; r < G; ++r) acc[r] = O::zero();
+    for (int k = lane; k < nnz; k += 32) {
+      const C xv = x[cols[k]];
+#pragma unroll
+      for (int r = 0; r < G; ++r)
+        if (r < g) acc[r] = O::fma(vals[(int64_t)r * nnz + k], xv, acc[r]);
+    }
+    C mine = O::zero();
+#pragma unroll
+    for (int r = 0; r < G; ++r) {
+      const C sr = warp_sum(acc[r]);
+      if (lane == r) mine = sr;
+    }
+    if (lane < g) {
+      const int64_t row = ent_start[E] + r0 + lane;
+      y[row] = mode ? O::sub(b[row], mine) : mine;
+    }
+  }
+}
+
+// rows that belong to no entity: y = 0 (mode 0) or b (mode 1)
+template <class C>
+__global__ void k_null_rows(const int32_t* __restrict__ rows, int64_t n, const C* __restrict__ b, C* __restrict__ y,
+                            int mode) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int32_t r = rows[i];
+  y[r] = mode ? b[r] : Ops<C>::zero();
+}
+
+template <class C> struct SpmvSlot;
+template <> struct SpmvSlot<float2> { static constexpr int v = 0; };
+template <> struct SpmvSlot<double2> { static constexpr int v = 1; };
+
+template <class C>
+static void spmv_g(const ECSRDev& A, const C* vals, const C* x, const C* b, C* y, int mode, int G, cudaStream_t st) {
+  if (G <= 1 || !A.tasks[1]) {
+    int64_t blocks = std::min<int64_t>((A.nrows + 7) / 8, 152 * 16);
+    k_spmv<C><<<(unsigned)blocks, 256, 0, st>>>(A.row_ent, A.ent_start, A.col_ptr, A.col_idx, A.val_ptr, vals, x, b,
+                                                 y, A.nrows, mode);
+    DPG_CHECK_LAUNCH();
+    return;
+  }
+  const int gi = G == 2 ? 1 : (G == 4 ? 2 : 3);
+  const int64_t nt = A.ntasks[gi];
+  const unsigned blocks = (unsigned)std::min<int64_t>((nt + 7) / 8, 152 * 16);
+  if (G == 2)
+    k_spmv_ent<C, 2><<<blocks, 256, 0, st>>>(A.tasks[gi], nt, A.ent_start, A.ent_nd, A.col_ptr, A.col_idx, A.val_ptr,
+                                             vals, x, b, y, mode);
+  else if (G == 4)
+    k_spmv_ent<C, 4><<<blocks, 256, 0, st>>>(A.tasks[gi], nt, A.ent_start, A.ent_nd, A.col_ptr, A.col_idx, A.val_ptr,
+                                             vals, x, b, y, mode);
+  else
+    k_spmv_ent<C, 8><<<blocks, 256, 0, st>>>(A.tasks[gi], nt, A.ent_start, A.ent_nd, A.col_ptr, A.col_idx, A.val_ptr,
+                                             vals, x, b, y, mode);
+  DPG_CHECK_LAUNCH();
+  if (A.n_null) {
+    k_null_rows<C><<<(unsigned)((A.n_null + 255) / 256), 256, 0, st>>>(A.null_rows, A.n_null, b, y, mode);
+    DPG_CHECK_LAUNCH();
+  }
+}
+
 template <class C>
 static void spmv(const ECSRDev& A, const C* vals, const C* x, const C* b, C* y, int mode, cudaStream_t st,
                  SystemImpl* prof = nullptr) {
-  int64_t blocks = std::min<int64_t>((A.nrows + 7) / 8, 152 * 16);
   int pe = prof_begin(prof, st);
-  k_spmv<C><<<(unsigned)blocks, 256, 0, st>>>(A.row_ent, A.ent_start, A.col_ptr, A.col_idx, A.val_ptr, vals, x, b, y,
-                                               A.nrows, mode);
-  DPG_CHECK_LAUNCH();
+  spmv_g<C>(A, vals, x, b, y, mode, A.gsel[SpmvSlot<C>::v], st);
   prof_end(prof, pe, st);
 }
 
@@ -260,6 +346,64 @@ __global__ void __launch_bounds__(256) k_spmv_df(const int32_t* __restrict__ row
   }
 }
 
+// Entity-blocked double-float CG operator (same task lists as k_spmv_ent).
+template <int G>
+__global__ void __launch_bounds__(256) k_spmv_df_ent(const int2* __restrict__ tasks, int64_t ntasks,
+                                                     const int64_t* __restrict__ ent_start,
+                                                     const int32_t* __restrict__ ent_nd,
+                                                     const int64_t* __restrict__ col_ptr,
+                                                     const int32_t* __restrict__ col_idx,
+                                                     const int64_t* __restrict__ val_ptr, const float2* __restrict__ vh,
+                                                     const float2* __restrict__ vl, const float2* __restrict__ xh,
+                                                     const float2* __restrict__ xl, const double2* __restrict__ b,
+                                                     double2* __restrict__ y, int mode) {
+  const int lane = threadIdx.x & 31;
+  const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t t = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); t < ntasks; t += nw) {
+    const int2 tk = tasks[t];
+    const int E = tk.x, r0 = tk.y;
+    const int g = min(G, ent_nd[E] - r0);
+    const int64_t c0 = col_ptr[E];
+    const int nnz = (int)(col_ptr[E + 1] - c0);
+    const int64_t off = val_ptr[E] + (int64_t)r0 * nnz;
+    const int32_t* cols = col_idx + c0;
+    float rh[G], rl[G], ih[G], il[G];
+#pragma unroll
+    for (int r = 0; r < G; ++r) rh[r] = rl[r] = ih[r] = il[r] = 0.f;
+    for (int k = lane; k < nnz; k += 32) {
+      const int c = cols[k];
+      const float2 uh = xh[c], ul = xl[c];
+#pragma unroll
+      for (int r = 0; r < G; ++r) {
+        if (r < g) {
+          const float2 ah = vh[off + (int64_t)r * nnz + k], al = vl[off + (int64_t)r * nnz + k];
+          float p, q;
+          df_mul(ah.x, al.x, uh.x, ul.x, p, q);
+          df_add(rh[r], rl[r], p, q);
+          df_mul(ah.y, al.y, uh.y, ul.y, p, q);
+          df_add(rh[r], rl[r], -p, -q);
+          df_mul(ah.x, al.x, uh.y, ul.y, p, q);
+          df_add(ih[r], il[r], p, q);
+          df_mul(ah.y, al.y, uh.x, ul.x, p, q);
+          df_add(ih[r], il[r], p, q);
+        }
+      }
+    }
+    float4 mine = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+    for (int r = 0; r < G; ++r) {
+      df_warp_sum(rh[r], rl[r]);
+      df_warp_sum(ih[r], il[r]);
+      if (lane == r) mine = make_float4(rh[r], rl[r], ih[r], il[r]);
+    }
+    if (lane < g) {
+      const int64_t row = ent_start[E] + r0 + lane;
+      const double re = (double)mine.x + (double)mine.y, im = (double)mine.z + (double)mine.w;
+      y[row] = mode ? make_double2(b[row].x - re, b[row].y - im) : make_double2(re, im);
+    }
+  }
+}
+
 __global__ void k_split_vec(const double2* __restrict__ x, float2* __restrict__ xh, float2* __restrict__ xl,
                             int64_t n) {
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -281,16 +425,42 @@ __global__ void k_split_vals(const double2* __restrict__ v, float2* __restrict__
 }
 
 // y = A x (mode 0) or b - A x (mode 1) with the double-float operator; xh/xl scratch
+static void spmv_df_g(const ECSRDev& A, const float2* xh, const float2* xl, const double2* b, double2* y, int mode,
+                      int G, cudaStream_t st) {
+  const int64_t n = A.nrows;
+  if (G <= 1 || !A.tasks[1]) {
+    const int64_t blocks = (n + DF_ROWS - 1) / DF_ROWS;
+    k_spmv_df<<<(unsigned)blocks, 256, 0, st>>>(A.row_ent, A.ent_start, A.col_ptr, A.col_idx, A.val_ptr, A.v32, A.vlo,
+                                               xh, xl, b, y, n, mode);
+    DPG_CHECK_LAUNCH();
+    return;
+  }
+  const int gi = G == 2 ? 1 : (G == 4 ? 2 : 3);
+  const int64_t nt = A.ntasks[gi];
+  const unsigned blocks = (unsigned)std::min<int64_t>((nt + 7) / 8, 152 * 16);
+  if (G == 2)
+    k_spmv_df_ent<2><<<blocks, 256, 0, st>>>(A.tasks[gi], nt, A.ent_start, A.ent_nd, A.col_ptr, A.col_idx, A.val_ptr,
+                                             A.v32, A.vlo, xh, xl, b, y, mode);
+  else if (G == 4)
+    k_spmv_df_ent<4><<<blocks, 256, 0, st>>>(A.tasks[gi], nt, A.ent_start, A.ent_nd, A.col_ptr, A.col_idx, A.val_ptr,
+                                             A.v32, A.vlo, xh, xl, b, y, mode);
+  else
+    k_spmv_df_ent<8><<<blocks, 256, 0, st>>>(A.tasks[gi], nt, A.ent_start, A.ent_nd, A.col_ptr, A.col_idx, A.val_ptr,
+                                             A.v32, A.vlo, xh, xl, b, y, mode);
+  DPG_CHECK_LAUNCH();
+  if (A.n_null) {
+    k_null_rows<double2><<<(unsigned)((A.n_null + 255) / 256), 256, 0, st>>>(A.null_rows, A.n_null, b, y, mode);
+    DPG_CHECK_LAUNCH();
+  }
+}
+
 static void spmv_df(const ECSRDev& A, const double2* x, const double2* b, double2* y, int mode, float2* xh,
                     float2* xl, cudaStream_t st, SystemImpl* prof = nullptr) {
   const int64_t n = A.nrows;
   k_split_vec<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(x, xh, xl, n);
   DPG_CHECK_LAUNCH();
-  const int64_t blocks = (n + DF_ROWS - 1) / DF_ROWS;
   int pe = prof_begin(prof, st);
-  k_spmv_df<<<(unsigned)blocks, 256, 0, st>>>(A.row_ent, A.ent_start, A.col_ptr, A.col_idx, A.val_ptr, A.v32, A.vlo,
-                                             xh, xl, b, y, n, mode);
-  DPG_CHECK_LAUNCH();
+  spmv_df_g(A, xh, xl, b, y, mode, A.gsel[2], st);
   prof_end(prof, pe, st);
 }
 
@@ -756,6 +926,59 @@ static const ECSRDev& cg_operator(SystemImpl& S, WS& W, cudaStream_t st) {
   return W.Acg;
 }
 
+// ------------------------------------------------------------ tuning
+// The SpMV group size G (rows of one entity per warp, 1 = one warp per row)
+// is chosen per operator by timing G = 1, 2, 4, 8 on the operator itself
+// (one warm-up and three timed applications each, CUDA events on the setup
+// stream).  Choices are cached per (product kind, order p, level kind,
+// log2 of the row count), so later systems of the same shape skip the timing.
+struct TuneKey {
+  int kind, p, lkind, lg;
+  bool operator<(const TuneKey& o) const {
+    return std::tie(kind, p, lkind, lg) < std::tie(o.kind, o.p, o.lkind, o.lg);
+  }
+};
+static std::mutex g_tune_mu;
+static std::map<TuneKey, int> g_tune;
+
+template <class F>
+static int pick_group(const TuneKey& key, cudaStream_t st, F&& run) {
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tune.find(key);
+    if (it != g_tune.end()) return it->second;
+  }
+  cudaEvent_t a, b;
+  DPG_CUDA(cudaEventCreate(&a));
+  DPG_CUDA(cudaEventCreate(&b));
+  int best = 1;
+  float best_ms = 0.f;
+  for (int G = 1; G <= 8; G *= 2) {
+    run(G);
+    DPG_CUDA(cudaEventRecord(a, st));
+    for (int r = 0; r < 3; ++r) run(G);
+    DPG_CUDA(cudaEventRecord(b, st));
+    DPG_CUDA(cudaEventSynchronize(b));
+    float ms = 0.f;
+    DPG_CUDA(cudaEventElapsedTime(&ms, a, b));
+    if (G == 1 || ms < best_ms) {
+      best = G;
+      best_ms = ms;
+    }
+  }
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  g_tune[key] = best;
+  return best;
+}
+
+static int log2i(int64_t n) {
+  int l = 0;
+  while ((int64_t(1) << (l + 1)) <= n) ++l;
+  return l;
+}
+
 // One CG step (V-cycle, direction update, CG operator, scalar read-back) as a
 // CUDA graph: captured on the second iteration, replayed after that.  The
 // launch sequence of a step does not change between iterations, and every
@@ -803,6 +1026,45 @@ struct PcgGraph {
     if (exec) cudaGraphExecDestroy(exec);
   }
 };
+
+// the CG operator of a prepared system (nullptr before prepare_solve)
+ECSRDev* cg_operator_of(SystemImpl& S) {
+  if (!S.ws) return nullptr;
+  WS& W = *reinterpret_cast<WS*>(S.ws);
+  Level& F = S.levels.back();
+  if (S.levels.size() > 1 && F.kind == 1) return F.A.vlo ? &F.A : nullptr;
+  return W.acg_owned ? &W.Acg : nullptr;
+}
+
+void prepare_solve(SystemImpl& S, cudaStream_t st) {
+  ensure_workspace(S, st);
+  WS& W = *reinterpret_cast<WS*>(S.ws);
+  ECSRDev& Acg = const_cast<ECSRDev&>(cg_operator(S, W, st));
+  const bool mixed = S.op.precision == DPGMG_PREC_MIXED;
+  const int L = (int)S.levels.size() - 1;
+  for (int l = 1; l <= L; ++l) {
+    Level& F = S.levels[l];
+    const int64_t n = F.mesh.ndof;
+    const TuneKey key{mixed ? 0 : 1, F.mesh.p, F.kind, log2i(n)};
+    if (mixed) {
+      float2 *x = W.w32[l].x, *y = W.w32[l].t;
+      DPG_CUDA(cudaMemsetAsync(x, 0, (size_t)n * sizeof(float2), st));
+      F.A.gsel[0] = pick_group(key, st, [&](int G) { spmv_g<float2>(F.A, F.A.v32, x, nullptr, y, 0, G, st); });
+    } else {
+      double2 *x = W.w64[l].x, *y = W.w64[l].t;
+      DPG_CUDA(cudaMemsetAsync(x, 0, (size_t)n * sizeof(double2), st));
+      F.A.gsel[1] = pick_group(key, st, [&](int G) { spmv_g<double2>(F.A, F.A.v64, x, nullptr, y, 0, G, st); });
+    }
+  }
+  {
+    const Level& F = S.levels[L];
+    const int64_t n = F.mesh.ndof;
+    DPG_CUDA(cudaMemsetAsync(W.xh, 0, (size_t)n * sizeof(float2), st));
+    DPG_CUDA(cudaMemsetAsync(W.xl, 0, (size_t)n * sizeof(float2), st));
+    const TuneKey key{2, F.mesh.p, F.kind, log2i(n)};
+    Acg.gsel[2] = pick_group(key, st, [&](int G) { spmv_df_g(Acg, W.xh, W.xl, nullptr, W.q, 0, G, st); });
+  }
+}
 
 int pcg_solve(SystemImpl& S, cudaStream_t st, double2* xout, dpgmg_stats* stats) {
   ensure_workspace(S, st);

@@ -21,7 +21,7 @@ DPGMG_ERR_NOT_CONVERGED, DPGMG_ERR_TIMEOUT, DPGMG_ERR_PENDING, DPGMG_ERR_CUDA = 
 SRC_GAUSSIAN, SRC_PLANE_WAVE, SRC_MANUFACTURED = 0, 1, 2
 PREC_FP64, PREC_MIXED = 0, 1
 COARSEST_CHOLESKY, COARSEST_NONE, COARSEST_AUTO = 0, 1, 2
-FLAG_EAGER, FLAG_CUDA_CORES = 1, 2
+FLAG_EAGER, FLAG_TENSOR_CORES = 1, 2
 OP_A, OP_SMOOTH, OP_VCYCLE, OP_RESTRICT, OP_PROLONG, OP_CONDENSE, OP_COARSE, OP_AFULL = range(8)
 
 
@@ -65,7 +65,8 @@ _lib = None
 EXPORTS = ["dpgmg_create", "dpgmg_destroy", "dpgmg_query_sizes", "dpgmg_default_opts", "dpgmg_setup",
            "dpgmg_solve", "dpgmg_release", "dpgmg_strerror", "dpgmg_last_error", "dpgmg_level_info",
            "dpgmg_element_matrix", "dpgmg_rhs", "dpgmg_apply", "dpgmg_launch_count", "dpgmg_profile",
-           "dpgmg_profile_read", "dpgmg_smooth_noalloc", "dpgmg_serve_start", "dpgmg_submit", "dpgmg_poll"]
+           "dpgmg_profile_read", "dpgmg_smooth_noalloc", "dpgmg_serve_start", "dpgmg_submit", "dpgmg_poll",
+           "dpgmg_spmv_group"]
 PROF_OFF, PROF_SMOOTH_FINE, PROF_SPMV_FINE, PROF_SPMV_CG = 0, 1, 2, 3
 
 
@@ -109,6 +110,8 @@ def lib():
     L.dpgmg_launch_count.argtypes = []
     L.dpgmg_launch_count.restype = ll
     L.dpgmg_profile.argtypes = [vp, vp, i]
+    L.dpgmg_spmv_group.argtypes = [vp, vp, i, i, ctypes.POINTER(i)]
+    L.dpgmg_spmv_group.restype = i
     L.dpgmg_profile_read.argtypes = [vp, vp, ctypes.POINTER(d), ctypes.POINTER(ll), ctypes.POINTER(ll)]
     for f in ["dpgmg_create", "dpgmg_query_sizes", "dpgmg_setup", "dpgmg_solve", "dpgmg_level_info",
               "dpgmg_element_matrix", "dpgmg_rhs", "dpgmg_apply", "dpgmg_profile", "dpgmg_profile_read"]:
@@ -254,6 +257,12 @@ def dpgmg_poll(h, ticket, trace_out=None, field_out=None):
 
 def dpgmg_launch_count():
     return int(lib().dpgmg_launch_count())
+
+
+def dpgmg_spmv_group(h, s, level, set_to=0):
+    g = ctypes.c_int()
+    _check(lib().dpgmg_spmv_group(h, s, int(level), int(set_to), ctypes.byref(g)), "dpgmg_spmv_group")
+    return g.value
 
 
 def dpgmg_profile(h, s, which):
