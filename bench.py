@@ -259,9 +259,17 @@ def run_gb300(args, rank, world, local_rank):
     trace = torch.empty(2 * n_dof, dtype=torch.float64, device="cuda")
     fields = torch.empty(2 * n_field, dtype=torch.float64, device="cuda")
 
+    tuned = {}
+
     def step(prof=D.PROF_OFF):
         s = D.dpgmg_setup(h, pb, op)
         try:
+            for l in range(1, w["opts"]["n_levels"]):
+                try:
+                    tuned["level%d" % l] = D.dpgmg_spmv_group(h, s, l)
+                except D.DpgmgError:
+                    break
+            tuned["cg"] = D.dpgmg_spmv_group(h, s, -1)
             if prof:
                 D.dpgmg_profile(h, s, prof)
             code, st = D.dpgmg_solve(h, s, trace.data_ptr(), fields.data_ptr(), out_is_device=True)
@@ -373,6 +381,7 @@ def run_gb300(args, rank, world, local_rank):
                      "traffic": traffic_for("k_patch_apply")},
         "clocks": clk, "e2e": e2e, "fp64_path": fp64,
         "kernels": [dict(k, frac=k["achieved"] / peak) for k in kernels],
+        "spmv_group_tuned": tuned,
     }
     return out
 

@@ -142,34 +142,39 @@ __global__ void __launch_bounds__(TC_THREADS) k_tc_update(float2* __restrict__ C
   bool ok = true;
   for (int pass = 0; pass < 2 && ok; ++pass) {
     const int t0 = pass * (TC_KP / 2);
-    for (int q = tid; q < TC_T * (TC_KP / 2); q += TC_THREADS) {
+    constexpr int PER = TC_T * (TC_KP / 2) / TC_THREADS;   // operand values per thread
+    // all global loads first (they are independent), then split and store
+    float2 av[PER], bv[PER];
+#pragma unroll
+    for (int u = 0; u < PER; ++u) {
+      const int q = tid + u * TC_THREADS;
       const int r = q / (TC_KP / 2), t = q % (TC_KP / 2);
       const int64_t gi = i0 + r;
-      float2 a = make_float2(0.f, 0.f);
-      if (gi < N && t0 + t < kw) a = A[gi * N + k0 + t0 + t];
+      av[u] = (gi < N && t0 + t < kw) ? A[gi * N + k0 + t0 + t] : make_float2(0.f, 0.f);
+      if (mode == TC_HERK) {
+        const int64_t gj = j0 + r;
+        bv[u] = (gj < N && t0 + t < kw) ? A[gj * N + k0 + t0 + t] : make_float2(0.f, 0.f);
+      } else {
+        const int tb = q / TC_T, c = q % TC_T;
+        const int64_t gj = j0 + c;
+        bv[u] = (gj < N && t0 + tb < kw) ? B[((int64_t)k0 + t0 + tb) * N + gj] : make_float2(0.f, 0.f);
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < PER; ++u) {
+      const int q = tid + u * TC_THREADS;
+      const int r = q / (TC_KP / 2), t = q % (TC_KP / 2);
+      const float2 a = av[u];
       if (mode == TC_HERK) {
         store_split(pAhi, pAlo, r, 2 * t, a.x, a.y);
         store_split(pAhi, pAlo, TC_T + r, 2 * t, a.y, -a.x);
+        store_split(pBhi, pBlo, r, 2 * t, bv[u].x, bv[u].y);
       } else {
         store_split(pAhi, pAlo, r, 2 * t, a.x, -a.y);
         store_split(pAhi, pAlo, TC_T + r, 2 * t, a.y, a.x);
+        const int tb = q / TC_T, c = q % TC_T;
+        store_split(pBhi, pBlo, c, 2 * tb, bv[u].x, bv[u].y);
       }
-    }
-    for (int q = tid; q < TC_T * (TC_KP / 2); q += TC_THREADS) {
-      int c, t;
-      float2 b = make_float2(0.f, 0.f);
-      if (mode == TC_HERK) {
-        c = q / (TC_KP / 2);
-        t = q % (TC_KP / 2);
-        const int64_t gj = j0 + c;
-        if (gj < N && t0 + t < kw) b = A[gj * N + k0 + t0 + t];
-      } else {
-        t = q / TC_T;
-        c = q % TC_T;
-        const int64_t gj = j0 + c;
-        if (gj < N && t0 + t < kw) b = B[((int64_t)k0 + t0 + t) * N + gj];
-      }
-      store_split(pBhi, pBlo, c, 2 * t, b.x, b.y);
     }
     // make the generic-proxy stores visible to the tensor core (async proxy)
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
