@@ -59,6 +59,7 @@ def parse():
     ap.add_argument("--max-dofs", type=float, default=2.5e5, help="batch/serve: sample only problems up to this size")
     ap.add_argument("--slots", type=int, default=4, help="batch/serve: concurrent serving slots")
     ap.add_argument("--rate", type=float, default=0.0, help="serve: arrival rate in requests/s (0: all at t = 0)")
+    ap.add_argument("--budget-gb", type=float, default=160.0, help="batch/serve: device-memory admission budget")
     ap.add_argument("--oracle-sample", action="store_true", help=argparse.SUPPRESS)
     ap.add_argument("--oracle-steps", type=int, default=1, help=argparse.SUPPRESS)
     return ap.parse_args()
@@ -232,6 +233,20 @@ def traffic_for(kernel):
     return e.get("traffic_bytes_per_launch")
 
 
+FP64_PEAK_TFLOPS = 1.25   # nominal dense FP64 of one GB300 (no measured FP64 figure is provided)
+
+
+def element_line(acc):
+    """Roofline line of the batched element stage (FP64 arithmetic)."""
+    ms, gflop, n = acc
+    if not n or ms <= 0:
+        return None
+    tf = gflop / (ms / 1e3) / 1e3
+    return {"kernels": "k_elem_build/potrf/trsm/herk/condense", "bound": "alu", "achieved": tf,
+            "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": tf / FP64_PEAK_TFLOPS,
+            "peak_source": "nominal FP64", "gflop_per_setup": gflop / n, "ms_per_setup": ms / n}
+
+
 def run_gb300(args, rank, world, local_rank):
     import numpy as np
     import torch
@@ -260,6 +275,7 @@ def run_gb300(args, rank, world, local_rank):
     fields = torch.empty(2 * n_field, dtype=torch.float64, device="cuda")
 
     tuned = {}
+    elem_acc = [0.0, 0.0, 0]   # element-stage ms, GFLOP, setups
 
     def step(prof=D.PROF_OFF):
         s = D.dpgmg_setup(h, pb, op)
@@ -270,6 +286,10 @@ def run_gb300(args, rank, world, local_rank):
                 except D.DpgmgError:
                     break
             tuned["cg"] = D.dpgmg_spmv_group(h, s, -1)
+            em, eg, _ = D.dpgmg_setup_profile(h, s)
+            elem_acc[0] += em
+            elem_acc[1] += eg
+            elem_acc[2] += 1
             if prof:
                 D.dpgmg_profile(h, s, prof)
             code, st = D.dpgmg_solve(h, s, trace.data_ptr(), fields.data_ptr(), out_is_device=True)
@@ -282,6 +302,7 @@ def run_gb300(args, rank, world, local_rank):
 
     for _ in range(args.warmup):
         step()
+    elem_acc[:] = [0.0, 0.0, 0]
     clocks = Clocks(local_rank)
     clocks.start()
     if dist:
@@ -302,6 +323,7 @@ def run_gb300(args, rank, world, local_rank):
     if dist:
         dist.barrier()
     launches = D.dpgmg_launch_count() - l0
+    elem_acc_timed = list(elem_acc)
     clk = clocks.stop()
     total_ms = e0.elapsed_time(e1)
     dof_iters = float(sum(n_dof * s[0] for s in stats))
@@ -382,6 +404,7 @@ def run_gb300(args, rank, world, local_rank):
         "clocks": clk, "e2e": e2e, "fp64_path": fp64,
         "kernels": [dict(k, frac=k["achieved"] / peak) for k in kernels],
         "spmv_group_tuned": tuned,
+        "element_stage": element_line(elem_acc_timed),
     }
     return out
 
@@ -404,7 +427,7 @@ def run_stream(args):
     prec = args.precision
     stream = WL.config4(64, prec) if args.mode == "batch" else WL.config5(max(args.count, 1), prec)
     drawn = stream[:args.count]
-    h = D.dpgmg_create(0)
+    h = D.dpgmg_create(0, int(args.budget_gb * 1e9))
     D.dpgmg_serve_start(h, args.slots)
     sample, skipped = [], 0
     for it in drawn:
@@ -419,19 +442,23 @@ def run_stream(args):
     for it, *_ in sample:
         t += (it.get("gap", 0.0) / args.rate) if (args.mode == "serve" and args.rate > 0) else 0.0
         t_arr.append(t)
-    tickets, refused = [], 0
+    tickets, refused, per = [], 0, []
     t0 = time.perf_counter()
     for (it, pb, op, keep, nt, nf), ta in zip(sample, t_arr):
         while time.perf_counter() - t0 < ta:
             time.sleep(0.0005)
+        rec = {"n": it["problem"]["n"][0], "p": it["problem"]["p"], "omega": round(it["problem"]["omega"], 3),
+               "dofs": nt, "est_gb": round(D.dpgmg_query_sizes(pb, op)[2] / 1e9, 2)}
+        per.append(rec)
         try:
-            tickets.append((D.dpgmg_submit(h, pb, op), nt, nf))
+            tickets.append((D.dpgmg_submit(h, pb, op), nt, nf, rec))
         except D.DpgmgError as e:
             if e.code != D.DPGMG_ERR_NOMEM:
                 raise
             refused += 1
+            rec["status"] = "refused (NOMEM)"
     lat, dof_iters, iters, fails = [], 0.0, [], 0
-    for tk, nt, nf in tickets:
+    for tk, nt, nf, rec in tickets:
         x = np.zeros(nt, dtype=np.complex128)
         f = np.zeros(nf, dtype=np.complex128)
         while True:
@@ -439,9 +466,12 @@ def run_stream(args):
             if code != D.DPGMG_ERR_PENDING:
                 break
             time.sleep(0.001)
+        rec["status"] = D.strerror(code)
         if code != D.DPGMG_OK:
             fails += 1
             continue
+        rec.update(iters=st.iters, latency_ms=round(l, 1), setup_ms=round(st.t_setup_ms, 1),
+                   pcg_ms=round(st.t_pcg_ms, 2))
         lat.append(l)
         dof_iters += nt * st.iters
         iters.append(st.iters)
@@ -453,6 +483,7 @@ def run_stream(args):
            "p99_ms": float(np.percentile(lat, 99)) if lat else None, "completed": done, "failed": fails,
            "refused_nomem": refused, "drawn": len(drawn), "left_out_above_max_dofs": skipped,
            "max_dofs": args.max_dofs, "slots": args.slots, "rate_per_s": args.rate, "precision": prec,
+           "budget_gb": args.budget_gb, "requests": per,
            "wall_s": wall, "iters_mean": float(np.mean(iters)) if iters else None,
            "sample": "first %d problems of the seeded %s stream, those with <= %g trace DOFs" % (
                len(drawn), "batch (n~U{8..24}, p~U{2,3,4})" if args.mode == "batch" else

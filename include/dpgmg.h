@@ -273,6 +273,16 @@ long long dpgmg_launch_count(void);
  * invalid level or size.  Results do not depend on G beyond rounding order. */
 int dpgmg_spmv_group(dpgmg_handle h, dpgmg_system sys, int level, int set, int* group);
 
+/* Setup phases of a system: device time of the batched element stage
+ * (Sec. 2: Gram, B and load, Cholesky, optimal test functions, DPG matrix,
+ * field condensation), its algorithmic GFLOP (an FMA counts 2 flops, a
+ * complex FMA 8; Gram Cholesky nt^3/3, W = L^-1 [B l] nt^2 (m+1)/2,
+ * K = W^H W (m+1)^2 nt/2, condensation nf^3/3 + nf^2 (ntr+1) + ntr (ntr+1) nf
+ * multiply-adds per element), and the whole setup's device time.  Outputs
+ * may be NULL.  Returns DPGMG_ERR_ARG for a null handle or system. */
+int dpgmg_setup_profile(dpgmg_handle h, dpgmg_system sys, double* element_ms, double* element_gflop,
+                        double* setup_ms);
+
 /* Bracket every launch of one kernel with CUDA events on the launching
  * stream during subsequent dpgmg_solve calls (which = DPGMG_PROF_*; OFF
  * clears).  dpgmg_profile_read() synchronises, returns the summed device

@@ -200,21 +200,26 @@ void setup_system(SystemImpl& S, const dpgmg_problem* pb, const dpgmg_opts* op, 
     L.kind = specs[i].kind_below;
     L.nloc = (int)L.mesh.loc.size();
   }
-  cudaEvent_t e0, e1;
+  cudaEvent_t e0, e1, ee;
   DPG_CUDA(cudaEventCreate(&e0));
   DPG_CUDA(cudaEventCreate(&e1));
+  DPG_CUDA(cudaEventCreate(&ee));
   DPG_CUDA(cudaEventRecord(e0, st));
   element_stage(S, st);
+  DPG_CUDA(cudaEventRecord(ee, st));
   build_hierarchy(S, st);
   assemble_rhs(S, st);
   prepare_solve(S, st);
   DPG_CUDA(cudaEventRecord(e1, st));
   DPG_CUDA(cudaEventSynchronize(e1));
-  float ms = 0.f;
+  float ms = 0.f, mse = 0.f;
   DPG_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+  DPG_CUDA(cudaEventElapsedTime(&mse, e0, ee));
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
+  cudaEventDestroy(ee);
   S.t_setup_ms = ms;
+  S.t_elem_ms = mse;
   fill_bytes_per_iter(S);
 }
 
@@ -415,6 +420,16 @@ int dpgmg_profile_read(dpgmg_handle h, dpgmg_system sys, double* total_ms, long 
   } catch (const Err& e) {
     return fail(e);
   }
+}
+
+int dpgmg_setup_profile(dpgmg_handle h, dpgmg_system sys, double* element_ms, double* element_gflop,
+                        double* setup_ms) {
+  if (!h || !sys) return DPGMG_ERR_ARG;
+  const SystemImpl& S = sys->s;
+  if (element_ms) *element_ms = S.t_elem_ms;
+  if (element_gflop) *element_gflop = S.elem_flops * 1e-9;
+  if (setup_ms) *setup_ms = S.t_setup_ms;
+  return DPGMG_OK;
 }
 
 int dpgmg_spmv_group(dpgmg_handle h, dpgmg_system sys, int level, int set, int* group) {

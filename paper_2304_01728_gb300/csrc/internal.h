@@ -146,6 +146,8 @@ struct SystemImpl {
   double t_setup_ms = 0.0;
   int64_t bytes_per_iter = 0;
   void* ws = nullptr;            // solver workspace
+  double elem_flops = 0.0;       // algorithmic flops of the element stage
+  double t_elem_ms = 0.0;        // its device time (events around the stage)
   int prof_which = 0;            // DPGMG_PROF_* being bracketed with events
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> prof_events;
   std::vector<int> prof_graph_pairs;   // pairs recorded by a captured graph (re-read after each replay)

@@ -135,24 +135,16 @@ __global__ void __launch_bounds__(256) k_spmv(const int32_t* __restrict__ row_en
       const int nnz = (int)(col_ptr[E + 1] - c0);
       const C* vals = v + val_ptr[E] + (row - ent_start[E]) * nnz;
       const int32_t* cols = col_idx + c0;
-      // up to 8 columns per lane per pass: all index and value loads are
-      // issued first, then the 8 gathers of x, then the products
-      for (int k0 = 0; k0 < nnz; k0 += 256) {
-        int c[8];
-        C vv[8];
-#pragma unroll
-        for (int u = 0; u < 8; ++u) {
-          const int k = k0 + lane + 32 * u;
-          c[u] = k < nnz ? cols[k] : -1;
-          vv[u] = k < nnz ? vals[k] : O::zero();
-        }
-        C xv[8];
-#pragma unroll
-        for (int u = 0; u < 8; ++u) xv[u] = c[u] >= 0 ? x[c[u]] : O::zero();
-#pragma unroll
-        for (int u = 0; u < 8; ++u) acc = O::fma(vv[u], xv[u], acc);
+      C acc1 = O::zero();
+      int k = lane;
+      for (; k + 32 < nnz; k += 64) {   // two independent loads per lane per step
+        const C v0 = vals[k], v1 = vals[k + 32];
+        const int cA = cols[k], cB = cols[k + 32];
+        acc = O::fma(v0, x[cA], acc);
+        acc1 = O::fma(v1, x[cB], acc1);
       }
-      acc = warp_sum(acc);
+      if (k < nnz) acc = O::fma(vals[k], x[cols[k]], acc);
+      acc = warp_sum(O::add(acc, acc1));
     }
     if (lane == 0) y[row] = mode ? O::sub(b[row], acc) : acc;
   }
@@ -311,36 +303,32 @@ __global__ void __launch_bounds__(256) k_spmv_df(const int32_t* __restrict__ row
       const int nnz = (int)(col_ptr[E + 1] - c0);
       const int64_t off = val_ptr[E] + (row - ent_start[E]) * nnz;
       const int32_t* cols = col_idx + c0;
-      // up to 4 columns per lane per pass, loads first (as in k_spmv)
-      for (int k0 = 0; k0 < nnz; k0 += 128) {
-        int c[4];
-        float2 ah[4], al[4];
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          const int k = k0 + lane + 32 * u;
-          const bool in = k < nnz;
-          c[u] = in ? cols[k] : -1;
-          ah[u] = in ? vh[off + k] : make_float2(0.f, 0.f);
-          al[u] = in ? vl[off + k] : make_float2(0.f, 0.f);
-        }
-        float2 uh[4], ul[4];
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          uh[u] = c[u] >= 0 ? xh[c[u]] : make_float2(0.f, 0.f);
-          ul[u] = c[u] >= 0 ? xl[c[u]] : make_float2(0.f, 0.f);
-        }
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          float p, q;
-          df_mul(ah[u].x, al[u].x, uh[u].x, ul[u].x, p, q);
-          df_add(rh, rl, p, q);
-          df_mul(ah[u].y, al[u].y, uh[u].y, ul[u].y, p, q);
-          df_add(rh, rl, -p, -q);
-          df_mul(ah[u].x, al[u].x, uh[u].y, ul[u].y, p, q);
-          df_add(ih, il, p, q);
-          df_mul(ah[u].y, al[u].y, uh[u].x, ul[u].x, p, q);
-          df_add(ih, il, p, q);
-        }
+      for (int k = lane; k < nnz; k += 64) {
+        // two columns per lane per step, all loads issued before the arithmetic
+        const bool two = k + 32 < nnz;
+        const float2 ah0 = vh[off + k], al0 = vl[off + k];
+        const int cA = cols[k];
+        const float2 ah1 = two ? vh[off + k + 32] : make_float2(0.f, 0.f);
+        const float2 al1 = two ? vl[off + k + 32] : make_float2(0.f, 0.f);
+        const int cB = two ? cols[k + 32] : cA;
+        const float2 uh0 = xh[cA], ul0 = xl[cA], uh1 = xh[cB], ul1 = xl[cB];
+        float p, q;
+        df_mul(ah0.x, al0.x, uh0.x, ul0.x, p, q);
+        df_add(rh, rl, p, q);
+        df_mul(ah0.y, al0.y, uh0.y, ul0.y, p, q);
+        df_add(rh, rl, -p, -q);
+        df_mul(ah0.x, al0.x, uh0.y, ul0.y, p, q);
+        df_add(ih, il, p, q);
+        df_mul(ah0.y, al0.y, uh0.x, ul0.x, p, q);
+        df_add(ih, il, p, q);
+        df_mul(ah1.x, al1.x, uh1.x, ul1.x, p, q);
+        df_add(rh, rl, p, q);
+        df_mul(ah1.y, al1.y, uh1.y, ul1.y, p, q);
+        df_add(rh, rl, -p, -q);
+        df_mul(ah1.x, al1.x, uh1.y, ul1.y, p, q);
+        df_add(ih, il, p, q);
+        df_mul(ah1.y, al1.y, uh1.x, ul1.x, p, q);
+        df_add(ih, il, p, q);
       }
       df_warp_sum(rh, rl);
       df_warp_sum(ih, il);

@@ -66,7 +66,7 @@ EXPORTS = ["dpgmg_create", "dpgmg_destroy", "dpgmg_query_sizes", "dpgmg_default_
            "dpgmg_solve", "dpgmg_release", "dpgmg_strerror", "dpgmg_last_error", "dpgmg_level_info",
            "dpgmg_element_matrix", "dpgmg_rhs", "dpgmg_apply", "dpgmg_launch_count", "dpgmg_profile",
            "dpgmg_profile_read", "dpgmg_smooth_noalloc", "dpgmg_serve_start", "dpgmg_submit", "dpgmg_poll",
-           "dpgmg_spmv_group"]
+           "dpgmg_spmv_group", "dpgmg_setup_profile"]
 PROF_OFF, PROF_SMOOTH_FINE, PROF_SPMV_FINE, PROF_SPMV_CG = 0, 1, 2, 3
 
 
@@ -112,6 +112,8 @@ def lib():
     L.dpgmg_profile.argtypes = [vp, vp, i]
     L.dpgmg_spmv_group.argtypes = [vp, vp, i, i, ctypes.POINTER(i)]
     L.dpgmg_spmv_group.restype = i
+    L.dpgmg_setup_profile.argtypes = [vp, vp, ctypes.POINTER(d), ctypes.POINTER(d), ctypes.POINTER(d)]
+    L.dpgmg_setup_profile.restype = i
     L.dpgmg_profile_read.argtypes = [vp, vp, ctypes.POINTER(d), ctypes.POINTER(ll), ctypes.POINTER(ll)]
     for f in ["dpgmg_create", "dpgmg_query_sizes", "dpgmg_setup", "dpgmg_solve", "dpgmg_level_info",
               "dpgmg_element_matrix", "dpgmg_rhs", "dpgmg_apply", "dpgmg_profile", "dpgmg_profile_read"]:
@@ -257,6 +259,13 @@ def dpgmg_poll(h, ticket, trace_out=None, field_out=None):
 
 def dpgmg_launch_count():
     return int(lib().dpgmg_launch_count())
+
+
+def dpgmg_setup_profile(h, s):
+    """(element-stage ms, element-stage GFLOP, setup ms)"""
+    a, b, c = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    _check(lib().dpgmg_setup_profile(h, s, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)), "dpgmg_setup_profile")
+    return a.value, b.value, c.value
 
 
 def dpgmg_spmv_group(h, s, level, set_to=0):
