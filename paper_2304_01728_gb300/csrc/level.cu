@@ -205,16 +205,65 @@ __global__ void k_patch_gather(ECSRDev A, const int64_t* ptr, const int32_t* dof
   }
 }
 
-// In place: M (n x n) -> M^-1 via Cholesky in the scratch copy W (precision C).
+// Unit phases of the real form: p-hat DOFs (global index < offU) carry i,
+// u-hat DOFs carry 1.  rot(v, a, b) = conj(beta_a) v beta_b and its inverse
+// unrot(x, a, b) = beta_a x conj(beta_b); multiplying by +-i only swaps
+// components, so both are exact.
+__device__ __forceinline__ double2 mul_i(double2 v, int s) {   // v * (i)^s, s in {-1, 0, 1}
+  return s == 0 ? v : (s > 0 ? make_double2(-v.y, v.x) : make_double2(v.y, -v.x));
+}
+
+// In place: M (n x n) -> M^-1 via Cholesky in the scratch copy W.
+// Real path: on a patch whose block is real after the unit phases are removed
+// (every element touching it runs the real element path, so its entries are
+// exactly phased: the test below is exact), Cholesky, triangular inverse and
+// L^-H L^-1 run in real arithmetic (a quarter of the flops) and the phases
+// are put back on the inverse.  Other patches take the complex path.
 template <class C>
-__global__ void __launch_bounds__(CTA_THREADS) k_patch_invert(const int64_t* ptr, const int64_t* vptr, C* vals,
-                                                            C* scratch, const int64_t* soff, int64_t j0, int* info) {
+__global__ void __launch_bounds__(CTA_THREADS) k_patch_invert(const int64_t* ptr, const int32_t* pdofs,
+                                                            const int64_t* vptr, C* vals, C* scratch,
+                                                            const int64_t* soff, int64_t j0, int64_t offU, int* info) {
   extern __shared__ unsigned char shraw[];
   C* sh = reinterpret_cast<C*>(shraw);
   const int64_t j = j0 + blockIdx.x;
-  const int n = (int)(ptr[j + 1] - ptr[j]);
+  const int64_t b = ptr[j];
+  const int n = (int)(ptr[j + 1] - b);
   C* M = vals + vptr[j];
   C* W = scratch + soff[blockIdx.x];
+  bool cplx = false;
+  if (sizeof(C) == sizeof(double2)) {
+    for (int q = threadIdx.x; q < n * n; q += blockDim.x) {
+      const int r = q / n, c = q % n;
+      const int sr = pdofs[b + r] < offU ? 1 : 0, sc = pdofs[b + c] < offU ? 1 : 0;
+      const double2 v = mul_i(*reinterpret_cast<const double2*>(M + q), sc - sr);
+      if (v.y != 0.0) cplx = true;
+    }
+  } else {
+    cplx = true;
+  }
+  if (!__syncthreads_or(cplx)) {
+    double* Wr = reinterpret_cast<double*>(W);
+    double* Mr = reinterpret_cast<double*>(M);
+    double* shr = reinterpret_cast<double*>(shraw);
+    for (int q = threadIdx.x; q < n * n; q += blockDim.x) {
+      const int r = q / n, c = q % n;
+      const int sr = pdofs[b + r] < offU ? 1 : 0, sc = pdofs[b + c] < offU ? 1 : 0;
+      Wr[q] = mul_i(*reinterpret_cast<const double2*>(M + q), sc - sr).x;
+    }
+    __syncthreads();
+    int inf = cta_potrf<double>(Wr, n, n, shr);
+    if (threadIdx.x == 0 && inf) atomicOr(info, 8);
+    for (int q = threadIdx.x; q < n * n; q += blockDim.x) Mr[q] = (q / n == q % n) ? 1.0 : 0.0;
+    __syncthreads();
+    cta_trinv_lower<double>(Wr, n, n, Mr, n, reinterpret_cast<char*>(shr));
+    cta_herk_lower_tri<double>(Mr, n, n, Wr, n, shr);
+    for (int q = threadIdx.x; q < n * n; q += blockDim.x) {
+      const int r = q / n, c = q % n;
+      const int sr = pdofs[b + r] < offU ? 1 : 0, sc = pdofs[b + c] < offU ? 1 : 0;
+      *reinterpret_cast<double2*>(M + q) = mul_i(make_double2(Wr[q], 0.0), sr - sc);
+    }
+    return;
+  }
   for (int q = threadIdx.x; q < n * n; q += blockDim.x) W[q] = M[q];
   __syncthreads();
   int inf = cta_potrf<C>(W, n, n, sh);
@@ -270,7 +319,8 @@ constexpr bool kHalfStorageSmoother = false;
 // --------------------------------------------------------------- driver
 // Invert all patch blocks in place, in chunks that bound the scratch copy.
 template <class C>
-static void invert_patches(Alloc& A, PatchDev& D, const Patches& P, C* vals, int* dinfo, cudaStream_t st) {
+static void invert_patches(Alloc& A, PatchDev& D, const Patches& P, C* vals, int64_t offU, int* dinfo,
+                           cudaStream_t st) {
   const size_t sm = (size_t)(NB * NB + 2 * TL * NB) * sizeof(C) + 64;
   DPG_CUDA(cudaFuncSetAttribute(k_patch_invert<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
   const size_t one = (size_t)D.max_n * D.max_n;
@@ -290,7 +340,8 @@ static void invert_patches(Alloc& A, PatchDev& D, const Patches& P, C* vals, int
       ++j;
     }
     DPG_CUDA(cudaMemcpyAsync(soff, offs.data(), offs.size() * sizeof(int64_t), cudaMemcpyHostToDevice, st));
-    k_patch_invert<C><<<(unsigned)(j - j0), CTA_THREADS, sm, st>>>(D.ptr, D.val_ptr, vals, scratch, soff, j0, dinfo);
+    k_patch_invert<C><<<(unsigned)(j - j0), CTA_THREADS, sm, st>>>(D.ptr, D.dofs, D.val_ptr, vals, scratch, soff, j0,
+                                                                   offU, dinfo);
     DPG_CHECK_LAUNCH();
     DPG_CUDA(cudaStreamSynchronize(st));   // the offsets buffer is reused
     j0 = j;
@@ -332,7 +383,7 @@ static void setup_patches(SystemImpl& S, Level& F, const std::vector<char>& smas
   // Patch inverses are computed in FP64 on both paths; the mixed path rounds
   // them to complex64 after theta is estimated (a complex64 factorisation of
   // blocks with condition numbers up to ~5e4 perturbs the smoother by ~1e-3).
-  invert_patches<double2>(A, D, P, D.inv64, dinfo, st);
+  invert_patches<double2>(A, D, P, D.inv64, F.mesh.offU, dinfo, st);
   (void)mixed;
 }
 

@@ -32,6 +32,9 @@ template <class C, class V> __device__ __forceinline__ C cvt_in(V v) {
   return Ops<C>::mk((typename Ops<C>::R)v.x, (typename Ops<C>::R)v.y);
 }
 
+// patch inverses are read once per application: streaming loads (evict first)
+template <class C> __device__ __forceinline__ C ld_stream(const C* p) { return __ldcs(p); }
+
 template <class C, class TIN>
 __global__ void __launch_bounds__(256) k_patch_apply(const int64_t* __restrict__ ptr, const int32_t* __restrict__ dofs,
                                                      const int64_t* __restrict__ vptr, const int2* __restrict__ chunks,
@@ -54,14 +57,14 @@ __global__ void __launch_bounds__(256) k_patch_apply(const int64_t* __restrict__
   if (a < n) {
     int k = w;
     for (; k + 24 < n; k += 32) {
-      const C m0 = M[(size_t)k * n], m1 = M[(size_t)(k + 8) * n];
-      const C m2 = M[(size_t)(k + 16) * n], m3 = M[(size_t)(k + 24) * n];
+      const C m0 = ld_stream(M + (size_t)k * n), m1 = ld_stream(M + (size_t)(k + 8) * n);
+      const C m2 = ld_stream(M + (size_t)(k + 16) * n), m3 = ld_stream(M + (size_t)(k + 24) * n);
       a0 = O::fmac(rj[k], m0, a0);
       a1 = O::fmac(rj[k + 8], m1, a1);
       a2 = O::fmac(rj[k + 16], m2, a2);
       a3 = O::fmac(rj[k + 24], m3, a3);
     }
-    for (; k < n; k += 8) a0 = O::fmac(rj[k], M[(size_t)k * n], a0);
+    for (; k < n; k += 8) a0 = O::fmac(rj[k], ld_stream(M + (size_t)k * n), a0);
   }
   part[w][lane] = O::add(O::add(a0, a1), O::add(a2, a3));
   __syncthreads();

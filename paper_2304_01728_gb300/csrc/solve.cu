@@ -138,12 +138,12 @@ __global__ void __launch_bounds__(256) k_spmv(const int32_t* __restrict__ row_en
       C acc1 = O::zero();
       int k = lane;
       for (; k + 32 < nnz; k += 64) {   // two independent loads per lane per step
-        const C v0 = vals[k], v1 = vals[k + 32];
+        const C v0 = __ldcs(vals + k), v1 = __ldcs(vals + k + 32);
         const int cA = cols[k], cB = cols[k + 32];
         acc = O::fma(v0, x[cA], acc);
         acc1 = O::fma(v1, x[cB], acc1);
       }
-      if (k < nnz) acc = O::fma(vals[k], x[cols[k]], acc);
+      if (k < nnz) acc = O::fma(__ldcs(vals + k), x[cols[k]], acc);
       acc = warp_sum(O::add(acc, acc1));
     }
     if (lane == 0) y[row] = mode ? O::sub(b[row], acc) : acc;
@@ -179,7 +179,7 @@ __global__ void __launch_bounds__(256) k_spmv_ent(const int2* __restrict__ tasks
       const C xv = x[cols[k]];
 #pragma unroll
       for (int r = 0; r < G; ++r)
-        if (r < g) acc[r] = O::fma(vals[(int64_t)r * nnz + k], xv, acc[r]);
+        if (r < g) acc[r] = O::fma(__ldcs(vals + (int64_t)r * nnz + k), xv, acc[r]);
     }
     C mine = O::zero();
 #pragma unroll
@@ -306,10 +306,10 @@ __global__ void __launch_bounds__(256) k_spmv_df(const int32_t* __restrict__ row
       for (int k = lane; k < nnz; k += 64) {
         // two columns per lane per step, all loads issued before the arithmetic
         const bool two = k + 32 < nnz;
-        const float2 ah0 = vh[off + k], al0 = vl[off + k];
+        const float2 ah0 = __ldcs(vh + off + k), al0 = __ldcs(vl + off + k);
         const int cA = cols[k];
-        const float2 ah1 = two ? vh[off + k + 32] : make_float2(0.f, 0.f);
-        const float2 al1 = two ? vl[off + k + 32] : make_float2(0.f, 0.f);
+        const float2 ah1 = two ? __ldcs(vh + off + k + 32) : make_float2(0.f, 0.f);
+        const float2 al1 = two ? __ldcs(vl + off + k + 32) : make_float2(0.f, 0.f);
         const int cB = two ? cols[k + 32] : cA;
         const float2 uh0 = xh[cA], ul0 = xl[cA], uh1 = xh[cB], ul1 = xl[cB];
         float p, q;
@@ -376,7 +376,7 @@ __global__ void __launch_bounds__(256) k_spmv_df_ent(const int2* __restrict__ ta
 #pragma unroll
       for (int r = 0; r < G; ++r) {
         if (r < g) {
-          const float2 ah = vh[off + (int64_t)r * nnz + k], al = vl[off + (int64_t)r * nnz + k];
+          const float2 ah = __ldcs(vh + off + (int64_t)r * nnz + k), al = __ldcs(vl + off + (int64_t)r * nnz + k);
           float p, q;
           df_mul(ah.x, al.x, uh.x, ul.x, p, q);
           df_add(rh[r], rl[r], p, q);
