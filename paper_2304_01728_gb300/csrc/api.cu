@@ -132,7 +132,7 @@ size_t estimate_bytes(const dpgmg_problem* pb, const dpgmg_opts* op) {
       auto ps = patch_sizes(m, hlev, hlev ? 4 : 2, nco);
       double nvals = 0.0, nslots = 0.0, nmax = 0.0;
       for (int64_t v : ps) {
-        nvals += (double)v * v;
+        nvals += (double)v * (double)patch_ld(v);
         nslots += (double)v;
         nmax = std::max(nmax, (double)v);
       }
@@ -169,7 +169,7 @@ static void fill_bytes_per_iter(SystemImpl& S) {
   const int nu = S.op.nu_pre + S.op.nu_post;
   for (size_t l = 1; l < S.levels.size(); ++l) {
     const Level& L = S.levels[l];
-    b += nu * (double)L.P.nvals * esz;                                           // smoother
+    b += nu * (double)L.P.sum_sq * esz;                                          // smoother (n_j^2 per patch)
     b += std::max(1, nu) * (double)L.A.nnz * esz;                                // residual SpMVs
     if (L.kind == 2) b += (double)L.nK * (2.0 * L.nI * L.nS + L.nI * L.nI) * esz; // condense + backsub
   }

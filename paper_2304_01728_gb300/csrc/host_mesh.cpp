@@ -500,7 +500,7 @@ Patches build_patches(const MeshL& m, const std::vector<char>& smask, int H, con
   P.val_ptr.assign(npatch + 1, 0);
   for (int64_t j = 0; j < npatch; ++j) {
     int64_t nj = P.ptr[j + 1] - P.ptr[j];
-    P.val_ptr[j + 1] = P.val_ptr[j] + nj * nj;
+    P.val_ptr[j + 1] = P.val_ptr[j] + nj * patch_ld(nj);
   }
   // slots of each DOF
   std::vector<int64_t> sc(m.ndof + 1, 0);

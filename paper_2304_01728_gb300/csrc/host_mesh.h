@@ -88,11 +88,17 @@ ECSRHost build_ecsr(const MeshL& m, const std::vector<std::vector<int64_t>>& gro
 struct Patches {
   std::vector<int64_t> ptr;    // per patch (+1)
   std::vector<int32_t> dofs;   // patch-major DOF lists (sorted within a patch)
-  std::vector<int64_t> val_ptr;// per patch (+1): offset of the n_j x n_j block
+  std::vector<int64_t> val_ptr;// per patch (+1): offset of the n_j x ld_j block (ld_j = patch_ld(n_j))
   std::vector<int64_t> slot_ptr; // per DOF (+1): CSR of the DOF's slots in dofs[]
   std::vector<int32_t> slots;
 };
 Patches build_patches(const MeshL& m, const std::vector<char>& smask, int H, const int nco[3]);
+// Row length of a stored n x n patch block: n rounded up to even, so that
+// every row of a complex64 block starts on a 16-byte boundary.
+#if defined(__CUDACC__)
+__host__ __device__
+#endif
+inline int64_t patch_ld(int64_t n) { return n + (n & 1); }
 // Patch sizes only (same rule), for memory estimates: n_j per coarse vertex.
 // macro = true selects the h-level smoothing space (fine DOFs on the coarse skeleton).
 std::vector<int64_t> patch_sizes(const MeshL& m, bool macro, int H, const int nco[3]);

@@ -86,8 +86,10 @@ struct PatchDev {
   int32_t* slots = nullptr;
   double2* inv64 = nullptr;
   float2* inv32 = nullptr;
-  int2* chunks = nullptr;      // (patch, first row) of each 32-row work item
+  int2* chunks = nullptr;      // (patch, first column) of each 32-column work item (complex128)
   int64_t nchunks = 0;
+  int2* chunks64 = nullptr;    // the same for 64-column work items (complex64)
+  int64_t nchunks64 = 0;
   // Hermitian half storage (lower triangles packed by rows), used for the
   // complex64 operators of the mixed path
   bool half = false;

@@ -197,10 +197,11 @@ __global__ void k_patch_gather(ECSRDev A, const int64_t* ptr, const int32_t* dof
   const int64_t j = j0 + blockIdx.x;
   const int64_t b = ptr[j];
   const int n = (int)(ptr[j + 1] - b);
+  const int ld = (int)patch_ld(n);
   double2* M = out + vptr[j];
-  for (int q = threadIdx.x; q < n * n; q += blockDim.x) {
-    int r = q / n, c = q % n;
-    int64_t pos = ecsr_find(A, dofs[b + r], dofs[b + c]);
+  for (int q = threadIdx.x; q < n * ld; q += blockDim.x) {
+    int r = q / ld, c = q % ld;
+    int64_t pos = c < n ? ecsr_find(A, dofs[b + r], dofs[b + c]) : -1;
     M[q] = pos >= 0 ? A.v64[pos] : make_double2(0, 0);
   }
 }
@@ -228,6 +229,7 @@ __global__ void __launch_bounds__(CTA_THREADS) k_patch_invert(const int64_t* ptr
   const int64_t j = j0 + blockIdx.x;
   const int64_t b = ptr[j];
   const int n = (int)(ptr[j + 1] - b);
+  const int ld = (int)patch_ld(n);   // stored row length; column n (if any) is padding, left 0
   C* M = vals + vptr[j];
   C* W = scratch + soff[blockIdx.x];
   bool cplx = false;
@@ -235,7 +237,7 @@ __global__ void __launch_bounds__(CTA_THREADS) k_patch_invert(const int64_t* ptr
     for (int q = threadIdx.x; q < n * n; q += blockDim.x) {
       const int r = q / n, c = q % n;
       const int sr = pdofs[b + r] < offU ? 1 : 0, sc = pdofs[b + c] < offU ? 1 : 0;
-      const double2 v = mul_i(*reinterpret_cast<const double2*>(M + q), sc - sr);
+      const double2 v = mul_i(*reinterpret_cast<const double2*>(M + (size_t)r * ld + c), sc - sr);
       if (v.y != 0.0) cplx = true;
     }
   } else {
@@ -243,12 +245,12 @@ __global__ void __launch_bounds__(CTA_THREADS) k_patch_invert(const int64_t* ptr
   }
   if (!__syncthreads_or(cplx)) {
     double* Wr = reinterpret_cast<double*>(W);
-    double* Mr = reinterpret_cast<double*>(M);
+    double* Mr = reinterpret_cast<double*>(M);   // L^-1 (n x n, row length n) in the block's storage
     double* shr = reinterpret_cast<double*>(shraw);
     for (int q = threadIdx.x; q < n * n; q += blockDim.x) {
       const int r = q / n, c = q % n;
       const int sr = pdofs[b + r] < offU ? 1 : 0, sc = pdofs[b + c] < offU ? 1 : 0;
-      Wr[q] = mul_i(*reinterpret_cast<const double2*>(M + q), sc - sr).x;
+      Wr[q] = mul_i(*reinterpret_cast<const double2*>(M + (size_t)r * ld + c), sc - sr).x;
     }
     __syncthreads();
     int inf = cta_potrf<double>(Wr, n, n, shr);
@@ -257,24 +259,28 @@ __global__ void __launch_bounds__(CTA_THREADS) k_patch_invert(const int64_t* ptr
     __syncthreads();
     cta_trinv_lower<double>(Wr, n, n, Mr, n, reinterpret_cast<char*>(shr));
     cta_herk_lower_tri<double>(Mr, n, n, Wr, n, shr);
-    for (int q = threadIdx.x; q < n * n; q += blockDim.x) {
-      const int r = q / n, c = q % n;
-      const int sr = pdofs[b + r] < offU ? 1 : 0, sc = pdofs[b + c] < offU ? 1 : 0;
-      *reinterpret_cast<double2*>(M + q) = mul_i(make_double2(Wr[q], 0.0), sr - sc);
+    for (int q = threadIdx.x; q < n * ld; q += blockDim.x) {
+      const int r = q / ld, c = q % ld;
+      const int sr = pdofs[b + r] < offU ? 1 : 0, sc = c < n && pdofs[b + c] < offU ? 1 : 0;
+      *reinterpret_cast<double2*>(M + q) =
+          c < n ? mul_i(make_double2(Wr[(size_t)r * n + c], 0.0), sr - sc) : make_double2(0.0, 0.0);
     }
     return;
   }
-  for (int q = threadIdx.x; q < n * n; q += blockDim.x) W[q] = M[q];
+  for (int q = threadIdx.x; q < n * n; q += blockDim.x) W[q] = M[(size_t)(q / n) * ld + q % n];
   __syncthreads();
   int inf = cta_potrf<C>(W, n, n, sh);
   if (threadIdx.x == 0 && inf) atomicOr(info, 8);
-  // M = L^-1 (lower), then W = L^-H L^-1 = A^-1, copied back into M
-  for (int q = threadIdx.x; q < n * n; q += blockDim.x)
-    M[q] = (q / n == q % n) ? Ops<C>::from_re(1) : Ops<C>::zero();
+  // M = L^-1 (lower, row length ld), then W = L^-H L^-1 = A^-1, copied back into M
+  for (int q = threadIdx.x; q < n * ld; q += blockDim.x)
+    M[q] = (q / ld == q % ld) ? Ops<C>::from_re(1) : Ops<C>::zero();
   __syncthreads();
-  cta_trinv_lower<C>(W, n, n, M, n, reinterpret_cast<char*>(sh));
-  cta_herk_lower_tri<C>(M, n, n, W, n, sh);
-  for (int q = threadIdx.x; q < n * n; q += blockDim.x) M[q] = W[q];
+  cta_trinv_lower<C>(W, n, n, M, ld, reinterpret_cast<char*>(sh));
+  cta_herk_lower_tri<C>(M, n, ld, W, n, sh);
+  for (int q = threadIdx.x; q < n * ld; q += blockDim.x) {
+    const int r = q / ld, c = q % ld;
+    M[q] = c < n ? W[(size_t)r * n + c] : Ops<C>::zero();
+  }
 }
 
 // --------------------------------------------------------------- precision
@@ -359,23 +365,27 @@ static void setup_patches(SystemImpl& S, Level& F, const std::vector<char>& smas
   D.nslots = (int64_t)P.dofs.size();
   D.nvals = P.val_ptr.back();
   D.max_n = 0;
-  D.sum_sq = D.nvals;
-  for (int64_t j = 0; j < D.np; ++j) D.max_n = std::max(D.max_n, P.ptr[j + 1] - P.ptr[j]);
+  D.sum_sq = 0;
+  for (int64_t j = 0; j < D.np; ++j) {
+    const int64_t nj = P.ptr[j + 1] - P.ptr[j];
+    D.max_n = std::max(D.max_n, nj);
+    D.sum_sq += nj * nj;
+  }
   D.ptr = upload(A, P.ptr, st);
   D.dofs = upload(A, P.dofs, st);
   D.val_ptr = upload(A, P.val_ptr, st);
   D.slot_ptr = upload(A, P.slot_ptr, st);
   D.slots = upload(A, P.slots, st);
-  {
+  for (int width : {32, 64}) {
     std::vector<int2> ch;
     for (int64_t j = 0; j < D.np; ++j)
-      for (int64_t a0 = 0; a0 < P.ptr[j + 1] - P.ptr[j]; a0 += 32) ch.push_back(make_int2((int)j, (int)a0));
+      for (int64_t a0 = 0; a0 < P.ptr[j + 1] - P.ptr[j]; a0 += width) ch.push_back(make_int2((int)j, (int)a0));
     // largest patches first: the short work items of small patches end the launch
     std::stable_sort(ch.begin(), ch.end(), [&](const int2& u, const int2& v) {
       return P.ptr[u.x + 1] - P.ptr[u.x] > P.ptr[v.x + 1] - P.ptr[v.x];
     });
-    D.nchunks = (int64_t)ch.size();
-    D.chunks = upload(A, ch, st);
+    (width == 32 ? D.nchunks : D.nchunks64) = (int64_t)ch.size();
+    (width == 32 ? D.chunks : D.chunks64) = upload(A, ch, st);
   }
   D.inv64 = A.arr<double2>((size_t)D.nvals);
   k_patch_gather<<<(unsigned)D.np, 256, 0, st>>>(F.A, D.ptr, D.dofs, D.val_ptr, D.inv64, 0);

@@ -61,8 +61,9 @@ static void na_smooth(const Level& L, const C* inv_full, const C* inv_half, cons
     k_patch_apply_h<C, double2><<<(unsigned)P.np, 256, sm, st>>>(P.ptr, P.dofs, P.hptr, inv_half, r, scratch);
   } else {
     const size_t sm = (size_t)P.max_n * sizeof(C) + 16;
-    k_patch_apply<C, double2><<<(unsigned)P.nchunks, 256, sm, st>>>(P.ptr, P.dofs, P.val_ptr, P.chunks, inv_full, r,
-                                                                     scratch);
+    int64_t nch = 0;
+    const int2* chunks = patch_chunks<C>(P, &nch);
+    k_patch_apply<C, double2><<<(unsigned)nch, 256, sm, st>>>(P.ptr, P.dofs, P.val_ptr, chunks, inv_full, r, scratch);
   }
   DPG_CHECK_LAUNCH();
   k_slot_sum<C, double2><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(P.slot_ptr, P.slots, scratch, y, n, L.theta, 0);

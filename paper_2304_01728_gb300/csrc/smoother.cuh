@@ -2,11 +2,11 @@
 //   y = theta * sum_j R_j^T A_jj^-1 R_j r
 // over the vertex patches of a level.  A_jj^-1 is Hermitian.
 //
-// Full storage (n_j x n_j blocks): one CTA per 32-row chunk of a patch; lane a
-// of warp w reads M[k][a0 + a] for k = w, w + 8, ... (coalesced), the 8 warp
-// partials are summed in shared memory; y_a = sum_k conj(M[k][a]) r_k.  The
-// chunk list is ordered by decreasing patch size so that the small boundary
-// patches fill the last wave.
+// Full storage (n_j x n_j blocks, rows padded to even length): one CTA per
+// chunk of 32 (complex128) or 64 (complex64) columns of a patch; warp w reads
+// rows k = w, w + 8, ... (coalesced), the 8 warp partials are summed in shared
+// memory; y_a = sum_k conj(M[k][a]) r_k.  The chunk lists are ordered by
+// decreasing patch size so that the small boundary patches fill the last wave.
 //
 // Half storage (lower triangle packed by rows, n_j (n_j + 1) / 2 entries):
 // every stored entry is read once and used twice (row sum and mirrored
@@ -14,6 +14,8 @@
 // up to HALF_MAX_N DOFs (the shared-memory buffers scale with n_j).
 #pragma once
 #include "common.cuh"
+#include "host_mesh.h"
+#include "internal.h"
 
 namespace dpgmg {
 
@@ -35,45 +37,96 @@ template <class C, class V> __device__ __forceinline__ C cvt_in(V v) {
 // patch inverses are read once per application: streaming loads (evict first)
 template <class C> __device__ __forceinline__ C ld_stream(const C* p) { return __ldcs(p); }
 
+// Rows of a stored block have length ld = patch_ld(n) (even).  Work item
+// (patch j, first column a0) of COLS columns; lane `lane` of warp w handles
+// columns a0 + PER * lane .. + PER - 1 (PER = 1 for complex128, 2 for
+// complex64: one 16-byte load per row), warps split the rows k = w, w + 8, ...
+template <class C> struct PatchCols { static constexpr int per = 1; };
+template <> struct PatchCols<float2> { static constexpr int per = 2; };
+
 template <class C, class TIN>
-__global__ void __launch_bounds__(256) k_patch_apply(const int64_t* __restrict__ ptr, const int32_t* __restrict__ dofs,
+__global__ void __launch_bounds__(256, PatchCols<C>::per == 2 ? 8 : 3) k_patch_apply(const int64_t* __restrict__ ptr, const int32_t* __restrict__ dofs,
                                                      const int64_t* __restrict__ vptr, const int2* __restrict__ chunks,
                                                      const C* __restrict__ inv, const TIN* __restrict__ r,
                                                      C* __restrict__ pbuf) {
+  constexpr int PER = PatchCols<C>::per;
   extern __shared__ unsigned char shraw[];
-  __shared__ C part[8][33];
+  __shared__ C part[8][32 * PER + 1];
   C* rj = reinterpret_cast<C*>(shraw);
   using O = Ops<C>;
   const int2 ch = chunks[blockIdx.x];
   const int64_t j = ch.x;
   const int64_t b = ptr[j];
   const int n = (int)(ptr[j + 1] - b);
+  const int64_t ld = patch_ld(n);
   for (int q = threadIdx.x; q < n; q += blockDim.x) rj[q] = cvt_in<C>(r[dofs[b + q]]);
   __syncthreads();
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  const int a = ch.y + lane;
-  const C* M = inv + vptr[j] + a;
-  C a0 = O::zero(), a1 = O::zero(), a2 = O::zero(), a3 = O::zero();
-  if (a < n) {
-    int k = w;
-    for (; k + 24 < n; k += 32) {
-      const C m0 = ld_stream(M + (size_t)k * n), m1 = ld_stream(M + (size_t)(k + 8) * n);
-      const C m2 = ld_stream(M + (size_t)(k + 16) * n), m3 = ld_stream(M + (size_t)(k + 24) * n);
-      a0 = O::fmac(rj[k], m0, a0);
-      a1 = O::fmac(rj[k + 8], m1, a1);
-      a2 = O::fmac(rj[k + 16], m2, a2);
-      a3 = O::fmac(rj[k + 24], m3, a3);
-    }
-    for (; k < n; k += 8) a0 = O::fmac(rj[k], ld_stream(M + (size_t)k * n), a0);
-  }
-  part[w][lane] = O::add(O::add(a0, a1), O::add(a2, a3));
-  __syncthreads();
-  if (w == 0 && a < n) {
-    C s = part[0][lane];
+  const int a = ch.y + PER * lane;
+  C acc[PER][2];
 #pragma unroll
-    for (int q = 1; q < 8; ++q) s = O::add(s, part[q][lane]);
-    pbuf[b + a] = s;
+  for (int u = 0; u < PER; ++u) acc[u][0] = acc[u][1] = O::zero();
+  if (a < n) {
+    const C* M = inv + vptr[j] + a;
+    int k = w;
+    if (PER == 2) {
+      // 16-byte loads of (M[k][a], M[k][a+1]); a is even and ld even, so aligned
+      const float4* M4 = reinterpret_cast<const float4*>(M);
+      const int64_t s4 = ld / 2;
+      for (; k + 24 < n; k += 32) {
+        const float4 m0 = __ldcs(M4 + (int64_t)k * s4), m1 = __ldcs(M4 + (int64_t)(k + 8) * s4);
+        const float4 m2 = __ldcs(M4 + (int64_t)(k + 16) * s4), m3 = __ldcs(M4 + (int64_t)(k + 24) * s4);
+        const C r0 = rj[k], r1 = rj[k + 8], r2 = rj[k + 16], r3 = rj[k + 24];
+        acc[0][0] = O::fmac(r0, Ops<C>::mk(m0.x, m0.y), acc[0][0]);
+        acc[1 % PER][0] = O::fmac(r0, Ops<C>::mk(m0.z, m0.w), acc[1 % PER][0]);
+        acc[0][1] = O::fmac(r1, Ops<C>::mk(m1.x, m1.y), acc[0][1]);
+        acc[1 % PER][1] = O::fmac(r1, Ops<C>::mk(m1.z, m1.w), acc[1 % PER][1]);
+        acc[0][0] = O::fmac(r2, Ops<C>::mk(m2.x, m2.y), acc[0][0]);
+        acc[1 % PER][0] = O::fmac(r2, Ops<C>::mk(m2.z, m2.w), acc[1 % PER][0]);
+        acc[0][1] = O::fmac(r3, Ops<C>::mk(m3.x, m3.y), acc[0][1]);
+        acc[1 % PER][1] = O::fmac(r3, Ops<C>::mk(m3.z, m3.w), acc[1 % PER][1]);
+      }
+      for (; k < n; k += 8) {
+        const float4 m0 = __ldcs(M4 + (int64_t)k * s4);
+        acc[0][0] = O::fmac(rj[k], Ops<C>::mk(m0.x, m0.y), acc[0][0]);
+        acc[1 % PER][0] = O::fmac(rj[k], Ops<C>::mk(m0.z, m0.w), acc[1 % PER][0]);
+      }
+    } else {
+      C a2 = O::zero(), a3 = O::zero();
+      for (; k + 24 < n; k += 32) {
+        const C m0 = ld_stream(M + (size_t)k * ld), m1 = ld_stream(M + (size_t)(k + 8) * ld);
+        const C m2 = ld_stream(M + (size_t)(k + 16) * ld), m3 = ld_stream(M + (size_t)(k + 24) * ld);
+        acc[0][0] = O::fmac(rj[k], m0, acc[0][0]);
+        acc[0][1] = O::fmac(rj[k + 8], m1, acc[0][1]);
+        a2 = O::fmac(rj[k + 16], m2, a2);
+        a3 = O::fmac(rj[k + 24], m3, a3);
+      }
+      for (; k < n; k += 8) acc[0][0] = O::fmac(rj[k], ld_stream(M + (size_t)k * ld), acc[0][0]);
+      acc[0][0] = O::add(acc[0][0], a2);
+      acc[0][1] = O::add(acc[0][1], a3);
+    }
   }
+#pragma unroll
+  for (int u = 0; u < PER; ++u) part[w][PER * lane + u] = O::add(acc[u][0], acc[u][1]);
+  __syncthreads();
+  if (w == 0) {
+#pragma unroll
+    for (int u = 0; u < PER; ++u) {
+      const int c = ch.y + PER * lane + u;
+      if (c < n) {
+        C s2 = part[0][PER * lane + u];
+#pragma unroll
+        for (int q = 1; q < 8; ++q) s2 = O::add(s2, part[q][PER * lane + u]);
+        pbuf[b + c] = s2;
+      }
+    }
+  }
+}
+
+// work items of k_patch_apply<C>: 32 columns (complex128) or 64 (complex64)
+template <class C> inline const int2* patch_chunks(const PatchDev& P, int64_t* n) {
+  *n = PatchCols<C>::per == 2 ? P.nchunks64 : P.nchunks;
+  return PatchCols<C>::per == 2 ? P.chunks64 : P.chunks;
 }
 
 // y[g] = (accumulate ? y[g] : 0) + theta * sum_{slots of g} pbuf[slot]
@@ -175,10 +228,11 @@ __global__ void k_pack_half(const int64_t* __restrict__ ptr, const int64_t* __re
   const int64_t j = blockIdx.x;
   const int n = (int)(ptr[j + 1] - ptr[j]);
   const CF* M = full + vptr[j];
+  const int64_t ld = patch_ld(n);
   CH* Hj = half + hptr[j];
   for (int64_t q = threadIdx.x; q < (int64_t)n * n; q += blockDim.x) {
     const int a = (int)(q / n), k = (int)(q % n);
-    if (k <= a) Hj[(int64_t)a * (a + 1) / 2 + k] = cvt_in<CH>(M[q]);
+    if (k <= a) Hj[(int64_t)a * (a + 1) / 2 + k] = cvt_in<CH>(M[a * ld + k]);
   }
 }
 

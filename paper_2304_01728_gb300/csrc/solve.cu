@@ -499,9 +499,10 @@ static void smooth(const Level& L, const C* r, C* y, double theta, int accumulat
     return;
   }
   size_t sm = (size_t)P.max_n * sizeof(C) + 16;
+  int64_t nch = 0;
+  const int2* chunks = patch_chunks<C>(P, &nch);
   int pe = prof_begin(prof, st);
-  k_patch_apply<C, C><<<(unsigned)P.nchunks, 256, sm, st>>>(P.ptr, P.dofs, P.val_ptr, P.chunks, Prec<C>::inv(P), r,
-                                                            pbuf);
+  k_patch_apply<C, C><<<(unsigned)nch, 256, sm, st>>>(P.ptr, P.dofs, P.val_ptr, chunks, Prec<C>::inv(P), r, pbuf);
   DPG_CHECK_LAUNCH();
   prof_end(prof, pe, st);
   k_slot_sum<C, C><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(P.slot_ptr, P.slots, pbuf, y, n, theta, accumulate);
@@ -1120,7 +1121,7 @@ int pcg_solve(SystemImpl& S, cudaStream_t st, double2* xout, dpgmg_stats* stats)
   {
     const Level& Ff = S.levels.back();
     const int64_t esz = S.op.precision == DPGMG_PREC_MIXED ? 8 : 16;
-    if (S.prof_which == DPGMG_PROF_SMOOTH_FINE) S.prof_bytes = Ff.P.nvals * esz;   // full-storage algorithmic bytes
+    if (S.prof_which == DPGMG_PROF_SMOOTH_FINE) S.prof_bytes = Ff.P.sum_sq * esz;   // full-storage algorithmic bytes
     else if (S.prof_which == DPGMG_PROF_SPMV_FINE) S.prof_bytes = Ff.A.nnz * esz;
     else if (S.prof_which == DPGMG_PROF_SPMV_CG) S.prof_bytes = A.nnz * 16;   // hi + lo complex64
   }
