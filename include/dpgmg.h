@@ -276,8 +276,8 @@ int dpgmg_spmv_group(dpgmg_handle h, dpgmg_system sys, int level, int set, int* 
 /* Setup phases of a system: device time of the batched element stage
  * (Sec. 2: Gram, B and load, Cholesky, optimal test functions, DPG matrix,
  * field condensation), its algorithmic GFLOP (an FMA counts 2 flops, a
- * complex FMA 8; Gram Cholesky nt^3/3, W = L^-1 [B l] nt^2 (m+1)/2,
- * K = W^H W (m+1)^2 nt/2, condensation nf^3/3 + nf^2 (ntr+1) + ntr (ntr+1) nf
+ * complex FMA 8; Gram Cholesky nt^3/6, W = L^-1 [B l] nt^2 (m+1)/2,
+ * K = W^H W (m+1)^2 nt/2, condensation nf^3/6 + nf^2 (ntr+1) + ntr (ntr+1) nf
  * multiply-adds per element), and the whole setup's device time.  Outputs
  * may be NULL.  Returns DPGMG_ERR_ARG for a null handle or system. */
 int dpgmg_setup_profile(dpgmg_handle h, dpgmg_system sys, double* element_ms, double* element_gflop,

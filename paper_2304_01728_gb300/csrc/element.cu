@@ -494,12 +494,12 @@ void element_stage(SystemImpl& S, cudaStream_t st) {
   run_list(dreal, (int64_t)lreal.size(), true);
   run_list(dcplx, (int64_t)lcplx.size(), false);
   {
-    // algorithmic flops (an FMA is 2 flops, a complex FMA 8): Gram Cholesky
-    // nt^3/3, W = L^-1 [B l] nt^2 (m+1)/2, K = W^H W (lower) (m+1)^2 nt/2,
-    // field condensation nf^3/3 + nf^2 (ntr+1) + ntr (ntr+1) nf
+    // algorithmic multiply-adds (an FMA is 2 flops, a complex FMA 8): Gram
+    // Cholesky nt^3/6, W = L^-1 [B l] nt^2 (m+1)/2, K = W^H W (lower)
+    // (m+1)^2 nt/2, field condensation nf^3/6 + nf^2 (ntr+1) + ntr (ntr+1) nf
     const double n = a.nt, m1 = a.m + 1, nf = a.nf, t1 = a.ntr + 1.0;
-    const double fma_g = n * n * n / 3.0;
-    const double fma_w = n * n * m1 / 2.0 + m1 * m1 * n / 2.0 + nf * nf * nf / 3.0 + nf * nf * t1 + a.ntr * t1 * nf;
+    const double fma_g = n * n * n / 6.0;
+    const double fma_w = n * n * m1 / 2.0 + m1 * m1 * n / 2.0 + nf * nf * nf / 6.0 + nf * nf * t1 + a.ntr * t1 * nf;
     S.elem_flops = (double)lreal.size() * (2.0 * fma_g + 2.0 * fma_w) + (double)lcplx.size() * (2.0 * fma_g + 8.0 * fma_w);
   }
   int info = 0;

@@ -90,6 +90,7 @@ struct PatchDev {
   int64_t nchunks = 0;
   int2* chunks64 = nullptr;    // the same for 64-column work items (complex64)
   int64_t nchunks64 = 0;
+  int cols = 2;                // complex64 product: columns per lane (1 or 2), tuned at setup
   // Hermitian half storage (lower triangles packed by rows), used for the
   // complex64 operators of the mixed path
   bool half = false;

@@ -223,10 +223,11 @@ __device__ __forceinline__ double2 mul_i(double2 v, int s) {   // v * (i)^s, s i
 template <class C>
 __global__ void __launch_bounds__(CTA_THREADS) k_patch_invert(const int64_t* ptr, const int32_t* pdofs,
                                                             const int64_t* vptr, C* vals, C* scratch,
-                                                            const int64_t* soff, int64_t j0, int64_t offU, int* info) {
+                                                            const int64_t* soff, const int64_t* order, int64_t j0,
+                                                            int64_t offU, int* info) {
   extern __shared__ unsigned char shraw[];
   C* sh = reinterpret_cast<C*>(shraw);
-  const int64_t j = j0 + blockIdx.x;
+  const int64_t j = order[j0 + blockIdx.x];
   const int64_t b = ptr[j];
   const int n = (int)(ptr[j + 1] - b);
   const int ld = (int)patch_ld(n);   // stored row length; column n (if any) is padding, left 0
@@ -334,24 +335,33 @@ static void invert_patches(Alloc& A, PatchDev& D, const Patches& P, C* vals, int
   cap = std::max(std::min<size_t>(cap, (size_t)D.nvals), one);
   C* scratch = A.arr<C>(cap);
   int64_t* soff = A.arr<int64_t>((size_t)D.np + 1);
+  // largest patches first (the launch ends with the short ones)
+  std::vector<int64_t> order(D.np);
+  for (int64_t j = 0; j < D.np; ++j) order[j] = j;
+  std::stable_sort(order.begin(), order.end(), [&](int64_t u, int64_t v) {
+    return P.ptr[u + 1] - P.ptr[u] > P.ptr[v + 1] - P.ptr[v];
+  });
+  int64_t* dorder = upload(A, order, st);
   std::vector<int64_t> offs;
   for (int64_t j0 = 0; j0 < D.np;) {
     offs.clear();
-    int64_t acc = 0, j = j0;
-    while (j < D.np) {
+    int64_t acc = 0, q = j0;
+    while (q < D.np) {
+      const int64_t j = order[q];
       int64_t nj = P.ptr[j + 1] - P.ptr[j];
-      if (acc + nj * nj > (int64_t)cap && j > j0) break;
+      if (acc + nj * nj > (int64_t)cap && q > j0) break;
       offs.push_back(acc);
       acc += nj * nj;
-      ++j;
+      ++q;
     }
     DPG_CUDA(cudaMemcpyAsync(soff, offs.data(), offs.size() * sizeof(int64_t), cudaMemcpyHostToDevice, st));
-    k_patch_invert<C><<<(unsigned)(j - j0), CTA_THREADS, sm, st>>>(D.ptr, D.dofs, D.val_ptr, vals, scratch, soff, j0,
-                                                                   offU, dinfo);
+    k_patch_invert<C><<<(unsigned)(q - j0), CTA_THREADS, sm, st>>>(D.ptr, D.dofs, D.val_ptr, vals, scratch, soff,
+                                                                   dorder, j0, offU, dinfo);
     DPG_CHECK_LAUNCH();
     DPG_CUDA(cudaStreamSynchronize(st));   // the offsets buffer is reused
-    j0 = j;
+    j0 = q;
   }
+  A.release(dorder);
   A.release(soff);
   A.release(scratch);
 }

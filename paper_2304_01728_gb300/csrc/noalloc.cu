@@ -62,7 +62,7 @@ static void na_smooth(const Level& L, const C* inv_full, const C* inv_half, cons
   } else {
     const size_t sm = (size_t)P.max_n * sizeof(C) + 16;
     int64_t nch = 0;
-    const int2* chunks = patch_chunks<C>(P, &nch);
+    const int2* chunks = patch_chunks(P, PatchCols<C>::per, &nch);
     k_patch_apply<C, double2><<<(unsigned)nch, 256, sm, st>>>(P.ptr, P.dofs, P.val_ptr, chunks, inv_full, r, scratch);
   }
   DPG_CHECK_LAUNCH();

@@ -44,12 +44,11 @@ template <class C> __device__ __forceinline__ C ld_stream(const C* p) { return _
 template <class C> struct PatchCols { static constexpr int per = 1; };
 template <> struct PatchCols<float2> { static constexpr int per = 2; };
 
-template <class C, class TIN>
-__global__ void __launch_bounds__(256, PatchCols<C>::per == 2 ? 8 : 3) k_patch_apply(const int64_t* __restrict__ ptr, const int32_t* __restrict__ dofs,
+template <class C, class TIN, int PER = PatchCols<C>::per>
+__global__ void __launch_bounds__(256, PER == 2 ? 8 : 3) k_patch_apply(const int64_t* __restrict__ ptr, const int32_t* __restrict__ dofs,
                                                      const int64_t* __restrict__ vptr, const int2* __restrict__ chunks,
                                                      const C* __restrict__ inv, const TIN* __restrict__ r,
                                                      C* __restrict__ pbuf) {
-  constexpr int PER = PatchCols<C>::per;
   extern __shared__ unsigned char shraw[];
   __shared__ C part[8][32 * PER + 1];
   C* rj = reinterpret_cast<C*>(shraw);
@@ -123,10 +122,24 @@ __global__ void __launch_bounds__(256, PatchCols<C>::per == 2 ? 8 : 3) k_patch_a
   }
 }
 
-// work items of k_patch_apply<C>: 32 columns (complex128) or 64 (complex64)
-template <class C> inline const int2* patch_chunks(const PatchDev& P, int64_t* n) {
-  *n = PatchCols<C>::per == 2 ? P.nchunks64 : P.nchunks;
-  return PatchCols<C>::per == 2 ? P.chunks64 : P.chunks;
+// work items of k_patch_apply with PER columns per lane: 32 * PER columns
+inline const int2* patch_chunks(const PatchDev& P, int per, int64_t* n) {
+  *n = per == 2 ? P.nchunks64 : P.nchunks;
+  return per == 2 ? P.chunks64 : P.chunks;
+}
+
+// complex64 smoother product with the tuned columns per lane (1 or 2)
+template <class TIN>
+inline void launch_patch_apply_c64(const PatchDev& P, int per, const float2* inv, const TIN* r, float2* pbuf,
+                                   cudaStream_t st) {
+  const size_t sm = (size_t)P.max_n * sizeof(float2) + 16;
+  int64_t nch = 0;
+  const int2* chunks = patch_chunks(P, per, &nch);
+  if (per == 2)
+    k_patch_apply<float2, TIN, 2><<<(unsigned)nch, 256, sm, st>>>(P.ptr, P.dofs, P.val_ptr, chunks, inv, r, pbuf);
+  else
+    k_patch_apply<float2, TIN, 1><<<(unsigned)nch, 256, sm, st>>>(P.ptr, P.dofs, P.val_ptr, chunks, inv, r, pbuf);
+  DPG_CHECK_LAUNCH();
 }
 
 // y[g] = (accumulate ? y[g] : 0) + theta * sum_{slots of g} pbuf[slot]

@@ -10,6 +10,7 @@
 // Every kernel is templated on the complex type of the V-cycle (complex128
 // on the FP64 path, complex64 on the mixed path); CG always runs in FP64.
 #include <algorithm>
+#include <initializer_list>
 #include <map>
 #include <mutex>
 #include <tuple>
@@ -483,6 +484,21 @@ static void configure_smoother_kernels() {
   DPG_CUDA(cudaFuncSetAttribute(k_patch_apply_h<float2, float2>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
 }
 
+// pbuf = per-patch products A_jj^-1 (R_j r) (full storage)
+template <class C> static void patch_product(const PatchDev& P, const C* inv, const C* r, C* pbuf, cudaStream_t st);
+template <>
+void patch_product<float2>(const PatchDev& P, const float2* inv, const float2* r, float2* pbuf, cudaStream_t st) {
+  launch_patch_apply_c64<float2>(P, P.cols, inv, r, pbuf, st);
+}
+template <>
+void patch_product<double2>(const PatchDev& P, const double2* inv, const double2* r, double2* pbuf, cudaStream_t st) {
+  const size_t sm = (size_t)P.max_n * sizeof(double2) + 16;
+  int64_t nch = 0;
+  const int2* chunks = patch_chunks(P, 1, &nch);
+  k_patch_apply<double2, double2><<<(unsigned)nch, 256, sm, st>>>(P.ptr, P.dofs, P.val_ptr, chunks, inv, r, pbuf);
+  DPG_CHECK_LAUNCH();
+}
+
 template <class C>
 static void smooth(const Level& L, const C* r, C* y, double theta, int accumulate, C* pbuf, cudaStream_t st,
                    SystemImpl* prof = nullptr) {
@@ -498,12 +514,8 @@ static void smooth(const Level& L, const C* r, C* y, double theta, int accumulat
     DPG_CHECK_LAUNCH();
     return;
   }
-  size_t sm = (size_t)P.max_n * sizeof(C) + 16;
-  int64_t nch = 0;
-  const int2* chunks = patch_chunks<C>(P, &nch);
   int pe = prof_begin(prof, st);
-  k_patch_apply<C, C><<<(unsigned)nch, 256, sm, st>>>(P.ptr, P.dofs, P.val_ptr, chunks, Prec<C>::inv(P), r, pbuf);
-  DPG_CHECK_LAUNCH();
+  patch_product<C>(P, Prec<C>::inv(P), r, pbuf, st);
   prof_end(prof, pe, st);
   k_slot_sum<C, C><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(P.slot_ptr, P.slots, pbuf, y, n, theta, accumulate);
   DPG_CHECK_LAUNCH();
@@ -966,7 +978,17 @@ struct Evict {
 };
 
 template <class F>
+static int pick_variant(const TuneKey& key, const Evict& ev, cudaStream_t st, std::initializer_list<int> variants,
+                        F&& run);
+
+template <class F>
 static int pick_group(const TuneKey& key, const Evict& ev, cudaStream_t st, F&& run) {
+  return pick_variant(key, ev, st, {1, 2, 4, 8}, run);
+}
+
+template <class F>
+static int pick_variant(const TuneKey& key, const Evict& ev, cudaStream_t st, std::initializer_list<int> variants,
+                        F&& run) {
   {
     std::lock_guard<std::mutex> lk(g_tune_mu);
     auto it = g_tune.find(key);
@@ -978,9 +1000,9 @@ static int pick_group(const TuneKey& key, const Evict& ev, cudaStream_t st, F&& 
     DPG_CUDA(cudaEventCreate(&a[r]));
     DPG_CUDA(cudaEventCreate(&b[r]));
   }
-  int best = 1;
+  int best = *variants.begin();
   float best_ms = 0.f;
-  for (int G = 1; G <= 8; G *= 2) {
+  for (int G : variants) {
     run(G);
     for (int r = 0; r < REPS; ++r) {
       ev.run(st);
@@ -995,7 +1017,7 @@ static int pick_group(const TuneKey& key, const Evict& ev, cudaStream_t st, F&& 
       DPG_CUDA(cudaEventElapsedTime(&t, a[r], b[r]));
       ms += t;
     }
-    if (G == 1 || ms < best_ms) {
+    if (G == *variants.begin() || ms < best_ms) {
       best = G;
       best_ms = ms;
     }
@@ -1098,6 +1120,13 @@ void prepare_solve(SystemImpl& S, cudaStream_t st) {
       float2 *x = W.w32[l].x, *y = W.w32[l].t;
       DPG_CUDA(cudaMemsetAsync(x, 0, (size_t)n * sizeof(float2), st));
       F.A.gsel[0] = pick_group(key, ev, st, [&](int G) { spmv_g<float2>(F.A, F.A.v32, x, nullptr, y, 0, G, st); });
+      if (F.P.inv32 && F.P.np) {
+        // smoother product: 1 or 2 columns per lane (32- or 64-column work items)
+        const TuneKey skey{3, F.mesh.p, F.kind, log2i(F.P.np)};
+        F.P.cols = pick_variant(skey, ev, st, {1, 2}, [&](int c) {
+          launch_patch_apply_c64<float2>(F.P, c, F.P.inv32, x, W.w32[l].pbuf, st);
+        });
+      }
     } else {
       double2 *x = W.w64[l].x, *y = W.w64[l].t;
       DPG_CUDA(cudaMemsetAsync(x, 0, (size_t)n * sizeof(double2), st));

@@ -1,0 +1,94 @@
+"""Edge and degenerate cases of the solve path, through the C ABI.
+
+* zero load: b = 0 gives x = 0 and fields 0 after no CG step;
+* one level: the V-cycle is the dense coarsest solve, so PCG converges at
+  once and equals the oracle's dense solve;
+* the smallest mesh (one element, p = 1) and a flat, ragged 1 x 2 x 5 mesh;
+* a max_iter cap reports NOT_CONVERGED with the iterate written;
+* invalid inputs are refused with DPGMG_ERR_ARG before any device work.
+"""
+import numpy as np
+import pytest
+
+from oracle.solver import mg_pcg
+from paper_2304_01728_gb300 import dpgmg as D
+from tests.oracle_adapter import oracle_system, rel
+
+pytestmark = pytest.mark.gpu
+
+
+def _solve(pk, ok):
+    with D.Solver(pk, **ok) as s:
+        x, f, st, code = s.solve()
+    return x, f, st, code
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_zero_load(precision):
+    pk = dict(n=(3, 3, 3), p=2, omega=5.0, src_amp=0.0)
+    x, f, st, code = _solve(pk, dict(n_levels=2, p_min=1, precision=precision))
+    assert code == D.DPGMG_OK and st.iters == 0
+    assert not np.any(x) and not np.any(f)
+
+
+@pytest.mark.parametrize("n,p", [((1, 1, 1), 1), ((2, 1, 3), 2), ((3, 3, 3), 2)])
+def test_single_level_is_a_direct_solve(n, p):
+    pk = dict(n=n, p=p, omega=4.0, src_center=(0.4, 0.5, 0.6), src_width=0.3)
+    ok = dict(n_levels=1, p_min=p, precision="fp64", tol=1e-10)
+    fs, A, b, _ = oracle_system(pk, ok, hierarchy=False)
+    x_ref = np.linalg.solve(A.toarray() if hasattr(A, "toarray") else A, b)
+    x, f, st, code = _solve(pk, ok)
+    assert code == D.DPGMG_OK and st.iters <= 2, st.iters
+    assert rel(x, x_ref) < 1e-10
+    f_ref = fs.fields(x_ref)
+    assert rel(f.reshape(f_ref.shape), f_ref) < 1e-10
+
+
+def test_flat_ragged_mesh_matches_oracle():
+    pk = dict(n=(1, 2, 5), p=2, omega=6.0, x1=(0.4, 0.8, 2.0), src_center=(0.2, 0.4, 1.1), src_width=0.2)
+    ok = dict(n_levels=2, p_min=1, precision="fp64", tol=1e-8)
+    fs, A, b, levels = oracle_system(pk, ok)
+    x_ref, it_ref, _ = mg_pcg(levels, A, b, tol=ok["tol"])
+    x, f, st, code = _solve(pk, ok)
+    assert code == D.DPGMG_OK
+    assert abs(st.iters - it_ref) <= max(1, 0.1 * it_ref), (st.iters, it_ref)
+    assert rel(x, x_ref) < 1e-7
+
+
+def test_iteration_cap_reports_not_converged():
+    pk = dict(n=(4, 4, 4), p=2, omega=4.0)
+    x, f, st, code = _solve(pk, dict(n_levels=2, p_min=1, precision="fp64", max_iter=2))
+    assert code == D.DPGMG_ERR_NOT_CONVERGED
+    assert st.iters == 2 and st.relres > 1e-8
+    assert np.linalg.norm(x) > 0
+
+
+@pytest.mark.parametrize("bad", [
+    dict(problem=dict(n=(0, 4, 4))),
+    dict(problem=dict(omega=0.0)),
+    dict(problem=dict(omega=-1.0)),
+    dict(problem=dict(p=6)),
+    dict(problem=dict(src_width=0.0)),
+    dict(problem=dict(x1=(1.0, 0.0, 1.0))),
+    dict(problem=dict(wavespeed=np.r_[np.ones(63), -1.0])),
+    dict(problem=dict(wavespeed=np.r_[np.ones(63), np.nan])),
+    dict(opts=dict(tol=0.0)),
+    dict(opts=dict(n_levels=0)),
+    dict(opts=dict(max_iter=0)),
+    dict(opts=dict(flags=8)),
+])
+def test_invalid_inputs_are_refused(bad):
+    pk = dict(dict(n=(4, 4, 4), p=2, omega=4.0), **bad.get("problem", {}))
+    ok = dict(dict(n_levels=2, p_min=1), **bad.get("opts", {}))
+    pb, keep = D.make_problem(**pk)
+    op = D.make_opts(**ok)
+    with pytest.raises(D.DpgmgError) as e:
+        D.dpgmg_query_sizes(pb, op)
+    assert e.value.code == D.DPGMG_ERR_ARG
+    h = D.dpgmg_create(0)
+    try:
+        with pytest.raises(D.DpgmgError) as e:
+            D.dpgmg_setup(h, pb, op)
+        assert e.value.code == D.DPGMG_ERR_ARG
+    finally:
+        D.dpgmg_destroy(h)
