@@ -163,14 +163,14 @@ static void fill_bytes_per_iter(SystemImpl& S) {
   const Level& F = S.levels.back();
   // CG operator (FP64)
   int64_t cg_nnz = 0;
-  if (S.levels.size() > 1 && F.kind == 1) cg_nnz = F.A.nnz;
+  if (S.levels.size() > 1 && F.kind == 1) cg_nnz = F.A.nnz_alg;
   else cg_nnz = (int64_t)(F.mesh.nelem * (double)F.nloc * F.nloc * 0.8);
   b += cg_nnz * 16.0;
   const int nu = S.op.nu_pre + S.op.nu_post;
   for (size_t l = 1; l < S.levels.size(); ++l) {
     const Level& L = S.levels[l];
     b += nu * (double)L.P.sum_sq * esz;                                          // smoother (n_j^2 per patch)
-    b += std::max(1, nu) * (double)L.A.nnz * esz;                                // residual SpMVs
+    b += std::max(1, nu) * (double)L.A.nnz_alg * esz;                            // residual SpMVs
     if (L.kind == 2) b += (double)L.nK * (2.0 * L.nI * L.nS + L.nI * L.nI) * esz; // condense + backsub
   }
   const Level& C0 = S.levels[0];
@@ -465,7 +465,7 @@ int dpgmg_level_info(dpgmg_handle h, dpgmg_system sys, int level, dpgmg_level_de
   out->n_patches = L.P.np;
   out->patch_max = L.P.max_n;
   out->sum_patch_sq = L.P.sum_sq;
-  out->op_nnz = L.A.nnz;
+  out->op_nnz = L.A.nnz_alg;
   out->theta = L.theta;
   out->patch_stored = L.P.half ? L.P.nhvals : L.P.nvals;
   return DPGMG_OK;

@@ -422,7 +422,7 @@ ECSRHost build_ecsr(const MeshL& m, const std::vector<std::vector<int64_t>>& gro
         c += fn;
       }
       nb[r] = cols;
-      ncol[r] = c;
+      ncol[r] = c;   // padded to even below
     }
   });
   A.row_ent.assign(m.ndof, -1);
@@ -430,14 +430,17 @@ ECSRHost build_ecsr(const MeshL& m, const std::vector<std::vector<int64_t>>& gro
   A.ent_nd.resize(R);
   A.col_ptr.assign(R + 1, 0);
   A.val_ptr.assign(R + 1, 0);
+  A.nnz_alg = 0;
   for (int64_t r = 0; r < R; ++r) {
     int64_t st;
     int nd;
     m.ent_range(rows[r], &st, &nd);
     A.ent_start[r] = st;
     A.ent_nd[r] = nd;
-    A.col_ptr[r + 1] = A.col_ptr[r] + ncol[r];
-    A.val_ptr[r + 1] = A.val_ptr[r] + ncol[r] * nd;
+    const int64_t padded = ncol[r] + (ncol[r] & 1);
+    A.col_ptr[r + 1] = A.col_ptr[r] + padded;
+    A.val_ptr[r + 1] = A.val_ptr[r] + padded * nd;
+    A.nnz_alg += ncol[r] * nd;
     for (int k = 0; k < nd; ++k) A.row_ent[st + k] = (int32_t)r;
   }
   A.col_idx.resize(A.col_ptr[R]);
@@ -450,6 +453,7 @@ ECSRHost build_ecsr(const MeshL& m, const std::vector<std::vector<int64_t>>& gro
         m.ent_range(F, &fs, &fn);
         for (int k = 0; k < fn; ++k) *out++ = (int32_t)(fs + k);
       }
+      if (ncol[r] & 1) *out = out[-1];   // padding: repeat the last column
     }
   });
   return A;

@@ -24,6 +24,7 @@ void assemble_ecsr(Alloc& A, const MeshL& m, const ECSRHost& H, ECSRDev& D, cuda
   D.nrows = H.nrows;
   D.nent = (int64_t)H.ent_start.size();
   D.nnz = H.nnz();
+  D.nnz_alg = H.nnz_alg;
   D.row_ent = upload(A, H.row_ent, st);
   D.ent_start = upload(A, H.ent_start, st);
   D.ent_nd = upload(A, H.ent_nd, st);

@@ -151,6 +151,39 @@ __global__ void __launch_bounds__(256) k_spmv(const int32_t* __restrict__ row_en
   }
 }
 
+// complex64 rows, two columns per lane: rows have even length (padded column
+// lists), so (value, value) pairs are 16-byte and (column, column) pairs
+// 8-byte aligned loads.
+__global__ void __launch_bounds__(256) k_spmv_pairs(const int32_t* __restrict__ row_ent,
+                                                    const int64_t* __restrict__ ent_start,
+                                                    const int64_t* __restrict__ col_ptr,
+                                                    const int32_t* __restrict__ col_idx,
+                                                    const int64_t* __restrict__ val_ptr, const float2* __restrict__ v,
+                                                    const float2* __restrict__ x, const float2* __restrict__ b,
+                                                    float2* __restrict__ y, int64_t nrows, int mode) {
+  using O = Ops<float2>;
+  const int lane = threadIdx.x & 31;
+  const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t row = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); row < nrows; row += nw) {
+    const int32_t E = row_ent[row];
+    float2 acc = O::zero(), acc1 = O::zero();
+    if (E >= 0) {
+      const int64_t c0 = col_ptr[E];
+      const int nnz = (int)(col_ptr[E + 1] - c0);   // even
+      const float4* v4 = reinterpret_cast<const float4*>(v + val_ptr[E] + (row - ent_start[E]) * nnz);
+      const int2* c2 = reinterpret_cast<const int2*>(col_idx + c0);
+      for (int k = lane; 2 * k < nnz; k += 32) {
+        const float4 vv = __ldcs(v4 + k);
+        const int2 cc = c2[k];
+        acc = O::fma(make_float2(vv.x, vv.y), x[cc.x], acc);
+        acc1 = O::fma(make_float2(vv.z, vv.w), x[cc.y], acc1);
+      }
+      acc = warp_sum(O::add(acc, acc1));
+    }
+    if (lane == 0) y[row] = mode ? O::sub(b[row], acc) : acc;
+  }
+}
+
 // Entity-blocked SpMV: one warp per task (entity E, rows r0 .. r0 + G - 1 of
 // E).  The G rows share E's column list, so each column index and x entry is
 // loaded once for G rows and G value streams are in flight per column.
@@ -213,8 +246,15 @@ template <class C>
 static void spmv_g(const ECSRDev& A, const C* vals, const C* x, const C* b, C* y, int mode, int G, cudaStream_t st) {
   if (G <= 1 || !A.tasks[1]) {
     int64_t blocks = std::min<int64_t>((A.nrows + 7) / 8, 152 * 16);
-    k_spmv<C><<<(unsigned)blocks, 256, 0, st>>>(A.row_ent, A.ent_start, A.col_ptr, A.col_idx, A.val_ptr, vals, x, b,
-                                                 y, A.nrows, mode);
+    if (sizeof(C) == sizeof(float2))
+      k_spmv_pairs<<<(unsigned)blocks, 256, 0, st>>>(A.row_ent, A.ent_start, A.col_ptr, A.col_idx, A.val_ptr,
+                                                     reinterpret_cast<const float2*>(vals),
+                                                     reinterpret_cast<const float2*>(x),
+                                                     reinterpret_cast<const float2*>(b), reinterpret_cast<float2*>(y),
+                                                     A.nrows, mode);
+    else
+      k_spmv<C><<<(unsigned)blocks, 256, 0, st>>>(A.row_ent, A.ent_start, A.col_ptr, A.col_idx, A.val_ptr, vals, x, b,
+                                                   y, A.nrows, mode);
     DPG_CHECK_LAUNCH();
     return;
   }
@@ -304,14 +344,17 @@ __global__ void __launch_bounds__(256) k_spmv_df(const int32_t* __restrict__ row
       const int nnz = (int)(col_ptr[E + 1] - c0);
       const int64_t off = val_ptr[E] + (row - ent_start[E]) * nnz;
       const int32_t* cols = col_idx + c0;
-      for (int k = lane; k < nnz; k += 64) {
-        // two columns per lane per step, all loads issued before the arithmetic
-        const bool two = k + 32 < nnz;
-        const float2 ah0 = __ldcs(vh + off + k), al0 = __ldcs(vl + off + k);
-        const int cA = cols[k];
-        const float2 ah1 = two ? __ldcs(vh + off + k + 32) : make_float2(0.f, 0.f);
-        const float2 al1 = two ? __ldcs(vl + off + k + 32) : make_float2(0.f, 0.f);
-        const int cB = two ? cols[k + 32] : cA;
+      // two adjacent columns per lane (rows have even length): 16-byte value
+      // loads and one 8-byte load of the column pair
+      const float4* vh4 = reinterpret_cast<const float4*>(vh + off);
+      const float4* vl4 = reinterpret_cast<const float4*>(vl + off);
+      const int2* c2 = reinterpret_cast<const int2*>(cols);
+      for (int k = lane; 2 * k < nnz; k += 32) {
+        const float4 h = __ldcs(vh4 + k), l = __ldcs(vl4 + k);
+        const int2 cc = c2[k];
+        const float2 ah0 = make_float2(h.x, h.y), al0 = make_float2(l.x, l.y);
+        const float2 ah1 = make_float2(h.z, h.w), al1 = make_float2(l.z, l.w);
+        const int cA = cc.x, cB = cc.y;
         const float2 uh0 = xh[cA], ul0 = xl[cA], uh1 = xh[cB], ul1 = xl[cB];
         float p, q;
         df_mul(ah0.x, al0.x, uh0.x, ul0.x, p, q);
@@ -1151,8 +1194,8 @@ int pcg_solve(SystemImpl& S, cudaStream_t st, double2* xout, dpgmg_stats* stats)
     const Level& Ff = S.levels.back();
     const int64_t esz = S.op.precision == DPGMG_PREC_MIXED ? 8 : 16;
     if (S.prof_which == DPGMG_PROF_SMOOTH_FINE) S.prof_bytes = Ff.P.sum_sq * esz;   // full-storage algorithmic bytes
-    else if (S.prof_which == DPGMG_PROF_SPMV_FINE) S.prof_bytes = Ff.A.nnz * esz;
-    else if (S.prof_which == DPGMG_PROF_SPMV_CG) S.prof_bytes = A.nnz * 16;   // hi + lo complex64
+    else if (S.prof_which == DPGMG_PROF_SPMV_FINE) S.prof_bytes = Ff.A.nnz_alg * esz;
+    else if (S.prof_which == DPGMG_PROF_SPMV_CG) S.prof_bytes = A.nnz_alg * 16;   // hi + lo complex64
   }
   const int64_t n = S.levels.back().mesh.ndof;
   cudaEvent_t e0, e1;
