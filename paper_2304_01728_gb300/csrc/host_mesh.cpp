@@ -422,7 +422,7 @@ ECSRHost build_ecsr(const MeshL& m, const std::vector<std::vector<int64_t>>& gro
         c += fn;
       }
       nb[r] = cols;
-      ncol[r] = c;   // padded to even below
+      ncol[r] = c;
     }
   });
   A.row_ent.assign(m.ndof, -1);
@@ -437,9 +437,8 @@ ECSRHost build_ecsr(const MeshL& m, const std::vector<std::vector<int64_t>>& gro
     m.ent_range(rows[r], &st, &nd);
     A.ent_start[r] = st;
     A.ent_nd[r] = nd;
-    const int64_t padded = ncol[r] + (ncol[r] & 1);
-    A.col_ptr[r + 1] = A.col_ptr[r] + padded;
-    A.val_ptr[r + 1] = A.val_ptr[r] + padded * nd;
+    A.col_ptr[r + 1] = A.col_ptr[r] + ncol[r];
+    A.val_ptr[r + 1] = A.val_ptr[r] + ncol[r] * nd;
     A.nnz_alg += ncol[r] * nd;
     for (int k = 0; k < nd; ++k) A.row_ent[st + k] = (int32_t)r;
   }
@@ -453,7 +452,6 @@ ECSRHost build_ecsr(const MeshL& m, const std::vector<std::vector<int64_t>>& gro
         m.ent_range(F, &fs, &fn);
         for (int k = 0; k < fn; ++k) *out++ = (int32_t)(fs + k);
       }
-      if (ncol[r] & 1) *out = out[-1];   // padding: repeat the last column
     }
   });
   return A;

@@ -67,10 +67,7 @@ std::vector<LevelSpec> plan_levels(const int n[3], int p, int n_levels, int p_mi
 
 // Entity-shared CSR ("ECSR"): rows are grouped by entity; all rows of one
 // entity share one sorted list of column DOFs.  Values of row r of entity E
-// start at val_ptr[E] + (r - start(E)) * nnz_row(E).  Each column list is
-// padded to even length by repeating its last column (the padded value
-// slots stay 0 and a lower-bound search never lands on them), so complex64
-// values and column pairs can be read with 16- and 8-byte loads.
+// start at val_ptr[E] + (r - start(E)) * nnz_row(E).
 struct ECSRHost {
   int64_t nrows = 0;                 // = ndof of the level (non-row DOFs have row_ent = -1)
   std::vector<int32_t> row_ent;      // per DOF: compact row-entity index or -1
@@ -79,8 +76,8 @@ struct ECSRHost {
   std::vector<int64_t> col_ptr;      // per row entity (+1): offset in col_idx
   std::vector<int32_t> col_idx;      // expanded column DOFs, sorted per entity
   std::vector<int64_t> val_ptr;      // per row entity (+1): value offset
-  int64_t nnz() const { return val_ptr.empty() ? 0 : val_ptr.back(); }   // stored (padded) entries
-  int64_t nnz_alg = 0;               // entries of the operator itself (without padding)
+  int64_t nnz() const { return val_ptr.empty() ? 0 : val_ptr.back(); }
+  int64_t nnz_alg = 0;               // = nnz(): entries of the operator
 };
 // groups: for each super-element, the list of entity ids it touches.
 ECSRHost build_ecsr(const MeshL& m, const std::vector<std::vector<int64_t>>& groups);

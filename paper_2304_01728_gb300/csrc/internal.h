@@ -57,7 +57,7 @@ template <class T> T* upload(Alloc& A, const std::vector<T>& h, cudaStream_t s) 
 // ----------------------------------------------------------- device structs
 struct ECSRDev {
   int64_t nrows = 0, nent = 0, nnz = 0, max_nnz_row = 0;
-  int64_t nnz_alg = 0;     // operator entries without the even-length padding of the rows
+  int64_t nnz_alg = 0;     // operator entries (algorithmic bytes count these)
   int32_t* row_ent = nullptr;
   int64_t* ent_start = nullptr;
   int32_t* ent_nd = nullptr;
