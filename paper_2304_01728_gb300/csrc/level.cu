@@ -531,6 +531,7 @@ void build_hierarchy(SystemImpl& S, cudaStream_t st) {
   int info = 0;
   DPG_CUDA(cudaMemcpyAsync(&info, dinfo, sizeof(int), cudaMemcpyDeviceToHost, st));
   DPG_CUDA(cudaStreamSynchronize(st));
+  if (info & 32) throw Err{DPGMG_ERR_TIMEOUT, "tensor-core update: a bounded wait for the MMAs ran out"};
   if (info) throw Err{DPGMG_ERR_NOT_HPD, "a macro, patch or coarsest factorisation lost positive definiteness"};
 }
 

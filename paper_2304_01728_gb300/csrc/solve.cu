@@ -729,7 +729,6 @@ struct WS {
   double2 *x = nullptr, *r = nullptr, *p = nullptr, *q = nullptr, *z = nullptr, *part = nullptr, *sc = nullptr;
   float2 *xh = nullptr, *xl = nullptr;     // double-float split of the CG operand
   double2* sc_host = nullptr;    // pinned scalar read-back (a few bytes per CG step)
-  int* err = nullptr;
   ECSRDev Acg;                   // the CG operator (finest A_L, FP64)
   bool acg_owned = false;
 };
@@ -771,8 +770,6 @@ void ensure_workspace(SystemImpl& S, cudaStream_t st) {
   W->xl = S.mem.arr<float2>((size_t)n);
   W->sc = S.mem.arr<double2>(SC_COUNT);
   DPG_CUDA(cudaMallocHost(&W->sc_host, SC_COUNT * sizeof(double2)));
-  W->err = S.mem.arr<int>(1);
-  DPG_CUDA(cudaMemsetAsync(W->err, 0, sizeof(int), st));
   alloc_level_ws<double2>(*W, S);
   if (S.op.precision == DPGMG_PREC_MIXED) alloc_level_ws<float2>(*W, S);
   DPG_CUDA(cudaStreamSynchronize(st));
@@ -903,13 +900,6 @@ static void dot(WS& W, const double2* u, const double2* v, int64_t n, int which,
   DPG_CHECK_LAUNCH();
   k_dot_finish<<<1, 256, 0, st>>>(W.part, RED_BLOCKS, W.sc, which);
   DPG_CHECK_LAUNCH();
-}
-
-static int check_err(WS& W, cudaStream_t st) {
-  int e = 0;
-  DPG_CUDA(cudaMemcpyAsync(&e, W.err, sizeof(int), cudaMemcpyDeviceToHost, st));
-  DPG_CUDA(cudaStreamSynchronize(st));
-  return e;
 }
 
 static const ECSRDev& cg_operator(SystemImpl& S, WS& W, cudaStream_t st) {
@@ -1223,7 +1213,6 @@ int pcg_solve(SystemImpl& S, cudaStream_t st, double2* xout, dpgmg_stats* stats)
   DPG_CUDA(cudaEventElapsedTime(&ms, e0, e1));
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
-  if (check_err(W, st)) status = DPGMG_ERR_TIMEOUT;
   // true residual ||b - A x|| / ||b|| in FP64
   double true_rel = 0.0;
   if (nb > 0.0) {
@@ -1417,7 +1406,6 @@ void apply_op(SystemImpl& S, int op, int l, const double2* x, double2* y, cudaSt
     apply_t<double2>(S, W, op, l, x, y, st);
   }
   DPG_CHECK_LAUNCH();
-  if (check_err(W, st)) throw Err{DPGMG_ERR_TIMEOUT, "coarse solve barrier timed out"};
 }
 
 }  // namespace dpgmg
