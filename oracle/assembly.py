@@ -21,6 +21,7 @@ class FineSystem:
     def __init__(self, mesh, omega, wavespeed=None, load=None, elements=None):
         self.mesh = mesh
         self.omega = float(omega)
+        self.load = load
         ne = mesh.n_elem
         self.c = np.ones(ne) if wavespeed is None else np.asarray(wavespeed, dtype=np.float64)
         p = mesh.p
