@@ -273,6 +273,18 @@ long long dpgmg_launch_count(void);
  * invalid level or size.  Results do not depend on G beyond rounding order. */
 int dpgmg_spmv_group(dpgmg_handle h, dpgmg_system sys, int level, int set, int* group);
 
+/* DPG error indicator (Sec. 1.2: the residual that DPG minimises, in the
+ * dual test norm, is the method's built-in error indicator; Sec. 3 refines
+ * by it).  For the trace vector x (host, interleaved complex128 [n_trace],
+ * e.g. the output of dpgmg_solve) the fields are recovered element by element
+ * and every finest element's
+ *     eta_K^2 = (l_K - B_K u_K)^* G_K^-1 (l_K - B_K u_K)
+ * is written to eta2 (host double [n0*n1*n2], element order of the mesh),
+ * u_K = [fields, local traces].  The global DPG residual is sum_K eta_K^2.
+ * Recomputes G_K, B_K, l_K and the Gram Cholesky per element (FP64).
+ * Errors: ARG (null argument), NOT_HPD, CUDA. */
+int dpgmg_error_indicator(dpgmg_handle h, dpgmg_system sys, const double* x, double* eta2);
+
 /* Setup phases of a system: device time of the batched element stage
  * (Sec. 2: Gram, B and load, Cholesky, optimal test functions, DPG matrix,
  * field condensation), its algorithmic GFLOP (an FMA counts 2 flops, a

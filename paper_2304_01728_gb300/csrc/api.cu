@@ -422,6 +422,29 @@ int dpgmg_profile_read(dpgmg_handle h, dpgmg_system sys, double* total_ms, long 
   }
 }
 
+int dpgmg_error_indicator(dpgmg_handle h, dpgmg_system sys, const double* x, double* eta2) {
+  if (!h || !sys || !x || !eta2) return DPGMG_ERR_ARG;
+  std::lock_guard<std::mutex> lk(h->mu);
+  SystemImpl& S = sys->s;
+  try {
+    DPG_CUDA(cudaSetDevice(h->h.device));
+    cudaStream_t s = h->h.stream;
+    const int64_t n = S.levels.back().mesh.ndof;
+    Alloc tmp;
+    tmp.budget = (size_t)-1;
+    tmp.stream = s;
+    double2* dx = tmp.arr<double2>((size_t)std::max<int64_t>(n, 1));
+    double* de = tmp.arr<double>((size_t)std::max<int64_t>(S.nelem, 1));
+    DPG_CUDA(cudaMemcpyAsync(dx, x, (size_t)n * sizeof(double2), cudaMemcpyHostToDevice, s));
+    error_indicator(S, dx, de, s);
+    DPG_CUDA(cudaMemcpyAsync(eta2, de, (size_t)S.nelem * sizeof(double), cudaMemcpyDeviceToHost, s));
+    DPG_CUDA(cudaStreamSynchronize(s));
+    return DPGMG_OK;
+  } catch (const Err& e) {
+    return fail(e);
+  }
+}
+
 int dpgmg_setup_profile(dpgmg_handle h, dpgmg_system sys, double* element_ms, double* element_gflop,
                         double* setup_ms) {
   if (!h || !sys) return DPGMG_ERR_ARG;

@@ -510,7 +510,107 @@ void element_stage(SystemImpl& S, cudaStream_t st) {
   A.release(a.K);
   A.release(dreal);
   A.release(dcplx);
+  a.G = nullptr;
+  a.W = nullptr;
+  a.K = nullptr;
+  a.elist = nullptr;
+  S.eargs = std::make_shared<ElemArgs>(a);
   if (info) throw Err{DPGMG_ERR_NOT_HPD, "element Gram or field block not positive definite"};
+}
+
+// DPG error indicator (Sec. 1.2: the minimised residual is the method's
+// built-in error indicator; it drives the refinements of Sec. 3):
+//   eta_K^2 = (l - B u_K)^* G^-1 (l - B u_K)
+// for the element trial vector u_K = [fields, local traces].  With the test
+// scaling of the real form (G = D G' D^H, B = D B', l = D l', D unitary and
+// diagonal) this is || L^-1 (l' - B' u_K) ||^2 with G' = L L^T.  Per element
+// (after k_elem_build<double2> and k_elem_potrf on the same chunk): r = l' -
+// B' u_K into the load column, forward substitution, squared norm.
+__global__ void __launch_bounds__(CTA_THREADS) k_elem_eta(ElemArgs a, const double2* __restrict__ fields,
+                                                          const int64_t* __restrict__ dofs,
+                                                          const double2* __restrict__ x, double* __restrict__ eta2) {
+  extern __shared__ unsigned char she[];
+  const int64_t le = blockIdx.x;
+  const int64_t e = a.elist[a.e0 + le];
+  const int nt = a.nt, m = a.m, ldw = m + 1;
+  const double* L = a.G + le * (size_t)nt * nt;
+  double2* W = reinterpret_cast<double2*>(a.W) + le * (size_t)nt * ldw;
+  double2* u = reinterpret_cast<double2*>(she);               // [m]
+  char* tsm = reinterpret_cast<char*>(u + m);                   // triangular-solve scratch
+  for (int j = threadIdx.x; j < m; j += blockDim.x) {
+    if (j < a.nf) {
+      u[j] = fields[e * a.nf + j];
+    } else {
+      const int64_t g = dofs[e * a.ntr + (j - a.nf)];
+      u[j] = g >= 0 ? x[g] : make_double2(0.0, 0.0);
+    }
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < nt; i += blockDim.x) {
+    const double2* row = W + (size_t)i * ldw;
+    double2 acc = row[m];
+    for (int j = 0; j < m; ++j) acc = Ops<double2>::fnma(row[j], u[j], acc);
+    W[(size_t)i * ldw + m] = acc;
+  }
+  __syncthreads();
+  cta_trsm_lower<double, double2>(L, nt, nt, W + m, 1, ldw, tsm);
+  __shared__ double red[CTA_THREADS / 32];
+  double s2 = 0.0;
+  for (int i = threadIdx.x; i < nt; i += blockDim.x) {
+    const double2 y = W[(size_t)i * ldw + m];
+    s2 += y.x * y.x + y.y * y.y;
+  }
+  for (int o = 16; o > 0; o >>= 1) s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s2;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < CTA_THREADS / 32; ++w) t += red[w];
+    eta2[e] = t;
+  }
+}
+
+void error_indicator(SystemImpl& S, const double2* x, double* eta2, cudaStream_t st) {
+  if (!S.eargs) throw Err{DPGMG_ERR_ARG, "the system has no element stage"};
+  ElemArgs a = *S.eargs;
+  Alloc& A = S.mem;
+  const Level& L = S.levels.back();
+  const int64_t nel = S.nelem;
+  double2* fields = A.arr<double2>((size_t)std::max<int64_t>(nel * a.nf, 1));
+  recover_fields(S, x, fields, st);
+  std::vector<int64_t> all(nel);
+  for (int64_t e = 0; e < nel; ++e) all[e] = e;
+  int64_t* dall = upload(A, all, st);
+  const size_t per = (size_t)a.nt * a.nt * 8 + (size_t)a.nt * (a.m + 1) * 16;
+  const int64_t chunk = element_chunk(nel, per);
+  a.G = A.arr<double>((size_t)chunk * a.nt * a.nt);
+  a.W = A.arr<double2>((size_t)chunk * a.nt * (a.m + 1));
+  a.elist = dall;
+  a.info = A.arr<int>(1);
+  DPG_CUDA(cudaMemsetAsync(a.info, 0, sizeof(int), st));
+  const size_t sm_build = (size_t)4 * a.nql * a.nql * a.nql * sizeof(double2) + 64;
+  const size_t sm_real = smem_bytes_dense(8);
+  const size_t sm_eta = (size_t)a.m * sizeof(double2) + smem_bytes_dense(16);
+  DPG_CUDA(cudaFuncSetAttribute(k_elem_eta, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_eta));
+  for (int64_t e0 = 0; e0 < nel; e0 += chunk) {
+    a.e0 = e0;
+    const int nb = (int)std::min<int64_t>(chunk, nel - e0);
+    k_elem_build<double2><<<nb, CTA_THREADS, sm_build, st>>>(a);
+    DPG_CHECK_LAUNCH();
+    k_elem_potrf<<<nb, CTA_THREADS, sm_real, st>>>(a);
+    DPG_CHECK_LAUNCH();
+    k_elem_eta<<<nb, CTA_THREADS, sm_eta, st>>>(a, fields, L.dofs, x, eta2);
+    DPG_CHECK_LAUNCH();
+  }
+  int info = 0;
+  DPG_CUDA(cudaMemcpyAsync(&info, a.info, sizeof(int), cudaMemcpyDeviceToHost, st));
+  DPG_CUDA(cudaStreamSynchronize(st));
+  A.release(a.G);
+  A.release(a.W);
+  A.release(a.info);
+  A.release(dall);
+  A.release(fields);
+  if (info) throw Err{DPGMG_ERR_NOT_HPD, "element Gram not positive definite"};
 }
 
 void recover_fields(SystemImpl& S, const double2* x, double2* fields, cudaStream_t st) {

@@ -5,6 +5,7 @@
 #include <cstdint>
 #include <mutex>
 #include <string>
+#include <memory>
 #include <vector>
 
 #include "../../include/dpgmg.h"
@@ -136,6 +137,8 @@ struct Level {
 struct Workspace;   // V-cycle work vectors (per precision)
 struct Server;      // serving loop (server.cu)
 
+struct ElemArgs;   // element-stage arguments (element.cu), kept for the error indicator
+
 struct SystemImpl {
   dpgmg_problem pb;
   dpgmg_opts op;
@@ -159,6 +162,7 @@ struct SystemImpl {
   long long prof_graph_n = 0;          // and their number of timed launches
   int64_t prof_bytes = 0;
   int coarse_blocks = 0;
+  std::shared_ptr<ElemArgs> eargs;   // device tables of the element stage (resident with the system)
 };
 
 struct HandleImpl {
@@ -174,6 +178,8 @@ struct HandleImpl {
 int64_t element_chunk(int64_t nel, size_t per_elem);
 void element_stage(SystemImpl& S, cudaStream_t st);
 void recover_fields(SystemImpl& S, const double2* x, double2* fields, cudaStream_t st);
+// DPG error indicator eta_K^2 of every finest element for the trace vector x (device)
+void error_indicator(SystemImpl& S, const double2* x, double* eta2, cudaStream_t st);
 // level.cu
 void assemble_ecsr(Alloc& A, const MeshL& m, const ECSRHost& H, ECSRDev& D, cudaStream_t st);
 void ecsr_add_elements(ECSRDev& D, const double2* E, const int64_t* dofs, int64_t nel, int nloc,

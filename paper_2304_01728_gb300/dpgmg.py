@@ -66,7 +66,7 @@ EXPORTS = ["dpgmg_create", "dpgmg_destroy", "dpgmg_query_sizes", "dpgmg_default_
            "dpgmg_solve", "dpgmg_release", "dpgmg_strerror", "dpgmg_last_error", "dpgmg_level_info",
            "dpgmg_element_matrix", "dpgmg_rhs", "dpgmg_apply", "dpgmg_launch_count", "dpgmg_profile",
            "dpgmg_profile_read", "dpgmg_smooth_noalloc", "dpgmg_serve_start", "dpgmg_submit", "dpgmg_poll",
-           "dpgmg_spmv_group", "dpgmg_setup_profile"]
+           "dpgmg_spmv_group", "dpgmg_setup_profile", "dpgmg_error_indicator"]
 PROF_OFF, PROF_SMOOTH_FINE, PROF_SPMV_FINE, PROF_SPMV_CG = 0, 1, 2, 3
 
 
@@ -114,6 +114,8 @@ def lib():
     L.dpgmg_spmv_group.restype = i
     L.dpgmg_setup_profile.argtypes = [vp, vp, ctypes.POINTER(d), ctypes.POINTER(d), ctypes.POINTER(d)]
     L.dpgmg_setup_profile.restype = i
+    L.dpgmg_error_indicator.argtypes = [vp, vp, dptr, dptr]
+    L.dpgmg_error_indicator.restype = i
     L.dpgmg_profile_read.argtypes = [vp, vp, ctypes.POINTER(d), ctypes.POINTER(ll), ctypes.POINTER(ll)]
     for f in ["dpgmg_create", "dpgmg_query_sizes", "dpgmg_setup", "dpgmg_solve", "dpgmg_level_info",
               "dpgmg_element_matrix", "dpgmg_rhs", "dpgmg_apply", "dpgmg_profile", "dpgmg_profile_read"]:
@@ -259,6 +261,15 @@ def dpgmg_poll(h, ticket, trace_out=None, field_out=None):
 
 def dpgmg_launch_count():
     return int(lib().dpgmg_launch_count())
+
+
+def dpgmg_error_indicator(h, s, x, nelem):
+    """eta_K^2 of every element for the trace vector x (complex128)."""
+    x = np.ascontiguousarray(x, dtype=np.complex128)
+    eta2 = np.zeros(int(nelem), dtype=np.float64)
+    _check(lib().dpgmg_error_indicator(h, s, _dptr(x), eta2.ctypes.data_as(ctypes.POINTER(ctypes.c_double))),
+           "dpgmg_error_indicator")
+    return eta2
 
 
 def dpgmg_setup_profile(h, s):
