@@ -121,6 +121,12 @@ typedef struct dpgmg_opts {
    where CG stops (on the 16^3 p=3 workload the solution then differs from the
    FP64 oracle's by 2.4e-7 instead of 7.7e-8, with the same iteration count). */
 #define DPGMG_FLAG_TENSOR_CORES 2
+/* Coarse operators "stored" instead of restricted (Sec. 3, the paper's
+   alternative construction): every coarser level's operator is the DPG system
+   assembled directly on its own mesh and order (enriched test order p_c + 1)
+   rather than I^T M I of the finer operator.  Needs a constant wavespeed
+   (DPGMG_ERR_ARG otherwise); transfers and smoothers are unchanged. */
+#define DPGMG_FLAG_STORE_COARSE 4
 
 typedef struct dpgmg_stats {
   int iters;               /* CG iterations (= V-cycle applications) */

@@ -238,8 +238,14 @@ def _patch_rule_R1(lev_mesh, coarse_mesh, table, kind, smask):
 
 
 def build_hierarchy(fine_mesh, Kc, dofs, n_levels, p_min=2, coarsest="cholesky",
-                    theta=None):
-    """All levels from the fine element matrices Kc (condensed) and DOF maps."""
+                    theta=None, stored=None):
+    """All levels from the fine element matrices Kc (condensed) and DOF maps.
+
+    Coarse operators are restricted (Sec. 3, A_c = I^* M I) unless ``stored``
+    is given: stored(mesh) returns the condensed element matrices of the DPG
+    system assembled directly on a coarser mesh (the paper's "stored"
+    alternative), which then replace the restricted ones level by level.
+    """
     specs, kinds = level_specs(fine_mesh.n, fine_mesh.p, n_levels, p_min)
     levels = []
     top = Level()
@@ -332,6 +338,8 @@ def build_hierarchy(fine_mesh, Kc, dofs, n_levels, p_min=2, coarsest="cholesky",
             lev.smask = np.zeros(nf, dtype=bool)
             for Sg in lev.S:
                 lev.smask[Sg] = True
+        if stored is not None:
+            crs.E = stored(cmesh)
         lev.patches = _patch_rule_R1(lev.mesh, cmesh, lev.mesh.dof_table(), kind, lev.smask)
         Md = lev.M
         lev.patch_inv = [np.linalg.inv(Md[idx][:, idx].toarray()) for idx in lev.patches]

@@ -82,8 +82,13 @@ int validate_problem(const dpgmg_problem* pb, const dpgmg_opts* op) {
       op->p_min < 1 || (op->precision != DPGMG_PREC_FP64 && op->precision != DPGMG_PREC_MIXED) ||
       (op->coarsest != DPGMG_COARSEST_CHOLESKY && op->coarsest != DPGMG_COARSEST_NONE &&
        op->coarsest != DPGMG_COARSEST_AUTO) ||
-      (op->flags & ~(DPGMG_FLAG_EAGER | DPGMG_FLAG_TENSOR_CORES)))
+      (op->flags & ~(DPGMG_FLAG_EAGER | DPGMG_FLAG_TENSOR_CORES | DPGMG_FLAG_STORE_COARSE)))
     return DPGMG_ERR_ARG;
+  if ((op->flags & DPGMG_FLAG_STORE_COARSE) && pb->wavespeed) {
+    const int64_t ne = (int64_t)pb->n[0] * pb->n[1] * pb->n[2];
+    for (int64_t e = 1; e < ne; ++e)
+      if (pb->wavespeed[e] != pb->wavespeed[0]) return DPGMG_ERR_ARG;
+  }
   return DPGMG_OK;
 }
 

@@ -371,8 +371,21 @@ int64_t element_chunk(int64_t nel, size_t per_elem) {
 
 static size_t smem_bytes_dense(size_t elt) { return (size_t)(NB * NB + 2 * TL * NB) * elt + 64; }
 
-void element_stage(SystemImpl& S, cudaStream_t st) {
-  Level& L = S.levels.back();
+// Condensed element matrices L.E of level L (c: wavespeed per element of L's
+// mesh).  On the finest level the condensed loads, the recovery blocks and
+// the flop count are kept for the solve; on a coarser level ("stored" coarse
+// operators) they are scratch.
+static void element_core(SystemImpl& S, Level& L, const std::vector<double>& cvals, bool finest, cudaStream_t st);
+
+void element_stage(SystemImpl& S, cudaStream_t st) { element_core(S, S.levels.back(), S.wavespeed, true, st); }
+
+void element_stage_level(SystemImpl& S, Level& L, cudaStream_t st) {
+  // stored coarse operators need a wavespeed per coarse element: only constant c is allowed
+  std::vector<double> c((size_t)L.mesh.nelem, S.wavespeed.empty() ? 1.0 : S.wavespeed[0]);
+  element_core(S, L, c, false, st);
+}
+
+static void element_core(SystemImpl& S, Level& L, const std::vector<double>& cvals, bool finest, cudaStream_t st) {
   const MeshL& m = L.mesh;
   const int p = m.p;
   std::vector<int4> tf, ff, tr;
@@ -403,7 +416,7 @@ void element_stage(SystemImpl& S, cudaStream_t st) {
   a.sw = S.pb.src_width;
   a.sa = S.pb.src_amp;
   a.mfm = S.pb.mf_order;
-  a.c = upload(A, S.wavespeed, st);
+  a.c = upload(A, cvals, st);
   std::vector<double2> mfc(S.mf_coeffs.size() / 2);
   for (size_t i = 0; i < mfc.size(); ++i) mfc[i] = make_double2(S.mf_coeffs[2 * i], S.mf_coeffs[2 * i + 1]);
   a.mfc = upload(A, mfc, st);
@@ -424,16 +437,22 @@ void element_stage(SystemImpl& S, cudaStream_t st) {
   DPG_CUDA(cudaMemsetAsync(a.info, 0, sizeof(int), st));
 
   const int64_t nel = m.nelem;
-  S.nelem = nel;
-  S.nf = a.nf;
-  S.ntr = a.ntr;
+  if (finest) {
+    S.nelem = nel;
+    S.nf = a.nf;
+    S.ntr = a.ntr;
+  }
   L.nloc = a.ntr;
   L.E = A.arr<double2>((size_t)nel * a.ntr * a.ntr);
-  S.Fc = A.arr<double2>((size_t)nel * a.ntr);
-  S.Yrec = A.arr<double2>((size_t)nel * a.nf * (a.ntr + 1));
+  double2* Fc = A.arr<double2>((size_t)nel * a.ntr);
+  double2* Yrec = A.arr<double2>((size_t)nel * a.nf * (a.ntr + 1));
+  if (finest) {
+    S.Fc = Fc;
+    S.Yrec = Yrec;
+  }
   a.Eout = L.E;
-  a.Fc = S.Fc;
-  a.Yrec = S.Yrec;
+  a.Fc = Fc;
+  a.Yrec = Yrec;
 
   // scratch per element: G (nt^2 doubles), W (nt (m+1)), K ((m+1)^2)
   const size_t per = (size_t)a.nt * a.nt * 8 + (size_t)a.nt * (a.m + 1) * 16 + (size_t)(a.m + 1) * (a.m + 1) * 16;
@@ -493,7 +512,7 @@ void element_stage(SystemImpl& S, cudaStream_t st) {
   };
   run_list(dreal, (int64_t)lreal.size(), true);
   run_list(dcplx, (int64_t)lcplx.size(), false);
-  {
+  if (finest) {
     // algorithmic multiply-adds (an FMA is 2 flops, a complex FMA 8): Gram
     // Cholesky nt^3/6, W = L^-1 [B l] nt^2 (m+1)/2, K = W^H W (lower)
     // (m+1)^2 nt/2, field condensation nf^3/6 + nf^2 (ntr+1) + ntr (ntr+1) nf
@@ -514,7 +533,12 @@ void element_stage(SystemImpl& S, cudaStream_t st) {
   a.W = nullptr;
   a.K = nullptr;
   a.elist = nullptr;
-  S.eargs = std::make_shared<ElemArgs>(a);
+  if (finest) {
+    S.eargs = std::make_shared<ElemArgs>(a);
+  } else {
+    A.release(Fc);
+    A.release(Yrec);
+  }
   if (info) throw Err{DPGMG_ERR_NOT_HPD, "element Gram or field block not positive definite"};
 }
 

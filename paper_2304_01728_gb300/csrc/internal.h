@@ -177,6 +177,9 @@ struct HandleImpl {
 // element.cu
 int64_t element_chunk(int64_t nel, size_t per_elem);
 void element_stage(SystemImpl& S, cudaStream_t st);
+// condensed element matrices of a coarser level assembled directly on its mesh
+// (the "stored" coarse operators of Sec. 3; constant wavespeed)
+void element_stage_level(SystemImpl& S, Level& L, cudaStream_t st);
 void recover_fields(SystemImpl& S, const double2* x, double2* fields, cudaStream_t st);
 // DPG error indicator eta_K^2 of every finest element for the trace vector x (device)
 void error_indicator(SystemImpl& S, const double2* x, double* eta2, cudaStream_t st);

@@ -488,6 +488,13 @@ void build_hierarchy(SystemImpl& S, cudaStream_t st) {
       smask.assign(M.smask.begin(), M.smask.end());
       H = 4;
     }
+    if (S.op.flags & DPGMG_FLAG_STORE_COARSE) {
+      // "stored" coarse operator (Sec. 3): the DPG system assembled directly on
+      // the coarser mesh (its own enriched test space) replaces the restriction
+      DPG_CUDA(cudaStreamSynchronize(st));
+      A.release(C.E);
+      element_stage_level(S, C, st);
+    }
     F.n_smooth = 0;
     for (char c : smask) F.n_smooth += c;
     setup_patches(S, F, smask, H, C.mesh.n, dinfo, st, mixed);

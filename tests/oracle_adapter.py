@@ -25,8 +25,16 @@ def oracle_system(pk, ok, hierarchy=True):
     A, b = fs.assemble()
     levels = None
     if hierarchy:
+        stored = None
+        if ok.get("flags", 0) & 4:   # coarse operators assembled on each coarser mesh
+            c = np.asarray(pk["wavespeed"]).ravel()[0] if pk.get("wavespeed") is not None else 1.0
+
+            def stored(cmesh):
+                cf = build_fine(cmesh.n, cmesh.p, pk["omega"], wavespeed=np.full(cmesh.n_elem, c),
+                                load=oracle_load(pk), x0=cmesh.x0, x1=cmesh.x1)
+                return cf.Kc
         levels = build_hierarchy(fs.mesh, fs.Kc, fs.dofs, ok.get("n_levels", 2), ok.get("p_min", 2),
-                                 coarsest=ok.get("coarsest", "cholesky"))
+                                 coarsest=ok.get("coarsest", "cholesky"), stored=stored)
     return fs, A, b, levels
 
 

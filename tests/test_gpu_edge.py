@@ -76,6 +76,7 @@ def test_iteration_cap_reports_not_converged():
     dict(opts=dict(n_levels=0)),
     dict(opts=dict(max_iter=0)),
     dict(opts=dict(flags=8)),
+    dict(problem=dict(wavespeed=np.r_[np.ones(63), 2.0]), opts=dict(flags=4)),   # stored needs constant c
 ])
 def test_invalid_inputs_are_refused(bad):
     pk = dict(dict(n=(4, 4, 4), p=2, omega=4.0), **bad.get("problem", {}))

@@ -338,6 +338,27 @@ def test_spmv_group_sizes_mixed(c1):
                 assert rel(y, c1.levels[l].M @ x) < 1e-6, (G, l)
 
 
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-11), ("mixed", 1e-11)])
+def test_stored_coarse_operators(precision, tol):
+    """Stored coarse operators (assembled on each coarser mesh, Sec. 3) against
+    the oracle: every coarse element matrix, then PCG iterations and solution."""
+    pk = dict(n=(4, 4, 4), p=2, omega=4.0, src_center=(0.45, 0.5, 0.55), src_width=0.15)
+    ok = dict(n_levels=3, p_min=1, precision=precision, tol=1e-8, flags=D.FLAG_STORE_COARSE)
+    fs, A, b, levels = oracle_system(pk, ok)
+    L = len(levels) - 1
+    with D.Solver(pk, **ok) as s:
+        for l in range(L):
+            E = levels[l].E
+            for e in range(0, E.shape[0], max(1, E.shape[0] // 7)):
+                M = D.dpgmg_element_matrix(s.h, s.s, l, e, E.shape[1])
+                assert rel(M, E[e]) < tol, (l, e, rel(M, E[e]))
+        x, f, st, code = s.solve()
+    x_ref, it_ref, _ = mg_pcg(levels, A, b, tol=ok["tol"])
+    assert code == D.DPGMG_OK
+    assert abs(st.iters - it_ref) <= max(1, 0.1 * it_ref), (st.iters, it_ref)
+    assert rel(x, x_ref) < 1e-7
+
+
 def test_error_statuses():
     w = workloads.config1()
     h = D.dpgmg_create(0)

@@ -199,3 +199,45 @@ def test_pcg_reaches_manufactured_solution(small_ph):
     x, it, hist = mg_pcg(lv, A, b, tol=1e-10)
     xt = trace_dofs(fs.mesh, ld.p, ld.u)
     assert np.linalg.norm(x - xt) / np.linalg.norm(xt) < 1e-8
+
+
+@pytest.fixture(scope="module")
+def stored_ph():
+    """4^3 p2 -> 4^3 p1 -> 2^3 p1 with stored coarse operators (assembled on each coarser mesh)."""
+    ld = GaussianSource((0.5, 0.5, 0.5), 0.1)
+    fs = build_fine((4, 4, 4), 2, 4.0, load=ld)
+    A, b = fs.assemble()
+
+    def stored(cmesh):
+        return build_fine(cmesh.n, cmesh.p, 4.0, load=ld, x0=cmesh.x0, x1=cmesh.x1).Kc
+    levels = build_hierarchy(fs.mesh, fs.Kc, fs.dofs, n_levels=3, p_min=1, stored=stored)
+    return fs, A, b, levels
+
+
+def test_stored_coarse_operators_are_the_coarse_dpg_systems(stored_ph, small_ph):
+    # each coarser level's operator is the DPG system of its own mesh and order,
+    # which differs from the restriction of the finer operator
+    fs, A, b, levels = stored_ph
+    _, _, _, restricted = small_ph
+    for l in range(len(levels) - 1):
+        m = levels[l].mesh
+        direct = build_fine(m.n, m.p, 4.0, load=GaussianSource((0.5, 0.5, 0.5), 0.1)).assemble()[0]
+        Al = assemble(levels[l].E, levels[l].dofs, m.n_dof)
+        assert abs(Al - direct).max() <= 1e-13 * abs(direct).max()
+        Ar = assemble(restricted[l].E, restricted[l].dofs, m.n_dof)
+        assert abs(Al - Ar).max() > 1e-3 * abs(Ar).max()
+
+
+def test_stored_vcycle_hermitian_positive_and_same_solution(stored_ph, small_ph):
+    fs, A, b, levels = stored_ph
+    L = len(levels) - 1
+    rng = np.random.default_rng(11)
+    u = rng.standard_normal(A.shape[0]) + 1j * rng.standard_normal(A.shape[0])
+    v = rng.standard_normal(A.shape[0]) + 1j * rng.standard_normal(A.shape[0])
+    Bu, Bv = vcycle(levels, L, u), vcycle(levels, L, v)
+    assert abs(np.vdot(v, Bu) - np.vdot(Bv, u)) / (np.linalg.norm(u) * np.linalg.norm(Bv)) < 1e-12
+    assert np.vdot(u, Bu).real > 0
+    # the preconditioner changes the iteration, not the discrete solution
+    x_s, it_s, _ = mg_pcg(levels, A, b, tol=1e-12)
+    x_r, it_r, _ = mg_pcg(small_ph[3], A, b, tol=1e-12)
+    assert np.linalg.norm(x_s - x_r) <= 1e-9 * np.linalg.norm(x_r)
