@@ -127,6 +127,13 @@ typedef struct dpgmg_opts {
    rather than I^T M I of the finer operator.  Needs a constant wavespeed
    (DPGMG_ERR_ARG otherwise); transfers and smoothers are unchanged. */
 #define DPGMG_FLAG_STORE_COARSE 4
+/* Warm start: dpgmg_solve takes its initial CG iterate from the trace_out
+   buffer (host or device per out_is_device) instead of 0, e.g. the solution of
+   a nearby load or frequency (Sec. 5 starts each adaptive mesh from the
+   previous solution); the stopping test stays ||r|| <= tol ||b||, and an
+   initial guess that already meets it returns after 0 iterations.  The
+   serving path always starts from 0. */
+#define DPGMG_FLAG_WARM_START 8
 
 typedef struct dpgmg_stats {
   int iters;               /* CG iterations (= V-cycle applications) */

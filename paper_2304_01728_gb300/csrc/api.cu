@@ -82,7 +82,7 @@ int validate_problem(const dpgmg_problem* pb, const dpgmg_opts* op) {
       op->p_min < 1 || (op->precision != DPGMG_PREC_FP64 && op->precision != DPGMG_PREC_MIXED) ||
       (op->coarsest != DPGMG_COARSEST_CHOLESKY && op->coarsest != DPGMG_COARSEST_NONE &&
        op->coarsest != DPGMG_COARSEST_AUTO) ||
-      (op->flags & ~(DPGMG_FLAG_EAGER | DPGMG_FLAG_TENSOR_CORES | DPGMG_FLAG_STORE_COARSE)))
+      (op->flags & ~(DPGMG_FLAG_EAGER | DPGMG_FLAG_TENSOR_CORES | DPGMG_FLAG_STORE_COARSE | DPGMG_FLAG_WARM_START)))
     return DPGMG_ERR_ARG;
   if ((op->flags & DPGMG_FLAG_STORE_COARSE) && pb->wavespeed) {
     const int64_t ne = (int64_t)pb->n[0] * pb->n[1] * pb->n[2];
@@ -374,7 +374,15 @@ int dpgmg_solve(dpgmg_handle h, dpgmg_system sys, void* trace_out, void* field_o
     tmp.budget = (size_t)-1;
     tmp.stream = s;
     double2* x = (trace_out && out_is_device) ? reinterpret_cast<double2*>(trace_out) : tmp.arr<double2>((size_t)n);
-    int status = pcg_solve(S, s, x, st);
+    const double2* x0 = nullptr;
+    if (S.op.flags & DPGMG_FLAG_WARM_START) {
+      if (!trace_out) throw Err{DPGMG_ERR_ARG, "a warm start reads its initial guess from trace_out"};
+      double2* g = tmp.arr<double2>((size_t)n);
+      DPG_CUDA(cudaMemcpyAsync(g, trace_out, (size_t)n * sizeof(double2),
+                               out_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
+      x0 = g;
+    }
+    int status = pcg_solve(S, s, x, st, x0);
     if (field_out) {
       double2* f = out_is_device ? reinterpret_cast<double2*>(field_out) : tmp.arr<double2>((size_t)nfld);
       recover_fields(S, x, f, s);

@@ -194,7 +194,8 @@ void coarse_setup(SystemImpl& S, Level& C0, int* info, cudaStream_t st);
 void coarse_apply64(const Level& C0, const double2* r, double2* e, double2* tmp, cudaStream_t st);
 void coarse_apply32(const Level& C0, const float2* r, float2* e, float2* tmp, cudaStream_t st);
 // solve.cu
-int pcg_solve(SystemImpl& S, cudaStream_t st, double2* x, dpgmg_stats* stats);
+// x0 (device, may be null): initial guess of the CG iteration (0 if null)
+int pcg_solve(SystemImpl& S, cudaStream_t st, double2* x, dpgmg_stats* stats, const double2* x0 = nullptr);
 void apply_op(SystemImpl& S, int op, int level, const double2* x, double2* y, cudaStream_t st);
 void ensure_workspace(SystemImpl& S, cudaStream_t st);
 // CG operator split and kernel-variant tuning, run once at the end of setup

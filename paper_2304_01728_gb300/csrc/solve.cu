@@ -1136,7 +1136,7 @@ void prepare_solve(SystemImpl& S, cudaStream_t st) {
   }
 }
 
-int pcg_solve(SystemImpl& S, cudaStream_t st, double2* xout, dpgmg_stats* stats) {
+int pcg_solve(SystemImpl& S, cudaStream_t st, double2* xout, dpgmg_stats* stats, const double2* x0) {
   ensure_workspace(S, st);
   WS& W = *reinterpret_cast<WS*>(S.ws);
   const ECSRDev& A = cg_operator(S, W, st);
@@ -1152,17 +1152,27 @@ int pcg_solve(SystemImpl& S, cudaStream_t st, double2* xout, dpgmg_stats* stats)
   DPG_CUDA(cudaEventCreate(&e0));
   DPG_CUDA(cudaEventCreate(&e1));
   DPG_CUDA(cudaEventRecord(e0, st));
-  k_zero<double2><<<nblk(n), 256, 0, st>>>(W.x, n);
-  DPG_CHECK_LAUNCH();
   DPG_CUDA(cudaMemcpyAsync(W.r, S.b, (size_t)n * sizeof(double2), cudaMemcpyDeviceToDevice, st));
   dot(W, W.r, W.r, n, 1, st);   // ||b||^2
   DPG_CUDA(cudaMemcpyAsync(W.sc_host, W.sc, SC_COUNT * sizeof(double2), cudaMemcpyDeviceToHost, st));
   DPG_CUDA(cudaStreamSynchronize(st));
   const double nb = std::sqrt(W.sc_host[SC_RR].x);
+  double rel = 1.0;
+  if (x0) {
+    // warm start: x = x0, r = b - A x0
+    DPG_CUDA(cudaMemcpyAsync(W.x, x0, (size_t)n * sizeof(double2), cudaMemcpyDeviceToDevice, st));
+    spmv_df(A, W.x, S.b, W.r, 1, W.xh, W.xl, st);
+    dot(W, W.r, W.r, n, 1, st);
+    DPG_CUDA(cudaMemcpyAsync(W.sc_host, W.sc, SC_COUNT * sizeof(double2), cudaMemcpyDeviceToHost, st));
+    DPG_CUDA(cudaStreamSynchronize(st));
+    rel = nb > 0.0 ? std::sqrt(W.sc_host[SC_RR].x) / nb : 0.0;
+  } else {
+    k_zero<double2><<<nblk(n), 256, 0, st>>>(W.x, n);
+    DPG_CHECK_LAUNCH();
+  }
   int status = DPGMG_OK;
   int it = 0;
-  double rel = 1.0;
-  if (nb > 0.0) {
+  if (nb > 0.0 && !(x0 && rel <= S.op.tol)) {
     SystemImpl* pcg_prof = S.prof_which == DPGMG_PROF_SPMV_CG ? &S : nullptr;
     // q = A p, alpha = rho / p^H q, x += alpha p, r -= alpha q, ||r||^2, scalars to the host
     auto tail = [&]() {

@@ -93,3 +93,28 @@ def test_invalid_inputs_are_refused(bad):
         assert e.value.code == D.DPGMG_ERR_ARG
     finally:
         D.dpgmg_destroy(h)
+
+
+def test_warm_start():
+    pk = dict(n=(4, 4, 4), p=2, omega=6.0, src_center=(0.4, 0.5, 0.6))
+    ok = dict(n_levels=2, p_min=1, precision="fp64", tol=1e-8)
+    x, f, st, code = _solve(pk, ok)
+    assert code == D.DPGMG_OK
+    cold = st.iters
+    with D.Solver(pk, **dict(ok, flags=D.FLAG_WARM_START)) as s:
+        # from the converged solution: no iteration, the guess is returned
+        g = x.copy()
+        code, st = D.dpgmg_solve(s.h, s.s, g, None)
+        assert code == D.DPGMG_OK and st.iters == 0 and st.relres <= ok["tol"]
+        assert np.array_equal(g, x)
+        # from a perturbed solution: converges in fewer iterations to the same solution
+        rng = np.random.default_rng(2)
+        g = x + 1e-4 * np.abs(x).max() * (rng.standard_normal(x.shape) + 1j * rng.standard_normal(x.shape))
+        code, st = D.dpgmg_solve(s.h, s.s, g, None)
+        assert code == D.DPGMG_OK and 0 < st.iters < cold, (st.iters, cold)
+        assert rel(g, x) < 1e-6
+        # from zero: the cold iteration
+        g = np.zeros_like(x)
+        code, st = D.dpgmg_solve(s.h, s.s, g, None)
+        assert code == D.DPGMG_OK and st.iters == cold
+        assert rel(g, x) < 1e-12
