@@ -75,7 +75,7 @@ def test_iteration_cap_reports_not_converged():
     dict(opts=dict(tol=0.0)),
     dict(opts=dict(n_levels=0)),
     dict(opts=dict(max_iter=0)),
-    dict(opts=dict(flags=8)),
+    dict(opts=dict(flags=16)),
     dict(problem=dict(wavespeed=np.r_[np.ones(63), 2.0]), opts=dict(flags=4)),   # stored needs constant c
 ])
 def test_invalid_inputs_are_refused(bad):
