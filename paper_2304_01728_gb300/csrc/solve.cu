@@ -209,22 +209,10 @@ template <class C> struct SpmvSlot;
 template <> struct SpmvSlot<float2> { static constexpr int v = 0; };
 template <> struct SpmvSlot<double2> { static constexpr int v = 1; };
 
-// Blocks of 256 threads that fit on the device at once for `kernel` (one full
-// wave; the SpMV kernels stride over their rows from there, so every warp
-// starts at once and they finish together).
-template <class K> static int64_t one_wave(K kernel) {
-  int dev = 0, sms = 0, per = 0;
-  DPG_CUDA(cudaGetDevice(&dev));
-  DPG_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-  DPG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kernel, 256, 0));
-  return (int64_t)std::max(1, sms) * std::max(1, per);
-}
-
 template <class C>
 static void spmv_g(const ECSRDev& A, const C* vals, const C* x, const C* b, C* y, int mode, int G, cudaStream_t st) {
   if (G <= 1 || !A.tasks[1]) {
-    static const int64_t wave = one_wave(k_spmv<C>);
-    int64_t blocks = std::min<int64_t>((A.nrows + 7) / 8, wave);
+    int64_t blocks = std::min<int64_t>((A.nrows + 7) / 8, 152 * 16);
     k_spmv<C><<<(unsigned)blocks, 256, 0, st>>>(A.row_ent, A.ent_start, A.col_ptr, A.col_idx, A.val_ptr, vals, x, b,
                                                  y, A.nrows, mode);
     DPG_CHECK_LAUNCH();
