@@ -41,6 +41,11 @@ void* Alloc::get(size_t bytes) {
   return p;
 }
 
+SystemImpl::~SystemImpl() {
+  mem_aux.free_all();
+  if (aux) cudaStreamDestroy(aux);
+}
+
 void Alloc::release(void* p) {
   for (size_t i = 0; i < ptrs.size(); ++i)
     if (ptrs[i] == p) {
@@ -104,7 +109,7 @@ size_t estimate_bytes(const dpgmg_problem* pb, const dpgmg_opts* op) {
   const bool mixed = op->precision == DPGMG_PREC_MIXED;
   const double vsz = mixed ? 8.0 : 16.0;       // V-cycle complex size
   const double x32 = mixed ? 8.0 : 0.0;        // extra complex64 copies on the mixed path
-  double resident = 0.0, transient = 0.0;
+  double resident = 0.0, transient = 0.0, coarse_transient = 0.0;
   const int p = pb->p;
   const double ne = (double)nn[0] * nn[1] * nn[2];
   const double ntr = n_trace_local(p), nf = 4.0 * p * p * p;
@@ -154,11 +159,12 @@ size_t estimate_bytes(const dpgmg_problem* pb, const dpgmg_opts* op) {
     } else if (op->coarsest == DPGMG_COARSEST_CHOLESKY || specs.size() == 1 ||
                (op->coarsest == DPGMG_COARSEST_AUTO && nd <= kAutoCoarsestMax)) {
       resident += nd * (nd + 1.0) * vsz;                              // packed L^-1 and L^-H
-      transient = std::max(transient, nd * nd * (mixed ? 24.0 : 32.0) + nd * 64.0 * 16.0);
+      // built concurrently with the level above: its scratch adds to theirs
+      coarse_transient = nd * nd * (mixed ? 24.0 : 32.0) + nd * 64.0 * 16.0;
     }
   }
   resident += (xdofs + ne * nf) * 16.0;                              // solution outputs
-  return (size_t)((resident + transient) * 1.05) + ((size_t)64 << 20);
+  return (size_t)((resident + transient + coarse_transient) * 1.05) + ((size_t)64 << 20);
 }
 
 static void fill_bytes_per_iter(SystemImpl& S) {
@@ -343,7 +349,7 @@ int dpgmg_setup(dpgmg_handle h, const dpgmg_problem* pb, const dpgmg_opts* op, d
   try {
     DPG_CUDA(cudaSetDevice(h->h.device));
     setup_system(S, pb, op, h->h.budget - h->h.used, h->h.stream);
-    h->h.used += S.mem.used;
+    h->h.used += S.mem_used();
     *out = sys;
     return DPGMG_OK;
   } catch (const Err& e) {
@@ -405,7 +411,7 @@ void dpgmg_release(dpgmg_handle h, dpgmg_system sys) {
     std::lock_guard<std::mutex> lk(h->mu);
     cudaSetDevice(h->h.device);
     cudaStreamSynchronize(h->h.stream);
-    h->h.used -= std::min(h->h.used, sys->s.mem.used);
+    h->h.used -= std::min(h->h.used, sys->s.mem_used());
   }
   profile_clear(sys->s);
   free_workspace(sys->s);

@@ -303,8 +303,7 @@ static void coarse_factor(Alloc& A, C* dense, int64_t N, C** Lp, C** Up, int* in
   A.release(Dinv);
 }
 
-void coarse_setup(SystemImpl& S, Level& C0, int* info, cudaStream_t st) {
-  Alloc& A = S.mem;
+void coarse_setup(SystemImpl& S, Level& C0, int* info, cudaStream_t st, Alloc& A) {
   const int64_t N = C0.mesh.ndof;
   C0.N0 = N;
   double2* dense = A.arr<double2>((size_t)N * N);

@@ -163,6 +163,16 @@ struct SystemImpl {
   int64_t prof_bytes = 0;
   int coarse_blocks = 0;
   std::shared_ptr<ElemArgs> eargs;   // device tables of the element stage (resident with the system)
+  // The coarsest factorisation is built on a side stream, concurrently with the
+  // patch work of the level above it; its memory is tracked separately.
+  cudaStream_t aux = nullptr;
+  Alloc mem_aux;
+  size_t mem_used() const { return mem.used + mem_aux.used; }
+  size_t mem_peak() const { return mem.peak + mem_aux.peak; }
+  SystemImpl() = default;
+  SystemImpl(const SystemImpl&) = delete;
+  SystemImpl& operator=(const SystemImpl&) = delete;
+  ~SystemImpl();
 };
 
 struct HandleImpl {
@@ -190,7 +200,7 @@ void ecsr_add_elements(ECSRDev& D, const double2* E, const int64_t* dofs, int64_
 void build_hierarchy(SystemImpl& S, cudaStream_t st);
 void assemble_rhs(SystemImpl& S, cudaStream_t st);
 // coarse.cu
-void coarse_setup(SystemImpl& S, Level& C0, int* info, cudaStream_t st);
+void coarse_setup(SystemImpl& S, Level& C0, int* info, cudaStream_t st, Alloc& A);
 void coarse_apply64(const Level& C0, const double2* r, double2* e, double2* tmp, cudaStream_t st);
 void coarse_apply32(const Level& C0, const float2* r, float2* e, float2* tmp, cudaStream_t st);
 // solve.cu

@@ -10,6 +10,8 @@
 //     ("V-cycle and smoother"),
 //   * the coarsest level (coarse.cu).
 #include <algorithm>
+#include <exception>
+#include <thread>
 #include <cmath>
 #include <cstring>
 
@@ -408,12 +410,51 @@ static void setup_patches(SystemImpl& S, Level& F, const std::vector<char>& smas
   (void)mixed;
 }
 
+// joins the side thread on every exit path (an exception included)
+struct JoinOnExit {
+  std::thread t;
+  ~JoinOnExit() {
+    if (t.joinable()) t.join();
+  }
+};
+
 void build_hierarchy(SystemImpl& S, cudaStream_t st) {
   Alloc& A = S.mem;
   const int L = (int)S.levels.size() - 1;
   const bool mixed = S.op.precision == DPGMG_PREC_MIXED;
   int* dinfo = A.arr<int>(1);
   DPG_CUDA(cudaMemsetAsync(dinfo, 0, sizeof(int), st));
+  const bool dense = S.op.coarsest == DPGMG_COARSEST_CHOLESKY || L == 0 ||
+                     (S.op.coarsest == DPGMG_COARSEST_AUTO && S.levels[0].mesh.ndof <= 20000);
+  // The coarsest factorisation (FP32/FP64 dense work) runs on a side stream from
+  // a second host thread as soon as level 0's element matrices exist, overlapping
+  // the patch inversion and damping estimate of level 1 (FP64, other SM pipes).
+  JoinOnExit side;
+  std::exception_ptr side_err;
+  int* cinfo = nullptr;
+  auto start_coarse = [&]() {
+    int dev = 0;
+    DPG_CUDA(cudaGetDevice(&dev));
+    DPG_CUDA(cudaStreamCreateWithFlags(&S.aux, cudaStreamNonBlocking));
+    S.mem_aux.stream = S.aux;
+    S.mem_aux.budget = S.mem.budget > S.mem.used ? S.mem.budget - S.mem.used : 0;
+    cudaEvent_t ready;
+    DPG_CUDA(cudaEventCreateWithFlags(&ready, cudaEventDisableTiming));
+    DPG_CUDA(cudaEventRecord(ready, st));
+    side.t = std::thread([&S, &side_err, &cinfo, dev, ready]() {
+      try {
+        DPG_CUDA(cudaSetDevice(dev));
+        DPG_CUDA(cudaStreamWaitEvent(S.aux, ready, 0));
+        cinfo = S.mem_aux.arr<int>(1);
+        DPG_CUDA(cudaMemsetAsync(cinfo, 0, sizeof(int), S.aux));
+        coarse_setup(S, S.levels[0], cinfo, S.aux, S.mem_aux);
+        DPG_CUDA(cudaStreamSynchronize(S.aux));
+      } catch (...) {
+        side_err = std::current_exception();
+      }
+      cudaEventDestroy(ready);
+    });
+  };
   S.levels[L].dofs = upload_dofs(A, S.levels[L].mesh, st);
   for (int l = L; l >= 1; --l) {
     Level& F = S.levels[l];
@@ -495,6 +536,7 @@ void build_hierarchy(SystemImpl& S, cudaStream_t st) {
       A.release(C.E);
       element_stage_level(S, C, st);
     }
+    if (l == 1 && dense) start_coarse();
     F.n_smooth = 0;
     for (char c : smask) F.n_smooth += c;
     setup_patches(S, F, smask, H, C.mesh.n, dinfo, st, mixed);
@@ -532,12 +574,18 @@ void build_hierarchy(SystemImpl& S, cudaStream_t st) {
   // coarsest
   Level& C0 = S.levels[0];
   if (L == 0) C0.dofs = S.levels[0].dofs;
-  const bool dense = S.op.coarsest == DPGMG_COARSEST_CHOLESKY || L == 0 ||
-                     (S.op.coarsest == DPGMG_COARSEST_AUTO && C0.mesh.ndof <= 20000);
-  if (dense) coarse_setup(S, C0, dinfo, st);
   int info = 0;
-  DPG_CUDA(cudaMemcpyAsync(&info, dinfo, sizeof(int), cudaMemcpyDeviceToHost, st));
+  if (side.t.joinable()) {
+    side.t.join();
+    if (side_err) std::rethrow_exception(side_err);
+    DPG_CUDA(cudaMemcpy(&info, cinfo, sizeof(int), cudaMemcpyDeviceToHost));
+  } else if (dense) {
+    coarse_setup(S, C0, dinfo, st, A);
+  }
+  int info_main = 0;
+  DPG_CUDA(cudaMemcpyAsync(&info_main, dinfo, sizeof(int), cudaMemcpyDeviceToHost, st));
   DPG_CUDA(cudaStreamSynchronize(st));
+  info |= info_main;
   if (info & 32) throw Err{DPGMG_ERR_TIMEOUT, "tensor-core update: a bounded wait for the MMAs ran out"};
   if (info) throw Err{DPGMG_ERR_NOT_HPD, "a macro, patch or coarsest factorisation lost positive definiteness"};
 }

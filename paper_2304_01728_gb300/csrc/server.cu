@@ -80,7 +80,9 @@ static void run_request(Request& rq, cudaStream_t st, size_t budget) {
   profile_clear(S);
   free_workspace(S);
   S.mem.free_all();
+  S.mem_aux.free_all();
   cudaStreamSynchronize(st);
+  if (S.aux) cudaStreamSynchronize(S.aux);
 }
 
 static void worker_loop(Server* sv) {

@@ -1241,7 +1241,7 @@ int pcg_solve(SystemImpl& S, cudaStream_t st, double2* xout, dpgmg_stats* stats,
     stats->t_setup_ms = S.t_setup_ms;
     stats->bytes_per_iter = S.bytes_per_iter;
     stats->n_dof = n;
-    stats->dev_bytes_peak = (long long)S.mem.peak;
+    stats->dev_bytes_peak = (long long)S.mem_peak();
   }
   return status;
 }
