@@ -578,7 +578,8 @@ void build_hierarchy(SystemImpl& S, cudaStream_t st) {
   if (side.t.joinable()) {
     side.t.join();
     if (side_err) std::rethrow_exception(side_err);
-    DPG_CUDA(cudaMemcpy(&info, cinfo, sizeof(int), cudaMemcpyDeviceToHost));
+    DPG_CUDA(cudaMemcpyAsync(&info, cinfo, sizeof(int), cudaMemcpyDeviceToHost, S.aux));
+    DPG_CUDA(cudaStreamSynchronize(S.aux));
   } else if (dense) {
     coarse_setup(S, C0, dinfo, st, A);
   }
