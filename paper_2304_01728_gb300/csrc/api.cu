@@ -41,10 +41,7 @@ void* Alloc::get(size_t bytes) {
   return p;
 }
 
-SystemImpl::~SystemImpl() {
-  mem_aux.free_all();
-  if (aux) cudaStreamDestroy(aux);
-}
+SystemImpl::~SystemImpl() { mem_aux.free_all(); }
 
 void Alloc::release(void* p) {
   for (size_t i = 0; i < ptrs.size(); ++i)

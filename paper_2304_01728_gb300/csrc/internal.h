@@ -165,7 +165,7 @@ struct SystemImpl {
   std::shared_ptr<ElemArgs> eargs;   // device tables of the element stage (resident with the system)
   // The coarsest factorisation is built on a side stream, concurrently with the
   // patch work of the level above it; its memory is tracked separately.
-  cudaStream_t aux = nullptr;
+  cudaStream_t aux = nullptr;    // shared per setup stream, not owned
   Alloc mem_aux;
   size_t mem_used() const { return mem.used + mem_aux.used; }
   size_t mem_peak() const { return mem.peak + mem_aux.peak; }

@@ -10,6 +10,8 @@
 //     ("V-cycle and smoother"),
 //   * the coarsest level (coarse.cu).
 #include <algorithm>
+#include <mutex>
+#include <map>
 #include <exception>
 #include <thread>
 #include <cmath>
@@ -410,6 +412,27 @@ static void setup_patches(SystemImpl& S, Level& F, const std::vector<char>& smas
   (void)mixed;
 }
 
+// The side stream paired with a setup stream (one per device and stream, kept
+// for the life of the process): memory freed on it is reused by the next
+// system set up on the same stream, which a fresh stream per system would not
+// allow.
+static cudaStream_t side_stream_for(cudaStream_t st) {
+  static std::mutex mu;
+  static std::map<std::pair<int, cudaStream_t>, cudaStream_t> streams;
+  int dev = 0;
+  DPG_CUDA(cudaGetDevice(&dev));
+  std::lock_guard<std::mutex> lk(mu);
+  cudaStream_t& s = streams[{dev, st}];
+  if (!s) {
+    // highest priority: the factorisation is a chain of small dependent
+    // launches, the patch work it overlaps is many independent CTAs
+    int least = 0, greatest = 0;
+    DPG_CUDA(cudaDeviceGetStreamPriorityRange(&least, &greatest));
+    DPG_CUDA(cudaStreamCreateWithPriority(&s, cudaStreamNonBlocking, greatest));
+  }
+  return s;
+}
+
 // joins the side thread on every exit path (an exception included)
 struct JoinOnExit {
   std::thread t;
@@ -435,7 +458,7 @@ void build_hierarchy(SystemImpl& S, cudaStream_t st) {
   auto start_coarse = [&]() {
     int dev = 0;
     DPG_CUDA(cudaGetDevice(&dev));
-    DPG_CUDA(cudaStreamCreateWithFlags(&S.aux, cudaStreamNonBlocking));
+    S.aux = side_stream_for(st);
     S.mem_aux.stream = S.aux;
     S.mem_aux.budget = S.mem.budget > S.mem.used ? S.mem.budget - S.mem.used : 0;
     cudaEvent_t ready;
