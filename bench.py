@@ -53,8 +53,9 @@ def parse():
     ap.add_argument("--n", type=int, default=0, help="override the mesh size n^3 (profiling of a smaller case)")
     ap.add_argument("--tensor-cores", action="store_true",
                     help="coarsest complex64 factor updates on the tensor cores (DPGMG_FLAG_TENSOR_CORES)")
-    ap.add_argument("--mode", default="step", choices=["step", "batch", "serve"],
-                    help="step: the bench line; batch: independent uneven problems; serve: Poisson request stream")
+    ap.add_argument("--mode", default="step", choices=["step", "batch", "serve", "sweep"],
+                    help="step: the bench line; batch: independent uneven problems; serve: Poisson request stream; "
+                         "sweep: iteration counts of the convergence studies (h, p, omega, smoothing steps)")
     ap.add_argument("--count", type=int, default=16, help="batch/serve: problems drawn from the seeded stream")
     ap.add_argument("--max-dofs", type=float, default=2.5e5, help="batch/serve: sample only problems up to this size")
     ap.add_argument("--slots", type=int, default=4, help="batch/serve: concurrent serving slots")
@@ -491,6 +492,41 @@ def run_stream(args):
     print(json.dumps(out))
 
 
+# ------------------------------------------------------------------ sweep
+def run_sweep(args):
+    """Iteration counts of the convergence studies (Sec. 4: h-robustness at
+    fixed omega, growth with omega, p-robustness, smoothing steps), with
+    restricted and stored coarse operators, on the unit cube with a Gaussian
+    source (x0 = (0.45, 0.5, 0.55), sigma = 0.1), mixed V-cycle, tol 1e-8.
+    Prints one JSON line with a row per solve (iterations, PCG and setup ms)."""
+    from paper_2304_01728_gb300 import build as B
+    B.build()
+    from paper_2304_01728_gb300 import dpgmg as D
+    pi = math.pi
+    studies = []
+    for n in (4, 8, 16):                               # h at fixed omega (2 elements per wavelength at n = 16)
+        studies.append(("h", n, 3, 8 * pi, 1))
+    for om in (4 * pi, 8 * pi, 12 * pi, 16 * pi):      # omega at fixed mesh
+        studies.append(("omega", 16, 3, om, 1))
+    for p in (2, 3, 4):                                # p at fixed mesh and omega
+        studies.append(("p", 8, p, 8 * pi, 1))
+    for nu in (1, 2, 3):                               # V(nu, nu)
+        studies.append(("nu", 16, 3, 8 * pi, nu))
+    rows = []
+    for study, n, p, om, nu in studies:
+        row = {"study": study, "n": n, "p": p, "omega": round(om, 4), "nu": nu}
+        for name, flags in (("restricted", 0), ("stored", D.FLAG_STORE_COARSE)):
+            pk = dict(n=(n, n, n), p=p, omega=om, src_center=(0.45, 0.5, 0.55), src_width=0.1)
+            opts = dict(n_levels=3, p_min=2 if p > 2 else 1, precision="mixed", tol=1e-8, flags=flags,
+                        nu_pre=nu, nu_post=nu, max_iter=3000)
+            with D.Solver(pk, **opts) as s:
+                x, f, st, code = s.solve(fields=False)
+            row[name] = {"iters": st.iters, "pcg_ms": round(st.t_pcg_ms, 2), "setup_ms": round(st.t_setup_ms, 1),
+                         "status": D.strerror(code)}
+        rows.append(row)
+    print(json.dumps({"mode": "sweep", "levels": 3, "precision": "mixed", "tol": 1e-8, "rows": rows}))
+
+
 # ------------------------------------------------------------------ main
 def main():
     args = parse()
@@ -516,6 +552,10 @@ def main():
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": r["sample"]},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
             "wall_s": time.perf_counter() - t0}))
+        return
+    if args.mode == "sweep":
+        if rank == 0:
+            run_sweep(args)
         return
     if args.mode != "step":
         if rank == 0:
