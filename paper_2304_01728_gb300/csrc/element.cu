@@ -42,6 +42,8 @@ struct ElemArgs {
   const int64_t* elist;    // element ids of the batch list
   int64_t e0;
   double* G;
+  int nph;                 // number of p-hat trace columns (split path)
+  const int* phq;          // per trace column: its index among the p-hat columns, or -1
   void* W;                 // [chunk][nt][m+1] of the path's scalar type
   void* K;                 // [chunk][m+1][m+1]
   double2* Eout;
@@ -157,7 +159,11 @@ template <class T> __device__ __forceinline__ T to_path(double2 v, bool rot);
 template <> __device__ __forceinline__ double2 to_path<double2>(double2 v, bool) { return v; }
 template <> __device__ __forceinline__ double to_path<double>(double2 v, bool rot) { return rot ? -v.y : v.x; }
 
-template <class T>
+// Split path (boundary elements, real source): with the trial phases of the
+// real path, B' = B_r + i B_i where B_i is non-zero only in the p-hat columns
+// (the impedance term <p-hat, Z^-1 q> on boundary faces).  The builder writes
+// one real matrix [B_r | l' | B_i(p-hat columns)] of row length m + 1 + nph.
+template <class T, bool SPLIT = false>
 __global__ void __launch_bounds__(CTA_THREADS) k_elem_build(ElemArgs a) {
   extern __shared__ double2 sh2[];
   const int64_t le = blockIdx.x;
@@ -167,9 +173,11 @@ __global__ void __launch_bounds__(CTA_THREADS) k_elem_build(ElemArgs a) {
   elem_geom(a, e, ec, corner, bmask);
   const double c = a.c[e];
   const double beta = a.omega / (c * c);
-  const int nt = a.nt, m = a.m, ldw = m + 1;
+  const int nt = a.nt, m = a.m, ldw = SPLIT ? m + 1 + a.nph : m + 1;
   double* G = a.G + le * (size_t)nt * nt;
-  T* W = reinterpret_cast<T*>(a.W) + le * (size_t)nt * ldw;
+  // per-element slot of nt (m+1) complex values (the split path's real rows fit in it)
+  T* W = SPLIT ? reinterpret_cast<T*>(reinterpret_cast<double2*>(a.W) + le * (size_t)nt * (m + 1))
+               : reinterpret_cast<T*>(a.W) + le * (size_t)nt * ldw;
   for (int64_t q = threadIdx.x; q < (int64_t)nt * nt; q += blockDim.x) {
     int i = (int)(q / nt), j = (int)(q % nt);
     G[q] = (j <= i) ? gram_entry(a.tab, a.tf[i], a.tf[j], a.h, beta, a.omega) : 0.0;
@@ -180,6 +188,11 @@ __global__ void __launch_bounds__(CTA_THREADS) k_elem_build(ElemArgs a) {
                            : btrace_entry(a.tab, a.tf[i], a.tr[j - a.nf], a.h, 1.0 / c, bmask);
     const bool rot = (j < a.nf) ? a.ff[j].x == 0 : a.tr[j - a.nf].x == 0;
     W[(size_t)i * ldw + j] = to_path<T>(v, rot);
+    if (SPLIT && j >= a.nf) {
+      const int q = a.phq[j - a.nf];
+      // imaginary part of the phased value i v (p-hat columns carry the phase i)
+      if (q >= 0) reinterpret_cast<double*>(W)[(size_t)i * ldw + m + 1 + q] = v.x;
+    }
   }
   // ---- load l' (v rows scaled by -i)
   const int nq = a.nql, nq3 = nq * nq * nq;
@@ -281,15 +294,65 @@ __global__ void __launch_bounds__(CTA_THREADS) k_elem_herk(ElemArgs a) {
   cta_herk_lower<T>(W, a.nt, ld, ld, K, ld, reinterpret_cast<T*>(shraw), false);
 }
 
+// ---- split path: real TRSM and HERK on [B_r | l' | B_i(p-hat)], then the
+// complex K' = W^H W from the real Gram matrix R of the extended columns:
+//   Re K'[a][b] = R[a][b] + R[a~][b~],   Im K'[a][b] = R[a][b~] - R[a~][b]
+// (a~ = the imaginary column of a, terms absent where a has none).
+__global__ void __launch_bounds__(CTA_THREADS) k_elem_trsm_split(ElemArgs a) {
+  extern __shared__ char shc[];
+  const int64_t le = blockIdx.x;
+  const int ld2 = a.m + 1 + a.nph;
+  const double* G = a.G + le * (size_t)a.nt * a.nt;
+  double* W = reinterpret_cast<double*>(reinterpret_cast<double2*>(a.W) + le * (size_t)a.nt * (a.m + 1));
+  cta_trsm_lower<double, double>(G, a.nt, a.nt, W, ld2, ld2, shc);
+}
+
+__global__ void __launch_bounds__(CTA_THREADS) k_elem_herk_split(ElemArgs a) {
+  extern __shared__ unsigned char shraw[];
+  const int64_t le = blockIdx.x;
+  const int ld = a.m + 1, ld2 = ld + a.nph;
+  const double* W = reinterpret_cast<const double*>(reinterpret_cast<const double2*>(a.W) + le * (size_t)a.nt * ld);
+  double* R = reinterpret_cast<double*>(reinterpret_cast<double2*>(a.K) + le * (size_t)ld * ld);
+  cta_herk_lower<double>(W, a.nt, ld2, ld2, R, ld2, reinterpret_cast<double*>(shraw), false);
+}
+
+// R (real, ld2 x ld2, in the K slot) -> complex K' (ld x ld) in the same slot,
+// staged through the element's W slot (no longer needed after the HERK)
+__global__ void __launch_bounds__(CTA_THREADS) k_elem_split_assemble(ElemArgs a) {
+  const int64_t le = blockIdx.x;
+  const int ld = a.m + 1, ld2 = ld + a.nph, nf = a.nf, m = a.m;
+  double2* Kc = reinterpret_cast<double2*>(a.K) + le * (size_t)ld * ld;
+  const double* R = reinterpret_cast<const double*>(Kc);
+  double2* T = reinterpret_cast<double2*>(a.W) + le * (size_t)a.nt * ld;
+  for (int q = threadIdx.x; q < ld * ld; q += blockDim.x) {
+    const int i = q / ld, j = q % ld;
+    const int qi = (i >= nf && i < m) ? a.phq[i - nf] : -1;
+    const int qj = (j >= nf && j < m) ? a.phq[j - nf] : -1;
+    double re = R[(size_t)i * ld2 + j], im = 0.0;
+    if (qi >= 0 && qj >= 0) re += R[(size_t)(ld + qi) * ld2 + ld + qj];
+    if (qj >= 0) im += R[(size_t)i * ld2 + ld + qj];
+    if (qi >= 0) im -= R[(size_t)(ld + qi) * ld2 + j];
+    T[q] = make_double2(re, im);
+  }
+  __syncthreads();
+  for (int q = threadIdx.x; q < ld * ld; q += blockDim.x) Kc[q] = T[q];
+}
+
 // complex output of the path's value; ph = 0: x1, 1: x i, 2: x (-i)
 template <class T> __device__ __forceinline__ double2 phased(T v, int ph);
 template <> __device__ __forceinline__ double2 phased<double2>(double2 v, int) { return v; }
 template <> __device__ __forceinline__ double2 phased<double>(double v, int ph) {
   return ph == 0 ? make_double2(v, 0.0) : (ph == 1 ? make_double2(0.0, v) : make_double2(0.0, -v));
 }
+// the split path's complex values carry the unit phases too
+__device__ __forceinline__ double2 phased_c(double2 v, int ph) {
+  return ph == 0 ? v : (ph == 1 ? make_double2(-v.y, v.x) : make_double2(v.y, -v.x));
+}
+template <class T, bool PH> __device__ __forceinline__ double2 out_value(T v, int ph) { return phased<T>(v, ph); }
+template <> __device__ __forceinline__ double2 out_value<double2, true>(double2 v, int ph) { return phased_c(v, ph); }
 __device__ __forceinline__ int phase_of(bool a_i, bool b_i) { return (a_i && !b_i) ? 1 : ((!a_i && b_i) ? 2 : 0); }
 
-template <class T>
+template <class T, bool PH = false>
 __global__ void __launch_bounds__(CTA_THREADS) k_elem_condense(ElemArgs a) {
   extern __shared__ unsigned char shraw[];
   T* sh = reinterpret_cast<T*>(shraw);
@@ -306,16 +369,16 @@ __global__ void __launch_bounds__(CTA_THREADS) k_elem_condense(ElemArgs a) {
   double2* E = a.Eout + e * (size_t)ntr * ntr;
   for (int q = threadIdx.x; q < ntr * ntr; q += blockDim.x) {
     int i = q / ntr, j = q % ntr;
-    E[q] = phased<T>(K[(size_t)(nf + i) * ld + nf + j], phase_of(a.tr[i].x == 0, a.tr[j].x == 0));
+    E[q] = out_value<T, PH>(K[(size_t)(nf + i) * ld + nf + j], phase_of(a.tr[i].x == 0, a.tr[j].x == 0));
   }
   for (int i = threadIdx.x; i < ntr; i += blockDim.x)
-    a.Fc[e * ntr + i] = phased<T>(K[(size_t)(nf + i) * ld + a.m], a.tr[i].x == 0 ? 1 : 0);
+    a.Fc[e * ntr + i] = out_value<T, PH>(K[(size_t)(nf + i) * ld + a.m], a.tr[i].x == 0 ? 1 : 0);
   double2* Y = a.Yrec + e * (size_t)nf * (ntr + 1);
   for (int q = threadIdx.x; q < nf * (ntr + 1); q += blockDim.x) {
     int i = q / (ntr + 1), j = q % (ntr + 1);
     const bool fi = a.ff[i].x == 0;
     const int ph = (j < ntr) ? phase_of(fi, a.tr[j].x == 0) : (fi ? 1 : 0);
-    Y[q] = phased<T>(K[(size_t)i * ld + nf + j], ph);
+    Y[q] = out_value<T, PH>(K[(size_t)i * ld + nf + j], ph);
   }
 }
 
@@ -423,6 +486,15 @@ static void element_core(SystemImpl& S, Level& L, const std::vector<double>& cva
   a.tf = upload(A, tf, st);
   a.ff = upload(A, ff, st);
   a.tr = upload(A, tr, st);
+  {
+    // index of every p-hat trace column among the p-hat columns (split path)
+    std::vector<int> phq(tr.size(), -1);
+    int q = 0;
+    for (size_t j = 0; j < tr.size(); ++j)
+      if (tr[j].x == 0) phq[j] = q++;
+    a.nph = q;
+    a.phq = upload(A, phq, st);
+  }
   a.tab.p = p;
   a.tab.pt = p + 1;
   a.tab.n1 = p + 2;
@@ -476,19 +548,52 @@ static void element_core(SystemImpl& S, Level& L, const std::vector<double>& cva
   DPG_CUDA(cudaFuncSetAttribute(k_elem_herk<double2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_cplx));
   DPG_CUDA(cudaFuncSetAttribute(k_elem_condense<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_cplx));
   DPG_CUDA(cudaFuncSetAttribute(k_elem_condense<double2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_cplx));
+  DPG_CUDA(cudaFuncSetAttribute(k_elem_build<double, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)sm_build_max));
+  DPG_CUDA(cudaFuncSetAttribute(k_elem_trsm_split, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_cplx));
+  DPG_CUDA(cudaFuncSetAttribute(k_elem_herk_split, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_cplx));
+  DPG_CUDA(cudaFuncSetAttribute(k_elem_condense<double2, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)sm_cplx));
   // element lists: real path (no impedance face, real source) and complex path
-  std::vector<int64_t> lreal, lcplx;
+  // element lists: real path (no impedance face, real source), split path
+  // (impedance faces, Gaussian source: the only complex entries are the
+  // impedance terms of the p-hat columns) and complex path (other sources)
+  std::vector<int64_t> lreal, lsplit, lcplx;
   const bool real_src = S.pb.source != DPGMG_SRC_MANUFACTURED;
+  const int64_t ld1 = a.m + 1, ld2 = ld1 + a.nph;
+  const bool split_ok = S.pb.source == DPGMG_SRC_GAUSSIAN && ld2 * ld2 <= 2 * ld1 * ld1;
   for (int64_t e = 0; e < nel; ++e) {
     int ec[3];
     m.elem_coord(e, ec);
     bool interior = true;
     for (int d = 0; d < 3; ++d)
       if (ec[d] == 0 || ec[d] == m.n[d] - 1) interior = false;
-    (interior && real_src ? lreal : lcplx).push_back(e);
+    if (interior && real_src) lreal.push_back(e);
+    else if (split_ok) lsplit.push_back(e);
+    else lcplx.push_back(e);
   }
   int64_t* dreal = upload(A, lreal, st);
+  int64_t* dsplit = upload(A, lsplit, st);
   int64_t* dcplx = upload(A, lcplx, st);
+  auto run_split = [&](const int64_t* dl, int64_t cnt) {
+    a.elist = dl;
+    for (int64_t e0 = 0; e0 < cnt; e0 += chunk) {
+      a.e0 = e0;
+      const int nb = (int)std::min<int64_t>(chunk, cnt - e0);
+      k_elem_build<double, true><<<nb, CTA_THREADS, sm_build, st>>>(a);
+      DPG_CHECK_LAUNCH();
+      k_elem_potrf<<<nb, CTA_THREADS, sm_real, st>>>(a);
+      DPG_CHECK_LAUNCH();
+      k_elem_trsm_split<<<nb, CTA_THREADS, sm_cplx, st>>>(a);
+      DPG_CHECK_LAUNCH();
+      k_elem_herk_split<<<nb, CTA_THREADS, sm_cplx, st>>>(a);
+      DPG_CHECK_LAUNCH();
+      k_elem_split_assemble<<<nb, CTA_THREADS, 0, st>>>(a);
+      DPG_CHECK_LAUNCH();
+      k_elem_condense<double2, true><<<nb, CTA_THREADS, sm_cplx, st>>>(a);
+      DPG_CHECK_LAUNCH();
+    }
+  };
   auto run_list = [&](const int64_t* dl, int64_t cnt, bool real) {
     a.elist = dl;
     for (int64_t e0 = 0; e0 < cnt; e0 += chunk) {
@@ -511,6 +616,7 @@ static void element_core(SystemImpl& S, Level& L, const std::vector<double>& cva
     }
   };
   run_list(dreal, (int64_t)lreal.size(), true);
+  run_split(dsplit, (int64_t)lsplit.size());
   run_list(dcplx, (int64_t)lcplx.size(), false);
   if (finest) {
     // algorithmic multiply-adds (an FMA is 2 flops, a complex FMA 8): Gram
@@ -519,7 +625,12 @@ static void element_core(SystemImpl& S, Level& L, const std::vector<double>& cva
     const double n = a.nt, m1 = a.m + 1, nf = a.nf, t1 = a.ntr + 1.0;
     const double fma_g = n * n * n / 6.0;
     const double fma_w = n * n * m1 / 2.0 + m1 * m1 * n / 2.0 + nf * nf * nf / 6.0 + nf * nf * t1 + a.ntr * t1 * nf;
-    S.elem_flops = (double)lreal.size() * (2.0 * fma_g + 2.0 * fma_w) + (double)lcplx.size() * (2.0 * fma_g + 8.0 * fma_w);
+    // split path: real TRSM and HERK over m + 1 + nph columns, complex condensation
+    const double m2 = (double)ld2, fma_c = nf * nf * nf / 6.0 + nf * nf * t1 + a.ntr * t1 * nf;
+    const double fma_s = n * n * m2 / 2.0 + m2 * m2 * n / 2.0;
+    S.elem_flops = (double)lreal.size() * (2.0 * fma_g + 2.0 * fma_w) +
+                   (double)lsplit.size() * (2.0 * fma_g + 2.0 * fma_s + 8.0 * fma_c) +
+                   (double)lcplx.size() * (2.0 * fma_g + 8.0 * fma_w);
   }
   int info = 0;
   DPG_CUDA(cudaMemcpyAsync(&info, a.info, sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -528,6 +639,7 @@ static void element_core(SystemImpl& S, Level& L, const std::vector<double>& cva
   A.release(a.W);
   A.release(a.K);
   A.release(dreal);
+  A.release(dsplit);
   A.release(dcplx);
   a.G = nullptr;
   a.W = nullptr;
