@@ -479,14 +479,19 @@ void build_hierarchy(SystemImpl& S, cudaStream_t st) {
     });
   };
   S.levels[L].dofs = upload_dofs(A, S.levels[L].mesh, st);
+  // Pass 1: every level's operator (restriction chain) and transfer data, down
+  // to level 0; pass 2: smoothers and damping.  The coarsest factorisation
+  // starts between the two and overlaps all of pass 2.
+  std::vector<std::vector<char>> smasks(L + 1);
+  std::vector<int> Hs(L + 1, 2);
   for (int l = L; l >= 1; --l) {
     Level& F = S.levels[l];
     Level& C = S.levels[l - 1];
     C.dofs = upload_dofs(A, C.mesh, st);
     C.nloc = (int)C.mesh.loc.size();
     C.E = A.arr<double2>((size_t)C.mesh.nelem * C.nloc * C.nloc);
-    std::vector<char> smask;
-    int H;
+    std::vector<char>& smask = smasks[l];
+    int& H = Hs[l];
     if (F.kind == 1) {
       std::vector<int32_t> sel, inj;
       p_selection(F.mesh.p, sel);
@@ -559,10 +564,15 @@ void build_hierarchy(SystemImpl& S, cudaStream_t st) {
       A.release(C.E);
       element_stage_level(S, C, st);
     }
-    if (l == 1 && dense) start_coarse();
+  }
+  if (L >= 1 && dense) start_coarse();
+  for (int l = L; l >= 1; --l) {
+    Level& F = S.levels[l];
+    Level& C = S.levels[l - 1];
+    const std::vector<char>& smask = smasks[l];
     F.n_smooth = 0;
     for (char c : smask) F.n_smooth += c;
-    setup_patches(S, F, smask, H, C.mesh.n, dinfo, st, mixed);
+    setup_patches(S, F, smask, Hs[l], C.mesh.n, dinfo, st, mixed);
     estimate_theta(S, l, st);
     if (mixed) {
       F.A.v32 = to_c64(A, F.A.v64, F.A.nnz, st);
