@@ -308,6 +308,25 @@ int dpgmg_error_indicator(dpgmg_handle h, dpgmg_system sys, const double* x, dou
 int dpgmg_setup_profile(dpgmg_handle h, dpgmg_system sys, double* element_ms, double* element_gflop,
                         double* setup_ms);
 
+/* Device time of each setup phase of a system, in ms, from CUDA events
+ * recorded at the phase boundaries (the setup stream and the side stream of
+ * the coarsest factorisation):
+ *   [0] batched element stage (Sec. 2);
+ *   [1] level operators and transfer data, finest to coarsest (restriction
+ *       A_c = I^* M I, macro condensation of the h-levels, Sec. 3);
+ *   [2] smoothers of all levels (patch extraction and inversion, damping
+ *       theta, complex64 copies on the mixed path);
+ *   [3] coarsest factorisation on the side stream, overlapping [2]
+ *       (0 when it ran on the setup stream);
+ *   [4] wait for the coarsest factorisation after [2] (its whole time when
+ *       it ran on the setup stream);
+ *   [5] load assembly and solve preparation (CG operator split, tuning).
+ * [0] + [1] + [2] + [4] + [5] is the setup's device time.  Writes
+ * min(n, DPGMG_SETUP_NPHASES) values to ms (host).  Errors: ARG (null
+ * argument, n < 1). */
+#define DPGMG_SETUP_NPHASES 6
+int dpgmg_setup_phases(dpgmg_handle h, dpgmg_system sys, double* ms, int n);
+
 /* Bracket every launch of one kernel with CUDA events on the launching
  * stream during subsequent dpgmg_solve calls (which = DPGMG_PROF_*; OFF
  * clears).  dpgmg_profile_read() synchronises, returns the summed device

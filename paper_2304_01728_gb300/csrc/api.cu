@@ -208,26 +208,52 @@ void setup_system(SystemImpl& S, const dpgmg_problem* pb, const dpgmg_opts* op, 
     L.kind = specs[i].kind_below;
     L.nloc = (int)L.mesh.loc.size();
   }
-  cudaEvent_t e0, e1, ee;
-  DPG_CUDA(cudaEventCreate(&e0));
-  DPG_CUDA(cudaEventCreate(&e1));
-  DPG_CUDA(cudaEventCreate(&ee));
-  DPG_CUDA(cudaEventRecord(e0, st));
+  struct PhaseEvents {   // destroyed on every exit path
+    cudaEvent_t e[8] = {};
+    ~PhaseEvents() {
+      for (cudaEvent_t x : e)
+        if (x) cudaEventDestroy(x);
+    }
+  } ph;
+  for (cudaEvent_t& x : ph.e) DPG_CUDA(cudaEventCreate(&x));
+  S.ph_ev = ph.e;
+  S.ph_side = false;
+  struct ClearPh {
+    SystemImpl& S;
+    ~ClearPh() { S.ph_ev = nullptr; }
+  } clear_ph{S};
+  // host index plan of the hierarchy: built on a host thread during the element stage
+  S.plan.reset();
+  S.host_plan = std::async(std::launch::async, [&S]() { return plan_host(S); });
+  struct DropPlan {   // the plan is setup-only memory; the future is drained on every exit path
+    SystemImpl& S;
+    ~DropPlan() {
+      if (S.host_plan.valid()) S.host_plan.wait();
+      S.host_plan = {};
+      S.plan.reset();
+    }
+  } drop_plan{S};
+  DPG_CUDA(cudaEventRecord(ph.e[0], st));
   element_stage(S, st);
-  DPG_CUDA(cudaEventRecord(ee, st));
-  build_hierarchy(S, st);
+  DPG_CUDA(cudaEventRecord(ph.e[1], st));
+  build_hierarchy(S, st);   // records 2, 3, 4 (and 5, 6 on the side stream)
   assemble_rhs(S, st);
   prepare_solve(S, st);
-  DPG_CUDA(cudaEventRecord(e1, st));
-  DPG_CUDA(cudaEventSynchronize(e1));
-  float ms = 0.f, mse = 0.f;
-  DPG_CUDA(cudaEventElapsedTime(&ms, e0, e1));
-  DPG_CUDA(cudaEventElapsedTime(&mse, e0, ee));
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
-  cudaEventDestroy(ee);
-  S.t_setup_ms = ms;
-  S.t_elem_ms = mse;
+  DPG_CUDA(cudaEventRecord(ph.e[7], st));
+  DPG_CUDA(cudaEventSynchronize(ph.e[7]));
+  auto span = [&](int a, int b) {
+    float ms = 0.f;
+    DPG_CUDA(cudaEventElapsedTime(&ms, ph.e[a], ph.e[b]));
+    return (double)ms;
+  };
+  S.t_setup_ms = span(0, 7);
+  S.t_elem_ms = span(0, 1);
+  S.t_phase[0] = span(0, 1);
+  S.t_phase[1] = span(1, 2);
+  S.t_phase[2] = span(2, 3);
+  S.t_phase[3] = S.ph_side ? span(5, 6) : 0.0;
+  S.t_phase[4] = span(3, 4);
+  S.t_phase[5] = span(4, 7);
   fill_bytes_per_iter(S);
 }
 
@@ -468,6 +494,13 @@ int dpgmg_setup_profile(dpgmg_handle h, dpgmg_system sys, double* element_ms, do
   if (element_ms) *element_ms = S.t_elem_ms;
   if (element_gflop) *element_gflop = S.elem_flops * 1e-9;
   if (setup_ms) *setup_ms = S.t_setup_ms;
+  return DPGMG_OK;
+}
+
+int dpgmg_setup_phases(dpgmg_handle h, dpgmg_system sys, double* ms, int n) {
+  if (!h || !sys || !ms || n < 1) return DPGMG_ERR_ARG;
+  const SystemImpl& S = sys->s;
+  for (int i = 0; i < n && i < DPGMG_SETUP_NPHASES; ++i) ms[i] = S.t_phase[i];
   return DPGMG_OK;
 }
 

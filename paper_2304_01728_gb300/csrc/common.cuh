@@ -81,18 +81,64 @@ constexpr int CTA_THREADS = 256;
 constexpr int NB = 32;          // panel width
 constexpr int TL = 32;          // output tile edge of the tiled updates
 
+// The CTAs that share one dense problem.  Team<false> is one CTA (the
+// default of every routine below).  Team<true> is a thread-block cluster of
+// `n` CTAs on different SMs: each routine gives every output tile to one CTA
+// (`rank`), the CTAs meet at cluster barriers between dependent phases, and
+// global reads of the shared matrix bypass L1 (another SM may have written
+// them since this SM cached the line).  Tile ownership is by absolute tile
+// coordinates, so every entry is computed by the same instructions in the
+// same order as with one CTA: results are bitwise those of Team<false>.
+template <bool CL>
+struct Team {
+  int rank = 0, n = 1;
+  __device__ __forceinline__ void sync() const {
+    if constexpr (CL) {
+      asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+    } else {
+      __syncthreads();
+    }
+  }
+  template <class T>
+  __device__ __forceinline__ T ld(const T* p) const {
+    if constexpr (CL) return __ldcg(p);
+    else return *p;
+  }
+  // owner of lower-triangle tile (I, J), J <= I: round robin over the packed index
+  __device__ __forceinline__ bool own2(int I, int J) const {
+    if constexpr (CL) return (((int64_t)I * (I + 1) / 2 + J) % n) == rank;
+    else return true;
+  }
+  // owner of column tile t: zigzag (0..n-1, n-1..0, ...), which balances the
+  // triangular work of the column tiles of a triangular inverse
+  __device__ __forceinline__ bool own_col(int t) const {
+    if constexpr (CL) {
+      const int c = t / n, q = t % n;
+      return ((c & 1) ? n - 1 - q : q) == rank;
+    } else {
+      return true;
+    }
+  }
+  // owner of row tile t (plain copies)
+  __device__ __forceinline__ bool own_row(int t) const {
+    if constexpr (CL) return t % n == rank;
+    else return true;
+  }
+};
+
 // In-place lower Cholesky A = L L^H of an n x n Hermitian matrix (row-major,
 // leading dimension lda).  The strict upper triangle is not referenced and
 // is left unchanged.  Returns 0 or k+1 if the k-th pivot is not positive.
 // smem: >= NB*NB + 2*TL*NB elements of T.
-template <class T>
-__device__ int cta_potrf(T* A, int n, int lda, T* smem) {
+template <class T, bool CL = false>
+__device__ int cta_potrf(T* A, int n, int lda, T* smem, Team<CL> tm = Team<CL>()) {
   using O = Ops<T>;
   using R = typename O::R;
   T* D = smem;
   T* Pi = smem + NB * NB;
   T* Pj = Pi + TL * NB;
   __shared__ int info;
+  __shared__ R rdiag[NB];   // 1 / L[j][j] of the current diagonal block
   const int tid = threadIdx.x;
   if (tid == 0) info = 0;
   __syncthreads();
@@ -101,7 +147,7 @@ __device__ int cta_potrf(T* A, int n, int lda, T* smem) {
     // diagonal block -> shared, unblocked factorisation
     for (int e = tid; e < kb * kb; e += blockDim.x) {
       int i = e / kb, j = e % kb;
-      D[i * NB + j] = A[(size_t)(k0 + i) * lda + k0 + j];
+      D[i * NB + j] = tm.ld(&A[(size_t)(k0 + i) * lda + k0 + j]);
     }
     __syncthreads();
     for (int j = 0; j < kb; ++j) {
@@ -109,9 +155,10 @@ __device__ int cta_potrf(T* A, int n, int lda, T* smem) {
         R d = O::re(D[j * NB + j]);
         if (!(d > R(0))) { if (info == 0) info = k0 + j + 1; d = R(1); }
         D[j * NB + j] = O::from_re(sqrt(d));
+        rdiag[j] = R(1) / O::re(D[j * NB + j]);
       }
       __syncthreads();
-      R inv = R(1) / O::re(D[j * NB + j]);
+      const R inv = rdiag[j];
       for (int i = j + 1 + tid; i < kb; i += blockDim.x) D[i * NB + j] = O::scale(D[i * NB + j], inv);
       __syncthreads();
       // rank-1 update of the remaining lower part
@@ -122,33 +169,37 @@ __device__ int cta_potrf(T* A, int n, int lda, T* smem) {
       }
       __syncthreads();
     }
-    for (int e = tid; e < kb * kb; e += blockDim.x) {
-      int i = e / kb, j = e % kb;
-      if (j <= i) A[(size_t)(k0 + i) * lda + k0 + j] = D[i * NB + j];
+    if (tm.own2(k0 / TL, k0 / TL)) {
+      for (int e = tid; e < kb * kb; e += blockDim.x) {
+        int i = e / kb, j = e % kb;
+        if (j <= i) A[(size_t)(k0 + i) * lda + k0 + j] = D[i * NB + j];
+      }
     }
     // panel: rows below solve x L_kk^H = a
     const int k1 = k0 + kb;
     for (int i = k1 + tid; i < n; i += blockDim.x) {
+      if (!tm.own2(i / TL, k0 / TL)) continue;
       T* row = A + (size_t)i * lda + k0;
       T x[NB];
       for (int j = 0; j < kb; ++j) {
-        T v = row[j];
+        T v = tm.ld(&row[j]);
         for (int t = 0; t < j; ++t) v = O::fnmac(x[t], D[j * NB + t], v);
-        x[j] = O::scale(v, R(1) / O::re(D[j * NB + j]));
+        x[j] = O::scale(v, rdiag[j]);
       }
       for (int j = 0; j < kb; ++j) row[j] = x[j];
     }
-    __syncthreads();
+    tm.sync();
     // trailing update A[i][j] -= sum_t L[i][t] conj(L[j][t]), lower part
     const int m = n - k1;
     const int nt = (m + TL - 1) / TL;
     for (int bi = 0; bi < nt; ++bi) {
       for (int bj = 0; bj <= bi; ++bj) {
         const int i0 = k1 + bi * TL, j0 = k1 + bj * TL;
+        if (!tm.own2(i0 / TL, j0 / TL)) continue;
         for (int e = tid; e < TL * NB; e += blockDim.x) {
           int r = e / NB, t = e % NB;
-          Pi[e] = (i0 + r < n && t < kb) ? A[(size_t)(i0 + r) * lda + k0 + t] : O::zero();
-          Pj[e] = (j0 + r < n && t < kb) ? A[(size_t)(j0 + r) * lda + k0 + t] : O::zero();
+          Pi[e] = (i0 + r < n && t < kb) ? tm.ld(&A[(size_t)(i0 + r) * lda + k0 + t]) : O::zero();
+          Pj[e] = (j0 + r < n && t < kb) ? tm.ld(&A[(size_t)(j0 + r) * lda + k0 + t]) : O::zero();
         }
         __syncthreads();
         for (int e = tid; e < TL * TL; e += blockDim.x) {
@@ -158,12 +209,13 @@ __device__ int cta_potrf(T* A, int n, int lda, T* smem) {
             T acc = O::zero();
             for (int t = 0; t < kb; ++t) acc = O::fmac(Pi[r * NB + t], Pj[c * NB + t], acc);
             size_t o = (size_t)i * lda + j;
-            A[o] = O::sub(A[o], acc);
+            A[o] = O::sub(tm.ld(&A[o]), acc);
           }
         }
         __syncthreads();
       }
     }
+    if constexpr (CL) tm.sync();
   }
   __syncthreads();
   return info;
@@ -189,6 +241,7 @@ __device__ void cta_trsm_lower(const TLt* L, int n, int ldl, TB* B, int nrhs, in
   TLt* D = reinterpret_cast<TLt*>(smem);
   TLt* Lt = D + NB * NB;
   TB* Xt = reinterpret_cast<TB*>(Lt + TL * NB);
+  __shared__ RB rdiag[NB];
   const int tid = threadIdx.x;
   for (int k0 = 0; k0 < n; k0 += NB) {
     const int kb = min(NB, n - k0);
@@ -196,6 +249,7 @@ __device__ void cta_trsm_lower(const TLt* L, int n, int ldl, TB* B, int nrhs, in
       int i = e / kb, j = e % kb;
       D[i * NB + j] = (j <= i) ? L[(size_t)(k0 + i) * ldl + k0 + j] : OL::zero();
     }
+    if (tid < kb) rdiag[tid] = RB(1) / OL::re(L[(size_t)(k0 + tid) * ldl + k0 + tid]);
     __syncthreads();
     // diagonal solve: one thread per right-hand-side column
     for (int c = tid; c < nrhs; c += blockDim.x) {
@@ -203,7 +257,7 @@ __device__ void cta_trsm_lower(const TLt* L, int n, int ldl, TB* B, int nrhs, in
       for (int r = 0; r < kb; ++r) {
         TB v = B[(size_t)(k0 + r) * ldb + c];
         for (int t = 0; t < r; ++t) v = OB::sub(v, lmul(D[r * NB + t], x[t]));
-        x[r] = OB::scale(v, RB(1) / OL::re(D[r * NB + r]));
+        x[r] = OB::scale(v, rdiag[r]);
         B[(size_t)(k0 + r) * ldb + c] = x[r];
       }
     }
@@ -247,6 +301,7 @@ __device__ void cta_trsm_lower_h(const T* L, int n, int ldl, T* B, int nrhs, int
   T* D = reinterpret_cast<T*>(smem);
   T* Lt = D + NB * NB;
   T* Xt = Lt + TL * NB;
+  __shared__ R rdiag[NB];
   const int tid = threadIdx.x;
   const int nblk = (n + NB - 1) / NB;
   for (int kbI = nblk - 1; kbI >= 0; --kbI) {
@@ -256,6 +311,7 @@ __device__ void cta_trsm_lower_h(const T* L, int n, int ldl, T* B, int nrhs, int
       int i = e / kb, j = e % kb;
       D[i * NB + j] = (j <= i) ? L[(size_t)(k0 + i) * ldl + k0 + j] : O::zero();
     }
+    if (tid < kb) rdiag[tid] = R(1) / O::re(L[(size_t)(k0 + tid) * ldl + k0 + tid]);
     __syncthreads();
     // diagonal: (L_kk^H) x = b  ->  x_r = (b_r - sum_{t>r} conj(D[t][r]) x_t) / D[r][r]
     for (int c = tid; c < nrhs; c += blockDim.x) {
@@ -263,7 +319,7 @@ __device__ void cta_trsm_lower_h(const T* L, int n, int ldl, T* B, int nrhs, int
       for (int r = kb - 1; r >= 0; --r) {
         T v = B[(size_t)(k0 + r) * ldb + c];
         for (int t = r + 1; t < kb; ++t) v = O::sub(v, O::mul(O::conj(D[t * NB + r]), x[t]));
-        x[r] = O::scale(v, R(1) / O::re(D[r * NB + r]));
+        x[r] = O::scale(v, rdiag[r]);
         B[(size_t)(k0 + r) * ldb + c] = x[r];
       }
     }
@@ -354,28 +410,31 @@ __device__ void cta_gemm(bool transA, int m, int n, int k, typename Ops<T>::R al
 // X = L^-1 in place of X = I (L lower triangular, n x n).  Blocks of X above
 // the diagonal stay zero and are skipped: n^3/6 multiply-adds.
 // smem: as cta_trsm_lower<T, T>.
-template <class T>
-__device__ void cta_trinv_lower(const T* L, int n, int ldl, T* X, int ldx, char* smem) {
+template <class T, bool CL = false>
+__device__ void cta_trinv_lower(const T* L, int n, int ldl, T* X, int ldx, char* smem, Team<CL> tm = Team<CL>()) {
   using O = Ops<T>;
   using R = typename O::R;
   T* D = reinterpret_cast<T*>(smem);
   T* Lt = D + NB * NB;
   T* Xt = Lt + TL * NB;
+  __shared__ R rdiag[NB];
   const int tid = threadIdx.x;
   for (int k0 = 0; k0 < n; k0 += NB) {
     const int kb = min(NB, n - k0);
     const int k1 = k0 + kb;
     for (int e = tid; e < kb * kb; e += blockDim.x) {
       int i = e / kb, j = e % kb;
-      D[i * NB + j] = (j <= i) ? L[(size_t)(k0 + i) * ldl + k0 + j] : O::zero();
+      D[i * NB + j] = (j <= i) ? tm.ld(&L[(size_t)(k0 + i) * ldl + k0 + j]) : O::zero();
     }
+    if (tid < kb) rdiag[tid] = R(1) / O::re(tm.ld(&L[(size_t)(k0 + tid) * ldl + k0 + tid]));
     __syncthreads();
     for (int c = tid; c < k1; c += blockDim.x) {
+      if (!tm.own_col(c / TL)) continue;
       T x[NB];
       for (int r = 0; r < kb; ++r) {
-        T v = X[(size_t)(k0 + r) * ldx + c];
+        T v = tm.ld(&X[(size_t)(k0 + r) * ldx + c]);
         for (int t = 0; t < r; ++t) v = O::fnma(D[r * NB + t], x[t], v);
-        x[r] = O::scale(v, R(1) / O::re(D[r * NB + r]));
+        x[r] = O::scale(v, rdiag[r]);
         X[(size_t)(k0 + r) * ldx + c] = x[r];
       }
     }
@@ -383,12 +442,13 @@ __device__ void cta_trinv_lower(const T* L, int n, int ldl, T* X, int ldx, char*
     for (int i0 = k1; i0 < n; i0 += TL) {
       for (int e = tid; e < TL * NB; e += blockDim.x) {
         int r = e / NB, t = e % NB;
-        Lt[e] = (i0 + r < n && t < kb) ? L[(size_t)(i0 + r) * ldl + k0 + t] : O::zero();
+        Lt[e] = (i0 + r < n && t < kb) ? tm.ld(&L[(size_t)(i0 + r) * ldl + k0 + t]) : O::zero();
       }
       for (int c0 = 0; c0 < k1; c0 += TL) {
+        if (!tm.own_col(c0 / TL)) continue;
         for (int e = tid; e < NB * TL; e += blockDim.x) {
           int t = e / TL, c = e % TL;
-          Xt[e] = (t < kb && c0 + c < k1) ? X[(size_t)(k0 + t) * ldx + c0 + c] : O::zero();
+          Xt[e] = (t < kb && c0 + c < k1) ? tm.ld(&X[(size_t)(k0 + t) * ldx + c0 + c]) : O::zero();
         }
         __syncthreads();
         for (int e = tid; e < TL * TL; e += blockDim.x) {
@@ -398,7 +458,7 @@ __device__ void cta_trinv_lower(const T* L, int n, int ldl, T* X, int ldx, char*
             T acc = O::zero();
             for (int t = 0; t < kb; ++t) acc = O::fma(Lt[r * NB + t], Xt[t * TL + c], acc);
             size_t o = (size_t)i * ldx + cc;
-            X[o] = O::sub(X[o], acc);
+            X[o] = O::sub(tm.ld(&X[o]), acc);
           }
         }
         __syncthreads();
@@ -413,8 +473,9 @@ __device__ void cta_trinv_lower(const T* L, int n, int ldl, T* X, int ldx, char*
 // of a full product).  With `tri` X is lower triangular (kdim = n) and each
 // tile sums only over rows k >= its first row (X[k][i] = 0 for k < i):
 // n^3/6 multiply-adds.  smem: 2*TL*NB elements of T.
-template <class T>
-__device__ void cta_herk_lower(const T* X, int kdim, int n, int ldx, T* M, int ldm, T* smem, bool tri) {
+template <class T, bool CL = false>
+__device__ void cta_herk_lower(const T* X, int kdim, int n, int ldx, T* M, int ldm, T* smem, bool tri,
+                               Team<CL> tm = Team<CL>()) {
   using O = Ops<T>;
   T* At = smem;
   T* Bt = smem + TL * NB;
@@ -422,16 +483,17 @@ __device__ void cta_herk_lower(const T* X, int kdim, int n, int ldx, T* M, int l
   constexpr int PER = TL * TL / CTA_THREADS;
   for (int i0 = 0; i0 < n; i0 += TL) {
     for (int j0 = 0; j0 <= i0; j0 += TL) {
+      if (!tm.own2(i0 / TL, j0 / TL)) continue;
       T acc[PER];
       for (int q = 0; q < PER; ++q) acc[q] = O::zero();
       for (int k0 = tri ? i0 : 0; k0 < kdim; k0 += NB) {
         for (int e = tid; e < TL * NB; e += blockDim.x) {
           int r = e / NB, t = e % NB;
-          At[e] = (i0 + r < n && k0 + t < kdim) ? O::conj(X[(size_t)(k0 + t) * ldx + i0 + r]) : O::zero();
+          At[e] = (i0 + r < n && k0 + t < kdim) ? O::conj(tm.ld(&X[(size_t)(k0 + t) * ldx + i0 + r])) : O::zero();
         }
         for (int e = tid; e < NB * TL; e += blockDim.x) {
           int t = e / TL, c = e % TL;
-          Bt[e] = (k0 + t < kdim && j0 + c < n) ? X[(size_t)(k0 + t) * ldx + j0 + c] : O::zero();
+          Bt[e] = (k0 + t < kdim && j0 + c < n) ? tm.ld(&X[(size_t)(k0 + t) * ldx + j0 + c]) : O::zero();
         }
         __syncthreads();
         for (int q = 0; q < PER; ++q) {
@@ -458,9 +520,9 @@ __device__ void cta_herk_lower(const T* X, int kdim, int n, int ldx, T* M, int l
   __syncthreads();
 }
 
-template <class T>
-__device__ void cta_herk_lower_tri(const T* X, int n, int ldx, T* M, int ldm, T* smem) {
-  cta_herk_lower<T>(X, n, n, ldx, M, ldm, smem, true);
+template <class T, bool CL = false>
+__device__ void cta_herk_lower_tri(const T* X, int n, int ldx, T* M, int ldm, T* smem, Team<CL> tm = Team<CL>()) {
+  cta_herk_lower<T, CL>(X, n, n, ldx, M, ldm, smem, true, tm);
 }
 
 }  // namespace dpgmg

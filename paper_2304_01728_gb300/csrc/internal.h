@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <future>
 #include <mutex>
 #include <string>
 #include <memory>
@@ -139,6 +140,40 @@ struct Server;      // serving loop (server.cu)
 
 struct ElemArgs;   // element-stage arguments (element.cu), kept for the error indicator
 
+// Host side of an ECSR operator: index arrays and the SpMV work lists.
+struct EcsrPrep {
+  ECSRHost H;
+  std::vector<int2> tasks[4];      // (entity, first row) groups of 2^i rows (i = 1, 2, 3)
+  std::vector<int32_t> null_rows;  // rows with no entity
+  int64_t max_nnz_row = 0;
+};
+EcsrPrep prep_ecsr(const MeshL& m, const std::vector<std::vector<int64_t>>& groups);
+// entity lists of the elements of m (one group per element)
+std::vector<std::vector<int64_t>> element_groups(const MeshL& m);
+
+// Every host-only index structure of a hierarchy (integer bookkeeping: DOF
+// maps, ECSR lists, macro transfer data, patch lists and work orders).  It
+// depends on the meshes only, so setup builds it on a host thread while the
+// element stage runs on the GPU; the later phases only upload and launch.
+struct LevelPlan {
+  std::vector<int64_t> cdofs;      // element DOFs of level l-1 (element-major)
+  std::vector<int32_t> sel, inj;   // p-transition below l: local selection and injection
+  MacroHost M;                     // h-transition below l: macro-element data
+  EcsrPrep E;                      // level l's operator
+  std::vector<char> smask;         // DOFs smoothed on level l
+  int H = 2;                       // patch half-width in level-l elements
+  Patches P;
+  std::vector<int2> ch32, ch64;    // smoother work items of 32 / 64 rows, largest patch first
+  std::vector<int64_t> order;      // inversion order, largest patch first
+  int64_t max_n = 0, sum_sq = 0;
+};
+struct HostPlan {
+  std::vector<int64_t> fdofs;      // element DOFs of the finest level
+  std::vector<LevelPlan> lv;       // by level (entry 0 unused)
+  bool has_acg = false;            // finest operator with element groups (CG operator), when
+  EcsrPrep acg;                    // the finest level's own operator is not that
+};
+
 struct SystemImpl {
   dpgmg_problem pb;
   dpgmg_opts op;
@@ -155,6 +190,14 @@ struct SystemImpl {
   void* ws = nullptr;            // solver workspace
   double elem_flops = 0.0;       // algorithmic flops of the element stage
   double t_elem_ms = 0.0;        // its device time (events around the stage)
+  // setup phase boundaries (events owned by the setup call; null outside it):
+  // 0 start, 1 element stage, 2 operators, 3 smoothers, 4 after the coarsest
+  // join, 5/6 coarsest factorisation start/end on the side stream, 7 end
+  cudaEvent_t* ph_ev = nullptr;
+  bool ph_side = false;
+  std::future<std::shared_ptr<HostPlan>> host_plan;   // pending host index plan (setup only)
+  std::shared_ptr<HostPlan> plan;                     // the plan, from the hierarchy build to the end of setup
+  double t_phase[6] = {0, 0, 0, 0, 0, 0};
   int prof_which = 0;            // DPGMG_PROF_* being bracketed with events
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> prof_events;
   std::vector<int> prof_graph_pairs;   // pairs recorded by a captured graph (re-read after each replay)
@@ -194,7 +237,8 @@ void recover_fields(SystemImpl& S, const double2* x, double2* fields, cudaStream
 // DPG error indicator eta_K^2 of every finest element for the trace vector x (device)
 void error_indicator(SystemImpl& S, const double2* x, double* eta2, cudaStream_t st);
 // level.cu
-void assemble_ecsr(Alloc& A, const MeshL& m, const ECSRHost& H, ECSRDev& D, cudaStream_t st);
+void assemble_ecsr(Alloc& A, const EcsrPrep& P, ECSRDev& D, cudaStream_t st);
+std::shared_ptr<HostPlan> plan_host(const SystemImpl& S);
 void ecsr_add_elements(ECSRDev& D, const double2* E, const int64_t* dofs, int64_t nel, int nloc,
                        cudaStream_t st);
 void build_hierarchy(SystemImpl& S, cudaStream_t st);
@@ -213,7 +257,10 @@ void prepare_solve(SystemImpl& S, cudaStream_t st);
 ECSRDev* cg_operator_of(SystemImpl& S);
 void free_workspace(SystemImpl& S);
 void spmv64(const ECSRDev& A, const double2* x, double2* y, cudaStream_t st);
-void estimate_theta(SystemImpl& S, int level, cudaStream_t st);
+// enqueues the damping estimate of a level: rayleigh[0..1] (device) receive the
+// numerator and denominator of lambda; theta = theta_from_rayleigh(num, den)
+void estimate_theta(SystemImpl& S, int level, double* rayleigh, cudaStream_t st);
+double theta_from_rayleigh(double num, double den);
 void profile_read(SystemImpl& S, double* ms, long long* launches, long long* bytes);
 // api.cu: validation, footprint estimate and the whole setup of one system
 int validate_problem(const dpgmg_problem* pb, const dpgmg_opts* op);

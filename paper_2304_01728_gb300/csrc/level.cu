@@ -11,6 +11,7 @@
 //   * the coarsest level (coarse.cu).
 #include <algorithm>
 #include <mutex>
+#include <cstdlib>
 #include <map>
 #include <exception>
 #include <thread>
@@ -24,7 +25,24 @@
 namespace dpgmg {
 
 // ------------------------------------------------------------ ECSR assembly
-void assemble_ecsr(Alloc& A, const MeshL& m, const ECSRHost& H, ECSRDev& D, cudaStream_t st) {
+EcsrPrep prep_ecsr(const MeshL& m, const std::vector<std::vector<int64_t>>& groups) {
+  EcsrPrep P;
+  P.H = build_ecsr(m, groups);
+  const ECSRHost& H = P.H;
+  const int64_t nent = (int64_t)H.ent_start.size();
+  for (int64_t E = 0; E < nent; ++E) P.max_nnz_row = std::max(P.max_nnz_row, H.col_ptr[E + 1] - H.col_ptr[E]);
+  for (int gi = 1; gi <= 3; ++gi) {
+    const int G = 1 << gi;
+    for (int64_t E = 0; E < nent; ++E)
+      for (int r0 = 0; r0 < H.ent_nd[E]; r0 += G) P.tasks[gi].push_back(make_int2((int)E, r0));
+  }
+  for (int64_t r = 0; r < H.nrows; ++r)
+    if (H.row_ent[r] < 0) P.null_rows.push_back((int32_t)r);
+  return P;
+}
+
+void assemble_ecsr(Alloc& A, const EcsrPrep& P, ECSRDev& D, cudaStream_t st) {
+  const ECSRHost& H = P.H;
   D.nrows = H.nrows;
   D.nent = (int64_t)H.ent_start.size();
   D.nnz = H.nnz();
@@ -35,26 +53,15 @@ void assemble_ecsr(Alloc& A, const MeshL& m, const ECSRHost& H, ECSRDev& D, cuda
   D.col_ptr = upload(A, H.col_ptr, st);
   D.col_idx = upload(A, H.col_idx, st);
   D.val_ptr = upload(A, H.val_ptr, st);
-  D.max_nnz_row = 0;
-  for (int64_t E = 0; E < D.nent; ++E) D.max_nnz_row = std::max(D.max_nnz_row, H.col_ptr[E + 1] - H.col_ptr[E]);
+  D.max_nnz_row = P.max_nnz_row;
   for (int gi = 1; gi <= 3; ++gi) {
-    const int G = 1 << gi;
-    std::vector<int2> t;
-    for (int64_t E = 0; E < D.nent; ++E)
-      for (int r0 = 0; r0 < H.ent_nd[E]; r0 += G) t.push_back(make_int2((int)E, r0));
-    D.ntasks[gi] = (int64_t)t.size();
-    D.tasks[gi] = t.empty() ? nullptr : upload(A, t, st);
+    D.ntasks[gi] = (int64_t)P.tasks[gi].size();
+    D.tasks[gi] = P.tasks[gi].empty() ? nullptr : upload(A, P.tasks[gi], st);
   }
-  {
-    std::vector<int32_t> nr;
-    for (int64_t r = 0; r < H.nrows; ++r)
-      if (H.row_ent[r] < 0) nr.push_back((int32_t)r);
-    D.n_null = (int64_t)nr.size();
-    D.null_rows = nr.empty() ? nullptr : upload(A, nr, st);
-  }
+  D.n_null = (int64_t)P.null_rows.size();
+  D.null_rows = P.null_rows.empty() ? nullptr : upload(A, P.null_rows, st);
   D.v64 = A.arr<double2>((size_t)D.nnz);
   DPG_CUDA(cudaMemsetAsync(D.v64, 0, (size_t)D.nnz * sizeof(double2), st));
-  (void)m;
 }
 
 __device__ __forceinline__ int64_t ecsr_find(const ECSRDev& A, int64_t row, int64_t col) {
@@ -94,7 +101,7 @@ void ecsr_add_elements(ECSRDev& D, const double2* E, const int64_t* dofs, int64_
   DPG_CHECK_LAUNCH();
 }
 
-static std::vector<std::vector<int64_t>> element_groups(const MeshL& m) {
+std::vector<std::vector<int64_t>> element_groups(const MeshL& m) {
   std::vector<std::vector<int64_t>> g(m.nelem);
   std::vector<int64_t> ent(m.loc.size());
   for (int64_t e = 0; e < m.nelem; ++e) {
@@ -107,10 +114,10 @@ static std::vector<std::vector<int64_t>> element_groups(const MeshL& m) {
   return g;
 }
 
-static int64_t* upload_dofs(Alloc& A, const MeshL& m, cudaStream_t st) {
+static std::vector<int64_t> elem_dof_table(const MeshL& m) {
   std::vector<int64_t> d((size_t)m.nelem * m.loc.size());
   for (int64_t e = 0; e < m.nelem; ++e) m.elem_dofs(e, d.data() + e * m.loc.size());
-  return upload(A, d, st);
+  return d;
 }
 
 // ------------------------------------------------------------ p-transition
@@ -225,19 +232,38 @@ __device__ __forceinline__ double2 mul_i(double2 v, int s) {   // v * (i)^s, s i
 // exactly phased: the test below is exact), Cholesky, triangular inverse and
 // L^-H L^-1 run in real arithmetic (a quarter of the flops) and the phases
 // are put back on the inverse.  Other patches take the complex path.
-template <class C>
+// CL: one patch per thread-block cluster; the cluster's CTAs share every
+// dense step (Team<true>), which spreads a large patch over several SMs.
+__device__ __forceinline__ unsigned cluster_rank() {
+  unsigned r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+__device__ __forceinline__ unsigned cluster_size() {
+  unsigned r;
+  asm volatile("mov.u32 %0, %%cluster_nctarank;" : "=r"(r));
+  return r;
+}
+
+template <class C, bool CL>
 __global__ void __launch_bounds__(CTA_THREADS) k_patch_invert(const int64_t* ptr, const int32_t* pdofs,
                                                             const int64_t* vptr, C* vals, C* scratch,
                                                             const int64_t* soff, const int64_t* order, int64_t j0,
                                                             int64_t offU, int* info) {
   extern __shared__ unsigned char shraw[];
   C* sh = reinterpret_cast<C*>(shraw);
-  const int64_t j = order[j0 + blockIdx.x];
+  Team<CL> tm;
+  if constexpr (CL) {
+    tm.rank = (int)cluster_rank();
+    tm.n = (int)cluster_size();
+  }
+  const int64_t slot = blockIdx.x / tm.n;
+  const int64_t j = order[j0 + slot];
   const int64_t b = ptr[j];
   const int n = (int)(ptr[j + 1] - b);
   const int ld = (int)patch_ld(n);   // stored row length; column n (if any) is padding, left 0
   C* M = vals + vptr[j];
-  C* W = scratch + soff[blockIdx.x];
+  C* W = scratch + soff[j0 + slot];
   bool cplx = false;
   if (sizeof(C) == sizeof(double2)) {
     for (int q = threadIdx.x; q < n * n; q += blockDim.x) {
@@ -255,37 +281,46 @@ __global__ void __launch_bounds__(CTA_THREADS) k_patch_invert(const int64_t* ptr
     double* shr = reinterpret_cast<double*>(shraw);
     for (int q = threadIdx.x; q < n * n; q += blockDim.x) {
       const int r = q / n, c = q % n;
+      if (!tm.own_row(r / TL)) continue;
       const int sr = pdofs[b + r] < offU ? 1 : 0, sc = pdofs[b + c] < offU ? 1 : 0;
       Wr[q] = mul_i(*reinterpret_cast<const double2*>(M + (size_t)r * ld + c), sc - sr).x;
     }
-    __syncthreads();
-    int inf = cta_potrf<double>(Wr, n, n, shr);
-    if (threadIdx.x == 0 && inf) atomicOr(info, 8);
-    for (int q = threadIdx.x; q < n * n; q += blockDim.x) Mr[q] = (q / n == q % n) ? 1.0 : 0.0;
-    __syncthreads();
-    cta_trinv_lower<double>(Wr, n, n, Mr, n, reinterpret_cast<char*>(shr));
-    cta_herk_lower_tri<double>(Mr, n, n, Wr, n, shr);
+    tm.sync();   // every CTA has read M before any overwrites it
+    int inf = cta_potrf<double, CL>(Wr, n, n, shr, tm);
+    if (threadIdx.x == 0 && inf && tm.rank == 0) atomicOr(info, 8);
+    for (int q = threadIdx.x; q < n * n; q += blockDim.x)
+      if (tm.own_row((q / n) / TL)) Mr[q] = (q / n == q % n) ? 1.0 : 0.0;
+    tm.sync();
+    cta_trinv_lower<double, CL>(Wr, n, n, Mr, n, reinterpret_cast<char*>(shr), tm);
+    tm.sync();
+    cta_herk_lower_tri<double, CL>(Mr, n, n, Wr, n, shr, tm);
+    tm.sync();
     for (int q = threadIdx.x; q < n * ld; q += blockDim.x) {
       const int r = q / ld, c = q % ld;
+      if (!tm.own_row(r / TL)) continue;
       const int sr = pdofs[b + r] < offU ? 1 : 0, sc = c < n && pdofs[b + c] < offU ? 1 : 0;
       *reinterpret_cast<double2*>(M + q) =
-          c < n ? mul_i(make_double2(Wr[(size_t)r * n + c], 0.0), sr - sc) : make_double2(0.0, 0.0);
+          c < n ? mul_i(make_double2(tm.ld(&Wr[(size_t)r * n + c]), 0.0), sr - sc) : make_double2(0.0, 0.0);
     }
     return;
   }
-  for (int q = threadIdx.x; q < n * n; q += blockDim.x) W[q] = M[(size_t)(q / n) * ld + q % n];
-  __syncthreads();
-  int inf = cta_potrf<C>(W, n, n, sh);
-  if (threadIdx.x == 0 && inf) atomicOr(info, 8);
+  for (int q = threadIdx.x; q < n * n; q += blockDim.x)
+    if (tm.own_row((q / n) / TL)) W[q] = M[(size_t)(q / n) * ld + q % n];
+  tm.sync();
+  int inf = cta_potrf<C, CL>(W, n, n, sh, tm);
+  if (threadIdx.x == 0 && inf && tm.rank == 0) atomicOr(info, 8);
   // M = L^-1 (lower, row length ld), then W = L^-H L^-1 = A^-1, copied back into M
   for (int q = threadIdx.x; q < n * ld; q += blockDim.x)
-    M[q] = (q / ld == q % ld) ? Ops<C>::from_re(1) : Ops<C>::zero();
-  __syncthreads();
-  cta_trinv_lower<C>(W, n, n, M, ld, reinterpret_cast<char*>(sh));
-  cta_herk_lower_tri<C>(M, n, ld, W, n, sh);
+    if (tm.own_row((q / ld) / TL)) M[q] = (q / ld == q % ld) ? Ops<C>::from_re(1) : Ops<C>::zero();
+  tm.sync();
+  cta_trinv_lower<C, CL>(W, n, n, M, ld, reinterpret_cast<char*>(sh), tm);
+  tm.sync();
+  cta_herk_lower_tri<C, CL>(M, n, ld, W, n, sh, tm);
+  tm.sync();
   for (int q = threadIdx.x; q < n * ld; q += blockDim.x) {
     const int r = q / ld, c = q % ld;
-    M[q] = c < n ? W[(size_t)r * n + c] : Ops<C>::zero();
+    if (!tm.own_row(r / TL)) continue;
+    M[q] = c < n ? tm.ld(&W[(size_t)r * n + c]) : Ops<C>::zero();
   }
 }
 
@@ -330,86 +365,173 @@ constexpr bool kHalfStorageSmoother = false;
 
 // --------------------------------------------------------------- driver
 // Invert all patch blocks in place, in chunks that bound the scratch copy.
+// CTAs per patch.  A level with few large patches (the macro patches of an
+// h-level) leaves most SMs idle while a handful of them factor the largest
+// blocks one CTA each; a cluster of 2 or 4 CTAs per patch spreads those over
+// several SMs.  Chosen so that the level has at least ~4 largest-patch shares
+// per SM; DPGMG_PATCH_TEAM = 1, 2 or 4 overrides the choice.
+static int patch_team(const Patches& P, int64_t max_n) {
+  if (const char* e = std::getenv("DPGMG_PATCH_TEAM")) {
+    const int t = std::atoi(e);
+    if (t == 1 || t == 2 || t == 4) return t;
+  }
+  if (max_n < 96) return 1;
+  int dev = 0, nsm = 0;
+  DPG_CUDA(cudaGetDevice(&dev));
+  DPG_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+  double sum = 0.0;
+  for (size_t j = 0; j + 1 < P.ptr.size(); ++j) {
+    const double nj = (double)(P.ptr[j + 1] - P.ptr[j]);
+    sum += nj * nj * nj;
+  }
+  const double shares = sum / ((double)max_n * max_n * max_n);
+  int t = 1;
+  while (t < 4 && shares * t < 4.0 * nsm) t *= 2;
+  return t;
+}
+
 template <class C>
-static void invert_patches(Alloc& A, PatchDev& D, const Patches& P, C* vals, int64_t offU, int* dinfo,
+static void invert_patches(Alloc& A, PatchDev& D, const LevelPlan& lp, C* vals, int64_t offU, int* dinfo,
                            cudaStream_t st) {
+  const Patches& P = lp.P;
   const size_t sm = (size_t)(NB * NB + 2 * TL * NB) * sizeof(C) + 64;
-  DPG_CUDA(cudaFuncSetAttribute(k_patch_invert<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+  DPG_CUDA(cudaFuncSetAttribute(k_patch_invert<C, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+  DPG_CUDA(cudaFuncSetAttribute(k_patch_invert<C, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+  int team = patch_team(P, D.max_n);
+  cudaLaunchAttribute cattr[1];
+  cattr[0].id = cudaLaunchAttributeClusterDimension;
+  cattr[0].val.clusterDim.x = (unsigned)team;
+  cattr[0].val.clusterDim.y = 1;
+  cattr[0].val.clusterDim.z = 1;
+  cudaLaunchConfig_t cfg = {};
+  cfg.blockDim = dim3(CTA_THREADS);
+  cfg.dynamicSmemBytes = sm;
+  cfg.stream = st;
+  cfg.attrs = cattr;
+  cfg.numAttrs = 1;
+  if (team > 1) {
+    cfg.gridDim = dim3((unsigned)team);
+    int ncl = 0;
+    if (cudaOccupancyMaxActiveClusters(&ncl, k_patch_invert<C, true>, &cfg) != cudaSuccess || ncl < 1) {
+      (void)cudaGetLastError();
+      team = 1;
+    }
+  }
   const size_t one = (size_t)D.max_n * D.max_n;
   size_t cap = std::min<size_t>(std::max<size_t>(((size_t)1 << 28) / sizeof(C), one) * 4, ((size_t)2 << 30) / sizeof(C));
   cap = std::max(std::min<size_t>(cap, (size_t)D.nvals), one);
   C* scratch = A.arr<C>(cap);
-  int64_t* soff = A.arr<int64_t>((size_t)D.np + 1);
-  // largest patches first (the launch ends with the short ones)
-  std::vector<int64_t> order(D.np);
-  for (int64_t j = 0; j < D.np; ++j) order[j] = j;
-  std::stable_sort(order.begin(), order.end(), [&](int64_t u, int64_t v) {
-    return P.ptr[u + 1] - P.ptr[u] > P.ptr[v + 1] - P.ptr[v];
-  });
-  int64_t* dorder = upload(A, order, st);
-  std::vector<int64_t> offs;
-  for (int64_t j0 = 0; j0 < D.np;) {
-    offs.clear();
-    int64_t acc = 0, q = j0;
-    while (q < D.np) {
-      const int64_t j = order[q];
-      int64_t nj = P.ptr[j + 1] - P.ptr[j];
-      if (acc + nj * nj > (int64_t)cap && q > j0) break;
-      offs.push_back(acc);
-      acc += nj * nj;
-      ++q;
+  // launches of consecutive patches (largest first) whose scratch copies fit
+  // `cap`; offs[q] = scratch offset of the q-th patch within its launch
+  const std::vector<int64_t>& order = lp.order;
+  std::vector<int64_t> offs(D.np), starts;
+  for (int64_t q = 0, acc = 0; q < D.np; ++q) {
+    const int64_t j = order[q];
+    const int64_t nj = P.ptr[j + 1] - P.ptr[j];
+    if (q == 0 || acc + nj * nj > (int64_t)cap) {
+      starts.push_back(q);
+      acc = 0;
     }
-    DPG_CUDA(cudaMemcpyAsync(soff, offs.data(), offs.size() * sizeof(int64_t), cudaMemcpyHostToDevice, st));
-    k_patch_invert<C><<<(unsigned)(q - j0), CTA_THREADS, sm, st>>>(D.ptr, D.dofs, D.val_ptr, vals, scratch, soff,
-                                                                   dorder, j0, offU, dinfo);
-    DPG_CHECK_LAUNCH();
-    DPG_CUDA(cudaStreamSynchronize(st));   // the offsets buffer is reused
-    j0 = q;
+    offs[q] = acc;
+    acc += nj * nj;
+  }
+  starts.push_back(D.np);
+  int64_t* soff = upload(A, offs, st);
+  int64_t* dorder = upload(A, order, st);
+  for (size_t c = 0; c + 1 < starts.size(); ++c) {
+    const int64_t j0 = starts[c], q = starts[c + 1];
+    if (team == 1) {
+      k_patch_invert<C, false><<<(unsigned)(q - j0), CTA_THREADS, sm, st>>>(D.ptr, D.dofs, D.val_ptr, vals, scratch,
+                                                                          soff, dorder, j0, offU, dinfo);
+      DPG_CHECK_LAUNCH();
+    } else {
+      cfg.gridDim = dim3((unsigned)((q - j0) * team));
+      DPG_CUDA(cudaLaunchKernelEx(&cfg, k_patch_invert<C, true>, (const int64_t*)D.ptr, (const int32_t*)D.dofs,
+                                  (const int64_t*)D.val_ptr, vals, scratch, (const int64_t*)soff,
+                                  (const int64_t*)dorder, j0, offU, dinfo));
+      count_launch();
+    }
   }
   A.release(dorder);
   A.release(soff);
   A.release(scratch);
 }
 
-static void setup_patches(SystemImpl& S, Level& F, const std::vector<char>& smask, int H, const int nco[3],
-                          int* dinfo, cudaStream_t st, bool mixed) {
+static void setup_patches(SystemImpl& S, Level& F, const LevelPlan& lp, int* dinfo, cudaStream_t st) {
   Alloc& A = S.mem;
-  Patches P = build_patches(F.mesh, smask, H, nco);
+  const Patches& P = lp.P;
   PatchDev& D = F.P;
   D.np = (int64_t)P.ptr.size() - 1;
   D.nslots = (int64_t)P.dofs.size();
   D.nvals = P.val_ptr.back();
-  D.max_n = 0;
-  D.sum_sq = 0;
-  for (int64_t j = 0; j < D.np; ++j) {
-    const int64_t nj = P.ptr[j + 1] - P.ptr[j];
-    D.max_n = std::max(D.max_n, nj);
-    D.sum_sq += nj * nj;
-  }
+  D.max_n = lp.max_n;
+  D.sum_sq = lp.sum_sq;
   D.ptr = upload(A, P.ptr, st);
   D.dofs = upload(A, P.dofs, st);
   D.val_ptr = upload(A, P.val_ptr, st);
   D.slot_ptr = upload(A, P.slot_ptr, st);
   D.slots = upload(A, P.slots, st);
-  for (int width : {32, 64}) {
-    std::vector<int2> ch;
-    for (int64_t j = 0; j < D.np; ++j)
-      for (int64_t a0 = 0; a0 < P.ptr[j + 1] - P.ptr[j]; a0 += width) ch.push_back(make_int2((int)j, (int)a0));
-    // largest patches first: the short work items of small patches end the launch
-    std::stable_sort(ch.begin(), ch.end(), [&](const int2& u, const int2& v) {
-      return P.ptr[u.x + 1] - P.ptr[u.x] > P.ptr[v.x + 1] - P.ptr[v.x];
-    });
-    (width == 32 ? D.nchunks : D.nchunks64) = (int64_t)ch.size();
-    (width == 32 ? D.chunks : D.chunks64) = upload(A, ch, st);
-  }
+  D.nchunks = (int64_t)lp.ch32.size();
+  D.chunks = upload(A, lp.ch32, st);
+  D.nchunks64 = (int64_t)lp.ch64.size();
+  D.chunks64 = upload(A, lp.ch64, st);
   D.inv64 = A.arr<double2>((size_t)D.nvals);
   k_patch_gather<<<(unsigned)D.np, 256, 0, st>>>(F.A, D.ptr, D.dofs, D.val_ptr, D.inv64, 0);
   DPG_CHECK_LAUNCH();
   // Patch inverses are computed in FP64 on both paths; the mixed path rounds
   // them to complex64 after theta is estimated (a complex64 factorisation of
   // blocks with condition numbers up to ~5e4 perturbs the smoother by ~1e-3).
-  invert_patches<double2>(A, D, P, D.inv64, F.mesh.offU, dinfo, st);
-  (void)mixed;
+  invert_patches<double2>(A, D, lp, D.inv64, F.mesh.offU, dinfo, st);
+}
+
+// Host index plan of a hierarchy (every level's integer structures); runs on
+// a host thread concurrently with the element stage.
+std::shared_ptr<HostPlan> plan_host(const SystemImpl& S) {
+  auto HP = std::make_shared<HostPlan>();
+  const int L = (int)S.levels.size() - 1;
+  HP->fdofs = elem_dof_table(S.levels[L].mesh);
+  HP->lv.resize(L + 1);
+  for (int l = L; l >= 1; --l) {
+    const Level& F = S.levels[l];
+    const Level& C = S.levels[l - 1];
+    LevelPlan& lp = HP->lv[l];
+    lp.cdofs = elem_dof_table(C.mesh);
+    if (F.kind == 1) {
+      p_selection(F.mesh.p, lp.sel);
+      p_injection(F.mesh, C.mesh, lp.inj);
+      lp.E = prep_ecsr(F.mesh, element_groups(F.mesh));
+      lp.smask.assign(F.mesh.ndof, 1);
+      lp.H = 2;
+    } else {
+      lp.M = build_macro(F.mesh, C.mesh);
+      lp.E = prep_ecsr(F.mesh, lp.M.groups);
+      lp.smask.assign(lp.M.smask.begin(), lp.M.smask.end());
+      lp.H = 4;
+    }
+    lp.P = build_patches(F.mesh, lp.smask, lp.H, C.mesh.n);
+    const Patches& P = lp.P;
+    const int64_t np = (int64_t)P.ptr.size() - 1;
+    auto size_of = [&](int64_t j) { return P.ptr[j + 1] - P.ptr[j]; };
+    for (int64_t j = 0; j < np; ++j) {
+      lp.max_n = std::max(lp.max_n, size_of(j));
+      lp.sum_sq += size_of(j) * size_of(j);
+    }
+    // largest patches first: the short work items of small patches end a launch
+    for (int width : {32, 64}) {
+      std::vector<int2>& ch = width == 32 ? lp.ch32 : lp.ch64;
+      for (int64_t j = 0; j < np; ++j)
+        for (int64_t a0 = 0; a0 < size_of(j); a0 += width) ch.push_back(make_int2((int)j, (int)a0));
+      std::stable_sort(ch.begin(), ch.end(), [&](const int2& u, const int2& v) { return size_of(u.x) > size_of(v.x); });
+    }
+    lp.order.resize(np);
+    for (int64_t j = 0; j < np; ++j) lp.order[j] = j;
+    std::stable_sort(lp.order.begin(), lp.order.end(), [&](int64_t u, int64_t v) { return size_of(u) > size_of(v); });
+  }
+  if (L == 0 || S.levels[L].kind != 1) {
+    HP->has_acg = true;
+    HP->acg = prep_ecsr(S.levels[L].mesh, element_groups(S.levels[L].mesh));
+  }
+  return HP;
 }
 
 // The side stream paired with a setup stream (one per device and stream, kept
@@ -468,9 +590,11 @@ void build_hierarchy(SystemImpl& S, cudaStream_t st) {
       try {
         DPG_CUDA(cudaSetDevice(dev));
         DPG_CUDA(cudaStreamWaitEvent(S.aux, ready, 0));
+        if (S.ph_ev) DPG_CUDA(cudaEventRecord(S.ph_ev[5], S.aux));
         cinfo = S.mem_aux.arr<int>(1);
         DPG_CUDA(cudaMemsetAsync(cinfo, 0, sizeof(int), S.aux));
         coarse_setup(S, S.levels[0], cinfo, S.aux, S.mem_aux);
+        if (S.ph_ev) DPG_CUDA(cudaEventRecord(S.ph_ev[6], S.aux));
         DPG_CUDA(cudaStreamSynchronize(S.aux));
       } catch (...) {
         side_err = std::current_exception();
@@ -478,35 +602,29 @@ void build_hierarchy(SystemImpl& S, cudaStream_t st) {
       cudaEventDestroy(ready);
     });
   };
-  S.levels[L].dofs = upload_dofs(A, S.levels[L].mesh, st);
+  // host index plan, built on a host thread while the element stage ran
+  if (!S.plan) S.plan = S.host_plan.valid() ? S.host_plan.get() : plan_host(S);
+  const HostPlan& HP = *S.plan;
+  S.levels[L].dofs = upload(A, HP.fdofs, st);
   // Pass 1: every level's operator (restriction chain) and transfer data, down
   // to level 0; pass 2: smoothers and damping.  The coarsest factorisation
   // starts between the two and overlaps all of pass 2.
-  std::vector<std::vector<char>> smasks(L + 1);
-  std::vector<int> Hs(L + 1, 2);
   for (int l = L; l >= 1; --l) {
     Level& F = S.levels[l];
     Level& C = S.levels[l - 1];
-    C.dofs = upload_dofs(A, C.mesh, st);
+    const LevelPlan& lp = HP.lv[l];
+    C.dofs = upload(A, lp.cdofs, st);
     C.nloc = (int)C.mesh.loc.size();
     C.E = A.arr<double2>((size_t)C.mesh.nelem * C.nloc * C.nloc);
-    std::vector<char>& smask = smasks[l];
-    int& H = Hs[l];
     if (F.kind == 1) {
-      std::vector<int32_t> sel, inj;
-      p_selection(F.mesh.p, sel);
-      p_injection(F.mesh, C.mesh, inj);
-      F.inj = upload(A, inj, st);
-      int32_t* dsel = upload(A, sel, st);
+      F.inj = upload(A, lp.inj, st);
+      int32_t* dsel = upload(A, lp.sel, st);
       k_p_restrict<<<(unsigned)C.mesh.nelem, 256, 0, st>>>(F.E, C.E, dsel, F.nloc, C.nloc);
       DPG_CHECK_LAUNCH();
-      ECSRHost H_ = build_ecsr(F.mesh, element_groups(F.mesh));
-      assemble_ecsr(A, F.mesh, H_, F.A, st);
+      assemble_ecsr(A, lp.E, F.A, st);
       ecsr_add_elements(F.A, F.E, F.dofs, F.mesh.nelem, F.nloc, st);
-      smask.assign(F.mesh.ndof, 1);
-      H = 2;
     } else {
-      MacroHost M = build_macro(F.mesh, C.mesh);
+      const MacroHost& M = lp.M;
       F.nS = M.nS;
       F.nI = M.nI;
       F.nK = C.mesh.nelem;
@@ -527,8 +645,7 @@ void build_hierarchy(SystemImpl& S, cudaStream_t st) {
       double2* dIK = upload(A, ik, st);
       F.Y64 = A.arr<double2>((size_t)F.nK * F.nI * F.nS);
       F.Ai64 = A.arr<double2>((size_t)F.nK * F.nI * F.nI);
-      ECSRHost H_ = build_ecsr(F.mesh, M.groups);
-      assemble_ecsr(A, F.mesh, H_, F.A, st);
+      assemble_ecsr(A, lp.E, F.A, st);
       const int n = F.nS + F.nI;
       int64_t chunk = std::min<int64_t>(F.nK, 2048);
       double2* AK = A.arr<double2>((size_t)chunk * n * n);
@@ -550,12 +667,9 @@ void build_hierarchy(SystemImpl& S, cudaStream_t st) {
         DPG_CHECK_LAUNCH();
         ecsr_add_elements(F.A, MK, F.S_glob + K0 * F.nS, nb, F.nS, st);
       }
-      DPG_CUDA(cudaStreamSynchronize(st));
-      A.release(AK);
+      A.release(AK);   // stream-ordered frees: after the launches above
       A.release(T1);
       A.release(MK);
-      smask.assign(M.smask.begin(), M.smask.end());
-      H = 4;
     }
     if (S.op.flags & DPGMG_FLAG_STORE_COARSE) {
       // "stored" coarse operator (Sec. 3): the DPG system assembled directly on
@@ -565,15 +679,17 @@ void build_hierarchy(SystemImpl& S, cudaStream_t st) {
       element_stage_level(S, C, st);
     }
   }
+  if (S.ph_ev) DPG_CUDA(cudaEventRecord(S.ph_ev[2], st));
   if (L >= 1 && dense) start_coarse();
+  // theta's Rayleigh quotient stays on the device until the end of the build
+  double* dtheta = A.arr<double>((size_t)2 * (L + 1));
   for (int l = L; l >= 1; --l) {
     Level& F = S.levels[l];
-    Level& C = S.levels[l - 1];
-    const std::vector<char>& smask = smasks[l];
+    const LevelPlan& lp = HP.lv[l];
     F.n_smooth = 0;
-    for (char c : smask) F.n_smooth += c;
-    setup_patches(S, F, smask, Hs[l], C.mesh.n, dinfo, st, mixed);
-    estimate_theta(S, l, st);
+    for (char c : lp.smask) F.n_smooth += c;
+    setup_patches(S, F, lp, dinfo, st);
+    estimate_theta(S, l, dtheta + 2 * l, st);
     if (mixed) {
       F.A.v32 = to_c64(A, F.A.v64, F.A.nnz, st);
       PatchDev& Pd = F.P;
@@ -595,8 +711,7 @@ void build_hierarchy(SystemImpl& S, cudaStream_t st) {
       } else {
         Pd.inv32 = to_c64(A, Pd.inv64, Pd.nvals, st);
       }
-      DPG_CUDA(cudaStreamSynchronize(st));
-      A.release(Pd.inv64);      // the mixed V-cycle only reads the complex64 copy
+      A.release(Pd.inv64);      // the mixed V-cycle only reads the complex64 copy (stream-ordered free)
       Pd.inv64 = nullptr;
       if (F.kind == 2) {
         F.Y32 = to_c64(A, F.Y64, F.nK * F.nI * F.nS, st);
@@ -605,20 +720,28 @@ void build_hierarchy(SystemImpl& S, cudaStream_t st) {
     }
   }
   // coarsest
+  if (S.ph_ev) DPG_CUDA(cudaEventRecord(S.ph_ev[3], st));
   Level& C0 = S.levels[0];
   if (L == 0) C0.dofs = S.levels[0].dofs;
   int info = 0;
   if (side.t.joinable()) {
     side.t.join();
     if (side_err) std::rethrow_exception(side_err);
+    S.ph_side = true;
     DPG_CUDA(cudaMemcpyAsync(&info, cinfo, sizeof(int), cudaMemcpyDeviceToHost, S.aux));
     DPG_CUDA(cudaStreamSynchronize(S.aux));
   } else if (dense) {
     coarse_setup(S, C0, dinfo, st, A);
   }
+  if (S.ph_ev) DPG_CUDA(cudaEventRecord(S.ph_ev[4], st));
   int info_main = 0;
+  std::vector<double> th((size_t)2 * (L + 1));
   DPG_CUDA(cudaMemcpyAsync(&info_main, dinfo, sizeof(int), cudaMemcpyDeviceToHost, st));
+  DPG_CUDA(cudaMemcpyAsync(th.data(), dtheta, th.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
   DPG_CUDA(cudaStreamSynchronize(st));
+  A.release(dtheta);
+  for (int l = 1; l <= L; ++l)
+    if (!(S.op.theta > 0.0)) S.levels[l].theta = theta_from_rayleigh(th[2 * l], th[2 * l + 1]);
   info |= info_main;
   if (info & 32) throw Err{DPGMG_ERR_TIMEOUT, "tensor-core update: a bounded wait for the MMAs ran out"};
   if (info) throw Err{DPGMG_ERR_NOT_HPD, "a macro, patch or coarsest factorisation lost positive definiteness"};

@@ -909,18 +909,13 @@ static const ECSRDev& cg_operator(SystemImpl& S, WS& W, cudaStream_t st) {
     return F.A;
   }
   if (!W.acg_owned) {
-    // finest operator assembled separately (single level, or h-transition below the finest)
-    std::vector<std::vector<int64_t>> g(F.mesh.nelem);
-    std::vector<int64_t> ent(F.mesh.loc.size());
-    for (int64_t e = 0; e < F.mesh.nelem; ++e) {
-      F.mesh.elem_entities(e, ent.data());
-      for (int64_t E : ent)
-        if (E >= 0) g[e].push_back(E);
-      std::sort(g[e].begin(), g[e].end());
-      g[e].erase(std::unique(g[e].begin(), g[e].end()), g[e].end());
+    // finest operator assembled separately (single level, or h-transition below the finest);
+    // its index lists come from the setup's host plan when it is still held
+    if (S.plan && S.plan->has_acg) {
+      assemble_ecsr(S.mem, S.plan->acg, W.Acg, st);
+    } else {
+      assemble_ecsr(S.mem, prep_ecsr(F.mesh, element_groups(F.mesh)), W.Acg, st);
     }
-    ECSRHost H = build_ecsr(F.mesh, g);
-    assemble_ecsr(S.mem, F.mesh, H, W.Acg, st);
     ecsr_add_elements(W.Acg, F.E, F.dofs, F.mesh.nelem, F.nloc, st);
     split_operator(S.mem, W.Acg, st);
     DPG_CUDA(cudaStreamSynchronize(st));
@@ -1304,9 +1299,15 @@ static void dot_t(WS& W, const C* u, const C* v, int64_t n, int which, cudaStrea
   DPG_CHECK_LAUNCH();
 }
 
-// theta = 1 / (1.05 lambda) with the smoother and operator of the V-cycle precision C.
+__global__ void k_take_re(const double2* sc, int idx, double* out) { *out = sc[idx].x; }
+
+double theta_from_rayleigh(double num, double den) { return 1.0 / (1.05 * (num / den)); }
+
+// lambda = (M x)^H (S M x) / (x^H M x) after 30 power iterations of S M, with the
+// smoother and operator of the V-cycle precision C; out[0] = numerator,
+// out[1] = denominator (device), theta = 1 / (1.05 lambda).
 template <class C>
-static double estimate_theta_t(SystemImpl& S, Level& F, cudaStream_t st) {
+static void estimate_theta_t(SystemImpl& S, Level& F, double* out, cudaStream_t st) {
   const int64_t n = F.mesh.ndof;
   Alloc tmp;
   tmp.budget = (size_t)-1;
@@ -1334,21 +1335,17 @@ static double estimate_theta_t(SystemImpl& S, Level& F, cudaStream_t st) {
   }
   spmv<C>(F.A, Av, x, nullptr, t, 0, st);   // M x
   smooth<C>(F, t, y, 1.0, 0, pbuf, st);     // S M x
-  double2 h[SC_COUNT];
   dot_t<C>(W, t, y, n, 3, st);               // (M x)^H (S M x)
-  DPG_CUDA(cudaMemcpyAsync(h, W.sc, sizeof(h), cudaMemcpyDeviceToHost, st));
-  DPG_CUDA(cudaStreamSynchronize(st));
-  const double num = h[SC_RHO].x;
+  k_take_re<<<1, 1, 0, st>>>(W.sc, SC_RHO, out);
+  DPG_CHECK_LAUNCH();
   dot_t<C>(W, x, t, n, 3, st);               // x^H M x
-  DPG_CUDA(cudaMemcpyAsync(h, W.sc, sizeof(h), cudaMemcpyDeviceToHost, st));
-  DPG_CUDA(cudaStreamSynchronize(st));
-  const double den = h[SC_RHO].x;
+  k_take_re<<<1, 1, 0, st>>>(W.sc, SC_RHO, out + 1);
+  DPG_CHECK_LAUNCH();
   W.part = nullptr;
   W.sc = nullptr;
-  return 1.0 / (1.05 * (num / den));
 }
 
-void estimate_theta(SystemImpl& S, int l, cudaStream_t st) {
+void estimate_theta(SystemImpl& S, int l, double* rayleigh, cudaStream_t st) {
   Level& F = S.levels[l];
   configure_smoother_kernels();
   if (S.op.theta > 0.0) {
@@ -1356,7 +1353,7 @@ void estimate_theta(SystemImpl& S, int l, cudaStream_t st) {
     return;
   }
   // FP64 on both paths (the mixed path's complex64 operators are made after)
-  F.theta = estimate_theta_t<double2>(S, F, st);
+  estimate_theta_t<double2>(S, F, rayleigh, st);
 }
 
 // ------------------------------------------------------------ introspection

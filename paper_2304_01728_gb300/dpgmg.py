@@ -66,7 +66,7 @@ EXPORTS = ["dpgmg_create", "dpgmg_destroy", "dpgmg_query_sizes", "dpgmg_default_
            "dpgmg_solve", "dpgmg_release", "dpgmg_strerror", "dpgmg_last_error", "dpgmg_level_info",
            "dpgmg_element_matrix", "dpgmg_rhs", "dpgmg_apply", "dpgmg_launch_count", "dpgmg_profile",
            "dpgmg_profile_read", "dpgmg_smooth_noalloc", "dpgmg_serve_start", "dpgmg_submit", "dpgmg_poll",
-           "dpgmg_spmv_group", "dpgmg_setup_profile", "dpgmg_error_indicator"]
+           "dpgmg_spmv_group", "dpgmg_setup_profile", "dpgmg_error_indicator", "dpgmg_setup_phases"]
 PROF_OFF, PROF_SMOOTH_FINE, PROF_SPMV_FINE, PROF_SPMV_CG = 0, 1, 2, 3
 
 
@@ -114,6 +114,8 @@ def lib():
     L.dpgmg_spmv_group.restype = i
     L.dpgmg_setup_profile.argtypes = [vp, vp, ctypes.POINTER(d), ctypes.POINTER(d), ctypes.POINTER(d)]
     L.dpgmg_setup_profile.restype = i
+    L.dpgmg_setup_phases.argtypes = [vp, vp, ctypes.POINTER(d), i]
+    L.dpgmg_setup_phases.restype = i
     L.dpgmg_error_indicator.argtypes = [vp, vp, dptr, dptr]
     L.dpgmg_error_indicator.restype = i
     L.dpgmg_profile_read.argtypes = [vp, vp, ctypes.POINTER(d), ctypes.POINTER(ll), ctypes.POINTER(ll)]
@@ -270,6 +272,17 @@ def dpgmg_error_indicator(h, s, x, nelem):
     _check(lib().dpgmg_error_indicator(h, s, _dptr(x), eta2.ctypes.data_as(ctypes.POINTER(ctypes.c_double))),
            "dpgmg_error_indicator")
     return eta2
+
+
+SETUP_PHASES = ("element stage", "operators", "smoothers", "coarsest (side stream)", "coarsest wait",
+                "solve preparation")
+
+
+def dpgmg_setup_phases(h, s):
+    """Device ms of each setup phase, in the order of SETUP_PHASES."""
+    out = (ctypes.c_double * len(SETUP_PHASES))()
+    _check(lib().dpgmg_setup_phases(h, s, out, len(SETUP_PHASES)), "dpgmg_setup_phases")
+    return list(out)
 
 
 def dpgmg_setup_profile(h, s):

@@ -118,3 +118,14 @@ def test_warm_start():
         code, st = D.dpgmg_solve(s.h, s.s, g, None)
         assert code == D.DPGMG_OK and st.iters == cold
         assert rel(g, x) < 1e-12
+
+
+def test_setup_phases_add_up():
+    pk = dict(n=(6, 6, 6), p=2, omega=8.0, src_center=(0.5, 0.45, 0.55), src_width=0.2)
+    with D.Solver(pk, n_levels=3, p_min=1, precision="mixed") as s:
+        ph = D.dpgmg_setup_phases(s.h, s.s)
+        el_ms, gflop, setup_ms = D.dpgmg_setup_profile(s.h, s.s)
+    assert len(ph) == len(D.SETUP_PHASES) and min(ph) >= 0.0
+    assert ph[0] == pytest.approx(el_ms)
+    assert ph[0] + ph[1] + ph[2] + ph[4] + ph[5] == pytest.approx(setup_ms, rel=1e-3)
+    assert ph[3] > 0.0   # the coarsest factorisation ran on the side stream
