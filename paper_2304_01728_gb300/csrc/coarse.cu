@@ -62,8 +62,10 @@ __global__ void k_dense_panel(C* A, int64_t N, int k0) {
   C* D = reinterpret_cast<C*>(shraw);
   using O = Ops<C>;
   using R = typename O::R;
+  __shared__ R rdiag[CNB];
   const int kb = (int)(N - k0 < CNB ? N - k0 : CNB);
   for (int q = threadIdx.x; q < kb * kb; q += blockDim.x) D[q] = A[(size_t)(k0 + q / kb) * N + k0 + q % kb];
+  if (threadIdx.x < kb) rdiag[threadIdx.x] = R(1) / O::re(A[(size_t)(k0 + threadIdx.x) * N + k0 + threadIdx.x]);
   __syncthreads();
   int64_t i = (int64_t)k0 + kb + blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= N) return;
@@ -72,7 +74,7 @@ __global__ void k_dense_panel(C* A, int64_t N, int k0) {
   for (int j = 0; j < kb; ++j) {
     C v = row[j];
     for (int t = 0; t < j; ++t) v = O::fnmac(x[t], D[j * kb + t], v);
-    x[j] = O::scale(v, R(1) / O::re(D[j * kb + j]));
+    x[j] = O::scale(v, rdiag[j]);
   }
   for (int j = 0; j < kb; ++j) row[j] = x[j];
 }
@@ -103,10 +105,12 @@ __global__ void __launch_bounds__(CTA_THREADS) k_dense_herk(C* A, int64_t N, int
       Pj[r][c] = (jj < N && t0 + c < kb) ? A[jj * N + k0 + t0 + c] : O::zero();
     }
     __syncthreads();
+    // thread (tx, ty) owns rows ty*4 + a and columns tx + 16 b: the 16 lanes of
+    // a half-warp read 16 consecutive rows of Pj (row stride 17: distinct banks)
     for (int c = 0; c < 16; ++c) {
       C av[4], bv[4];
       for (int a = 0; a < 4; ++a) av[a] = Pi[ty * 4 + a][c];
-      for (int b = 0; b < 4; ++b) bv[b] = Pj[tx * 4 + b][c];
+      for (int b = 0; b < 4; ++b) bv[b] = Pj[tx + 16 * b][c];
       for (int a = 0; a < 4; ++a)
         for (int b = 0; b < 4; ++b) acc[a][b] = O::fmac(av[a], bv[b], acc[a][b]);
     }
@@ -114,7 +118,7 @@ __global__ void __launch_bounds__(CTA_THREADS) k_dense_herk(C* A, int64_t N, int
   }
   for (int a = 0; a < 4; ++a)
     for (int b = 0; b < 4; ++b) {
-      int64_t i = i0 + ty * 4 + a, j = j0 + tx * 4 + b;
+      int64_t i = i0 + ty * 4 + a, j = j0 + tx + 16 * b;
       if (i < N && j <= i) {
         C& o = A[i * N + j];
         o = O::sub(o, acc[a][b]);
@@ -234,7 +238,7 @@ __global__ void __launch_bounds__(CTA_THREADS) k_trinv_update(C* X, const C* L, 
     for (int c = 0; c < 16; ++c) {
       C av[4], bv[4];
       for (int a = 0; a < 4; ++a) av[a] = La[ty * 4 + a][c];
-      for (int b = 0; b < 4; ++b) bv[b] = Xb[c][tx * 4 + b];
+      for (int b = 0; b < 4; ++b) bv[b] = Xb[c][tx + 16 * b];   // consecutive columns: distinct banks
       for (int a = 0; a < 4; ++a)
         for (int b = 0; b < 4; ++b) acc[a][b] = O::fma(av[a], bv[b], acc[a][b]);
     }
@@ -242,7 +246,7 @@ __global__ void __launch_bounds__(CTA_THREADS) k_trinv_update(C* X, const C* L, 
   }
   for (int a = 0; a < 4; ++a)
     for (int b = 0; b < 4; ++b) {
-      int64_t i = i0 + ty * 4 + a, j = j0 + tx * 4 + b;
+      int64_t i = i0 + ty * 4 + a, j = j0 + tx + 16 * b;
       if (i < N && j < N) {
         C& o = X[i * N + j];
         o = O::sub(o, acc[a][b]);
