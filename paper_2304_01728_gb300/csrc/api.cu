@@ -148,6 +148,10 @@ size_t estimate_bytes(const dpgmg_problem* pb, const dpgmg_opts* op) {
       const double cap = std::max(std::min(std::min(std::max((double)(1 << 28), one) * 4.0, (double)(2ull << 30)),
                                            nvals * 16.0), one);
       transient = std::max(transient, nvals * (16.0 + x32) + cap + nd * 48.0 + nslots * 16.0);
+      // damping estimate: double-float patch inverses (high parts resident on the mixed
+      // path) and operator split, vectors, slot buffer
+      transient = std::max(transient, nvals * (mixed ? 24.0 : 16.0) + nnz * (mixed ? 8.0 : 16.0) + nd * 64.0 +
+                                          nslots * 16.0);
       if (hlev) {
         resident += nK * (nI * nS + nI * nI) * (16.0 + x32) + nK * (nS + nI) * 8.0 + nK * nS * (16.0 + x32 + 4.0);
         const double nlc = n_trace_local(q);

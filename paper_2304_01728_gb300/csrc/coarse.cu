@@ -47,36 +47,117 @@ __global__ void k_narrow_mat(const double2* a, float2* b, int64_t n) {
 }
 
 // ---------------------------------------------------------------- Cholesky
+// One CTA per step: Cholesky of the diagonal block A[k0:k0+kb, k0:k0+kb]
+// (written back, lower triangle) and its triangular inverse L_kk^-1, stored
+// as a CNB x CNB block (zero outside the kb x kb lower triangle) at
+// Dinv + (k0 / CNB) CNB^2: the panel below is then a plain product with it,
+// and the inverse phase reuses it.
 template <class C>
-__global__ void __launch_bounds__(CTA_THREADS) k_dense_diag(C* A, int64_t N, int k0, int* info) {
+__global__ void __launch_bounds__(CTA_THREADS) k_dense_diag(C* A, int64_t N, int k0, C* Dinv, int* info) {
   extern __shared__ unsigned char shraw[];
-  int kb = (int)(N - k0 < CNB ? N - k0 : CNB);
-  int inf = cta_potrf<C>(A + (size_t)k0 * N + k0, kb, (int)N, reinterpret_cast<C*>(shraw));
-  if (threadIdx.x == 0 && inf) atomicOr(info, 16);
-}
-
-// rows i >= k0 + kb: A[i, k0:k0+kb] <- A[i, k0:k0+kb] L_kk^-H ; one thread per row
-template <class C>
-__global__ void k_dense_panel(C* A, int64_t N, int k0) {
-  extern __shared__ unsigned char shraw[];
-  C* D = reinterpret_cast<C*>(shraw);
   using O = Ops<C>;
   using R = typename O::R;
+  constexpr int LD = CNB + 1;
+  C* D = reinterpret_cast<C*>(shraw);   // [CNB][LD] the block, then L_kk
+  C* X = D + CNB * LD;                  // [CNB][LD] L_kk^-1
   __shared__ R rdiag[CNB];
   const int kb = (int)(N - k0 < CNB ? N - k0 : CNB);
-  for (int q = threadIdx.x; q < kb * kb; q += blockDim.x) D[q] = A[(size_t)(k0 + q / kb) * N + k0 + q % kb];
-  if (threadIdx.x < kb) rdiag[threadIdx.x] = R(1) / O::re(A[(size_t)(k0 + threadIdx.x) * N + k0 + threadIdx.x]);
-  __syncthreads();
-  int64_t i = (int64_t)k0 + kb + blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (i >= N) return;
-  C* row = A + i * N + k0;
-  C x[CNB];
-  for (int j = 0; j < kb; ++j) {
-    C v = row[j];
-    for (int t = 0; t < j; ++t) v = O::fnmac(x[t], D[j * kb + t], v);
-    x[j] = O::scale(v, rdiag[j]);
+  const int tid = threadIdx.x, tx = tid % 16, ty = tid / 16;
+  for (int q = tid; q < kb * kb; q += blockDim.x) {
+    const int i = q / kb, c = q % kb;
+    D[i * LD + c] = c <= i ? A[(size_t)(k0 + i) * N + k0 + c] : O::zero();
   }
-  for (int j = 0; j < kb; ++j) row[j] = x[j];
+  __syncthreads();
+  // right-looking, one barrier per column: step j updates the trailing lower
+  // entries with L[i][j] conj(L[c][j]) (column j scaled on the fly) and writes
+  // the scaled column j - 1, which step j does not read
+  int bad = 0;
+  R sprev = R(1), rsprev = R(1);
+  for (int j = 0; j < kb; ++j) {
+    R d = O::re(D[j * LD + j]);
+    if (!(d > R(0))) {
+      if (!bad) bad = k0 + j + 1;
+      d = R(1);
+    }
+    const R s = sqrt(d), rs = R(1) / s;
+    if (j > 0)
+      for (int i = j - 1 + tid; i < kb; i += blockDim.x)
+        D[i * LD + j - 1] = i == j - 1 ? O::from_re(sprev) : O::scale(D[i * LD + j - 1], rsprev);
+    for (int i = j + 1 + ty; i < kb; i += 16) {
+      const C lij = O::scale(D[i * LD + j], rs);
+      for (int c = j + 1 + tx; c <= i; c += 16) D[i * LD + c] = O::fnmac(lij, O::scale(D[c * LD + j], rs), D[i * LD + c]);
+    }
+    sprev = s;
+    rsprev = rs;
+    __syncthreads();
+  }
+  for (int i = kb - 1 + tid; i < kb; i += blockDim.x) D[i * LD + kb - 1] = O::from_re(sprev);
+  __syncthreads();
+  for (int q = tid; q < kb * kb; q += blockDim.x) {
+    const int i = q / kb, c = q % kb;
+    if (c <= i) A[(size_t)(k0 + i) * N + k0 + c] = D[i * LD + c];
+  }
+  if (tid < kb) rdiag[tid] = R(1) / O::re(D[tid * LD + tid]);
+  __syncthreads();
+  // X = L_kk^-1 row by row: X[r][c] = (delta_rc - sum_{c<=t<r} L[r][t] X[t][c]) / L[r][r];
+  // four lanes per column split the sum
+  const int col = tid / 4, part = tid % 4;
+  for (int r = 0; r < kb; ++r) {
+    C acc = O::zero();
+    if (col <= r && col < kb)
+      for (int t = col + part; t < r; t += 4) acc = O::fma(D[r * LD + t], X[t * LD + col], acc);
+    for (int o = 1; o < 4; o <<= 1) {
+      acc.x += __shfl_xor_sync(0xffffffffu, acc.x, o);
+      acc.y += __shfl_xor_sync(0xffffffffu, acc.y, o);
+    }
+    if (part == 0 && col <= r && col < kb)
+      X[r * LD + col] = O::scale(O::sub(r == col ? O::from_re(R(1)) : O::zero(), acc), rdiag[r]);
+    __syncthreads();
+  }
+  C* Dk = Dinv + (size_t)(k0 / CNB) * CNB * CNB;
+  for (int q = tid; q < CNB * CNB; q += blockDim.x) {
+    const int r = q / CNB, c = q % CNB;
+    Dk[q] = (r < kb && c <= r) ? X[r * LD + c] : O::zero();
+  }
+  if (tid == 0 && bad) atomicOr(info, 16);
+}
+
+// Panel: rows i >= k0 + kb, A[i, k0:k0+kb] <- A[i, k0:k0+kb] L_kk^-H, as the
+// product with the stored inverse (one CTA per 64 rows; thread (tx, ty) owns
+// rows ty*4 + a and columns tx + 16 b).
+template <class C>
+__global__ void __launch_bounds__(CTA_THREADS) k_dense_panel(C* A, int64_t N, int k0, const C* __restrict__ Dinv) {
+  extern __shared__ unsigned char shraw[];
+  using O = Ops<C>;
+  constexpr int LD = CNB + 1;
+  C* Pa = reinterpret_cast<C*>(shraw);   // [CNB][LD] Pa[r][t] = A[i0 + r][k0 + t]
+  C* Bt = Pa + CNB * LD;                 // [CNB][LD] Bt[t][j] = conj(L_kk^-1[j][t])
+  const int kb = (int)(N - k0 < CNB ? N - k0 : CNB);
+  const int64_t i0 = (int64_t)k0 + kb + (int64_t)blockIdx.x * CNB;
+  const C* Dk = Dinv + (size_t)(k0 / CNB) * CNB * CNB;
+  const int tid = threadIdx.x, tx = tid % 16, ty = tid / 16;
+  for (int q = tid; q < CNB * CNB; q += blockDim.x) {
+    const int r = q / CNB, t = q % CNB;
+    Pa[r * LD + t] = (i0 + r < N && t < kb) ? A[(size_t)(i0 + r) * N + k0 + t] : O::zero();
+    Bt[t * LD + r] = O::conj(Dk[q]);
+  }
+  __syncthreads();
+  C acc[4][4];
+  for (int a = 0; a < 4; ++a)
+    for (int b = 0; b < 4; ++b) acc[a][b] = O::zero();
+  for (int t = 0; t < kb; ++t) {
+    C av[4], bv[4];
+    for (int a = 0; a < 4; ++a) av[a] = Pa[(ty * 4 + a) * LD + t];
+    for (int b = 0; b < 4; ++b) bv[b] = Bt[t * LD + tx + 16 * b];
+    for (int a = 0; a < 4; ++a)
+      for (int b = 0; b < 4; ++b) acc[a][b] = O::fma(av[a], bv[b], acc[a][b]);
+  }
+  for (int a = 0; a < 4; ++a)
+    for (int b = 0; b < 4; ++b) {
+      const int64_t i = i0 + ty * 4 + a;
+      const int j = tx + 16 * b;
+      if (i < N && j < kb) A[(size_t)i * N + k0 + j] = acc[a][b];
+    }
 }
 
 // trailing update of one lower 64x64 tile pair: A[i][j] -= sum_t L[i][t] conj(L[j][t])
@@ -146,19 +227,20 @@ bool tc_trinv<float2>(float2* X, const float2* L, int64_t N, int kb, int* info, 
   return true;
 }
 
+// Blocked right-looking Cholesky A = L L^H in place (lower); Dinv receives the
+// inverses of the diagonal blocks of L.
 template <class C>
-static void dense_cholesky(C* A, int64_t N, int* info, bool tensor, cudaStream_t st) {
-  const size_t sm = (size_t)(NB * NB + 2 * TL * NB) * sizeof(C) + 64;
-  const size_t smp = (size_t)CNB * CNB * sizeof(C);
+static void dense_cholesky(C* A, int64_t N, C* Dinv, int* info, bool tensor, cudaStream_t st) {
+  const size_t sm = (size_t)2 * CNB * (CNB + 1) * sizeof(C);
   DPG_CUDA(cudaFuncSetAttribute(k_dense_diag<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-  DPG_CUDA(cudaFuncSetAttribute(k_dense_panel<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smp));
+  DPG_CUDA(cudaFuncSetAttribute(k_dense_panel<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
   for (int64_t k0 = 0; k0 < N; k0 += CNB) {
     int kb = (int)std::min<int64_t>(CNB, N - k0);
-    k_dense_diag<C><<<1, CTA_THREADS, sm, st>>>(A, N, (int)k0, info);
+    k_dense_diag<C><<<1, CTA_THREADS, sm, st>>>(A, N, (int)k0, Dinv, info);
     DPG_CHECK_LAUNCH();
     int64_t rows = N - k0 - kb;
     if (rows <= 0) break;
-    k_dense_panel<C><<<(unsigned)((rows + 127) / 128), 128, smp, st>>>(A, N, (int)k0);
+    k_dense_panel<C><<<(unsigned)((rows + CNB - 1) / CNB), CTA_THREADS, sm, st>>>(A, N, (int)k0, Dinv);
     DPG_CHECK_LAUNCH();
     if (tensor && tc_herk<C>(A, N, (int)k0, kb, info, st)) continue;
     int64_t nt = (rows + CNB - 1) / CNB;
@@ -168,22 +250,6 @@ static void dense_cholesky(C* A, int64_t N, int* info, bool tensor, cudaStream_t
 }
 
 // ---------------------------------------------------------- L^-1 (blocked)
-// Dinv[kb] = L_kk^-1 for every diagonal block.
-template <class C>
-__global__ void __launch_bounds__(CTA_THREADS) k_diag_inverse(const C* L, int64_t N, C* Dinv) {
-  extern __shared__ unsigned char shraw[];
-  const int kb = blockIdx.x;
-  const int64_t k0 = (int64_t)kb * CNB;
-  const int kw = (int)(N - k0 < CNB ? N - k0 : CNB);
-  C* D = Dinv + (size_t)kb * CNB * CNB;
-  for (int q = threadIdx.x; q < CNB * CNB; q += blockDim.x) {
-    int r = q / CNB, c = q % CNB;
-    D[q] = (r == c && r < kw) ? Ops<C>::from_re(1) : Ops<C>::zero();
-  }
-  __syncthreads();
-  cta_trsm_lower<C, C>(L + (size_t)k0 * N + k0, kw, (int)N, D, kw, CNB, reinterpret_cast<char*>(shraw));
-}
-
 // X[kb rows, tile cols] <- Dinv_kb * X[kb rows, tile cols], one CTA per 64-column tile
 template <class C>
 __global__ void __launch_bounds__(CTA_THREADS) k_trinv_scale(C* X, const C* Dinv, int64_t N, int kb) {
@@ -276,13 +342,9 @@ __global__ void k_pack(const C* X, int64_t N, C* Lp, C* Up) {
 template <class C>
 static void coarse_factor(Alloc& A, C* dense, int64_t N, C** Lp, C** Up, int* info, bool tensor, cudaStream_t st) {
   if (tensor) tc_configure();
-  dense_cholesky<C>(dense, N, info, tensor, st);
   const int nb = (int)((N + CNB - 1) / CNB);
   C* Dinv = A.arr<C>((size_t)nb * CNB * CNB);
-  const size_t smd = (size_t)(NB * NB + TL * NB) * sizeof(C) + (size_t)NB * TL * sizeof(C) + 64;
-  DPG_CUDA(cudaFuncSetAttribute(k_diag_inverse<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smd));
-  k_diag_inverse<C><<<nb, CTA_THREADS, smd, st>>>(dense, N, Dinv);
-  DPG_CHECK_LAUNCH();
+  dense_cholesky<C>(dense, N, Dinv, info, tensor, st);
   C* X = A.arr<C>((size_t)N * N);
   k_identity_lower<C><<<1216, 256, 0, st>>>(X, N);
   DPG_CHECK_LAUNCH();

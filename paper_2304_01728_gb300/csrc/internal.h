@@ -259,7 +259,13 @@ void free_workspace(SystemImpl& S);
 void spmv64(const ECSRDev& A, const double2* x, double2* y, cudaStream_t st);
 // enqueues the damping estimate of a level: rayleigh[0..1] (device) receive the
 // numerator and denominator of lambda; theta = theta_from_rayleigh(num, den)
-void estimate_theta(SystemImpl& S, int level, double* rayleigh, cudaStream_t st);
+// (the level's operator must carry its double-float split v32 + vlo, its patch
+// inverses their high parts in P.inv32 and low parts in plo)
+void estimate_theta(SystemImpl& S, int level, double* rayleigh, const float2* plo, cudaStream_t st);
+// double-float split of an operator's values: v32 (kept if already set) + vlo
+void split_operator(Alloc& M, ECSRDev& A, cudaStream_t st);
+// hi + lo = v (complex64 parts of complex128 values)
+void split_df(const double2* v, float2* hi, float2* lo, int64_t n, cudaStream_t st);
 double theta_from_rayleigh(double num, double den);
 void profile_read(SystemImpl& S, double* ms, long long* launches, long long* bytes);
 // api.cu: validation, footprint estimate and the whole setup of one system

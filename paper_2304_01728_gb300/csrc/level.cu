@@ -689,10 +689,34 @@ void build_hierarchy(SystemImpl& S, cudaStream_t st) {
     F.n_smooth = 0;
     for (char c : lp.smask) F.n_smooth += c;
     setup_patches(S, F, lp, dinfo, st);
-    estimate_theta(S, l, dtheta + 2 * l, st);
+    // double-float copies for the damping estimate; the mixed V-cycle keeps the
+    // high parts (its complex64 operator and patch inverses), the CG operator
+    // (finest level of a p-transition) the operator's split
+    PatchDev& Pd = F.P;
+    const bool keep_split = l == L && F.kind == 1;
+    float2* plo = nullptr;
+    if (!(S.op.theta > 0.0)) {
+      Pd.inv32 = A.arr<float2>((size_t)std::max<int64_t>(Pd.nvals, 1));
+      plo = A.arr<float2>((size_t)std::max<int64_t>(Pd.nvals, 1));
+      split_df(Pd.inv64, Pd.inv32, plo, Pd.nvals, st);
+      if (!F.A.vlo) split_operator(A, F.A, st);
+    }
+    estimate_theta(S, l, dtheta + 2 * l, plo, st);
+    if (plo) A.release(plo);
+    if (F.A.vlo && !keep_split) {
+      A.release(F.A.vlo);
+      F.A.vlo = nullptr;
+    }
+    if (!mixed) {
+      if (Pd.inv32) A.release(Pd.inv32);
+      Pd.inv32 = nullptr;
+      if (F.A.v32 && !keep_split) {
+        A.release(F.A.v32);
+        F.A.v32 = nullptr;
+      }
+    }
     if (mixed) {
-      F.A.v32 = to_c64(A, F.A.v64, F.A.nnz, st);
-      PatchDev& Pd = F.P;
+      if (!F.A.v32) F.A.v32 = to_c64(A, F.A.v64, F.A.nnz, st);
       if (kHalfStorageSmoother && Pd.max_n <= HALF_MAX_N) {
         // complex64 Hermitian half storage: lower triangles packed by rows
         std::vector<int64_t> hp(Pd.np + 1, 0), pp(Pd.np + 1);
@@ -708,7 +732,7 @@ void build_hierarchy(SystemImpl& S, cudaStream_t st) {
         k_pack_half<double2, float2><<<(unsigned)Pd.np, 256, 0, st>>>(Pd.ptr, Pd.val_ptr, Pd.hptr, Pd.inv64, Pd.h32);
         DPG_CHECK_LAUNCH();
         Pd.half = true;
-      } else {
+      } else if (!Pd.inv32) {
         Pd.inv32 = to_c64(A, Pd.inv64, Pd.nvals, st);
       }
       A.release(Pd.inv64);      // the mixed V-cycle only reads the complex64 copy (stream-ordered free)

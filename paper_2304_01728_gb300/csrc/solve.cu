@@ -472,6 +472,105 @@ void split_operator(Alloc& M, ECSRDev& A, cudaStream_t st) {
   DPG_CHECK_LAUNCH();
 }
 
+void split_df(const double2* v, float2* hi, float2* lo, int64_t n, cudaStream_t st) {
+  k_split_vals<<<1216, 256, 0, st>>>(v, hi, lo, n);
+  DPG_CHECK_LAUNCH();
+}
+
+// Double-float smoother product for the damping estimate: the patch inverses
+// as complex64 high and low parts (M = Mh + Ml), r in complex128 split into
+// FP32 pairs in shared memory; conj(M[k][a]) r_k with the error-free products
+// and sums of the CG operator.  One column per lane (32-column work items),
+// warp w takes rows k = w + 8 i with two accumulator pairs; the 8 warp
+// partials are combined in a fixed order and written in complex128.
+__global__ void __launch_bounds__(256) k_patch_apply_df(const int64_t* __restrict__ ptr, const int32_t* __restrict__ dofs,
+                                                        const int64_t* __restrict__ vptr, const int2* __restrict__ chunks,
+                                                        const float2* __restrict__ Mh, const float2* __restrict__ Ml,
+                                                        const double2* __restrict__ r, double2* __restrict__ pbuf) {
+  extern __shared__ unsigned char shraw[];
+  float4* rj = reinterpret_cast<float4*>(shraw);   // (re_hi, re_lo, im_hi, im_lo) per patch DOF
+  __shared__ float4 part[8][33];
+  const int2 ch = chunks[blockIdx.x];
+  const int64_t j = ch.x;
+  const int64_t b = ptr[j];
+  const int n = (int)(ptr[j + 1] - b);
+  const int64_t ld = patch_ld(n);
+  for (int q = threadIdx.x; q < n; q += blockDim.x) {
+    const double2 v = r[dofs[b + q]];
+    const float hx = (float)v.x, hy = (float)v.y;
+    rj[q] = make_float4(hx, (float)(v.x - (double)hx), hy, (float)(v.y - (double)hy));
+  }
+  __syncthreads();
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int a = ch.y + lane;
+  float rh0 = 0.f, rl0 = 0.f, ih0 = 0.f, il0 = 0.f, rh1 = 0.f, rl1 = 0.f, ih1 = 0.f, il1 = 0.f;
+  if (a < n) {
+    const float2* H = Mh + vptr[j] + a;
+    const float2* Lo = Ml + vptr[j] + a;
+    int k = w;
+    float p, q;
+    for (; k + 8 < n; k += 16) {
+      const float2 h0 = __ldcs(H + (int64_t)k * ld), l0 = __ldcs(Lo + (int64_t)k * ld);
+      const float2 h1 = __ldcs(H + (int64_t)(k + 8) * ld), l1 = __ldcs(Lo + (int64_t)(k + 8) * ld);
+      const float4 x0 = rj[k], x1 = rj[k + 8];
+      // conj(m) x: re = m.x x.re + m.y x.im, im = m.x x.im - m.y x.re
+      df_mul(h0.x, l0.x, x0.x, x0.y, p, q);
+      df_add(rh0, rl0, p, q);
+      df_mul(h0.y, l0.y, x0.z, x0.w, p, q);
+      df_add(rh0, rl0, p, q);
+      df_mul(h0.x, l0.x, x0.z, x0.w, p, q);
+      df_add(ih0, il0, p, q);
+      df_mul(h0.y, l0.y, x0.x, x0.y, p, q);
+      df_add(ih0, il0, -p, -q);
+      df_mul(h1.x, l1.x, x1.x, x1.y, p, q);
+      df_add(rh1, rl1, p, q);
+      df_mul(h1.y, l1.y, x1.z, x1.w, p, q);
+      df_add(rh1, rl1, p, q);
+      df_mul(h1.x, l1.x, x1.z, x1.w, p, q);
+      df_add(ih1, il1, p, q);
+      df_mul(h1.y, l1.y, x1.x, x1.y, p, q);
+      df_add(ih1, il1, -p, -q);
+    }
+    if (k < n) {
+      const float2 h0 = __ldcs(H + (int64_t)k * ld), l0 = __ldcs(Lo + (int64_t)k * ld);
+      const float4 x0 = rj[k];
+      df_mul(h0.x, l0.x, x0.x, x0.y, p, q);
+      df_add(rh0, rl0, p, q);
+      df_mul(h0.y, l0.y, x0.z, x0.w, p, q);
+      df_add(rh0, rl0, p, q);
+      df_mul(h0.x, l0.x, x0.z, x0.w, p, q);
+      df_add(ih0, il0, p, q);
+      df_mul(h0.y, l0.y, x0.x, x0.y, p, q);
+      df_add(ih0, il0, -p, -q);
+    }
+    df_add(rh0, rl0, rh1, rl1);
+    df_add(ih0, il0, ih1, il1);
+  }
+  part[w][lane] = make_float4(rh0, rl0, ih0, il0);
+  __syncthreads();
+  if (w == 0 && a < n) {
+    float4 s4 = part[0][lane];
+    for (int u = 1; u < 8; ++u) {
+      const float4 o = part[u][lane];
+      df_add(s4.x, s4.y, o.x, o.y);
+      df_add(s4.z, s4.w, o.z, o.w);
+    }
+    pbuf[b + a] = make_double2((double)s4.x + (double)s4.y, (double)s4.z + (double)s4.w);
+  }
+}
+
+// y = sum_j R_j^T A_jj^-1 R_j r with the double-float patch inverses (F.P.inv32 = high parts)
+static void smooth_df(const Level& F, const float2* plo, const double2* r, double2* y, double2* pbuf,
+                      cudaStream_t st) {
+  const PatchDev& P = F.P;
+  const int64_t n = F.mesh.ndof;
+  const size_t sm = (size_t)P.max_n * sizeof(float4) + 16;
+  k_patch_apply_df<<<(unsigned)P.nchunks, 256, sm, st>>>(P.ptr, P.dofs, P.val_ptr, P.chunks, P.inv32, plo, r, pbuf);
+  DPG_CHECK_LAUNCH();
+  k_slot_sum<double2, double2><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(P.slot_ptr, P.slots, pbuf, y, n, 1.0, 0);
+  DPG_CHECK_LAUNCH();
+}
+
 void spmv64(const ECSRDev& A, const double2* x, double2* y, cudaStream_t st) {
   spmv<double2>(A, A.v64, x, nullptr, y, 0, st);
 }
@@ -1303,57 +1402,59 @@ __global__ void k_take_re(const double2* sc, int idx, double* out) { *out = sc[i
 
 double theta_from_rayleigh(double num, double den) { return 1.0 / (1.05 * (num / den)); }
 
-// lambda = (M x)^H (S M x) / (x^H M x) after 30 power iterations of S M, with the
-// smoother and operator of the V-cycle precision C; out[0] = numerator,
-// out[1] = denominator (device), theta = 1 / (1.05 lambda).
-template <class C>
-static void estimate_theta_t(SystemImpl& S, Level& F, double* out, cudaStream_t st) {
+// lambda = (M x)^H (S M x) / (x^H M x) after 30 power iterations of S M, with
+// the operator and the patch inverses in double-float (complex64 high and low
+// parts of the FP64 values: products and sums carry ~48 bits, on the FP32
+// pipe) and FP64 vectors and dot products; out[0] = numerator, out[1] =
+// denominator (device), theta = 1 / (1.05 lambda).
+static void estimate_theta_df(SystemImpl& S, Level& F, const float2* plo, double* out, cudaStream_t st) {
   const int64_t n = F.mesh.ndof;
   Alloc tmp;
   tmp.budget = (size_t)-1;
   tmp.stream = st;
-  C* x = tmp.arr<C>((size_t)n);
-  C* y = tmp.arr<C>((size_t)n);
-  C* t = tmp.arr<C>((size_t)n);
-  C* pbuf = tmp.arr<C>((size_t)std::max<int64_t>(F.P.scratch_entries(), 1));
+  double2* x = tmp.arr<double2>((size_t)n);
+  double2* y = tmp.arr<double2>((size_t)n);
+  double2* t = tmp.arr<double2>((size_t)n);
+  float2* xh = tmp.arr<float2>((size_t)n);
+  float2* xl = tmp.arr<float2>((size_t)n);
+  double2* pbuf = tmp.arr<double2>((size_t)std::max<int64_t>(F.P.scratch_entries(), 1));
   WS W;
   W.part = tmp.arr<double2>(RED_BLOCKS);
   W.sc = tmp.arr<double2>(SC_COUNT);
-  const C* Av = Prec<C>::A(F.A);
-  k_start_vector<C><<<nblk(n), 256, 0, st>>>(x, n, F.P.slot_ptr);
+  k_start_vector<double2><<<nblk(n), 256, 0, st>>>(x, n, F.P.slot_ptr);
   DPG_CHECK_LAUNCH();
-  dot_t<C>(W, x, x, n, 1, st);
-  k_scale<C><<<RED_BLOCKS, 256, 0, st>>>(x, n, W.sc, SC_RR);
+  dot_t<double2>(W, x, x, n, 1, st);
+  k_scale<double2><<<RED_BLOCKS, 256, 0, st>>>(x, n, W.sc, SC_RR);
   DPG_CHECK_LAUNCH();
   for (int k = 0; k < 30; ++k) {
-    spmv<C>(F.A, Av, x, nullptr, t, 0, st);
-    smooth<C>(F, t, y, 1.0, 0, pbuf, st);
-    dot_t<C>(W, y, y, n, 1, st);
-    k_scale<C><<<RED_BLOCKS, 256, 0, st>>>(y, n, W.sc, SC_RR);
+    spmv_df(F.A, x, nullptr, t, 0, xh, xl, st);
+    smooth_df(F, plo, t, y, pbuf, st);
+    dot_t<double2>(W, y, y, n, 1, st);
+    k_scale<double2><<<RED_BLOCKS, 256, 0, st>>>(y, n, W.sc, SC_RR);
     DPG_CHECK_LAUNCH();
     std::swap(x, y);
   }
-  spmv<C>(F.A, Av, x, nullptr, t, 0, st);   // M x
-  smooth<C>(F, t, y, 1.0, 0, pbuf, st);     // S M x
-  dot_t<C>(W, t, y, n, 3, st);               // (M x)^H (S M x)
+  spmv_df(F.A, x, nullptr, t, 0, xh, xl, st);   // M x
+  smooth_df(F, plo, t, y, pbuf, st);            // S M x
+  dot_t<double2>(W, t, y, n, 3, st);            // (M x)^H (S M x)
   k_take_re<<<1, 1, 0, st>>>(W.sc, SC_RHO, out);
   DPG_CHECK_LAUNCH();
-  dot_t<C>(W, x, t, n, 3, st);               // x^H M x
+  dot_t<double2>(W, x, t, n, 3, st);            // x^H M x
   k_take_re<<<1, 1, 0, st>>>(W.sc, SC_RHO, out + 1);
   DPG_CHECK_LAUNCH();
   W.part = nullptr;
   W.sc = nullptr;
 }
 
-void estimate_theta(SystemImpl& S, int l, double* rayleigh, cudaStream_t st) {
+void estimate_theta(SystemImpl& S, int l, double* rayleigh, const float2* plo, cudaStream_t st) {
   Level& F = S.levels[l];
   configure_smoother_kernels();
   if (S.op.theta > 0.0) {
     F.theta = S.op.theta;
     return;
   }
-  // FP64 on both paths (the mixed path's complex64 operators are made after)
-  estimate_theta_t<double2>(S, F, rayleigh, st);
+  // the same double-float estimate on both paths (the operators' FP64 values)
+  estimate_theta_df(S, F, plo, rayleigh, st);
 }
 
 // ------------------------------------------------------------ introspection
