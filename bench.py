@@ -313,6 +313,8 @@ def run_gb300(args, rank, world, local_rank):
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     stats, prof_ms, prof_n, prof_b = [], 0.0, 0, 0
+    # profiler range = the timed steps (ncu --profile-from-start off); no-op otherwise
+    torch.cuda.profiler.start()
     for _ in range(args.steps):
         st, pr = step(D.PROF_SMOOTH_FINE)
         stats.append((st.iters, st.t_pcg_ms, st.t_setup_ms, st.true_relres, st.relres, st.bytes_per_iter))
@@ -321,6 +323,7 @@ def run_gb300(args, rank, world, local_rank):
         prof_b = pr[2]
     e1.record(stream)
     torch.cuda.synchronize()
+    torch.cuda.profiler.stop()
     if dist:
         dist.barrier()
     launches = D.dpgmg_launch_count() - l0
