@@ -392,17 +392,28 @@ void coarse_setup(SystemImpl& S, Level& C0, int* info, cudaStream_t st, Alloc& A
 }
 
 // ------------------------------------------------------------------ apply
-// One warp per row pair (i, N-1-i): every warp reads N+1 entries.
+// One warp per row pair (i, N-1-i): every warp reads N+1 entries.  Four
+// streaming loads per lane per step keep enough bytes in flight; the two
+// accumulators take the entries in the same order as a two-load loop (a0:
+// t, t + 64, ...; a1: t + 32, t + 96, ...), so the result is bitwise that
+// of the plain loop the V-cycle's tolerances were measured with.
 template <class C>
 __device__ __forceinline__ C dot_row(const C* __restrict__ row, const C* __restrict__ v, int64_t len, int lane) {
   using O = Ops<C>;
   C a0 = O::zero(), a1 = O::zero();
   int64_t t = lane;
-  for (; t + 32 < len; t += 64) {
-    a0 = O::fma(row[t], v[t], a0);
-    a1 = O::fma(row[t + 32], v[t + 32], a1);
+  for (; t + 96 < len; t += 128) {
+    const C m0 = __ldcs(row + t), m1 = __ldcs(row + t + 32), m2 = __ldcs(row + t + 64), m3 = __ldcs(row + t + 96);
+    a0 = O::fma(m0, v[t], a0);
+    a1 = O::fma(m1, v[t + 32], a1);
+    a0 = O::fma(m2, v[t + 64], a0);
+    a1 = O::fma(m3, v[t + 96], a1);
   }
-  if (t < len) a0 = O::fma(row[t], v[t], a0);
+  for (; t + 32 < len; t += 64) {
+    a0 = O::fma(__ldcs(row + t), v[t], a0);
+    a1 = O::fma(__ldcs(row + t + 32), v[t + 32], a1);
+  }
+  if (t < len) a0 = O::fma(__ldcs(row + t), v[t], a0);
   return warp_sum_c(O::add(a0, a1));
 }
 
