@@ -29,15 +29,18 @@ template <class C> __device__ __forceinline__ C warp_sum_c(C v) {
   return v;
 }
 
-__global__ void k_dense_scatter(double2* A, int64_t N, const double2* E, const int64_t* dofs, int nloc) {
+// one colour pass (elem_color) of the dense assembly: no two elements of the pass share a DOF
+__global__ void k_dense_scatter(double2* A, int64_t N, const double2* E, const int64_t* dofs, int nloc, int n0,
+                                int n1, int color) {
   const int64_t e = blockIdx.x;
+  if (elem_color(e, n0, n1) != color) return;
   for (int q = threadIdx.x; q < nloc * nloc; q += blockDim.x) {
     int i = q / nloc, j = q % nloc;
     int64_t gi = dofs[e * nloc + i], gj = dofs[e * nloc + j];
     if (gi < 0 || gj < 0) continue;
-    double2 v = E[e * (size_t)nloc * nloc + q];
-    atomicAdd(&A[gi * N + gj].x, v.x);
-    atomicAdd(&A[gi * N + gj].y, v.y);
+    const double2 v = E[e * (size_t)nloc * nloc + q];
+    double2& o = A[gi * N + gj];
+    o = make_double2(o.x + v.x, o.y + v.y);
   }
 }
 
@@ -374,8 +377,11 @@ void coarse_setup(SystemImpl& S, Level& C0, int* info, cudaStream_t st, Alloc& A
   C0.N0 = N;
   double2* dense = A.arr<double2>((size_t)N * N);
   DPG_CUDA(cudaMemsetAsync(dense, 0, (size_t)N * N * sizeof(double2), st));
-  k_dense_scatter<<<(unsigned)C0.mesh.nelem, 256, 0, st>>>(dense, N, C0.E, C0.dofs, C0.nloc);
-  DPG_CHECK_LAUNCH();
+  for (int c = 0; c < 8; ++c) {
+    k_dense_scatter<<<(unsigned)C0.mesh.nelem, 256, 0, st>>>(dense, N, C0.E, C0.dofs, C0.nloc, C0.mesh.n[0],
+                                                             C0.mesh.n[1], c);
+    DPG_CHECK_LAUNCH();
+  }
   if (S.op.precision == DPGMG_PREC_MIXED) {
     float2* d32 = A.arr<float2>((size_t)N * N);
     k_narrow_mat<<<1216, 256, 0, st>>>(dense, d32, N * N);

@@ -76,6 +76,16 @@ template <class V, class S> struct CplxOps {
 template <> struct Ops<double2> : CplxOps<double2, double> {};
 template <> struct Ops<float2> : CplxOps<float2, float> {};
 
+// Element colours of a structured grid: (ex mod 2, ey mod 2, ez mod 2).  Two
+// elements of one colour share no vertex, edge or face, so an assembly pass
+// over one colour has no write conflicts; the 8 passes run in colour order,
+// which fixes the order of every sum (assembly is bitwise reproducible, unlike
+// FP64 atomics).
+__device__ __forceinline__ int elem_color(int64_t e, int n0, int n1) {
+  const int64_t ex = e % n0, ey = (e / n0) % n1, ez = e / ((int64_t)n0 * n1);
+  return (int)((ex & 1) | ((ey & 1) << 1) | ((ez & 1) << 2));
+}
+
 // ------------------------------------------------------- CTA dense kernels
 constexpr int CTA_THREADS = 256;
 constexpr int NB = 32;          // panel width

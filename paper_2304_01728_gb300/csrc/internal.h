@@ -239,8 +239,10 @@ void error_indicator(SystemImpl& S, const double2* x, double* eta2, cudaStream_t
 // level.cu
 void assemble_ecsr(Alloc& A, const EcsrPrep& P, ECSRDev& D, cudaStream_t st);
 std::shared_ptr<HostPlan> plan_host(const SystemImpl& S);
-void ecsr_add_elements(ECSRDev& D, const double2* E, const int64_t* dofs, int64_t nel, int nloc,
-                       cudaStream_t st);
+// adds the element matrices of elements e0 .. e0 + nel - 1 of a grid with extents ext
+// (colour passes: deterministic, no atomics)
+void ecsr_add_elements(ECSRDev& D, const double2* E, const int64_t* dofs, int64_t nel, int nloc, int64_t e0,
+                       const int ext[3], cudaStream_t st);
 void build_hierarchy(SystemImpl& S, cudaStream_t st);
 void assemble_rhs(SystemImpl& S, cudaStream_t st);
 // coarse.cu

@@ -79,8 +79,10 @@ __device__ __forceinline__ int64_t ecsr_find(const ECSRDev& A, int64_t row, int6
   return A.val_ptr[E] + r * (c1 - c0) + (lo - c0);
 }
 
-__global__ void k_ecsr_add(ECSRDev A, const double2* E, const int64_t* dofs, int64_t nel, int nloc) {
+__global__ void k_ecsr_add(ECSRDev A, const double2* E, const int64_t* dofs, int64_t nel, int nloc, int64_t e0,
+                           int n0, int n1, int color) {
   const int64_t e = blockIdx.x;
+  if (elem_color(e0 + e, n0, n1) != color) return;
   const double2* Ee = E + e * (size_t)nloc * nloc;
   const int64_t* g = dofs + e * nloc;
   for (int q = threadIdx.x; q < nloc * nloc; q += blockDim.x) {
@@ -89,16 +91,19 @@ __global__ void k_ecsr_add(ECSRDev A, const double2* E, const int64_t* dofs, int
     if (gi < 0 || gj < 0) continue;
     int64_t pos = ecsr_find(A, gi, gj);
     if (pos < 0) continue;
-    double2 v = Ee[q];
-    atomicAdd(&A.v64[pos].x, v.x);
-    atomicAdd(&A.v64[pos].y, v.y);
+    const double2 v = Ee[q];
+    double2& o = A.v64[pos];
+    o = make_double2(o.x + v.x, o.y + v.y);
   }
 }
 
-void ecsr_add_elements(ECSRDev& D, const double2* E, const int64_t* dofs, int64_t nel, int nloc, cudaStream_t st) {
+void ecsr_add_elements(ECSRDev& D, const double2* E, const int64_t* dofs, int64_t nel, int nloc, int64_t e0,
+                       const int ext[3], cudaStream_t st) {
   if (nel == 0) return;
-  k_ecsr_add<<<(unsigned)nel, 256, 0, st>>>(D, E, dofs, nel, nloc);
-  DPG_CHECK_LAUNCH();
+  for (int c = 0; c < 8; ++c) {
+    k_ecsr_add<<<(unsigned)nel, 256, 0, st>>>(D, E, dofs, nel, nloc, e0, ext[0], ext[1], c);
+    DPG_CHECK_LAUNCH();
+  }
 }
 
 std::vector<std::vector<int64_t>> element_groups(const MeshL& m) {
@@ -339,13 +344,13 @@ static float2* to_c64(Alloc& A, const double2* src, int64_t n, cudaStream_t st) 
 }
 
 // --------------------------------------------------------------- rhs
-__global__ void k_rhs(const double2* Fc, const int64_t* dofs, double2* b, int64_t nel, int nloc) {
+__global__ void k_rhs(const double2* Fc, const int64_t* dofs, double2* b, int64_t nel, int nloc, int n0, int n1,
+                      int color) {
   int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (q >= nel * nloc) return;
+  if (q >= nel * nloc || elem_color(q / nloc, n0, n1) != color) return;
   int64_t g = dofs[q];
   if (g < 0) return;
-  atomicAdd(&b[g].x, Fc[q].x);
-  atomicAdd(&b[g].y, Fc[q].y);
+  b[g] = make_double2(b[g].x + Fc[q].x, b[g].y + Fc[q].y);
 }
 
 void assemble_rhs(SystemImpl& S, cudaStream_t st) {
@@ -353,8 +358,11 @@ void assemble_rhs(SystemImpl& S, cudaStream_t st) {
   S.b = S.mem.arr<double2>((size_t)L.mesh.ndof);
   DPG_CUDA(cudaMemsetAsync(S.b, 0, (size_t)L.mesh.ndof * sizeof(double2), st));
   int64_t n = S.nelem * S.ntr;
-  k_rhs<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(S.Fc, L.dofs, S.b, S.nelem, (int)S.ntr);
-  DPG_CHECK_LAUNCH();
+  for (int c = 0; c < 8; ++c) {   // colour passes (see elem_color)
+    k_rhs<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(S.Fc, L.dofs, S.b, S.nelem, (int)S.ntr, L.mesh.n[0],
+                                                       L.mesh.n[1], c);
+    DPG_CHECK_LAUNCH();
+  }
 }
 
 // Hermitian half storage of the complex64 patch inverses halves the smoother's
@@ -622,7 +630,7 @@ void build_hierarchy(SystemImpl& S, cudaStream_t st) {
       k_p_restrict<<<(unsigned)C.mesh.nelem, 256, 0, st>>>(F.E, C.E, dsel, F.nloc, C.nloc);
       DPG_CHECK_LAUNCH();
       assemble_ecsr(A, lp.E, F.A, st);
-      ecsr_add_elements(F.A, F.E, F.dofs, F.mesh.nelem, F.nloc, st);
+      ecsr_add_elements(F.A, F.E, F.dofs, F.mesh.nelem, F.nloc, 0, F.mesh.n, st);
     } else {
       const MacroHost& M = lp.M;
       F.nS = M.nS;
@@ -665,7 +673,7 @@ void build_hierarchy(SystemImpl& S, cudaStream_t st) {
         int nb = (int)std::min<int64_t>(chunk, F.nK - K0);
         k_macro<<<nb, CTA_THREADS, sm, st>>>(a);
         DPG_CHECK_LAUNCH();
-        ecsr_add_elements(F.A, MK, F.S_glob + K0 * F.nS, nb, F.nS, st);
+        ecsr_add_elements(F.A, MK, F.S_glob + K0 * F.nS, nb, F.nS, K0, C.mesh.n, st);
       }
       A.release(AK);   // stream-ordered frees: after the launches above
       A.release(T1);

@@ -728,31 +728,15 @@ __global__ void k_widen(const float2* a, double2* b, int64_t n) {
 
 constexpr int RED_BLOCKS = 608;
 
-// partial[b] = sum conj(u_i) v_i over the block's share (FP64)
-__global__ void k_dot_partial(const double2* __restrict__ u, const double2* __restrict__ v, int64_t n,
-                              double2* __restrict__ part) {
-  __shared__ double2 sh[8];
-  double2 acc = make_double2(0, 0);
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    acc = Ops<double2>::fmac(v[i], u[i], acc);
-  acc = warp_sum(acc);
-  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = acc;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double2 s = make_double2(0, 0);
-    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) s = Ops<double2>::add(s, sh[k]);
-    part[blockIdx.x] = s;
-  }
-}
-
 // scalar slots of the CG state
 enum { SC_RHO = 0, SC_PQ, SC_ALPHA, SC_BETA, SC_RR, SC_RHONEW, SC_COUNT };
 
 // which: 0 -> PQ then ALPHA = RHO / PQ ; 1 -> RR ; 2 -> RHONEW, BETA, RHO ; 3 -> RHO
-__global__ void k_dot_finish(const double2* part, int nparts, double2* sc, int which) {
+// (one block of 256 threads; the partials are read from L2: other SMs wrote them)
+__device__ void block_finish(const double2* part, int nparts, double2* sc, int which) {
   __shared__ double2 sh[256];
   double2 acc = make_double2(0, 0);
-  for (int k = threadIdx.x; k < nparts; k += blockDim.x) acc = Ops<double2>::add(acc, part[k]);
+  for (int k = threadIdx.x; k < nparts; k += blockDim.x) acc = Ops<double2>::add(acc, __ldcg(part + k));
   sh[threadIdx.x] = acc;
   __syncthreads();
   for (int s = blockDim.x / 2; s > 0; s >>= 1) {
@@ -779,10 +763,49 @@ __global__ void k_dot_finish(const double2* part, int nparts, double2* sc, int w
   }
 }
 
-// x += alpha p ; r -= alpha q ; rr-partials of ||r||^2
-__global__ void k_cg_update(double2* __restrict__ x, double2* __restrict__ r, const double2* __restrict__ p,
-                            const double2* __restrict__ q, const double2* __restrict__ sc, int64_t n,
-                            double2* __restrict__ part) {
+__global__ void k_dot_finish(const double2* part, int nparts, double2* sc, int which) {
+  block_finish(part, nparts, sc, which);
+}
+
+// After thread 0 of every block has written its partial: true in the last
+// block to arrive (ticket = gridDim.x - 1), which then finishes the reduction
+// (block_finish, the same order as k_dot_finish) and resets the ticket for the
+// next reduction.  No block waits for another.
+__device__ __forceinline__ bool last_block(unsigned* ticket) {
+  __shared__ int s_last;
+  if (threadIdx.x == 0) {
+    __threadfence();   // this block's partial is visible before its ticket
+    s_last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (s_last) __threadfence();
+  return s_last;
+}
+
+// sum conj(u_i) v_i over FP64 vectors: block partials, finished by the last block
+__global__ void k_dot_fused(const double2* __restrict__ u, const double2* __restrict__ v, int64_t n,
+                            double2* __restrict__ part, double2* sc, int which, unsigned* ticket) {
+  __shared__ double2 sh[8];
+  double2 acc = make_double2(0, 0);
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    acc = Ops<double2>::fmac(v[i], u[i], acc);
+  acc = warp_sum(acc);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double2 s = make_double2(0, 0);
+    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) s = Ops<double2>::add(s, sh[k]);
+    part[blockIdx.x] = s;
+  }
+  if (!last_block(ticket)) return;
+  block_finish(part, gridDim.x, sc, which);
+  if (threadIdx.x == 0) *ticket = 0u;
+}
+
+// x += alpha p ; r -= alpha q ; ||r||^2 from block partials, finished by the last block (into sc[SC_RR])
+__global__ void k_cg_update_fused(double2* __restrict__ x, double2* __restrict__ r, const double2* __restrict__ p,
+                                  const double2* __restrict__ q, double2* sc, int64_t n, double2* __restrict__ part,
+                                  unsigned* ticket) {
   __shared__ double2 sh[8];
   const double2 al = sc[SC_ALPHA];
   double acc = 0.0;
@@ -804,15 +827,22 @@ __global__ void k_cg_update(double2* __restrict__ x, double2* __restrict__ r, co
     for (int k = 0; k < (int)(blockDim.x >> 5); ++k) s = Ops<double2>::add(s, sh[k]);
     part[blockIdx.x] = s;
   }
+  if (!last_block(ticket)) return;
+  block_finish(part, gridDim.x, sc, 1);
+  if (threadIdx.x == 0) *ticket = 0u;
 }
 
-// p = z + beta p
+// p = z + beta p, and p's double-float split (hi, lo) for the CG operator
 __global__ void k_cg_dir(double2* __restrict__ p, const double2* __restrict__ z, const double2* __restrict__ sc,
-                         int64_t n) {
+                         int64_t n, float2* __restrict__ ph, float2* __restrict__ pl) {
   const double2 be = sc[SC_BETA];
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     double2 pi = p[i], zi = z[i];
-    p[i] = make_double2(zi.x + be.x * pi.x - be.y * pi.y, zi.y + be.x * pi.y + be.y * pi.x);
+    const double2 v = make_double2(zi.x + be.x * pi.x - be.y * pi.y, zi.y + be.x * pi.y + be.y * pi.x);
+    p[i] = v;
+    const float hx = (float)v.x, hy = (float)v.y;
+    ph[i] = make_float2(hx, hy);
+    pl[i] = make_float2((float)(v.x - (double)hx), (float)(v.y - (double)hy));
   }
 }
 
@@ -826,6 +856,7 @@ struct WS {
   std::vector<LevelWS<double2>> w64;
   std::vector<LevelWS<float2>> w32;
   double2 *x = nullptr, *r = nullptr, *p = nullptr, *q = nullptr, *z = nullptr, *part = nullptr, *sc = nullptr;
+  unsigned* ticket = nullptr;              // last-block counter of the fused reductions (0 between them)
   float2 *xh = nullptr, *xl = nullptr;     // double-float split of the CG operand
   double2* sc_host = nullptr;    // pinned scalar read-back (a few bytes per CG step)
   ECSRDev Acg;                   // the CG operator (finest A_L, FP64)
@@ -868,6 +899,8 @@ void ensure_workspace(SystemImpl& S, cudaStream_t st) {
   W->xh = S.mem.arr<float2>((size_t)n);
   W->xl = S.mem.arr<float2>((size_t)n);
   W->sc = S.mem.arr<double2>(SC_COUNT);
+  W->ticket = S.mem.arr<unsigned>(1);
+  DPG_CUDA(cudaMemsetAsync(W->ticket, 0, sizeof(unsigned), st));
   DPG_CUDA(cudaMallocHost(&W->sc_host, SC_COUNT * sizeof(double2)));
   alloc_level_ws<double2>(*W, S);
   if (S.op.precision == DPGMG_PREC_MIXED) alloc_level_ws<float2>(*W, S);
@@ -995,9 +1028,7 @@ static void precondition(SystemImpl& S, WS& W, const double2* r, double2* z, cud
 }
 
 static void dot(WS& W, const double2* u, const double2* v, int64_t n, int which, cudaStream_t st) {
-  k_dot_partial<<<RED_BLOCKS, 256, 0, st>>>(u, v, n, W.part);
-  DPG_CHECK_LAUNCH();
-  k_dot_finish<<<1, 256, 0, st>>>(W.part, RED_BLOCKS, W.sc, which);
+  k_dot_fused<<<RED_BLOCKS, 256, 0, st>>>(u, v, n, W.part, W.sc, which, W.ticket);
   DPG_CHECK_LAUNCH();
 }
 
@@ -1015,7 +1046,7 @@ static const ECSRDev& cg_operator(SystemImpl& S, WS& W, cudaStream_t st) {
     } else {
       assemble_ecsr(S.mem, prep_ecsr(F.mesh, element_groups(F.mesh)), W.Acg, st);
     }
-    ecsr_add_elements(W.Acg, F.E, F.dofs, F.mesh.nelem, F.nloc, st);
+    ecsr_add_elements(W.Acg, F.E, F.dofs, F.mesh.nelem, F.nloc, 0, F.mesh.n, st);
     split_operator(S.mem, W.Acg, st);
     DPG_CUDA(cudaStreamSynchronize(st));
     W.acg_owned = true;
@@ -1269,26 +1300,31 @@ int pcg_solve(SystemImpl& S, cudaStream_t st, double2* xout, dpgmg_stats* stats,
   if (nb > 0.0 && !(x0 && rel <= S.op.tol)) {
     SystemImpl* pcg_prof = S.prof_which == DPGMG_PROF_SPMV_CG ? &S : nullptr;
     // q = A p, alpha = rho / p^H q, x += alpha p, r -= alpha q, ||r||^2, scalars to the host
-    auto tail = [&]() {
-      spmv_df(A, W.p, nullptr, W.q, 0, W.xh, W.xl, st, pcg_prof);
+    // presplit: p's double-float split is already in W.xh / W.xl (written by k_cg_dir)
+    auto tail = [&](bool presplit) {
+      if (presplit) {
+        int pe = prof_begin(pcg_prof, st);
+        spmv_df_g(A, W.xh, W.xl, nullptr, W.q, 0, A.gsel[2], st);
+        prof_end(pcg_prof, pe, st);
+      } else {
+        spmv_df(A, W.p, nullptr, W.q, 0, W.xh, W.xl, st, pcg_prof);
+      }
       dot(W, W.p, W.q, n, 0, st);   // pq = p^H q
-      k_cg_update<<<RED_BLOCKS, 256, 0, st>>>(W.x, W.r, W.p, W.q, W.sc, n, W.part);
-      DPG_CHECK_LAUNCH();
-      k_dot_finish<<<1, 256, 0, st>>>(W.part, RED_BLOCKS, W.sc, 1);
+      k_cg_update_fused<<<RED_BLOCKS, 256, 0, st>>>(W.x, W.r, W.p, W.q, W.sc, n, W.part, W.ticket);
       DPG_CHECK_LAUNCH();
       DPG_CUDA(cudaMemcpyAsync(W.sc_host, W.sc, SC_COUNT * sizeof(double2), cudaMemcpyDeviceToHost, st));
     };
-    // z = B r, rho_new = z^H r, beta = rho_new / rho, p = z + beta p
+    // z = B r, rho_new = z^H r, beta = rho_new / rho, p = z + beta p (and its split)
     auto head = [&]() {
       precondition(S, W, W.r, W.z, st);
       dot(W, W.z, W.r, n, 2, st);
-      k_cg_dir<<<RED_BLOCKS, 256, 0, st>>>(W.p, W.z, W.sc, n);
+      k_cg_dir<<<RED_BLOCKS, 256, 0, st>>>(W.p, W.z, W.sc, n, W.xh, W.xl);
       DPG_CHECK_LAUNCH();
     };
     precondition(S, W, W.r, W.z, st);
     dot(W, W.z, W.r, n, 3, st);   // rho = z^H r
     DPG_CUDA(cudaMemcpyAsync(W.p, W.z, (size_t)n * sizeof(double2), cudaMemcpyDeviceToDevice, st));
-    tail();
+    tail(false);
     PcgGraph G;
     const bool graphs = !(S.op.flags & DPGMG_FLAG_EAGER);
     bool replayed = false;
@@ -1301,12 +1337,12 @@ int pcg_solve(SystemImpl& S, cudaStream_t st, double2* xout, dpgmg_stats* stats,
       rel = std::sqrt(W.sc_host[SC_RR].x) / nb;
       if (!std::isfinite(rel)) { status = DPGMG_ERR_BREAKDOWN; break; }
       if (rel <= S.op.tol || it >= S.op.max_iter) break;
-      if (graphs && G.ready(st, [&]() { head(); tail(); })) {
+      if (graphs && G.ready(st, [&]() { head(); tail(true); })) {
         G.launch(st);
         replayed = true;
       } else {
         head();
-        tail();
+        tail(true);
       }
     }
     if (status == DPGMG_OK && rel > S.op.tol) status = DPGMG_ERR_NOT_CONVERGED;

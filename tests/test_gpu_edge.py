@@ -129,3 +129,16 @@ def test_setup_phases_add_up():
     assert ph[0] == pytest.approx(el_ms)
     assert ph[0] + ph[1] + ph[2] + ph[4] + ph[5] == pytest.approx(setup_ms, rel=1e-3)
     assert ph[3] > 0.0   # the coarsest factorisation ran on the side stream
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_setup_and_solve_are_bitwise_reproducible(precision):
+    # no atomics anywhere on the path (assembly in element-colour passes,
+    # reductions in a fixed order): two systems of one problem agree bitwise
+    pk = dict(n=(5, 4, 6), p=2, omega=7.0, src_center=(0.4, 0.6, 0.5), src_width=0.2,
+              wavespeed=np.linspace(0.7, 1.3, 120))
+    ok = dict(n_levels=3, p_min=1, precision=precision)
+    runs = [_solve(pk, ok) for _ in range(2)]
+    assert runs[0][3] == runs[1][3] == D.DPGMG_OK
+    assert runs[0][2].iters == runs[1][2].iters
+    assert np.array_equal(runs[0][0], runs[1][0]) and np.array_equal(runs[0][1], runs[1][1])
