@@ -34,7 +34,7 @@ __global__ void k_dense_scatter(double2* A, int64_t N, const double2* E, const i
                                 int n1, int color) {
   const int64_t e = blockIdx.x;
   if (elem_color(e, n0, n1) != color) return;
-  for (int q = threadIdx.x; q < nloc * nloc; q += blockDim.x) {
+  for (int q = blockIdx.y * blockDim.x + threadIdx.x; q < nloc * nloc; q += gridDim.y * blockDim.x) {
     int i = q / nloc, j = q % nloc;
     int64_t gi = dofs[e * nloc + i], gj = dofs[e * nloc + j];
     if (gi < 0 || gj < 0) continue;
@@ -378,8 +378,9 @@ void coarse_setup(SystemImpl& S, Level& C0, int* info, cudaStream_t st, Alloc& A
   double2* dense = A.arr<double2>((size_t)N * N);
   DPG_CUDA(cudaMemsetAsync(dense, 0, (size_t)N * N * sizeof(double2), st));
   for (int c = 0; c < 8; ++c) {
-    k_dense_scatter<<<(unsigned)C0.mesh.nelem, 256, 0, st>>>(dense, N, C0.E, C0.dofs, C0.nloc, C0.mesh.n[0],
-                                                             C0.mesh.n[1], c);
+    const unsigned slices = (unsigned)std::max(1, std::min(64, (C0.nloc * C0.nloc + 2047) / 2048));
+    k_dense_scatter<<<dim3((unsigned)C0.mesh.nelem, slices), 256, 0, st>>>(dense, N, C0.E, C0.dofs, C0.nloc,
+                                                                          C0.mesh.n[0], C0.mesh.n[1], c);
     DPG_CHECK_LAUNCH();
   }
   if (S.op.precision == DPGMG_PREC_MIXED) {

@@ -79,13 +79,14 @@ __device__ __forceinline__ int64_t ecsr_find(const ECSRDev& A, int64_t row, int6
   return A.val_ptr[E] + r * (c1 - c0) + (lo - c0);
 }
 
+// block (e, s): slice s of element e's entries (the slices of one element are disjoint)
 __global__ void k_ecsr_add(ECSRDev A, const double2* E, const int64_t* dofs, int64_t nel, int nloc, int64_t e0,
                            int n0, int n1, int color) {
   const int64_t e = blockIdx.x;
   if (elem_color(e0 + e, n0, n1) != color) return;
   const double2* Ee = E + e * (size_t)nloc * nloc;
   const int64_t* g = dofs + e * nloc;
-  for (int q = threadIdx.x; q < nloc * nloc; q += blockDim.x) {
+  for (int q = blockIdx.y * blockDim.x + threadIdx.x; q < nloc * nloc; q += gridDim.y * blockDim.x) {
     int i = q / nloc, j = q % nloc;
     int64_t gi = g[i], gj = g[j];
     if (gi < 0 || gj < 0) continue;
@@ -100,8 +101,10 @@ __global__ void k_ecsr_add(ECSRDev A, const double2* E, const int64_t* dofs, int
 void ecsr_add_elements(ECSRDev& D, const double2* E, const int64_t* dofs, int64_t nel, int nloc, int64_t e0,
                        const int ext[3], cudaStream_t st) {
   if (nel == 0) return;
+  // one colour holds ~nel / 8 elements: slices of ~2048 entries per block keep the passes wide
+  const unsigned slices = (unsigned)std::max<int64_t>(1, std::min<int64_t>(64, ((int64_t)nloc * nloc + 2047) / 2048));
   for (int c = 0; c < 8; ++c) {
-    k_ecsr_add<<<(unsigned)nel, 256, 0, st>>>(D, E, dofs, nel, nloc, e0, ext[0], ext[1], c);
+    k_ecsr_add<<<dim3((unsigned)nel, slices), 256, 0, st>>>(D, E, dofs, nel, nloc, e0, ext[0], ext[1], c);
     DPG_CHECK_LAUNCH();
   }
 }
