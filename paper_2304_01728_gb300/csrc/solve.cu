@@ -782,13 +782,18 @@ __device__ __forceinline__ bool last_block(unsigned* ticket) {
   return s_last;
 }
 
-// sum conj(u_i) v_i over FP64 vectors: block partials, finished by the last block
-__global__ void k_dot_fused(const double2* __restrict__ u, const double2* __restrict__ v, int64_t n,
+__device__ __forceinline__ double2 to_c128(double2 a) { return a; }
+__device__ __forceinline__ double2 to_c128(float2 a) { return make_double2(a.x, a.y); }   // exact
+
+// sum conj(u_i) v_i in FP64 (u complex128, or complex64 widened exactly): block
+// partials, finished by the last block
+template <class TU>
+__global__ void k_dot_fused(const TU* __restrict__ u, const double2* __restrict__ v, int64_t n,
                             double2* __restrict__ part, double2* sc, int which, unsigned* ticket) {
   __shared__ double2 sh[8];
   double2 acc = make_double2(0, 0);
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    acc = Ops<double2>::fmac(v[i], u[i], acc);
+    acc = Ops<double2>::fmac(v[i], to_c128(u[i]), acc);
   acc = warp_sum(acc);
   if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = acc;
   __syncthreads();
@@ -802,10 +807,11 @@ __global__ void k_dot_fused(const double2* __restrict__ u, const double2* __rest
   if (threadIdx.x == 0) *ticket = 0u;
 }
 
-// x += alpha p ; r -= alpha q ; ||r||^2 from block partials, finished by the last block (into sc[SC_RR])
+// x += alpha p ; r -= alpha q ; ||r||^2 from block partials, finished by the last block (into sc[SC_RR]);
+// r32 (may be null): complex64 copy of the new r for the mixed V-cycle
 __global__ void k_cg_update_fused(double2* __restrict__ x, double2* __restrict__ r, const double2* __restrict__ p,
                                   const double2* __restrict__ q, double2* sc, int64_t n, double2* __restrict__ part,
-                                  unsigned* ticket) {
+                                  unsigned* ticket, float2* __restrict__ r32) {
   __shared__ double2 sh[8];
   const double2 al = sc[SC_ALPHA];
   double acc = 0.0;
@@ -817,6 +823,7 @@ __global__ void k_cg_update_fused(double2* __restrict__ x, double2* __restrict__
     ri.y -= al.x * qi.y + al.y * qi.x;
     x[i] = xi;
     r[i] = ri;
+    if (r32) r32[i] = make_float2((float)ri.x, (float)ri.y);
     acc += ri.x * ri.x + ri.y * ri.y;
   }
   double2 a2 = warp_sum(make_double2(acc, 0.0));
@@ -832,12 +839,14 @@ __global__ void k_cg_update_fused(double2* __restrict__ x, double2* __restrict__
   if (threadIdx.x == 0) *ticket = 0u;
 }
 
-// p = z + beta p, and p's double-float split (hi, lo) for the CG operator
-__global__ void k_cg_dir(double2* __restrict__ p, const double2* __restrict__ z, const double2* __restrict__ sc,
+// p = z + beta p, and p's double-float split (hi, lo) for the CG operator (z complex128, or
+// the mixed V-cycle's complex64 output widened exactly)
+template <class TZ>
+__global__ void k_cg_dir(double2* __restrict__ p, const TZ* __restrict__ z, const double2* __restrict__ sc,
                          int64_t n, float2* __restrict__ ph, float2* __restrict__ pl) {
   const double2 be = sc[SC_BETA];
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    double2 pi = p[i], zi = z[i];
+    double2 pi = p[i], zi = to_c128(z[i]);
     const double2 v = make_double2(zi.x + be.x * pi.x - be.y * pi.y, zi.y + be.x * pi.y + be.y * pi.x);
     p[i] = v;
     const float hx = (float)v.x, hy = (float)v.y;
@@ -1012,23 +1021,30 @@ static void vcycle(SystemImpl& S, WS& W, int l, const C* r, C* x, cudaStream_t s
 }
 
 // z = B r on the finest level in the V-cycle precision
-static void precondition(SystemImpl& S, WS& W, const double2* r, double2* z, cudaStream_t st) {
+// Mixed path: narrowed = r's complex64 copy is already in the finest level's
+// V-cycle input (written by the CG update); z = null leaves the result in
+// complex64 (the V-cycle's output buffer) for consumers that widen it on load.
+static void precondition(SystemImpl& S, WS& W, const double2* r, double2* z, cudaStream_t st, bool narrowed = false) {
   const int L = (int)S.levels.size() - 1;
   const int64_t n = S.levels[L].mesh.ndof;
   if (S.op.precision == DPGMG_PREC_MIXED) {
     auto& V = W.w32;
-    k_narrow<<<nblk(n), 256, 0, st>>>(r, V[L].r, n);
-    DPG_CHECK_LAUNCH();
+    if (!narrowed) {
+      k_narrow<<<nblk(n), 256, 0, st>>>(r, V[L].r, n);
+      DPG_CHECK_LAUNCH();
+    }
     vcycle<float2>(S, W, L, V[L].r, V[L].x, st);
-    k_widen<<<nblk(n), 256, 0, st>>>(V[L].x, z, n);
-    DPG_CHECK_LAUNCH();
+    if (z) {
+      k_widen<<<nblk(n), 256, 0, st>>>(V[L].x, z, n);
+      DPG_CHECK_LAUNCH();
+    }
   } else {
     vcycle<double2>(S, W, L, r, z, st);
   }
 }
 
 static void dot(WS& W, const double2* u, const double2* v, int64_t n, int which, cudaStream_t st) {
-  k_dot_fused<<<RED_BLOCKS, 256, 0, st>>>(u, v, n, W.part, W.sc, which, W.ticket);
+  k_dot_fused<double2><<<RED_BLOCKS, 256, 0, st>>>(u, v, n, W.part, W.sc, which, W.ticket);
   DPG_CHECK_LAUNCH();
 }
 
@@ -1300,6 +1316,9 @@ int pcg_solve(SystemImpl& S, cudaStream_t st, double2* xout, dpgmg_stats* stats,
   if (nb > 0.0 && !(x0 && rel <= S.op.tol)) {
     SystemImpl* pcg_prof = S.prof_which == DPGMG_PROF_SPMV_CG ? &S : nullptr;
     // q = A p, alpha = rho / p^H q, x += alpha p, r -= alpha q, ||r||^2, scalars to the host
+    const bool mixed = S.op.precision == DPGMG_PREC_MIXED;
+    const int Lf = (int)S.levels.size() - 1;
+    float2* r32 = mixed ? W.w32[Lf].r : nullptr;
     // presplit: p's double-float split is already in W.xh / W.xl (written by k_cg_dir)
     auto tail = [&](bool presplit) {
       if (presplit) {
@@ -1310,16 +1329,26 @@ int pcg_solve(SystemImpl& S, cudaStream_t st, double2* xout, dpgmg_stats* stats,
         spmv_df(A, W.p, nullptr, W.q, 0, W.xh, W.xl, st, pcg_prof);
       }
       dot(W, W.p, W.q, n, 0, st);   // pq = p^H q
-      k_cg_update_fused<<<RED_BLOCKS, 256, 0, st>>>(W.x, W.r, W.p, W.q, W.sc, n, W.part, W.ticket);
+      k_cg_update_fused<<<RED_BLOCKS, 256, 0, st>>>(W.x, W.r, W.p, W.q, W.sc, n, W.part, W.ticket, r32);
       DPG_CHECK_LAUNCH();
       DPG_CUDA(cudaMemcpyAsync(W.sc_host, W.sc, SC_COUNT * sizeof(double2), cudaMemcpyDeviceToHost, st));
     };
     // z = B r, rho_new = z^H r, beta = rho_new / rho, p = z + beta p (and its split)
     auto head = [&]() {
-      precondition(S, W, W.r, W.z, st);
-      dot(W, W.z, W.r, n, 2, st);
-      k_cg_dir<<<RED_BLOCKS, 256, 0, st>>>(W.p, W.z, W.sc, n, W.xh, W.xl);
-      DPG_CHECK_LAUNCH();
+      if (mixed) {
+        // r's complex64 copy comes from the CG update; z stays in complex64 and is widened on load
+        precondition(S, W, W.r, nullptr, st, true);
+        const float2* z32 = W.w32[Lf].x;
+        k_dot_fused<float2><<<RED_BLOCKS, 256, 0, st>>>(z32, W.r, n, W.part, W.sc, 2, W.ticket);
+        DPG_CHECK_LAUNCH();
+        k_cg_dir<float2><<<RED_BLOCKS, 256, 0, st>>>(W.p, z32, W.sc, n, W.xh, W.xl);
+        DPG_CHECK_LAUNCH();
+      } else {
+        precondition(S, W, W.r, W.z, st);
+        dot(W, W.z, W.r, n, 2, st);
+        k_cg_dir<double2><<<RED_BLOCKS, 256, 0, st>>>(W.p, W.z, W.sc, n, W.xh, W.xl);
+        DPG_CHECK_LAUNCH();
+      }
     };
     precondition(S, W, W.r, W.z, st);
     dot(W, W.z, W.r, n, 3, st);   // rho = z^H r
