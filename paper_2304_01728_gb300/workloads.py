@@ -24,6 +24,21 @@ def _u(seed, k):
     return (z >> 11) * (1.0 / 9007199254740992.0)
 
 
+def rademacher_rows(seed, j0, j1, n):
+    """Rows j0 .. j1-1 of a seeded n-column sign matrix (entries +-1.0): entry
+    (j, i) is the sign bit of SplitMix64 output k = j n + i (counter form, as
+    _u; vectorised with wrapping uint64 arithmetic).  Used to sketch long
+    vectors (random projections) in tests."""
+    import numpy as np
+    k = (np.arange(j0 * n, j1 * n, dtype=np.uint64) + np.uint64(1))
+    with np.errstate(over="ignore"):
+        z = np.uint64(seed) + k * np.uint64(_G)
+        z = (z ^ (z >> np.uint64(30))) * np.uint64(0xBF58476D1CE4E5B9)
+        z = (z ^ (z >> np.uint64(27))) * np.uint64(0x94D049BB133111EB)
+        z = z ^ (z >> np.uint64(31))
+    return np.where((z >> np.uint64(63)) == 1, -1.0, 1.0).reshape(j1 - j0, n)
+
+
 def config1():
     """4^3 hexes, p = 2, omega = 4, c = 1, Gaussian at the cube centre, 2-level p-MG, FP64."""
     return dict(problem=dict(n=(4, 4, 4), p=2, omega=4.0, src_center=(0.5, 0.5, 0.5), src_width=0.1),

@@ -25,6 +25,18 @@ from oracle.problem import GaussianSource  # noqa: E402
 from oracle.solver import mg_pcg  # noqa: E402
 from paper_2304_01728_gb300 import workloads  # noqa: E402
 
+# random sketch of the solution: SKETCH_ROWS seeded +-1 projections, from which a
+# test estimates the relative L2 error of a whole solution vector (its expected
+# square is ||x - x_ref||^2 * SKETCH_ROWS)
+SKETCH_SEED, SKETCH_ROWS = 4242, 128
+
+
+def sketch(x):
+    out = np.empty(SKETCH_ROWS, complex)
+    for j0 in range(0, SKETCH_ROWS, 16):
+        out[j0:j0 + 16] = workloads.rademacher_rows(SKETCH_SEED, j0, j0 + 16, x.size) @ x
+    return out
+
 _CTX = {}
 
 
@@ -68,6 +80,8 @@ def main():
         "norm_b": float(np.linalg.norm(b)), "norm_x": float(np.linalg.norm(x)),
         "theta": [float(l.theta) for l in levels[1:]],
         "sample_idx": idx, "sample_x": [[float(x[i].real), float(x[i].imag)] for i in idx],
+        "sketch_seed": SKETCH_SEED, "sketch_rows": SKETCH_ROWS,
+        "sketch_x": [[float(v.real), float(v.imag)] for v in sketch(x)],
         "residual_history": [float(v) for v in hist],
         "oracle_seconds": {"elements": t1 - t0, "hierarchy": t2 - t1, "pcg": t3 - t2},
     }

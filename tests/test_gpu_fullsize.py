@@ -2,9 +2,14 @@
 
 Reference values come from tests/golden/c2_oracle.json, written by
 tests/golden/make_c2_golden.py from a full oracle run (FP64, same seeds).
-Sampled element matrices are recomputed by the oracle on the spot; the
-solution is compared on 64 sampled trace DOFs; theta per level and the
-iteration count against the oracle's.
+Sampled element matrices are recomputed by the oracle on the spot; theta per
+level and the iteration count against the oracle's.  The solution's relative
+L2 error against the oracle's is estimated from a seeded random sketch (128
++-1 projections of the whole trace vector; E||S e||^2 = 128 ||e||^2, measured
+within 4% of the exact error on both paths) and checked against the parity
+bar; 64 sampled trace DOFs are compared pointwise as a sanity check (the
+mixed path's CG error is uneven across DOFs: 1.9e-8 in L2, 8.9e-8 on the
+sample).
 """
 import json
 import os
@@ -47,9 +52,16 @@ def test_c2_full_size(precision):
     assert code == D.DPGMG_OK
     assert st.relres <= 1e-8 and st.true_relres <= 1e-8
     assert abs(st.iters - GOLD["iters"]) <= max(1, round(0.1 * GOLD["iters"]))
+    sk = np.empty(GOLD["sketch_rows"], complex)
+    for j0 in range(0, GOLD["sketch_rows"], 16):
+        sk[j0:j0 + 16] = workloads.rademacher_rows(GOLD["sketch_seed"], j0, j0 + 16, x.size) @ x
+    skr = np.array([complex(*v) for v in GOLD["sketch_x"]])
+    l2 = np.linalg.norm(sk - skr) / np.sqrt(GOLD["sketch_rows"]) / GOLD["norm_x"]
     idx = np.array(GOLD["sample_idx"])
     xr = np.array([complex(*v) for v in GOLD["sample_x"]])
     err = np.linalg.norm(x[idx] - xr) / np.linalg.norm(xr)
-    print("sampled solution error vs oracle (%s): %.3e, iterations %d" % (precision, err, st.iters))
-    assert err < (1e-9 if precision == "fp64" else 1e-7), err
+    print("solution error vs oracle (%s): relative L2 (sketch) %.3e, 64 sampled DOFs %.3e, iterations %d"
+          % (precision, l2, err, st.iters))
+    assert l2 < (1e-9 if precision == "fp64" else 1e-7), l2
+    assert err < (1e-9 if precision == "fp64" else 5e-7), err
     assert abs(np.linalg.norm(x) - GOLD["norm_x"]) < 1e-7 * GOLD["norm_x"]
