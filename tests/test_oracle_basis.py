@@ -68,3 +68,17 @@ def test_splitmix64_reference_vectors():
     assert [splitmix64(1234567, k) for k in range(5)] == ref
     u = [uniform01(7, k) for k in range(1000)]
     assert 0.0 <= min(u) and max(u) < 1.0 and abs(np.mean(u) - 0.5) < 0.05
+
+
+def test_workload_sign_generator_matches_reference_vectors():
+    # the vectorised sign rows of the shared input module take the sign bit of
+    # the same SplitMix64 outputs (counter k = row * n + column)
+    from paper_2304_01728_gb300.workloads import rademacher_rows
+    with open(os.path.join(GOLDEN, "splitmix64_seed1234567.txt")) as f:
+        ref = [int(l) for l in f if l.strip() and not l.startswith("#")]
+    signs = rademacher_rows(1234567, 0, 1, 5)[0]
+    assert signs.tolist() == [-1.0 if v >> 63 else 1.0 for v in ref]
+    rows = rademacher_rows(99, 2, 4, 1000)
+    assert rows.shape == (2, 1000) and set(np.unique(rows)) == {-1.0, 1.0}
+    assert np.array_equal(rows, rademacher_rows(99, 0, 4, 1000)[2:])
+    assert abs(rows.mean()) < 0.1
