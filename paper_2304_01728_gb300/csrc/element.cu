@@ -17,6 +17,8 @@
 // the complex flops); the unit phases are put back on the outputs:
 // K_c[i][j] = beta_i conj(beta_j) K'_c[i][j], F_c[i] = beta_i F'_c[i].
 #include <algorithm>
+#include <cstdlib>
+#include <map>
 #include <cmath>
 
 #include "common.cuh"
@@ -159,6 +161,40 @@ template <class T> __device__ __forceinline__ T to_path(double2 v, bool rot);
 template <> __device__ __forceinline__ double2 to_path<double2>(double2 v, bool) { return v; }
 template <> __device__ __forceinline__ double to_path<double>(double2 v, bool rot) { return rot ? -v.y : v.x; }
 
+// Volume load l' of one element (Sec. 2: (f, v) + (g, q); v rows scaled by
+// -i in the real form) into out[i * stride], i < nt.  sh2: 4 nq^3 complex.
+template <class T>
+__device__ void build_load(const ElemArgs& a, const double corner[3], double c, double2* sh2, T* out, size_t stride) {
+  const int nq = a.nql, nq3 = nq * nq * nq, nt = a.nt;
+  double2* fv = sh2;                 // [nq3]
+  double2* gv = sh2 + nq3;           // [3][nq3]
+  const double J = a.h[0] * a.h[1] * a.h[2];
+  for (int q = threadIdx.x; q < nq3; q += blockDim.x) {
+    int qa = q % nq, qb = (q / nq) % nq, qc = q / (nq * nq);
+    double x[3] = {corner[0] + a.xq[qa] * a.h[0], corner[1] + a.xq[qb] * a.h[1], corner[2] + a.xq[qc] * a.h[2]};
+    double2 f, g[3];
+    src_volume(a, c, x, f, g);
+    double w = a.wq[qa] * a.wq[qb] * a.wq[qc] * J;
+    fv[q] = make_double2(f.x * w, f.y * w);
+    for (int d = 0; d < 3; ++d) gv[d * nq3 + q] = make_double2(g[d].x * w, g[d].y * w);
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < nt; i += blockDim.x) {
+    int4 t = a.tf[i];
+    double2 acc = make_double2(0, 0);
+    const double2* src = (t.x == 3) ? fv : gv + (size_t)t.x * nq3;
+    for (int q = 0; q < nq3; ++q) {
+      int qa = q % nq, qb = (q / nq) % nq, qc = q / (nq * nq);
+      double bv = a.Lq[t.y * nq + qa] * a.Lq[t.z * nq + qb] * a.Lq[t.w * nq + qc];
+      acc.x += src[q].x * bv;
+      acc.y += src[q].y * bv;
+    }
+    if (t.x != 3) acc = make_double2(acc.y, -acc.x);
+    out[(size_t)i * stride] = to_path<T>(acc, false);
+  }
+  __syncthreads();
+}
+
 // Split path (boundary elements, real source): with the trial phases of the
 // real path, B' = B_r + i B_i where B_i is non-zero only in the p-hat columns
 // (the impedance term <p-hat, Z^-1 q> on boundary faces).  The builder writes
@@ -195,35 +231,10 @@ __global__ void __launch_bounds__(CTA_THREADS) k_elem_build(ElemArgs a) {
     }
   }
   // ---- load l' (v rows scaled by -i)
-  const int nq = a.nql, nq3 = nq * nq * nq;
+  const int nq = a.nql;
   const int n1 = a.tab.n1;
   double2* fv = sh2;                 // [nq3]
-  double2* gv = sh2 + nq3;           // [3][nq3]
-  const double J = a.h[0] * a.h[1] * a.h[2];
-  for (int q = threadIdx.x; q < nq3; q += blockDim.x) {
-    int qa = q % nq, qb = (q / nq) % nq, qc = q / (nq * nq);
-    double x[3] = {corner[0] + a.xq[qa] * a.h[0], corner[1] + a.xq[qb] * a.h[1], corner[2] + a.xq[qc] * a.h[2]};
-    double2 f, g[3];
-    src_volume(a, c, x, f, g);
-    double w = a.wq[qa] * a.wq[qb] * a.wq[qc] * J;
-    fv[q] = make_double2(f.x * w, f.y * w);
-    for (int d = 0; d < 3; ++d) gv[d * nq3 + q] = make_double2(g[d].x * w, g[d].y * w);
-  }
-  __syncthreads();
-  for (int i = threadIdx.x; i < nt; i += blockDim.x) {
-    int4 t = a.tf[i];
-    double2 acc = make_double2(0, 0);
-    const double2* src = (t.x == 3) ? fv : gv + (size_t)t.x * nq3;
-    for (int q = 0; q < nq3; ++q) {
-      int qa = q % nq, qb = (q / nq) % nq, qc = q / (nq * nq);
-      double bv = a.Lq[t.y * nq + qa] * a.Lq[t.z * nq + qb] * a.Lq[t.w * nq + qc];
-      acc.x += src[q].x * bv;
-      acc.y += src[q].y * bv;
-    }
-    if (t.x != 3) acc = make_double2(acc.y, -acc.x);
-    W[(size_t)i * ldw + m] = to_path<T>(acc, false);
-  }
-  __syncthreads();
+  build_load<T>(a, corner, c, sh2, W + m, ldw);
   // boundary faces: <u0, q>
   if (a.src != DPGMG_SRC_GAUSSIAN) {
     for (int d = 0; d < 3; ++d)
@@ -349,6 +360,9 @@ __device__ __forceinline__ double2 phased_c(double2 v, int ph) {
   return ph == 0 ? v : (ph == 1 ? make_double2(-v.y, v.x) : make_double2(v.y, -v.x));
 }
 template <class T, bool PH> __device__ __forceinline__ double2 out_value(T v, int ph) { return phased<T>(v, ph); }
+template <class T> __device__ __forceinline__ T from_c128(double2 v);
+template <> __device__ __forceinline__ double from_c128<double>(double2 v) { return v.x; }
+template <> __device__ __forceinline__ double2 from_c128<double2>(double2 v) { return v; }
 template <> __device__ __forceinline__ double2 out_value<double2, true>(double2 v, int ph) { return phased_c(v, ph); }
 __device__ __forceinline__ int phase_of(bool a_i, bool b_i) { return (a_i && !b_i) ? 1 : ((!a_i && b_i) ? 2 : 0); }
 
@@ -379,6 +393,88 @@ __global__ void __launch_bounds__(CTA_THREADS) k_elem_condense(ElemArgs a) {
     const bool fi = a.ff[i].x == 0;
     const int ph = (j < ntr) ? phase_of(fi, a.tr[j].x == 0) : (fi ? 1 : 0);
     Y[q] = out_value<T, PH>(K[(size_t)i * ld + nf + j], ph);
+  }
+}
+
+// ---- element classes (constant coefficients): G, B and the condensed matrix
+// of an element depend on (h, omega, c) and its impedance faces only, so one
+// representative per class runs the full pipeline and every other member of
+// the class computes only what its load changes.  Member b (element mem_e[b],
+// representative in slot mem_slot[b] of the current batch) uses the
+// representative's scratch: G = L (Gram Cholesky), W = L^-1 [B | l | B_i],
+// and after condensation K = [L_ff | Y ; K_tf | K_c].  Per member scratch
+// (stride doubles): w [nt] (even-padded), F [m] complex, u [nf] complex.
+//
+// Stage 1 (after the representatives' HERK, before the split path overwrites
+// W): w = L^-1 l', F = W_B'^H w (the load column of K; on the split path
+// Re F_a = sum_k W[k][a] w_k, Im F_a = -sum_k W[k][a~] w_k as in
+// k_elem_split_assemble).
+template <bool SPLIT>
+__global__ void __launch_bounds__(CTA_THREADS) k_elem_member_load(ElemArgs a, const int64_t* __restrict__ mem_e,
+                                                                  const int* __restrict__ mem_slot, double* scr,
+                                                                  int64_t stride) {
+  extern __shared__ double2 sh2[];
+  const int64_t b = blockIdx.x;
+  const int64_t e = mem_e[b];
+  const int slot = mem_slot[b];
+  const int nt = a.nt, m = a.m, nf = a.nf;
+  int ec[3], bmask;
+  double corner[3];
+  elem_geom(a, e, ec, corner, bmask);
+  double* w = scr + b * stride;
+  double2* F = reinterpret_cast<double2*>(w + nt + (nt & 1));
+  build_load<double>(a, corner, a.c[e], sh2, w, 1);
+  const double* L = a.G + (size_t)slot * nt * nt;
+  cta_trsm_lower<double, double>(L, nt, nt, w, 1, 1, reinterpret_cast<char*>(sh2));
+  const int ldw = SPLIT ? m + 1 + a.nph : m + 1;
+  const double* W = SPLIT ? reinterpret_cast<const double*>(reinterpret_cast<const double2*>(a.W) + (size_t)slot * nt * (m + 1))
+                          : reinterpret_cast<const double*>(a.W) + (size_t)slot * nt * ldw;
+  for (int j = threadIdx.x; j < m; j += blockDim.x) {
+    const int qj = (SPLIT && j >= nf) ? a.phq[j - nf] : -1;
+    double re = 0.0, im = 0.0;
+    for (int k = 0; k < nt; ++k) {
+      const double wk = w[k];
+      re = fma(W[(size_t)k * ldw + j], wk, re);
+      if (qj >= 0) im = fma(-W[(size_t)k * ldw + m + 1 + qj], wk, im);
+    }
+    F[j] = make_double2(re, im);
+  }
+}
+
+// Stage 2 (after the representatives' condensation): u = K_ff^-1 F_f,
+// F_c = F_t - K_tf u; outputs as k_elem_condense writes them, with the
+// load-independent parts (K_c, the recovery columns of the traces) copied
+// from the representative.
+template <class T, bool PH>
+__global__ void __launch_bounds__(CTA_THREADS) k_elem_member_condense(ElemArgs a, const int64_t* __restrict__ mem_e,
+                                                                      const int* __restrict__ mem_slot, double* scr,
+                                                                      int64_t stride) {
+  extern __shared__ unsigned char shraw[];
+  const int64_t b = blockIdx.x;
+  const int64_t e = mem_e[b];
+  const int slot = mem_slot[b];
+  const int64_t rep = a.elist[a.e0 + slot];
+  const int nt = a.nt, m = a.m, nf = a.nf, ntr = a.ntr, ld = m + 1;
+  const T* K = reinterpret_cast<const T*>(a.K) + (size_t)slot * ld * ld;
+  const double2* F = reinterpret_cast<const double2*>(scr + b * stride + nt + (nt & 1));
+  T* u = reinterpret_cast<T*>(const_cast<double2*>(F) + m);
+  for (int i = threadIdx.x; i < nf; i += blockDim.x) u[i] = from_c128<T>(F[i]);
+  __syncthreads();
+  cta_trsm_lower<T, T>(K, nf, ld, u, 1, 1, reinterpret_cast<char*>(shraw));
+  cta_trsm_lower_h<T>(K, nf, ld, u, 1, 1, reinterpret_cast<char*>(shraw));
+  for (int i = threadIdx.x; i < ntr; i += blockDim.x) {
+    T acc = from_c128<T>(F[nf + i]);
+    for (int j = 0; j < nf; ++j) acc = Ops<T>::fnma(K[(size_t)(nf + i) * ld + j], u[j], acc);
+    a.Fc[e * ntr + i] = out_value<T, PH>(acc, a.tr[i].x == 0 ? 1 : 0);
+  }
+  const double2* Er = a.Eout + rep * (size_t)ntr * ntr;
+  double2* E = a.Eout + e * (size_t)ntr * ntr;
+  for (int q = threadIdx.x; q < ntr * ntr; q += blockDim.x) E[q] = Er[q];
+  const double2* Yr = a.Yrec + rep * (size_t)nf * (ntr + 1);
+  double2* Y = a.Yrec + e * (size_t)nf * (ntr + 1);
+  for (int q = threadIdx.x; q < nf * (ntr + 1); q += blockDim.x) {
+    const int i = q / (ntr + 1), j = q % (ntr + 1);
+    Y[q] = j < ntr ? Yr[q] : out_value<T, PH>(u[i], a.ff[i].x == 0 ? 1 : 0);
   }
 }
 
@@ -615,9 +711,116 @@ static void element_core(SystemImpl& S, Level& L, const std::vector<double>& cva
       DPG_CHECK_LAUNCH();
     }
   };
-  run_list(dreal, (int64_t)lreal.size(), true);
-  run_split(dsplit, (int64_t)lsplit.size());
-  run_list(dcplx, (int64_t)lcplx.size(), false);
+  // Element classes (Gaussian source: real loads, no boundary loads): the key
+  // (impedance-face mask, wavespeed) fixes G, B and the condensed matrix, so
+  // one representative per class runs the full pipeline and the other
+  // members run the two member stages.  Used when the classes are few (at
+  // most nel / 4) and their representatives fit one batch; DPGMG_ELEMENT_REUSE=0
+  // runs every element through the full pipeline.
+  bool reuse = S.pb.source == DPGMG_SRC_GAUSSIAN && lcplx.empty();
+  if (const char* ev = std::getenv("DPGMG_ELEMENT_REUSE")) reuse = reuse && std::atoi(ev) != 0;
+  std::vector<int64_t> rreps, sreps, rmem, smem;   // representatives and members (real / split path)
+  std::vector<int> rslot, sslot;                   // member -> slot of its representative
+  if (reuse) {
+    std::map<std::pair<int, double>, int> cls;
+    for (int64_t e = 0; e < nel; ++e) {
+      int ec[3];
+      m.elem_coord(e, ec);
+      int bm = 0;
+      for (int d = 0; d < 3; ++d) {
+        if (ec[d] == 0) bm |= 1 << (2 * d);
+        if (ec[d] == m.n[d] - 1) bm |= 1 << (2 * d + 1);
+      }
+      const bool interior = bm == 0;
+      std::vector<int64_t>& reps = interior ? rreps : sreps;
+      auto it = cls.find(std::make_pair(bm, cvals[e]));
+      if (it == cls.end()) {
+        cls.emplace(std::make_pair(bm, cvals[e]), (int)reps.size());
+        reps.push_back(e);
+      } else {
+        (interior ? rmem : smem).push_back(e);
+        (interior ? rslot : sslot).push_back(it->second);
+      }
+    }
+    reuse = (int64_t)(rreps.size() + sreps.size()) * 4 <= nel && (int64_t)rreps.size() <= chunk &&
+            (int64_t)sreps.size() <= chunk;
+  }
+  const int64_t mstride = (a.nt + (a.nt & 1)) + 2 * (int64_t)a.m + 2 * (int64_t)a.nf;   // member scratch (doubles)
+  if (reuse) {
+    const size_t sm_mem = std::max(sm_build_max, sm_cplx);
+    DPG_CUDA(cudaFuncSetAttribute(k_elem_member_load<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_mem));
+    DPG_CUDA(cudaFuncSetAttribute(k_elem_member_load<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_mem));
+    DPG_CUDA(cudaFuncSetAttribute(k_elem_member_condense<double, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)sm_cplx));
+    DPG_CUDA(cudaFuncSetAttribute(k_elem_member_condense<double2, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)sm_cplx));
+    double* scr = A.arr<double>((size_t)std::max<int64_t>((int64_t)std::max(rmem.size(), smem.size()), 1) * mstride);
+    if (!rreps.empty()) {
+      int64_t* dl = upload(A, rreps, st);
+      a.elist = dl;
+      a.e0 = 0;
+      const int nb = (int)rreps.size(), nm = (int)rmem.size();
+      int64_t* de = nm ? upload(A, rmem, st) : nullptr;
+      int* ds = nm ? upload(A, rslot, st) : nullptr;
+      k_elem_build<double><<<nb, CTA_THREADS, sm_build, st>>>(a);
+      DPG_CHECK_LAUNCH();
+      k_elem_potrf<<<nb, CTA_THREADS, sm_real, st>>>(a);
+      DPG_CHECK_LAUNCH();
+      k_elem_trsm<double><<<nb, CTA_THREADS, sm_cplx, st>>>(a);
+      DPG_CHECK_LAUNCH();
+      k_elem_herk<double><<<nb, CTA_THREADS, sm_cplx, st>>>(a);
+      DPG_CHECK_LAUNCH();
+      if (nm) {
+        k_elem_member_load<false><<<nm, CTA_THREADS, sm_mem, st>>>(a, de, ds, scr, mstride);
+        DPG_CHECK_LAUNCH();
+      }
+      k_elem_condense<double><<<nb, CTA_THREADS, sm_cplx, st>>>(a);
+      DPG_CHECK_LAUNCH();
+      if (nm) {
+        k_elem_member_condense<double, false><<<nm, CTA_THREADS, sm_cplx, st>>>(a, de, ds, scr, mstride);
+        DPG_CHECK_LAUNCH();
+        A.release(de);
+        A.release(ds);
+      }
+      A.release(dl);
+    }
+    if (!sreps.empty()) {
+      int64_t* dl = upload(A, sreps, st);
+      a.elist = dl;
+      a.e0 = 0;
+      const int nb = (int)sreps.size(), nm = (int)smem.size();
+      int64_t* de = nm ? upload(A, smem, st) : nullptr;
+      int* ds = nm ? upload(A, sslot, st) : nullptr;
+      k_elem_build<double, true><<<nb, CTA_THREADS, sm_build, st>>>(a);
+      DPG_CHECK_LAUNCH();
+      k_elem_potrf<<<nb, CTA_THREADS, sm_real, st>>>(a);
+      DPG_CHECK_LAUNCH();
+      k_elem_trsm_split<<<nb, CTA_THREADS, sm_cplx, st>>>(a);
+      DPG_CHECK_LAUNCH();
+      k_elem_herk_split<<<nb, CTA_THREADS, sm_cplx, st>>>(a);
+      DPG_CHECK_LAUNCH();
+      if (nm) {   // before the assembly below reuses the W slots
+        k_elem_member_load<true><<<nm, CTA_THREADS, sm_mem, st>>>(a, de, ds, scr, mstride);
+        DPG_CHECK_LAUNCH();
+      }
+      k_elem_split_assemble<<<nb, CTA_THREADS, 0, st>>>(a);
+      DPG_CHECK_LAUNCH();
+      k_elem_condense<double2, true><<<nb, CTA_THREADS, sm_cplx, st>>>(a);
+      DPG_CHECK_LAUNCH();
+      if (nm) {
+        k_elem_member_condense<double2, true><<<nm, CTA_THREADS, sm_cplx, st>>>(a, de, ds, scr, mstride);
+        DPG_CHECK_LAUNCH();
+        A.release(de);
+        A.release(ds);
+      }
+      A.release(dl);
+    }
+    A.release(scr);
+  } else {
+    run_list(dreal, (int64_t)lreal.size(), true);
+    run_split(dsplit, (int64_t)lsplit.size());
+    run_list(dcplx, (int64_t)lcplx.size(), false);
+  }
   if (finest) {
     // algorithmic multiply-adds (an FMA is 2 flops, a complex FMA 8): Gram
     // Cholesky nt^3/6, W = L^-1 [B l] nt^2 (m+1)/2, K = W^H W (lower)
@@ -628,9 +831,19 @@ static void element_core(SystemImpl& S, Level& L, const std::vector<double>& cva
     // split path: real TRSM and HERK over m + 1 + nph columns, complex condensation
     const double m2 = (double)ld2, fma_c = nf * nf * nf / 6.0 + nf * nf * t1 + a.ntr * t1 * nf;
     const double fma_s = n * n * m2 / 2.0 + m2 * m2 * n / 2.0;
-    S.elem_flops = (double)lreal.size() * (2.0 * fma_g + 2.0 * fma_w) +
-                   (double)lsplit.size() * (2.0 * fma_g + 2.0 * fma_s + 8.0 * fma_c) +
-                   (double)lcplx.size() * (2.0 * fma_g + 8.0 * fma_w);
+    if (reuse) {
+      // representatives: the full count; members: w = L^-1 l (nt^2/2), F = W^H w, u = K_ff^-1 F_f
+      // (nf^2), F_c = F_t - K_tf u (ntr nf); the split path's F over m + nph real columns
+      const double mem_r = n * n / 2.0 + a.m * n + nf * nf + a.ntr * nf;
+      const double mem_s_real = n * n / 2.0 + (a.m + a.nph) * n, mem_s_cplx = nf * nf + a.ntr * nf;
+      S.elem_flops = (double)rreps.size() * (2.0 * fma_g + 2.0 * fma_w) +
+                     (double)sreps.size() * (2.0 * fma_g + 2.0 * fma_s + 8.0 * fma_c) +
+                     (double)rmem.size() * 2.0 * mem_r + (double)smem.size() * (2.0 * mem_s_real + 8.0 * mem_s_cplx);
+    } else {
+      S.elem_flops = (double)lreal.size() * (2.0 * fma_g + 2.0 * fma_w) +
+                     (double)lsplit.size() * (2.0 * fma_g + 2.0 * fma_s + 8.0 * fma_c) +
+                     (double)lcplx.size() * (2.0 * fma_g + 8.0 * fma_w);
+    }
   }
   int info = 0;
   DPG_CUDA(cudaMemcpyAsync(&info, a.info, sizeof(int), cudaMemcpyDeviceToHost, st));

@@ -142,3 +142,27 @@ def test_setup_and_solve_are_bitwise_reproducible(precision):
     assert runs[0][3] == runs[1][3] == D.DPGMG_OK
     assert runs[0][2].iters == runs[1][2].iters
     assert np.array_equal(runs[0][0], runs[1][0]) and np.array_equal(runs[0][1], runs[1][1])
+
+
+@pytest.mark.parametrize("n,p,prec", [((6, 6, 6), 2, "fp64"), ((8, 7, 6), 3, "mixed")])
+def test_element_class_reuse_matches_full_pipeline(n, p, prec, monkeypatch):
+    # constant wavespeed: 27 element classes (impedance-face masks); members of a
+    # class take the representative's factors and compute only their load
+    pk = dict(n=n, p=p, omega=9.0, src_center=(0.45, 0.55, 0.5), src_width=0.15)
+    ok = dict(n_levels=2, p_min=p - 1, precision=prec)
+    nel = int(np.prod(n))
+    picks = [0, n[0] // 2, (n[1] // 2) * n[0] + n[0] // 2, nel // 2 + n[0] // 2, nel - 1, nel // 3]
+    out = {}
+    for reuse in ("0", "1"):
+        monkeypatch.setenv("DPGMG_ELEMENT_REUSE", reuse)
+        with D.Solver(pk, **ok) as s:
+            ntr = (p + 1) ** 3 - (p - 1) ** 3 + 6 * p * p   # local traces: u-hat (H^1 trace) and p-hat
+            mats = [D.dpgmg_element_matrix(s.h, s.s, ok["n_levels"] - 1, e, ntr, with_load=True) for e in picks]
+            x, f, st, code = s.solve()
+            assert code == D.DPGMG_OK
+            out[reuse] = (mats, x, f, st.iters)
+    (m0, x0, f0, i0), (m1, x1, f1, i1) = out["0"], out["1"]
+    for a, b in zip(m0, m1):
+        assert rel(b[0], a[0]) < 1e-13 and rel(b[1], a[1]) < 1e-11
+    assert i1 == i0
+    assert rel(x1, x0) < 1e-9 and rel(f1, f0) < 1e-9
