@@ -4,7 +4,7 @@ All calls go through the C ABI (libdpgmg.so via the ctypes binding).  The
 FP64 path is compared at 1e-11 relative (roundoff of a different but
 equivalent arithmetic order: the library uses the real form of the Gram
 matrix and closed-form 1D integrals, the oracle complex quadrature); the
-solution at the spec bar of 1e-7 relative L2 with the iteration count
+solution at the parity bar of 1e-7 relative L2 with the iteration count
 within 10% (equal in practice on the FP64 path).
 """
 import numpy as np
