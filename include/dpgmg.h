@@ -300,11 +300,15 @@ int dpgmg_error_indicator(dpgmg_handle h, dpgmg_system sys, const double* x, dou
 
 /* Setup phases of a system: device time of the batched element stage
  * (Sec. 2: Gram, B and load, Cholesky, optimal test functions, DPG matrix,
- * field condensation), its algorithmic GFLOP (an FMA counts 2 flops, a
- * complex FMA 8; Gram Cholesky nt^3/6, W = L^-1 [B l] nt^2 (m+1)/2,
- * K = W^H W (m+1)^2 nt/2, condensation nf^3/6 + nf^2 (ntr+1) + ntr (ntr+1) nf
- * multiply-adds per element), and the whole setup's device time.  Outputs
- * may be NULL.  Returns DPGMG_ERR_ARG for a null handle or system. */
+ * field condensation), the algorithmic GFLOP it executed (an FMA counts 2
+ * flops, a complex FMA 8; per element of the full pipeline: Gram Cholesky
+ * nt^3/6, W = L^-1 [B l] nt^2 (m+1)/2, K = W^H W (m+1)^2 nt/2, condensation
+ * nf^3/6 + nf^2 (ntr+1) + ntr (ntr+1) nf multiply-adds; with element classes
+ * (elements sharing impedance faces and wavespeed under a Gaussian source)
+ * one representative per class runs the full pipeline and the others only
+ * their load: nt^2/2 + m nt + nf^2 + ntr nf multiply-adds), and the whole
+ * setup's device time.  Outputs may be NULL.  Returns DPGMG_ERR_ARG for a
+ * null handle or system. */
 int dpgmg_setup_profile(dpgmg_handle h, dpgmg_system sys, double* element_ms, double* element_gflop,
                         double* setup_ms);
 
