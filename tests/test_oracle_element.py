@@ -144,3 +144,36 @@ def test_global_system_hpd_and_test_basis_invariance():
     G2, B2 = T.conj().T @ G @ T, T.conj().T @ B
     K2 = B2[:, keep].conj().T @ np.linalg.solve(G2, B2[:, keep])
     assert np.linalg.norm(K1 - K2) / np.linalg.norm(K1) < 1e-10
+
+
+def test_condensed_matrix_depends_only_on_impedance_faces_and_wavespeed():
+    # the premise of computing each element class once (Sec. 2: on a uniform
+    # mesh G, B and K depend on h, omega, c and the impedance faces only; the
+    # load depends on the position): two interior elements and two elements
+    # with the same boundary face set give equal condensed matrices and
+    # different condensed loads; another face set or wavespeed gives another matrix
+    p, om = 2, 6.0
+    m = Mesh((5, 5, 5), p)
+    ld = GaussianSource((0.35, 0.5, 0.6), 0.2)
+
+    def cond(e, c=1.0):
+        bf = boundary_faces(m, e)
+        corner = m.x0 + np.asarray(m.elem_coord(e)) * m.h
+        K, F = dpg_element(p, m.h, corner, c, om, bf, ld)
+        return condense(p, K, F, bf)
+
+    idx = lambda i, j, k: i + 5 * (j + 5 * k)
+    pairs = [(idx(1, 1, 1), idx(3, 2, 3)),       # interior
+             (idx(0, 2, 2), idx(0, 3, 1)),       # x- face
+             (idx(4, 0, 2), idx(4, 0, 3)),       # x+ y- edge
+             (idx(0, 0, 0), idx(0, 0, 0))]       # corner with itself (load equal too)
+    for a, b in pairs:
+        (Ka, Fa), (Kb, Fb) = cond(a), cond(b)
+        assert np.linalg.norm(Ka - Kb) <= 1e-13 * np.linalg.norm(Ka)
+        if a != b:
+            assert np.linalg.norm(Fa - Fb) > 1e-3 * np.linalg.norm(Fa)
+    K1, _ = cond(idx(1, 1, 1))
+    K2, _ = cond(idx(0, 2, 2))
+    K3, _ = cond(idx(1, 1, 1), c=1.3)
+    assert np.linalg.norm(K1 - K2) > 1e-3 * np.linalg.norm(K1)
+    assert np.linalg.norm(K1 - K3) > 1e-3 * np.linalg.norm(K1)
