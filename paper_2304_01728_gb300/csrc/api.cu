@@ -114,7 +114,9 @@ size_t estimate_bytes(const dpgmg_problem* pb, const dpgmg_opts* op) {
   const double m1 = nf + ntr + 1.0;
   resident += ne * (ntr * ntr + nf * (ntr + 1.0) + ntr) * 16.0;     // finest E, Yrec, Fc
   const double per = nt * nt * 8.0 + nt * m1 * 16.0 + m1 * m1 * 16.0;
-  transient = std::max(transient, (double)element_chunk((int64_t)ne, (size_t)per) * per);
+  // element batch scratch, plus the load-only scratch of the element-class members (at most every element)
+  transient = std::max(transient, (double)element_chunk((int64_t)ne, (size_t)per) * per +
+                                      ne * (nt + 1.0 + 2.0 * m1 + 2.0 * nf) * 8.0);
   double xdofs = 0.0;
   for (size_t i = 0; i < specs.size(); ++i) {
     const LevelSpec& s = specs[i];
