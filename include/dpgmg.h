@@ -134,6 +134,28 @@ typedef struct dpgmg_opts {
    initial guess that already meets it returns after 0 iterations.  The
    serving path always starts from 0. */
 #define DPGMG_FLAG_WARM_START 8
+/* CG operator in complex128 on the FP64 pipe instead of the default
+   double-float form (complex64 high and low parts of every FP64 entry, products
+   and sums by error-free FP32 transformations, ~48 significant bits; Sec. 3
+   runs CG on the condensed FP64 system).  The damping estimate of setup then
+   iterates with the complex128 operator and patch inverses too.  With
+   DPGMG_PREC_FP64 every step of the path is then complex128.  Same results to
+   rounding; the FP64 pipe of this GPU makes the CG operator several times
+   slower. */
+#define DPGMG_FLAG_CG_C128 16
+/* Host-made failures for testing the error paths (the paper has no
+   counterpart; no GPU fault is involved):
+   FAULT_NOT_HPD: the host overwrites the first diagonal entry of the dense
+     coarsest matrix with -1 before its factorisation, which then reports a
+     non-positive pivot: dpgmg_setup returns DPGMG_ERR_NOT_HPD (needs a dense
+     coarsest level).
+   FAULT_TC_WAIT: with DPGMG_FLAG_TENSOR_CORES on the mixed path, the first
+     tensor-core update launch issues no MMA and no commit, so its bounded
+     wait (about half a second) runs out with nothing in flight: dpgmg_setup
+     returns DPGMG_ERR_TIMEOUT and the later launches of the setup skip their
+     work.  In both cases the handle stays usable. */
+#define DPGMG_FLAG_FAULT_NOT_HPD (1 << 28)
+#define DPGMG_FLAG_FAULT_TC_WAIT (1 << 29)
 
 typedef struct dpgmg_stats {
   int iters;               /* CG iterations (= V-cycle applications) */
@@ -203,18 +225,22 @@ const char* dpgmg_strerror(int code);
 
 /* Start the serving loop of a handle with `slots` concurrent solves (1..64);
  * optional, the first dpgmg_submit starts it with 4 slots.  Each slot owns a
- * CUDA stream; the serving memory budget is the handle's budget not held by
- * systems set up with dpgmg_setup at that moment.  Errors: ARG (bad count,
- * or already started with another count). */
+ * CUDA stream.  One memory ledger per handle covers both kinds of use: a
+ * request is admitted only while its footprint estimate, the estimates of the
+ * running requests and the memory held by systems set up with dpgmg_setup
+ * together fit the handle's budget, and dpgmg_setup counts the running
+ * requests' estimates in the same way.  Errors: ARG (bad count, or already
+ * started with another count). */
 int dpgmg_serve_start(dpgmg_handle h, int slots);
 
 /* Queue one solve (the same problem and options as dpgmg_setup + dpgmg_solve,
  * copied during the call) and return its ticket without waiting.  Requests
  * are admitted first-fit as a slot is free and their footprint estimate
- * (dpgmg_query_sizes) fits the serving memory not held by running requests,
- * so requests arriving while others run start as memory frees up and their
- * work overlaps on the device.  Errors: ARG; NOMEM if the footprint exceeds
- * the whole serving budget (the request is refused, not queued). */
+ * (dpgmg_query_sizes) fits the handle's memory not held by running requests
+ * or set-up systems, so requests arriving while others run start as memory
+ * frees up and their work overlaps on the device.  Errors: ARG; NOMEM if the
+ * footprint exceeds the handle's whole budget (the request is refused, not
+ * queued). */
 int dpgmg_submit(dpgmg_handle h, const dpgmg_problem* pb, const dpgmg_opts* op, dpgmg_ticket* ticket);
 
 /* Collect a finished request: DPGMG_ERR_PENDING while it is queued or running;
@@ -353,9 +379,12 @@ int dpgmg_profile_read(dpgmg_handle h, dpgmg_system sys, double* total_ms, long 
  * complex entry per patch slot) is a fixed array compiled into the library,
  * DPGMG_NOALLOC_MAX_SLOTS entries (64 MiB), which every GPU that loads the
  * library holds until the process exits.  A level with more patch slots is
- * rejected with DPGMG_ERR_ARG (message in dpgmg_last_error).  The first call
- * on a device looks up the array's device address (cudaGetSymbolAddress);
- * make that first call before any stream capture on that device.  Every
+ * rejected with DPGMG_ERR_ARG (message in dpgmg_last_error).  Every call looks
+ * up the array's device address on the handle's device
+ * (cudaGetSymbolAddress), so an address is never reused after the caller
+ * resets the device context; the first call on a device also loads the
+ * library's device code there, so make it before any stream capture on that
+ * device.  Every
  * entry of the scratch that is read is written first in the same call, so
  * leftover contents of earlier calls do not matter; but all calls share the
  * one array, so calls whose work overlaps on the GPU (other handles, other

@@ -84,7 +84,8 @@ int validate_problem(const dpgmg_problem* pb, const dpgmg_opts* op) {
       op->p_min < 1 || (op->precision != DPGMG_PREC_FP64 && op->precision != DPGMG_PREC_MIXED) ||
       (op->coarsest != DPGMG_COARSEST_CHOLESKY && op->coarsest != DPGMG_COARSEST_NONE &&
        op->coarsest != DPGMG_COARSEST_AUTO) ||
-      (op->flags & ~(DPGMG_FLAG_EAGER | DPGMG_FLAG_TENSOR_CORES | DPGMG_FLAG_STORE_COARSE | DPGMG_FLAG_WARM_START)))
+      (op->flags & ~(DPGMG_FLAG_EAGER | DPGMG_FLAG_TENSOR_CORES | DPGMG_FLAG_STORE_COARSE | DPGMG_FLAG_WARM_START |
+                     DPGMG_FLAG_CG_C128 | DPGMG_FLAG_FAULT_NOT_HPD | DPGMG_FLAG_FAULT_TC_WAIT)))
     return DPGMG_ERR_ARG;
   if ((op->flags & DPGMG_FLAG_STORE_COARSE) && pb->wavespeed) {
     const int64_t ne = (int64_t)pb->n[0] * pb->n[1] * pb->n[2];
@@ -367,18 +368,35 @@ int dpgmg_setup(dpgmg_handle h, const dpgmg_problem* pb, const dpgmg_opts* op, d
     return v;
   }
   std::lock_guard<std::mutex> lk(h->mu);
-  size_t est = estimate_bytes(pb, op);
-  if (h->h.used + est > h->h.budget) {
-    set_last_error("estimated device footprint exceeds the handle's budget");
+  const size_t est = estimate_bytes(pb, op);
+  size_t room = 0;
+  {
+    // reserve the estimate in the handle's ledger (shared with the serving loop)
+    std::lock_guard<std::mutex> lg(h->ledger);
+    if (h->h.used + h->h.serving + est > h->h.budget) {
+      set_last_error("estimated device footprint exceeds the handle's budget (set-up systems and running requests)");
+      return DPGMG_ERR_NOMEM;
+    }
+    room = h->h.budget - h->h.used - h->h.serving;
+    h->h.used += est;
+  }
+  auto unreserve = [&](size_t keep) {
+    {
+      std::lock_guard<std::mutex> lg(h->ledger);
+      h->h.used = h->h.used - std::min(h->h.used, est) + keep;
+    }
+    if (keep < est) server_notify(h);
+  };
+  auto* sys = new (std::nothrow) dpgmg_system_s();
+  if (!sys) {
+    unreserve(0);
     return DPGMG_ERR_NOMEM;
   }
-  auto* sys = new (std::nothrow) dpgmg_system_s();
-  if (!sys) return DPGMG_ERR_NOMEM;
   SystemImpl& S = sys->s;
   try {
     DPG_CUDA(cudaSetDevice(h->h.device));
-    setup_system(S, pb, op, h->h.budget - h->h.used, h->h.stream);
-    h->h.used += S.mem_used();
+    setup_system(S, pb, op, room, h->h.stream);
+    unreserve(S.mem_used());
     *out = sys;
     return DPGMG_OK;
   } catch (const Err& e) {
@@ -386,11 +404,13 @@ int dpgmg_setup(dpgmg_handle h, const dpgmg_problem* pb, const dpgmg_opts* op, d
     profile_clear(S);
     free_workspace(S);
     delete sys;
+    unreserve(0);
     return fail(e);
   } catch (const std::exception& e) {
     cudaStreamSynchronize(h->h.stream);
     free_workspace(S);
     delete sys;
+    unreserve(0);
     return fail(Err{DPGMG_ERR_ARG, e.what()});
   }
 }
@@ -440,11 +460,13 @@ void dpgmg_release(dpgmg_handle h, dpgmg_system sys) {
     std::lock_guard<std::mutex> lk(h->mu);
     cudaSetDevice(h->h.device);
     cudaStreamSynchronize(h->h.stream);
+    std::lock_guard<std::mutex> lg(h->ledger);
     h->h.used -= std::min(h->h.used, sys->s.mem_used());
   }
   profile_clear(sys->s);
   free_workspace(sys->s);
   delete sys;
+  if (h) server_notify(h);
 }
 
 long long dpgmg_launch_count(void) { return g_launches.load(); }

@@ -212,14 +212,14 @@ __global__ void __launch_bounds__(CTA_THREADS) k_dense_herk(C* A, int64_t N, int
 
 // Complex64 rank-64 updates on the tensor cores (tc_update.cu).
 void tc_configure();
-void tc_herk_update(float2* A, int64_t N, int k0, int kw, int* err, cudaStream_t st);
+void tc_herk_update(float2* A, int64_t N, int k0, int kw, int* err, int fault, cudaStream_t st);
 void tc_trinv_update(float2* X, const float2* L, int64_t N, int kb, int* err, cudaStream_t st);
 
 template <class C>
-static bool tc_herk(C*, int64_t, int, int, int*, cudaStream_t) { return false; }
+static bool tc_herk(C*, int64_t, int, int, int*, int, cudaStream_t) { return false; }
 template <>
-bool tc_herk<float2>(float2* A, int64_t N, int k0, int kw, int* info, cudaStream_t st) {
-  tc_herk_update(A, N, k0, kw, info, st);
+bool tc_herk<float2>(float2* A, int64_t N, int k0, int kw, int* info, int fault, cudaStream_t st) {
+  tc_herk_update(A, N, k0, kw, info, fault, st);
   return true;
 }
 template <class C>
@@ -231,9 +231,11 @@ bool tc_trinv<float2>(float2* X, const float2* L, int64_t N, int kb, int* info, 
 }
 
 // Blocked right-looking Cholesky A = L L^H in place (lower); Dinv receives the
-// inverses of the diagonal blocks of L.
+// inverses of the diagonal blocks of L.  tensor: 0 CUDA cores, 1 tensor-core
+// updates, 2 tensor-core updates whose first launch issues no MMA (the
+// DPGMG_FLAG_FAULT_TC_WAIT test of the bounded wait).
 template <class C>
-static void dense_cholesky(C* A, int64_t N, C* Dinv, int* info, bool tensor, cudaStream_t st) {
+static void dense_cholesky(C* A, int64_t N, C* Dinv, int* info, int tensor, cudaStream_t st) {
   const size_t sm = (size_t)2 * CNB * (CNB + 1) * sizeof(C);
   DPG_CUDA(cudaFuncSetAttribute(k_dense_diag<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
   DPG_CUDA(cudaFuncSetAttribute(k_dense_panel<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
@@ -245,7 +247,7 @@ static void dense_cholesky(C* A, int64_t N, C* Dinv, int* info, bool tensor, cud
     if (rows <= 0) break;
     k_dense_panel<C><<<(unsigned)((rows + CNB - 1) / CNB), CTA_THREADS, sm, st>>>(A, N, (int)k0, Dinv);
     DPG_CHECK_LAUNCH();
-    if (tensor && tc_herk<C>(A, N, (int)k0, kb, info, st)) continue;
+    if (tensor && tc_herk<C>(A, N, (int)k0, kb, info, tensor == 2 && k0 == 0 ? 1 : 0, st)) continue;
     int64_t nt = (rows + CNB - 1) / CNB;
     k_dense_herk<C><<<(unsigned)(nt * (nt + 1) / 2), CTA_THREADS, 0, st>>>(A, N, (int)k0);
     DPG_CHECK_LAUNCH();
@@ -343,7 +345,7 @@ __global__ void k_pack(const C* X, int64_t N, C* Lp, C* Up) {
 }
 
 template <class C>
-static void coarse_factor(Alloc& A, C* dense, int64_t N, C** Lp, C** Up, int* info, bool tensor, cudaStream_t st) {
+static void coarse_factor(Alloc& A, C* dense, int64_t N, C** Lp, C** Up, int* info, int tensor, cudaStream_t st) {
   if (tensor) tc_configure();
   const int nb = (int)((N + CNB - 1) / CNB);
   C* Dinv = A.arr<C>((size_t)nb * CNB * CNB);
@@ -383,16 +385,22 @@ void coarse_setup(SystemImpl& S, Level& C0, int* info, cudaStream_t st, Alloc& A
                                                                           C0.mesh.n[0], C0.mesh.n[1], c);
     DPG_CHECK_LAUNCH();
   }
+  if (S.op.flags & DPGMG_FLAG_FAULT_NOT_HPD) {
+    // host-made failure for the error-path tests: a negative first pivot
+    static const double2 neg = make_double2(-1.0, 0.0);
+    DPG_CUDA(cudaMemcpyAsync(dense, &neg, sizeof(double2), cudaMemcpyHostToDevice, st));
+  }
   if (S.op.precision == DPGMG_PREC_MIXED) {
     float2* d32 = A.arr<float2>((size_t)N * N);
     k_narrow_mat<<<1216, 256, 0, st>>>(dense, d32, N * N);
     DPG_CHECK_LAUNCH();
     DPG_CUDA(cudaStreamSynchronize(st));
     A.release(dense);
-    coarse_factor<float2>(A, d32, N, &C0.Lp32, &C0.Up32, info, (S.op.flags & DPGMG_FLAG_TENSOR_CORES) != 0, st);
+    const int tc = (S.op.flags & DPGMG_FLAG_TENSOR_CORES) ? ((S.op.flags & DPGMG_FLAG_FAULT_TC_WAIT) ? 2 : 1) : 0;
+    coarse_factor<float2>(A, d32, N, &C0.Lp32, &C0.Up32, info, tc, st);
     A.release(d32);
   } else {
-    coarse_factor<double2>(A, dense, N, &C0.Lp64, &C0.Up64, info, false, st);
+    coarse_factor<double2>(A, dense, N, &C0.Lp64, &C0.Up64, info, 0, st);
     A.release(dense);
   }
   C0.has_coarse = true;

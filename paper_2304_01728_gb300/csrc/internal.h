@@ -218,12 +218,16 @@ struct SystemImpl {
   ~SystemImpl();
 };
 
+// Memory ledger of a handle: `used` = bytes held by systems set up with
+// dpgmg_setup (reserved at the estimate during a setup), `serving` = the
+// footprint estimates of the running serving requests; both under `ledger`.
 struct HandleImpl {
   int device = 0;
   cudaStream_t stream = nullptr;
   bool own_stream = false;
   size_t budget = 0;
   size_t used = 0;
+  size_t serving = 0;
 };
 
 // ----------------------------------------------------------- stage entry points
@@ -282,11 +286,14 @@ void smooth_apply64(const Level& L, const double2* r, double2* y, double theta, 
 
 struct dpgmg_handle_s {
   dpgmg::HandleImpl h;
-  std::mutex mu;
+  std::mutex mu;       // serialises the calls on the handle
+  std::mutex ledger;   // guards h.used and h.serving (innermost lock)
   dpgmg::Server* server = nullptr;
 };
 namespace dpgmg {
 void server_shutdown(dpgmg_handle h);
+// wakes the serving workers after memory was returned to the handle's ledger
+void server_notify(dpgmg_handle h);
 }
 struct dpgmg_system_s {
   dpgmg::SystemImpl s;

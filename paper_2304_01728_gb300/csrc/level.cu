@@ -706,7 +706,7 @@ void build_hierarchy(SystemImpl& S, cudaStream_t st) {
     PatchDev& Pd = F.P;
     const bool keep_split = l == L && F.kind == 1;
     float2* plo = nullptr;
-    if (!(S.op.theta > 0.0)) {
+    if (!(S.op.theta > 0.0) && !(S.op.flags & DPGMG_FLAG_CG_C128)) {   // double-float estimate
       Pd.inv32 = A.arr<float2>((size_t)std::max<int64_t>(Pd.nvals, 1));
       plo = A.arr<float2>((size_t)std::max<int64_t>(Pd.nvals, 1));
       split_df(Pd.inv64, Pd.inv32, plo, Pd.nvals, st);

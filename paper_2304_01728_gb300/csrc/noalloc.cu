@@ -12,10 +12,10 @@
 // The array lives in every GPU context that loads the library, until the
 // process exits (NOALLOC_MAX_SLOTS complex128 entries = 64 MiB).  Host code
 // must not use the array's name as a device address: its device address is
-// looked up once per device with cudaGetSymbolAddress, with that device
-// current, on the first call made on the device.
+// looked up with cudaGetSymbolAddress, with the handle's device current, on
+// every call (a cheap query), so a context the caller has reset and recreated
+// in between is never given a stale address.
 #include <cstdint>
-#include <mutex>
 
 #include "common.cuh"
 #include "internal.h"
@@ -24,27 +24,18 @@
 namespace dpgmg {
 
 constexpr int64_t NOALLOC_MAX_SLOTS = (int64_t)1 << 22;   // patch-product entries (complex128)
-constexpr int NOALLOC_MAX_DEVICES = 64;
 
 static __device__ __align__(256) double2 g_noalloc_scratch[NOALLOC_MAX_SLOTS];
 
-static std::mutex g_noalloc_mu;
-static void* g_noalloc_addr[NOALLOC_MAX_DEVICES] = {};
-
-// Device address of the scratch array on the current device (looked up once).
-static void* noalloc_scratch(int dev) {
-  std::lock_guard<std::mutex> lk(g_noalloc_mu);
-  if (dev < 0 || dev >= NOALLOC_MAX_DEVICES) throw Err{DPGMG_ERR_ARG, "device ordinal out of range"};
-  if (!g_noalloc_addr[dev]) {
-    void* p = nullptr;
-    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-    if (e != cudaSuccess || !p) {
-      cudaGetLastError();
-      throw Err{DPGMG_ERR_CUDA, std::string("cudaGetSymbolAddress(scratch): ") + cudaGetErrorString(e)};
-    }
-    g_noalloc_addr[dev] = p;
+// Device address of the scratch array in the current device's context.
+static void* noalloc_scratch() {
+  void* p = nullptr;
+  cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+  if (e != cudaSuccess || !p) {
+    cudaGetLastError();
+    throw Err{DPGMG_ERR_CUDA, std::string("cudaGetSymbolAddress(scratch): ") + cudaGetErrorString(e)};
   }
-  return g_noalloc_addr[dev];
+  return p;
 }
 
 // The same smoother kernels as the solver (smoother.cuh), reading and
@@ -91,7 +82,7 @@ extern "C" int dpgmg_smooth_noalloc(dpgmg_handle h, dpgmg_system sys, int level,
   }
   try {
     DPG_CUDA(cudaSetDevice(h->h.device));
-    void* scratch = noalloc_scratch(h->h.device);
+    void* scratch = noalloc_scratch();
     cudaStream_t st = h->h.stream;
     const double2* r = reinterpret_cast<const double2*>(r_dev);
     double2* y = reinterpret_cast<double2*>(y_dev);

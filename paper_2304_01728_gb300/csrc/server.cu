@@ -40,7 +40,7 @@ struct Request {
 struct Server {
   int device = 0;
   int slots = 0;
-  size_t budget = 0, mem_used = 0;
+  dpgmg_handle owner = nullptr;   // its ledger admits requests (h.used + h.serving <= h.budget)
   std::mutex mu;
   std::condition_variable cv;
   std::deque<std::shared_ptr<Request>> queue;
@@ -95,25 +95,33 @@ static void worker_loop(Server* sv) {
       std::unique_lock<std::mutex> lk(sv->mu);
       for (;;) {
         if (sv->stop) break;
-        for (auto it = sv->queue.begin(); it != sv->queue.end(); ++it) {
-          if ((*it)->est + sv->mem_used <= sv->budget) {
-            rq = *it;
-            sv->queue.erase(it);
-            break;
+        {
+          // first fit against the handle's ledger: set-up systems and running requests
+          std::lock_guard<std::mutex> lg(sv->owner->ledger);
+          HandleImpl& H = sv->owner->h;
+          for (auto it = sv->queue.begin(); it != sv->queue.end(); ++it) {
+            if ((*it)->est + H.serving + H.used <= H.budget) {
+              rq = *it;
+              sv->queue.erase(it);
+              H.serving += rq->est;
+              break;
+            }
           }
         }
         if (rq) break;
         sv->cv.wait(lk);
       }
       if (!rq) break;
-      sv->mem_used += rq->est;
       rq->state = 1;
       rq->t_start = now_ms();
     }
     run_request(*rq, st, rq->est);
     {
       std::lock_guard<std::mutex> lk(sv->mu);
-      sv->mem_used -= rq->est;
+      {
+        std::lock_guard<std::mutex> lg(sv->owner->ledger);
+        sv->owner->h.serving -= std::min(sv->owner->h.serving, rq->est);
+      }
       rq->t_done = now_ms();
       rq->state = 2;
     }
@@ -127,11 +135,18 @@ static Server* server_of(dpgmg_handle h, int slots) {
     auto* sv = new Server();
     sv->device = h->h.device;
     sv->slots = slots > 0 ? slots : 4;
-    sv->budget = h->h.budget > h->h.used ? h->h.budget - h->h.used : 0;
+    sv->owner = h;
     for (int i = 0; i < sv->slots; ++i) sv->workers.emplace_back(worker_loop, sv);
     h->server = sv;
   }
   return h->server;
+}
+
+void server_notify(dpgmg_handle h) {
+  Server* sv = h ? h->server : nullptr;
+  if (!sv) return;
+  { std::lock_guard<std::mutex> lk(sv->mu); }
+  sv->cv.notify_all();
 }
 
 void server_shutdown(dpgmg_handle h) {
@@ -186,8 +201,8 @@ int dpgmg_submit(dpgmg_handle h, const dpgmg_problem* pb, const dpgmg_opts* op, 
   rq->pb.wavespeed = nullptr;
   rq->pb.mf_coeffs = nullptr;
   rq->est = estimate_bytes(pb, op);
-  if (rq->est > sv->budget) {
-    set_last_error("request footprint exceeds the serving memory budget");
+  if (rq->est > h->h.budget) {
+    set_last_error("request footprint exceeds the handle's memory budget");
     return DPGMG_ERR_NOMEM;
   }
   {

@@ -1048,10 +1048,12 @@ static void dot(WS& W, const double2* u, const double2* v, int64_t n, int which,
   DPG_CHECK_LAUNCH();
 }
 
+static bool cg_c128(const SystemImpl& S) { return (S.op.flags & DPGMG_FLAG_CG_C128) != 0; }
+
 static const ECSRDev& cg_operator(SystemImpl& S, WS& W, cudaStream_t st) {
   Level& F = S.levels.back();
   if (S.levels.size() > 1 && F.kind == 1) {
-    if (!F.A.vlo) split_operator(S.mem, F.A, st);
+    if (!F.A.vlo && !cg_c128(S)) split_operator(S.mem, F.A, st);
     return F.A;
   }
   if (!W.acg_owned) {
@@ -1063,11 +1065,21 @@ static const ECSRDev& cg_operator(SystemImpl& S, WS& W, cudaStream_t st) {
       assemble_ecsr(S.mem, prep_ecsr(F.mesh, element_groups(F.mesh)), W.Acg, st);
     }
     ecsr_add_elements(W.Acg, F.E, F.dofs, F.mesh.nelem, F.nloc, 0, F.mesh.n, st);
-    split_operator(S.mem, W.Acg, st);
+    if (!cg_c128(S)) split_operator(S.mem, W.Acg, st);
     DPG_CUDA(cudaStreamSynchronize(st));
     W.acg_owned = true;
   }
   return W.Acg;
+}
+
+// y = A x (mode 0) or b - A x (mode 1) with the CG operator: double-float by
+// default, complex128 on the FP64 pipe under DPGMG_FLAG_CG_C128
+static void cg_apply(SystemImpl& S, WS& W, const ECSRDev& A, const double2* x, const double2* b, double2* y,
+                     int mode, cudaStream_t st, SystemImpl* prof = nullptr) {
+  if (cg_c128(S))
+    spmv<double2>(A, A.v64, x, b, y, mode, st, prof);
+  else
+    spmv_df(A, x, b, y, mode, W.xh, W.xl, st, prof);
 }
 
 // ------------------------------------------------------------ tuning
@@ -1272,8 +1284,14 @@ void prepare_solve(SystemImpl& S, cudaStream_t st) {
     const int64_t n = F.mesh.ndof;
     DPG_CUDA(cudaMemsetAsync(W.xh, 0, (size_t)n * sizeof(float2), st));
     DPG_CUDA(cudaMemsetAsync(W.xl, 0, (size_t)n * sizeof(float2), st));
-    const TuneKey key{2, F.mesh.p, F.kind, log2i(n)};
-    Acg.gsel[2] = pick_group(key, ev, st, [&](int G) { spmv_df_g(Acg, W.xh, W.xl, nullptr, W.q, 0, G, st); });
+    if (cg_c128(S)) {
+      DPG_CUDA(cudaMemsetAsync(W.p, 0, (size_t)n * sizeof(double2), st));
+      const TuneKey key{1, F.mesh.p, F.kind, log2i(n)};
+      Acg.gsel[1] = pick_group(key, ev, st, [&](int G) { spmv_g<double2>(Acg, Acg.v64, W.p, nullptr, W.q, 0, G, st); });
+    } else {
+      const TuneKey key{2, F.mesh.p, F.kind, log2i(n)};
+      Acg.gsel[2] = pick_group(key, ev, st, [&](int G) { spmv_df_g(Acg, W.xh, W.xl, nullptr, W.q, 0, G, st); });
+    }
   }
 }
 
@@ -1302,7 +1320,7 @@ int pcg_solve(SystemImpl& S, cudaStream_t st, double2* xout, dpgmg_stats* stats,
   if (x0) {
     // warm start: x = x0, r = b - A x0
     DPG_CUDA(cudaMemcpyAsync(W.x, x0, (size_t)n * sizeof(double2), cudaMemcpyDeviceToDevice, st));
-    spmv_df(A, W.x, S.b, W.r, 1, W.xh, W.xl, st);
+    cg_apply(S, W, A, W.x, S.b, W.r, 1, st);
     dot(W, W.r, W.r, n, 1, st);
     DPG_CUDA(cudaMemcpyAsync(W.sc_host, W.sc, SC_COUNT * sizeof(double2), cudaMemcpyDeviceToHost, st));
     DPG_CUDA(cudaStreamSynchronize(st));
@@ -1321,7 +1339,9 @@ int pcg_solve(SystemImpl& S, cudaStream_t st, double2* xout, dpgmg_stats* stats,
     float2* r32 = mixed ? W.w32[Lf].r : nullptr;
     // presplit: p's double-float split is already in W.xh / W.xl (written by k_cg_dir)
     auto tail = [&](bool presplit) {
-      if (presplit) {
+      if (cg_c128(S)) {
+        spmv<double2>(A, A.v64, W.p, nullptr, W.q, 0, st, pcg_prof);
+      } else if (presplit) {
         int pe = prof_begin(pcg_prof, st);
         spmv_df_g(A, W.xh, W.xl, nullptr, W.q, 0, A.gsel[2], st);
         prof_end(pcg_prof, pe, st);
@@ -1385,7 +1405,7 @@ int pcg_solve(SystemImpl& S, cudaStream_t st, double2* xout, dpgmg_stats* stats,
   // true residual ||b - A x|| / ||b|| in FP64
   double true_rel = 0.0;
   if (nb > 0.0) {
-    spmv_df(A, W.x, S.b, W.q, 1, W.xh, W.xl, st);
+    cg_apply(S, W, A, W.x, S.b, W.q, 1, st);
     dot(W, W.q, W.q, n, 1, st);
     DPG_CUDA(cudaMemcpyAsync(W.sc_host, W.sc, SC_COUNT * sizeof(double2), cudaMemcpyDeviceToHost, st));
     DPG_CUDA(cudaStreamSynchronize(st));
@@ -1511,11 +1531,54 @@ static void estimate_theta_df(SystemImpl& S, Level& F, const float2* plo, double
   W.sc = nullptr;
 }
 
+// The same iteration in complex128 on the FP64 pipe (DPGMG_FLAG_CG_C128): the
+// level operator's FP64 values and the FP64 patch inverses.
+static void estimate_theta_z(SystemImpl& S, Level& F, double* out, cudaStream_t st) {
+  const int64_t n = F.mesh.ndof;
+  Alloc tmp;
+  tmp.budget = (size_t)-1;
+  tmp.stream = st;
+  double2* x = tmp.arr<double2>((size_t)n);
+  double2* y = tmp.arr<double2>((size_t)n);
+  double2* t = tmp.arr<double2>((size_t)n);
+  double2* pbuf = tmp.arr<double2>((size_t)std::max<int64_t>(F.P.scratch_entries(), 1));
+  WS W;
+  W.part = tmp.arr<double2>(RED_BLOCKS);
+  W.sc = tmp.arr<double2>(SC_COUNT);
+  k_start_vector<double2><<<nblk(n), 256, 0, st>>>(x, n, F.P.slot_ptr);
+  DPG_CHECK_LAUNCH();
+  dot_t<double2>(W, x, x, n, 1, st);
+  k_scale<double2><<<RED_BLOCKS, 256, 0, st>>>(x, n, W.sc, SC_RR);
+  DPG_CHECK_LAUNCH();
+  for (int k = 0; k < 30; ++k) {
+    spmv<double2>(F.A, F.A.v64, x, nullptr, t, 0, st);
+    smooth<double2>(F, t, y, 1.0, 0, pbuf, st);
+    dot_t<double2>(W, y, y, n, 1, st);
+    k_scale<double2><<<RED_BLOCKS, 256, 0, st>>>(y, n, W.sc, SC_RR);
+    DPG_CHECK_LAUNCH();
+    std::swap(x, y);
+  }
+  spmv<double2>(F.A, F.A.v64, x, nullptr, t, 0, st);   // M x
+  smooth<double2>(F, t, y, 1.0, 0, pbuf, st);           // S M x
+  dot_t<double2>(W, t, y, n, 3, st);
+  k_take_re<<<1, 1, 0, st>>>(W.sc, SC_RHO, out);
+  DPG_CHECK_LAUNCH();
+  dot_t<double2>(W, x, t, n, 3, st);
+  k_take_re<<<1, 1, 0, st>>>(W.sc, SC_RHO, out + 1);
+  DPG_CHECK_LAUNCH();
+  W.part = nullptr;
+  W.sc = nullptr;
+}
+
 void estimate_theta(SystemImpl& S, int l, double* rayleigh, const float2* plo, cudaStream_t st) {
   Level& F = S.levels[l];
   configure_smoother_kernels();
   if (S.op.theta > 0.0) {
     F.theta = S.op.theta;
+    return;
+  }
+  if (cg_c128(S)) {
+    estimate_theta_z(S, F, rayleigh, st);
     return;
   }
   // the same double-float estimate on both paths (the operators' FP64 values)
@@ -1558,7 +1621,7 @@ void apply_op(SystemImpl& S, int op, int l, const double2* x, double2* y, cudaSt
   WS& W = *reinterpret_cast<WS*>(S.ws);
   if (op == DPGMG_OP_AFULL) {
     const ECSRDev& A = cg_operator(S, W, st);
-    spmv_df(A, x, nullptr, y, 0, W.xh, W.xl, st);
+    cg_apply(S, W, A, x, nullptr, y, 0, st);
     return;
   }
   if (S.op.precision == DPGMG_PREC_MIXED) {

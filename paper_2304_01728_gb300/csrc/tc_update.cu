@@ -37,7 +37,8 @@ constexpr uint32_t TC_A_BYTES = 128 * TC_KP * 4;   // 32 KiB
 constexpr uint32_t TC_B_BYTES = 64 * TC_KP * 4;    // 16 KiB
 constexpr uint32_t TC_SMEM = 2 * TC_A_BYTES + 2 * TC_B_BYTES + 1024;
 constexpr int TC_HERK = 0, TC_GEMM = 1;
-constexpr long long TC_WAIT_LIMIT = 1LL << 22;
+constexpr long long TC_WAIT_LIMIT = 1LL << 24;             // polls of one wait, at most
+constexpr unsigned long long TC_WAIT_NS = 500000000ull;    // and at most 0.5 s of wall time
 
 // byte offset of element (row r, K index k) in the canonical layout
 __device__ __forceinline__ uint32_t core_off(int r, int k) {
@@ -72,8 +73,16 @@ __device__ __forceinline__ void mma_tf32(uint32_t d, uint64_t a, uint64_t b, uin
       "l"(a), "l"(b), "r"(idesc), "r"(acc));
 }
 
-// bounded wait for the completion of mbarrier phase `parity`
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// bounded wait for the completion of mbarrier phase `parity`: gives up after
+// limit_ns of wall time (or TC_WAIT_LIMIT polls)
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, unsigned long long limit_ns) {
+  const unsigned long long t0 = global_ns();
   for (long long it = 0; it < TC_WAIT_LIMIT; ++it) {
     uint32_t done;
     asm volatile(
@@ -83,17 +92,22 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
         : "r"(bar), "r"(parity)
         : "memory");
     if (done) return true;
+    if ((it & 63) == 63 && global_ns() - t0 > limit_ns) return false;
   }
   return false;
 }
 
 __global__ void __launch_bounds__(TC_THREADS) k_tc_update(float2* __restrict__ C, const float2* __restrict__ A,
                                                           const float2* __restrict__ B, int64_t N, int k0, int kw,
-                                                          int mode, int kb, int* __restrict__ err) {
+                                                          int mode, int kb, int* __restrict__ err, int fault) {
   extern __shared__ unsigned char tc_raw[];
   __shared__ __align__(8) uint64_t mbar;
   __shared__ uint32_t tmem_slot;
   const int tid = threadIdx.x, warp = tid >> 5;
+  // once a wait of this factorisation has run out, later launches do nothing
+  // (setup reports DPGMG_ERR_TIMEOUT); the test is uniform over the CTA and
+  // comes before any TMEM allocation or barrier
+  if (*reinterpret_cast<volatile int*>(err) & 32) return;
 
   // output tile (same enumeration as the CUDA-core kernels)
   int64_t i0, j0;
@@ -140,6 +154,7 @@ __global__ void __launch_bounds__(TC_THREADS) k_tc_update(float2* __restrict__ C
   // kind::tf32, D in F32, A and B TF32 and K-major, N = 64, M = 128
   const uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(TC_T >> 3) << 17) | ((128u >> 4) << 24);
   bool ok = true;
+  int failed_pass = -1;
   for (int pass = 0; pass < 2 && ok; ++pass) {
     const int t0 = pass * (TC_KP / 2);
     constexpr int PER = TC_T * (TC_KP / 2) / TC_THREADS;   // operand values per thread
@@ -181,7 +196,7 @@ __global__ void __launch_bounds__(TC_THREADS) k_tc_update(float2* __restrict__ C
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    if (tid == 0) {
+    if (tid == 0 && !fault) {   // fault (tests): issue nothing, so that the wait below runs out
 #pragma unroll 1
       for (int s = 0; s < TC_KP / 8; ++s) {   // K = 8 TF32 values (32 bytes) per instruction
         const uint64_t ah = smem_desc(sAhi + 256u * s), al = smem_desc(sAlo + 256u * s);
@@ -194,11 +209,18 @@ __global__ void __launch_bounds__(TC_THREADS) k_tc_update(float2* __restrict__ C
                    : "memory");
     }
     // the next pass overwrites the operands, the epilogue reads D: wait for the MMAs
-    const bool done = mbar_wait(bar, (uint32_t)(pass & 1));
+    const bool done = mbar_wait(bar, (uint32_t)(pass & 1), TC_WAIT_NS);
     ok = __syncthreads_and(done) != 0;
+    if (!ok) failed_pass = pass;
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   }
-  if (!ok && tid == 0) atomicOr(err, 32);
+  if (!ok && tid == 0) {
+    atomicOr(err, 32);
+    // MMAs issued in the failed pass may still be running: give them (and
+    // their commit to the barrier) a second bounded wait before the
+    // accumulator is freed and the CTA's shared memory goes away
+    if (!fault) mbar_wait(bar, (uint32_t)(failed_pass & 1), 2 * TC_WAIT_NS);
+  }
 
   float* Ds = reinterpret_cast<float*>(gbase);   // [128][65] staging of D
   if (ok) {
@@ -244,11 +266,13 @@ void tc_configure() {
 
 // Trailing update of the blocked Cholesky after panel k0 (width kw <= 64):
 // every lower 64 x 64 tile of A[k0+kw:, k0+kw:].
-void tc_herk_update(float2* A, int64_t N, int k0, int kw, int* err, cudaStream_t st) {
+// fault != 0 (tests): the launch issues no MMA, so its bounded waits run out.
+void tc_herk_update(float2* A, int64_t N, int k0, int kw, int* err, int fault, cudaStream_t st) {
   const int64_t rows = N - k0 - kw;
   if (rows <= 0) return;
   const int64_t nt = (rows + TC_T - 1) / TC_T;
-  k_tc_update<<<(unsigned)(nt * (nt + 1) / 2), TC_THREADS, TC_SMEM, st>>>(A, A, A, N, k0, kw, TC_HERK, 0, err);
+  k_tc_update<<<(unsigned)(nt * (nt + 1) / 2), TC_THREADS, TC_SMEM, st>>>(A, A, A, N, k0, kw, TC_HERK, 0, err,
+                                                                          fault);
   DPG_CHECK_LAUNCH();
 }
 
@@ -260,7 +284,7 @@ void tc_trinv_update(float2* X, const float2* L, int64_t N, int kb, int* err, cu
   if (rows <= 0) return;
   const int k0 = kb * TC_T;
   const int kw = (int)(N - k0 < TC_T ? N - k0 : TC_T);
-  k_tc_update<<<(unsigned)(rows * (kb + 1)), TC_THREADS, TC_SMEM, st>>>(X, L, X, N, k0, kw, TC_GEMM, kb, err);
+  k_tc_update<<<(unsigned)(rows * (kb + 1)), TC_THREADS, TC_SMEM, st>>>(X, L, X, N, k0, kw, TC_GEMM, kb, err, 0);
   DPG_CHECK_LAUNCH();
 }
 

@@ -82,6 +82,22 @@ def config3(precision="mixed"):
                 layers=dict(cuts=cuts, speeds=speeds))
 
 
+def config3_small(precision="fp64"):
+    """The layered-medium hierarchy shape at test size: [0,2]x[0,2]x[0,1],
+    8x8x4 hexes, p = 3, omega = 8 pi, one seeded wavespeed per horizontal
+    element layer (4 layers, U[0.1, 1], seed 33), source centre drawn in
+    [0.5,1.5]^2 x [0.25,0.75] (seed 33), width 0.08; 4 levels
+    p3 -> p2 -> 4x4x2 -> 2x2x1 (two stacked h-transitions)."""
+    n = (8, 8, 4)
+    speeds = [0.1 + 0.9 * _u(33, k) for k in range(4)]
+    x0 = (0.5 + _u(33, 4), 0.5 + _u(33, 5), 0.25 + 0.5 * _u(33, 6))
+    c = [speeds[kz] for kz in range(n[2]) for _ in range(n[0] * n[1])]
+    return dict(problem=dict(n=n, p=3, omega=8 * math.pi, x0=(0, 0, 0), x1=(2, 2, 1), wavespeed=c,
+                             src_center=x0, src_width=0.08),
+                opts=dict(n_levels=4, p_min=2, precision=precision, tol=1e-8),
+                name="layered box 8x8x4 p=3 omega=8pi, 4-level, %s V-cycle" % precision)
+
+
 def _stream_opts(n, precision):
     return dict(n_levels=4, p_min=2 if n % 2 == 0 else 1, precision=precision, tol=1e-8, coarsest="auto")
 

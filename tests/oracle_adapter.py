@@ -3,9 +3,14 @@
 Test infrastructure: the tests drive both sides with identical seeded inputs
 (``paper_2304_01728_gb300.workloads``) and compare element by element.
 """
+import multiprocessing as mp
+import os
+
 import numpy as np
 
-from oracle.assembly import build_fine
+from oracle.assembly import FineSystem, build_fine
+from oracle.element import condense, dpg_element
+from oracle.mesh import Mesh
 from oracle.hierarchy import build_hierarchy
 from oracle.problem import GaussianSource, Manufactured, PlaneWave
 
@@ -19,9 +24,46 @@ def oracle_load(pk):
     return Manufactured(pk["mf_coeffs"], pk["omega"], pk.get("x0", (0, 0, 0)), pk.get("x1", (1, 1, 1)))
 
 
-def oracle_system(pk, ok, hierarchy=True):
-    fs = build_fine(pk["n"], pk["p"], pk["omega"], wavespeed=pk.get("wavespeed"), load=oracle_load(pk),
-                    x0=pk.get("x0", (0, 0, 0)), x1=pk.get("x1", (1, 1, 1)))
+_CTX = {}
+
+
+def _pinit(pk):
+    _CTX.update(pk=pk, mesh=Mesh(pk["n"], pk["p"], pk.get("x0", (0, 0, 0)), pk.get("x1", (1, 1, 1))),
+                load=oracle_load(pk))
+
+
+def _pelem(e):
+    """One element of the oracle's FineSystem, computed by the oracle's own
+    dpg_element / condense exactly as FineSystem does."""
+    pk, m = _CTX["pk"], _CTX["mesh"]
+    from oracle.element import boundary_faces
+    bf = boundary_faces(m, e)
+    corner = m.x0 + np.asarray(m.elem_coord(e)) * m.h
+    c = 1.0 if pk.get("wavespeed") is None else float(np.asarray(pk["wavespeed"]).ravel()[e])
+    K, F = dpg_element(m.p, m.h, corner, c, pk["omega"], bf, _CTX["load"])
+    Kc, Fc = condense(m.p, K, F, bf)
+    return e, K, F, Kc, Fc
+
+
+def build_fine_parallel(pk, workers=None):
+    """The oracle's FineSystem with its element loop spread over processes
+    (started with 'spawn', so that no GPU context is inherited); the same
+    numbers as oracle.assembly.build_fine."""
+    workers = workers or min(16, os.cpu_count() or 1)
+    mesh = Mesh(pk["n"], pk["p"], pk.get("x0", (0, 0, 0)), pk.get("x1", (1, 1, 1)))
+    fs = FineSystem(mesh, pk["omega"], pk.get("wavespeed"), oracle_load(pk), elements=[])
+    with mp.get_context("spawn").Pool(workers, initializer=_pinit, initargs=(pk,)) as pool:
+        for e, K, F, Kc, Fc in pool.imap_unordered(_pelem, range(mesh.n_elem), chunksize=2):
+            fs.K[e], fs.F[e], fs.Kc[e], fs.Fc[e] = K, F, Kc, Fc
+    return fs
+
+
+def oracle_system(pk, ok, hierarchy=True, parallel=False):
+    if parallel and np.prod(pk["n"]) >= 8 and (os.cpu_count() or 1) > 1:
+        fs = build_fine_parallel(pk)
+    else:
+        fs = build_fine(pk["n"], pk["p"], pk["omega"], wavespeed=pk.get("wavespeed"), load=oracle_load(pk),
+                        x0=pk.get("x0", (0, 0, 0)), x1=pk.get("x1", (1, 1, 1)))
     A, b = fs.assemble()
     levels = None
     if hierarchy:

@@ -75,7 +75,7 @@ def test_iteration_cap_reports_not_converged():
     dict(opts=dict(tol=0.0)),
     dict(opts=dict(n_levels=0)),
     dict(opts=dict(max_iter=0)),
-    dict(opts=dict(flags=16)),
+    dict(opts=dict(flags=1 << 20)),
     dict(problem=dict(wavespeed=np.r_[np.ones(63), 2.0]), opts=dict(flags=4)),   # stored needs constant c
 ])
 def test_invalid_inputs_are_refused(bad):
@@ -144,24 +144,34 @@ def test_setup_and_solve_are_bitwise_reproducible(precision):
     assert np.array_equal(runs[0][0], runs[1][0]) and np.array_equal(runs[0][1], runs[1][1])
 
 
-@pytest.mark.parametrize("n,p,prec", [((6, 6, 6), 2, "fp64"), ((8, 7, 6), 3, "mixed")])
-def test_element_class_reuse_matches_full_pipeline(n, p, prec, monkeypatch):
-    # constant wavespeed: 27 element classes (impedance-face masks); members of a
-    # class take the representative's factors and compute only their load
+@pytest.mark.parametrize("n,p,prec,layers", [((6, 6, 6), 2, "fp64", 0), ((8, 7, 6), 3, "mixed", 0),
+                                              ((8, 7, 6), 3, "mixed", 3)])
+def test_element_class_reuse_matches_full_pipeline(n, p, prec, layers, monkeypatch):
+    # element classes = (impedance-face mask, wavespeed): 27 with a constant
+    # wavespeed, up to 27 per distinct wavespeed with `layers` horizontal layers;
+    # members of a class take the representative's factors and compute only
+    # their load
     pk = dict(n=n, p=p, omega=9.0, src_center=(0.45, 0.55, 0.5), src_width=0.15)
+    if layers:
+        speeds = np.random.default_rng(7).uniform(0.3, 1.0, layers)
+        kz = np.arange(n[2]) * layers // n[2]
+        pk["wavespeed"] = np.repeat(speeds[kz], n[0] * n[1])
     ok = dict(n_levels=2, p_min=p - 1, precision=prec)
     nel = int(np.prod(n))
-    picks = [0, n[0] // 2, (n[1] // 2) * n[0] + n[0] // 2, nel // 2 + n[0] // 2, nel - 1, nel // 3]
+    picks = [0, n[0] // 2, (n[1] // 2) * n[0] + n[0] // 2, nel // 2 + n[0] // 2, nel - 1, nel // 3,
+             nel - n[0] * n[1] // 2, n[0] * n[1] * (n[2] // 2) + 5]
     out = {}
     for reuse in ("0", "1"):
         monkeypatch.setenv("DPGMG_ELEMENT_REUSE", reuse)
         with D.Solver(pk, **ok) as s:
             ntr = (p + 1) ** 3 - (p - 1) ** 3 + 6 * p * p   # local traces: u-hat (H^1 trace) and p-hat
             mats = [D.dpgmg_element_matrix(s.h, s.s, ok["n_levels"] - 1, e, ntr, with_load=True) for e in picks]
+            gflop = D.dpgmg_setup_profile(s.h, s.s)[1]
             x, f, st, code = s.solve()
             assert code == D.DPGMG_OK
-            out[reuse] = (mats, x, f, st.iters)
-    (m0, x0, f0, i0), (m1, x1, f1, i1) = out["0"], out["1"]
+            out[reuse] = (mats, x, f, st.iters, gflop)
+    (m0, x0, f0, i0, g0), (m1, x1, f1, i1, g1) = out["0"], out["1"]
+    assert g1 < 0.5 * g0, (g1, g0)   # the classes were used
     for a, b in zip(m0, m1):
         assert rel(b[0], a[0]) < 1e-13 and rel(b[1], a[1]) < 1e-11
     assert i1 == i0

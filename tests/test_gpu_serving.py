@@ -96,3 +96,27 @@ def test_admission_by_memory():
         assert D.dpgmg_poll(h, tickets[0])[0] == D.DPGMG_ERR_ARG   # collected tickets are forgotten
     finally:
         D.dpgmg_destroy(h)
+
+
+def test_one_ledger_for_setup_and_serving():
+    """Systems set up with dpgmg_setup and running requests share the
+    handle's memory budget: a request that fits the budget on its own waits
+    while a set-up system holds memory, and runs once the system is released."""
+    pk, ok = MIX[3]
+    pb, keep = D.make_problem(**pk)
+    op = D.make_opts(**ok)
+    nt, nf, est = D.dpgmg_query_sizes(pb, op)
+    h = D.dpgmg_create(0, mem_budget_bytes=est + (1 << 20))
+    try:
+        s = D.dpgmg_setup(h, pb, op)
+        D.dpgmg_serve_start(h, 2)
+        t = D.dpgmg_submit(h, pb, op)
+        time.sleep(1.0)
+        assert D.dpgmg_poll(h, t)[0] == D.DPGMG_ERR_PENDING   # held back by the set-up system
+        D.dpgmg_release(h, s)
+        code, x, f, st, lat = _wait(h, t, nt, nf)
+        assert code == D.DPGMG_OK, D.lib().dpgmg_last_error().decode()
+        s = D.dpgmg_setup(h, pb, op)                           # the budget is free again
+        D.dpgmg_release(h, s)
+    finally:
+        D.dpgmg_destroy(h)
