@@ -74,7 +74,7 @@ extern "C" {
 #define DPGMG_SRC_MANUFACTURED  2   /* f, g, u0 of given polynomials p_ex, u_ex */
 
 #define DPGMG_PREC_FP64   0         /* V-cycle in complex128 */
-#define DPGMG_PREC_MIXED  1         /* V-cycle in complex64, CG in complex128 */
+#define DPGMG_PREC_MIXED  1         /* V-cycle in complex64 (patch factors in FP32), CG in complex128 */
 
 #define DPGMG_COARSEST_CHOLESKY 0   /* dense Cholesky solve on level 0 */
 #define DPGMG_COARSEST_NONE     1   /* no level-0 correction (Sec. 4 list) */
@@ -143,6 +143,12 @@ typedef struct dpgmg_opts {
    rounding; the FP64 pipe of this GPU makes the CG operator several times
    slower. */
 #define DPGMG_FLAG_CG_C128 16
+/* Mixed path: factor the vertex-patch blocks in FP64 and round their inverses
+   to complex64 afterwards, instead of the default complex64 blocks factored in
+   FP32 (Cholesky, triangular inverse and L^-H L^-1), the V-cycle's own
+   precision.  Setup is slower (the FP64 pipe of this GPU); the smoother then
+   differs from the FP64 one by the rounding of its entries only. */
+#define DPGMG_FLAG_PATCH_FP64 32
 /* Host-made failures for testing the error paths (the paper has no
    counterpart; no GPU fault is involved):
    FAULT_NOT_HPD: the host overwrites the first diagonal entry of the dense

@@ -85,7 +85,8 @@ int validate_problem(const dpgmg_problem* pb, const dpgmg_opts* op) {
       (op->coarsest != DPGMG_COARSEST_CHOLESKY && op->coarsest != DPGMG_COARSEST_NONE &&
        op->coarsest != DPGMG_COARSEST_AUTO) ||
       (op->flags & ~(DPGMG_FLAG_EAGER | DPGMG_FLAG_TENSOR_CORES | DPGMG_FLAG_STORE_COARSE | DPGMG_FLAG_WARM_START |
-                     DPGMG_FLAG_CG_C128 | DPGMG_FLAG_FAULT_NOT_HPD | DPGMG_FLAG_FAULT_TC_WAIT)))
+                     DPGMG_FLAG_CG_C128 | DPGMG_FLAG_PATCH_FP64 | DPGMG_FLAG_FAULT_NOT_HPD |
+                     DPGMG_FLAG_FAULT_TC_WAIT)))
     return DPGMG_ERR_ARG;
   if ((op->flags & DPGMG_FLAG_STORE_COARSE) && pb->wavespeed) {
     const int64_t ne = (int64_t)pb->n[0] * pb->n[1] * pb->n[2];

@@ -79,12 +79,18 @@ __device__ __forceinline__ int64_t ecsr_find(const ECSRDev& A, int64_t row, int6
   return A.val_ptr[E] + r * (c1 - c0) + (lo - c0);
 }
 
-// block (e, s): slice s of element e's entries (the slices of one element are disjoint)
-__global__ void k_ecsr_add(ECSRDev A, const double2* E, const int64_t* dofs, int64_t nel, int nloc, int64_t e0,
+__device__ __forceinline__ double2 widen(double2 a) { return a; }
+__device__ __forceinline__ double2 widen(float2 a) { return make_double2(a.x, a.y); }   // exact
+
+// block (e, s): slice s of element e's entries (the slices of one element are
+// disjoint); TE = double2, or float2 for the mixed path's complex64 macro
+// element matrices (widened exactly)
+template <class TE>
+__global__ void k_ecsr_add(ECSRDev A, const TE* E, const int64_t* dofs, int64_t nel, int nloc, int64_t e0,
                            int n0, int n1, int color) {
   const int64_t e = blockIdx.x;
   if (elem_color(e0 + e, n0, n1) != color) return;
-  const double2* Ee = E + e * (size_t)nloc * nloc;
+  const TE* Ee = E + e * (size_t)nloc * nloc;
   const int64_t* g = dofs + e * nloc;
   for (int q = blockIdx.y * blockDim.x + threadIdx.x; q < nloc * nloc; q += gridDim.y * blockDim.x) {
     int i = q / nloc, j = q % nloc;
@@ -92,21 +98,27 @@ __global__ void k_ecsr_add(ECSRDev A, const double2* E, const int64_t* dofs, int
     if (gi < 0 || gj < 0) continue;
     int64_t pos = ecsr_find(A, gi, gj);
     if (pos < 0) continue;
-    const double2 v = Ee[q];
+    const double2 v = widen(Ee[q]);
     double2& o = A.v64[pos];
     o = make_double2(o.x + v.x, o.y + v.y);
   }
 }
 
-void ecsr_add_elements(ECSRDev& D, const double2* E, const int64_t* dofs, int64_t nel, int nloc, int64_t e0,
+template <class TE>
+static void ecsr_add_t(ECSRDev& D, const TE* E, const int64_t* dofs, int64_t nel, int nloc, int64_t e0,
                        const int ext[3], cudaStream_t st) {
   if (nel == 0) return;
   // one colour holds ~nel / 8 elements: slices of ~2048 entries per block keep the passes wide
   const unsigned slices = (unsigned)std::max<int64_t>(1, std::min<int64_t>(64, ((int64_t)nloc * nloc + 2047) / 2048));
   for (int c = 0; c < 8; ++c) {
-    k_ecsr_add<<<dim3((unsigned)nel, slices), 256, 0, st>>>(D, E, dofs, nel, nloc, e0, ext[0], ext[1], c);
+    k_ecsr_add<TE><<<dim3((unsigned)nel, slices), 256, 0, st>>>(D, E, dofs, nel, nloc, e0, ext[0], ext[1], c);
     DPG_CHECK_LAUNCH();
   }
+}
+
+void ecsr_add_elements(ECSRDev& D, const double2* E, const int64_t* dofs, int64_t nel, int nloc, int64_t e0,
+                       const int ext[3], cudaStream_t st) {
+  ecsr_add_t<double2>(D, E, dofs, nel, nloc, e0, ext, st);
 }
 
 std::vector<std::vector<int64_t>> element_groups(const MeshL& m) {
@@ -137,7 +149,24 @@ __global__ void k_p_restrict(const double2* Ef, double2* Ec, const int32_t* sel,
   }
 }
 
+// Mixed path: patch blocks gathered as complex64 and factored in FP32 (the
+// V-cycle's precision), unless DPGMG_FLAG_PATCH_FP64 asks for FP64 factors
+// rounded to complex64 afterwards.
+static bool patches_fp32(const SystemImpl& S) {
+  return S.op.precision == DPGMG_PREC_MIXED && !(S.op.flags & DPGMG_FLAG_PATCH_FP64);
+}
+// Mixed path: macro condensation and restriction in complex64 (same option).
+// With stored coarse operators the coarse element matrices come from the
+// element stage; the macro operators and transfers are still complex64.
+static bool macro_fp32(const SystemImpl& S) { return patches_fp32(S); }
+
 // ------------------------------------------------------------ h-transition
+// C = double2 (FP64 path), or float2 on the mixed path: every output of the
+// macro condensation (macro element matrices, transfer blocks Y and A_II^-1,
+// restricted coarse element matrices) feeds only the V-cycle, which runs in
+// complex64 there; the fine element matrices are rounded on load and the
+// outputs that are stored in FP64 (coarse element matrices) are widened.
+template <class C>
 struct MacroArgs {
   int nS, nI, nlf, nlc;
   int64_t K0;
@@ -146,23 +175,28 @@ struct MacroArgs {
   const int32_t* child_map;   // [8][nlf]
   int nf0, nf1;               // fine mesh extents x, y
   int nc0, nc1;               // coarse mesh extents x, y
-  const double2* IK;          // [nS][nlc] (real values)
-  double2* AK;                // scratch [chunk][(nS+nI)^2]
-  double2* T1;                // scratch [chunk][nS][nlc]
-  double2* MK;                // out [chunk][nS][nS]
-  double2* Y;                 // out [nK][nI][nS]
-  double2* Ai;                // out [nK][nI][nI]
-  double2* Ec;                // out [nK][nlc][nlc]
+  const C* IK;                // [nS][nlc] (real values)
+  C* AK;                      // scratch [chunk][(nS+nI)^2]
+  C* T1;                      // scratch [chunk][nS][nlc]
+  C* MK;                      // out [chunk][nS][nS]
+  C* Y;                       // out [nK][nI][nS]
+  C* Ai;                      // out [nK][nI][nI]
+  C* Ec;                      // scratch [chunk][nlc][nlc] (C = float2), or null: written to EcOut directly
+  double2* EcOut;             // out [nK][nlc][nlc]
   int* info;
 };
 
-__global__ void __launch_bounds__(CTA_THREADS) k_macro(MacroArgs a) {
-  extern __shared__ double2 sh2[];
+template <class C>
+__global__ void __launch_bounds__(CTA_THREADS) k_macro(MacroArgs<C> a) {
+  extern __shared__ unsigned char shm[];
+  C* sh2 = reinterpret_cast<C*>(shm);
+  using O = Ops<C>;
+  using R = typename O::R;
   const int64_t lk = blockIdx.x;
   const int64_t K = a.K0 + lk;
   const int nS = a.nS, nI = a.nI, n = nS + nI;
-  double2* AK = a.AK + lk * (size_t)n * n;
-  for (int64_t q = threadIdx.x; q < (int64_t)n * n; q += blockDim.x) AK[q] = make_double2(0, 0);
+  C* AK = a.AK + lk * (size_t)n * n;
+  for (int64_t q = threadIdx.x; q < (int64_t)n * n; q += blockDim.x) AK[q] = O::zero();
   __syncthreads();
   int kc[3];
   kc[0] = (int)(K % a.nc0);
@@ -177,52 +211,101 @@ __global__ void __launch_bounds__(CTA_THREADS) k_macro(MacroArgs a) {
     for (int q = threadIdx.x; q < a.nlf * a.nlf; q += blockDim.x) {
       int i = q / a.nlf, j = q % a.nlf;
       if (g[i] < 0 || g[j] < 0) continue;
-      double2& t = AK[(size_t)cm[i] * n + cm[j]];
-      t.x += E[q].x;
-      t.y += E[q].y;
+      C& t = AK[(size_t)cm[i] * n + cm[j]];
+      const double2 v = E[q];
+      t = O::add(t, O::mk((R)v.x, (R)v.y));
     }
     __syncthreads();
   }
   // Cholesky of A_II (trailing block), Y = A_II^-1 A_IS (in place of A_IS)
-  double2* AII = AK + (size_t)nS * n + nS;
-  int info = cta_potrf<double2>(AII, nI, n, sh2);
+  C* AII = AK + (size_t)nS * n + nS;
+  int info = cta_potrf<C>(AII, nI, n, sh2);
   if (threadIdx.x == 0 && info) atomicOr(a.info, 4);
-  double2* AIS = AK + (size_t)nS * n;
-  cta_trsm_lower<double2, double2>(AII, nI, n, AIS, nS, n, reinterpret_cast<char*>(sh2));
-  cta_trsm_lower_h<double2>(AII, nI, n, AIS, nS, n, reinterpret_cast<char*>(sh2));
+  C* AIS = AK + (size_t)nS * n;
+  cta_trsm_lower<C, C>(AII, nI, n, AIS, nS, n, reinterpret_cast<char*>(sh2));
+  cta_trsm_lower_h<C>(AII, nI, n, AIS, nS, n, reinterpret_cast<char*>(sh2));
   // M^K = A_SS - A_SI Y
-  double2* MK = a.MK + lk * (size_t)nS * nS;
+  C* MK = a.MK + lk * (size_t)nS * nS;
   for (int q = threadIdx.x; q < nS * nS; q += blockDim.x) MK[q] = AK[(size_t)(q / nS) * n + (q % nS)];
   __syncthreads();
-  cta_gemm<double2>(false, nS, nS, nI, -1.0, AK + nS, n, AIS, n, 1.0, MK, nS, sh2);
+  cta_gemm<C>(false, nS, nS, nI, R(-1), AK + nS, n, AIS, n, R(1), MK, nS, sh2);
   // store Y and A_II^-1
-  double2* Y = a.Y + K * (size_t)nI * nS;
+  C* Y = a.Y + K * (size_t)nI * nS;
   for (int q = threadIdx.x; q < nI * nS; q += blockDim.x) Y[q] = AIS[(size_t)(q / nS) * n + (q % nS)];
-  double2* Ai = a.Ai + K * (size_t)nI * nI;
-  for (int q = threadIdx.x; q < nI * nI; q += blockDim.x)
-    Ai[q] = (q / nI == q % nI) ? make_double2(1, 0) : make_double2(0, 0);
+  C* Ai = a.Ai + K * (size_t)nI * nI;
+  for (int q = threadIdx.x; q < nI * nI; q += blockDim.x) Ai[q] = (q / nI == q % nI) ? O::from_re(R(1)) : O::zero();
   __syncthreads();
-  cta_trsm_lower<double2, double2>(AII, nI, n, Ai, nI, nI, reinterpret_cast<char*>(sh2));
-  cta_trsm_lower_h<double2>(AII, nI, n, Ai, nI, nI, reinterpret_cast<char*>(sh2));
+  cta_trsm_lower<C, C>(AII, nI, n, Ai, nI, nI, reinterpret_cast<char*>(sh2));
+  cta_trsm_lower_h<C>(AII, nI, n, Ai, nI, nI, reinterpret_cast<char*>(sh2));
   // restriction: E_c = I_K^T (M^K I_K)
-  double2* T1 = a.T1 + lk * (size_t)nS * a.nlc;
-  cta_gemm<double2>(false, nS, a.nlc, nS, 1.0, MK, nS, a.IK, a.nlc, 0.0, T1, a.nlc, sh2);
-  double2* Ec = a.Ec + K * (size_t)a.nlc * a.nlc;
-  cta_gemm<double2>(true, a.nlc, a.nlc, nS, 1.0, a.IK, a.nlc, T1, a.nlc, 0.0, Ec, a.nlc, sh2);
+  C* T1 = a.T1 + lk * (size_t)nS * a.nlc;
+  cta_gemm<C>(false, nS, a.nlc, nS, R(1), MK, nS, a.IK, a.nlc, R(0), T1, a.nlc, sh2);
+  double2* Eo = a.EcOut + K * (size_t)a.nlc * a.nlc;
+  if constexpr (sizeof(C) == sizeof(double2)) {
+    cta_gemm<C>(true, a.nlc, a.nlc, nS, R(1), a.IK, a.nlc, T1, a.nlc, R(0), reinterpret_cast<C*>(Eo), a.nlc, sh2);
+  } else {
+    C* Ec = a.Ec + lk * (size_t)a.nlc * a.nlc;
+    cta_gemm<C>(true, a.nlc, a.nlc, nS, R(1), a.IK, a.nlc, T1, a.nlc, R(0), Ec, a.nlc, sh2);
+    __syncthreads();
+    for (int q = threadIdx.x; q < a.nlc * a.nlc; q += blockDim.x) Eo[q] = widen(Ec[q]);
+  }
+}
+
+template <class C>
+static void macro_condense(SystemImpl& S, Level& F, Level& C_, const MacroHost& M, const int32_t* cmap, int* dinfo,
+                           C* Y, C* Ai, cudaStream_t st) {
+  Alloc& A = S.mem;
+  std::vector<C> ik(M.IK.size());
+  for (size_t i = 0; i < ik.size(); ++i) {
+    ik[i].x = (typename Ops<C>::R)M.IK[i];
+    ik[i].y = 0;
+  }
+  C* dIK = upload(A, ik, st);
+  const int n = F.nS + F.nI;
+  int64_t chunk = std::min<int64_t>(F.nK, 2048);
+  C* AK = A.arr<C>((size_t)chunk * n * n);
+  C* T1 = A.arr<C>((size_t)chunk * F.nS * C_.nloc);
+  C* MK = A.arr<C>((size_t)chunk * F.nS * F.nS);
+  C* Ec = sizeof(C) == sizeof(double2) ? nullptr : A.arr<C>((size_t)chunk * C_.nloc * C_.nloc);
+  MacroArgs<C> a{};
+  a.nS = F.nS; a.nI = F.nI; a.nlf = F.nloc; a.nlc = C_.nloc;
+  a.Ef = F.E; a.fdofs = F.dofs; a.child_map = cmap;
+  a.nf0 = F.mesh.n[0]; a.nf1 = F.mesh.n[1];
+  a.nc0 = C_.mesh.n[0]; a.nc1 = C_.mesh.n[1];
+  a.IK = dIK; a.AK = AK; a.T1 = T1; a.MK = MK;
+  a.Y = Y; a.Ai = Ai; a.Ec = Ec; a.EcOut = C_.E; a.info = dinfo;
+  const size_t sm = (size_t)(NB * NB + 2 * TL * NB) * sizeof(C) + 64;
+  DPG_CUDA(cudaFuncSetAttribute(k_macro<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+  for (int64_t K0 = 0; K0 < F.nK; K0 += chunk) {
+    a.K0 = K0;
+    int nb = (int)std::min<int64_t>(chunk, F.nK - K0);
+    k_macro<C><<<nb, CTA_THREADS, sm, st>>>(a);
+    DPG_CHECK_LAUNCH();
+    ecsr_add_t<C>(F.A, MK, F.S_glob + K0 * F.nS, nb, F.nS, K0, C_.mesh.n, st);
+  }
+  A.release(AK);   // stream-ordered frees: after the launches above
+  A.release(T1);
+  A.release(MK);
+  if (Ec) A.release(Ec);
+  A.release(dIK);
 }
 
 // ------------------------------------------------------------------ patches
-__global__ void k_patch_gather(ECSRDev A, const int64_t* ptr, const int32_t* dofs, const int64_t* vptr,
-                               double2* out, int64_t j0) {
+// Patch block R_j A R_j^T, read from the operator's FP64 values; C = float2
+// rounds every entry to complex64 (the mixed path factors in FP32).
+template <class C>
+__global__ void k_patch_gather(ECSRDev A, const int64_t* ptr, const int32_t* dofs, const int64_t* vptr, C* out,
+                               int64_t j0) {
   const int64_t j = j0 + blockIdx.x;
   const int64_t b = ptr[j];
   const int n = (int)(ptr[j + 1] - b);
   const int ld = (int)patch_ld(n);
-  double2* M = out + vptr[j];
+  C* M = out + vptr[j];
   for (int q = threadIdx.x; q < n * ld; q += blockDim.x) {
     int r = q / ld, c = q % ld;
     int64_t pos = c < n ? ecsr_find(A, dofs[b + r], dofs[b + c]) : -1;
-    M[q] = pos >= 0 ? A.v64[pos] : make_double2(0, 0);
+    const double2 v = pos >= 0 ? A.v64[pos] : make_double2(0, 0);
+    M[q] = Ops<C>::mk((typename Ops<C>::R)v.x, (typename Ops<C>::R)v.y);
   }
 }
 
@@ -230,8 +313,9 @@ __global__ void k_patch_gather(ECSRDev A, const int64_t* ptr, const int32_t* dof
 // u-hat DOFs carry 1.  rot(v, a, b) = conj(beta_a) v beta_b and its inverse
 // unrot(x, a, b) = beta_a x conj(beta_b); multiplying by +-i only swaps
 // components, so both are exact.
-__device__ __forceinline__ double2 mul_i(double2 v, int s) {   // v * (i)^s, s in {-1, 0, 1}
-  return s == 0 ? v : (s > 0 ? make_double2(-v.y, v.x) : make_double2(v.y, -v.x));
+template <class C>
+__device__ __forceinline__ C mul_i(C v, int s) {   // v * (i)^s, s in {-1, 0, 1}
+  return s == 0 ? v : (s > 0 ? Ops<C>::mk(-v.y, v.x) : Ops<C>::mk(v.y, -v.x));
 }
 
 // In place: M (n x n) -> M^-1 via Cholesky in the scratch copy W.
@@ -272,43 +356,39 @@ __global__ void __launch_bounds__(CTA_THREADS) k_patch_invert(const int64_t* ptr
   const int ld = (int)patch_ld(n);   // stored row length; column n (if any) is padding, left 0
   C* M = vals + vptr[j];
   C* W = scratch + soff[j0 + slot];
+  using R = typename Ops<C>::R;
   bool cplx = false;
-  if (sizeof(C) == sizeof(double2)) {
-    for (int q = threadIdx.x; q < n * n; q += blockDim.x) {
-      const int r = q / n, c = q % n;
-      const int sr = pdofs[b + r] < offU ? 1 : 0, sc = pdofs[b + c] < offU ? 1 : 0;
-      const double2 v = mul_i(*reinterpret_cast<const double2*>(M + (size_t)r * ld + c), sc - sr);
-      if (v.y != 0.0) cplx = true;
-    }
-  } else {
-    cplx = true;
+  for (int q = threadIdx.x; q < n * n; q += blockDim.x) {
+    const int r = q / n, c = q % n;
+    const int sr = pdofs[b + r] < offU ? 1 : 0, sc = pdofs[b + c] < offU ? 1 : 0;
+    const C v = mul_i(M[(size_t)r * ld + c], sc - sr);
+    if (v.y != R(0)) cplx = true;
   }
   if (!__syncthreads_or(cplx)) {
-    double* Wr = reinterpret_cast<double*>(W);
-    double* Mr = reinterpret_cast<double*>(M);   // L^-1 (n x n, row length n) in the block's storage
-    double* shr = reinterpret_cast<double*>(shraw);
+    R* Wr = reinterpret_cast<R*>(W);
+    R* Mr = reinterpret_cast<R*>(M);   // L^-1 (n x n, row length n) in the block's storage
+    R* shr = reinterpret_cast<R*>(shraw);
     for (int q = threadIdx.x; q < n * n; q += blockDim.x) {
       const int r = q / n, c = q % n;
       if (!tm.own_row(r / TL)) continue;
       const int sr = pdofs[b + r] < offU ? 1 : 0, sc = pdofs[b + c] < offU ? 1 : 0;
-      Wr[q] = mul_i(*reinterpret_cast<const double2*>(M + (size_t)r * ld + c), sc - sr).x;
+      Wr[q] = mul_i(M[(size_t)r * ld + c], sc - sr).x;
     }
     tm.sync();   // every CTA has read M before any overwrites it
-    int inf = cta_potrf<double, CL>(Wr, n, n, shr, tm);
+    int inf = cta_potrf<R, CL>(Wr, n, n, shr, tm);
     if (threadIdx.x == 0 && inf && tm.rank == 0) atomicOr(info, 8);
     for (int q = threadIdx.x; q < n * n; q += blockDim.x)
-      if (tm.own_row((q / n) / TL)) Mr[q] = (q / n == q % n) ? 1.0 : 0.0;
+      if (tm.own_row((q / n) / TL)) Mr[q] = (q / n == q % n) ? R(1) : R(0);
     tm.sync();
-    cta_trinv_lower<double, CL>(Wr, n, n, Mr, n, reinterpret_cast<char*>(shr), tm);
+    cta_trinv_lower<R, CL>(Wr, n, n, Mr, n, reinterpret_cast<char*>(shr), tm);
     tm.sync();
-    cta_herk_lower_tri<double, CL>(Mr, n, n, Wr, n, shr, tm);
+    cta_herk_lower_tri<R, CL>(Mr, n, n, Wr, n, shr, tm);
     tm.sync();
     for (int q = threadIdx.x; q < n * ld; q += blockDim.x) {
       const int r = q / ld, c = q % ld;
       if (!tm.own_row(r / TL)) continue;
       const int sr = pdofs[b + r] < offU ? 1 : 0, sc = c < n && pdofs[b + c] < offU ? 1 : 0;
-      *reinterpret_cast<double2*>(M + q) =
-          c < n ? mul_i(make_double2(tm.ld(&Wr[(size_t)r * n + c]), 0.0), sr - sc) : make_double2(0.0, 0.0);
+      M[q] = c < n ? mul_i(Ops<C>::mk(tm.ld(&Wr[(size_t)r * n + c]), R(0)), sr - sc) : Ops<C>::zero();
     }
     return;
   }
@@ -468,6 +548,7 @@ static void invert_patches(Alloc& A, PatchDev& D, const LevelPlan& lp, C* vals, 
   A.release(scratch);
 }
 
+
 static void setup_patches(SystemImpl& S, Level& F, const LevelPlan& lp, int* dinfo, cudaStream_t st) {
   Alloc& A = S.mem;
   const Patches& P = lp.P;
@@ -486,12 +567,20 @@ static void setup_patches(SystemImpl& S, Level& F, const LevelPlan& lp, int* din
   D.chunks = upload(A, lp.ch32, st);
   D.nchunks64 = (int64_t)lp.ch64.size();
   D.chunks64 = upload(A, lp.ch64, st);
+  if (patches_fp32(S)) {
+    // complex64 blocks, Cholesky, triangular inverse and L^-H L^-1 in FP32; the
+    // smoother and its damping estimate use exactly these inverses
+    D.inv32 = A.arr<float2>((size_t)std::max<int64_t>(D.nvals, 1));
+    k_patch_gather<float2><<<(unsigned)D.np, 256, 0, st>>>(F.A, D.ptr, D.dofs, D.val_ptr, D.inv32, 0);
+    DPG_CHECK_LAUNCH();
+    invert_patches<float2>(A, D, lp, D.inv32, F.mesh.offU, dinfo, st);
+    return;
+  }
   D.inv64 = A.arr<double2>((size_t)D.nvals);
-  k_patch_gather<<<(unsigned)D.np, 256, 0, st>>>(F.A, D.ptr, D.dofs, D.val_ptr, D.inv64, 0);
+  k_patch_gather<double2><<<(unsigned)D.np, 256, 0, st>>>(F.A, D.ptr, D.dofs, D.val_ptr, D.inv64, 0);
   DPG_CHECK_LAUNCH();
-  // Patch inverses are computed in FP64 on both paths; the mixed path rounds
-  // them to complex64 after theta is estimated (a complex64 factorisation of
-  // blocks with condition numbers up to ~5e4 perturbs the smoother by ~1e-3).
+  // FP64 inverses (FP64 path, or the mixed path under DPGMG_FLAG_PATCH_FP64,
+  // which rounds them to complex64 after theta is estimated)
   invert_patches<double2>(A, D, lp, D.inv64, F.mesh.offU, dinfo, st);
 }
 
@@ -651,36 +740,16 @@ void build_hierarchy(SystemImpl& S, cudaStream_t st) {
       F.sslots = upload(A, M.sslots, st);
       F.smask = upload(A, M.smask, st);
       int32_t* cmap = upload(A, M.child_map, st);
-      std::vector<double2> ik(M.IK.size());
-      for (size_t i = 0; i < ik.size(); ++i) ik[i] = make_double2(M.IK[i], 0.0);
-      double2* dIK = upload(A, ik, st);
-      F.Y64 = A.arr<double2>((size_t)F.nK * F.nI * F.nS);
-      F.Ai64 = A.arr<double2>((size_t)F.nK * F.nI * F.nI);
       assemble_ecsr(A, lp.E, F.A, st);
-      const int n = F.nS + F.nI;
-      int64_t chunk = std::min<int64_t>(F.nK, 2048);
-      double2* AK = A.arr<double2>((size_t)chunk * n * n);
-      double2* T1 = A.arr<double2>((size_t)chunk * F.nS * C.nloc);
-      double2* MK = A.arr<double2>((size_t)chunk * F.nS * F.nS);
-      MacroArgs a{};
-      a.nS = F.nS; a.nI = F.nI; a.nlf = F.nloc; a.nlc = C.nloc;
-      a.Ef = F.E; a.fdofs = F.dofs; a.child_map = cmap;
-      a.nf0 = F.mesh.n[0]; a.nf1 = F.mesh.n[1];
-      a.nc0 = C.mesh.n[0]; a.nc1 = C.mesh.n[1];
-      a.IK = dIK; a.AK = AK; a.T1 = T1; a.MK = MK;
-      a.Y = F.Y64; a.Ai = F.Ai64; a.Ec = C.E; a.info = dinfo;
-      const size_t sm = (size_t)(NB * NB + 2 * TL * NB) * sizeof(double2) + 64;
-      DPG_CUDA(cudaFuncSetAttribute(k_macro, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-      for (int64_t K0 = 0; K0 < F.nK; K0 += chunk) {
-        a.K0 = K0;
-        int nb = (int)std::min<int64_t>(chunk, F.nK - K0);
-        k_macro<<<nb, CTA_THREADS, sm, st>>>(a);
-        DPG_CHECK_LAUNCH();
-        ecsr_add_elements(F.A, MK, F.S_glob + K0 * F.nS, nb, F.nS, K0, C.mesh.n, st);
+      if (macro_fp32(S)) {
+        F.Y32 = A.arr<float2>((size_t)F.nK * F.nI * F.nS);
+        F.Ai32 = A.arr<float2>((size_t)F.nK * F.nI * F.nI);
+        macro_condense<float2>(S, F, C, M, cmap, dinfo, F.Y32, F.Ai32, st);
+      } else {
+        F.Y64 = A.arr<double2>((size_t)F.nK * F.nI * F.nS);
+        F.Ai64 = A.arr<double2>((size_t)F.nK * F.nI * F.nI);
+        macro_condense<double2>(S, F, C, M, cmap, dinfo, F.Y64, F.Ai64, st);
       }
-      A.release(AK);   // stream-ordered frees: after the launches above
-      A.release(T1);
-      A.release(MK);
     }
     if (S.op.flags & DPGMG_FLAG_STORE_COARSE) {
       // "stored" coarse operator (Sec. 3): the DPG system assembled directly on
@@ -706,10 +775,13 @@ void build_hierarchy(SystemImpl& S, cudaStream_t st) {
     PatchDev& Pd = F.P;
     const bool keep_split = l == L && F.kind == 1;
     float2* plo = nullptr;
-    if (!(S.op.theta > 0.0) && !(S.op.flags & DPGMG_FLAG_CG_C128)) {   // double-float estimate
-      Pd.inv32 = A.arr<float2>((size_t)std::max<int64_t>(Pd.nvals, 1));
-      plo = A.arr<float2>((size_t)std::max<int64_t>(Pd.nvals, 1));
-      split_df(Pd.inv64, Pd.inv32, plo, Pd.nvals, st);
+    const bool c128 = (S.op.flags & DPGMG_FLAG_CG_C128) != 0;
+    if (!(S.op.theta > 0.0) && !c128) {   // double-float estimate
+      if (!patches_fp32(S)) {               // FP64 inverses: high and low parts (FP32 ones are exact)
+        Pd.inv32 = A.arr<float2>((size_t)std::max<int64_t>(Pd.nvals, 1));
+        plo = A.arr<float2>((size_t)std::max<int64_t>(Pd.nvals, 1));
+        split_df(Pd.inv64, Pd.inv32, plo, Pd.nvals, st);
+      }
       if (!F.A.vlo) split_operator(A, F.A, st);
     }
     estimate_theta(S, l, dtheta + 2 * l, plo, st);
@@ -728,7 +800,7 @@ void build_hierarchy(SystemImpl& S, cudaStream_t st) {
     }
     if (mixed) {
       if (!F.A.v32) F.A.v32 = to_c64(A, F.A.v64, F.A.nnz, st);
-      if (kHalfStorageSmoother && Pd.max_n <= HALF_MAX_N) {
+      if (kHalfStorageSmoother && Pd.max_n <= HALF_MAX_N && Pd.inv64) {
         // complex64 Hermitian half storage: lower triangles packed by rows
         std::vector<int64_t> hp(Pd.np + 1, 0), pp(Pd.np + 1);
         DPG_CUDA(cudaMemcpyAsync(pp.data(), Pd.ptr, (Pd.np + 1) * sizeof(int64_t), cudaMemcpyDeviceToHost, st));
@@ -746,9 +818,9 @@ void build_hierarchy(SystemImpl& S, cudaStream_t st) {
       } else if (!Pd.inv32) {
         Pd.inv32 = to_c64(A, Pd.inv64, Pd.nvals, st);
       }
-      A.release(Pd.inv64);      // the mixed V-cycle only reads the complex64 copy (stream-ordered free)
+      if (Pd.inv64) A.release(Pd.inv64);   // the mixed V-cycle only reads the complex64 copy (stream-ordered free)
       Pd.inv64 = nullptr;
-      if (F.kind == 2) {
+      if (F.kind == 2 && !F.Y32) {
         F.Y32 = to_c64(A, F.Y64, F.nK * F.nI * F.nS, st);
         F.Ai32 = to_c64(A, F.Ai64, F.nK * F.nI * F.nI, st);
       }

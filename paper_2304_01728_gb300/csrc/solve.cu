@@ -478,11 +478,14 @@ void split_df(const double2* v, float2* hi, float2* lo, int64_t n, cudaStream_t 
 }
 
 // Double-float smoother product for the damping estimate: the patch inverses
-// as complex64 high and low parts (M = Mh + Ml), r in complex128 split into
-// FP32 pairs in shared memory; conj(M[k][a]) r_k with the error-free products
-// and sums of the CG operator.  One column per lane (32-column work items),
-// warp w takes rows k = w + 8 i with two accumulator pairs; the 8 warp
-// partials are combined in a fixed order and written in complex128.
+// as complex64 high and low parts (M = Mh + Ml; LO = false: Ml = 0, the
+// complex64 inverses of the mixed path's FP32 factorisation taken exactly),
+// r in complex128 split into FP32 pairs in shared memory; conj(M[k][a]) r_k
+// with the error-free products and sums of the CG operator.  One column per
+// lane (32-column work items), warp w takes rows k = w + 8 i with two
+// accumulator pairs; the 8 warp partials are combined in a fixed order and
+// written in complex128.
+template <bool LO>
 __global__ void __launch_bounds__(256) k_patch_apply_df(const int64_t* __restrict__ ptr, const int32_t* __restrict__ dofs,
                                                         const int64_t* __restrict__ vptr, const int2* __restrict__ chunks,
                                                         const float2* __restrict__ Mh, const float2* __restrict__ Ml,
@@ -506,12 +509,13 @@ __global__ void __launch_bounds__(256) k_patch_apply_df(const int64_t* __restric
   float rh0 = 0.f, rl0 = 0.f, ih0 = 0.f, il0 = 0.f, rh1 = 0.f, rl1 = 0.f, ih1 = 0.f, il1 = 0.f;
   if (a < n) {
     const float2* H = Mh + vptr[j] + a;
-    const float2* Lo = Ml + vptr[j] + a;
+    const float2* Lo = LO ? Ml + vptr[j] + a : nullptr;
     int k = w;
     float p, q;
     for (; k + 8 < n; k += 16) {
-      const float2 h0 = __ldcs(H + (int64_t)k * ld), l0 = __ldcs(Lo + (int64_t)k * ld);
-      const float2 h1 = __ldcs(H + (int64_t)(k + 8) * ld), l1 = __ldcs(Lo + (int64_t)(k + 8) * ld);
+      const float2 h0 = __ldcs(H + (int64_t)k * ld), l0 = LO ? __ldcs(Lo + (int64_t)k * ld) : make_float2(0.f, 0.f);
+      const float2 h1 = __ldcs(H + (int64_t)(k + 8) * ld);
+      const float2 l1 = LO ? __ldcs(Lo + (int64_t)(k + 8) * ld) : make_float2(0.f, 0.f);
       const float4 x0 = rj[k], x1 = rj[k + 8];
       // conj(m) x: re = m.x x.re + m.y x.im, im = m.x x.im - m.y x.re
       df_mul(h0.x, l0.x, x0.x, x0.y, p, q);
@@ -532,7 +536,7 @@ __global__ void __launch_bounds__(256) k_patch_apply_df(const int64_t* __restric
       df_add(ih1, il1, -p, -q);
     }
     if (k < n) {
-      const float2 h0 = __ldcs(H + (int64_t)k * ld), l0 = __ldcs(Lo + (int64_t)k * ld);
+      const float2 h0 = __ldcs(H + (int64_t)k * ld), l0 = LO ? __ldcs(Lo + (int64_t)k * ld) : make_float2(0.f, 0.f);
       const float4 x0 = rj[k];
       df_mul(h0.x, l0.x, x0.x, x0.y, p, q);
       df_add(rh0, rl0, p, q);
@@ -559,13 +563,19 @@ __global__ void __launch_bounds__(256) k_patch_apply_df(const int64_t* __restric
   }
 }
 
-// y = sum_j R_j^T A_jj^-1 R_j r with the double-float patch inverses (F.P.inv32 = high parts)
+// y = sum_j R_j^T A_jj^-1 R_j r with the double-float patch inverses (F.P.inv32 = high parts,
+// plo = low parts, or null for complex64 inverses taken exactly)
 static void smooth_df(const Level& F, const float2* plo, const double2* r, double2* y, double2* pbuf,
                       cudaStream_t st) {
   const PatchDev& P = F.P;
   const int64_t n = F.mesh.ndof;
   const size_t sm = (size_t)P.max_n * sizeof(float4) + 16;
-  k_patch_apply_df<<<(unsigned)P.nchunks, 256, sm, st>>>(P.ptr, P.dofs, P.val_ptr, P.chunks, P.inv32, plo, r, pbuf);
+  if (plo)
+    k_patch_apply_df<true><<<(unsigned)P.nchunks, 256, sm, st>>>(P.ptr, P.dofs, P.val_ptr, P.chunks, P.inv32, plo, r,
+                                                                  pbuf);
+  else
+    k_patch_apply_df<false><<<(unsigned)P.nchunks, 256, sm, st>>>(P.ptr, P.dofs, P.val_ptr, P.chunks, P.inv32,
+                                                                   nullptr, r, pbuf);
   DPG_CHECK_LAUNCH();
   k_slot_sum<double2, double2><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(P.slot_ptr, P.slots, pbuf, y, n, 1.0, 0);
   DPG_CHECK_LAUNCH();
@@ -1487,22 +1497,37 @@ __global__ void k_take_re(const double2* sc, int idx, double* out) { *out = sc[i
 
 double theta_from_rayleigh(double num, double den) { return 1.0 / (1.05 * (num / den)); }
 
-// lambda = (M x)^H (S M x) / (x^H M x) after 30 power iterations of S M, with
-// the operator and the patch inverses in double-float (complex64 high and low
-// parts of the FP64 values: products and sums carry ~48 bits, on the FP32
-// pipe) and FP64 vectors and dot products; out[0] = numerator, out[1] =
-// denominator (device), theta = 1 / (1.05 lambda).
-static void estimate_theta_df(SystemImpl& S, Level& F, const float2* plo, double* out, cudaStream_t st) {
+// lambda = (M x)^H (S M x) / (x^H M x) after 30 power iterations of S M from a
+// SplitMix64 vector on the smoothing space, with FP64 vectors and dot products;
+// out[0] = numerator, out[1] = denominator (device), theta = 1 / (1.05 lambda).
+//   operator M: double-float (complex64 high and low parts of the FP64 values,
+//     ~48-bit products and sums on the FP32 pipe), or complex128 on the FP64
+//     pipe under DPGMG_FLAG_CG_C128;
+//   smoother S: the FP64 patch inverses in double-float (high parts in
+//     P.inv32, low parts in plo), or complex128 under DPGMG_FLAG_CG_C128; on the
+//     mixed path with FP32 patch factors, the complex64 inverses the V-cycle
+//     applies, taken exactly (plo null), so theta damps the smoother in use.
+static void estimate_theta_fp(SystemImpl& S, Level& F, const float2* plo, double* out, cudaStream_t st) {
   const int64_t n = F.mesh.ndof;
+  const bool c128 = cg_c128(S);
+  const bool z_smooth = c128 && F.P.inv64;
   Alloc tmp;
   tmp.budget = (size_t)-1;
   tmp.stream = st;
   double2* x = tmp.arr<double2>((size_t)n);
   double2* y = tmp.arr<double2>((size_t)n);
   double2* t = tmp.arr<double2>((size_t)n);
-  float2* xh = tmp.arr<float2>((size_t)n);
-  float2* xl = tmp.arr<float2>((size_t)n);
+  float2* xh = c128 ? nullptr : tmp.arr<float2>((size_t)n);
+  float2* xl = c128 ? nullptr : tmp.arr<float2>((size_t)n);
   double2* pbuf = tmp.arr<double2>((size_t)std::max<int64_t>(F.P.scratch_entries(), 1));
+  auto op = [&](const double2* v, double2* o) {
+    if (c128) spmv<double2>(F.A, F.A.v64, v, nullptr, o, 0, st);
+    else spmv_df(F.A, v, nullptr, o, 0, xh, xl, st);
+  };
+  auto sm = [&](const double2* v, double2* o) {
+    if (z_smooth) smooth<double2>(F, v, o, 1.0, 0, pbuf, st);
+    else smooth_df(F, plo, v, o, pbuf, st);
+  };
   WS W;
   W.part = tmp.arr<double2>(RED_BLOCKS);
   W.sc = tmp.arr<double2>(SC_COUNT);
@@ -1512,58 +1537,19 @@ static void estimate_theta_df(SystemImpl& S, Level& F, const float2* plo, double
   k_scale<double2><<<RED_BLOCKS, 256, 0, st>>>(x, n, W.sc, SC_RR);
   DPG_CHECK_LAUNCH();
   for (int k = 0; k < 30; ++k) {
-    spmv_df(F.A, x, nullptr, t, 0, xh, xl, st);
-    smooth_df(F, plo, t, y, pbuf, st);
+    op(x, t);
+    sm(t, y);
     dot_t<double2>(W, y, y, n, 1, st);
     k_scale<double2><<<RED_BLOCKS, 256, 0, st>>>(y, n, W.sc, SC_RR);
     DPG_CHECK_LAUNCH();
     std::swap(x, y);
   }
-  spmv_df(F.A, x, nullptr, t, 0, xh, xl, st);   // M x
-  smooth_df(F, plo, t, y, pbuf, st);            // S M x
+  op(x, t);                                     // M x
+  sm(t, y);                                     // S M x
   dot_t<double2>(W, t, y, n, 3, st);            // (M x)^H (S M x)
   k_take_re<<<1, 1, 0, st>>>(W.sc, SC_RHO, out);
   DPG_CHECK_LAUNCH();
   dot_t<double2>(W, x, t, n, 3, st);            // x^H M x
-  k_take_re<<<1, 1, 0, st>>>(W.sc, SC_RHO, out + 1);
-  DPG_CHECK_LAUNCH();
-  W.part = nullptr;
-  W.sc = nullptr;
-}
-
-// The same iteration in complex128 on the FP64 pipe (DPGMG_FLAG_CG_C128): the
-// level operator's FP64 values and the FP64 patch inverses.
-static void estimate_theta_z(SystemImpl& S, Level& F, double* out, cudaStream_t st) {
-  const int64_t n = F.mesh.ndof;
-  Alloc tmp;
-  tmp.budget = (size_t)-1;
-  tmp.stream = st;
-  double2* x = tmp.arr<double2>((size_t)n);
-  double2* y = tmp.arr<double2>((size_t)n);
-  double2* t = tmp.arr<double2>((size_t)n);
-  double2* pbuf = tmp.arr<double2>((size_t)std::max<int64_t>(F.P.scratch_entries(), 1));
-  WS W;
-  W.part = tmp.arr<double2>(RED_BLOCKS);
-  W.sc = tmp.arr<double2>(SC_COUNT);
-  k_start_vector<double2><<<nblk(n), 256, 0, st>>>(x, n, F.P.slot_ptr);
-  DPG_CHECK_LAUNCH();
-  dot_t<double2>(W, x, x, n, 1, st);
-  k_scale<double2><<<RED_BLOCKS, 256, 0, st>>>(x, n, W.sc, SC_RR);
-  DPG_CHECK_LAUNCH();
-  for (int k = 0; k < 30; ++k) {
-    spmv<double2>(F.A, F.A.v64, x, nullptr, t, 0, st);
-    smooth<double2>(F, t, y, 1.0, 0, pbuf, st);
-    dot_t<double2>(W, y, y, n, 1, st);
-    k_scale<double2><<<RED_BLOCKS, 256, 0, st>>>(y, n, W.sc, SC_RR);
-    DPG_CHECK_LAUNCH();
-    std::swap(x, y);
-  }
-  spmv<double2>(F.A, F.A.v64, x, nullptr, t, 0, st);   // M x
-  smooth<double2>(F, t, y, 1.0, 0, pbuf, st);           // S M x
-  dot_t<double2>(W, t, y, n, 3, st);
-  k_take_re<<<1, 1, 0, st>>>(W.sc, SC_RHO, out);
-  DPG_CHECK_LAUNCH();
-  dot_t<double2>(W, x, t, n, 3, st);
   k_take_re<<<1, 1, 0, st>>>(W.sc, SC_RHO, out + 1);
   DPG_CHECK_LAUNCH();
   W.part = nullptr;
@@ -1577,12 +1563,7 @@ void estimate_theta(SystemImpl& S, int l, double* rayleigh, const float2* plo, c
     F.theta = S.op.theta;
     return;
   }
-  if (cg_c128(S)) {
-    estimate_theta_z(S, F, rayleigh, st);
-    return;
-  }
-  // the same double-float estimate on both paths (the operators' FP64 values)
-  estimate_theta_df(S, F, plo, rayleigh, st);
+  estimate_theta_fp(S, F, plo, rayleigh, st);
 }
 
 // ------------------------------------------------------------ introspection

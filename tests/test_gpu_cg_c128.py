@@ -7,7 +7,7 @@ flag applies it in complex128 on the FP64 pipe and also runs the damping
 estimate in FP64, so that with the FP64 V-cycle every step is complex128
 (the 4^3, p = 2 workload's "complex128 throughout").  Both forms are checked
 against the oracle: the operator at 1e-11 (1e-13 for complex128), theta at
-1e-9, the solution at the parity bar of 1e-7 with the iteration count within
+1e-9 (1e-4 on the mixed path, whose patch factors are FP32), the solution at the parity bar of 1e-7 with the iteration count within
 10%; the relative L2 error of each form against the oracle is printed.
 """
 import numpy as np
@@ -16,7 +16,7 @@ import pytest
 from oracle.solver import mg_pcg
 from paper_2304_01728_gb300 import dpgmg as D
 from paper_2304_01728_gb300 import workloads
-from tests.oracle_adapter import oracle_system, rand_vec, rel
+from tests.oracle_adapter import MIXED_THETA_TOL, oracle_system, rand_vec, rel
 
 pytestmark = pytest.mark.gpu
 
@@ -40,8 +40,9 @@ def test_cg_operator_forms_against_oracle(c1_oracle, precision, flags):
         y = D.dpgmg_apply(s.h, s.s, D.OP_AFULL, L, x, A.shape[0])
         err_op = rel(y, A @ x)
         assert err_op < (1e-13 if flags else 1e-11), err_op
+        th_tol = 1e-9 if precision == "fp64" else MIXED_THETA_TOL   # mixed: FP32 patch factors
         for l in range(1, L + 1):
-            assert abs(s.level(l).theta - levels[l].theta) < 1e-9 * levels[l].theta
+            assert abs(s.level(l).theta - levels[l].theta) < th_tol * levels[l].theta
         xs, f, st, code = s.solve()
     err = rel(xs, x_ref)
     print("CG operator %s, %s V-cycle: operator error %.2e, solution error %.2e, iterations %d (oracle %d), "

@@ -174,5 +174,11 @@ def test_element_class_reuse_matches_full_pipeline(n, p, prec, layers, monkeypat
     assert g1 < 0.5 * g0, (g1, g0)   # the classes were used
     for a, b in zip(m0, m1):
         assert rel(b[0], a[0]) < 1e-13 and rel(b[1], a[1]) < 1e-11
-    assert i1 == i0
-    assert rel(x1, x0) < 1e-9 and rel(f1, f0) < 1e-9
+    if prec == "fp64":
+        assert i1 == i0
+        assert rel(x1, x0) < 1e-9 and rel(f1, f0) < 1e-9
+    else:
+        # complex64 patch blocks rounded from operators that agree to ~1e-13 and
+        # factored in FP32: the preconditioners may differ in a few entries
+        assert abs(i1 - i0) <= 1
+        assert rel(x1, x0) < 1e-7 and rel(f1, f0) < 1e-7

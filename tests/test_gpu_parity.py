@@ -14,7 +14,7 @@ from oracle.solver import mg_pcg, vcycle
 from oracle.traces import field_dofs, trace_dofs
 from paper_2304_01728_gb300 import dpgmg as D
 from paper_2304_01728_gb300 import workloads
-from tests.oracle_adapter import oracle_system, rand_vec, rel
+from tests.oracle_adapter import MIXED_VCYCLE_TOL, oracle_system, rand_vec, rel
 
 pytestmark = pytest.mark.gpu
 
@@ -217,7 +217,7 @@ def test_mixed_precision_c1(c1):
         n = c1.A.shape[0]
         v = rand_vec(n, 9)
         y = D.dpgmg_apply(s.h, s.s, D.OP_VCYCLE, c1.L, v, n)
-        assert rel(y, vcycle(c1.levels, c1.L, v)) < 1e-5
+        assert rel(y, vcycle(c1.levels, c1.L, v)) < MIXED_VCYCLE_TOL
         x, f, st, code = s.solve()
     assert code == D.DPGMG_OK and st.true_relres <= 1e-8 * 10
     assert abs(st.iters - it_ref) <= max(1, 0.1 * it_ref)

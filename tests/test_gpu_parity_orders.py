@@ -12,9 +12,10 @@ layered-medium workloads, against the FP64 oracle, through the C ABI.
 
 FP64 path: every operator at 1e-11 relative (different but exact evaluations
 of the same integrals), the solution at the parity bar of 1e-7 relative L2
-with the iteration count within 10%.  Mixed path: the V-cycle within 1e-5
-(complex64 rounding of the stored operators and patch inverses), solution and
-iterations at the same bar.
+with the iteration count within 10%.  Mixed path: the V-cycle and theta
+within 1e-4 (complex64 storage and FP32 patch factorisations and macro
+condensations, see tests/oracle_adapter.py), solution and iterations at the
+same bar.
 """
 import numpy as np
 import pytest
@@ -23,7 +24,7 @@ from oracle.hierarchy import smoother
 from oracle.solver import mg_pcg, vcycle
 from paper_2304_01728_gb300 import dpgmg as D
 from paper_2304_01728_gb300 import workloads
-from tests.oracle_adapter import oracle_system, rand_vec, rel
+from tests.oracle_adapter import MIXED_THETA_TOL, MIXED_VCYCLE_TOL, oracle_system, rand_vec, rel
 
 pytestmark = pytest.mark.gpu
 
@@ -164,13 +165,17 @@ def test_mixed_path(name, cases):
     ok = dict(c.ok, precision="mixed", tol=1e-8)
     x_ref, it_ref, _ = mg_pcg(c.levels, c.A, c.b, tol=ok["tol"])
     with D.Solver(c.pk, **ok) as s:
+        ev, et = [], []
         for l in range(1, c.L + 1):
             n = c.levels[l].mesh.n_dof
             v = rand_vec(n, 50 + l)
             y = D.dpgmg_apply(s.h, s.s, D.OP_VCYCLE, l, v, n)
-            assert rel(y, vcycle(c.levels, l, v)) < 1e-5, (l, rel(y, vcycle(c.levels, l, v)))
+            ev.append(rel(y, vcycle(c.levels, l, v)))
+            et.append(abs(s.level(l).theta - c.levels[l].theta) / c.levels[l].theta)
         x, f, st, code = s.solve()
-    print("%s mixed: iterations %d (oracle %d), solution error %.2e" % (name, st.iters, it_ref, rel(x, x_ref)))
+    print("%s mixed: V-cycle error per level %s, theta error %s, iterations %d (oracle %d), solution error %.2e"
+          % (name, ["%.1e" % v for v in ev], ["%.1e" % v for v in et], st.iters, it_ref, rel(x, x_ref)))
+    assert max(ev) < MIXED_VCYCLE_TOL and max(et) < MIXED_THETA_TOL
     assert code == D.DPGMG_OK and st.true_relres <= 10 * ok["tol"]
     assert abs(st.iters - it_ref) <= max(1, 0.1 * it_ref), (st.iters, it_ref)
     assert rel(x, x_ref) < 1e-7
