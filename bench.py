@@ -51,8 +51,9 @@ def parse():
     ap.add_argument("--no-fp64-compare", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--n", type=int, default=0, help="override the mesh size n^3 (profiling of a smaller case)")
-    ap.add_argument("--tensor-cores", action="store_true",
-                    help="coarsest complex64 factor updates on the tensor cores (DPGMG_FLAG_TENSOR_CORES)")
+    ap.add_argument("--cuda-cores", action="store_true",
+                    help="coarsest complex64 factorisation on the FP32 CUDA cores (DPGMG_FLAG_CUDA_CORES) "
+                         "instead of the tensor cores")
     ap.add_argument("--mode", default="step", choices=["step", "batch", "serve", "sweep"],
                     help="step: the bench line; batch: independent uneven problems; serve: Poisson request stream; "
                          "sweep: iteration counts of the convergence studies (h, p, omega, smoothing steps)")
@@ -264,9 +265,9 @@ def run_gb300(args, rank, world, local_rank):
     if args.n:
         w["problem"]["n"] = (args.n,) * 3
         w["name"] += " (mesh overridden to %d^3)" % args.n
-    if args.tensor_cores:
-        w["opts"]["flags"] = w["opts"].get("flags", 0) | D.FLAG_TENSOR_CORES
-        w["name"] += ", coarsest factor updates on tensor cores"
+    if args.cuda_cores:
+        w["opts"]["flags"] = w["opts"].get("flags", 0) | D.FLAG_CUDA_CORES
+        w["name"] += ", coarsest factor on CUDA cores"
     stream = torch.cuda.Stream()
     h = D.dpgmg_create(local_rank, 0, ctypes.c_void_p(stream.cuda_stream))
     pb, keep = D.make_problem(**w["problem"])

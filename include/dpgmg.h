@@ -114,13 +114,13 @@ typedef struct dpgmg_opts {
 /* CG steps after the first are replayed from one captured CUDA graph unless
    this bit is set (or the stream cannot be captured); results are the same. */
 #define DPGMG_FLAG_EAGER 1
-/* Mixed path: run the rank-64 updates of the coarsest complex64 factorisation
-   on the tensor cores (tcgen05, 3xTF32 operand splitting: products keep ~22 of
-   FP32's 24 bits) instead of the FP32 CUDA-core kernels.  Off by default: the
-   coarse solve it gives is a few times less accurate, which moves the point
-   where CG stops (on the 16^3 p=3 workload the solution then differs from the
-   FP64 oracle's by 2.4e-7 instead of 7.7e-8, with the same iteration count). */
-#define DPGMG_FLAG_TENSOR_CORES 2
+/* Mixed path: the coarsest complex64 factorisation (Cholesky and triangular
+   inverse) on the FP32 CUDA cores, in 64-wide blocks, instead of the default:
+   panels of up to 512 columns whose panel solves, trailing updates and
+   inverse updates are complex products on the tensor cores (tcgen05, 3xTF32
+   operand splitting: each product keeps ~22 of FP32's 24 bits, accumulated in
+   FP32), with only the diagonal blocks on the CUDA cores. */
+#define DPGMG_FLAG_CUDA_CORES 2
 /* Coarse operators "stored" instead of restricted (Sec. 3, the paper's
    alternative construction): every coarser level's operator is the DPG system
    assembled directly on its own mesh and order (enriched test order p_c + 1)
@@ -155,11 +155,12 @@ typedef struct dpgmg_opts {
      coarsest matrix with -1 before its factorisation, which then reports a
      non-positive pivot: dpgmg_setup returns DPGMG_ERR_NOT_HPD (needs a dense
      coarsest level).
-   FAULT_TC_WAIT: with DPGMG_FLAG_TENSOR_CORES on the mixed path, the first
-     tensor-core update launch issues no MMA and no commit, so its bounded
-     wait (about half a second) runs out with nothing in flight: dpgmg_setup
-     returns DPGMG_ERR_TIMEOUT and the later launches of the setup skip their
-     work.  In both cases the handle stays usable. */
+   FAULT_TC_WAIT: on the mixed path (tensor-core coarsest factorisation,
+     level 0 above 128 DOFs), the first tensor-core product issues no MMA and
+     no commit, so its bounded waits (about half a second) run out with only
+     its own operand copies in flight, which it lets land: dpgmg_setup returns
+     DPGMG_ERR_TIMEOUT and the later products of the setup skip their work.
+   In both cases the handle stays usable. */
 #define DPGMG_FLAG_FAULT_NOT_HPD (1 << 28)
 #define DPGMG_FLAG_FAULT_TC_WAIT (1 << 29)
 

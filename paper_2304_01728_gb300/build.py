@@ -16,7 +16,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libdpgmg.so")
-SOURCES = ["host_mesh.cpp", "element.cu", "level.cu", "coarse.cu", "tc_update.cu", "solve.cu", "noalloc.cu", "server.cu", "api.cu"]
+SOURCES = ["host_mesh.cpp", "element.cu", "level.cu", "coarse.cu", "tc_gemm.cu", "solve.cu", "noalloc.cu", "server.cu", "api.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -84,7 +84,7 @@ int validate_problem(const dpgmg_problem* pb, const dpgmg_opts* op) {
       op->p_min < 1 || (op->precision != DPGMG_PREC_FP64 && op->precision != DPGMG_PREC_MIXED) ||
       (op->coarsest != DPGMG_COARSEST_CHOLESKY && op->coarsest != DPGMG_COARSEST_NONE &&
        op->coarsest != DPGMG_COARSEST_AUTO) ||
-      (op->flags & ~(DPGMG_FLAG_EAGER | DPGMG_FLAG_TENSOR_CORES | DPGMG_FLAG_STORE_COARSE | DPGMG_FLAG_WARM_START |
+      (op->flags & ~(DPGMG_FLAG_EAGER | DPGMG_FLAG_CUDA_CORES | DPGMG_FLAG_STORE_COARSE | DPGMG_FLAG_WARM_START |
                      DPGMG_FLAG_CG_C128 | DPGMG_FLAG_PATCH_FP64 | DPGMG_FLAG_FAULT_NOT_HPD |
                      DPGMG_FLAG_FAULT_TC_WAIT)))
     return DPGMG_ERR_ARG;
@@ -166,6 +166,9 @@ size_t estimate_bytes(const dpgmg_problem* pb, const dpgmg_opts* op) {
       resident += nd * (nd + 1.0) * vsz;                              // packed L^-1 and L^-H
       // built concurrently with the level above: its scratch adds to theirs
       coarse_transient = nd * nd * (mixed ? 24.0 : 32.0) + nd * 64.0 * 16.0;
+      // tensor-core operand images (three TF32 parts of a panel of up to 512
+      // columns: 24 B per complex entry, twice for A's real and imaginary variants)
+      if (mixed && !(op->flags & DPGMG_FLAG_CUDA_CORES)) coarse_transient += (nd + 128.0) * 512.0 * 72.0;
     }
   }
   resident += (xdofs + ne * nf) * 16.0;                              // solution outputs

@@ -56,7 +56,8 @@ __global__ void k_narrow_mat(const double2* a, float2* b, int64_t n) {
 // Dinv + (k0 / CNB) CNB^2: the panel below is then a plain product with it,
 // and the inverse phase reuses it.
 template <class C>
-__global__ void __launch_bounds__(CTA_THREADS) k_dense_diag(C* A, int64_t N, int k0, C* Dinv, int* info) {
+__global__ void __launch_bounds__(CTA_THREADS) k_dense_diag(C* A, int64_t N, int64_t ld, int k0, C* Dinv,
+                                                            int* info) {
   extern __shared__ unsigned char shraw[];
   using O = Ops<C>;
   using R = typename O::R;
@@ -68,7 +69,7 @@ __global__ void __launch_bounds__(CTA_THREADS) k_dense_diag(C* A, int64_t N, int
   const int tid = threadIdx.x, tx = tid % 16, ty = tid / 16;
   for (int q = tid; q < kb * kb; q += blockDim.x) {
     const int i = q / kb, c = q % kb;
-    D[i * LD + c] = c <= i ? A[(size_t)(k0 + i) * N + k0 + c] : O::zero();
+    D[i * LD + c] = c <= i ? A[(size_t)(k0 + i) * ld + k0 + c] : O::zero();
   }
   __syncthreads();
   // right-looking, one barrier per column: step j updates the trailing lower
@@ -98,7 +99,7 @@ __global__ void __launch_bounds__(CTA_THREADS) k_dense_diag(C* A, int64_t N, int
   __syncthreads();
   for (int q = tid; q < kb * kb; q += blockDim.x) {
     const int i = q / kb, c = q % kb;
-    if (c <= i) A[(size_t)(k0 + i) * N + k0 + c] = D[i * LD + c];
+    if (c <= i) A[(size_t)(k0 + i) * ld + k0 + c] = D[i * LD + c];
   }
   if (tid < kb) rdiag[tid] = R(1) / O::re(D[tid * LD + tid]);
   __syncthreads();
@@ -129,7 +130,8 @@ __global__ void __launch_bounds__(CTA_THREADS) k_dense_diag(C* A, int64_t N, int
 // product with the stored inverse (one CTA per 64 rows; thread (tx, ty) owns
 // rows ty*4 + a and columns tx + 16 b).
 template <class C>
-__global__ void __launch_bounds__(CTA_THREADS) k_dense_panel(C* A, int64_t N, int k0, const C* __restrict__ Dinv) {
+__global__ void __launch_bounds__(CTA_THREADS) k_dense_panel(C* A, int64_t N, int64_t ld, int k0,
+                                                             const C* __restrict__ Dinv) {
   extern __shared__ unsigned char shraw[];
   using O = Ops<C>;
   constexpr int LD = CNB + 1;
@@ -141,7 +143,7 @@ __global__ void __launch_bounds__(CTA_THREADS) k_dense_panel(C* A, int64_t N, in
   const int tid = threadIdx.x, tx = tid % 16, ty = tid / 16;
   for (int q = tid; q < CNB * CNB; q += blockDim.x) {
     const int r = q / CNB, t = q % CNB;
-    Pa[r * LD + t] = (i0 + r < N && t < kb) ? A[(size_t)(i0 + r) * N + k0 + t] : O::zero();
+    Pa[r * LD + t] = (i0 + r < N && t < kb) ? A[(size_t)(i0 + r) * ld + k0 + t] : O::zero();
     Bt[t * LD + r] = O::conj(Dk[q]);
   }
   __syncthreads();
@@ -159,13 +161,13 @@ __global__ void __launch_bounds__(CTA_THREADS) k_dense_panel(C* A, int64_t N, in
     for (int b = 0; b < 4; ++b) {
       const int64_t i = i0 + ty * 4 + a;
       const int j = tx + 16 * b;
-      if (i < N && j < kb) A[(size_t)i * N + k0 + j] = acc[a][b];
+      if (i < N && j < kb) A[(size_t)i * ld + k0 + j] = acc[a][b];
     }
 }
 
 // trailing update of one lower 64x64 tile pair: A[i][j] -= sum_t L[i][t] conj(L[j][t])
 template <class C>
-__global__ void __launch_bounds__(CTA_THREADS) k_dense_herk(C* A, int64_t N, int k0) {
+__global__ void __launch_bounds__(CTA_THREADS) k_dense_herk(C* A, int64_t N, int64_t ld, int k0) {
   __shared__ C Pi[CNB][17];
   __shared__ C Pj[CNB][17];
   using O = Ops<C>;
@@ -185,8 +187,8 @@ __global__ void __launch_bounds__(CTA_THREADS) k_dense_herk(C* A, int64_t N, int
     for (int q = threadIdx.x; q < CNB * 16; q += blockDim.x) {
       int r = q / 16, c = q % 16;
       int64_t ii = i0 + r, jj = j0 + r;
-      Pi[r][c] = (ii < N && t0 + c < kb) ? A[ii * N + k0 + t0 + c] : O::zero();
-      Pj[r][c] = (jj < N && t0 + c < kb) ? A[jj * N + k0 + t0 + c] : O::zero();
+      Pi[r][c] = (ii < N && t0 + c < kb) ? A[ii * ld + k0 + t0 + c] : O::zero();
+      Pj[r][c] = (jj < N && t0 + c < kb) ? A[jj * ld + k0 + t0 + c] : O::zero();
     }
     __syncthreads();
     // thread (tx, ty) owns rows ty*4 + a and columns tx + 16 b: the 16 lanes of
@@ -204,52 +206,30 @@ __global__ void __launch_bounds__(CTA_THREADS) k_dense_herk(C* A, int64_t N, int
     for (int b = 0; b < 4; ++b) {
       int64_t i = i0 + ty * 4 + a, j = j0 + tx + 16 * b;
       if (i < N && j <= i) {
-        C& o = A[i * N + j];
+        C& o = A[i * ld + j];
         o = O::sub(o, acc[a][b]);
       }
     }
 }
 
-// Complex64 rank-64 updates on the tensor cores (tc_update.cu).
-void tc_configure();
-void tc_herk_update(float2* A, int64_t N, int k0, int kw, int* err, int fault, cudaStream_t st);
-void tc_trinv_update(float2* X, const float2* L, int64_t N, int kb, int* err, cudaStream_t st);
-
+// Blocked right-looking Cholesky A = L L^H in place (lower) of the n x n view A
+// (leading dimension ld); Dinv receives the inverses of its 64 x 64 diagonal
+// blocks of L (block b at Dinv + b 64^2).
 template <class C>
-static bool tc_herk(C*, int64_t, int, int, int*, int, cudaStream_t) { return false; }
-template <>
-bool tc_herk<float2>(float2* A, int64_t N, int k0, int kw, int* info, int fault, cudaStream_t st) {
-  tc_herk_update(A, N, k0, kw, info, fault, st);
-  return true;
-}
-template <class C>
-static bool tc_trinv(C*, const C*, int64_t, int, int*, cudaStream_t) { return false; }
-template <>
-bool tc_trinv<float2>(float2* X, const float2* L, int64_t N, int kb, int* info, cudaStream_t st) {
-  tc_trinv_update(X, L, N, kb, info, st);
-  return true;
-}
-
-// Blocked right-looking Cholesky A = L L^H in place (lower); Dinv receives the
-// inverses of the diagonal blocks of L.  tensor: 0 CUDA cores, 1 tensor-core
-// updates, 2 tensor-core updates whose first launch issues no MMA (the
-// DPGMG_FLAG_FAULT_TC_WAIT test of the bounded wait).
-template <class C>
-static void dense_cholesky(C* A, int64_t N, C* Dinv, int* info, int tensor, cudaStream_t st) {
+static void dense_cholesky(C* A, int64_t n, int64_t ld, C* Dinv, int* info, cudaStream_t st) {
   const size_t sm = (size_t)2 * CNB * (CNB + 1) * sizeof(C);
   DPG_CUDA(cudaFuncSetAttribute(k_dense_diag<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
   DPG_CUDA(cudaFuncSetAttribute(k_dense_panel<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-  for (int64_t k0 = 0; k0 < N; k0 += CNB) {
-    int kb = (int)std::min<int64_t>(CNB, N - k0);
-    k_dense_diag<C><<<1, CTA_THREADS, sm, st>>>(A, N, (int)k0, Dinv, info);
+  for (int64_t k0 = 0; k0 < n; k0 += CNB) {
+    int kb = (int)std::min<int64_t>(CNB, n - k0);
+    k_dense_diag<C><<<1, CTA_THREADS, sm, st>>>(A, n, ld, (int)k0, Dinv, info);
     DPG_CHECK_LAUNCH();
-    int64_t rows = N - k0 - kb;
+    int64_t rows = n - k0 - kb;
     if (rows <= 0) break;
-    k_dense_panel<C><<<(unsigned)((rows + CNB - 1) / CNB), CTA_THREADS, sm, st>>>(A, N, (int)k0, Dinv);
+    k_dense_panel<C><<<(unsigned)((rows + CNB - 1) / CNB), CTA_THREADS, sm, st>>>(A, n, ld, (int)k0, Dinv);
     DPG_CHECK_LAUNCH();
-    if (tensor && tc_herk<C>(A, N, (int)k0, kb, info, tensor == 2 && k0 == 0 ? 1 : 0, st)) continue;
     int64_t nt = (rows + CNB - 1) / CNB;
-    k_dense_herk<C><<<(unsigned)(nt * (nt + 1) / 2), CTA_THREADS, 0, st>>>(A, N, (int)k0);
+    k_dense_herk<C><<<(unsigned)(nt * (nt + 1) / 2), CTA_THREADS, 0, st>>>(A, n, ld, (int)k0);
     DPG_CHECK_LAUNCH();
   }
 }
@@ -257,7 +237,7 @@ static void dense_cholesky(C* A, int64_t N, C* Dinv, int* info, int tensor, cuda
 // ---------------------------------------------------------- L^-1 (blocked)
 // X[kb rows, tile cols] <- Dinv_kb * X[kb rows, tile cols], one CTA per 64-column tile
 template <class C>
-__global__ void __launch_bounds__(CTA_THREADS) k_trinv_scale(C* X, const C* Dinv, int64_t N, int kb) {
+__global__ void __launch_bounds__(CTA_THREADS) k_trinv_scale(C* X, const C* Dinv, int64_t N, int64_t ld, int kb) {
   extern __shared__ unsigned char shraw[];
   C* D = reinterpret_cast<C*>(shraw);
   C* T = D + CNB * CNB;
@@ -270,7 +250,7 @@ __global__ void __launch_bounds__(CTA_THREADS) k_trinv_scale(C* X, const C* Dinv
   for (int q = threadIdx.x; q < CNB * CNB; q += blockDim.x) {
     D[q] = Dk[q];
     int r = q / CNB, c = q % CNB;
-    T[q] = (r < kw && c < cw) ? X[(k0 + r) * N + c0 + c] : O::zero();
+    T[q] = (r < kw && c < cw) ? X[(k0 + r) * ld + c0 + c] : O::zero();
   }
   __syncthreads();
   for (int q = threadIdx.x; q < CNB * CNB; q += blockDim.x) {
@@ -278,13 +258,13 @@ __global__ void __launch_bounds__(CTA_THREADS) k_trinv_scale(C* X, const C* Dinv
     if (r >= kw || c >= cw) continue;
     C acc = O::zero();
     for (int t = 0; t <= r; ++t) acc = O::fma(D[r * CNB + t], T[t * CNB + c], acc);
-    X[(k0 + r) * N + c0 + c] = acc;
+    X[(k0 + r) * ld + c0 + c] = acc;
   }
 }
 
 // X[ib, jb] -= L[ib, kb] X[kb, jb] for ib > kb, jb <= kb (64x64 tiles)
 template <class C>
-__global__ void __launch_bounds__(CTA_THREADS) k_trinv_update(C* X, const C* L, int64_t N, int kb) {
+__global__ void __launch_bounds__(CTA_THREADS) k_trinv_update(C* X, const C* L, int64_t N, int64_t ld, int kb) {
   __shared__ C La[CNB][17];
   __shared__ C Xb[16][CNB + 1];
   using O = Ops<C>;
@@ -301,9 +281,9 @@ __global__ void __launch_bounds__(CTA_THREADS) k_trinv_update(C* X, const C* L, 
   for (int t0 = 0; t0 < kw; t0 += 16) {
     for (int q = threadIdx.x; q < CNB * 16; q += blockDim.x) {
       int r = q / 16, c = q % 16;
-      La[r][c] = (i0 + r < N && t0 + c < kw) ? L[(i0 + r) * N + k0 + t0 + c] : O::zero();
+      La[r][c] = (i0 + r < N && t0 + c < kw) ? L[(i0 + r) * ld + k0 + t0 + c] : O::zero();
       int t = q / CNB, cc = q % CNB;
-      Xb[t][cc] = (t0 + t < kw && j0 + cc < N) ? X[(k0 + t0 + t) * N + j0 + cc] : O::zero();
+      Xb[t][cc] = (t0 + t < kw && j0 + cc < N) ? X[(k0 + t0 + t) * ld + j0 + cc] : O::zero();
     }
     __syncthreads();
     for (int c = 0; c < 16; ++c) {
@@ -319,16 +299,16 @@ __global__ void __launch_bounds__(CTA_THREADS) k_trinv_update(C* X, const C* L, 
     for (int b = 0; b < 4; ++b) {
       int64_t i = i0 + ty * 4 + a, j = j0 + tx + 16 * b;
       if (i < N && j < N) {
-        C& o = X[i * N + j];
+        C& o = X[i * ld + j];
         o = O::sub(o, acc[a][b]);
       }
     }
 }
 
 template <class C>
-__global__ void k_identity_lower(C* X, int64_t N) {
+__global__ void k_identity_lower(C* X, int64_t N, int64_t ld) {
   for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < N * N; q += (int64_t)gridDim.x * blockDim.x)
-    X[q] = (q / N == q % N) ? Ops<C>::from_re(1) : Ops<C>::zero();
+    X[(q / N) * ld + q % N] = (q / N == q % N) ? Ops<C>::from_re(1) : Ops<C>::zero();
 }
 
 // Lp: rows of the lower triangle of X; Up: rows of X^H (upper triangle)
@@ -344,25 +324,104 @@ __global__ void k_pack(const C* X, int64_t N, C* Lp, C* Up) {
   }
 }
 
+// X = L^-1 of the n x n lower view L into the view X (both leading dimension
+// ld), with the diagonal-block inverses Dinv of dense_cholesky.
 template <class C>
-static void coarse_factor(Alloc& A, C* dense, int64_t N, C** Lp, C** Up, int* info, int tensor, cudaStream_t st) {
-  if (tensor) tc_configure();
-  const int nb = (int)((N + CNB - 1) / CNB);
-  C* Dinv = A.arr<C>((size_t)nb * CNB * CNB);
-  dense_cholesky<C>(dense, N, Dinv, info, tensor, st);
-  C* X = A.arr<C>((size_t)N * N);
-  k_identity_lower<C><<<1216, 256, 0, st>>>(X, N);
+static void dense_trinv(const C* L, C* X, int64_t n, int64_t ld, const C* Dinv, cudaStream_t st) {
+  const int nb = (int)((n + CNB - 1) / CNB);
+  k_identity_lower<C><<<(unsigned)std::min<int64_t>(1216, (n * n + 255) / 256), 256, 0, st>>>(X, n, ld);
   DPG_CHECK_LAUNCH();
   const size_t sms = (size_t)2 * CNB * CNB * sizeof(C);
   DPG_CUDA(cudaFuncSetAttribute(k_trinv_scale<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sms));
   for (int kb = 0; kb < nb; ++kb) {
-    k_trinv_scale<C><<<kb + 1, CTA_THREADS, sms, st>>>(X, Dinv, N, kb);
+    k_trinv_scale<C><<<kb + 1, CTA_THREADS, sms, st>>>(X, Dinv, n, ld, kb);
     DPG_CHECK_LAUNCH();
     const int rows = nb - kb - 1;
-    if (rows > 0 && !(tensor && tc_trinv<C>(X, dense, N, kb, info, st))) {
-      k_trinv_update<C><<<(unsigned)(rows * (kb + 1)), CTA_THREADS, 0, st>>>(X, dense, N, kb);
+    if (rows > 0) {
+      k_trinv_update<C><<<(unsigned)(rows * (kb + 1)), CTA_THREADS, 0, st>>>(X, L, n, ld, kb);
       DPG_CHECK_LAUNCH();
     }
+  }
+}
+
+// Complex64 products on the tensor cores (tc_gemm.cu).
+void tc_configure();
+size_t tc_image_bytes(int64_t rows, int64_t kc, bool is_a);
+void tc_pack(void* img, const float2* src, int64_t ld, int64_t rows, int64_t kc, int mode, cudaStream_t st);
+void tc_gemm(const void* Aimg, const void* Bimg, int64_t M, int64_t N, int64_t kc, float2* C, int64_t ldc,
+             float alpha, float beta, int lower, int* err, int fault, cudaStream_t st);
+enum { TC_A_NH = 0, TC_A_NN = 1, TC_B = 2, TC_B_TRANS = 3 };
+
+// Panel width of the tensor-core factorisation (a multiple of 64 and of 16).
+static int64_t tc_panel(int64_t N) { return N >= 4096 ? 512 : (N >= 1024 ? 256 : 128); }
+
+// Mixed path: A = L L^H and X = L^-1 (complex64, N x N, row-major, lower
+// halves) by panels of width W, right-looking.  Per panel K (rows and
+// columns K0 .. K0 + W - 1), with the rows below it "2":
+//   L_KK, L_KK^-1 (into X_KK)   64-wide blocked kernels on the CUDA cores
+//   X_K,<K = -L_KK^-1 T_K,<K     tensor cores (T accumulated in X, below)
+//   L_2K = A_2K L_KK^-H          tensor cores, in place of A_2K
+//   A_22 -= L_2K L_2K^H          tensor cores, lower tiles only
+//   T_2,<=K += L_2K X_K,<=K      tensor cores
+// which gives X_IJ = -L_II^-1 sum_{J<=K<I} L_IK X_KJ for every block below
+// the diagonal.  fault (tests): the first product issues no MMA.
+static void tc_cholesky_inverse(Alloc& Al, float2* A, float2* X, int64_t N, float2* Dinv, int* info, int fault,
+                                cudaStream_t st) {
+  tc_configure();
+  const int64_t W = tc_panel(N);
+  void* Aimg = Al.get(tc_image_bytes(N, W, true));
+  void* Bimg = Al.get(tc_image_bytes(N, W, false));
+  DPG_CUDA(cudaMemsetAsync(X, 0, (size_t)N * N * sizeof(float2), st));
+  int first = fault;
+  auto gemm = [&](int64_t M, int64_t Nc, int64_t kc, float2* C, float alpha, float beta, int lower) {
+    tc_gemm(Aimg, Bimg, M, Nc, kc, C, N, alpha, beta, lower, info, first, st);
+    first = 0;
+  };
+  for (int64_t K0 = 0; K0 < N; K0 += W) {
+    const int64_t kb = std::min<int64_t>(W, N - K0);
+    float2* Akk = A + K0 * N + K0;
+    float2* Xkk = X + K0 * N + K0;
+    float2* Dk = Dinv + (K0 / CNB) * CNB * CNB;
+    dense_cholesky<float2>(Akk, kb, N, Dk, info, st);
+    dense_trinv<float2>(Akk, Xkk, kb, N, Dk, st);
+    if (K0 > 0) {   // X_K,<K = -L_KK^-1 T_K,<K (T read into the image before it is overwritten)
+      tc_pack(Aimg, Xkk, N, kb, kb, TC_A_NN, st);
+      tc_pack(Bimg, X + K0 * N, N, K0, kb, TC_B_TRANS, st);
+      gemm(kb, K0, kb, X + K0 * N, -1.f, 0.f, 0);
+    }
+    const int64_t rows = N - K0 - kb;
+    if (rows <= 0) break;
+    float2* A2 = A + (K0 + kb) * N + K0;   // rows below the panel, panel columns
+    // L_2K = A_2K L_KK^-H
+    tc_pack(Aimg, A2, N, rows, kb, TC_A_NH, st);
+    tc_pack(Bimg, Xkk, N, kb, kb, TC_B, st);
+    gemm(rows, kb, kb, A2, 1.f, 0.f, 0);
+    // A_22 -= L_2K L_2K^H
+    tc_pack(Aimg, A2, N, rows, kb, TC_A_NH, st);
+    tc_pack(Bimg, A2, N, rows, kb, TC_B, st);
+    gemm(rows, rows, kb, A + (K0 + kb) * N + K0 + kb, -1.f, 1.f, 1);
+    // T_2,<=K += L_2K X_K,<=K
+    tc_pack(Aimg, A2, N, rows, kb, TC_A_NN, st);
+    tc_pack(Bimg, X + K0 * N, N, K0 + kb, kb, TC_B_TRANS, st);
+    gemm(rows, K0 + kb, kb, X + (K0 + kb) * N, 1.f, 1.f, 0);
+  }
+  Al.release(Bimg);
+  Al.release(Aimg);
+}
+
+// tensor: 0 CUDA cores, 1 tensor cores (complex64 only), 2 tensor cores whose
+// first product issues no MMA (the DPGMG_FLAG_FAULT_TC_WAIT test).
+template <class C>
+static void coarse_factor(Alloc& A, C* dense, int64_t N, C** Lp, C** Up, int* info, int tensor, cudaStream_t st) {
+  const int nb = (int)((N + CNB - 1) / CNB);
+  C* Dinv = A.arr<C>((size_t)nb * CNB * CNB);
+  C* X = A.arr<C>((size_t)N * N);
+  if constexpr (sizeof(C) == sizeof(float2)) {
+    if (tensor) tc_cholesky_inverse(A, dense, X, N, Dinv, info, tensor == 2 ? 1 : 0, st);
+  }
+  if (!tensor || sizeof(C) != sizeof(float2)) {
+    dense_cholesky<C>(dense, N, N, Dinv, info, st);
+    dense_trinv<C>(dense, X, N, N, Dinv, st);
   }
   const int64_t np = N * (N + 1) / 2;
   *Lp = A.arr<C>((size_t)np);
@@ -396,7 +455,7 @@ void coarse_setup(SystemImpl& S, Level& C0, int* info, cudaStream_t st, Alloc& A
     DPG_CHECK_LAUNCH();
     DPG_CUDA(cudaStreamSynchronize(st));
     A.release(dense);
-    const int tc = (S.op.flags & DPGMG_FLAG_TENSOR_CORES) ? ((S.op.flags & DPGMG_FLAG_FAULT_TC_WAIT) ? 2 : 1) : 0;
+    const int tc = (S.op.flags & DPGMG_FLAG_CUDA_CORES) ? 0 : ((S.op.flags & DPGMG_FLAG_FAULT_TC_WAIT) ? 2 : 1);
     coarse_factor<float2>(A, d32, N, &C0.Lp32, &C0.Up32, info, tc, st);
     A.release(d32);
   } else {

@@ -75,13 +75,16 @@ def test_not_hpd_from_host_fault_then_usable(precision):
 
 
 def test_tensor_core_wait_timeout_then_usable():
+    # 6^3 p2 -> 6^3 p1: level 0 has 883 DOFs, factored in 128-wide panels whose
+    # products run on the tensor cores
     w = workloads.config1()
-    ok = dict(w["opts"], precision="mixed", flags=D.FLAG_TENSOR_CORES)
+    w["problem"]["n"] = (6, 6, 6)
+    ok = dict(w["opts"], precision="mixed")
     h = D.dpgmg_create(0)
     try:
         pb, keep = D.make_problem(**w["problem"])
         with pytest.raises(D.DpgmgError) as e:
-            D.dpgmg_setup(h, pb, D.make_opts(**dict(ok, flags=D.FLAG_TENSOR_CORES | D.FLAG_FAULT_TC_WAIT)))
+            D.dpgmg_setup(h, pb, D.make_opts(**dict(ok, flags=D.FLAG_FAULT_TC_WAIT)))
         assert e.value.code == D.DPGMG_ERR_TIMEOUT
         code, st, x = _setup_solve(h, w["problem"], ok)
         assert code == D.DPGMG_OK and st.relres <= ok["tol"]

@@ -275,10 +275,15 @@ def test_graph_replay_matches_eager(precision, tol):
 
 @pytest.mark.parametrize("n", [4, 6])
 def test_coarse_factor_on_tensor_cores(n):
-    """Mixed path: the complex64 coarsest factor built with tensor-core
-    (3xTF32) updates solves level 0 within a small factor of the accuracy of
-    the CUDA-core FP32 factor.  Level 0 has 269 (n = 4) and 883 (n = 6) DOFs:
-    several 64-wide tiles with a ragged last one."""
+    """Mixed path: the complex64 coarsest factor built by panels whose solves
+    and updates are tensor-core (3xTF32) products solves level 0 within a
+    small factor of the accuracy of the CUDA-core FP32 factor.  Level 0 has
+    269 (n = 4) and 883 (n = 6) DOFs: 128-wide panels (3 and 7 of them) with
+    ragged last panels, 64-row and 128-column product tiles with ragged
+    edges, lower-triangle tiles that cross the diagonal.  The 3xTF32 products
+    keep ~22 of FP32's 24 bits and accumulate in the tensor cores' FP32, so the
+    bar is an order of magnitude (16x) of the CUDA-core factor's error; the
+    end-to-end parity of the mixed path is checked by the solution tests."""
     import scipy.linalg as sla
     w = workloads.config1()
     pk = dict(w["problem"], n=(n, n, n))
@@ -288,13 +293,13 @@ def test_coarse_factor_on_tensor_cores(n):
     x = rand_vec(o0.mesh.n_dof, 7)
     y_ref = sla.cho_solve(o0.chol, x)
     y = {}
-    for flags in (0, D.FLAG_TENSOR_CORES):
+    for flags in (D.FLAG_CUDA_CORES, 0):
         with D.Solver(pk, **dict(ok, flags=flags)) as s:
             y[flags] = D.dpgmg_apply(s.h, s.s, D.OP_COARSE, 0, x, o0.mesh.n_dof)
-    e_cc, e_tc = rel(y[0], y_ref), rel(y[D.FLAG_TENSOR_CORES], y_ref)
+    e_cc, e_tc = rel(y[D.FLAG_CUDA_CORES], y_ref), rel(y[0], y_ref)
     print("coarse solve error: CUDA cores %.2e, tensor cores %.2e" % (e_cc, e_tc))
     assert e_cc < 1e-3 and e_tc < 1e-3, (e_tc, e_cc)
-    assert e_tc < 8 * e_cc + 1e-6, (e_tc, e_cc)
+    assert e_tc < 16 * e_cc + 1e-6, (e_tc, e_cc)
 
 
 @pytest.mark.parametrize("name", CASES)
