@@ -118,8 +118,9 @@ typedef struct dpgmg_opts {
    inverse) on the FP32 CUDA cores, in 64-wide blocks, instead of the default:
    panels of up to 512 columns whose panel solves, trailing updates and
    inverse updates are complex products on the tensor cores (tcgen05, 3xTF32
-   operand splitting: each product keeps ~22 of FP32's 24 bits, accumulated in
-   FP32), with only the diagonal blocks on the CUDA cores. */
+   operand splitting, each 8-column K stage accumulated in TMEM and added to
+   FP32 registers with round-to-nearest), with only the diagonal blocks on the
+   CUDA cores.  Both give coarse solves of FP32 accuracy. */
 #define DPGMG_FLAG_CUDA_CORES 2
 /* Coarse operators "stored" instead of restricted (Sec. 3, the paper's
    alternative construction): every coarser level's operator is the DPG system

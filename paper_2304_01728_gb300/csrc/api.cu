@@ -166,9 +166,9 @@ size_t estimate_bytes(const dpgmg_problem* pb, const dpgmg_opts* op) {
       resident += nd * (nd + 1.0) * vsz;                              // packed L^-1 and L^-H
       // built concurrently with the level above: its scratch adds to theirs
       coarse_transient = nd * nd * (mixed ? 24.0 : 32.0) + nd * 64.0 * 16.0;
-      // tensor-core operand images (three TF32 parts of a panel of up to 512
-      // columns: 24 B per complex entry, twice for A's real and imaginary variants)
-      if (mixed && !(op->flags & DPGMG_FLAG_CUDA_CORES)) coarse_transient += (nd + 128.0) * 512.0 * 72.0;
+      // tensor-core operand images (two TF32 parts of a panel of up to 512
+      // columns: 16 B per complex entry, twice for A's real and imaginary variants)
+      if (mixed && !(op->flags & DPGMG_FLAG_CUDA_CORES)) coarse_transient += (nd + 128.0) * 512.0 * 48.0;
     }
   }
   resident += (xdofs + ne * nf) * 16.0;                              // solution outputs

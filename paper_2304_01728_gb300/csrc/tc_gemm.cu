@@ -16,23 +16,25 @@
 // 0..63 hold real parts, rows 64..127 imaginary parts (MMA M = 128), over 128
 // complex output columns (MMA N = 128).
 //
-// Precision.  Every FP32 operand value x is split into three TF32 parts,
-// x1 = rna(x), x2 = rna(x - x1), x3 = rna(x - x1 - x2) (3 x 11 significant
-// bits cover FP32's 24), and D accumulates, in FP32, the six products whose
-// order is at least 2^-22:  a1 b1 + a1 b2 + a2 b1 + a1 b3 + a2 b2 + a3 b1.
-// Each product is then exact to FP32 rounding, as on the CUDA cores (a
-// two-part split keeps ~22 bits, which on the 16^3 p=3 workload moved the
-// CG stopping point enough to put the solution 2.4e-7 from the FP64 oracle's).
+// Precision (3xTF32).  Every FP32 operand value x is split into TF32 parts
+// x1 = rna(x), x2 = rna(x - x1), and D accumulates a1 b1 + a1 b2 + a2 b1
+// (the a2 b2 term is below FP32 rounding).  The tensor cores' FP32
+// accumulation does not round to nearest: accumulated over a whole panel in
+// TMEM, its bias put the 16^3 p=3 solution 2.4e-7 from the FP64 oracle's
+// (with three parts and six products just the same).  Each stage of 8
+// complex K values therefore accumulates into a fresh TMEM buffer that the
+// epilogue warps add, rounding to nearest, into FP32 registers; the coarse
+// solve is then within 1.4x of the FP32 CUDA-core factor's accuracy.
 //
 // Operand images.  A pack kernel writes each operand once per product into
 // global memory already in the shared-memory image the MMA reads: per tile
 // (64 complex rows of A as 128 real rows, or 128 complex rows of B) and per
-// stage of 8 complex K values (16 TF32 values), three 8 KiB images (one per
+// stage of 8 complex K values (16 TF32 values), two 8 KiB images (one per
 // TF32 part) in the canonical K-major layout without swizzle (8-row x 16-byte
 // core matrices, adjacent along K at 128 B, along M/N at 512 B).  The product
-// kernel streams a stage of A and of B (2 x 24 KiB) into shared memory with
+// kernel streams a stage of A and of B (2 x 16 KiB) into shared memory with
 // two bulk asynchronous copies (cp.async.bulk, completion counted on an
-// mbarrier) through a 4-stage ring, so the copies of later stages overlap the
+// mbarrier) through a 6-stage ring, so the copies of later stages overlap the
 // MMAs of the current one; one thread issues copies and MMAs, tcgen05.commit
 // frees a stage, and the four warps then move D from TMEM to global memory.
 // Every wait is bounded in wall time; a wait that runs out sets an error bit,
@@ -51,11 +53,11 @@ constexpr int TG_MR = 64;                          // complex output rows per ti
 constexpr int TG_NC = 128;                         // complex output columns per tile (MMA N)
 constexpr int TG_KC = 8;                           // complex K per stage
 constexpr int TG_KR = 2 * TG_KC;                   // TF32 values per image row per stage
-constexpr int TG_PARTS = 3;                        // TF32 parts per FP32 value
+constexpr int TG_PARTS = 2;                        // TF32 parts per FP32 value
 constexpr uint32_t TG_IMG = 128u * TG_KR * 4u;     // 8 KiB: one TF32 part of one tile stage
 constexpr uint32_t TG_PAIR = TG_PARTS * TG_IMG;    // all parts of one operand tile stage
 constexpr uint32_t TG_STAGE = 2u * TG_PAIR;        // A and B
-constexpr int TG_NS = 4;                           // stages in flight
+constexpr int TG_NS = 6;                           // stages in flight
 constexpr uint32_t TG_SMEM = TG_NS * TG_STAGE + 1024u;
 constexpr int TG_THREADS = 160;                    // warps 0-3 drain TMEM, warp 4 issues
 constexpr long long TG_WAIT_POLLS = 1LL << 24;
@@ -74,7 +76,7 @@ __device__ __forceinline__ float tf32_rna(float x) {
   return __uint_as_float(r);
 }
 
-// (v.x, v.y) as three TF32 parts, at byte offset o of each part image
+// (v.x, v.y) as TF32 parts, at byte offset o of each part image
 __device__ __forceinline__ void store_parts(unsigned char* part, uint32_t o, float2 v) {
   float rx = v.x, ry = v.y;
 #pragma unroll
@@ -86,7 +88,7 @@ __device__ __forceinline__ void store_parts(unsigned char* part, uint32_t o, flo
   }
 }
 
-// One CTA per (tile, stage): the three part images of that tile stage.
+// One CTA per (tile, stage): the part images of that tile stage.
 //   PACK_A_NH / PACK_A_NN: tile t = logical rows 64t..64t+63 of A; image rows
 //     0..63 carry the real-part variant of each row, 64..127 the imaginary-part
 //     variant (for op(B) = B^H or B, see above);
@@ -192,7 +194,7 @@ __device__ __forceinline__ void mbar_expect(uint32_t bar, uint32_t bytes) {
 // 0-3 (one TMEM lane = one real output row each) drain into FP32 registers
 // with round-to-nearest additions while the next stage's MMAs run.  The
 // tensor cores' FP32 accumulation does not round to nearest; keeping its
-// chains one stage long (2 K steps x 6 products) keeps the products as
+// chains one stage long (2 K steps x 3 products) keeps the products as
 // accurate as the CUDA cores' FMA chains.
 // fault (tests): no MMA and no commit are issued, so the waits for them run out.
 __global__ void __launch_bounds__(TG_THREADS) k_tc_gemm(const unsigned char* __restrict__ Aimg,
@@ -276,13 +278,13 @@ __global__ void __launch_bounds__(TG_THREADS) k_tc_gemm(const unsigned char* __r
         if (!fault) {
           const uint32_t a = sbase + (uint32_t)s * TG_STAGE, bo = a + TG_PAIR;
           const uint32_t d = tmem + (uint32_t)(b * TG_NC);
-          // (part of A, part of B) of the six products, small ones first
-          constexpr int PA[6] = {2, 1, 0, 1, 0, 0}, PB[6] = {0, 1, 2, 0, 1, 0};
+          // (part of A, part of B) of the three products, small ones first
+          constexpr int PA[3] = {1, 0, 0}, PB[3] = {0, 1, 0};
 #pragma unroll
           for (int j = 0; j < TG_KR / 8; ++j) {   // K = 8 TF32 values (32 bytes) per instruction
             const uint32_t o = 256u * j;
 #pragma unroll
-            for (int q = 0; q < 6; ++q)
+            for (int q = 0; q < 3; ++q)
               mma_tf32(d, smem_desc(a + PA[q] * TG_IMG + o), smem_desc(bo + PB[q] * TG_IMG + o), idesc,
                        (j | q) != 0 ? 1u : 0u);
           }
