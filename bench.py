@@ -4,8 +4,10 @@
 One step = one pass of the whole hot path through the C ABI: dpgmg_setup
 (batched element DPG work, assembly, hierarchy, patch factorisations,
 coarsest factor) + dpgmg_solve (PCG to relative residual 1e-8, field
-recovery) + dpgmg_release, on the 16^3, p = 3, omega = 16 pi unit-cube
-workload with a 3-level h/p V(1,1)-cycle.
+recovery) + dpgmg_release.  Default workload: the layered medium, the
+largest single-GPU configuration ([0,2]x[0,2]x[0,1], 32x32x16 hexahedra,
+p = 3, omega = 20 pi, 6 seeded layers, 4 levels p3 -> p2 -> h -> h, mixed
+V-cycle, FP64 CG); --config 2 runs the 16^3 unit cube instead.
 
 value  = DOF-iterations per second of the PCG phase (N_dof * iterations /
          PCG device time), summed over ranks; ms_per_step is the whole step.
@@ -14,11 +16,15 @@ e2e    = the same metric with the end-to-end time of setup + solve through the
 roofline: the finest-level smoother product kernel, timed live with CUDA
          events on the library's stream inside the timed steps.
 cpu_baseline: the FP64 oracle (test infrastructure) on a bounded sample of
-         the same workload (a 4^3-element sub-box of the 16^3 mesh around the
-         source, same h, p, omega, 3 levels), PCG phase only, one core.
+         the same workload (a sub-box of its mesh around the source with the
+         same h, p, omega, wavespeeds and hierarchy shape), PCG phase timed,
+         on one core and as one replica per host core.
+Extra keys: error of each precision option against the oracle's full-size
+solution (tests/golden), the 16^3 workload's numbers, and bounded
+serving/batching summaries.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
-       [--config 2] [--precision mixed|fp64]
+       [--config 2|3] [--precision mixed|fp64] [--no-extras]
 """
 import argparse
 import ctypes
@@ -45,11 +51,13 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--config", type=int, default=2, choices=[1, 2, 3])
+    ap.add_argument("--config", type=int, default=3, choices=[1, 2, 3])
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64-compare", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the extra keys (oracle errors per option, the 16^3 workload, serving/batch)")
     ap.add_argument("--n", type=int, default=0, help="override the mesh size n^3 (profiling of a smaller case)")
     ap.add_argument("--cuda-cores", action="store_true",
                     help="coarsest complex64 factorisation on the FP32 CUDA cores (DPGMG_FLAG_CUDA_CORES) "
@@ -64,6 +72,7 @@ def parse():
     ap.add_argument("--budget-gb", type=float, default=160.0, help="batch/serve: device-memory admission budget")
     ap.add_argument("--oracle-sample", action="store_true", help=argparse.SUPPRESS)
     ap.add_argument("--oracle-steps", type=int, default=1, help=argparse.SUPPRESS)
+    ap.add_argument("--oracle-all-cores", action="store_true", help=argparse.SUPPRESS)
     return ap.parse_args()
 
 
@@ -74,48 +83,88 @@ def workload(cfg, precision):
 
 
 # ------------------------------------------------------------------ oracle
-def oracle_sample_problem(w):
-    """A 4^3-element sub-box of the workload mesh that contains the source."""
+def oracle_sample_problem(w, cfg):
+    """A sub-box of the workload mesh around the source, with the same element
+    size, order, frequency, wavespeeds and hierarchy shape: 8x8x4 elements and
+    4 levels (p3 -> p2 -> h -> h) for the layered medium, 4^3 elements and 3
+    levels for the unit cube."""
     pk = dict(w["problem"])
     n = pk["n"]
     x0 = pk.get("x0", (0, 0, 0))
     x1 = pk.get("x1", (1, 1, 1))
     h = [(x1[d] - x0[d]) / n[d] for d in range(3)]
-    sub = [min(4, n[d]) for d in range(3)]
-    lo, hi = [], []
+    sub = [min(8, n[0]), min(8, n[1]), min(4, n[2])] if cfg == 3 else [min(4, n[d]) for d in range(3)]
+    lo, hi, start = [], [], []
     for d in range(3):
         c = int(round((pk["src_center"][d] - x0[d]) / h[d])) - sub[d] // 2
         c = max(0, min(n[d] - sub[d], c))
+        start.append(c)
         lo.append(x0[d] + c * h[d])
         hi.append(x0[d] + (c + sub[d]) * h[d])
     ws = pk.get("wavespeed")
     wsub = None
     if ws is not None:
-        wsub = []
-        for kz in range(sub[2]):
-            for ky in range(sub[1]):
-                for kx in range(sub[0]):
-                    ix = int(round((lo[0] - x0[0]) / h[0])) + kx
-                    iy = int(round((lo[1] - x0[1]) / h[1])) + ky
-                    iz = int(round((lo[2] - x0[2]) / h[2])) + kz
-                    wsub.append(ws[ix + n[0] * (iy + n[1] * iz)])
-    levels = w["opts"]["n_levels"]
+        wsub = [ws[(start[0] + kx) + n[0] * ((start[1] + ky) + n[1] * (start[2] + kz))]
+                for kz in range(sub[2]) for ky in range(sub[1]) for kx in range(sub[0])]
+    levels = min(w["opts"]["n_levels"], 4 if cfg == 3 else 3)
     return dict(n=tuple(sub), p=pk["p"], omega=pk["omega"], x0=tuple(lo), x1=tuple(hi), wavespeed=wsub,
-                src_center=pk["src_center"], src_width=pk["src_width"]), dict(w["opts"], n_levels=min(levels, 3))
+                src_center=pk["src_center"], src_width=pk["src_width"]), dict(w["opts"], n_levels=levels)
+
+
+_ORC = {}
+
+
+def _orc_init(pk):
+    from oracle.mesh import Mesh
+    from oracle.problem import GaussianSource
+    _ORC.update(pk=pk, mesh=Mesh(pk["n"], pk["p"], pk["x0"], pk["x1"]),
+                load=GaussianSource(pk["src_center"], pk["src_width"]))
+
+
+def _orc_elem(e):
+    """One element of the oracle's FineSystem, by the oracle's own functions."""
+    import numpy as np
+    from oracle.element import boundary_faces, condense, dpg_element
+    pk, m = _ORC["pk"], _ORC["mesh"]
+    bf = boundary_faces(m, e)
+    corner = m.x0 + np.asarray(m.elem_coord(e)) * m.h
+    c = 1.0 if pk["wavespeed"] is None else pk["wavespeed"][e]
+    K, F = dpg_element(m.p, m.h, corner, c, pk["omega"], bf, _ORC["load"])
+    Kc, Fc = condense(m.p, K, F, bf)
+    return e, Kc, Fc
+
+
+def cpu_model():
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith(("model name", "cpu part", "hardware")):
+                return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    import platform
+    return platform.processor() or platform.machine()
 
 
 def oracle_sample_run(args):
-    """Runs in a fresh single-threaded process: oracle setup (untimed), PCG (timed)."""
-    import numpy as np  # noqa: F401
-    from oracle.assembly import build_fine
+    """Runs in a fresh process without a GPU: the oracle's setup of the sample
+    (untimed; its element loop over a spawned process pool), then its PCG
+    phase timed on one core (--oracle-steps times), then, with
+    --oracle-all-cores, once in each of one forked single-threaded replica per
+    host core at the same time."""
+    import multiprocessing as mp
+    from oracle.assembly import FineSystem
     from oracle.hierarchy import build_hierarchy
-    from oracle.problem import GaussianSource
+    from oracle.mesh import Mesh
     from oracle.solver import mg_pcg
     w = workload(args.config, "fp64")
-    pk, ok = oracle_sample_problem(w)
+    pk, ok = oracle_sample_problem(w, args.config)
     t0 = time.perf_counter()
-    fs = build_fine(pk["n"], pk["p"], pk["omega"], wavespeed=pk["wavespeed"],
-                    load=GaussianSource(pk["src_center"], pk["src_width"]), x0=pk["x0"], x1=pk["x1"])
+    mesh = Mesh(pk["n"], pk["p"], pk["x0"], pk["x1"])
+    fs = FineSystem(mesh, pk["omega"], pk["wavespeed"], None, elements=[])
+    ncpu = os.cpu_count() or 1
+    with mp.get_context("spawn").Pool(min(ncpu, 32), initializer=_orc_init, initargs=(pk,)) as pool:
+        for e, Kc, Fc in pool.imap_unordered(_orc_elem, range(mesh.n_elem), chunksize=4):
+            fs.Kc[e], fs.Fc[e] = Kc, Fc
     A, b = fs.assemble()
     levels = build_hierarchy(fs.mesh, fs.Kc, fs.dofs, ok["n_levels"], ok["p_min"])
     t_setup = time.perf_counter() - t0
@@ -127,23 +176,64 @@ def oracle_sample_run(args):
     n = A.shape[0]
     tot_t = sum(r[0] for r in res)
     tot_di = sum(n * r[1] for r in res)
+    all_core = None
+    if args.oracle_all_cores and ncpu > 1 and hasattr(os, "fork"):
+        t1 = time.perf_counter()
+        pids = []
+        for _ in range(ncpu):
+            pid = os.fork()
+            if pid == 0:
+                try:
+                    mg_pcg(levels, A, b, tol=ok["tol"])
+                    os._exit(0)
+                except BaseException:
+                    os._exit(1)
+            pids.append(pid)
+        ok_all = all(os.waitpid(pid, 0)[1] == 0 for pid in pids)
+        wall = time.perf_counter() - t1
+        if ok_all:
+            all_core = dict(value=ncpu * n * res[-1][1] / wall, cores=ncpu, wall_s=wall)
     print(json.dumps(dict(value=tot_di / tot_t, n_dof=n, iters=res[-1][1], pcg_s=[r[0] for r in res],
-                          setup_s=t_setup, sample="%dx%dx%d-element sub-box [%s]-[%s] of the %s mesh (same h, p=%d, "
-                          "omega, source), %d levels, PCG phase only" % (
+                          setup_s=t_setup, all_core=all_core, nproc=ncpu, cpu_model=cpu_model(),
+                          sample="%dx%dx%d-element sub-box [%s]-[%s] of the %s mesh (same h, p=%d, omega, "
+                          "wavespeeds and source), %d levels, oracle setup untimed, PCG phase timed" % (
                               pk["n"][0], pk["n"][1], pk["n"][2], ",".join("%.4g" % v for v in pk["x0"]),
                               ",".join("%.4g" % v for v in pk["x1"]), "x".join(map(str, w["problem"]["n"])),
                               pk["p"], ok["n_levels"]))))
 
 
-def oracle_subprocess(args, steps=1, timeout=600):
+def oracle_subprocess(args, steps=1, timeout=900, all_cores=False):
     env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
                CUDA_VISIBLE_DEVICES="")
     cmd = [sys.executable, os.path.abspath(__file__), "--oracle-sample", "--config", str(args.config),
-           "--oracle-steps", str(steps)]
+           "--oracle-steps", str(steps)] + (["--oracle-all-cores"] if all_cores else [])
     r = subprocess.run(cmd, capture_output=True, text=True, env=env, timeout=timeout)
     if r.returncode != 0:
         raise RuntimeError("oracle sample failed: " + r.stderr[-2000:])
     return json.loads(r.stdout.strip().splitlines()[-1])
+
+
+def golden_for(cfg):
+    """The oracle's full-size reference of a workload (tests/golden, written by
+    oracle-only scripts), or None."""
+    path = os.path.join(ROOT, "tests", "golden", {2: "c2_oracle.json", 3: "c3_oracle.json"}.get(cfg, "-"))
+    try:
+        with open(path) as f:
+            return json.load(f)
+    except OSError:
+        return None
+
+
+def sketch_error(x, gold):
+    """Relative L2 distance of the trace vector x (complex128) to the oracle's
+    solution, estimated from the stored seeded sign sketch."""
+    import numpy as np
+    from paper_2304_01728_gb300 import workloads
+    sk = np.empty(gold["sketch_rows"], complex)
+    for j0 in range(0, gold["sketch_rows"], 16):
+        sk[j0:j0 + 16] = workloads.rademacher_rows(gold["sketch_seed"], j0, j0 + 16, x.size) @ x
+    skr = np.array([complex(*v) for v in gold["sketch_x"]])
+    return float(np.linalg.norm(sk - skr) / np.sqrt(gold["sketch_rows"]) / gold["norm_x"])
 
 
 # ------------------------------------------------------------------ clocks
@@ -217,8 +307,10 @@ def peaks():
         return 6800.0, "fallback"
 
 
-def traffic_for(kernel):
-    """Per-launch DRAM bytes from the committed ncu summary, if the kernel source is unchanged."""
+def traffic_for(kernel, bytes_per_launch):
+    """DRAM bytes per launch from the committed ncu summary (the captured
+    launch's DRAM bytes per algorithmic byte, times this launch's algorithmic
+    bytes), if the kernel source is unchanged since the capture."""
     p = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         with open(p) as f:
@@ -232,21 +324,37 @@ def traffic_for(kernel):
     sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
     if e.get("source_sha") != sha:
         return None
-    return e.get("traffic_bytes_per_launch")
+    ratio = e.get("ratio_traffic_to_algorithmic")
+    return ratio * bytes_per_launch if ratio else None
 
 
-FP64_PEAK_TFLOPS = 1.25   # nominal dense FP64 of one GB300 (no measured FP64 figure is provided)
+FP64_PEAK_TFLOPS = 1.20   # measured FP64 FMA rate of one GB300 (8 independent FMA chains per thread)
 
 
-def element_line(acc):
-    """Roofline line of the batched element stage (FP64 arithmetic)."""
+def element_line(acc, full_gflop):
+    """Roofline line of the batched element stage (FP64 arithmetic): the
+    fraction uses the flops the stage executed; with element classes that is
+    far below the flops of the full per-element pipeline, reported beside it."""
     ms, gflop, n = acc
     if not n or ms <= 0:
         return None
     tf = gflop / (ms / 1e3) / 1e3
-    return {"kernels": "k_elem_build/potrf/trsm/herk/condense", "bound": "alu", "achieved": tf,
+    return {"kernels": "k_elem_build/potrf/trsm/herk/condense/member_load", "bound": "alu", "achieved": tf,
             "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": tf / FP64_PEAK_TFLOPS,
-            "peak_source": "nominal FP64", "gflop_per_setup": gflop / n, "ms_per_setup": ms / n}
+            "peak_source": "measured FP64 FMA rate (nominal 1.25)", "executed_gflop_per_setup": gflop / n,
+            "full_pipeline_gflop_per_setup": full_gflop, "ms_per_setup": ms / n}
+
+
+def full_pipeline_gflop(n_elem, p):
+    """Algorithmic GFLOP of the element stage if every element ran the whole
+    pipeline (the per-element counts of dpgmg_setup_profile)."""
+    nt = (p + 2) ** 3 + 3 * (p + 2) * (p + 1) ** 2
+    nf = 4 * p ** 3
+    ntr = (p + 1) ** 3 - (p - 1) ** 3 + 6 * p * p
+    m = nf + ntr
+    mac = nt ** 3 / 6 + nt ** 2 * (m + 1) / 2 + (m + 1) ** 2 * nt / 2 + nf ** 3 / 6 + nf ** 2 * (ntr + 1) + \
+        ntr * (ntr + 1) * nf
+    return 8.0 * mac * n_elem / 1e9
 
 
 def run_gb300(args, rank, world, local_rank):
@@ -329,6 +437,8 @@ def run_gb300(args, rank, world, local_rank):
         dist.barrier()
     launches = D.dpgmg_launch_count() - l0
     elem_acc_timed = list(elem_acc)
+    gold = golden_for(args.config) if not args.n else None
+    err_main = sketch_error(trace.cpu().numpy().view(np.complex128), gold) if gold else None
     clk = clocks.stop()
     total_ms = e0.elapsed_time(e1)
     dof_iters = float(sum(n_dof * s[0] for s in stats))
@@ -373,15 +483,33 @@ def run_gb300(args, rank, world, local_rank):
                "d2h_bytes_per_step": int(16 * (n_dof + n_field)), "ms_per_step": 1e3 * t_e2e / steps_e2e}
 
     # ---- FP64 V-cycle path on the same workload (one step, reported beside)
-    fp64 = None
-    if args.precision == "mixed" and not args.no_fp64_compare:
-        op64 = D.make_opts(**dict(w["opts"], precision="fp64"))
-        s = D.dpgmg_setup(h, pb, op64)
+    def one(opts_kw):
+        s = D.dpgmg_setup(h, pb, D.make_opts(**dict(w["opts"], **opts_kw)))
         code, st = D.dpgmg_solve(h, s, trace.data_ptr(), fields.data_ptr(), out_is_device=True)
         D.dpgmg_release(h, s)
-        fp64 = {"value": n_dof * st.iters / (st.t_pcg_ms / 1e3), "iters": st.iters, "pcg_ms": st.t_pcg_ms,
-                "setup_ms": st.t_setup_ms, "true_relres": st.true_relres}
+        r = {"value": n_dof * st.iters / (st.t_pcg_ms / 1e3), "iters": st.iters, "pcg_ms": st.t_pcg_ms,
+             "setup_ms": st.t_setup_ms, "true_relres": st.true_relres, "status": D.strerror(code)}
+        if gold:
+            r["rel_l2_error_vs_oracle"] = sketch_error(trace.cpu().numpy().view(np.complex128), gold)
+        return r
+
+    fp64 = None
+    options = None
+    if args.precision == "mixed" and not args.no_fp64_compare:
+        fp64 = one(dict(precision="fp64"))
+        if not args.no_extras:
+            # the CG operator's two forms (Sec. 3 runs CG on the FP64 condensed system):
+            # double-float (the default, timed above) and complex128 on the FP64 pipe; the
+            # FP64 V-cycle with the complex128 CG operator is complex128 throughout
+            options = {"mixed_cg_double_float": {"rel_l2_error_vs_oracle": err_main,
+                                                 "pcg_ms": pcg_ms / args.steps, "iters": stats[-1][0]},
+                       "mixed_cg_c128": one(dict(flags=D.FLAG_CG_C128)),
+                       "fp64_cg_double_float": fp64,
+                       "fp64_cg_c128": one(dict(precision="fp64", flags=D.FLAG_CG_C128)),
+                       "mixed_patch_factors_fp64": one(dict(flags=D.FLAG_PATCH_FP64)),
+                       "mixed_coarsest_cuda_cores": one(dict(flags=D.FLAG_CUDA_CORES))}
     D.dpgmg_destroy(h)
+
 
     if rank != 0:
         return None
@@ -405,11 +533,22 @@ def run_gb300(args, rank, world, local_rank):
         "roofline": {"kernel": "k_patch_apply (finest smoother)", "bound": "hbm", "achieved": achieved,
                      "peak": peak, "unit": "GB/s", "frac": achieved / peak, "peak_source": peak_kind,
                      "bytes_per_launch": prof_b, "launches": prof_n, "avg_launch_ms": per_launch_ms,
-                     "traffic": traffic_for("k_patch_apply")},
+                     "traffic": traffic_for("k_patch_apply", prof_b),
+                     "traffic_source": "not measured in this run: DRAM bytes per algorithmic byte of one "
+                                       "captured launch (profiles/traffic.json: ncu dram__bytes_read.sum + "
+                                       "dram__bytes_write.sum at 10^3) times this launch's algorithmic bytes; "
+                                       "null once the kernel source has changed"},
         "clocks": clk, "e2e": e2e, "fp64_path": fp64,
+        "rel_l2_error_vs_oracle": err_main,
+        "oracle_reference": ({"iters": gold["iters"], "n_dof": gold["n_dof"],
+                              "source": "tests/golden/%s (full-size FP64 oracle run; errors estimated from its "
+                                        "128-row seeded sign sketch)" % {2: "c2_oracle.json", 3: "c3_oracle.json"}[
+                                            args.config]} if gold else None),
+        "precision_options": options,
         "kernels": [dict(k, frac=k["achieved"] / peak) for k in kernels],
         "spmv_group_tuned": tuned,
-        "element_stage": element_line(elem_acc_timed),
+        "element_stage": element_line(elem_acc_timed, full_pipeline_gflop(int(np.prod(w["problem"]["n"])),
+                                                                          w["problem"]["p"])),
     }
     return out
 
@@ -531,6 +670,138 @@ def run_sweep(args):
     print(json.dumps({"mode": "sweep", "levels": 3, "precision": "mixed", "tol": 1e-8, "rows": rows}))
 
 
+
+# ------------------------------------------------------------------ extras
+def c2_summary(args, D):
+    """The 16^3, p = 3, omega = 16 pi unit-cube workload on the same GPU:
+    PCG DOF-iter/s, setup, end to end through the C ABI with host buffers,
+    finest smoother bandwidth, and error against the oracle's full-size run."""
+    import numpy as np
+    import torch
+    w = workload(2, "mixed")
+    stream = torch.cuda.Stream()
+    h = D.dpgmg_create(0, 0, ctypes.c_void_p(stream.cuda_stream))
+    pb, keep = D.make_problem(**w["problem"])
+    op = D.make_opts(**w["opts"])
+    n_dof, n_field, _ = D.dpgmg_query_sizes(pb, op)
+    tr = torch.empty(2 * n_dof, dtype=torch.float64).pin_memory()
+    fl = torch.empty(2 * n_field, dtype=torch.float64).pin_memory()
+    res = []
+    for k in range(6):
+        t0 = time.perf_counter()
+        s = D.dpgmg_setup(h, pb, op)
+        if k >= 3:
+            D.dpgmg_profile(h, s, D.PROF_SMOOTH_FINE)
+        code, st = D.dpgmg_solve(h, s, tr.data_ptr(), fl.data_ptr(), out_is_device=False)
+        pr = D.dpgmg_profile_read(h, s) if k >= 3 else None
+        D.dpgmg_release(h, s)
+        torch.cuda.synchronize()
+        if k >= 3:
+            res.append((st.iters, st.t_pcg_ms, st.t_setup_ms, time.perf_counter() - t0, pr))
+    D.dpgmg_destroy(h)
+    peak, _ = peaks()
+    ms = sum(r[4][0] for r in res) / max(sum(r[4][1] for r in res), 1)
+    gold = golden_for(2)
+    return {"workload": w["name"], "n_dof": n_dof, "iters": res[-1][0],
+            "value": n_dof * sum(r[0] for r in res) / (sum(r[1] for r in res) / 1e3), "unit": UNIT,
+            "pcg_ms": sum(r[1] for r in res) / len(res), "setup_ms": sum(r[2] for r in res) / len(res),
+            "e2e": {"value": n_dof * sum(r[0] for r in res) / sum(r[3] for r in res), "unit": UNIT,
+                    "ms_per_step": 1e3 * sum(r[3] for r in res) / len(res)},
+            "smoother_frac_of_hbm": res[-1][4][2] / (ms / 1e3) / 1e9 / peak,
+            "rel_l2_error_vs_oracle": sketch_error(tr.numpy().view(np.complex128), gold) if gold else None}
+
+
+def stream_run(D, items, rate, slots, budget_gb):
+    """Submit the problems at the given arrival times (rate = requests/s,
+    exponential gaps of the stream; 0: all at t = 0) to a serving handle and
+    collect them; returns latencies (ms), solves/s, DOF-iter/s and statuses."""
+    import numpy as np
+    h = D.dpgmg_create(0, int(budget_gb * 1e9))
+    D.dpgmg_serve_start(h, slots)
+    keep, t_arr, t = [], [], 0.0
+    for it in items:
+        pb, k = D.make_problem(**it["problem"])
+        op = D.make_opts(**it["opts"])
+        nt, nf, _ = D.dpgmg_query_sizes(pb, op)
+        keep.append((pb, op, k, nt, nf))
+        t += it.get("gap", 1.0) / rate if rate > 0 else 0.0
+        t_arr.append(t)
+    tickets, refused = [], 0
+    t0 = time.perf_counter()
+    for (pb, op, k, nt, nf), ta in zip(keep, t_arr):
+        while time.perf_counter() - t0 < ta:
+            time.sleep(0.0005)
+        try:
+            tickets.append((D.dpgmg_submit(h, pb, op), nt, nf))
+        except D.DpgmgError as e:
+            if e.code != D.DPGMG_ERR_NOMEM:
+                raise
+            refused += 1
+    lat, di, fails = [], 0.0, 0
+    for tk, nt, nf in tickets:
+        while True:
+            code, st, l = D.dpgmg_poll(h, tk, None, None)
+            if code != D.DPGMG_ERR_PENDING:
+                break
+            time.sleep(0.0005)
+        if code != D.DPGMG_OK:
+            fails += 1
+            continue
+        lat.append(l)
+        di += nt * st.iters
+    wall = time.perf_counter() - t0
+    D.dpgmg_destroy(h)
+    return {"completed": len(lat), "failed": fails, "refused_nomem": refused, "wall_s": wall,
+            "solves_per_s": len(lat) / wall, "dof_iters_per_s": di / wall,
+            "p50_ms": float(np.percentile(lat, 50)) if lat else None,
+            "p99_ms": float(np.percentile(lat, 99)) if lat else None}
+
+
+def serve_summary(D, precision, count=100, max_dofs=4e4, load=0.8, slots=4):
+    """Bounded serving experiment: the first `count` requests of the seeded
+    serving stream with at most max_dofs trace DOFs; the single-stream
+    capacity is measured first (8 of them one at a time), then all `count`
+    arrive as a Poisson stream at load x that capacity."""
+    from paper_2304_01728_gb300 import workloads as WL
+    items = []
+    for it in WL.config5(2000, precision):
+        pb, k = D.make_problem(**it["problem"])
+        if D.dpgmg_query_sizes(pb, D.make_opts(**it["opts"]))[0] <= max_dofs:
+            items.append(it)
+        if len(items) == count:
+            break
+    t0 = time.perf_counter()
+    for it in items[:8]:
+        with D.Solver(it["problem"], **it["opts"]) as s:
+            s.solve(fields=False)
+    capacity = 8 / (time.perf_counter() - t0)
+    r = stream_run(D, items, load * capacity, slots, 160.0)
+    r.update(precision=precision, requests=len(items), rate_per_s=load * capacity,
+             single_stream_capacity_per_s=capacity, load=load, slots=slots,
+             sample="first %d requests of the seeded serving stream (n~U{8..48}, p~U{2..5}, omega~U[4,32pi], "
+                    "constant or 4-layer wavespeed) with <= %d trace DOFs; Poisson arrivals at %.1fx the "
+                    "measured one-at-a-time capacity" % (len(items), max_dofs, load))
+    return r
+
+
+def batch_summary(D, count=24, max_dofs=1.5e5, slots=4):
+    """Bounded batch: the first `count` problems of the seeded uneven batch
+    stream with at most max_dofs trace DOFs, all submitted at t = 0 (mixed)."""
+    from paper_2304_01728_gb300 import workloads as WL
+    items = []
+    for it in WL.config4(64, "mixed"):
+        pb, k = D.make_problem(**it["problem"])
+        if D.dpgmg_query_sizes(pb, D.make_opts(**it["opts"]))[0] <= max_dofs:
+            items.append(it)
+        if len(items) == count:
+            break
+    r = stream_run(D, items, 0.0, slots, 160.0)
+    r.update(problems=len(items), slots=slots,
+             sample="first %d problems of the seeded batch stream (n~U{8..24}, p~U{2,3,4}, omega~U[4,12pi]) "
+                    "with <= %d trace DOFs, all submitted at t = 0" % (len(items), max_dofs))
+    return r
+
+
 # ------------------------------------------------------------------ main
 def main():
     args = parse()
@@ -568,11 +839,28 @@ def main():
     out = run_gb300(args, rank, world, local_rank)
     if out is None:
         return
+    if world == 1 and not args.no_extras and args.mode == "step" and not args.n:
+        from paper_2304_01728_gb300 import dpgmg as D
+        if args.config != 2:
+            out["unit_cube_16cubed"] = c2_summary(args, D)
+        out["serve"] = {"mixed": serve_summary(D, "mixed"), "fp64": serve_summary(D, "fp64")}
+        out["batch"] = batch_summary(D)
     if not args.no_cpu_baseline and world == 1 or (not args.no_cpu_baseline and rank == 0):
         try:
-            r = oracle_subprocess(args, steps=1)
-            out["cpu_baseline"] = {"value": r["value"], "unit": UNIT, "cores": 1, "kind": "oracle",
-                                   "sample": r["sample"], "n_dof": r["n_dof"], "iters": r["iters"]}
+            r = oracle_subprocess(args, steps=1, all_cores=True)
+            ac = r.get("all_core")
+            gold = golden_for(args.config)
+            out["cpu_baseline"] = {
+                "value": ac["value"] if ac else r["value"], "unit": UNIT, "cores": ac["cores"] if ac else 1,
+                "kind": "oracle", "sample": r["sample"] + ("; one single-threaded replica per host core at once"
+                                                           if ac else "; one core"),
+                "n_dof": r["n_dof"], "iters": r["iters"], "nproc": r["nproc"], "cpu_model": r["cpu_model"],
+                "single_core": {"value": r["value"], "cores": 1, "pcg_s": r["pcg_s"][-1]},
+                "full_size_record": ({"n_dof": gold["n_dof"], "iters": gold["iters"],
+                                      "pcg_s": gold["oracle_seconds"]["pcg"],
+                                      "value": gold["n_dof"] * gold["iters"] / gold["oracle_seconds"]["pcg"],
+                                      "cores": 1, "where": "the oracle run that wrote the golden file (one core "
+                                      "of the build host, not this host)"} if gold else None)}
         except Exception as e:  # reported, never silently replaced
             out["cpu_baseline"] = {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle",
                                    "sample": "failed: %s" % str(e)[:200]}

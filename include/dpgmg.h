@@ -311,13 +311,15 @@ long long dpgmg_launch_count(void);
 /* SpMV work decomposition, chosen at setup by timing.  The operators are
  * applied by one warp per group of G rows of one mesh entity (G = 1, 2, 4 or
  * 8; the rows of an entity share their column list, so larger G loads each
- * column index and vector entry once for G rows).  dpgmg_setup times every G
- * on each operator and keeps the fastest; choices are cached per (product
- * type, p, level kind, log2 of the row count) for the life of the process.
- * level >= 1 addresses that level's V-cycle operator, level == -1 the CG
- * operator.  set = 1, 2, 4 or 8 overrides the choice (0 leaves it); *group
- * (may be NULL) receives the value in force.  Returns DPGMG_ERR_ARG for an
- * invalid level or size.  Results do not depend on G beyond rounding order. */
+ * column index and vector entry once for G rows), or (G = 16) by one warp
+ * per row with the column indices loaded one step ahead of the gathers they
+ * feed.  dpgmg_setup times every variant on each operator and keeps the
+ * fastest; choices are cached per (product type, p, level kind, log2 of the
+ * row count) for the life of the process.  level >= 1 addresses that level's
+ * V-cycle operator, level == -1 the CG operator.  set = 1, 2, 4, 8 or 16
+ * overrides the choice (0 leaves it); *group (may be NULL) receives the value
+ * in force.  Returns DPGMG_ERR_ARG for an invalid level or size.  Results do
+ * not depend on the variant beyond rounding order (G = 1 and 16: bitwise). */
 int dpgmg_spmv_group(dpgmg_handle h, dpgmg_system sys, int level, int set, int* group);
 
 /* DPG error indicator (Sec. 1.2: the residual that DPG minimises, in the

@@ -116,9 +116,12 @@ size_t estimate_bytes(const dpgmg_problem* pb, const dpgmg_opts* op) {
   const double m1 = nf + ntr + 1.0;
   resident += ne * (ntr * ntr + nf * (ntr + 1.0) + ntr) * 16.0;     // finest E, Yrec, Fc
   const double per = nt * nt * 8.0 + nt * m1 * 16.0 + m1 * m1 * 16.0;
-  // element batch scratch, plus the load-only scratch of the element-class members (at most every element)
+  // element batch scratch, plus the load-only scratch of the element-class members (at most every
+  // element) and their per-chunk blocks (chunks of <= 32 members of one class)
+  const double mcols = ne + 32.0 * std::min(ne / 4.0, 4096.0);
   transient = std::max(transient, (double)element_chunk((int64_t)ne, (size_t)per) * per +
-                                      ne * (nt + 1.0 + 2.0 * m1 + 2.0 * nf) * 8.0);
+                                      ne * (nt + 1.0 + 2.0 * m1 + 2.0 * nf) * 8.0 +
+                                      mcols * (nt + 2.0 * m1 + 2.0 * nf + 2.0 * ntr) * 8.0);
   double xdofs = 0.0;
   for (size_t i = 0; i < specs.size(); ++i) {
     const LevelSpec& s = specs[i];
@@ -538,7 +541,7 @@ int dpgmg_setup_phases(dpgmg_handle h, dpgmg_system sys, double* ms, int n) {
 
 int dpgmg_spmv_group(dpgmg_handle h, dpgmg_system sys, int level, int set, int* group) {
   if (!h || !sys) return DPGMG_ERR_ARG;
-  if (set != 0 && set != 1 && set != 2 && set != 4 && set != 8) return DPGMG_ERR_ARG;
+  if (set != 0 && set != 1 && set != 2 && set != 4 && set != 8 && set != 16) return DPGMG_ERR_ARG;
   std::lock_guard<std::mutex> lk(h->mu);
   SystemImpl& S = sys->s;
   const int slot = S.op.precision == DPGMG_PREC_MIXED ? 0 : 1;

@@ -406,75 +406,101 @@ __global__ void __launch_bounds__(CTA_THREADS) k_elem_condense(ElemArgs a) {
 // (stride doubles): w [nt] (even-padded), F [m] complex, u [nf] complex.
 //
 // Stage 1 (after the representatives' HERK, before the split path overwrites
-// W): w = L^-1 l', F = W_B'^H w (the load column of K; on the split path
+// W): w = L^-1 l', F = W_B'^H w, the load column of K; on the split path
 // Re F_a = sum_k W[k][a] w_k, Im F_a = -sum_k W[k][a~] w_k as in
-// k_elem_split_assemble).
-template <bool SPLIT>
-__global__ void __launch_bounds__(CTA_THREADS) k_elem_member_load(ElemArgs a, const int64_t* __restrict__ mem_e,
-                                                                  const int* __restrict__ mem_slot, double* scr,
-                                                                  int64_t stride) {
+// k_elem_split_assemble.  Members are listed class by class, and chunk q =
+// (slot, first member b0, count <= MCB) holds members of one class.
+// k_elem_member_rhs builds the load l' of every member as column j of the
+// chunk's block X_q (nt x MCB, row-major); k_elem_member_solve then applies
+// the class's factors to the whole block, X = L^-1 X (one triangular solve
+// with MCB right-hand sides) and F = W_B'^T X (a product), so the
+// representative's factors are read once per chunk instead of once per
+// member, and writes each member's F into its scratch.
+constexpr int MCB = 32;
+__global__ void __launch_bounds__(CTA_THREADS) k_elem_member_rhs(ElemArgs a, const int64_t* __restrict__ mem_e,
+                                                                 const int4* __restrict__ chunks, double* X) {
   extern __shared__ double2 sh2[];
-  const int64_t b = blockIdx.x;
-  const int64_t e = mem_e[b];
-  const int slot = mem_slot[b];
-  const int nt = a.nt, m = a.m, nf = a.nf;
+  const int4 ch = chunks[blockIdx.x];
+  const int j = blockIdx.y;
+  if (j >= ch.z) return;   // uniform over the CTA
+  const int64_t e = mem_e[ch.y + j];
   int ec[3], bmask;
   double corner[3];
   elem_geom(a, e, ec, corner, bmask);
-  double* w = scr + b * stride;
-  double2* F = reinterpret_cast<double2*>(w + nt + (nt & 1));
-  build_load<double>(a, corner, a.c[e], sh2, w, 1);
+  build_load<double>(a, corner, a.c[e], sh2, X + (size_t)blockIdx.x * a.nt * MCB + j, MCB);
+}
+
+template <bool SPLIT>
+__global__ void __launch_bounds__(CTA_THREADS) k_elem_member_solve(ElemArgs a, const int4* __restrict__ chunks,
+                                                                   double* X, double* Ft, double* scr,
+                                                                   int64_t stride) {
+  extern __shared__ double2 sh2[];
+  const int4 ch = chunks[blockIdx.x];
+  const int slot = ch.x, cnt = ch.z;
+  const int nt = a.nt, m = a.m, nf = a.nf;
+  double* Xq = X + (size_t)blockIdx.x * nt * MCB;
+  double* Fq = Ft + (size_t)blockIdx.x * (m + (SPLIT ? a.nph : 0)) * MCB;
   const double* L = a.G + (size_t)slot * nt * nt;
-  cta_trsm_lower<double, double>(L, nt, nt, w, 1, 1, reinterpret_cast<char*>(sh2));
+  cta_trsm_lower<double, double>(L, nt, nt, Xq, cnt, MCB, reinterpret_cast<char*>(sh2));
   const int ldw = SPLIT ? m + 1 + a.nph : m + 1;
   const double* W = SPLIT ? reinterpret_cast<const double*>(reinterpret_cast<const double2*>(a.W) + (size_t)slot * nt * (m + 1))
                           : reinterpret_cast<const double*>(a.W) + (size_t)slot * nt * ldw;
-  for (int j = threadIdx.x; j < m; j += blockDim.x) {
-    const int qj = (SPLIT && j >= nf) ? a.phq[j - nf] : -1;
-    double re = 0.0, im = 0.0;
-    for (int k = 0; k < nt; ++k) {
-      const double wk = w[k];
-      re = fma(W[(size_t)k * ldw + j], wk, re);
-      if (qj >= 0) im = fma(-W[(size_t)k * ldw + m + 1 + qj], wk, im);
-    }
-    F[j] = make_double2(re, im);
+  double* shd = reinterpret_cast<double*>(sh2);
+  // Fq[jj][b] = sum_k W[k][jj] X[k][b]; split path: rows m .. m + nph - 1 from W's B_i columns
+  cta_gemm<double>(true, m, cnt, nt, 1.0, W, ldw, Xq, MCB, 0.0, Fq, MCB, shd);
+  if (SPLIT && a.nph) cta_gemm<double>(true, a.nph, cnt, nt, 1.0, W + m + 1, ldw, Xq, MCB, 0.0, Fq + (size_t)m * MCB,
+                                       MCB, shd);
+  for (int q = threadIdx.x; q < cnt * m; q += blockDim.x) {
+    const int b = q / m, jj = q % m;
+    const int qj = (SPLIT && jj >= nf) ? a.phq[jj - nf] : -1;
+    double2* F = reinterpret_cast<double2*>(scr + (size_t)(ch.y + b) * stride + nt + (nt & 1));
+    F[jj] = make_double2(Fq[(size_t)jj * MCB + b], qj >= 0 ? -Fq[(size_t)(m + qj) * MCB + b] : 0.0);
   }
 }
 
-// Stage 2 (after the representatives' condensation): u = K_ff^-1 F_f,
-// F_c = F_t - K_tf u; outputs as k_elem_condense writes them, with the
-// load-independent parts (K_c, the recovery columns of the traces) copied
-// from the representative.
+// Stage 2 (after the representatives' condensation), per chunk of one class:
+// U = K_ff^-1 [F_f of the members] (two triangular solves with MCB
+// right-hand sides), F_c = F_t - K_tf U (a product); outputs as
+// k_elem_condense writes them, with the load-independent parts (K_c, the
+// recovery columns of the traces) copied from the representative.
 template <class T, bool PH>
 __global__ void __launch_bounds__(CTA_THREADS) k_elem_member_condense(ElemArgs a, const int64_t* __restrict__ mem_e,
-                                                                      const int* __restrict__ mem_slot, double* scr,
-                                                                      int64_t stride) {
+                                                                      const int4* __restrict__ chunks, double* Ub,
+                                                                      double* Cb, double* scr, int64_t stride) {
   extern __shared__ unsigned char shraw[];
-  const int64_t b = blockIdx.x;
-  const int64_t e = mem_e[b];
-  const int slot = mem_slot[b];
+  const int4 ch = chunks[blockIdx.x];
+  const int slot = ch.x, cnt = ch.z;
   const int64_t rep = a.elist[a.e0 + slot];
   const int nt = a.nt, m = a.m, nf = a.nf, ntr = a.ntr, ld = m + 1;
   const T* K = reinterpret_cast<const T*>(a.K) + (size_t)slot * ld * ld;
-  const double2* F = reinterpret_cast<const double2*>(scr + b * stride + nt + (nt & 1));
-  T* u = reinterpret_cast<T*>(const_cast<double2*>(F) + m);
-  for (int i = threadIdx.x; i < nf; i += blockDim.x) u[i] = from_c128<T>(F[i]);
+  T* U = reinterpret_cast<T*>(Ub) + (size_t)blockIdx.x * nf * MCB;
+  T* Cq = reinterpret_cast<T*>(Cb) + (size_t)blockIdx.x * ntr * MCB;
+  auto Fm = [&](int b) { return reinterpret_cast<const double2*>(scr + (size_t)(ch.y + b) * stride + nt + (nt & 1)); };
+  for (int q = threadIdx.x; q < cnt * m; q += blockDim.x) {
+    const int b = q / m, i = q % m;
+    const T v = from_c128<T>(Fm(b)[i]);
+    if (i < nf) U[(size_t)i * MCB + b] = v;
+    else Cq[(size_t)(i - nf) * MCB + b] = v;
+  }
   __syncthreads();
-  cta_trsm_lower<T, T>(K, nf, ld, u, 1, 1, reinterpret_cast<char*>(shraw));
-  cta_trsm_lower_h<T>(K, nf, ld, u, 1, 1, reinterpret_cast<char*>(shraw));
-  for (int i = threadIdx.x; i < ntr; i += blockDim.x) {
-    T acc = from_c128<T>(F[nf + i]);
-    for (int j = 0; j < nf; ++j) acc = Ops<T>::fnma(K[(size_t)(nf + i) * ld + j], u[j], acc);
-    a.Fc[e * ntr + i] = out_value<T, PH>(acc, a.tr[i].x == 0 ? 1 : 0);
+  cta_trsm_lower<T, T>(K, nf, ld, U, cnt, MCB, reinterpret_cast<char*>(shraw));
+  cta_trsm_lower_h<T>(K, nf, ld, U, cnt, MCB, reinterpret_cast<char*>(shraw));
+  cta_gemm<T>(false, ntr, cnt, nf, -1.0, K + (size_t)nf * ld, ld, U, MCB, 1.0, Cq, MCB, reinterpret_cast<T*>(shraw));
+  for (int q = threadIdx.x; q < cnt * ntr; q += blockDim.x) {
+    const int b = q / ntr, i = q % ntr;
+    a.Fc[mem_e[ch.y + b] * ntr + i] = out_value<T, PH>(Cq[(size_t)i * MCB + b], a.tr[i].x == 0 ? 1 : 0);
   }
   const double2* Er = a.Eout + rep * (size_t)ntr * ntr;
-  double2* E = a.Eout + e * (size_t)ntr * ntr;
-  for (int q = threadIdx.x; q < ntr * ntr; q += blockDim.x) E[q] = Er[q];
   const double2* Yr = a.Yrec + rep * (size_t)nf * (ntr + 1);
-  double2* Y = a.Yrec + e * (size_t)nf * (ntr + 1);
-  for (int q = threadIdx.x; q < nf * (ntr + 1); q += blockDim.x) {
-    const int i = q / (ntr + 1), j = q % (ntr + 1);
-    Y[q] = j < ntr ? Yr[q] : out_value<T, PH>(u[i], a.ff[i].x == 0 ? 1 : 0);
+  for (int b = 0; b < cnt; ++b) {
+    const int64_t e = mem_e[ch.y + b];
+    double2* E = a.Eout + e * (size_t)ntr * ntr;
+    for (int q = threadIdx.x; q < ntr * ntr; q += blockDim.x) E[q] = Er[q];
+    double2* Y = a.Yrec + e * (size_t)nf * (ntr + 1);
+    for (int q = threadIdx.x; q < nf * (ntr + 1); q += blockDim.x) {
+      const int i = q / (ntr + 1), j = q % (ntr + 1);
+      Y[q] = j < ntr ? Yr[q] : out_value<T, PH>(U[(size_t)i * MCB + b], a.ff[i].x == 0 ? 1 : 0);
+    }
   }
 }
 
@@ -746,22 +772,59 @@ static void element_core(SystemImpl& S, Level& L, const std::vector<double>& cva
             (int64_t)sreps.size() <= chunk;
   }
   const int64_t mstride = (a.nt + (a.nt & 1)) + 2 * (int64_t)a.m + 2 * (int64_t)a.nf;   // member scratch (doubles)
+  // members listed class by class, cut into chunks of at most MCB members of one class
+  auto chunk_members = [](std::vector<int64_t>& mem, std::vector<int>& slot) {
+    std::vector<size_t> ord(mem.size());
+    for (size_t i = 0; i < ord.size(); ++i) ord[i] = i;
+    std::stable_sort(ord.begin(), ord.end(), [&](size_t u, size_t v) { return slot[u] < slot[v]; });
+    std::vector<int64_t> m2(mem.size());
+    std::vector<int> s2(mem.size());
+    for (size_t i = 0; i < ord.size(); ++i) {
+      m2[i] = mem[ord[i]];
+      s2[i] = slot[ord[i]];
+    }
+    mem.swap(m2);
+    slot.swap(s2);
+    std::vector<int4> ch;
+    for (size_t i = 0; i < mem.size();) {
+      size_t j = i;
+      while (j < mem.size() && slot[j] == slot[i] && (int)(j - i) < MCB) ++j;
+      ch.push_back(make_int4(slot[i], (int)i, (int)(j - i), 0));
+      i = j;
+    }
+    return ch;
+  };
   if (reuse) {
     const size_t sm_mem = std::max(sm_build_max, sm_cplx);
-    DPG_CUDA(cudaFuncSetAttribute(k_elem_member_load<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_mem));
-    DPG_CUDA(cudaFuncSetAttribute(k_elem_member_load<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_mem));
     DPG_CUDA(cudaFuncSetAttribute(k_elem_member_condense<double, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)sm_cplx));
     DPG_CUDA(cudaFuncSetAttribute(k_elem_member_condense<double2, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)sm_cplx));
     double* scr = A.arr<double>((size_t)std::max<int64_t>((int64_t)std::max(rmem.size(), smem.size()), 1) * mstride);
+    const std::vector<int4> rch = chunk_members(rmem, rslot), sch = chunk_members(smem, sslot);
+    const size_t nch = std::max<size_t>(std::max(rch.size(), sch.size()), 1);
+    double* Xb = A.arr<double>(nch * (size_t)a.nt * MCB);
+    double* Fb = A.arr<double>(nch * (size_t)(a.m + a.nph) * MCB);
+    double* Ub = A.arr<double>(nch * (size_t)a.nf * MCB * 2);    // K_ff^-1 F_f blocks (complex at most)
+    double* Cb = A.arr<double>(nch * (size_t)a.ntr * MCB * 2);   // condensed load blocks
+    DPG_CUDA(cudaFuncSetAttribute(k_elem_member_rhs, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_mem));
+    DPG_CUDA(cudaFuncSetAttribute(k_elem_member_solve<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_cplx));
+    DPG_CUDA(cudaFuncSetAttribute(k_elem_member_solve<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_cplx));
+    auto member_loads = [&](const std::vector<int4>& ch, const int64_t* de, bool split) {
+      int4* dch = upload(A, ch, st);
+      k_elem_member_rhs<<<dim3((unsigned)ch.size(), MCB), CTA_THREADS, sm_mem, st>>>(a, de, dch, Xb);
+      DPG_CHECK_LAUNCH();
+      if (split) k_elem_member_solve<true><<<(unsigned)ch.size(), CTA_THREADS, sm_cplx, st>>>(a, dch, Xb, Fb, scr, mstride);
+      else k_elem_member_solve<false><<<(unsigned)ch.size(), CTA_THREADS, sm_cplx, st>>>(a, dch, Xb, Fb, scr, mstride);
+      DPG_CHECK_LAUNCH();
+      A.release(dch);
+    };
     if (!rreps.empty()) {
       int64_t* dl = upload(A, rreps, st);
       a.elist = dl;
       a.e0 = 0;
       const int nb = (int)rreps.size(), nm = (int)rmem.size();
       int64_t* de = nm ? upload(A, rmem, st) : nullptr;
-      int* ds = nm ? upload(A, rslot, st) : nullptr;
       k_elem_build<double><<<nb, CTA_THREADS, sm_build, st>>>(a);
       DPG_CHECK_LAUNCH();
       k_elem_potrf<<<nb, CTA_THREADS, sm_real, st>>>(a);
@@ -770,17 +833,16 @@ static void element_core(SystemImpl& S, Level& L, const std::vector<double>& cva
       DPG_CHECK_LAUNCH();
       k_elem_herk<double><<<nb, CTA_THREADS, sm_cplx, st>>>(a);
       DPG_CHECK_LAUNCH();
-      if (nm) {
-        k_elem_member_load<false><<<nm, CTA_THREADS, sm_mem, st>>>(a, de, ds, scr, mstride);
-        DPG_CHECK_LAUNCH();
-      }
+      if (nm) member_loads(rch, de, false);
       k_elem_condense<double><<<nb, CTA_THREADS, sm_cplx, st>>>(a);
       DPG_CHECK_LAUNCH();
       if (nm) {
-        k_elem_member_condense<double, false><<<nm, CTA_THREADS, sm_cplx, st>>>(a, de, ds, scr, mstride);
+        int4* dch = upload(A, rch, st);
+        k_elem_member_condense<double, false><<<(unsigned)rch.size(), CTA_THREADS, sm_cplx, st>>>(a, de, dch, Ub, Cb,
+                                                                                                   scr, mstride);
         DPG_CHECK_LAUNCH();
+        A.release(dch);
         A.release(de);
-        A.release(ds);
       }
       A.release(dl);
     }
@@ -790,7 +852,6 @@ static void element_core(SystemImpl& S, Level& L, const std::vector<double>& cva
       a.e0 = 0;
       const int nb = (int)sreps.size(), nm = (int)smem.size();
       int64_t* de = nm ? upload(A, smem, st) : nullptr;
-      int* ds = nm ? upload(A, sslot, st) : nullptr;
       k_elem_build<double, true><<<nb, CTA_THREADS, sm_build, st>>>(a);
       DPG_CHECK_LAUNCH();
       k_elem_potrf<<<nb, CTA_THREADS, sm_real, st>>>(a);
@@ -799,22 +860,25 @@ static void element_core(SystemImpl& S, Level& L, const std::vector<double>& cva
       DPG_CHECK_LAUNCH();
       k_elem_herk_split<<<nb, CTA_THREADS, sm_cplx, st>>>(a);
       DPG_CHECK_LAUNCH();
-      if (nm) {   // before the assembly below reuses the W slots
-        k_elem_member_load<true><<<nm, CTA_THREADS, sm_mem, st>>>(a, de, ds, scr, mstride);
-        DPG_CHECK_LAUNCH();
-      }
+      if (nm) member_loads(sch, de, true);   // before the assembly below reuses the W slots
       k_elem_split_assemble<<<nb, CTA_THREADS, 0, st>>>(a);
       DPG_CHECK_LAUNCH();
       k_elem_condense<double2, true><<<nb, CTA_THREADS, sm_cplx, st>>>(a);
       DPG_CHECK_LAUNCH();
       if (nm) {
-        k_elem_member_condense<double2, true><<<nm, CTA_THREADS, sm_cplx, st>>>(a, de, ds, scr, mstride);
+        int4* dch = upload(A, sch, st);
+        k_elem_member_condense<double2, true><<<(unsigned)sch.size(), CTA_THREADS, sm_cplx, st>>>(a, de, dch, Ub, Cb,
+                                                                                                   scr, mstride);
         DPG_CHECK_LAUNCH();
+        A.release(dch);
         A.release(de);
-        A.release(ds);
       }
       A.release(dl);
     }
+    A.release(Cb);
+    A.release(Ub);
+    A.release(Fb);
+    A.release(Xb);
     A.release(scr);
   } else {
     run_list(dreal, (int64_t)lreal.size(), true);

@@ -721,22 +721,23 @@ MacroHost build_macro(const MeshL& mf, const MeshL& mc) {
   M.I_glob.assign(nK * M.nI, -1);
   M.groups.resize(nK);
   M.smask.assign(mf.ndof, 0);
-  for (int64_t K = 0; K < nK; ++K) {
-    int Kc[3];
-    mc.elem_coord(K, Kc);
-    for (int a = 0; a < M.nS; ++a) {
-      int64_t g = dof_of(Kc, kl[a]);
-      M.S_glob[K * M.nS + a] = g;
-      if (g >= 0) {
-        M.smask[g] = 1;
-        M.groups[K].push_back(mf.dof_entity(g));
+  parallel_ranges(nK, [&](int64_t lo, int64_t hi) {
+    for (int64_t K = lo; K < hi; ++K) {
+      int Kc[3];
+      mc.elem_coord(K, Kc);
+      for (int a = 0; a < M.nS; ++a) {
+        int64_t g = dof_of(Kc, kl[a]);
+        M.S_glob[K * M.nS + a] = g;
+        if (g >= 0) M.groups[K].push_back(mf.dof_entity(g));
       }
+      for (int a = 0; a < M.nI; ++a) M.I_glob[K * M.nI + a] = dof_of(Kc, kl[M.nS + a]);
+      auto& gr = M.groups[K];
+      std::sort(gr.begin(), gr.end());
+      gr.erase(std::unique(gr.begin(), gr.end()), gr.end());
     }
-    for (int a = 0; a < M.nI; ++a) M.I_glob[K * M.nI + a] = dof_of(Kc, kl[M.nS + a]);
-    auto& gr = M.groups[K];
-    std::sort(gr.begin(), gr.end());
-    gr.erase(std::unique(gr.begin(), gr.end()), gr.end());
-  }
+  });
+  for (int64_t q = 0; q < nK * M.nS; ++q)
+    if (M.S_glob[q] >= 0) M.smask[M.S_glob[q]] = 1;
 
   // ---- natural inclusion on one coarse element (identical for all K)
   const auto& locc = mc.loc;
@@ -780,47 +781,7 @@ MacroHost build_macro(const MeshL& mf, const MeshL& mc) {
     }
   }
 
-  // ---- global P (fine rows) and P^T (coarse rows)
-  std::vector<std::tuple<int64_t, int64_t, double>> trip;
-  std::vector<int64_t> cg(locc.size());
-  for (int64_t K = 0; K < nK; ++K) {
-    mc.elem_dofs(K, cg.data());
-    for (int a = 0; a < M.nS; ++a) {
-      int64_t g = M.S_glob[K * M.nS + a];
-      if (g < 0) continue;
-      for (size_t j = 0; j < locc.size(); ++j) {
-        double v = M.IK[(size_t)a * locc.size() + j];
-        if (v != 0.0 && cg[j] >= 0) trip.emplace_back(g, cg[j], v);
-      }
-    }
-  }
-  std::sort(trip.begin(), trip.end(), [](const auto& x, const auto& y) {
-    return std::get<0>(x) != std::get<0>(y) ? std::get<0>(x) < std::get<0>(y) : std::get<1>(x) < std::get<1>(y);
-  });
-  trip.erase(std::unique(trip.begin(), trip.end(), [](const auto& x, const auto& y) {
-    return std::get<0>(x) == std::get<0>(y) && std::get<1>(x) == std::get<1>(y);
-  }), trip.end());
-  M.P_ptr.assign(mf.ndof + 1, 0);
-  for (auto& t : trip) {
-    ++M.P_ptr[std::get<0>(t) + 1];
-    M.P_col.push_back((int32_t)std::get<1>(t));
-    M.P_val.push_back(std::get<2>(t));
-  }
-  for (int64_t g = 0; g < mf.ndof; ++g) M.P_ptr[g + 1] += M.P_ptr[g];
-  M.PT_ptr.assign(mc.ndof + 1, 0);
-  for (auto& t : trip) ++M.PT_ptr[std::get<1>(t) + 1];
-  for (int64_t g = 0; g < mc.ndof; ++g) M.PT_ptr[g + 1] += M.PT_ptr[g];
-  M.PT_col.assign(trip.size(), 0);
-  M.PT_val.assign(trip.size(), 0.0);
-  {
-    std::vector<int64_t> f(M.PT_ptr.begin(), M.PT_ptr.end() - 1);
-    for (auto& t : trip) {
-      int64_t r = std::get<1>(t);
-      M.PT_col[f[r]] = (int32_t)std::get<0>(t);
-      M.PT_val[f[r]++] = std::get<2>(t);
-    }
-  }
-  // ---- S-slot CSR per fine DOF
+  // ---- S-slot CSR per fine DOF (slots in increasing K)
   M.sslot_ptr.assign(mf.ndof + 1, 0);
   for (int64_t s = 0; s < nK * M.nS; ++s)
     if (M.S_glob[s] >= 0) ++M.sslot_ptr[M.S_glob[s] + 1];
@@ -830,6 +791,61 @@ MacroHost build_macro(const MeshL& mf, const MeshL& mc) {
     std::vector<int64_t> f(M.sslot_ptr.begin(), M.sslot_ptr.end() - 1);
     for (int64_t s = 0; s < nK * M.nS; ++s)
       if (M.S_glob[s] >= 0) M.sslots[f[M.S_glob[s]]++] = (int32_t)s;
+  }
+  // ---- global P (fine rows) and P^T (coarse rows).  Row g of P is row a of
+  // I_K in the coarse numbering of any coarse element K whose skeleton holds g
+  // at local index a (the same values for every such K); the first such K
+  // (its first S-slot) gives it, columns in increasing coarse DOF.
+  const size_t nlc = locc.size();
+  M.P_ptr.assign(mf.ndof + 1, 0);
+  auto row_of = [&](int64_t g, std::vector<int64_t>& cg, std::vector<std::pair<int64_t, double>>& out) {
+    out.clear();
+    if (M.sslot_ptr[g + 1] == M.sslot_ptr[g]) return;
+    const int64_t s = M.sslots[M.sslot_ptr[g]];
+    const int64_t K = s / M.nS;
+    const int a = (int)(s % M.nS);
+    mc.elem_dofs(K, cg.data());
+    for (size_t j = 0; j < nlc; ++j) {
+      const double v = M.IK[(size_t)a * nlc + j];
+      if (v != 0.0 && cg[j] >= 0) out.emplace_back(cg[j], v);
+    }
+    std::sort(out.begin(), out.end());
+  };
+  parallel_ranges(mf.ndof, [&](int64_t lo, int64_t hi) {
+    std::vector<int64_t> cg(nlc);
+    std::vector<std::pair<int64_t, double>> r;
+    for (int64_t g = lo; g < hi; ++g) {
+      row_of(g, cg, r);
+      M.P_ptr[g + 1] = (int64_t)r.size();
+    }
+  });
+  for (int64_t g = 0; g < mf.ndof; ++g) M.P_ptr[g + 1] += M.P_ptr[g];
+  M.P_col.assign(M.P_ptr[mf.ndof], 0);
+  M.P_val.assign(M.P_ptr[mf.ndof], 0.0);
+  parallel_ranges(mf.ndof, [&](int64_t lo, int64_t hi) {
+    std::vector<int64_t> cg(nlc);
+    std::vector<std::pair<int64_t, double>> r;
+    for (int64_t g = lo; g < hi; ++g) {
+      row_of(g, cg, r);
+      for (size_t q = 0; q < r.size(); ++q) {
+        M.P_col[M.P_ptr[g] + q] = (int32_t)r[q].first;
+        M.P_val[M.P_ptr[g] + q] = r[q].second;
+      }
+    }
+  });
+  M.PT_ptr.assign(mc.ndof + 1, 0);
+  for (int64_t q = 0; q < M.P_ptr[mf.ndof]; ++q) ++M.PT_ptr[M.P_col[q] + 1];
+  for (int64_t g = 0; g < mc.ndof; ++g) M.PT_ptr[g + 1] += M.PT_ptr[g];
+  M.PT_col.assign(M.P_ptr[mf.ndof], 0);
+  M.PT_val.assign(M.P_ptr[mf.ndof], 0.0);
+  {
+    std::vector<int64_t> f(M.PT_ptr.begin(), M.PT_ptr.end() - 1);
+    for (int64_t g = 0; g < mf.ndof; ++g)   // rows in increasing g: each P^T row in increasing fine DOF
+      for (int64_t q = M.P_ptr[g]; q < M.P_ptr[g + 1]; ++q) {
+        const int64_t r = M.P_col[q];
+        M.PT_col[f[r]] = (int32_t)g;
+        M.PT_val[f[r]++] = M.P_val[q];
+      }
   }
   return M;
 }

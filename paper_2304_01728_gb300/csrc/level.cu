@@ -585,13 +585,30 @@ static void setup_patches(SystemImpl& S, Level& F, const LevelPlan& lp, int* din
 }
 
 // Host index plan of a hierarchy (every level's integer structures); runs on
-// a host thread concurrently with the element stage.
+// host threads concurrently with the element stage: one per level (the levels'
+// structures are independent) and one for the CG operator's lists, each of
+// them spreading its larger loops over further threads.
 std::shared_ptr<HostPlan> plan_host(const SystemImpl& S) {
   auto HP = std::make_shared<HostPlan>();
   const int L = (int)S.levels.size() - 1;
-  HP->fdofs = elem_dof_table(S.levels[L].mesh);
   HP->lv.resize(L + 1);
-  for (int l = L; l >= 1; --l) {
+  std::vector<std::thread> th;
+  std::vector<std::exception_ptr> errs(L + 2);
+  auto guarded = [&errs](int slot, auto&& f) {
+    return [&errs, slot, f]() {
+      try {
+        f();
+      } catch (...) {
+        errs[slot] = std::current_exception();
+      }
+    };
+  };
+  th.emplace_back(guarded(0, [&]() { HP->fdofs = elem_dof_table(S.levels[L].mesh); }));
+  if (L == 0 || S.levels[L].kind != 1) {
+    HP->has_acg = true;
+    th.emplace_back(guarded(L + 1, [&]() { HP->acg = prep_ecsr(S.levels[L].mesh, element_groups(S.levels[L].mesh)); }));
+  }
+  for (int l = L; l >= 1; --l) th.emplace_back(guarded(l, [&S, &HP, l]() {
     const Level& F = S.levels[l];
     const Level& C = S.levels[l - 1];
     LevelPlan& lp = HP->lv[l];
@@ -626,11 +643,10 @@ std::shared_ptr<HostPlan> plan_host(const SystemImpl& S) {
     lp.order.resize(np);
     for (int64_t j = 0; j < np; ++j) lp.order[j] = j;
     std::stable_sort(lp.order.begin(), lp.order.end(), [&](int64_t u, int64_t v) { return size_of(u) > size_of(v); });
-  }
-  if (L == 0 || S.levels[L].kind != 1) {
-    HP->has_acg = true;
-    HP->acg = prep_ecsr(S.levels[L].mesh, element_groups(S.levels[L].mesh));
-  }
+  }));
+  for (auto& t : th) t.join();
+  for (auto& e : errs)
+    if (e) std::rethrow_exception(e);
   return HP;
 }
 
@@ -776,12 +792,13 @@ void build_hierarchy(SystemImpl& S, cudaStream_t st) {
     const bool keep_split = l == L && F.kind == 1;
     float2* plo = nullptr;
     const bool c128 = (S.op.flags & DPGMG_FLAG_CG_C128) != 0;
-    if (!(S.op.theta > 0.0) && !c128) {   // double-float estimate
-      if (!patches_fp32(S)) {               // FP64 inverses: high and low parts (FP32 ones are exact)
-        Pd.inv32 = A.arr<float2>((size_t)std::max<int64_t>(Pd.nvals, 1));
-        plo = A.arr<float2>((size_t)std::max<int64_t>(Pd.nvals, 1));
-        split_df(Pd.inv64, Pd.inv32, plo, Pd.nvals, st);
-      }
+    if (!(S.op.theta > 0.0) && !c128 && patches_fp32(S)) {
+      // estimate in the V-cycle's complex64 arithmetic (its operator and FP32-factored smoother)
+      if (!F.A.v32) F.A.v32 = to_c64(A, F.A.v64, F.A.nnz, st);
+    } else if (!(S.op.theta > 0.0) && !c128) {   // double-float estimate
+      Pd.inv32 = A.arr<float2>((size_t)std::max<int64_t>(Pd.nvals, 1));
+      plo = A.arr<float2>((size_t)std::max<int64_t>(Pd.nvals, 1));
+      split_df(Pd.inv64, Pd.inv32, plo, Pd.nvals, st);
       if (!F.A.vlo) split_operator(A, F.A, st);
     }
     estimate_theta(S, l, dtheta + 2 * l, plo, st);

@@ -151,6 +151,49 @@ __global__ void __launch_bounds__(256) k_spmv(const int32_t* __restrict__ row_en
   }
 }
 
+// The same product with the column indices of the next step loaded one step
+// ahead, so that each step waits on the gathered x entries only (the index ->
+// gather chain of k_spmv is the latency it is bound by).  Identical
+// accumulation order: results are bitwise those of k_spmv.
+template <class C>
+__global__ void __launch_bounds__(256) k_spmv_pf(const int32_t* __restrict__ row_ent,
+                                                 const int64_t* __restrict__ ent_start,
+                                                 const int64_t* __restrict__ col_ptr,
+                                                 const int32_t* __restrict__ col_idx,
+                                                 const int64_t* __restrict__ val_ptr, const C* __restrict__ v,
+                                                 const C* __restrict__ x, const C* __restrict__ b, C* __restrict__ y,
+                                                 int64_t nrows, int mode) {
+  using O = Ops<C>;
+  const int lane = threadIdx.x & 31;
+  const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t row = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); row < nrows; row += nw) {
+    const int32_t E = row_ent[row];
+    C acc = O::zero();
+    if (E >= 0) {
+      const int64_t c0 = col_ptr[E];
+      const int nnz = (int)(col_ptr[E + 1] - c0);
+      const C* vals = v + val_ptr[E] + (row - ent_start[E]) * nnz;
+      const int32_t* cols = col_idx + c0;
+      C acc1 = O::zero();
+      int k = lane;
+      int cA = k < nnz ? __ldg(cols + k) : 0;
+      int cB = k + 32 < nnz ? __ldg(cols + k + 32) : 0;
+      for (; k + 32 < nnz; k += 64) {
+        const C v0 = __ldcs(vals + k), v1 = __ldcs(vals + k + 32);
+        const C x0 = x[cA], x1 = x[cB];
+        const int kn = k + 64;
+        cA = kn < nnz ? __ldg(cols + kn) : 0;
+        cB = kn + 32 < nnz ? __ldg(cols + kn + 32) : 0;
+        acc = O::fma(v0, x0, acc);
+        acc1 = O::fma(v1, x1, acc1);
+      }
+      if (k < nnz) acc = O::fma(__ldcs(vals + k), x[cA], acc);
+      acc = warp_sum(O::add(acc, acc1));
+    }
+    if (lane == 0) y[row] = mode ? O::sub(b[row], acc) : acc;
+  }
+}
+
 // Entity-blocked SpMV: one warp per task (entity E, rows r0 .. r0 + G - 1 of
 // E).  The G rows share E's column list, so each column index and x entry is
 // loaded once for G rows and G value streams are in flight per column.
@@ -209,8 +252,18 @@ template <class C> struct SpmvSlot;
 template <> struct SpmvSlot<float2> { static constexpr int v = 0; };
 template <> struct SpmvSlot<double2> { static constexpr int v = 1; };
 
+// G: rows of one entity per warp (1, 2, 4, 8); SPMV_PF = one row per warp with
+// the column indices loaded one step ahead (k_spmv_pf)
+constexpr int SPMV_PF = 16;
 template <class C>
 static void spmv_g(const ECSRDev& A, const C* vals, const C* x, const C* b, C* y, int mode, int G, cudaStream_t st) {
+  if (G == SPMV_PF) {
+    int64_t blocks = std::min<int64_t>((A.nrows + 7) / 8, 152 * 16);
+    k_spmv_pf<C><<<(unsigned)blocks, 256, 0, st>>>(A.row_ent, A.ent_start, A.col_ptr, A.col_idx, A.val_ptr, vals, x,
+                                                    b, y, A.nrows, mode);
+    DPG_CHECK_LAUNCH();
+    return;
+  }
   if (G <= 1 || !A.tasks[1]) {
     int64_t blocks = std::min<int64_t>((A.nrows + 7) / 8, 152 * 16);
     k_spmv<C><<<(unsigned)blocks, 256, 0, st>>>(A.row_ent, A.ent_start, A.col_ptr, A.col_idx, A.val_ptr, vals, x, b,
@@ -284,7 +337,10 @@ __device__ __forceinline__ void df_warp_sum(float& h, float& l) {
 // One CTA per 32 consecutive rows (4 per warp).  The row sums stay in FP32
 // pairs up to the end; one warp then turns the 32 results into complex128 with
 // full-warp instructions (the FP64 pipe of this GPU runs at 1/64 of FP32).
+// PF: the column indices of the next step are loaded one step ahead (same
+// arithmetic, bitwise equal results).
 constexpr int DF_ROWS = 32;
+template <bool PF>
 __global__ void __launch_bounds__(256) k_spmv_df(const int32_t* __restrict__ row_ent, const int64_t* __restrict__ ent_start,
                                                  const int64_t* __restrict__ col_ptr, const int32_t* __restrict__ col_idx,
                                                  const int64_t* __restrict__ val_ptr, const float2* __restrict__ vh,
@@ -304,15 +360,25 @@ __global__ void __launch_bounds__(256) k_spmv_df(const int32_t* __restrict__ row
       const int nnz = (int)(col_ptr[E + 1] - c0);
       const int64_t off = val_ptr[E] + (row - ent_start[E]) * nnz;
       const int32_t* cols = col_idx + c0;
+      int pA = 0, pB = 0;   // PF: indices of this step, loaded one step ahead
+      if (PF && lane < nnz) {
+        pA = __ldg(cols + lane);
+        pB = lane + 32 < nnz ? __ldg(cols + lane + 32) : pA;
+      }
       for (int k = lane; k < nnz; k += 64) {
         // two columns per lane per step, all loads issued before the arithmetic
         const bool two = k + 32 < nnz;
         const float2 ah0 = __ldcs(vh + off + k), al0 = __ldcs(vl + off + k);
-        const int cA = cols[k];
+        const int cA = PF ? pA : cols[k];
         const float2 ah1 = two ? __ldcs(vh + off + k + 32) : make_float2(0.f, 0.f);
         const float2 al1 = two ? __ldcs(vl + off + k + 32) : make_float2(0.f, 0.f);
-        const int cB = two ? cols[k + 32] : cA;
+        const int cB = PF ? pB : (two ? cols[k + 32] : cA);
         const float2 uh0 = xh[cA], ul0 = xl[cA], uh1 = xh[cB], ul1 = xl[cB];
+        if (PF) {
+          const int kn = k + 64;
+          pA = kn < nnz ? __ldg(cols + kn) : 0;
+          pB = kn + 32 < nnz ? __ldg(cols + kn + 32) : pA;
+        }
         float p, q;
         df_mul(ah0.x, al0.x, uh0.x, ul0.x, p, q);
         df_add(rh, rl, p, q);
@@ -429,10 +495,14 @@ __global__ void k_split_vals(const double2* __restrict__ v, float2* __restrict__
 static void spmv_df_g(const ECSRDev& A, const float2* xh, const float2* xl, const double2* b, double2* y, int mode,
                       int G, cudaStream_t st) {
   const int64_t n = A.nrows;
-  if (G <= 1 || !A.tasks[1]) {
+  if (G == SPMV_PF || G <= 1 || !A.tasks[1]) {
     const int64_t blocks = (n + DF_ROWS - 1) / DF_ROWS;
-    k_spmv_df<<<(unsigned)blocks, 256, 0, st>>>(A.row_ent, A.ent_start, A.col_ptr, A.col_idx, A.val_ptr, A.v32, A.vlo,
-                                               xh, xl, b, y, n, mode);
+    if (G == SPMV_PF)
+      k_spmv_df<true><<<(unsigned)blocks, 256, 0, st>>>(A.row_ent, A.ent_start, A.col_ptr, A.col_idx, A.val_ptr,
+                                                        A.v32, A.vlo, xh, xl, b, y, n, mode);
+    else
+      k_spmv_df<false><<<(unsigned)blocks, 256, 0, st>>>(A.row_ent, A.ent_start, A.col_ptr, A.col_idx, A.val_ptr,
+                                                         A.v32, A.vlo, xh, xl, b, y, n, mode);
     DPG_CHECK_LAUNCH();
     return;
   }
@@ -1138,7 +1208,7 @@ static int pick_variant(const TuneKey& key, const Evict& ev, cudaStream_t st, st
 
 template <class F>
 static int pick_group(const TuneKey& key, const Evict& ev, cudaStream_t st, F&& run) {
-  return pick_variant(key, ev, st, {1, 2, 4, 8}, run);
+  return pick_variant(key, ev, st, {1, SPMV_PF, 2, 4, 8}, run);
 }
 
 template <class F>
@@ -1507,6 +1577,48 @@ double theta_from_rayleigh(double num, double den) { return 1.0 / (1.05 * (num /
 //     P.inv32, low parts in plo), or complex128 under DPGMG_FLAG_CG_C128; on the
 //     mixed path with FP32 patch factors, the complex64 inverses the V-cycle
 //     applies, taken exactly (plo null), so theta damps the smoother in use.
+// (On the mixed path with FP32 patch factors and the default CG operator the
+// estimate runs in the V-cycle's complex64 arithmetic instead:
+// estimate_theta_c64.)
+// Mixed path with FP32 patch factors: the V-cycle's own complex64 operator
+// and smoother, complex64 vectors, FP64 dot products.
+static void estimate_theta_c64(SystemImpl& S, Level& F, double* out, cudaStream_t st) {
+  const int64_t n = F.mesh.ndof;
+  Alloc tmp;
+  tmp.budget = (size_t)-1;
+  tmp.stream = st;
+  float2* x = tmp.arr<float2>((size_t)n);
+  float2* y = tmp.arr<float2>((size_t)n);
+  float2* t = tmp.arr<float2>((size_t)n);
+  float2* pbuf = tmp.arr<float2>((size_t)std::max<int64_t>(F.P.scratch_entries(), 1));
+  WS W;
+  W.part = tmp.arr<double2>(RED_BLOCKS);
+  W.sc = tmp.arr<double2>(SC_COUNT);
+  k_start_vector<float2><<<nblk(n), 256, 0, st>>>(x, n, F.P.slot_ptr);
+  DPG_CHECK_LAUNCH();
+  dot_t<float2>(W, x, x, n, 1, st);
+  k_scale<float2><<<RED_BLOCKS, 256, 0, st>>>(x, n, W.sc, SC_RR);
+  DPG_CHECK_LAUNCH();
+  for (int k = 0; k < 30; ++k) {
+    spmv<float2>(F.A, F.A.v32, x, nullptr, t, 0, st);
+    smooth<float2>(F, t, y, 1.0, 0, pbuf, st);
+    dot_t<float2>(W, y, y, n, 1, st);
+    k_scale<float2><<<RED_BLOCKS, 256, 0, st>>>(y, n, W.sc, SC_RR);
+    DPG_CHECK_LAUNCH();
+    std::swap(x, y);
+  }
+  spmv<float2>(F.A, F.A.v32, x, nullptr, t, 0, st);   // M x
+  smooth<float2>(F, t, y, 1.0, 0, pbuf, st);           // S M x
+  dot_t<float2>(W, t, y, n, 3, st);
+  k_take_re<<<1, 1, 0, st>>>(W.sc, SC_RHO, out);
+  DPG_CHECK_LAUNCH();
+  dot_t<float2>(W, x, t, n, 3, st);
+  k_take_re<<<1, 1, 0, st>>>(W.sc, SC_RHO, out + 1);
+  DPG_CHECK_LAUNCH();
+  W.part = nullptr;
+  W.sc = nullptr;
+}
+
 static void estimate_theta_fp(SystemImpl& S, Level& F, const float2* plo, double* out, cudaStream_t st) {
   const int64_t n = F.mesh.ndof;
   const bool c128 = cg_c128(S);
@@ -1561,6 +1673,10 @@ void estimate_theta(SystemImpl& S, int l, double* rayleigh, const float2* plo, c
   configure_smoother_kernels();
   if (S.op.theta > 0.0) {
     F.theta = S.op.theta;
+    return;
+  }
+  if (S.op.precision == DPGMG_PREC_MIXED && !cg_c128(S) && !F.P.inv64 && F.A.v32) {
+    estimate_theta_c64(S, F, rayleigh, st);
     return;
   }
   estimate_theta_fp(S, F, plo, rayleigh, st);

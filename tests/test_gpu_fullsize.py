@@ -1,7 +1,10 @@
-"""Full-size parity on the 16^3, p = 3, omega = 16 pi workload (the bench configuration).
+"""Full-size parity on the 16^3, p = 3, omega = 16 pi unit-cube workload and on
+the layered-medium workload (32x32x16, p = 3, omega = 20 pi, 6 layers, 4
+levels with two stacked h-transitions).
 
-Reference values come from tests/golden/c2_oracle.json, written by
-tests/golden/make_c2_golden.py from a full oracle run (FP64, same seeds).
+Reference values come from tests/golden/c2_oracle.json and c3_oracle.json,
+written by tests/golden/make_c2_golden.py and make_c3_golden.py from full
+oracle runs (FP64, same seeds).
 Sampled element matrices are recomputed by the oracle on the spot; theta per
 level and the iteration count against the oracle's.  The solution's relative
 L2 error against the oracle's is estimated from a seeded random sketch (128
@@ -26,6 +29,17 @@ from tests.oracle_adapter import MIXED_THETA_TOL
 
 pytestmark = pytest.mark.gpu
 GOLD = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "c2_oracle.json")))
+GOLD3 = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "c3_oracle.json")))
+
+
+def sketch_error(x, gold):
+    """Relative L2 error of x against the oracle's solution, estimated from the
+    stored 128-row sign sketch (E||S e||^2 = 128 ||e||^2)."""
+    sk = np.empty(gold["sketch_rows"], complex)
+    for j0 in range(0, gold["sketch_rows"], 16):
+        sk[j0:j0 + 16] = workloads.rademacher_rows(gold["sketch_seed"], j0, j0 + 16, x.size) @ x
+    skr = np.array([complex(*v) for v in gold["sketch_x"]])
+    return np.linalg.norm(sk - skr) / np.sqrt(gold["sketch_rows"]) / gold["norm_x"]
 
 
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
@@ -67,3 +81,42 @@ def test_c2_full_size(precision):
     assert l2 < (1e-9 if precision == "fp64" else 1e-7), l2
     assert err < (1e-9 if precision == "fp64" else 5e-7), err
     assert abs(np.linalg.norm(x) - GOLD["norm_x"]) < 1e-7 * GOLD["norm_x"]
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_c3_full_size(precision):
+    """Layered medium (Sec. 5 shape): sampled condensed element matrices of
+    every layer against the oracle recomputed on the spot, theta on the three
+    smoothed levels, ||b||, iterations within 10% and the relative L2 error of
+    the whole solution (sketch) at the parity bar."""
+    w = workloads.config3(precision)
+    pk, ok = w["problem"], w["opts"]
+    with D.Solver(pk, **ok) as s:
+        assert [s.level(l).n_dof for l in range(4)] == GOLD3["level_dofs"]
+        m = Mesh(pk["n"], pk["p"], pk["x0"], pk["x1"])
+        ld = GaussianSource(pk["src_center"], pk["src_width"])
+        c = np.asarray(pk["wavespeed"])
+        nx, ny, nz = pk["n"]
+        for e in [0, nx * ny * nz - 1, nx * ny * 3 + nx * 5 + 7, nx * ny * 8 + nx * 16 + 16,
+                  nx * ny * 12 + nx * 31, nx * ny * 15 + nx * 10 + 20]:
+            bf = boundary_faces(m, e)
+            corner = m.x0 + np.asarray(m.elem_coord(e)) * m.h
+            K, F = dpg_element(m.p, m.h, corner, c[e], pk["omega"], bf, ld)
+            Kc, Fc = condense(m.p, K, F, bf)
+            G, Fg = D.dpgmg_element_matrix(s.h, s.s, 3, e, Kc.shape[0], with_load=True)
+            assert np.linalg.norm(G - Kc) / np.linalg.norm(Kc) < 1e-11, e
+            if np.linalg.norm(Fc) > 1e-30:
+                assert np.linalg.norm(Fg - Fc) / np.linalg.norm(Fc) < 1e-10, e
+        for l, th in enumerate(GOLD3["theta"], start=1):
+            assert abs(s.level(l).theta - th) < (1e-8 if precision == "fp64" else MIXED_THETA_TOL) * th, l
+        b = D.dpgmg_rhs(s.h, s.s, s.n_trace)
+        assert abs(np.linalg.norm(b) - GOLD3["norm_b"]) < 1e-11 * GOLD3["norm_b"]
+        x, f, st, code = s.solve(fields=False)
+    assert code == D.DPGMG_OK
+    assert st.relres <= 1e-8 and st.true_relres <= 1e-8
+    assert abs(st.iters - GOLD3["iters"]) <= max(1, round(0.1 * GOLD3["iters"])), (st.iters, GOLD3["iters"])
+    l2 = sketch_error(x, GOLD3)
+    print("layered medium, solution error vs oracle (%s): relative L2 (sketch) %.3e, iterations %d (oracle %d)"
+          % (precision, l2, st.iters, GOLD3["iters"]))
+    assert l2 < 1e-7, l2
+    assert abs(np.linalg.norm(x) - GOLD3["norm_x"]) < 1e-7 * GOLD3["norm_x"]
