@@ -205,6 +205,19 @@ void dpgmg_destroy(dpgmg_handle h);
 int dpgmg_query_sizes(const dpgmg_problem* pb, const dpgmg_opts* op,
                       long long* n_trace, long long* n_field, size_t* dev_bytes);
 
+/* Entity and mode of every global trace DOF of a problem's finest mesh (the
+ * numbering documented above), without touching the device.  out: host int
+ * [n_trace][7], per DOF (kind, cx, cy, cz, axis, m1, m2):
+ *   kind 0 vertex, 1 edge, 2 face (p-hat), 3 interior face (u-hat_n);
+ *   (cx, cy, cz) the entity's centre in half-element units (vertex (i,j,k)
+ *   at (2i, 2j, 2k), the x-edge from it at (2i+1, 2j, 2k));
+ *   axis the edge direction (edges) or face normal (faces), -1 for vertices;
+ *   (m1, m2) the H^1 mode of an edge (m1 = 2..p, m2 = -1), the H^1 modes of
+ *   a face's tangential axes in increasing axis order (2..p each), or the
+ *   Legendre modes (a, b) of a u-hat face (0..p-1 each); -1 for vertices.
+ * n_trace must equal the count dpgmg_query_sizes reports.  Errors: ARG. */
+int dpgmg_dof_map(const dpgmg_problem* pb, long long n_trace, int* out);
+
 /* Default options: tol 1e-8, max_iter 2000, V(1,1), 2 levels, p_min 2, FP64,
  * Cholesky coarsest, theta estimated. */
 void dpgmg_default_opts(dpgmg_opts* op);

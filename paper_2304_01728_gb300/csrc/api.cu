@@ -354,6 +354,58 @@ void dpgmg_destroy(dpgmg_handle h) {
   delete h;
 }
 
+int dpgmg_dof_map(const dpgmg_problem* pb, long long n_trace, int* out) {
+  if (!pb || !out) return DPGMG_ERR_ARG;
+  for (int d = 0; d < 3; ++d)
+    if (pb->n[d] < 1 || !(pb->x1[d] > pb->x0[d])) return DPGMG_ERR_ARG;
+  if (pb->p < 1 || pb->p > 5) return DPGMG_ERR_ARG;
+  MeshL m;
+  m.init(pb->n, pb->p, pb->x0, pb->x1);
+  if (n_trace != m.ndof) {
+    set_last_error("dpgmg_dof_map: n_trace differs from the mesh's trace DOF count");
+    return DPGMG_ERR_ARG;
+  }
+  const int p = pb->p;
+  for (int64_t g = 0; g < m.ndof; ++g) {
+    const int64_t E = m.dof_entity(g);
+    int ctr[3];
+    m.ent_center(E, ctr);
+    int64_t st;
+    int nd;
+    m.ent_range(E, &st, &nd);
+    const int loc = (int)(g - st);
+    int kind, axis = -1, m1 = -1, m2 = -1;
+    if (E < m.entE) {
+      kind = 0;
+    } else if (E < m.entF) {
+      kind = 1;
+      for (int d = 0; d < 3; ++d)
+        if (ctr[d] & 1) axis = d;
+      m1 = loc + 2;
+    } else {
+      kind = E < m.entU ? 2 : 3;
+      for (int d = 0; d < 3; ++d)
+        if (!(ctr[d] & 1)) axis = d;
+      if (kind == 2) {
+        m1 = loc % (p - 1) + 2;
+        m2 = loc / (p - 1) + 2;
+      } else {
+        m1 = loc % p;
+        m2 = loc / p;
+      }
+    }
+    int* o = out + 7 * g;
+    o[0] = kind;
+    o[1] = ctr[0];
+    o[2] = ctr[1];
+    o[3] = ctr[2];
+    o[4] = axis;
+    o[5] = m1;
+    o[6] = m2;
+  }
+  return DPGMG_OK;
+}
+
 int dpgmg_query_sizes(const dpgmg_problem* pb, const dpgmg_opts* op, long long* n_trace, long long* n_field,
                       size_t* dev_bytes) {
   int v = validate_problem(pb, op);

@@ -68,7 +68,8 @@ EXPORTS = ["dpgmg_create", "dpgmg_destroy", "dpgmg_query_sizes", "dpgmg_default_
            "dpgmg_solve", "dpgmg_release", "dpgmg_strerror", "dpgmg_last_error", "dpgmg_level_info",
            "dpgmg_element_matrix", "dpgmg_rhs", "dpgmg_apply", "dpgmg_launch_count", "dpgmg_profile",
            "dpgmg_profile_read", "dpgmg_smooth_noalloc", "dpgmg_serve_start", "dpgmg_submit", "dpgmg_poll",
-           "dpgmg_spmv_group", "dpgmg_setup_profile", "dpgmg_error_indicator", "dpgmg_setup_phases"]
+           "dpgmg_spmv_group", "dpgmg_setup_profile", "dpgmg_error_indicator", "dpgmg_setup_phases",
+           "dpgmg_dof_map"]
 PROF_OFF, PROF_SMOOTH_FINE, PROF_SPMV_FINE, PROF_SPMV_CG = 0, 1, 2, 3
 
 
@@ -118,6 +119,8 @@ def lib():
     L.dpgmg_setup_profile.restype = i
     L.dpgmg_setup_phases.argtypes = [vp, vp, ctypes.POINTER(d), i]
     L.dpgmg_setup_phases.restype = i
+    L.dpgmg_dof_map.argtypes = [ctypes.POINTER(dpgmg_problem), ll, ctypes.POINTER(i)]
+    L.dpgmg_dof_map.restype = i
     L.dpgmg_error_indicator.argtypes = [vp, vp, dptr, dptr]
     L.dpgmg_error_indicator.restype = i
     L.dpgmg_profile_read.argtypes = [vp, vp, ctypes.POINTER(d), ctypes.POINTER(ll), ctypes.POINTER(ll)]
@@ -261,6 +264,14 @@ def dpgmg_poll(h, ticket, trace_out=None, field_out=None):
     fp = field_out.ctypes.data if isinstance(field_out, np.ndarray) else field_out
     code = lib().dpgmg_poll(h, ctypes.c_longlong(ticket), tp, fp, ctypes.byref(st), ctypes.byref(lat))
     return code, st, lat.value
+
+
+def dpgmg_dof_map(pb, n_trace):
+    """Per global trace DOF: (kind, cx, cy, cz, axis, m1, m2) as an int array [n_trace, 7]."""
+    out = np.zeros((n_trace, 7), dtype=np.int32)
+    _check(lib().dpgmg_dof_map(ctypes.byref(pb), n_trace, out.ctypes.data_as(ctypes.POINTER(ctypes.c_int))),
+           "dpgmg_dof_map")
+    return out
 
 
 def dpgmg_launch_count():

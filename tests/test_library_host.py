@@ -60,3 +60,29 @@ def test_struct_layouts_match_header(libpath):
     assert ctypes.sizeof(dpgmg.dpgmg_opts) == 48
     assert ctypes.sizeof(dpgmg.dpgmg_stats) == 64
     assert ctypes.sizeof(dpgmg.dpgmg_level_desc) == 88
+
+
+@pytest.mark.parametrize("n,p", [((3, 2, 4), 3), ((2, 2, 2), 1), ((1, 3, 2), 5)])
+def test_dof_map_matches_the_oracle_numbering(libpath, n, p):
+    """dpgmg_dof_map (host only) against the oracle's own DOF table: entity
+    kind, doubled centre and modes of every global trace DOF, in order."""
+    import numpy as np
+    from oracle.mesh import Mesh
+    from paper_2304_01728_gb300 import dpgmg
+    pb, keep = dpgmg.make_problem(n=n, p=p, omega=3.0)
+    nt, _, _ = dpgmg.dpgmg_query_sizes(pb, dpgmg.make_opts())
+    got = dpgmg.dpgmg_dof_map(pb, nt)
+    tab = Mesh(n, p).dof_table()
+    assert len(tab) == nt
+    kinds = {"v": 0, "e": 1, "f": 2, "u": 3}
+    for g, (k, ctr, modes) in enumerate(tab):
+        row = got[g]
+        assert row[0] == kinds[k] and tuple(row[1:4]) == tuple(ctr), (g, row, k, ctr)
+        if k == "v":
+            assert tuple(row[4:]) == (-1, -1, -1)
+        elif k == "e":
+            assert tuple(row[4:6]) == modes and row[6] == -1, (g, row, modes)
+        else:
+            assert tuple(row[4:]) == modes, (g, row, modes)
+    with pytest.raises(dpgmg.DpgmgError):
+        dpgmg.dpgmg_dof_map(pb, nt + 1)
