@@ -79,6 +79,9 @@ extern "C" {
 #define DPGMG_COARSEST_CHOLESKY 0   /* dense Cholesky solve on level 0 */
 #define DPGMG_COARSEST_NONE     1   /* no level-0 correction (Sec. 4 list) */
 #define DPGMG_COARSEST_AUTO     2   /* CHOLESKY if level 0 has at most 20,000 DOFs, else NONE */
+#define DPGMG_COARSEST_SMOOTH   3   /* one damped additive-Schwarz step on level 0 (vertex patches of
+                                       its own mesh, damping by the same power iteration) instead of
+                                       a solve; a single-level system still uses CHOLESKY */
 
 /* ---- problem and options ----------------------------------------------- */
 typedef struct dpgmg_problem {

@@ -33,7 +33,9 @@ power iterations of S M started from a SplitMix64 vector (seed 12345).
 
 Coarsest level: dense Cholesky factorisation of A_0 (the paper solves its
 initial mesh directly with MUMPS, Sec. 4 list; option "none" is its "no
-initial-grid solver during the iteration").
+initial-grid solver during the iteration"; option "smooth" applies one damped
+additive Schwarz step on level 0 instead, with the vertex patches of level 0's
+own mesh and theta from the same power iteration).
 """
 import itertools
 
@@ -349,8 +351,17 @@ def build_hierarchy(fine_mesh, Kc, dofs, n_levels, p_min=2, coarsest="cholesky",
     c0 = levels[-1]
     c0.A = assemble(c0.E, c0.dofs, c0.mesh.n_dof).toarray()
     c0.coarsest = coarsest
-    if coarsest == "cholesky":
+    if coarsest == "cholesky" or len(levels) == 1:
+        c0.coarsest = "cholesky"
         c0.chol = sla.cho_factor(c0.A, lower=True)
+    elif coarsest == "smooth":
+        # level 0 smoothed with the vertex patches of its own mesh (the p-level
+        # rule with the level itself as the coarse mesh)
+        c0.M = sp.csr_matrix(c0.A)
+        c0.smask = np.ones(c0.mesh.n_dof, dtype=bool)
+        c0.patches = _patch_rule_R1(c0.mesh, c0.mesh, c0.mesh.dof_table(), "p", c0.smask)
+        c0.patch_inv = [np.linalg.inv(c0.A[np.ix_(idx, idx)]) for idx in c0.patches]
+        c0.theta = theta if theta is not None else estimate_theta(c0)
     levels.reverse()
     return levels
 

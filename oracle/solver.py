@@ -30,6 +30,8 @@ def vcycle(levels, l, r, nu_pre=1, nu_post=1):
     if l == 0:
         if lev.coarsest == "cholesky":
             return sla.cho_solve(lev.chol, r)
+        if lev.coarsest == "smooth":
+            return lev.theta * smoother(lev, r)
         return np.zeros_like(r)
     if lev.kind == "h":
         rs = np.where(lev.smask, r, 0.0)

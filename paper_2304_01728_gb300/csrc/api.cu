@@ -83,7 +83,7 @@ int validate_problem(const dpgmg_problem* pb, const dpgmg_opts* op) {
   if (!(op->tol > 0.0) || op->max_iter < 1 || op->nu_pre < 0 || op->nu_post < 0 || op->n_levels < 1 ||
       op->p_min < 1 || (op->precision != DPGMG_PREC_FP64 && op->precision != DPGMG_PREC_MIXED) ||
       (op->coarsest != DPGMG_COARSEST_CHOLESKY && op->coarsest != DPGMG_COARSEST_NONE &&
-       op->coarsest != DPGMG_COARSEST_AUTO) ||
+       op->coarsest != DPGMG_COARSEST_AUTO && op->coarsest != DPGMG_COARSEST_SMOOTH) ||
       (op->flags & ~(DPGMG_FLAG_EAGER | DPGMG_FLAG_CUDA_CORES | DPGMG_FLAG_STORE_COARSE | DPGMG_FLAG_WARM_START |
                      DPGMG_FLAG_CG_C128 | DPGMG_FLAG_PATCH_FP64 | DPGMG_FLAG_FAULT_NOT_HPD |
                      DPGMG_FLAG_FAULT_TC_WAIT)))
@@ -132,7 +132,8 @@ size_t estimate_bytes(const dpgmg_problem* pb, const dpgmg_opts* op) {
     if (i == 0) xdofs = nd;
     if (i > 0) resident += nel * nl * nl * 16.0;                      // restricted element matrices
     resident += nel * nl * 8.0 + nd * 4.0 * (16.0 + x32) + nd * 80.0; // maps, work vectors, row indices, SpMV tasks
-    if (s.kind_below != 0) {
+    const bool smooth0 = s.kind_below == 0 && op->coarsest == DPGMG_COARSEST_SMOOTH && specs.size() > 1;
+    if (s.kind_below != 0 || smooth0) {
       const int q = s.p;
       const bool hlev = s.kind_below == 2;
       const double nS = 6.0 * (4.0 * (q - 1) * (q - 1) + 4.0 * (q - 1) + 1.0 + 4.0 * q * q) + 12.0 * (2.0 * (q - 1) + 1.0) + 8.0;
@@ -676,8 +677,8 @@ int dpgmg_apply(dpgmg_handle h, dpgmg_system sys, int op, int level, const doubl
   const int nl = (int)S.levels.size();
   if (level < 0 || level >= nl || op < 0 || op > DPGMG_OP_AFULL) return DPGMG_ERR_ARG;
   const Level& L = S.levels[level];
-  if ((op == DPGMG_OP_A || op == DPGMG_OP_SMOOTH || op == DPGMG_OP_RESTRICT || op == DPGMG_OP_PROLONG) && level == 0)
-    return DPGMG_ERR_ARG;
+  if ((op == DPGMG_OP_RESTRICT || op == DPGMG_OP_PROLONG) && level == 0) return DPGMG_ERR_ARG;
+  if ((op == DPGMG_OP_A || op == DPGMG_OP_SMOOTH) && level == 0 && L.P.np == 0) return DPGMG_ERR_ARG;
   if (op == DPGMG_OP_CONDENSE && L.kind != 2) return DPGMG_ERR_ARG;
   if (op == DPGMG_OP_COARSE && (level != 0 || !L.has_coarse)) return DPGMG_ERR_ARG;
   if (op == DPGMG_OP_AFULL && level != nl - 1) return DPGMG_ERR_ARG;

@@ -584,6 +584,12 @@ static void setup_patches(SystemImpl& S, Level& F, const LevelPlan& lp, int* din
   invert_patches<double2>(A, D, lp, D.inv64, F.mesh.offU, dinfo, st);
 }
 
+// DPGMG_COARSEST_SMOOTH on a hierarchy with more than one level: level 0 is
+// smoothed (its own operator and vertex patches) instead of solved.
+static bool smooth_coarsest(const SystemImpl& S) {
+  return S.op.coarsest == DPGMG_COARSEST_SMOOTH && S.levels.size() > 1;
+}
+
 // Host index plan of a hierarchy (every level's integer structures); runs on
 // host threads concurrently with the element stage: one per level (the levels'
 // structures are independent) and one for the CG operator's lists, each of
@@ -593,7 +599,7 @@ std::shared_ptr<HostPlan> plan_host(const SystemImpl& S) {
   const int L = (int)S.levels.size() - 1;
   HP->lv.resize(L + 1);
   std::vector<std::thread> th;
-  std::vector<std::exception_ptr> errs(L + 2);
+  std::vector<std::exception_ptr> errs(L + 3);
   auto guarded = [&errs](int slot, auto&& f) {
     return [&errs, slot, f]() {
       try {
@@ -603,17 +609,22 @@ std::shared_ptr<HostPlan> plan_host(const SystemImpl& S) {
       }
     };
   };
-  th.emplace_back(guarded(0, [&]() { HP->fdofs = elem_dof_table(S.levels[L].mesh); }));
+  th.emplace_back(guarded(L + 2, [&]() { HP->fdofs = elem_dof_table(S.levels[L].mesh); }));
   if (L == 0 || S.levels[L].kind != 1) {
     HP->has_acg = true;
     th.emplace_back(guarded(L + 1, [&]() { HP->acg = prep_ecsr(S.levels[L].mesh, element_groups(S.levels[L].mesh)); }));
   }
-  for (int l = L; l >= 1; --l) th.emplace_back(guarded(l, [&S, &HP, l]() {
+  const int lmin = smooth_coarsest(S) ? 0 : 1;
+  for (int l = L; l >= lmin; --l) th.emplace_back(guarded(l, [&S, &HP, l]() {
     const Level& F = S.levels[l];
-    const Level& C = S.levels[l - 1];
+    const Level& C = S.levels[l > 0 ? l - 1 : 0];   // level 0: the vertex patches of its own mesh
     LevelPlan& lp = HP->lv[l];
-    lp.cdofs = elem_dof_table(C.mesh);
-    if (F.kind == 1) {
+    if (l > 0) lp.cdofs = elem_dof_table(C.mesh);
+    if (l == 0) {
+      lp.E = prep_ecsr(F.mesh, element_groups(F.mesh));
+      lp.smask.assign(F.mesh.ndof, 1);
+      lp.H = 2;
+    } else if (F.kind == 1) {
       p_selection(F.mesh.p, lp.sel);
       p_injection(F.mesh, C.mesh, lp.inj);
       lp.E = prep_ecsr(F.mesh, element_groups(F.mesh));
@@ -686,6 +697,7 @@ void build_hierarchy(SystemImpl& S, cudaStream_t st) {
   int* dinfo = A.arr<int>(1);
   DPG_CUDA(cudaMemsetAsync(dinfo, 0, sizeof(int), st));
   const bool dense = S.op.coarsest == DPGMG_COARSEST_CHOLESKY || L == 0 ||
+                     (S.op.coarsest == DPGMG_COARSEST_SMOOTH && L == 0) ||
                      (S.op.coarsest == DPGMG_COARSEST_AUTO && S.levels[0].mesh.ndof <= 20000);
   // The coarsest factorisation (FP32/FP64 dense work) runs on a side stream from
   // a second host thread as soon as level 0's element matrices exist, overlapping
@@ -775,11 +787,17 @@ void build_hierarchy(SystemImpl& S, cudaStream_t st) {
       element_stage_level(S, C, st);
     }
   }
+  const int lmin = smooth_coarsest(S) ? 0 : 1;
+  if (lmin == 0) {   // level 0 smoothed: its own assembled operator
+    Level& C0 = S.levels[0];
+    assemble_ecsr(A, HP.lv[0].E, C0.A, st);
+    ecsr_add_elements(C0.A, C0.E, C0.dofs, C0.mesh.nelem, C0.nloc, 0, C0.mesh.n, st);
+  }
   if (S.ph_ev) DPG_CUDA(cudaEventRecord(S.ph_ev[2], st));
   if (L >= 1 && dense) start_coarse();
   // theta's Rayleigh quotient stays on the device until the end of the build
   double* dtheta = A.arr<double>((size_t)2 * (L + 1));
-  for (int l = L; l >= 1; --l) {
+  for (int l = L; l >= lmin; --l) {
     Level& F = S.levels[l];
     const LevelPlan& lp = HP.lv[l];
     F.n_smooth = 0;
@@ -864,7 +882,7 @@ void build_hierarchy(SystemImpl& S, cudaStream_t st) {
   DPG_CUDA(cudaMemcpyAsync(th.data(), dtheta, th.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
   DPG_CUDA(cudaStreamSynchronize(st));
   A.release(dtheta);
-  for (int l = 1; l <= L; ++l)
+  for (int l = lmin; l <= L; ++l)
     if (!(S.op.theta > 0.0)) S.levels[l].theta = theta_from_rayleigh(th[2 * l], th[2 * l + 1]);
   info |= info_main;
   if (info & 32) throw Err{DPGMG_ERR_TIMEOUT, "tensor-core update: a bounded wait for the MMAs ran out"};

@@ -967,7 +967,7 @@ static void alloc_level_ws(WS& W, SystemImpl& S) {
     v[l].rs = S.mem.arr<C>((size_t)n);
     v[l].x = S.mem.arr<C>((size_t)n);
     v[l].t = S.mem.arr<C>((size_t)n);
-    if (l >= 1) v[l].pbuf = S.mem.arr<C>((size_t)std::max<int64_t>(L.P.scratch_entries(), 1));
+    if (l >= 1 || L.P.np > 0) v[l].pbuf = S.mem.arr<C>((size_t)std::max<int64_t>(L.P.scratch_entries(), 1));
     if (L.kind == 2) v[l].cbuf = S.mem.arr<C>((size_t)L.nK * L.nS);
   }
 }
@@ -1059,6 +1059,7 @@ static void vcycle(SystemImpl& S, WS& W, int l, const C* r, C* x, cudaStream_t s
   const int64_t n = F.mesh.ndof;
   if (l == 0) {
     if (F.has_coarse) coarse_solve<C>(S, W, r, x, st);
+    else if (F.P.np > 0) smooth<C>(F, r, x, F.theta, 0, V[0].pbuf, st);   // DPGMG_COARSEST_SMOOTH
     else {
       k_zero<C><<<nblk(n), 256, 0, st>>>(x, n);
       DPG_CHECK_LAUNCH();

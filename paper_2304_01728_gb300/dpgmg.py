@@ -20,7 +20,7 @@ DPGMG_ERR_ARG, DPGMG_ERR_NOMEM, DPGMG_ERR_NOT_HPD, DPGMG_ERR_BREAKDOWN = -1, -2,
 DPGMG_ERR_NOT_CONVERGED, DPGMG_ERR_TIMEOUT, DPGMG_ERR_PENDING, DPGMG_ERR_CUDA = -5, -6, -7, -8
 SRC_GAUSSIAN, SRC_PLANE_WAVE, SRC_MANUFACTURED = 0, 1, 2
 PREC_FP64, PREC_MIXED = 0, 1
-COARSEST_CHOLESKY, COARSEST_NONE, COARSEST_AUTO = 0, 1, 2
+COARSEST_CHOLESKY, COARSEST_NONE, COARSEST_AUTO, COARSEST_SMOOTH = 0, 1, 2, 3
 FLAG_EAGER, FLAG_CUDA_CORES, FLAG_STORE_COARSE, FLAG_WARM_START, FLAG_CG_C128 = 1, 2, 4, 8, 16
 FLAG_PATCH_FP64 = 32
 FLAG_FAULT_NOT_HPD, FLAG_FAULT_TC_WAIT = 1 << 28, 1 << 29
@@ -175,7 +175,8 @@ def make_opts(**kw):
         if k == "precision" and isinstance(v, str):
             v = {"fp64": PREC_FP64, "mixed": PREC_MIXED}[v]
         if k == "coarsest" and isinstance(v, str):
-            v = {"cholesky": COARSEST_CHOLESKY, "none": COARSEST_NONE, "auto": COARSEST_AUTO}[v]
+            v = {"cholesky": COARSEST_CHOLESKY, "none": COARSEST_NONE, "auto": COARSEST_AUTO,
+                 "smooth": COARSEST_SMOOTH}[v]
         setattr(op, k, v)
     return op
 

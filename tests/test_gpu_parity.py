@@ -405,3 +405,38 @@ def test_error_statuses():
     with D.Solver(w["problem"], **dict(w["opts"], max_iter=2)) as s:
         x, f, st, code = s.solve()
         assert code == D.DPGMG_ERR_NOT_CONVERGED and st.iters == 2 and np.linalg.norm(x) > 0
+
+
+@pytest.mark.parametrize("nl,precision", [(2, "fp64"), (3, "fp64"), (3, "mixed")])
+def test_smoothing_coarsest_matches_oracle(nl, precision):
+    """DPGMG_COARSEST_SMOOTH: one damped additive Schwarz step on level 0 with
+    the vertex patches of its own mesh.  Level 0's patches and theta, its
+    smoother and the whole V-cycle against the oracle; PCG iterations and
+    solution at the parity bar."""
+    from oracle.hierarchy import smoother
+    from tests.oracle_adapter import MIXED_THETA_TOL, MIXED_VCYCLE_TOL
+    pk = dict(n=(4, 4, 4), p=2, omega=4.0, src_center=(0.4, 0.55, 0.5), src_width=0.2)
+    ok = dict(n_levels=nl, p_min=1, precision=precision, tol=1e-8, coarsest="smooth")
+    fs, A, b, levels = oracle_system(pk, ok)
+    o0 = levels[0]
+    L = len(levels) - 1
+    with D.Solver(pk, **ok) as s:
+        g0 = s.level(0)
+        sizes = np.array([len(x) for x in o0.patches])
+        assert g0.n_patches == len(sizes) and g0.patch_max == sizes.max()
+        assert g0.sum_patch_sq == int(np.sum(sizes ** 2))
+        th_tol = 1e-9 if precision == "fp64" else MIXED_THETA_TOL
+        assert abs(g0.theta - o0.theta) < th_tol * o0.theta, (g0.theta, o0.theta)
+        n0 = o0.mesh.n_dof
+        x = rand_vec(n0, 3)
+        y = D.dpgmg_apply(s.h, s.s, D.OP_SMOOTH, 0, x, n0)
+        vtol = 1e-10 if precision == "fp64" else MIXED_VCYCLE_TOL
+        assert rel(y, o0.theta * smoother(o0, x)) < vtol
+        n = A.shape[0]
+        v = rand_vec(n, 4)
+        assert rel(D.dpgmg_apply(s.h, s.s, D.OP_VCYCLE, L, v, n), vcycle(levels, L, v)) < vtol
+        xs, f, st, code = s.solve()
+    x_ref, it_ref, _ = mg_pcg(levels, A, b, tol=ok["tol"])
+    assert code == D.DPGMG_OK
+    assert abs(st.iters - it_ref) <= max(1, 0.1 * it_ref), (st.iters, it_ref)
+    assert rel(xs, x_ref) < 1e-7

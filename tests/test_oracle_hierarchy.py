@@ -241,3 +241,35 @@ def test_stored_vcycle_hermitian_positive_and_same_solution(stored_ph, small_ph)
     x_s, it_s, _ = mg_pcg(levels, A, b, tol=1e-12)
     x_r, it_r, _ = mg_pcg(small_ph[3], A, b, tol=1e-12)
     assert np.linalg.norm(x_s - x_r) <= 1e-9 * np.linalg.norm(x_r)
+
+
+@pytest.mark.parametrize("nl,pmin", [(2, 1), (3, 1)])
+def test_smoothing_coarsest_mode(nl, pmin):
+    """Coarsest mode "smooth" (one damped additive Schwarz step on level 0 with
+    the vertex patches of its own mesh): the V-cycle stays Hermitian positive,
+    theta_0 is within 5% below the largest eigenvalue of S_0 A_0 (dense), and
+    PCG reaches the dense solve."""
+    fs = build_fine((4, 4, 4), 2, 4.0, load=GaussianSource((0.4, 0.55, 0.5), 0.2))
+    A, b = fs.assemble()
+    levels = build_hierarchy(fs.mesh, fs.Kc, fs.dofs, n_levels=nl, p_min=pmin, coarsest="smooth")
+    c0 = levels[0]
+    assert c0.coarsest == "smooth" and len(c0.patches) == int(np.prod(np.asarray(c0.mesh.n) + 1))
+    N0 = c0.A.shape[0]
+    SA = np.zeros((N0, N0), dtype=np.complex128)
+    for j in range(N0):
+        e = np.zeros(N0, dtype=np.complex128)
+        e[j] = 1
+        SA[:, j] = smoother(c0, c0.A @ e)
+    lam = np.max(np.linalg.eigvals(SA).real)
+    est = 1.0 / (1.05 * c0.theta)
+    assert est <= lam * (1 + 1e-10) and est >= 0.95 * lam
+    L = len(levels) - 1
+    rng = np.random.default_rng(8)
+    u = rng.standard_normal(A.shape[0]) + 1j * rng.standard_normal(A.shape[0])
+    v = rng.standard_normal(A.shape[0]) + 1j * rng.standard_normal(A.shape[0])
+    Bu, Bv = vcycle(levels, L, u), vcycle(levels, L, v)
+    assert abs(np.vdot(v, Bu) - np.vdot(Bv, u)) / (np.linalg.norm(u) * np.linalg.norm(Bv)) < 1e-12
+    assert np.vdot(u, Bu).real > 0
+    x, it, hist = mg_pcg(levels, A, b, tol=1e-12)
+    x_ref = np.linalg.solve(A.toarray(), b)
+    assert np.linalg.norm(x - x_ref) / np.linalg.norm(x_ref) < 1e-9
