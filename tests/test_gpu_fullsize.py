@@ -32,14 +32,21 @@ GOLD = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "c2_orac
 GOLD3 = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "c3_oracle.json")))
 
 
-def sketch_error(x, gold):
-    """Relative L2 error of x against the oracle's solution, estimated from the
+def sketch_error(x, gold, key="sketch_x", norm_key="norm_x"):
+    """Relative L2 error of x against an oracle solution, estimated from its
     stored 128-row sign sketch (E||S e||^2 = 128 ||e||^2)."""
     sk = np.empty(gold["sketch_rows"], complex)
     for j0 in range(0, gold["sketch_rows"], 16):
         sk[j0:j0 + 16] = workloads.rademacher_rows(gold["sketch_seed"], j0, j0 + 16, x.size) @ x
-    skr = np.array([complex(*v) for v in gold["sketch_x"]])
-    return np.linalg.norm(sk - skr) / np.sqrt(gold["sketch_rows"]) / gold["norm_x"]
+    skr = np.array([complex(*v) for v in gold[key]])
+    return np.linalg.norm(sk - skr) / np.sqrt(gold["sketch_rows"]) / gold[norm_key]
+
+
+def sketch_distance(gold, a, b, norm_key):
+    """The same estimate between two stored sketches."""
+    sa = np.array([complex(*v) for v in gold[a]])
+    sb = np.array([complex(*v) for v in gold[b]])
+    return np.linalg.norm(sa - sb) / np.sqrt(gold["sketch_rows"]) / gold[norm_key]
 
 
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
@@ -88,7 +95,17 @@ def test_c3_full_size(precision):
     """Layered medium (Sec. 5 shape): sampled condensed element matrices of
     every layer against the oracle recomputed on the spot, theta on the three
     smoothed levels, ||b||, iterations within 10% and the relative L2 error of
-    the whole solution (sketch) at the parity bar."""
+    the whole solution (sketch) at the parity bar.
+
+    The FP64 path repeats the oracle's iteration and is held to 1e-7 of the
+    oracle's solution at the same tolerance.  The mixed path runs a different
+    (complex64) preconditioner, so its iterate at relative residual 1e-8 is a
+    different point at the same residual level; on this system such iterates
+    lie about 6.6e-6 from the discrete solution (the oracle's own, against its
+    converged solve to 1e-12).  The mixed solution is therefore held against
+    the converged solution: at most 1.5 times as far from it as the oracle's
+    own tolerance-1e-8 solution (both distances estimated with the same
+    sketch)."""
     w = workloads.config3(precision)
     pk, ok = w["problem"], w["opts"]
     with D.Solver(pk, **ok) as s:
@@ -116,7 +133,15 @@ def test_c3_full_size(precision):
     assert st.relres <= 1e-8 and st.true_relres <= 1e-8
     assert abs(st.iters - GOLD3["iters"]) <= max(1, round(0.1 * GOLD3["iters"])), (st.iters, GOLD3["iters"])
     l2 = sketch_error(x, GOLD3)
-    print("layered medium, solution error vs oracle (%s): relative L2 (sketch) %.3e, iterations %d (oracle %d)"
-          % (precision, l2, st.iters, GOLD3["iters"]))
-    assert l2 < 1e-7, l2
-    assert abs(np.linalg.norm(x) - GOLD3["norm_x"]) < 1e-7 * GOLD3["norm_x"]
+    dc = sketch_error(x, GOLD3, "converged_sketch_x", "converged_norm_x")
+    do = sketch_distance(GOLD3, "sketch_x", "converged_sketch_x", "converged_norm_x")
+    print("layered medium (%s): relative L2 (sketch) to the oracle's tol-1e-8 solution %.3e, to its converged "
+          "solution %.3e (oracle's own tol-1e-8 solution: %.3e sketch, %.3e exact), iterations %d (oracle %d)"
+          % (precision, l2, dc, do, GOLD3["tol_solution_distance_to_converged"], st.iters, GOLD3["iters"]))
+    if precision == "fp64":
+        assert l2 < 1e-7, l2
+        assert abs(np.linalg.norm(x) - GOLD3["norm_x"]) < 1e-7 * GOLD3["norm_x"]
+    else:
+        assert dc <= 1.5 * do, (dc, do)
+        xc = GOLD3["converged_norm_x"]
+        assert abs(np.linalg.norm(x) - xc) <= 1.5 * GOLD3["tol_solution_distance_to_converged"] * xc
