@@ -27,7 +27,9 @@ transition is element-local:
 
 Smoother (Sec. 3 "V-cycle and smoother"): additive Schwarz with one block per
 vertex w of the next coarser mesh; a DOF belongs to block w when every
-(macro-)element adjacent to its entity has w as a corner (rule R1).  Blocks
+(macro-)element adjacent to its entity has w as a corner (rule R1), or, as
+an option, when w lies in the closure of the (macro-)entity carrying the DOF
+(rule R2; the two differ only at the boundary).  Blocks
 are inverted densely.  Damping theta = 1 / (1.05 lambda), lambda from 30
 power iterations of S M started from a SplitMix64 vector (seed 12345).
 
@@ -239,15 +241,50 @@ def _patch_rule_R1(lev_mesh, coarse_mesh, table, kind, smask):
     return out
 
 
+def _patch_rule_R2(lev_mesh, coarse_mesh, table, kind, smask):
+    """Vertex patches (rule R2) of the smoothing space of a level.
+
+    A DOF belongs to block w when w lies in the closure of the coarse entity
+    that carries it: on a p level the DOF's own entity, on an h level the
+    coarse (macro) entity in whose relative interior the fine entity lies.
+    Per axis that closure is the single coarse plane the entity centre lies
+    on, or else the two coarse planes around it.  The two rules differ only on
+    DOFs of boundary entities: R1 also gives those to the vertices one layer
+    inside (the one adjacent element has them as corners), R2 does not.
+    Returns a list over coarse vertices of sorted DOF index arrays.
+    """
+    H = 2 if kind == "p" else 4
+    nco = coarse_mesh.n
+    members = {}
+    for i, (kd, ctr, _) in enumerate(table):
+        if not smask[i]:
+            continue
+        span = [(ctr[d] // H,) if ctr[d] % H == 0 else (ctr[d] // H, ctr[d] // H + 1) for d in range(3)]
+        for w in itertools.product(*span):
+            members.setdefault(w, []).append(i)
+    out = []
+    for w in itertools.product(*[range(v + 1) for v in reversed(nco)]):
+        w = (w[2], w[1], w[0])
+        out.append(np.array(sorted(members.get(w, [])), dtype=np.int64))
+    return out
+
+
+PATCH_RULES = {"R1": _patch_rule_R1, "R2": _patch_rule_R2}
+
+
 def build_hierarchy(fine_mesh, Kc, dofs, n_levels, p_min=2, coarsest="cholesky",
-                    theta=None, stored=None):
+                    theta=None, stored=None, patch_rule="R1"):
     """All levels from the fine element matrices Kc (condensed) and DOF maps.
 
     Coarse operators are restricted (Sec. 3, A_c = I^* M I) unless ``stored``
     is given: stored(mesh) returns the condensed element matrices of the DPG
     system assembled directly on a coarser mesh (the paper's "stored"
     alternative), which then replace the restricted ones level by level.
+    ``patch_rule`` picks the vertex-patch membership at the boundary ("R1",
+    the default, or "R2"; the paper does not say which, Sec. 3 "V-cycle and
+    smoother").
     """
+    rule = PATCH_RULES[patch_rule]
     specs, kinds = level_specs(fine_mesh.n, fine_mesh.p, n_levels, p_min)
     levels = []
     top = Level()
@@ -342,7 +379,7 @@ def build_hierarchy(fine_mesh, Kc, dofs, n_levels, p_min=2, coarsest="cholesky",
                 lev.smask[Sg] = True
         if stored is not None:
             crs.E = stored(cmesh)
-        lev.patches = _patch_rule_R1(lev.mesh, cmesh, lev.mesh.dof_table(), kind, lev.smask)
+        lev.patches = rule(lev.mesh, cmesh, lev.mesh.dof_table(), kind, lev.smask)
         Md = lev.M
         lev.patch_inv = [np.linalg.inv(Md[idx][:, idx].toarray()) for idx in lev.patches]
         lev.theta = theta if theta is not None else estimate_theta(lev)
@@ -359,7 +396,7 @@ def build_hierarchy(fine_mesh, Kc, dofs, n_levels, p_min=2, coarsest="cholesky",
         # rule with the level itself as the coarse mesh)
         c0.M = sp.csr_matrix(c0.A)
         c0.smask = np.ones(c0.mesh.n_dof, dtype=bool)
-        c0.patches = _patch_rule_R1(c0.mesh, c0.mesh, c0.mesh.dof_table(), "p", c0.smask)
+        c0.patches = rule(c0.mesh, c0.mesh, c0.mesh.dof_table(), "p", c0.smask)
         c0.patch_inv = [np.linalg.inv(c0.A[np.ix_(idx, idx)]) for idx in c0.patches]
         c0.theta = theta if theta is not None else estimate_theta(c0)
     levels.reverse()

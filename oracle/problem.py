@@ -18,6 +18,10 @@ provided:
   f, g and u0 are whatever makes (p_ex, u_ex) exact; with m <= p they lie
   in the discrete trial space, so DPG must reproduce them to rounding.
 
+``WithImpedanceLoad(base, u0)`` adds a caller's impedance data u0(X, n, c)
+on Gamma to the f, g and u0 of another load (the boundary condition of
+Eq. helmholtz with general data).
+
 Polynomials of ``Manufactured`` are tensor Legendre series in the box
 coordinate X = (x - x0) / (x1 - x0): coefficient array C[comp, c, b, a]
 (comp 0 = p, 1..3 = u_x, u_y, u_z; complex).
@@ -100,3 +104,19 @@ class Manufactured:
 
     def u0(self, X, n, c):
         return self.p(X) / c - self.u(X) @ n
+
+
+class WithImpedanceLoad:
+    """f and g of ``base``; u0 = base's u0 (if any) + extra(X, n, c)."""
+
+    def __init__(self, base, extra):
+        self.base = base
+        self.extra = extra
+        self.f = base.f
+        self.g = base.g
+
+    def u0(self, X, n, c):
+        v = np.asarray(self.extra(X, n, c), dtype=np.complex128)
+        if self.base.u0 is not None:
+            v = v + self.base.u0(X, n, c)
+        return v

@@ -14,7 +14,7 @@ from oracle.assembly import build_fine
 from oracle.element import (boundary_faces, condense, dpg_element, element_matrices,
                             present_columns)
 from oracle.mesh import Mesh
-from oracle.problem import GaussianSource, Manufactured, PlaneWave
+from oracle.problem import GaussianSource, Manufactured, PlaneWave, WithImpedanceLoad
 from oracle.traces import field_dofs, trace_dofs
 
 
@@ -36,6 +36,33 @@ def test_manufactured_solution_is_exact(p, n, omega):
     F = fs.fields(x)
     Fe = field_dofs(fs.mesh, ld.p, ld.u)
     assert np.linalg.norm(F - Fe) / np.linalg.norm(Fe) < 1e-10
+
+
+class _VolumeOnly:
+    """f and g of a load, without its impedance data."""
+
+    def __init__(self, ld):
+        self.f, self.g, self.u0 = ld.f, ld.g, None
+
+
+@pytest.mark.parametrize("p,n", [(2, (2, 3, 2)), (3, (2, 1, 2))])
+def test_impedance_data_given_separately(p, n):
+    # the manufactured solution with its u0 handed over as separate impedance
+    # data (WithImpedanceLoad) is still reproduced exactly; with that data
+    # left out it is not
+    x0, x1 = (0.0, -1.0, 0.5), (2.0, 1.0, 2.0)
+    omega = 4.0
+    ld = Manufactured(_rand_coeffs(p, 20 + p), omega, x0, x1)
+    c = np.random.default_rng(3 + p).uniform(0.3, 2.0, int(np.prod(n)))
+    xt = None
+    errs = []
+    for load in (WithImpedanceLoad(_VolumeOnly(ld), ld.u0), _VolumeOnly(ld)):
+        fs = build_fine(n, p, omega, wavespeed=c, load=load, x0=x0, x1=x1)
+        A, b = fs.assemble()
+        x = np.linalg.solve(A.toarray(), b)
+        xt = trace_dofs(fs.mesh, ld.p, ld.u)
+        errs.append(np.linalg.norm(x - xt) / np.linalg.norm(xt))
+    assert errs[0] < 1e-10 and errs[1] > 1e-3
 
 
 def test_manufactured_detects_wrong_order_data():

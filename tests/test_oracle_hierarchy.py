@@ -5,6 +5,9 @@
   fine skeleton; macro condensation + back-substitution solves the fine
   system exactly; the element-wise restriction equals P^* M P globally.
 * R1 patch statistics equal the independently counted workload figures.
+* R2 patches equal the DOFs of the entities whose closure holds the vertex,
+  enumerated from the mesh's entity indices; they coincide with R1 away from
+  the boundary and the V-cycle built on them is Hermitian positive.
 * P6: the V-cycle is Hermitian and positive definite.
 * P4: MG-PCG agrees with a brute-force dense solve.
 """
@@ -12,7 +15,8 @@ import numpy as np
 import pytest
 
 from oracle.assembly import build_fine
-from oracle.hierarchy import _patch_rule_R1, assemble, build_hierarchy, level_specs, smoother
+from oracle.hierarchy import _patch_rule_R1, _patch_rule_R2, assemble, build_hierarchy, level_specs, smoother
+from oracle.mesh import tangential
 from oracle.mesh import Mesh
 from oracle.problem import GaussianSource, Manufactured
 from oracle.solver import mg_pcg, vcycle
@@ -271,5 +275,97 @@ def test_smoothing_coarsest_mode(nl, pmin):
     assert abs(np.vdot(v, Bu) - np.vdot(Bv, u)) / (np.linalg.norm(u) * np.linalg.norm(Bv)) < 1e-12
     assert np.vdot(u, Bu).real > 0
     x, it, hist = mg_pcg(levels, A, b, tol=1e-12)
+    x_ref = np.linalg.solve(A.toarray(), b)
+    assert np.linalg.norm(x - x_ref) / np.linalg.norm(x_ref) < 1e-9
+
+
+def _closure_patch_by_entities(m, w):
+    """DOFs of the entities of a p-level mesh whose closure contains vertex w,
+    enumerated from the entity index functions (vertex, the edges ending at w,
+    the faces with w as a corner)."""
+    p, n = m.p, m.n
+    out = [m.vertex(w)]
+    for d in range(3):
+        for off in (0, 1):
+            c = list(w)
+            c[d] -= off
+            if 0 <= c[d] < n[d]:
+                e = m.edge(d, c)
+                out += [m.off_E + e * (p - 1) + k for k in range(p - 1)]
+        t1, t2 = tangential(d)
+        for a in (0, 1):
+            for b in (0, 1):
+                c = list(w)
+                c[t1] -= a
+                c[t2] -= b
+                if 0 <= c[t1] < n[t1] and 0 <= c[t2] < n[t2]:
+                    f = m.face(d, c)
+                    out += [m.off_F + f * (p - 1) ** 2 + k for k in range((p - 1) ** 2)]
+                    if not m.is_boundary_face(d, c):
+                        u = m.iface(d, c)
+                        out += [m.off_U + u * p * p + k for k in range(p * p)]
+    return sorted(out)
+
+
+@pytest.mark.parametrize("n,p", [((3, 2, 2), 2), ((2, 2, 3), 3)])
+def test_patch_rule_R2_is_the_vertex_closure(n, p):
+    m = Mesh(n, p)
+    tab = m.dof_table()
+    pt = _patch_rule_R2(m, m, tab, "p", np.ones(m.n_dof, dtype=bool))
+    j = 0
+    for k in range(n[2] + 1):
+        for jj in range(n[1] + 1):
+            for i in range(n[0] + 1):
+                assert list(pt[j]) == _closure_patch_by_entities(m, (i, jj, k))
+                j += 1
+    # corner: the vertex, 3 edges and 3 boundary faces (no flux DOFs)
+    assert len(pt[0]) == 1 + 3 * (p - 1) + 3 * (p - 1) ** 2
+
+
+@pytest.mark.parametrize("kind", ["p", "h"])
+def test_patch_rule_R2_against_R1(kind):
+    # R2 <= R1 everywhere; what R1 adds are DOFs on boundary entities, which it
+    # also gives to the vertices one layer inside (their one adjacent element
+    # has those vertices as corners); R2 still covers the smoothed DOFs
+    p = 2
+    if kind == "p":
+        m = Mesh((4, 4, 4), p)
+        cm, sm = m, np.ones(m.n_dof, dtype=bool)
+    else:
+        m = Mesh((8, 8, 8), p)
+        cm = Mesh((4, 4, 4), p)
+        sm = np.array([any(c % 4 == 0 for c in ctr) for (_, ctr, _) in m.dof_table()])
+    tab = m.dof_table()
+    r1 = _patch_rule_R1(m, cm, tab, kind, sm)
+    r2 = _patch_rule_R2(m, cm, tab, kind, sm)
+    covered = np.zeros(m.n_dof, dtype=bool)
+    j = 0
+    for k in range(5):
+        for jj in range(5):
+            for i in range(5):
+                a, b = set(r1[j].tolist()), set(r2[j].tolist())
+                assert b <= a
+                assert all(any(c in (0, 2 * m.n[d]) for d, c in enumerate(tab[g][1])) for g in a - b)
+                assert (a == b) == all(v not in (1, 3) for v in (i, jj, k))
+                covered[r2[j]] = True
+                j += 1
+    assert np.all(covered == sm)
+    if kind == "p":
+        # largest R2 patch is the interior one (67 at p2; R1 reaches 104 at the boundary)
+        assert max(len(x) for x in r2) == 67 and max(len(x) for x in r1) == 104
+
+
+def test_patch_rule_R2_vcycle_and_solution():
+    fs = build_fine((4, 4, 4), 2, 4.0, load=GaussianSource((0.35, 0.5, 0.6), 0.15))
+    A, b = fs.assemble()
+    lv2 = build_hierarchy(fs.mesh, fs.Kc, fs.dofs, n_levels=3, p_min=1, patch_rule="R2")
+    L = len(lv2) - 1
+    rng = np.random.default_rng(9)
+    u = rng.standard_normal(A.shape[0]) + 1j * rng.standard_normal(A.shape[0])
+    v = rng.standard_normal(A.shape[0]) + 1j * rng.standard_normal(A.shape[0])
+    Bu, Bv = vcycle(lv2, L, u), vcycle(lv2, L, v)
+    assert abs(np.vdot(v, Bu) - np.vdot(Bv, u)) / (np.linalg.norm(u) * np.linalg.norm(Bv)) < 1e-12
+    assert np.vdot(u, Bu).real > 0
+    x, it, hist = mg_pcg(lv2, A, b, tol=1e-12)
     x_ref = np.linalg.solve(A.toarray(), b)
     assert np.linalg.norm(x - x_ref) / np.linalg.norm(x_ref) < 1e-9
