@@ -100,6 +100,12 @@ typedef struct dpgmg_problem {
   const double* mf_coeffs; /* manufactured: host c128 [4][m][m][m] (comp, c, b, a):
                               comp 0 = p_ex, 1..3 = u_ex components; tensor Legendre
                               L_a(X) L_b(Y) L_c(Z) in box coordinates X = (x-x0)/(x1-x0) */
+  const double* u0_samples;/* optional impedance load of the caller, added to the source's own
+                              u0 (Sec. 2, impedance condition Z^-1 p - u.n = u0 on Gamma):
+                              host c128 [n_points] (re, im) of u0 at the boundary points that
+                              dpgmg_boundary_points lists, in that order; NULL = none.  The
+                              element stage integrates <u0, q> over each boundary face with
+                              the same Gauss rule, so u0 enters exactly as sampled. */
 } dpgmg_problem;
 
 typedef struct dpgmg_opts {
@@ -153,6 +159,17 @@ typedef struct dpgmg_opts {
    precision.  Setup is slower (the FP64 pipe of this GPU); the smoother then
    differs from the FP64 one by the rounding of its entries only. */
 #define DPGMG_FLAG_PATCH_FP64 32
+/* Vertex-patch membership rule R2 instead of R1 (Sec. 3, "V-cycle and
+   smoother": one block per vertex of the next coarser mesh; the paper does not
+   say how blocks end at the boundary).  R1, the default: a DOF is in the block
+   of vertex w when every (macro-)element adjacent to its entity has w as a
+   corner.  R2: when w lies in the closure of the coarse entity carrying the DOF
+   (its own entity on p levels, the coarse entity whose interior holds it on h
+   levels).  They differ on boundary entities only, which R1 also gives to the
+   vertices one layer inside: R2 blocks are smaller there (largest block 67
+   against 104 on a 4^3 p = 2 mesh).  Applies to every smoothed level,
+   including level 0 under DPGMG_COARSEST_SMOOTH. */
+#define DPGMG_FLAG_PATCH_R2 64
 /* Host-made failures for testing the error paths (the paper has no
    counterpart; no GPU fault is involved):
    FAULT_NOT_HPD: the host overwrites the first diagonal entry of the dense
@@ -221,6 +238,17 @@ int dpgmg_query_sizes(const dpgmg_problem* pb, const dpgmg_opts* op,
  * n_trace must equal the count dpgmg_query_sizes reports.  Errors: ARG. */
 int dpgmg_dof_map(const dpgmg_problem* pb, long long n_trace, int* out);
 
+/* Points at which to sample a caller's impedance load u0 (dpgmg_problem
+ * u0_samples), without touching the device.  On return *n_points = the count:
+ * 2 (n1 n2 + n0 n2 + n0 n1) boundary faces times q^2 points, q = p + 5 (the
+ * element stage's Gauss-Legendre load rule).  Order: sides (d, s) for d = 0,
+ * 1, 2 and s = 0 (x_d = x0_d), 1 (x_d = x1_d); within a side the faces (j1, j2)
+ * along the tangential axes t1 < t2, j1 fastest; within a face the points
+ * (a, b) at (x_t1, x_t2) = corner + (xi_a h_t1, xi_b h_t2), a fastest.
+ * xyz: host double [n][3] of capacity *n_points on entry, or NULL to query
+ * the count only.  Errors: ARG (invalid problem, capacity too small). */
+int dpgmg_boundary_points(const dpgmg_problem* pb, long long* n_points, double* xyz);
+
 /* Default options: tol 1e-8, max_iter 2000, V(1,1), 2 levels, p_min 2, FP64,
  * Cholesky coarsest, theta estimated. */
 void dpgmg_default_opts(dpgmg_opts* op);
@@ -241,6 +269,20 @@ int dpgmg_setup(dpgmg_handle h, const dpgmg_problem* pb, const dpgmg_opts* op,
  * Errors: NOT_CONVERGED (outputs written), BREAKDOWN, TIMEOUT, CUDA. */
 int dpgmg_solve(dpgmg_handle h, dpgmg_system sys, void* trace_out, void* field_out,
                 int out_is_device, dpgmg_stats* st);
+
+/* Several loads on one system at once (Sec. 5: loads solved together share the
+ * cost of the smoothing patches): k independent MG-PCG solves from x0 = 0, one
+ * per right-hand side, each with its own scalars and stopping test (the
+ * recurrence of dpgmg_solve), sharing every V-cycle.  The V-cycle's smoother
+ * and SpMV read their stored matrices once for up to 4 right-hand sides.
+ * rhs: c128 [k][n_trace] condensed right-hand sides (e.g. dpgmg_rhs of
+ * systems with other sources); trace_out: c128 [k][n_trace]; both device
+ * pointers when on_device != 0, else host.  stats: k entries or NULL; each
+ * gets its own iterations and residuals, t_pcg_ms is the time of the whole
+ * block.  1 <= k <= 64.  Returns the first non-OK status of the columns
+ * (NOT_CONVERGED, BREAKDOWN), with every column's outputs written. */
+int dpgmg_solve_block(dpgmg_handle h, dpgmg_system sys, int k, const void* rhs, void* trace_out,
+                      int on_device, dpgmg_stats* stats);
 
 void dpgmg_release(dpgmg_handle h, dpgmg_system sys);
 const char* dpgmg_strerror(int code);

@@ -85,7 +85,7 @@ int validate_problem(const dpgmg_problem* pb, const dpgmg_opts* op) {
       (op->coarsest != DPGMG_COARSEST_CHOLESKY && op->coarsest != DPGMG_COARSEST_NONE &&
        op->coarsest != DPGMG_COARSEST_AUTO && op->coarsest != DPGMG_COARSEST_SMOOTH) ||
       (op->flags & ~(DPGMG_FLAG_EAGER | DPGMG_FLAG_CUDA_CORES | DPGMG_FLAG_STORE_COARSE | DPGMG_FLAG_WARM_START |
-                     DPGMG_FLAG_CG_C128 | DPGMG_FLAG_PATCH_FP64 | DPGMG_FLAG_FAULT_NOT_HPD |
+                     DPGMG_FLAG_CG_C128 | DPGMG_FLAG_PATCH_FP64 | DPGMG_FLAG_PATCH_R2 | DPGMG_FLAG_FAULT_NOT_HPD |
                      DPGMG_FLAG_FAULT_TC_WAIT)))
     return DPGMG_ERR_ARG;
   if ((op->flags & DPGMG_FLAG_STORE_COARSE) && pb->wavespeed) {
@@ -144,7 +144,7 @@ size_t estimate_bytes(const dpgmg_problem* pb, const dpgmg_opts* op) {
       if (i == 0) resident += nnz * (mixed ? 8.0 : 16.0);             // double-float split of the CG operator
       int nco[3];
       for (int d = 0; d < 3; ++d) nco[d] = hlev ? s.n[d] / 2 : s.n[d];
-      auto ps = patch_sizes(m, hlev, hlev ? 4 : 2, nco);
+      auto ps = patch_sizes(m, hlev, hlev ? 4 : 2, nco, (op->flags & DPGMG_FLAG_PATCH_R2) != 0);
       double nvals = 0.0, nslots = 0.0, nmax = 0.0;
       for (int64_t v : ps) {
         nvals += (double)v * (double)patch_ld(v);
@@ -211,8 +211,10 @@ void setup_system(SystemImpl& S, const dpgmg_problem* pb, const dpgmg_opts* op, 
     size_t m = pb->mf_order;
     S.mf_coeffs.assign(pb->mf_coeffs, pb->mf_coeffs + 2 * 4 * m * m * m);
   }
+  if (pb->u0_samples) S.u0.assign(pb->u0_samples, pb->u0_samples + 2 * boundary_point_count(pb));
   S.pb.wavespeed = nullptr;
   S.pb.mf_coeffs = nullptr;
+  S.pb.u0_samples = nullptr;
   S.mem.budget = budget;
   S.mem.stream = st;
   auto specs = plan_levels(pb->n, pb->p, op->n_levels, op->p_min);
@@ -270,6 +272,12 @@ void setup_system(SystemImpl& S, const dpgmg_problem* pb, const dpgmg_opts* op, 
   S.t_phase[4] = span(3, 4);
   S.t_phase[5] = span(4, 7);
   fill_bytes_per_iter(S);
+}
+
+int64_t boundary_point_count(const dpgmg_problem* pb) {
+  int64_t off[6];
+  const int64_t nq = make_tables(pb->p).nql;
+  return boundary_face_offsets(pb->n, off) * nq * nq;
 }
 
 }  // namespace dpgmg
@@ -407,6 +415,25 @@ int dpgmg_dof_map(const dpgmg_problem* pb, long long n_trace, int* out) {
   return DPGMG_OK;
 }
 
+int dpgmg_boundary_points(const dpgmg_problem* pb, long long* n_points, double* xyz) {
+  if (!pb || !n_points) return DPGMG_ERR_ARG;
+  for (int d = 0; d < 3; ++d)
+    if (pb->n[d] < 1 || !(pb->x1[d] > pb->x0[d])) return DPGMG_ERR_ARG;
+  if (pb->p < 1 || pb->p > 5) return DPGMG_ERR_ARG;
+  const int64_t cnt = boundary_point_count(pb);
+  if (xyz) {
+    if (*n_points < cnt) {
+      set_last_error("dpgmg_boundary_points: capacity below the point count");
+      return DPGMG_ERR_ARG;
+    }
+    std::vector<double> pts;
+    boundary_points(pb->n, pb->x0, pb->x1, pb->p, pts);
+    std::copy(pts.begin(), pts.end(), xyz);
+  }
+  *n_points = cnt;
+  return DPGMG_OK;
+}
+
 int dpgmg_query_sizes(const dpgmg_problem* pb, const dpgmg_opts* op, long long* n_trace, long long* n_field,
                       size_t* dev_bytes) {
   int v = validate_problem(pb, op);
@@ -506,6 +533,36 @@ int dpgmg_solve(dpgmg_handle h, dpgmg_system sys, void* trace_out, void* field_o
     }
     if (trace_out && !out_is_device)
       DPG_CUDA(cudaMemcpyAsync(trace_out, x, (size_t)n * sizeof(double2), cudaMemcpyDeviceToHost, s));
+    DPG_CUDA(cudaStreamSynchronize(s));
+    if (status != DPGMG_OK) set_last_error(dpgmg_strerror(status));
+    return status;
+  } catch (const Err& e) {
+    return fail(e);
+  }
+}
+
+int dpgmg_solve_block(dpgmg_handle h, dpgmg_system sys, int k, const void* rhs, void* trace_out, int on_device,
+                      dpgmg_stats* st) {
+  if (!h || !sys || !rhs || !trace_out || k < 1 || k > 64) return DPGMG_ERR_ARG;
+  std::lock_guard<std::mutex> lk(h->mu);
+  SystemImpl& S = sys->s;
+  try {
+    DPG_CUDA(cudaSetDevice(h->h.device));
+    cudaStream_t s = h->h.stream;
+    const size_t bytes = (size_t)S.levels.back().mesh.ndof * k * sizeof(double2);
+    Alloc tmp;
+    tmp.budget = (size_t)-1;
+    tmp.stream = s;
+    const double2* b = reinterpret_cast<const double2*>(rhs);
+    double2* x = reinterpret_cast<double2*>(trace_out);
+    if (!on_device) {
+      double2* bd = tmp.arr<double2>(bytes / sizeof(double2));
+      DPG_CUDA(cudaMemcpyAsync(bd, rhs, bytes, cudaMemcpyHostToDevice, s));
+      b = bd;
+      x = tmp.arr<double2>(bytes / sizeof(double2));
+    }
+    int status = pcg_solve_block(S, s, k, b, x, st);
+    if (!on_device) DPG_CUDA(cudaMemcpyAsync(trace_out, x, bytes, cudaMemcpyDeviceToHost, s));
     DPG_CUDA(cudaStreamSynchronize(s));
     if (status != DPGMG_OK) set_last_error(dpgmg_strerror(status));
     return status;

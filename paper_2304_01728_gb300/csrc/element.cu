@@ -41,6 +41,8 @@ struct ElemArgs {
   const int4 *tf, *ff, *tr;
   Tab1D tab;
   const double *xq, *wq, *Lq;  // load rule and L_a at its points ([n1][nql])
+  const double2* u0s;      // caller's impedance load samples at the boundary points, or null
+  int64_t u0off[6];        // first boundary face of side (d, s) in the sample list
   const int64_t* elist;    // element ids of the batch list
   int64_t e0;
   double* G;
@@ -235,8 +237,8 @@ __global__ void __launch_bounds__(CTA_THREADS) k_elem_build(ElemArgs a) {
   const int n1 = a.tab.n1;
   double2* fv = sh2;                 // [nq3]
   build_load<T>(a, corner, c, sh2, W + m, ldw);
-  // boundary faces: <u0, q>
-  if (a.src != DPGMG_SRC_GAUSSIAN) {
+  // boundary faces: <u0, q>, u0 from the source and/or the caller's samples
+  if (a.src != DPGMG_SRC_GAUSSIAN || a.u0s) {
     for (int d = 0; d < 3; ++d)
       for (int s = 0; s < 2; ++s) {
         if (!((bmask >> (2 * d + s)) & 1)) continue;
@@ -250,6 +252,13 @@ __global__ void __launch_bounds__(CTA_THREADS) k_elem_build(ElemArgs a) {
           double nrm[3] = {0, 0, 0};
           nrm[d] = s ? 1.0 : -1.0;
           double2 u = src_u0(a, c, x, nrm);
+          if (a.u0s) {
+            // samples of face (ec[t1], ec[t2]) of side (d, s), points qa along t1 fastest
+            const int64_t f = a.u0off[2 * d + s] + ec[t1] + (int64_t)a.n[t1] * ec[t2];
+            const double2 v = a.u0s[(f * nq + qb) * nq + qa];
+            u.x += v.x;
+            u.y += v.y;
+          }
           double w = a.wq[qa] * a.wq[qb] * a.h[t1] * a.h[t2];
           fv[q] = make_double2(u.x * w, u.y * w);
         }
@@ -627,6 +636,14 @@ static void element_core(SystemImpl& S, Level& L, const std::vector<double>& cva
   a.xq = upload(A, T.xq, st);
   a.wq = upload(A, T.wq, st);
   a.Lq = upload(A, T.Lq, st);
+  if (finest && !S.u0.empty()) {
+    // caller's impedance load samples (finest mesh only: the stored coarse
+    // operators of coarser meshes keep only their matrices)
+    std::vector<double2> u0(S.u0.size() / 2);
+    for (size_t i = 0; i < u0.size(); ++i) u0[i] = make_double2(S.u0[2 * i], S.u0[2 * i + 1]);
+    a.u0s = upload(A, u0, st);
+    boundary_face_offsets(m.n, a.u0off);
+  }
   a.info = A.arr<int>(1);
   DPG_CUDA(cudaMemsetAsync(a.info, 0, sizeof(int), st));
 
@@ -683,7 +700,7 @@ static void element_core(SystemImpl& S, Level& L, const std::vector<double>& cva
   std::vector<int64_t> lreal, lsplit, lcplx;
   const bool real_src = S.pb.source != DPGMG_SRC_MANUFACTURED;
   const int64_t ld1 = a.m + 1, ld2 = ld1 + a.nph;
-  const bool split_ok = S.pb.source == DPGMG_SRC_GAUSSIAN && ld2 * ld2 <= 2 * ld1 * ld1;
+  const bool split_ok = S.pb.source == DPGMG_SRC_GAUSSIAN && a.u0s == nullptr && ld2 * ld2 <= 2 * ld1 * ld1;
   for (int64_t e = 0; e < nel; ++e) {
     int ec[3];
     m.elem_coord(e, ec);

@@ -457,26 +457,76 @@ ECSRHost build_ecsr(const MeshL& m, const std::vector<std::vector<int64_t>>& gro
   return A;
 }
 
+// ------------------------------------------------------- boundary points
+int64_t boundary_face_offsets(const int n[3], int64_t off[6]) {
+  int64_t k = 0;
+  for (int d = 0; d < 3; ++d) {
+    const int t1 = d == 0 ? 1 : 0, t2 = d == 2 ? 1 : 2;
+    for (int s = 0; s < 2; ++s) {
+      off[2 * d + s] = k;
+      k += (int64_t)n[t1] * n[t2];
+    }
+  }
+  return k;
+}
+
+void boundary_points(const int n[3], const double x0[3], const double x1[3], int p, std::vector<double>& xyz) {
+  Tables1D T = make_tables(p);
+  const int nq = T.nql;
+  int64_t off[6];
+  const int64_t nf = boundary_face_offsets(n, off);
+  double h[3];
+  for (int d = 0; d < 3; ++d) h[d] = (x1[d] - x0[d]) / n[d];
+  xyz.assign((size_t)nf * nq * nq * 3, 0.0);
+  for (int d = 0; d < 3; ++d) {
+    const int t1 = d == 0 ? 1 : 0, t2 = d == 2 ? 1 : 2;
+    for (int s = 0; s < 2; ++s)
+      for (int j2 = 0; j2 < n[t2]; ++j2)
+        for (int j1 = 0; j1 < n[t1]; ++j1) {
+          const int64_t f = off[2 * d + s] + j1 + (int64_t)n[t1] * j2;
+          // the element stage's own expressions: element corner + s h, corner + x_q h
+          const double cd = x0[d] + (s ? n[d] - 1 : 0) * h[d];
+          const double c1 = x0[t1] + j1 * h[t1], c2 = x0[t2] + j2 * h[t2];
+          for (int qb = 0; qb < nq; ++qb)
+            for (int qa = 0; qa < nq; ++qa) {
+              double* o = &xyz[(size_t)((f * nq + qb) * nq + qa) * 3];
+              o[d] = cd + s * h[d];
+              o[t1] = c1 + T.xq[qa] * h[t1];
+              o[t2] = c2 + T.xq[qb] * h[t2];
+            }
+        }
+  }
+}
+
 // ---------------------------------------------------------------- patches
-Patches build_patches(const MeshL& m, const std::vector<char>& smask, int H, const int nco[3]) {
+// Coarse vertex indices along one axis whose patches take an entity with
+// centre coordinate ctr (half-element units of the level's mesh, coarse
+// element width H).  Off a coarse plane: the two planes around it.  On an
+// interior coarse plane: that plane.  On a boundary plane, rule R1 (every
+// adjacent (macro-)element has the vertex as a corner) also takes the plane
+// one element inside; rule R2 (the vertex lies in the closure of the entity's
+// coarse entity) takes the boundary plane only.
+int patch_axis_span(int ctr, int H, int nco, bool r2, int W[2]) {
+  const int top = H * nco;
+  if (ctr % H != 0) {
+    W[0] = ctr / H;
+    W[1] = ctr / H + 1;
+    return 2;
+  }
+  if (!r2 && ctr == 0) { W[0] = 0; W[1] = 1; return 2; }
+  if (!r2 && ctr == top) { W[0] = nco - 1; W[1] = nco; return 2; }
+  W[0] = ctr / H;
+  return 1;
+}
+
+Patches build_patches(const MeshL& m, const std::vector<char>& smask, int H, const int nco[3], bool r2) {
   Patches P;
   int64_t npatch = (int64_t)(nco[0] + 1) * (nco[1] + 1) * (nco[2] + 1);
   std::vector<int64_t> count(npatch + 1, 0);
   auto sets = [&](int64_t g, int W[3][2], int cnt[3]) {
     int ctr[3];
     m.ent_center(m.dof_entity(g), ctr);
-    for (int d = 0; d < 3; ++d) {
-      int top = H * nco[d];
-      if (ctr[d] % H == 0) {
-        if (ctr[d] == 0) { W[d][0] = 0; W[d][1] = 1; cnt[d] = 2; }
-        else if (ctr[d] == top) { W[d][0] = nco[d] - 1; W[d][1] = nco[d]; cnt[d] = 2; }
-        else { W[d][0] = ctr[d] / H; cnt[d] = 1; }
-      } else {
-        W[d][0] = ctr[d] / H;
-        W[d][1] = ctr[d] / H + 1;
-        cnt[d] = 2;
-      }
-    }
+    for (int d = 0; d < 3; ++d) cnt[d] = patch_axis_span(ctr[d], H, nco[d], r2, W[d]);
   };
   for (int pass = 0; pass < 2; ++pass) {
     std::vector<int64_t> fill;
@@ -515,7 +565,7 @@ Patches build_patches(const MeshL& m, const std::vector<char>& smask, int H, con
   return P;
 }
 
-std::vector<int64_t> patch_sizes(const MeshL& m, bool macro, int H, const int nco[3]) {
+std::vector<int64_t> patch_sizes(const MeshL& m, bool macro, int H, const int nco[3], bool r2) {
   std::vector<int64_t> cnt((size_t)(nco[0] + 1) * (nco[1] + 1) * (nco[2] + 1), 0);
   for (int64_t E = 0; E < m.nent; ++E) {
     int64_t st;
@@ -531,18 +581,7 @@ std::vector<int64_t> patch_sizes(const MeshL& m, bool macro, int H, const int nc
       if (!on) continue;
     }
     int W[3][2], c[3];
-    for (int d = 0; d < 3; ++d) {
-      int top = H * nco[d];
-      if (ctr[d] % H == 0) {
-        if (ctr[d] == 0) { W[d][0] = 0; W[d][1] = 1; c[d] = 2; }
-        else if (ctr[d] == top) { W[d][0] = nco[d] - 1; W[d][1] = nco[d]; c[d] = 2; }
-        else { W[d][0] = ctr[d] / H; c[d] = 1; }
-      } else {
-        W[d][0] = ctr[d] / H;
-        W[d][1] = ctr[d] / H + 1;
-        c[d] = 2;
-      }
-    }
+    for (int d = 0; d < 3; ++d) c[d] = patch_axis_span(ctr[d], H, nco[d], r2, W[d]);
     for (int a = 0; a < c[0]; ++a)
       for (int b = 0; b < c[1]; ++b)
         for (int q = 0; q < c[2]; ++q)

@@ -82,10 +82,13 @@ struct ECSRHost {
 // groups: for each super-element, the list of entity ids it touches.
 ECSRHost build_ecsr(const MeshL& m, const std::vector<std::vector<int64_t>>& groups);
 
-// Vertex patches of a level's smoothing space (rule R1): a DOF is in the
-// patch of coarse vertex w when every (macro-)element adjacent to its entity
-// has w as a corner.  H = coarse element width in doubled fine units (2 on p
-// levels, 4 on h levels); nco = coarse mesh extents.
+// Vertex patches of a level's smoothing space.  Rule R1 (r2 = false): a DOF
+// is in the patch of coarse vertex w when every (macro-)element adjacent to
+// its entity has w as a corner.  Rule R2 (r2 = true): when w lies in the
+// closure of the coarse entity carrying the DOF (its own entity on p levels,
+// the macro entity on h levels); the two differ only on boundary entities.
+// H = coarse element width in doubled fine units (2 on p levels, 4 on h
+// levels); nco = coarse mesh extents.
 struct Patches {
   std::vector<int64_t> ptr;    // per patch (+1)
   std::vector<int32_t> dofs;   // patch-major DOF lists (sorted within a patch)
@@ -93,7 +96,8 @@ struct Patches {
   std::vector<int64_t> slot_ptr; // per DOF (+1): CSR of the DOF's slots in dofs[]
   std::vector<int32_t> slots;
 };
-Patches build_patches(const MeshL& m, const std::vector<char>& smask, int H, const int nco[3]);
+Patches build_patches(const MeshL& m, const std::vector<char>& smask, int H, const int nco[3], bool r2);
+int patch_axis_span(int ctr, int H, int nco, bool r2, int W[2]);
 // Row length of a stored n x n patch block: n rounded up to even, so that
 // every row of a complex64 block starts on a 16-byte boundary.
 #if defined(__CUDACC__)
@@ -102,7 +106,7 @@ __host__ __device__
 inline int64_t patch_ld(int64_t n) { return n + (n & 1); }
 // Patch sizes only (same rule), for memory estimates: n_j per coarse vertex.
 // macro = true selects the h-level smoothing space (fine DOFs on the coarse skeleton).
-std::vector<int64_t> patch_sizes(const MeshL& m, bool macro, int H, const int nco[3]);
+std::vector<int64_t> patch_sizes(const MeshL& m, bool macro, int H, const int nco[3], bool r2);
 
 // Macro-grid structure of one h-transition (fine level m, coarse level mc).
 struct MacroHost {
@@ -141,5 +145,14 @@ struct Tables1D {
 };
 Tables1D make_tables(int p);
 void gauss_legendre01(int n, std::vector<double>& x, std::vector<double>& w);
+
+// Boundary faces of the box mesh in the order of the impedance-load sample
+// list: sides (d, s) for d = 0, 1, 2 and s = 0 (x_d = x0_d), s = 1 (x_d =
+// x1_d); within a side the faces (j1, j2) along the tangential axes t1 < t2,
+// j1 fastest.  off[2d + s] = first face of side (d, s); returns the count.
+int64_t boundary_face_offsets(const int n[3], int64_t off[6]);
+// Physical points of the boundary load rule (nql x nql Gauss points per
+// boundary face, the t1 index fastest) in the order above: xyz[3 * count].
+void boundary_points(const int n[3], const double x0[3], const double x1[3], int p, std::vector<double>& xyz);
 
 }  // namespace dpgmg

@@ -179,6 +179,7 @@ struct SystemImpl {
   dpgmg_opts op;
   std::vector<double> wavespeed;
   std::vector<double> mf_coeffs;
+  std::vector<double> u0;             // caller's impedance load samples (re, im), or empty
   std::vector<Level> levels;     // 0 = coarsest
   Alloc mem;
   int64_t nf = 0, ntr = 0, nelem = 0;
@@ -256,6 +257,7 @@ void coarse_apply32(const Level& C0, const float2* r, float2* e, float2* tmp, cu
 // solve.cu
 // x0 (device, may be null): initial guess of the CG iteration (0 if null)
 int pcg_solve(SystemImpl& S, cudaStream_t st, double2* x, dpgmg_stats* stats, const double2* x0 = nullptr);
+int pcg_solve_block(SystemImpl& S, cudaStream_t st, int K, const double2* B, double2* X, dpgmg_stats* stats);
 void apply_op(SystemImpl& S, int op, int level, const double2* x, double2* y, cudaStream_t st);
 void ensure_workspace(SystemImpl& S, cudaStream_t st);
 // CG operator split and kernel-variant tuning, run once at the end of setup
@@ -277,6 +279,7 @@ void profile_read(SystemImpl& S, double* ms, long long* launches, long long* byt
 // api.cu: validation, footprint estimate and the whole setup of one system
 int validate_problem(const dpgmg_problem* pb, const dpgmg_opts* op);
 size_t estimate_bytes(const dpgmg_problem* pb, const dpgmg_opts* op);
+int64_t boundary_point_count(const dpgmg_problem* pb);   // points of the boundary load rule
 void setup_system(SystemImpl& S, const dpgmg_problem* pb, const dpgmg_opts* op, size_t budget, cudaStream_t st);
 void profile_clear(SystemImpl& S);
 void smooth_apply64(const Level& L, const double2* r, double2* y, double theta, double2* scratch,

@@ -636,7 +636,7 @@ std::shared_ptr<HostPlan> plan_host(const SystemImpl& S) {
       lp.smask.assign(lp.M.smask.begin(), lp.M.smask.end());
       lp.H = 4;
     }
-    lp.P = build_patches(F.mesh, lp.smask, lp.H, C.mesh.n);
+    lp.P = build_patches(F.mesh, lp.smask, lp.H, C.mesh.n, (S.op.flags & DPGMG_FLAG_PATCH_R2) != 0);
     const Patches& P = lp.P;
     const int64_t np = (int64_t)P.ptr.size() - 1;
     auto size_of = [&](int64_t j) { return P.ptr[j + 1] - P.ptr[j]; };

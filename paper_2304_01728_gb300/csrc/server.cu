@@ -27,7 +27,7 @@ struct Request {
   long long id = 0;
   dpgmg_problem pb{};
   dpgmg_opts op{};
-  std::vector<double> ws, mf;
+  std::vector<double> ws, mf, u0;
   size_t est = 0;
   double t_submit = 0, t_start = 0, t_done = 0;
   int state = 0;  // 0 queued, 1 running, 2 done
@@ -60,6 +60,7 @@ static void run_request(Request& rq, cudaStream_t st, size_t budget) {
     dpgmg_problem pb = rq.pb;
     pb.wavespeed = rq.ws.empty() ? nullptr : rq.ws.data();
     pb.mf_coeffs = rq.mf.empty() ? nullptr : rq.mf.data();
+    pb.u0_samples = rq.u0.empty() ? nullptr : rq.u0.data();
     setup_system(S, &pb, &rq.op, budget, st);
     const int64_t n = S.levels.back().mesh.ndof;
     const int64_t nf = S.nelem * S.nf;
@@ -198,8 +199,10 @@ int dpgmg_submit(dpgmg_handle h, const dpgmg_problem* pb, const dpgmg_opts* op, 
     size_t m = pb->mf_order;
     rq->mf.assign(pb->mf_coeffs, pb->mf_coeffs + 2 * 4 * m * m * m);
   }
+  if (pb->u0_samples) rq->u0.assign(pb->u0_samples, pb->u0_samples + 2 * boundary_point_count(pb));
   rq->pb.wavespeed = nullptr;
   rq->pb.mf_coeffs = nullptr;
+  rq->pb.u0_samples = nullptr;
   rq->est = estimate_bytes(pb, op);
   if (rq->est > h->h.budget) {
     set_last_error("request footprint exceeds the handle's memory budget");

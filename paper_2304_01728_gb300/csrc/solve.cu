@@ -14,12 +14,14 @@
 #include <map>
 #include <mutex>
 #include <tuple>
+#include <type_traits>
 #include <cmath>
 #include <cstring>
 #include <vector>
 
 #include "common.cuh"
 #include "internal.h"
+#include "block.cuh"
 #include "smoother.cuh"
 
 namespace dpgmg {
@@ -522,6 +524,74 @@ static void spmv_df_g(const ECSRDev& A, const float2* xh, const float2* xl, cons
   if (A.n_null) {
     k_null_rows<double2><<<(unsigned)((A.n_null + 255) / 256), 256, 0, st>>>(A.null_rows, A.n_null, b, y, mode);
     DPG_CHECK_LAUNCH();
+  }
+}
+
+// Block form of the double-float CG operator: KB vectors (split into FP32
+// pairs xh/xl at stride ld), one warp per row, each stored pair (ah, al) loaded
+// once for the KB vectors.  Per vector the lane sums run over k = lane,
+// lane + 32, ... in order with the error-free products and sums of k_spmv_df,
+// so every column equals k_spmv_df's result.
+template <int KB>
+__global__ void __launch_bounds__(256) k_spmv_df_blk(const int32_t* __restrict__ row_ent,
+                                                     const int64_t* __restrict__ ent_start,
+                                                     const int64_t* __restrict__ col_ptr,
+                                                     const int32_t* __restrict__ col_idx,
+                                                     const int64_t* __restrict__ val_ptr, const float2* __restrict__ vh,
+                                                     const float2* __restrict__ vl, const float2* __restrict__ xh,
+                                                     const float2* __restrict__ xl, const double2* __restrict__ b,
+                                                     double2* __restrict__ y, int64_t ld, int64_t nrows, int mode) {
+  const int lane = threadIdx.x & 31;
+  const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t row = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); row < nrows; row += nw) {
+    const int32_t E = row_ent[row];
+    float rh[KB], rl[KB], ih[KB], il[KB];
+#pragma unroll
+    for (int kb = 0; kb < KB; ++kb) rh[kb] = rl[kb] = ih[kb] = il[kb] = 0.f;
+    if (E >= 0) {
+      const int64_t c0 = col_ptr[E];
+      const int nnz = (int)(col_ptr[E + 1] - c0);
+      const int64_t off = val_ptr[E] + (row - ent_start[E]) * nnz;
+      const int32_t* cols = col_idx + c0;
+      int cA = lane < nnz ? __ldg(cols + lane) : 0;
+      for (int k = lane; k < nnz; k += 32) {
+        const float2 ah = __ldcs(vh + off + k), al = __ldcs(vl + off + k);
+        float2 uh[KB], ul[KB];
+#pragma unroll
+        for (int kb = 0; kb < KB; ++kb) {
+          uh[kb] = xh[kb * ld + cA];
+          ul[kb] = xl[kb * ld + cA];
+        }
+        const int kn = k + 32;
+        cA = kn < nnz ? __ldg(cols + kn) : 0;
+#pragma unroll
+        for (int kb = 0; kb < KB; ++kb) {
+          float p, q;
+          df_mul(ah.x, al.x, uh[kb].x, ul[kb].x, p, q);
+          df_add(rh[kb], rl[kb], p, q);
+          df_mul(ah.y, al.y, uh[kb].y, ul[kb].y, p, q);
+          df_add(rh[kb], rl[kb], -p, -q);
+          df_mul(ah.x, al.x, uh[kb].y, ul[kb].y, p, q);
+          df_add(ih[kb], il[kb], p, q);
+          df_mul(ah.y, al.y, uh[kb].x, ul[kb].x, p, q);
+          df_add(ih[kb], il[kb], p, q);
+        }
+      }
+#pragma unroll
+      for (int kb = 0; kb < KB; ++kb) {
+        df_warp_sum(rh[kb], rl[kb]);
+        df_warp_sum(ih[kb], il[kb]);
+      }
+    }
+    if (lane < KB) {
+      float4 mine = make_float4(rh[0], rl[0], ih[0], il[0]);
+#pragma unroll
+      for (int kb = 1; kb < KB; ++kb)
+        if (lane == kb) mine = make_float4(rh[kb], rl[kb], ih[kb], il[kb]);
+      const int64_t i = lane * ld + row;
+      const double re = (double)mine.x + (double)mine.y, im = (double)mine.z + (double)mine.w;
+      y[i] = mode ? make_double2(b[i].x - re, b[i].y - im) : make_double2(re, im);
+    }
   }
 }
 
@@ -1124,6 +1194,161 @@ static void precondition(SystemImpl& S, WS& W, const double2* r, double2* z, cud
   }
 }
 
+// ------------------------------------------------------ block V-cycle
+// K right-hand sides stored one after another (stride = the level's DOF
+// count).  The smoother and the SpMV stream their matrices once per group of
+// up to BLK_MAX vectors; the transfers, condensation, back-substitution and
+// the coarsest solve run per vector (their matrices are small or cached).
+template <class C> struct BlockLevel {
+  C *r = nullptr, *rs = nullptr, *x = nullptr, *t = nullptr, *pbuf = nullptr, *cbuf = nullptr;
+};
+
+template <class C, int KB>
+static void patch_apply_blk_launch(const PatchDev& P, int per, const C* inv, const C* r, int64_t ldr, C* pbuf,
+                                   int64_t ldp, cudaStream_t st) {
+  const size_t sm = (size_t)KB * P.max_n * sizeof(C) + 16;
+  int64_t nch = 0;
+  const int2* chunks = patch_chunks(P, per, &nch);
+  if (per == 2)
+    k_patch_apply_blk<C, C, 2, KB><<<(unsigned)nch, 256, sm, st>>>(P.ptr, P.dofs, P.val_ptr, chunks, inv, r, ldr,
+                                                                   pbuf, ldp);
+  else
+    k_patch_apply_blk<C, C, 1, KB><<<(unsigned)nch, 256, sm, st>>>(P.ptr, P.dofs, P.val_ptr, chunks, inv, r, ldr,
+                                                                   pbuf, ldp);
+  DPG_CHECK_LAUNCH();
+}
+
+// dynamic shared memory of the block products: the gathered right-hand sides
+// of one group (vectors x patch size), up to BLK_SMEM bytes
+constexpr int BLK_SMEM = 200 * 1024;
+static void configure_block_kernels() {
+  static std::once_flag once;
+  std::call_once(once, []() {
+    const int mx = BLK_SMEM;
+#define DPG_BLK_ATTR(C, PER, KB)                                                                        \
+  DPG_CUDA(cudaFuncSetAttribute(k_patch_apply_blk<C, C, PER, KB>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx))
+    DPG_BLK_ATTR(float2, 1, 1); DPG_BLK_ATTR(float2, 1, 2); DPG_BLK_ATTR(float2, 1, 3); DPG_BLK_ATTR(float2, 1, 4);
+    DPG_BLK_ATTR(float2, 2, 1); DPG_BLK_ATTR(float2, 2, 2); DPG_BLK_ATTR(float2, 2, 3); DPG_BLK_ATTR(float2, 2, 4);
+    DPG_BLK_ATTR(double2, 1, 1); DPG_BLK_ATTR(double2, 1, 2); DPG_BLK_ATTR(double2, 1, 3);
+    DPG_BLK_ATTR(double2, 1, 4);
+#undef DPG_BLK_ATTR
+  });
+}
+
+// y_k = (accumulate ? y_k : 0) + theta S r_k for k < K
+template <class C>
+static void smooth_blk(const Level& L, const C* r, C* y, double theta, int accumulate, C* pbuf, int K,
+                       cudaStream_t st) {
+  const PatchDev& P = L.P;
+  const int64_t n = L.mesh.ndof, ldp = std::max<int64_t>(P.scratch_entries(), 1);
+  const C* inv = Prec<C>::inv(P);
+  const int64_t cap = std::min<int64_t>(BLK_MAX, (BLK_SMEM - 16) / ((int64_t)P.max_n * sizeof(C) + 1));
+  if (!inv || cap < 1) {
+    for (int k = 0; k < K; ++k) smooth<C>(L, r + k * n, y + k * n, theta, accumulate, pbuf + k * ldp, st);
+    return;
+  }
+  configure_block_kernels();
+  const int per = std::is_same<C, float2>::value ? P.cols : 1;
+  for (int g = 0; g < K; g += (int)cap) {
+    const int kb = (int)std::min<int64_t>(cap, K - g);
+    const C* rg = r + g * n;
+    C* pg = pbuf + g * ldp;
+    if (kb == 4) patch_apply_blk_launch<C, 4>(P, per, inv, rg, n, pg, ldp, st);
+    else if (kb == 3) patch_apply_blk_launch<C, 3>(P, per, inv, rg, n, pg, ldp, st);
+    else if (kb == 2) patch_apply_blk_launch<C, 2>(P, per, inv, rg, n, pg, ldp, st);
+    else patch_apply_blk_launch<C, 1>(P, per, inv, rg, n, pg, ldp, st);
+  }
+  for (int k = 0; k < K; ++k) {
+    k_slot_sum<C, C><<<nblk(n), 256, 0, st>>>(P.slot_ptr, P.slots, pbuf + k * ldp, y + k * n, n, theta, accumulate);
+    DPG_CHECK_LAUNCH();
+  }
+}
+
+template <class C>
+static void spmv_blk(const ECSRDev& A, const C* vals, const C* x, const C* b, C* y, int mode, int K, cudaStream_t st) {
+  const int64_t n = A.nrows;
+  const unsigned blocks = (unsigned)std::min<int64_t>((A.nrows + 7) / 8, 152 * 16);
+  for (int g = 0; g < K; g += BLK_MAX) {
+    const int kb = std::min(BLK_MAX, K - g);
+    const C* xg = x + g * n;
+    const C* bg = b ? b + g * n : nullptr;
+    C* yg = y + g * n;
+#define DPG_SPMV_BLK(KB)                                                                                          \
+  k_spmv_blk<C, KB><<<blocks, 256, 0, st>>>(A.row_ent, A.ent_start, A.col_ptr, A.col_idx, A.val_ptr, vals, xg, bg, yg, \
+                                            n, A.nrows, mode)
+    if (kb == 4) DPG_SPMV_BLK(4);
+    else if (kb == 3) DPG_SPMV_BLK(3);
+    else if (kb == 2) DPG_SPMV_BLK(2);
+    else DPG_SPMV_BLK(1);
+#undef DPG_SPMV_BLK
+    DPG_CHECK_LAUNCH();
+  }
+}
+
+template <class C>
+static void vcycle_blk(SystemImpl& S, WS& W, std::vector<BlockLevel<C>>& V, int l, const C* r, C* x, int K,
+                       cudaStream_t st) {
+  const Level& F = S.levels[l];
+  const int64_t n = F.mesh.ndof;
+  if (l == 0) {
+    for (int k = 0; k < K; ++k) {
+      if (F.has_coarse) coarse_solve<C>(S, W, r + k * n, x + k * n, st);
+      else if (F.P.np > 0) smooth<C>(F, r + k * n, x + k * n, F.theta, 0, V[0].pbuf, st);
+      else {
+        k_zero<C><<<nblk(n), 256, 0, st>>>(x + k * n, n);
+        DPG_CHECK_LAUNCH();
+      }
+    }
+    return;
+  }
+  const Level& Cl = S.levels[l - 1];
+  const int64_t nc = Cl.mesh.ndof;
+  const C* Avals = Prec<C>::A(F.A);
+  const C* rs = r;
+  if (F.kind == 2) {
+    for (int k = 0; k < K; ++k) condense<C>(F, r + k * n, V[l].rs + k * n, V[l].cbuf, st);
+    rs = V[l].rs;
+  }
+  for (int q = 0; q < S.op.nu_pre; ++q) {
+    if (q == 0) {
+      smooth_blk<C>(F, rs, x, F.theta, 0, V[l].pbuf, K, st);
+    } else {
+      spmv_blk<C>(F.A, Avals, x, rs, V[l].t, 1, K, st);
+      smooth_blk<C>(F, V[l].t, x, F.theta, 1, V[l].pbuf, K, st);
+    }
+  }
+  if (S.op.nu_pre == 0) {
+    k_zero<C><<<nblk(n * K), 256, 0, st>>>(x, n * K);
+    DPG_CHECK_LAUNCH();
+  }
+  spmv_blk<C>(F.A, Avals, x, rs, V[l].t, 1, K, st);
+  for (int k = 0; k < K; ++k) restrict_vec<C>(F, Cl, V[l].t + k * n, V[l - 1].r + k * nc, st);
+  vcycle_blk<C>(S, W, V, l - 1, V[l - 1].r, V[l - 1].x, K, st);
+  for (int k = 0; k < K; ++k) prolong_add<C>(F, Cl, V[l - 1].x + k * nc, x + k * n, st);
+  for (int q = 0; q < S.op.nu_post; ++q) {
+    spmv_blk<C>(F.A, Avals, x, rs, V[l].t, 1, K, st);
+    smooth_blk<C>(F, V[l].t, x, F.theta, 1, V[l].pbuf, K, st);
+  }
+  if (F.kind == 2)
+    for (int k = 0; k < K; ++k) backsub<C>(F, r + k * n, x + k * n, st);
+}
+
+template <class C>
+static std::vector<BlockLevel<C>> alloc_block_levels(Alloc& M, const SystemImpl& S, int K) {
+  std::vector<BlockLevel<C>> v(S.levels.size());
+  for (size_t l = 0; l < S.levels.size(); ++l) {
+    const Level& L = S.levels[l];
+    const size_t n = (size_t)L.mesh.ndof * K;
+    v[l].r = M.arr<C>(n);
+    v[l].rs = M.arr<C>(n);
+    v[l].x = M.arr<C>(n);
+    v[l].t = M.arr<C>(n);
+    if (l >= 1 || L.P.np > 0) v[l].pbuf = M.arr<C>((size_t)std::max<int64_t>(L.P.scratch_entries(), 1) * K);
+    if (L.kind == 2) v[l].cbuf = M.arr<C>((size_t)L.nK * L.nS);
+  }
+  return v;
+}
+
 static void dot(WS& W, const double2* u, const double2* v, int64_t n, int which, cudaStream_t st) {
   k_dot_fused<double2><<<RED_BLOCKS, 256, 0, st>>>(u, v, n, W.part, W.sc, which, W.ticket);
   DPG_CHECK_LAUNCH();
@@ -1504,6 +1729,171 @@ int pcg_solve(SystemImpl& S, cudaStream_t st, double2* xout, dpgmg_stats* stats,
     stats->dev_bytes_peak = (long long)S.mem_peak();
   }
   return status;
+}
+
+// ------------------------------------------------------------ block PCG
+// K independent MG-PCG iterations (each with its own scalars and stopping
+// test, the recurrence of pcg_solve) that share every V-cycle: z_k = B r_k for
+// all k at once through vcycle_blk.  Right-hand sides B and solutions X are
+// device [K][n].  A right-hand side that has converged keeps its x and r; its
+// V-cycle column is still computed (the matrices are read once for all).
+int pcg_solve_block(SystemImpl& S, cudaStream_t st, int K, const double2* B, double2* X, dpgmg_stats* stats) {
+  ensure_workspace(S, st);
+  WS& W = *reinterpret_cast<WS*>(S.ws);
+  const ECSRDev& A = cg_operator(S, W, st);
+  const int L = (int)S.levels.size() - 1;
+  const int64_t n = S.levels[L].mesh.ndof;
+  const bool mixed = S.op.precision == DPGMG_PREC_MIXED;
+  Alloc M;
+  M.budget = (size_t)-1;
+  M.stream = st;
+  double2* R = M.arr<double2>((size_t)n * K);
+  double2* P = M.arr<double2>((size_t)n * K);
+  double2* Q = M.arr<double2>((size_t)n * K);
+  double2* Z = M.arr<double2>((size_t)n * K);
+  double2* sc = M.arr<double2>((size_t)SC_COUNT * K);
+  float2* XH = cg_c128(S) ? nullptr : M.arr<float2>((size_t)n * K);
+  float2* XL = cg_c128(S) ? nullptr : M.arr<float2>((size_t)n * K);
+  // Y = A X (mode 0) or B - A X (mode 1) for all K columns with the CG operator,
+  // its stored values read once per group of BLK_MAX columns
+  auto cg_apply_blk = [&](const double2* Xs, const double2* Bs, double2* Ys, int mode) {
+    if (cg_c128(S)) {
+      spmv_blk<double2>(A, A.v64, Xs, Bs, Ys, mode, K, st);
+      return;
+    }
+    k_split_vec<<<nblk(n * K), 256, 0, st>>>(Xs, XH, XL, n * K);
+    DPG_CHECK_LAUNCH();
+    const unsigned blocks = (unsigned)std::min<int64_t>((n + 7) / 8, 152 * 16);
+    for (int g = 0; g < K; g += BLK_MAX) {
+      const int kb = std::min(BLK_MAX, K - g);
+      const double2* bg = Bs ? Bs + (size_t)g * n : nullptr;
+#define DPG_DF_BLK(KB)                                                                                            \
+  k_spmv_df_blk<KB><<<blocks, 256, 0, st>>>(A.row_ent, A.ent_start, A.col_ptr, A.col_idx, A.val_ptr, A.v32, A.vlo, \
+                                            XH + (size_t)g * n, XL + (size_t)g * n, bg, Ys + (size_t)g * n, n, n, mode)
+      if (kb == 4) DPG_DF_BLK(4);
+      else if (kb == 3) DPG_DF_BLK(3);
+      else if (kb == 2) DPG_DF_BLK(2);
+      else DPG_DF_BLK(1);
+#undef DPG_DF_BLK
+      DPG_CHECK_LAUNCH();
+    }
+  };
+  std::vector<BlockLevel<float2>> V32;
+  std::vector<BlockLevel<double2>> V64;
+  if (mixed) V32 = alloc_block_levels<float2>(M, S, K);
+  else V64 = alloc_block_levels<double2>(M, S, K);
+  std::vector<double2> sch((size_t)SC_COUNT * K);
+  auto read_scalars = [&]() {
+    DPG_CUDA(cudaMemcpyAsync(sch.data(), sc, sch.size() * sizeof(double2), cudaMemcpyDeviceToHost, st));
+    DPG_CUDA(cudaStreamSynchronize(st));
+  };
+  auto rhs_of = [&](double2* base, int k) { return base + (size_t)k * n; };
+  // z = B r for every column (complex128 result in Z)
+  auto precondition_blk = [&]() {
+    if (mixed) {
+      k_narrow<<<nblk(n * K), 256, 0, st>>>(R, V32[L].r, n * K);
+      DPG_CHECK_LAUNCH();
+      vcycle_blk<float2>(S, W, V32, L, V32[L].r, V32[L].x, K, st);
+      k_widen<<<nblk(n * K), 256, 0, st>>>(V32[L].x, Z, n * K);
+      DPG_CHECK_LAUNCH();
+    } else {
+      vcycle_blk<double2>(S, W, V64, L, R, Z, K, st);
+    }
+  };
+  cudaEvent_t e0, e1;
+  DPG_CUDA(cudaEventCreate(&e0));
+  DPG_CUDA(cudaEventCreate(&e1));
+  DPG_CUDA(cudaEventRecord(e0, st));
+  DPG_CUDA(cudaMemcpyAsync(R, B, (size_t)n * K * sizeof(double2), cudaMemcpyDeviceToDevice, st));
+  k_zero<double2><<<nblk(n * K), 256, 0, st>>>(X, n * K);
+  DPG_CHECK_LAUNCH();
+  // column k's CG scalars: sc[k * SC_COUNT ..]
+  auto sck = [&](int k) { return sc + (size_t)k * SC_COUNT; };
+  auto dotk = [&](const double2* u, const double2* v, int which, int k) {
+    k_dot_fused<double2><<<RED_BLOCKS, 256, 0, st>>>(u, v, n, W.part, sck(k), which, W.ticket);
+    DPG_CHECK_LAUNCH();
+  };
+  DPG_CUDA(cudaMemsetAsync(sc, 0, (size_t)SC_COUNT * K * sizeof(double2), st));
+  for (int k = 0; k < K; ++k) dotk(rhs_of(R, k), rhs_of(R, k), 1, k);
+  read_scalars();
+  std::vector<double> nb(K), rel(K, 0.0);
+  std::vector<int> iters(K, 0), done(K, 0), status(K, DPGMG_OK);
+  int active = 0;
+  for (int k = 0; k < K; ++k) {
+    nb[k] = std::sqrt(sch[(size_t)k * SC_COUNT + SC_RR].x);
+    done[k] = !(nb[k] > 0.0);
+    active += !done[k];
+  }
+  int it = 0;
+  if (active) {
+    precondition_blk();
+    for (int k = 0; k < K; ++k) dotk(rhs_of(Z, k), rhs_of(R, k), 3, k);
+    DPG_CUDA(cudaMemcpyAsync(P, Z, (size_t)n * K * sizeof(double2), cudaMemcpyDeviceToDevice, st));
+    while (true) {
+      ++it;
+      cg_apply_blk(P, nullptr, Q, 0);
+      for (int k = 0; k < K; ++k) {
+        if (done[k]) continue;
+        dotk(rhs_of(P, k), rhs_of(Q, k), 0, k);
+        k_cg_update_fused<<<RED_BLOCKS, 256, 0, st>>>(rhs_of(X, k), rhs_of(R, k), rhs_of(P, k), rhs_of(Q, k), sck(k),
+                                                       n, W.part, W.ticket, nullptr);
+        DPG_CHECK_LAUNCH();
+      }
+      read_scalars();
+      active = 0;
+      for (int k = 0; k < K; ++k) {
+        if (done[k]) continue;
+        const double2* c = &sch[(size_t)k * SC_COUNT];
+        iters[k] = it;
+        const double pq = c[SC_PQ].x;
+        rel[k] = std::sqrt(c[SC_RR].x) / nb[k];
+        if (!(pq > 0.0) || !std::isfinite(pq) || !std::isfinite(rel[k])) {
+          status[k] = DPGMG_ERR_BREAKDOWN;
+          done[k] = 1;
+        } else if (rel[k] <= S.op.tol || it >= S.op.max_iter) {
+          done[k] = 1;
+        }
+        active += !done[k];
+      }
+      if (!active) break;
+      precondition_blk();
+      for (int k = 0; k < K; ++k) {
+        if (done[k]) continue;
+        dotk(rhs_of(Z, k), rhs_of(R, k), 2, k);
+        k_cg_dir<double2><<<RED_BLOCKS, 256, 0, st>>>(rhs_of(P, k), rhs_of(Z, k), sck(k), n, W.xh, W.xl);
+        DPG_CHECK_LAUNCH();
+      }
+    }
+  }
+  DPG_CUDA(cudaEventRecord(e1, st));
+  DPG_CUDA(cudaEventSynchronize(e1));
+  float ms = 0.f;
+  DPG_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  int worst = DPGMG_OK;
+  // true residuals ||b - A x|| / ||b|| in FP64
+  cg_apply_blk(X, B, Q, 1);
+  for (int k = 0; k < K; ++k) dotk(rhs_of(Q, k), rhs_of(Q, k), 1, k);
+  read_scalars();
+  for (int k = 0; k < K; ++k) {
+    if (status[k] == DPGMG_OK && nb[k] > 0.0 && rel[k] > S.op.tol) status[k] = DPGMG_ERR_NOT_CONVERGED;
+    const double true_rel = nb[k] > 0.0 ? std::sqrt(sch[(size_t)k * SC_COUNT + SC_RR].x) / nb[k] : 0.0;
+    if (stats) {
+      dpgmg_stats& o = stats[k];
+      o.iters = iters[k];
+      o.relres = rel[k];
+      o.true_relres = true_rel;
+      o.t_pcg_ms = ms;
+      o.t_setup_ms = S.t_setup_ms;
+      o.bytes_per_iter = S.bytes_per_iter;
+      o.n_dof = n;
+      o.dev_bytes_peak = (long long)(S.mem_peak() + M.peak);
+    }
+    if (worst == DPGMG_OK && status[k] != DPGMG_OK) worst = status[k];
+  }
+  DPG_CUDA(cudaStreamSynchronize(st));
+  return worst;
 }
 
 // ---------------------------------------------------------------- theta

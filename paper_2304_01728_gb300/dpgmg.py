@@ -22,7 +22,7 @@ SRC_GAUSSIAN, SRC_PLANE_WAVE, SRC_MANUFACTURED = 0, 1, 2
 PREC_FP64, PREC_MIXED = 0, 1
 COARSEST_CHOLESKY, COARSEST_NONE, COARSEST_AUTO, COARSEST_SMOOTH = 0, 1, 2, 3
 FLAG_EAGER, FLAG_CUDA_CORES, FLAG_STORE_COARSE, FLAG_WARM_START, FLAG_CG_C128 = 1, 2, 4, 8, 16
-FLAG_PATCH_FP64 = 32
+FLAG_PATCH_FP64, FLAG_PATCH_R2 = 32, 64
 FLAG_FAULT_NOT_HPD, FLAG_FAULT_TC_WAIT = 1 << 28, 1 << 29
 OP_A, OP_SMOOTH, OP_VCYCLE, OP_RESTRICT, OP_PROLONG, OP_CONDENSE, OP_COARSE, OP_AFULL = range(8)
 
@@ -39,7 +39,8 @@ class dpgmg_problem(ctypes.Structure):
                 ("wavespeed", ctypes.POINTER(ctypes.c_double)), ("source", ctypes.c_int),
                 ("src_center", ctypes.c_double * 3), ("src_width", ctypes.c_double),
                 ("src_amp", ctypes.c_double), ("wave_dir", ctypes.c_double * 3),
-                ("mf_order", ctypes.c_int), ("mf_coeffs", ctypes.POINTER(ctypes.c_double))]
+                ("mf_order", ctypes.c_int), ("mf_coeffs", ctypes.POINTER(ctypes.c_double)),
+                ("u0_samples", ctypes.POINTER(ctypes.c_double))]
 
 
 class dpgmg_opts(ctypes.Structure):
@@ -69,7 +70,7 @@ EXPORTS = ["dpgmg_create", "dpgmg_destroy", "dpgmg_query_sizes", "dpgmg_default_
            "dpgmg_element_matrix", "dpgmg_rhs", "dpgmg_apply", "dpgmg_launch_count", "dpgmg_profile",
            "dpgmg_profile_read", "dpgmg_smooth_noalloc", "dpgmg_serve_start", "dpgmg_submit", "dpgmg_poll",
            "dpgmg_spmv_group", "dpgmg_setup_profile", "dpgmg_error_indicator", "dpgmg_setup_phases",
-           "dpgmg_dof_map"]
+           "dpgmg_dof_map", "dpgmg_boundary_points", "dpgmg_solve_block"]
 PROF_OFF, PROF_SMOOTH_FINE, PROF_SPMV_FINE, PROF_SPMV_CG = 0, 1, 2, 3
 
 
@@ -121,6 +122,12 @@ def lib():
     L.dpgmg_setup_phases.restype = i
     L.dpgmg_dof_map.argtypes = [ctypes.POINTER(dpgmg_problem), ll, ctypes.POINTER(i)]
     L.dpgmg_dof_map.restype = i
+    L.dpgmg_boundary_points.argtypes = [ctypes.POINTER(dpgmg_problem), ctypes.POINTER(ll),
+                                        ctypes.POINTER(ctypes.c_double)]
+    L.dpgmg_boundary_points.restype = i
+    L.dpgmg_solve_block.argtypes = [ctypes.c_void_p, ctypes.c_void_p, i, ctypes.c_void_p, ctypes.c_void_p, i,
+                                    ctypes.POINTER(dpgmg_stats)]
+    L.dpgmg_solve_block.restype = i
     L.dpgmg_error_indicator.argtypes = [vp, vp, dptr, dptr]
     L.dpgmg_error_indicator.restype = i
     L.dpgmg_profile_read.argtypes = [vp, vp, ctypes.POINTER(d), ctypes.POINTER(ll), ctypes.POINTER(ll)]
@@ -143,7 +150,7 @@ def _dptr(a):
 
 def make_problem(n, p, omega, x0=(0, 0, 0), x1=(1, 1, 1), wavespeed=None, source="gaussian",
                  src_center=(0.5, 0.5, 0.5), src_width=0.1, src_amp=1.0, wave_dir=(1, 0, 0),
-                 mf_coeffs=None):
+                 mf_coeffs=None, u0_samples=None):
     """Fill a dpgmg_problem; returns (struct, keep-alive list of arrays)."""
     pb = dpgmg_problem()
     keep = []
@@ -165,6 +172,10 @@ def make_problem(n, p, omega, x0=(0, 0, 0), x1=(1, 1, 1), wavespeed=None, source
         keep.append(C)
         pb.mf_order = C.shape[1]
         pb.mf_coeffs = C.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    if u0_samples is not None:
+        U = np.ascontiguousarray(np.asarray(u0_samples, dtype=np.complex128))
+        keep.append(U)
+        pb.u0_samples = U.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
     return pb, keep
 
 
@@ -213,6 +224,24 @@ def dpgmg_solve(h, s, trace_out=None, field_out=None, out_is_device=False):
     if code not in (DPGMG_OK, DPGMG_ERR_NOT_CONVERGED):
         _check(code, "dpgmg_solve")
     return code, st
+
+
+def dpgmg_solve_block(h, s, rhs, trace_out=None, on_device=False, k=None):
+    """k right-hand sides at once.  rhs: numpy complex128 [k, n] (host) or a
+    device pointer (int, then k is required); trace_out likewise (host arrays
+    are allocated when None).  Returns (code, x, [stats per column])."""
+    if isinstance(rhs, np.ndarray):
+        rhs = np.ascontiguousarray(rhs, dtype=np.complex128)
+        k = rhs.shape[0]
+        if trace_out is None:
+            trace_out = np.zeros_like(rhs)
+    stats = (dpgmg_stats * k)()
+    rp = rhs.ctypes.data if isinstance(rhs, np.ndarray) else rhs
+    tp = trace_out.ctypes.data if isinstance(trace_out, np.ndarray) else trace_out
+    code = lib().dpgmg_solve_block(h, s, int(k), rp, tp, int(bool(on_device)), stats)
+    if code not in (DPGMG_OK, DPGMG_ERR_NOT_CONVERGED):
+        _check(code, "dpgmg_solve_block")
+    return code, trace_out, list(stats)
 
 
 def dpgmg_release(h, s):
@@ -272,6 +301,17 @@ def dpgmg_dof_map(pb, n_trace):
     out = np.zeros((n_trace, 7), dtype=np.int32)
     _check(lib().dpgmg_dof_map(ctypes.byref(pb), n_trace, out.ctypes.data_as(ctypes.POINTER(ctypes.c_int))),
            "dpgmg_dof_map")
+    return out
+
+
+def dpgmg_boundary_points(pb):
+    """Points [n, 3] at which a caller's impedance load u0 is sampled (problem u0_samples)."""
+    n = ctypes.c_longlong(0)
+    _check(lib().dpgmg_boundary_points(ctypes.byref(pb), ctypes.byref(n), None), "dpgmg_boundary_points")
+    out = np.zeros((n.value, 3))
+    _check(lib().dpgmg_boundary_points(ctypes.byref(pb), ctypes.byref(n),
+                                       out.ctypes.data_as(ctypes.POINTER(ctypes.c_double))),
+           "dpgmg_boundary_points")
     return out
 
 

@@ -76,7 +76,8 @@ def oracle_system(pk, ok, hierarchy=True, parallel=False):
                                 load=oracle_load(pk), x0=cmesh.x0, x1=cmesh.x1)
                 return cf.Kc
         levels = build_hierarchy(fs.mesh, fs.Kc, fs.dofs, ok.get("n_levels", 2), ok.get("p_min", 2),
-                                 coarsest=ok.get("coarsest", "cholesky"), stored=stored)
+                                 coarsest=ok.get("coarsest", "cholesky"), stored=stored,
+                                 patch_rule="R2" if ok.get("flags", 0) & 64 else "R1")
     return fs, A, b, levels
 
 

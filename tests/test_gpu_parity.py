@@ -440,3 +440,46 @@ def test_smoothing_coarsest_matches_oracle(nl, precision):
     assert code == D.DPGMG_OK
     assert abs(st.iters - it_ref) <= max(1, 0.1 * it_ref), (st.iters, it_ref)
     assert rel(xs, x_ref) < 1e-7
+
+
+@pytest.mark.parametrize("n,nl,pmin,coarsest,precision", [
+    ((4, 4, 4), 3, 1, "cholesky", "fp64"),
+    ((4, 4, 4), 3, 1, "cholesky", "mixed"),
+    ((4, 4, 4), 2, 1, "smooth", "fp64"),
+    ((8, 8, 4), 4, 1, "cholesky", "fp64"),
+])
+def test_patch_rule_r2_matches_oracle(n, nl, pmin, coarsest, precision):
+    """DPGMG_FLAG_PATCH_R2: every smoothed level's patch statistics, the
+    smoother of every level and the V-cycle against the oracle built with rule
+    R2; PCG iterations and solution at the parity bar."""
+    from oracle.hierarchy import smoother
+    from tests.oracle_adapter import MIXED_VCYCLE_TOL
+    pk = dict(n=n, p=2, omega=4.0, src_center=(0.4, 0.55, 0.5), src_width=0.2)
+    if n[2] == 4 and n[0] == 8:
+        pk["wavespeed"] = np.repeat(np.random.default_rng(3).uniform(0.5, 1.0, 4), 64)
+    ok = dict(n_levels=nl, p_min=pmin, precision=precision, tol=1e-8, coarsest=coarsest,
+              flags=D.FLAG_PATCH_R2)
+    fs, A, b, levels = oracle_system(pk, ok)
+    L = len(levels) - 1
+    vtol = 1e-10 if precision == "fp64" else MIXED_VCYCLE_TOL
+    with D.Solver(pk, **ok) as s:
+        for l in range(L + 1):
+            o = levels[l]
+            if not hasattr(o, "patches") or o.patches is None:
+                continue
+            g = s.level(l)
+            sizes = np.array([len(x) for x in o.patches])
+            assert g.n_patches == len(sizes) and g.patch_max == sizes.max()
+            assert g.sum_patch_sq == int(np.sum(sizes ** 2))
+            nl_ = o.mesh.n_dof
+            x = rand_vec(nl_, 5 + l)
+            y = D.dpgmg_apply(s.h, s.s, D.OP_SMOOTH, l, x, nl_)
+            assert rel(y, o.theta * smoother(o, x)) < vtol
+        nt = A.shape[0]
+        v = rand_vec(nt, 4)
+        assert rel(D.dpgmg_apply(s.h, s.s, D.OP_VCYCLE, L, v, nt), vcycle(levels, L, v)) < vtol
+        xs, f, st, code = s.solve()
+    x_ref, it_ref, _ = mg_pcg(levels, A, b, tol=ok["tol"])
+    assert code == D.DPGMG_OK
+    assert abs(st.iters - it_ref) <= max(1, 0.1 * it_ref), (st.iters, it_ref)
+    assert rel(xs, x_ref) < 1e-7

@@ -7,6 +7,7 @@ import ctypes
 import os
 import re
 
+import numpy as np
 import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
@@ -48,18 +49,42 @@ def test_query_sizes_without_device(libpath):
     nt, nf, nb = dpgmg.dpgmg_query_sizes(pb, dpgmg.make_opts(**w["opts"]))
     assert nt == 188561 and nf == 4096 * 4 * 27
     assert nb > 1e9
+    # rule R2 blocks are smaller at the boundary: less patch storage
+    nt2, _, nb2 = dpgmg.dpgmg_query_sizes(pb, dpgmg.make_opts(**dict(w["opts"], flags=dpgmg.FLAG_PATCH_R2)))
+    assert nt2 == nt and nb2 < nb
+    with pytest.raises(dpgmg.DpgmgError):
+        dpgmg.dpgmg_query_sizes(pb, dpgmg.make_opts(**dict(w["opts"], flags=1 << 20)))
     pb.dp = 2
     with pytest.raises(dpgmg.DpgmgError):
         dpgmg.dpgmg_query_sizes(pb, dpgmg.make_opts(**w["opts"]))
 
 
-def test_struct_layouts_match_header(libpath):
+def test_struct_layouts_match_header(libpath, tmp_path):
+    # every field offset and struct size of the binding's ctypes mirrors against
+    # the C compiler's view of include/dpgmg.h
+    import shutil
+    import subprocess
     from paper_2304_01728_gb300 import dpgmg
-    # sizes of the ABI structs on LP64 (x86_64 and aarch64 agree)
-    assert ctypes.sizeof(dpgmg.dpgmg_problem) == 176
-    assert ctypes.sizeof(dpgmg.dpgmg_opts) == 48
-    assert ctypes.sizeof(dpgmg.dpgmg_stats) == 64
-    assert ctypes.sizeof(dpgmg.dpgmg_level_desc) == 88
+    if shutil.which("gcc") is None:
+        pytest.skip("no C compiler")
+    structs = [dpgmg.dpgmg_problem, dpgmg.dpgmg_opts, dpgmg.dpgmg_stats, dpgmg.dpgmg_level_desc]
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "dpgmg.h"', 'int main(void) {']
+    expect = []
+    for st in structs:
+        name = st.__name__
+        lines.append('printf("%%zu\\n", sizeof(%s));' % name)
+        expect.append(ctypes.sizeof(st))
+        for fname, _ in st._fields_:
+            lines.append('printf("%%zu\\n", offsetof(%s, %s));' % (name, fname))
+            expect.append(getattr(st, fname).offset)
+    lines.append("return 0; }")
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-I", os.path.join(root, "include"), str(src), "-o", str(exe)], check=True)
+    got = [int(v) for v in subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split()]
+    assert got == expect
 
 
 @pytest.mark.parametrize("n,p", [((3, 2, 4), 3), ((2, 2, 2), 1), ((1, 3, 2), 5)])
@@ -86,3 +111,32 @@ def test_dof_map_matches_the_oracle_numbering(libpath, n, p):
             assert tuple(row[4:]) == modes, (g, row, modes)
     with pytest.raises(dpgmg.DpgmgError):
         dpgmg.dpgmg_dof_map(pb, nt + 1)
+
+
+@pytest.mark.parametrize("n,p", [((3, 2, 4), 2), ((1, 2, 1), 4)])
+def test_boundary_points_are_the_oracle_face_rule(libpath, n, p):
+    # the documented order (sides (d, s), faces j1 fastest, points a fastest)
+    # at the oracle's boundary load rule: Gauss-Legendre with p + 5 points
+    from oracle.basis import gauss01
+    from paper_2304_01728_gb300 import dpgmg
+    x0, x1 = np.array([0.5, -1.0, 0.0]), np.array([2.0, 1.0, 3.0])
+    pb, keep = dpgmg.make_problem(n=n, p=p, omega=3.0, x0=tuple(x0), x1=tuple(x1))
+    pts = dpgmg.dpgmg_boundary_points(pb)
+    xg, _ = gauss01(p + 5)
+    h = (x1 - x0) / np.asarray(n)
+    ref = []
+    for d in range(3):
+        t1, t2 = [e for e in range(3) if e != d]
+        for s in range(2):
+            for j2 in range(n[t2]):
+                for j1 in range(n[t1]):
+                    for b in xg:
+                        for a in xg:
+                            X = np.zeros(3)
+                            X[d] = x1[d] if s else x0[d]
+                            X[t1] = x0[t1] + (j1 + a) * h[t1]
+                            X[t2] = x0[t2] + (j2 + b) * h[t2]
+                            ref.append(X)
+    ref = np.array(ref)
+    assert pts.shape == ref.shape
+    assert np.abs(pts - ref).max() < 1e-13
