@@ -170,6 +170,18 @@ typedef struct dpgmg_opts {
    against 104 on a 4^3 p = 2 mesh).  Applies to every smoothed level,
    including level 0 under DPGMG_COARSEST_SMOOTH. */
 #define DPGMG_FLAG_PATCH_R2 64
+/* Memory-lean smoother (Sec. 5: patch storage limits the order; recomputing
+   the patches during the solve is the paper's proposed remedy on GPUs): the
+   patch inverses are not stored.  Every smoother application gathers the
+   complex64 blocks from the level operator, factors them in FP32 and applies
+   them, window by window (consecutive patches, largest first, a quarter of
+   the level's blocks and at most 256 MiB per window), so a level holds two
+   window buffers instead of its sum n_j^2 stored entries.
+   Same arithmetic as the stored FP32 factors: the same results.  Far more
+   work per iteration; several loads per solve (dpgmg_solve_block) share it.
+   Mixed path only, without DPGMG_FLAG_PATCH_FP64 and DPGMG_FLAG_CG_C128
+   (ARG otherwise); dpgmg_smooth_noalloc is not available (ARG). */
+#define DPGMG_FLAG_RECOMPUTE_PATCHES 128
 /* Host-made failures for testing the error paths (the paper has no
    counterpart; no GPU fault is involved):
    FAULT_NOT_HPD: the host overwrites the first diagonal entry of the dense

@@ -85,8 +85,13 @@ int validate_problem(const dpgmg_problem* pb, const dpgmg_opts* op) {
       (op->coarsest != DPGMG_COARSEST_CHOLESKY && op->coarsest != DPGMG_COARSEST_NONE &&
        op->coarsest != DPGMG_COARSEST_AUTO && op->coarsest != DPGMG_COARSEST_SMOOTH) ||
       (op->flags & ~(DPGMG_FLAG_EAGER | DPGMG_FLAG_CUDA_CORES | DPGMG_FLAG_STORE_COARSE | DPGMG_FLAG_WARM_START |
-                     DPGMG_FLAG_CG_C128 | DPGMG_FLAG_PATCH_FP64 | DPGMG_FLAG_PATCH_R2 | DPGMG_FLAG_FAULT_NOT_HPD |
+                     DPGMG_FLAG_CG_C128 | DPGMG_FLAG_PATCH_FP64 | DPGMG_FLAG_PATCH_R2 |
+                     DPGMG_FLAG_RECOMPUTE_PATCHES | DPGMG_FLAG_FAULT_NOT_HPD |
                      DPGMG_FLAG_FAULT_TC_WAIT)))
+    return DPGMG_ERR_ARG;
+  // recompute mode: the mixed path's FP32 patch factors and complex64 damping estimate only
+  if ((op->flags & DPGMG_FLAG_RECOMPUTE_PATCHES) &&
+      (op->precision != DPGMG_PREC_MIXED || (op->flags & (DPGMG_FLAG_PATCH_FP64 | DPGMG_FLAG_CG_C128))))
     return DPGMG_ERR_ARG;
   if ((op->flags & DPGMG_FLAG_STORE_COARSE) && pb->wavespeed) {
     const int64_t ne = (int64_t)pb->n[0] * pb->n[1] * pb->n[2];
@@ -151,7 +156,13 @@ size_t estimate_bytes(const dpgmg_problem* pb, const dpgmg_opts* op) {
         nslots += (double)v;
         nmax = std::max(nmax, (double)v);
       }
-      resident += nvals * vsz + nslots * (8.0 + 16.0 + x32) + nslots / 32.0 * 8.0;
+      if (op->flags & DPGMG_FLAG_RECOMPUTE_PATCHES) {
+        // two window buffers instead of the stored inverses, index lists
+        const double wcap = std::max(nmax * (nmax + 1.0), std::min(std::ceil(nvals / 4.0), (double)(32 << 20)));
+        resident += 2.0 * wcap * 8.0 + nslots * (8.0 + 16.0 + x32) + nslots / 32.0 * 8.0 + ps.size() * 24.0;
+      } else {
+        resident += nvals * vsz + nslots * (8.0 + 16.0 + x32) + nslots / 32.0 * 8.0;
+      }
       const double one = nmax * nmax * 16.0;
       const double cap = std::max(std::min(std::min(std::max((double)(1 << 28), one) * 4.0, (double)(2ull << 30)),
                                            nvals * 16.0), one);
@@ -684,7 +695,7 @@ int dpgmg_level_info(dpgmg_handle h, dpgmg_system sys, int level, dpgmg_level_de
   out->sum_patch_sq = L.P.sum_sq;
   out->op_nnz = L.A.nnz_alg;
   out->theta = L.theta;
-  out->patch_stored = L.P.half ? L.P.nhvals : L.P.nvals;
+  out->patch_stored = L.P.recompute ? 0 : (L.P.half ? L.P.nhvals : L.P.nvals);
   return DPGMG_OK;
 }
 

@@ -1,10 +1,11 @@
 // Several right-hand sides at once (Sec. 5: loads solved together share the
-// cost of reading the patches): block forms of the two products of the V-cycle
-// that stream stored matrices from HBM.  Each stored entry is read once and
-// applied to KB vectors (KB <= 4 per launch), so the bytes per right-hand side
-// fall by KB.  Vectors of a block are stored one after another with a fixed
-// stride; per vector the arithmetic and its order are those of the
-// single-vector kernels' simple loops (no cross-vector reductions).
+// cost of reading the patches): block forms of the V-cycle kernels that
+// stream stored matrices from HBM (smoother, SpMV, macro-grid condensation and
+// back-substitution).  Each stored entry is read once and applied to KB
+// vectors (KB <= 4 per launch), so the bytes per right-hand side fall by KB.
+// Vectors of a block are stored one after another with a fixed stride; per
+// vector the arithmetic is that of the single-vector kernels (no
+// cross-vector reductions).
 #pragma once
 #include "common.cuh"
 #include "host_mesh.h"
@@ -52,19 +53,22 @@ __global__ void __launch_bounds__(256) k_patch_apply_blk(const int64_t* __restri
     const C* M = inv + vptr[j] + a;
     int k = w;
     if (PER == 2) {
-      // 16-byte loads of (M[k][a], M[k][a+1]): a and ld are even
+      // 16-byte loads of (M[k][a], M[k][a+1]): a and ld are even; four rows
+      // in flight per lane
       const float4* M4 = reinterpret_cast<const float4*>(M);
       const int64_t s4 = ld / 2;
-      for (; k + 8 < n; k += 16) {
-        const float4 m0 = __ldcs(M4 + (int64_t)k * s4), m1 = __ldcs(M4 + (int64_t)(k + 8) * s4);
+      for (; k + 24 < n; k += 32) {
+        float4 m[4];
 #pragma unroll
-        for (int kb = 0; kb < KB; ++kb) {
-          const C r0 = rj[kb * n + k], r1 = rj[kb * n + k + 8];
-          acc[kb][0] = O::fmac(r0, Ops<C>::mk(m0.x, m0.y), acc[kb][0]);
-          acc[kb][1 % PER] = O::fmac(r0, Ops<C>::mk(m0.z, m0.w), acc[kb][1 % PER]);
-          acc[kb][0] = O::fmac(r1, Ops<C>::mk(m1.x, m1.y), acc[kb][0]);
-          acc[kb][1 % PER] = O::fmac(r1, Ops<C>::mk(m1.z, m1.w), acc[kb][1 % PER]);
-        }
+        for (int u = 0; u < 4; ++u) m[u] = __ldcs(M4 + (int64_t)(k + 8 * u) * s4);
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+          for (int kb = 0; kb < KB; ++kb) {
+            const C rv = rj[kb * n + k + 8 * u];
+            acc[kb][0] = O::fmac(rv, Ops<C>::mk(m[u].x, m[u].y), acc[kb][0]);
+            acc[kb][1 % PER] = O::fmac(rv, Ops<C>::mk(m[u].z, m[u].w), acc[kb][1 % PER]);
+          }
       }
       for (; k < n; k += 8) {
         const float4 m0 = __ldcs(M4 + (int64_t)k * s4);
@@ -75,13 +79,14 @@ __global__ void __launch_bounds__(256) k_patch_apply_blk(const int64_t* __restri
         }
       }
     } else {
-      for (; k + 8 < n; k += 16) {
-        const C m0 = ld_stream(M + (size_t)k * ld), m1 = ld_stream(M + (size_t)(k + 8) * ld);
+      for (; k + 24 < n; k += 32) {
+        C m[4];
 #pragma unroll
-        for (int kb = 0; kb < KB; ++kb) {
-          acc[kb][0] = O::fmac(rj[kb * n + k], m0, acc[kb][0]);
-          acc[kb][0] = O::fmac(rj[kb * n + k + 8], m1, acc[kb][0]);
-        }
+        for (int u = 0; u < 4; ++u) m[u] = ld_stream(M + (size_t)(k + 8 * u) * ld);
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+          for (int kb = 0; kb < KB; ++kb) acc[kb][0] = O::fmac(rj[kb * n + k + 8 * u], m[u], acc[kb][0]);
       }
       for (; k < n; k += 8) {
         const C m0 = ld_stream(M + (size_t)k * ld);
@@ -137,15 +142,28 @@ __global__ void __launch_bounds__(256) k_spmv_blk(const int32_t* __restrict__ ro
       const int32_t* cols = col_idx + c0;
       int k = lane;
       int cA = k < nnz ? __ldg(cols + k) : 0;
-      for (; k < nnz; k += 32) {
-        const C v0 = __ldcs(vals + k);
-        C xv[KB];
+      int cB = k + 32 < nnz ? __ldg(cols + k + 32) : 0;
+      for (; k + 32 < nnz; k += 64) {   // two columns per lane per step, indices one step ahead
+        const C v0 = __ldcs(vals + k), v1 = __ldcs(vals + k + 32);
+        C x0[KB], x1[KB];
 #pragma unroll
-        for (int kb = 0; kb < KB; ++kb) xv[kb] = x[kb * ld + cA];
-        const int kn = k + 32;
+        for (int kb = 0; kb < KB; ++kb) {
+          x0[kb] = x[kb * ld + cA];
+          x1[kb] = x[kb * ld + cB];
+        }
+        const int kn = k + 64;
         cA = kn < nnz ? __ldg(cols + kn) : 0;
+        cB = kn + 32 < nnz ? __ldg(cols + kn + 32) : 0;
 #pragma unroll
-        for (int kb = 0; kb < KB; ++kb) acc[kb] = O::fma(v0, xv[kb], acc[kb]);
+        for (int kb = 0; kb < KB; ++kb) {
+          acc[kb] = O::fma(v0, x0[kb], acc[kb]);
+          acc[kb] = O::fma(v1, x1[kb], acc[kb]);
+        }
+      }
+      if (k < nnz) {
+        const C v0 = __ldcs(vals + k);
+#pragma unroll
+        for (int kb = 0; kb < KB; ++kb) acc[kb] = O::fma(v0, x[kb * ld + cA], acc[kb]);
       }
 #pragma unroll
       for (int kb = 0; kb < KB; ++kb) acc[kb] = warp_sum_s(acc[kb]);
@@ -156,6 +174,101 @@ __global__ void __launch_bounds__(256) k_spmv_blk(const int32_t* __restrict__ ro
       for (int kb = 1; kb < KB; ++kb)
         if (lane == kb) mine = acc[kb];
       y[lane * ld + row] = mode ? O::sub(b[lane * ld + row], mine) : mine;
+    }
+  }
+}
+
+// y_kb[g] = (accumulate ? y_kb[g] : 0) + theta * sum_{slots of g} pbuf_kb[slot]
+// for kb = blockIdx.y (y at stride ld, pbuf at stride ldp)
+template <class C>
+__global__ void k_slot_sum_blk(const int64_t* __restrict__ sptr, const int32_t* __restrict__ slots,
+                               const C* __restrict__ pbuf, int64_t ldp, C* __restrict__ y, int64_t ld, int64_t n,
+                               double theta, int accumulate) {
+  const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (g >= n) return;
+  const C* pb = pbuf + blockIdx.y * ldp;
+  C acc = Ops<C>::zero();
+  for (int64_t s = sptr[g]; s < sptr[g + 1]; ++s) acc = Ops<C>::add(acc, pb[slots[s]]);
+  acc = Ops<C>::scale(acc, (typename Ops<C>::R)theta);
+  C* yk = y + blockIdx.y * ld;
+  yk[g] = accumulate ? Ops<C>::add(yk[g], acc) : acc;
+}
+
+// Block forms of the macro-grid transfers (one CTA per coarse element K): the
+// element's stored blocks Y_K (and A_II^-1 for the back-substitution) are read
+// once for KB vectors at stride ld (cbuf at stride ldc).
+template <class C, int KB>
+__global__ void k_condense_apply_blk(int nS, int nI, const int64_t* __restrict__ Ig, const C* __restrict__ Y,
+                                     const C* __restrict__ r, int64_t ld, C* __restrict__ cbuf, int64_t ldc) {
+  extern __shared__ unsigned char shraw[];
+  C* rI = reinterpret_cast<C*>(shraw);   // [KB][nI]
+  const int64_t K = blockIdx.x;
+  for (int i = threadIdx.x; i < nI; i += blockDim.x) {
+    const int64_t g = Ig[K * nI + i];
+#pragma unroll
+    for (int kb = 0; kb < KB; ++kb) rI[kb * nI + i] = r[kb * ld + g];
+  }
+  __syncthreads();
+  const C* YK = Y + K * (size_t)nI * nS;
+  for (int a = threadIdx.x; a < nS; a += blockDim.x) {
+    C acc[KB];
+#pragma unroll
+    for (int kb = 0; kb < KB; ++kb) acc[kb] = Ops<C>::zero();
+    for (int i = 0; i < nI; ++i) {
+      const C y = YK[(size_t)i * nS + a];
+#pragma unroll
+      for (int kb = 0; kb < KB; ++kb) acc[kb] = Ops<C>::fmac(rI[kb * nI + i], y, acc[kb]);
+    }
+#pragma unroll
+    for (int kb = 0; kb < KB; ++kb) cbuf[kb * ldc + K * nS + a] = acc[kb];
+  }
+}
+
+template <class C, int KB>
+__global__ void k_backsub_blk(int nS, int nI, const int64_t* __restrict__ Sg, const int64_t* __restrict__ Ig,
+                              const C* __restrict__ Ai, const C* __restrict__ Y, const C* __restrict__ r,
+                              C* __restrict__ x, int64_t ld) {
+  extern __shared__ unsigned char shraw[];
+  C* rI = reinterpret_cast<C*>(shraw);   // [KB][nI]
+  C* xS = rI + KB * nI;                  // [KB][nS]
+  using O = Ops<C>;
+  const int64_t K = blockIdx.x;
+  for (int i = threadIdx.x; i < nI; i += blockDim.x) {
+    const int64_t g = Ig[K * nI + i];
+#pragma unroll
+    for (int kb = 0; kb < KB; ++kb) rI[kb * nI + i] = r[kb * ld + g];
+  }
+  for (int a = threadIdx.x; a < nS; a += blockDim.x) {
+    const int64_t g = Sg[K * nS + a];
+#pragma unroll
+    for (int kb = 0; kb < KB; ++kb) xS[kb * nS + a] = g >= 0 ? x[kb * ld + g] : O::zero();
+  }
+  __syncthreads();
+  const C* AiK = Ai + K * (size_t)nI * nI;
+  const C* YK = Y + K * (size_t)nI * nS;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  for (int i = w; i < nI; i += blockDim.x >> 5) {
+    C acc[KB];
+#pragma unroll
+    for (int kb = 0; kb < KB; ++kb) acc[kb] = O::zero();
+    for (int k = lane; k < nI; k += 32) {
+      const C m = AiK[(size_t)i * nI + k];
+#pragma unroll
+      for (int kb = 0; kb < KB; ++kb) acc[kb] = O::fma(m, rI[kb * nI + k], acc[kb]);
+    }
+    for (int a = lane; a < nS; a += 32) {
+      const C m = YK[(size_t)i * nS + a];
+#pragma unroll
+      for (int kb = 0; kb < KB; ++kb) acc[kb] = O::fnma(m, xS[kb * nS + a], acc[kb]);
+    }
+#pragma unroll
+    for (int kb = 0; kb < KB; ++kb) acc[kb] = warp_sum_s(acc[kb]);
+    if (lane < KB) {
+      C mine = acc[0];
+#pragma unroll
+      for (int kb = 1; kb < KB; ++kb)
+        if (lane == kb) mine = acc[kb];
+      x[lane * ld + Ig[K * nI + i]] = mine;
     }
   }
 }

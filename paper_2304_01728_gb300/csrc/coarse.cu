@@ -534,6 +534,89 @@ static void coarse_apply_t(const C* Lp, const C* Up, int64_t N, const C* r, C* e
   DPG_CHECK_LAUNCH();
 }
 
+// Block forms for KB right-hand sides (vectors at stride ld): each packed
+// row is read once for the KB vectors.
+template <class C, int KB>
+__device__ __forceinline__ void dot_row_blk(const C* __restrict__ row, const C* __restrict__ v, int64_t ld,
+                                            int64_t len, int lane, C out[KB]) {
+  using O = Ops<C>;
+  C a[KB];
+#pragma unroll
+  for (int kb = 0; kb < KB; ++kb) a[kb] = O::zero();
+  int64_t t = lane;
+  for (; t + 32 < len; t += 64) {
+    const C m0 = __ldcs(row + t), m1 = __ldcs(row + t + 32);
+#pragma unroll
+    for (int kb = 0; kb < KB; ++kb) {
+      a[kb] = O::fma(m0, v[kb * ld + t], a[kb]);
+      a[kb] = O::fma(m1, v[kb * ld + t + 32], a[kb]);
+    }
+  }
+  if (t < len) {
+    const C m0 = __ldcs(row + t);
+#pragma unroll
+    for (int kb = 0; kb < KB; ++kb) a[kb] = O::fma(m0, v[kb * ld + t], a[kb]);
+  }
+#pragma unroll
+  for (int kb = 0; kb < KB; ++kb) out[kb] = warp_sum_c(a[kb]);
+}
+
+// UPPER = false: y = L^-1 r (packed lower rows); true: e = L^-H y (packed
+// upper rows, row j starts at column j)
+template <class C, int KB, bool UPPER>
+__global__ void __launch_bounds__(256) k_trmv_blk(const C* __restrict__ Tp, int64_t N, const C* __restrict__ x,
+                                                  C* __restrict__ y, int64_t ld) {
+  const int lane = threadIdx.x & 31;
+  const int64_t half = (N + 1) / 2;
+  const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t w = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); w < half; w += nw) {
+    for (int side = 0; side < 2; ++side) {
+      const int64_t i = side ? N - 1 - w : w;
+      if (side && i == w) break;
+      C s[KB];
+      if (UPPER) dot_row_blk<C, KB>(Tp + i * N - i * (i - 1) / 2, x + i, ld, N - i, lane, s);
+      else dot_row_blk<C, KB>(Tp + i * (i + 1) / 2, x, ld, i + 1, lane, s);
+      if (lane < KB) {
+        C mine = s[0];
+#pragma unroll
+        for (int kb = 1; kb < KB; ++kb)
+          if (lane == kb) mine = s[kb];
+        y[lane * ld + i] = mine;
+      }
+    }
+  }
+}
+
+template <class C>
+static void coarse_apply_blk_t(const C* Lp, const C* Up, int64_t N, const C* r, C* e, C* tmp, int K,
+                               cudaStream_t st) {
+  unsigned blocks = (unsigned)std::min<int64_t>(((N + 1) / 2 + 7) / 8, 152 * 16);
+  for (int g = 0; g < K; g += 4) {
+    const int kb = std::min(4, K - g);
+    const C* rg = r + g * N;
+    C* tg = tmp + g * N;
+    C* eg = e + g * N;
+#define DPG_TRMV_BLK(KB)                                                      \
+  k_trmv_blk<C, KB, false><<<blocks, 256, 0, st>>>(Lp, N, rg, tg, N);         \
+  DPG_CHECK_LAUNCH();                                                         \
+  k_trmv_blk<C, KB, true><<<blocks, 256, 0, st>>>(Up, N, tg, eg, N);          \
+  DPG_CHECK_LAUNCH()
+    if (kb == 4) { DPG_TRMV_BLK(4); }
+    else if (kb == 3) { DPG_TRMV_BLK(3); }
+    else if (kb == 2) { DPG_TRMV_BLK(2); }
+    else { DPG_TRMV_BLK(1); }
+#undef DPG_TRMV_BLK
+  }
+}
+
+// K right-hand sides at stride N0; tmp holds K * N0 values
+void coarse_apply64_blk(const Level& C0, const double2* r, double2* e, double2* tmp, int K, cudaStream_t st) {
+  coarse_apply_blk_t<double2>(C0.Lp64, C0.Up64, C0.N0, r, e, tmp, K, st);
+}
+void coarse_apply32_blk(const Level& C0, const float2* r, float2* e, float2* tmp, int K, cudaStream_t st) {
+  coarse_apply_blk_t<float2>(C0.Lp32, C0.Up32, C0.N0, r, e, tmp, K, st);
+}
+
 void coarse_apply64(const Level& C0, const double2* r, double2* e, double2* tmp, cudaStream_t st) {
   coarse_apply_t<double2>(C0.Lp64, C0.Up64, C0.N0, r, e, tmp, st);
 }

@@ -101,6 +101,20 @@ struct PatchDev {
   int64_t* hptr = nullptr;     // per patch (+1): offset of its packed triangle
   float2* h32 = nullptr;
   int64_t scratch_entries() const { return nslots; }
+  // DPGMG_FLAG_RECOMPUTE_PATCHES: no stored inverses; every application
+  // gathers, factors (FP32) and applies the blocks window by window, a window
+  // being consecutive patches of `order` (largest first) within wcap entries
+  bool recompute = false;
+  std::vector<int64_t> wq;       // window w = order positions [wq[w], wq[w+1])
+  std::vector<int64_t> wch;      // window w's work items [wch[w], wch[w+1]) of wchunks
+  int64_t wcap = 0;              // entries of the window buffer (and of its factorisation scratch)
+  int64_t* worder = nullptr;     // patch order (largest first)
+  int64_t* wvptr = nullptr;      // per patch: offset of its n x ld block within its window buffer
+  int64_t* wsoff = nullptr;      // per order position: offset of its scratch copy
+  int2* wchunks = nullptr;       // (patch, first column) of 64-column work items, window by window
+  float2* wbuf = nullptr;
+  float2* wscratch = nullptr;
+  int* winfo = nullptr;
 };
 
 struct Level {
@@ -254,6 +268,13 @@ void assemble_rhs(SystemImpl& S, cudaStream_t st);
 void coarse_setup(SystemImpl& S, Level& C0, int* info, cudaStream_t st, Alloc& A);
 void coarse_apply64(const Level& C0, const double2* r, double2* e, double2* tmp, cudaStream_t st);
 void coarse_apply32(const Level& C0, const float2* r, float2* e, float2* tmp, cudaStream_t st);
+// y-products of the smoother in recompute mode (complex64 blocks factored in
+// FP32): pbuf[slot] = A_jj^-1 (R_j r) for every patch of level L
+void patch_recompute_apply(const Level& L, const float2* r, float2* pbuf, cudaStream_t st);
+void patch_recompute_apply_blk(const Level& L, const float2* r, int64_t ldr, float2* pbuf, int64_t ldp, int K,
+                               cudaStream_t st);
+void coarse_apply64_blk(const Level& C0, const double2* r, double2* e, double2* tmp, int K, cudaStream_t st);
+void coarse_apply32_blk(const Level& C0, const float2* r, float2* e, float2* tmp, int K, cudaStream_t st);
 // solve.cu
 // x0 (device, may be null): initial guess of the CG iteration (0 if null)
 int pcg_solve(SystemImpl& S, cudaStream_t st, double2* x, dpgmg_stats* stats, const double2* x0 = nullptr);

@@ -21,6 +21,8 @@
 #include "common.cuh"
 #include "internal.h"
 #include "smoother.cuh"
+#include "block.cuh"
+#include "smoother.cuh"
 
 namespace dpgmg {
 
@@ -293,10 +295,11 @@ static void macro_condense(SystemImpl& S, Level& F, Level& C_, const MacroHost& 
 // ------------------------------------------------------------------ patches
 // Patch block R_j A R_j^T, read from the operator's FP64 values; C = float2
 // rounds every entry to complex64 (the mixed path factors in FP32).
+// The patch of CTA b is j0 + b, or order[j0 + b] when an order is given.
 template <class C>
 __global__ void k_patch_gather(ECSRDev A, const int64_t* ptr, const int32_t* dofs, const int64_t* vptr, C* out,
-                               int64_t j0) {
-  const int64_t j = j0 + blockIdx.x;
+                               int64_t j0, const int64_t* order = nullptr) {
+  const int64_t j = order ? order[j0 + blockIdx.x] : j0 + blockIdx.x;
   const int64_t b = ptr[j];
   const int n = (int)(ptr[j + 1] - b);
   const int ld = (int)patch_ld(n);
@@ -549,6 +552,112 @@ static void invert_patches(Alloc& A, PatchDev& D, const LevelPlan& lp, C* vals, 
 }
 
 
+// Windows of the recompute mode (see PatchDev): consecutive patches of the
+// largest-first order whose n x ld blocks fit wcap entries: a quarter of the
+// level's blocks, at most 256 MiB of complex64, at least the largest block.
+static void setup_recompute(Alloc& A, PatchDev& D, const LevelPlan& lp, int64_t offU, const ECSRDev& Aop,
+                            int* dinfo, cudaStream_t st) {
+  const Patches& P = lp.P;
+  const int64_t one = D.max_n * patch_ld(D.max_n);
+  D.wcap = std::max<int64_t>(one, std::min<int64_t>((D.nvals + 3) / 4, (int64_t)32 << 20));
+  std::vector<int64_t> wvptr(D.np), wsoff(D.np);
+  std::vector<int2> ch;
+  D.wq.clear();
+  D.wch.clear();
+  for (int64_t q = 0, acc = 0; q < D.np; ++q) {
+    const int64_t j = lp.order[q];
+    const int64_t nj = P.ptr[j + 1] - P.ptr[j];
+    const int64_t sz = nj * patch_ld(nj);
+    if (q == 0 || acc + sz > D.wcap) {
+      D.wq.push_back(q);
+      D.wch.push_back((int64_t)ch.size());
+      acc = 0;
+    }
+    wvptr[j] = acc;
+    wsoff[q] = acc;   // the n x n scratch copy fits in the n x ld block's extent
+    acc += sz;
+    for (int64_t a0 = 0; a0 < nj; a0 += 64) ch.push_back(make_int2((int)j, (int)a0));
+  }
+  D.wq.push_back(D.np);
+  D.wch.push_back((int64_t)ch.size());
+  D.worder = upload(A, lp.order, st);
+  D.wvptr = upload(A, wvptr, st);
+  D.wsoff = upload(A, wsoff, st);
+  D.wchunks = upload(A, ch, st);
+  D.wbuf = A.arr<float2>((size_t)D.wcap);
+  D.wscratch = A.arr<float2>((size_t)D.wcap);
+  D.winfo = A.arr<int>(1);
+  DPG_CUDA(cudaMemsetAsync(D.winfo, 0, sizeof(int), st));
+  D.recompute = true;
+  const size_t sm = (size_t)(NB * NB + 2 * TL * NB) * sizeof(float2) + 64;
+  DPG_CUDA(cudaFuncSetAttribute(k_patch_invert<float2, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+  // one pass over every block now, so that a non-HPD block fails the setup
+  for (size_t w = 0; w + 1 < D.wq.size(); ++w) {
+    const int64_t q0 = D.wq[w], q1 = D.wq[w + 1];
+    k_patch_gather<float2><<<(unsigned)(q1 - q0), 256, 0, st>>>(Aop, D.ptr, D.dofs, D.wvptr, D.wbuf, q0, D.worder);
+    DPG_CHECK_LAUNCH();
+    k_patch_invert<float2, false><<<(unsigned)(q1 - q0), CTA_THREADS, sm, st>>>(
+        D.ptr, D.dofs, D.wvptr, D.wbuf, D.wscratch, D.wsoff, D.worder, q0, offU, dinfo);
+    DPG_CHECK_LAUNCH();
+  }
+}
+
+void patch_recompute_apply(const Level& L, const float2* r, float2* pbuf, cudaStream_t st) {
+  const PatchDev& D = L.P;
+  const size_t smi = (size_t)(NB * NB + 2 * TL * NB) * sizeof(float2) + 64;
+  const size_t sma = (size_t)D.max_n * sizeof(float2) + 16;
+  for (size_t w = 0; w + 1 < D.wq.size(); ++w) {
+    const int64_t q0 = D.wq[w], q1 = D.wq[w + 1];
+    k_patch_gather<float2><<<(unsigned)(q1 - q0), 256, 0, st>>>(L.A, D.ptr, D.dofs, D.wvptr, D.wbuf, q0, D.worder);
+    DPG_CHECK_LAUNCH();
+    k_patch_invert<float2, false><<<(unsigned)(q1 - q0), CTA_THREADS, smi, st>>>(
+        D.ptr, D.dofs, D.wvptr, D.wbuf, D.wscratch, D.wsoff, D.worder, q0, L.mesh.offU, D.winfo);
+    DPG_CHECK_LAUNCH();
+    const int64_t c0 = D.wch[w], c1 = D.wch[w + 1];
+    k_patch_apply<float2, float2, 2><<<(unsigned)(c1 - c0), 256, sma, st>>>(D.ptr, D.dofs, D.wvptr, D.wchunks + c0,
+                                                                            D.wbuf, r, pbuf);
+    DPG_CHECK_LAUNCH();
+  }
+}
+
+// The same for K vectors (r and pbuf at strides ldr and ldp): every window is
+// gathered and factored once for all K.
+void patch_recompute_apply_blk(const Level& L, const float2* r, int64_t ldr, float2* pbuf, int64_t ldp, int K,
+                               cudaStream_t st) {
+  const PatchDev& D = L.P;
+  const size_t smi = (size_t)(NB * NB + 2 * TL * NB) * sizeof(float2) + 64;
+  static std::once_flag once;
+  std::call_once(once, []() {
+    const int mx = 200 * 1024;
+    DPG_CUDA(cudaFuncSetAttribute(k_patch_apply_blk<float2, float2, 2, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
+    DPG_CUDA(cudaFuncSetAttribute(k_patch_apply_blk<float2, float2, 2, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
+    DPG_CUDA(cudaFuncSetAttribute(k_patch_apply_blk<float2, float2, 2, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
+    DPG_CUDA(cudaFuncSetAttribute(k_patch_apply_blk<float2, float2, 2, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
+  });
+  for (size_t w = 0; w + 1 < D.wq.size(); ++w) {
+    const int64_t q0 = D.wq[w], q1 = D.wq[w + 1];
+    k_patch_gather<float2><<<(unsigned)(q1 - q0), 256, 0, st>>>(L.A, D.ptr, D.dofs, D.wvptr, D.wbuf, q0, D.worder);
+    DPG_CHECK_LAUNCH();
+    k_patch_invert<float2, false><<<(unsigned)(q1 - q0), CTA_THREADS, smi, st>>>(
+        D.ptr, D.dofs, D.wvptr, D.wbuf, D.wscratch, D.wsoff, D.worder, q0, L.mesh.offU, D.winfo);
+    DPG_CHECK_LAUNCH();
+    const int64_t c0 = D.wch[w], c1 = D.wch[w + 1];
+    for (int g = 0; g < K; g += BLK_MAX) {
+      const int kb = std::min(BLK_MAX, K - g);
+      const size_t sm = (size_t)kb * D.max_n * sizeof(float2) + 16;
+#define DPG_RC_BLK(KB)                                                                                     \
+  k_patch_apply_blk<float2, float2, 2, KB><<<(unsigned)(c1 - c0), 256, sm, st>>>(                          \
+      D.ptr, D.dofs, D.wvptr, D.wchunks + c0, D.wbuf, r + (int64_t)g * ldr, ldr, pbuf + (int64_t)g * ldp, ldp)
+      if (kb == 4) DPG_RC_BLK(4);
+      else if (kb == 3) DPG_RC_BLK(3);
+      else if (kb == 2) DPG_RC_BLK(2);
+      else DPG_RC_BLK(1);
+#undef DPG_RC_BLK
+      DPG_CHECK_LAUNCH();
+    }
+  }
+}
+
 static void setup_patches(SystemImpl& S, Level& F, const LevelPlan& lp, int* dinfo, cudaStream_t st) {
   Alloc& A = S.mem;
   const Patches& P = lp.P;
@@ -567,6 +676,10 @@ static void setup_patches(SystemImpl& S, Level& F, const LevelPlan& lp, int* din
   D.chunks = upload(A, lp.ch32, st);
   D.nchunks64 = (int64_t)lp.ch64.size();
   D.chunks64 = upload(A, lp.ch64, st);
+  if (S.op.flags & DPGMG_FLAG_RECOMPUTE_PATCHES) {
+    setup_recompute(A, D, lp, F.mesh.offU, F.A, dinfo, st);
+    return;
+  }
   if (patches_fp32(S)) {
     // complex64 blocks, Cholesky, triangular inverse and L^-H L^-1 in FP32; the
     // smoother and its damping estimate use exactly these inverses
@@ -850,7 +963,7 @@ void build_hierarchy(SystemImpl& S, cudaStream_t st) {
         k_pack_half<double2, float2><<<(unsigned)Pd.np, 256, 0, st>>>(Pd.ptr, Pd.val_ptr, Pd.hptr, Pd.inv64, Pd.h32);
         DPG_CHECK_LAUNCH();
         Pd.half = true;
-      } else if (!Pd.inv32) {
+      } else if (!Pd.inv32 && Pd.inv64) {
         Pd.inv32 = to_c64(A, Pd.inv64, Pd.nvals, st);
       }
       if (Pd.inv64) A.release(Pd.inv64);   // the mixed V-cycle only reads the complex64 copy (stream-ordered free)

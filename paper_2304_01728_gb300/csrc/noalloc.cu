@@ -75,6 +75,10 @@ extern "C" int dpgmg_smooth_noalloc(dpgmg_handle h, dpgmg_system sys, int level,
     return DPGMG_ERR_ARG;
   }
   const Level& L = S.levels[level];
+  if (L.P.recompute) {
+    set_last_error("dpgmg_smooth_noalloc: the system recomputes its patches (no stored inverses)");
+    return DPGMG_ERR_ARG;
+  }
   if (L.P.scratch_entries() > NOALLOC_MAX_SLOTS) {
     set_last_error("dpgmg_smooth_noalloc: level needs " + std::to_string(L.P.scratch_entries()) +
                    " scratch entries, above the fixed scratch of " + std::to_string(NOALLOC_MAX_SLOTS));

@@ -764,7 +764,12 @@ static void smooth(const Level& L, const C* r, C* y, double theta, int accumulat
     return;
   }
   int pe = prof_begin(prof, st);
-  patch_product<C>(P, Prec<C>::inv(P), r, pbuf, st);
+  if constexpr (std::is_same<C, float2>::value) {
+    if (P.recompute) patch_recompute_apply(L, r, pbuf, st);
+    else patch_product<C>(P, Prec<C>::inv(P), r, pbuf, st);
+  } else {
+    patch_product<C>(P, Prec<C>::inv(P), r, pbuf, st);
+  }
   prof_end(prof, pe, st);
   k_slot_sum<C, C><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(P.slot_ptr, P.slots, pbuf, y, n, theta, accumulate);
   DPG_CHECK_LAUNCH();
@@ -1232,6 +1237,16 @@ static void configure_block_kernels() {
     DPG_BLK_ATTR(double2, 1, 1); DPG_BLK_ATTR(double2, 1, 2); DPG_BLK_ATTR(double2, 1, 3);
     DPG_BLK_ATTR(double2, 1, 4);
 #undef DPG_BLK_ATTR
+#define DPG_BLK_ATTR2(K, C, KB) DPG_CUDA(cudaFuncSetAttribute(K<C, KB>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx))
+    DPG_BLK_ATTR2(k_condense_apply_blk, float2, 1); DPG_BLK_ATTR2(k_condense_apply_blk, float2, 2);
+    DPG_BLK_ATTR2(k_condense_apply_blk, float2, 3); DPG_BLK_ATTR2(k_condense_apply_blk, float2, 4);
+    DPG_BLK_ATTR2(k_condense_apply_blk, double2, 1); DPG_BLK_ATTR2(k_condense_apply_blk, double2, 2);
+    DPG_BLK_ATTR2(k_condense_apply_blk, double2, 3); DPG_BLK_ATTR2(k_condense_apply_blk, double2, 4);
+    DPG_BLK_ATTR2(k_backsub_blk, float2, 1); DPG_BLK_ATTR2(k_backsub_blk, float2, 2);
+    DPG_BLK_ATTR2(k_backsub_blk, float2, 3); DPG_BLK_ATTR2(k_backsub_blk, float2, 4);
+    DPG_BLK_ATTR2(k_backsub_blk, double2, 1); DPG_BLK_ATTR2(k_backsub_blk, double2, 2);
+    DPG_BLK_ATTR2(k_backsub_blk, double2, 3); DPG_BLK_ATTR2(k_backsub_blk, double2, 4);
+#undef DPG_BLK_ATTR2
   });
 }
 
@@ -1243,6 +1258,16 @@ static void smooth_blk(const Level& L, const C* r, C* y, double theta, int accum
   const int64_t n = L.mesh.ndof, ldp = std::max<int64_t>(P.scratch_entries(), 1);
   const C* inv = Prec<C>::inv(P);
   const int64_t cap = std::min<int64_t>(BLK_MAX, (BLK_SMEM - 16) / ((int64_t)P.max_n * sizeof(C) + 1));
+  if constexpr (std::is_same<C, float2>::value) {
+    if (P.recompute && cap == BLK_MAX) {
+      configure_block_kernels();
+      patch_recompute_apply_blk(L, r, n, pbuf, ldp, K, st);
+      k_slot_sum_blk<C><<<dim3(nblk(n), (unsigned)K), 256, 0, st>>>(P.slot_ptr, P.slots, pbuf, ldp, y, n, n, theta,
+                                                                     accumulate);
+      DPG_CHECK_LAUNCH();
+      return;
+    }
+  }
   if (!inv || cap < 1) {
     for (int k = 0; k < K; ++k) smooth<C>(L, r + k * n, y + k * n, theta, accumulate, pbuf + k * ldp, st);
     return;
@@ -1258,10 +1283,9 @@ static void smooth_blk(const Level& L, const C* r, C* y, double theta, int accum
     else if (kb == 2) patch_apply_blk_launch<C, 2>(P, per, inv, rg, n, pg, ldp, st);
     else patch_apply_blk_launch<C, 1>(P, per, inv, rg, n, pg, ldp, st);
   }
-  for (int k = 0; k < K; ++k) {
-    k_slot_sum<C, C><<<nblk(n), 256, 0, st>>>(P.slot_ptr, P.slots, pbuf + k * ldp, y + k * n, n, theta, accumulate);
-    DPG_CHECK_LAUNCH();
-  }
+  k_slot_sum_blk<C><<<dim3(nblk(n), (unsigned)K), 256, 0, st>>>(P.slot_ptr, P.slots, pbuf, ldp, y, n, n, theta,
+                                                                 accumulate);
+  DPG_CHECK_LAUNCH();
 }
 
 template <class C>
@@ -1285,19 +1309,87 @@ static void spmv_blk(const ECSRDev& A, const C* vals, const C* x, const C* b, C*
   }
 }
 
+// vectors per launch of a block kernel whose shared memory holds `per_vec`
+// values of C per vector (0: not even one vector fits)
+template <class C> static int blk_group(int64_t per_vec) {
+  return (int)std::min<int64_t>(BLK_MAX, (BLK_SMEM - 16) / (per_vec * (int64_t)sizeof(C) + 1));
+}
+
+// rs_k = r_k with the macro-interior residual condensed (h levels), k < K
+template <class C>
+static void condense_blk(const Level& F, const C* r, C* rs, C* cbuf, int K, cudaStream_t st) {
+  const int64_t n = F.mesh.ndof, ldc = (int64_t)F.nK * F.nS;
+  const int cap = blk_group<C>(F.nI);
+  if (cap < 1) {
+    for (int k = 0; k < K; ++k) condense<C>(F, r + k * n, rs + k * n, cbuf, st);
+    return;
+  }
+  configure_block_kernels();
+  for (int g = 0; g < K; g += cap) {
+    const int kb = std::min(cap, K - g);
+    const size_t sm = (size_t)kb * F.nI * sizeof(C) + 16;
+#define DPG_COND_BLK(KB)                                                                                   \
+  k_condense_apply_blk<C, KB><<<(unsigned)F.nK, 256, sm, st>>>(F.nS, F.nI, F.I_glob, Prec<C>::Y(F), r + g * n, n, \
+                                                               cbuf + g * ldc, ldc)
+    if (kb == 4) DPG_COND_BLK(4);
+    else if (kb == 3) DPG_COND_BLK(3);
+    else if (kb == 2) DPG_COND_BLK(2);
+    else DPG_COND_BLK(1);
+#undef DPG_COND_BLK
+    DPG_CHECK_LAUNCH();
+  }
+  for (int k = 0; k < K; ++k) {
+    k_condense_sum<C><<<nblk(n), 256, 0, st>>>(F.sslot_ptr, F.sslots, cbuf + k * ldc, F.smask, r + k * n, rs + k * n,
+                                               n);
+    DPG_CHECK_LAUNCH();
+  }
+}
+
+template <class C>
+static void backsub_blk(const Level& F, const C* r, C* x, int K, cudaStream_t st) {
+  const int64_t n = F.mesh.ndof;
+  const int cap = blk_group<C>((int64_t)F.nI + F.nS);
+  if (cap < 1) {
+    for (int k = 0; k < K; ++k) backsub<C>(F, r + k * n, x + k * n, st);
+    return;
+  }
+  configure_block_kernels();
+  for (int g = 0; g < K; g += cap) {
+    const int kb = std::min(cap, K - g);
+    const size_t sm = (size_t)kb * (F.nI + F.nS) * sizeof(C) + 16;
+#define DPG_BACK_BLK(KB)                                                                                       \
+  k_backsub_blk<C, KB><<<(unsigned)F.nK, 256, sm, st>>>(F.nS, F.nI, F.S_glob, F.I_glob, Prec<C>::Ai(F), Prec<C>::Y(F), \
+                                                        r + g * n, x + g * n, n)
+    if (kb == 4) DPG_BACK_BLK(4);
+    else if (kb == 3) DPG_BACK_BLK(3);
+    else if (kb == 2) DPG_BACK_BLK(2);
+    else DPG_BACK_BLK(1);
+#undef DPG_BACK_BLK
+    DPG_CHECK_LAUNCH();
+  }
+}
+
+template <class C> static void coarse_solve_blk(const Level& C0, const C* r, C* e, C* tmp, int K, cudaStream_t st);
+template <>
+void coarse_solve_blk<double2>(const Level& C0, const double2* r, double2* e, double2* tmp, int K, cudaStream_t st) {
+  coarse_apply64_blk(C0, r, e, tmp, K, st);
+}
+template <>
+void coarse_solve_blk<float2>(const Level& C0, const float2* r, float2* e, float2* tmp, int K, cudaStream_t st) {
+  coarse_apply32_blk(C0, r, e, tmp, K, st);
+}
+
 template <class C>
 static void vcycle_blk(SystemImpl& S, WS& W, std::vector<BlockLevel<C>>& V, int l, const C* r, C* x, int K,
                        cudaStream_t st) {
   const Level& F = S.levels[l];
   const int64_t n = F.mesh.ndof;
   if (l == 0) {
-    for (int k = 0; k < K; ++k) {
-      if (F.has_coarse) coarse_solve<C>(S, W, r + k * n, x + k * n, st);
-      else if (F.P.np > 0) smooth<C>(F, r + k * n, x + k * n, F.theta, 0, V[0].pbuf, st);
-      else {
-        k_zero<C><<<nblk(n), 256, 0, st>>>(x + k * n, n);
-        DPG_CHECK_LAUNCH();
-      }
+    if (F.has_coarse) coarse_solve_blk<C>(F, r, x, V[0].t, K, st);
+    else if (F.P.np > 0) smooth_blk<C>(F, r, x, F.theta, 0, V[0].pbuf, K, st);
+    else {
+      k_zero<C><<<nblk(n * K), 256, 0, st>>>(x, n * K);
+      DPG_CHECK_LAUNCH();
     }
     return;
   }
@@ -1306,7 +1398,7 @@ static void vcycle_blk(SystemImpl& S, WS& W, std::vector<BlockLevel<C>>& V, int 
   const C* Avals = Prec<C>::A(F.A);
   const C* rs = r;
   if (F.kind == 2) {
-    for (int k = 0; k < K; ++k) condense<C>(F, r + k * n, V[l].rs + k * n, V[l].cbuf, st);
+    condense_blk<C>(F, r, V[l].rs, V[l].cbuf, K, st);
     rs = V[l].rs;
   }
   for (int q = 0; q < S.op.nu_pre; ++q) {
@@ -1329,8 +1421,7 @@ static void vcycle_blk(SystemImpl& S, WS& W, std::vector<BlockLevel<C>>& V, int 
     spmv_blk<C>(F.A, Avals, x, rs, V[l].t, 1, K, st);
     smooth_blk<C>(F, V[l].t, x, F.theta, 1, V[l].pbuf, K, st);
   }
-  if (F.kind == 2)
-    for (int k = 0; k < K; ++k) backsub<C>(F, r + k * n, x + k * n, st);
+  if (F.kind == 2) backsub_blk<C>(F, r, x, K, st);
 }
 
 template <class C>
@@ -1344,7 +1435,7 @@ static std::vector<BlockLevel<C>> alloc_block_levels(Alloc& M, const SystemImpl&
     v[l].x = M.arr<C>(n);
     v[l].t = M.arr<C>(n);
     if (l >= 1 || L.P.np > 0) v[l].pbuf = M.arr<C>((size_t)std::max<int64_t>(L.P.scratch_entries(), 1) * K);
-    if (L.kind == 2) v[l].cbuf = M.arr<C>((size_t)L.nK * L.nS);
+    if (L.kind == 2) v[l].cbuf = M.arr<C>((size_t)L.nK * L.nS * K);
   }
   return v;
 }
@@ -1556,8 +1647,9 @@ void prepare_solve(SystemImpl& S, cudaStream_t st) {
   Evict ev;
   {
     const PatchDev& P = S.levels[L].P;
-    const void* buf = mixed && P.inv32 ? (const void*)P.inv32 : (const void*)P.inv64;
-    const int64_t bytes = std::min<int64_t>(P.nvals * (mixed && P.inv32 ? 8 : 16), (int64_t)256 << 20);
+    const void* buf = mixed && P.inv32 ? (const void*)P.inv32 : (P.inv64 ? (const void*)P.inv64 : (const void*)P.wbuf);
+    const int64_t bytes = std::min<int64_t>(P.inv32 || P.inv64 ? P.nvals * (mixed && P.inv32 ? 8 : 16) : P.wcap * 8,
+                                            (int64_t)256 << 20);
     if (L >= 1 && buf && bytes >= 16) {
       ev.buf = reinterpret_cast<const float4*>(buf);
       ev.n = bytes / 16;

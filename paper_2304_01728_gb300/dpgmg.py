@@ -22,7 +22,7 @@ SRC_GAUSSIAN, SRC_PLANE_WAVE, SRC_MANUFACTURED = 0, 1, 2
 PREC_FP64, PREC_MIXED = 0, 1
 COARSEST_CHOLESKY, COARSEST_NONE, COARSEST_AUTO, COARSEST_SMOOTH = 0, 1, 2, 3
 FLAG_EAGER, FLAG_CUDA_CORES, FLAG_STORE_COARSE, FLAG_WARM_START, FLAG_CG_C128 = 1, 2, 4, 8, 16
-FLAG_PATCH_FP64, FLAG_PATCH_R2 = 32, 64
+FLAG_PATCH_FP64, FLAG_PATCH_R2, FLAG_RECOMPUTE_PATCHES = 32, 64, 128
 FLAG_FAULT_NOT_HPD, FLAG_FAULT_TC_WAIT = 1 << 28, 1 << 29
 OP_A, OP_SMOOTH, OP_VCYCLE, OP_RESTRICT, OP_PROLONG, OP_CONDENSE, OP_COARSE, OP_AFULL = range(8)
 

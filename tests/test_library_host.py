@@ -54,6 +54,15 @@ def test_query_sizes_without_device(libpath):
     assert nt2 == nt and nb2 < nb
     with pytest.raises(dpgmg.DpgmgError):
         dpgmg.dpgmg_query_sizes(pb, dpgmg.make_opts(**dict(w["opts"], flags=1 << 20)))
+    # recomputed patches: no stored inverses in the estimate; mixed FP32 factors only
+    _, _, nb3 = dpgmg.dpgmg_query_sizes(pb, dpgmg.make_opts(**dict(w["opts"], flags=dpgmg.FLAG_RECOMPUTE_PATCHES)))
+    assert nb3 < nb
+    for bad in [dict(precision="fp64"), dict(flags=dpgmg.FLAG_RECOMPUTE_PATCHES | dpgmg.FLAG_PATCH_FP64),
+                dict(flags=dpgmg.FLAG_RECOMPUTE_PATCHES | dpgmg.FLAG_CG_C128)]:
+        o = dict(w["opts"], flags=dpgmg.FLAG_RECOMPUTE_PATCHES)
+        o.update(bad)
+        with pytest.raises(dpgmg.DpgmgError):
+            dpgmg.dpgmg_query_sizes(pb, dpgmg.make_opts(**o))
     pb.dp = 2
     with pytest.raises(dpgmg.DpgmgError):
         dpgmg.dpgmg_query_sizes(pb, dpgmg.make_opts(**w["opts"]))
