@@ -20,6 +20,25 @@ constexpr int BLK_MAX = 4;   // vectors per launch of a block kernel
 // item (patch j, first column a0; PER columns per lane, warps split the rows
 // k = w, w + 8, ...), for kb < KB.  r_kb = r + kb * ldr.  Shared memory:
 // KB * n_j values of the gathered right-hand sides.
+// 16-byte asynchronous global -> shared copies (cp.async, L2 only); each thread
+// later reads back only what it copied itself, after waiting on its own groups.
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N> __device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+constexpr int BLK_DEPTH = 8;   // rows in flight per thread in the block smoother
+
+// pbuf[kb * ldp + slot] = A_jj^-1 (R_j r_kb) for the patch columns of one work
+// item (patch j, first column a0; PER columns per lane, warps split the rows
+// k = w, w + 8, ...), for kb < KB.  r_kb = r + kb * ldr.  Shared memory:
+// KB * n_j values of the gathered right-hand sides (dynamic) and, for the
+// complex64 form, a ring of BLK_DEPTH 16-byte row pieces per thread that
+// cp.async fills, so that the rows in flight do not hold registers.
 template <class C, class TIN, int PER, int KB>
 __global__ void __launch_bounds__(256) k_patch_apply_blk(const int64_t* __restrict__ ptr,
                                                          const int32_t* __restrict__ dofs,
@@ -29,6 +48,7 @@ __global__ void __launch_bounds__(256) k_patch_apply_blk(const int64_t* __restri
                                                          C* __restrict__ pbuf, int64_t ldp) {
   extern __shared__ unsigned char shraw[];
   __shared__ C part[8][32 * PER + 1];
+  __shared__ float4 ring[PER == 2 ? BLK_DEPTH : 1][PER == 2 ? 256 : 1];
   C* rj = reinterpret_cast<C*>(shraw);   // [KB][n]
   using O = Ops<C>;
   const int2 ch = chunks[blockIdx.x];
@@ -36,49 +56,54 @@ __global__ void __launch_bounds__(256) k_patch_apply_blk(const int64_t* __restri
   const int64_t b = ptr[j];
   const int n = (int)(ptr[j + 1] - b);
   const int64_t ld = patch_ld(n);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int a = ch.y + PER * lane;
+  const C* M = inv + vptr[j] + a;
+  if (PER == 2 && a < n) {
+    // start the first BLK_DEPTH rows of this thread (k = w + 8 d) before the gather
+    const float4* M4 = reinterpret_cast<const float4*>(M);
+    const int64_t s4 = ld / 2;
+#pragma unroll
+    for (int d = 0; d < BLK_DEPTH; ++d) {
+      const int k = w + 8 * d;
+      if (k < n) cp_async16(&ring[d][threadIdx.x], M4 + (int64_t)k * s4);
+      cp_async_commit();
+    }
+  }
   for (int q = threadIdx.x; q < n; q += blockDim.x) {
     const int32_t g = dofs[b + q];
 #pragma unroll
     for (int kb = 0; kb < KB; ++kb) rj[kb * n + q] = cvt_in<C>(r[kb * ldr + g]);
   }
   __syncthreads();
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  const int a = ch.y + PER * lane;
   C acc[KB][PER];
 #pragma unroll
   for (int kb = 0; kb < KB; ++kb)
 #pragma unroll
     for (int u = 0; u < PER; ++u) acc[kb][u] = O::zero();
   if (a < n) {
-    const C* M = inv + vptr[j] + a;
-    int k = w;
     if (PER == 2) {
-      // 16-byte loads of (M[k][a], M[k][a+1]): a and ld are even; four rows
-      // in flight per lane
       const float4* M4 = reinterpret_cast<const float4*>(M);
       const int64_t s4 = ld / 2;
-      for (; k + 24 < n; k += 32) {
-        float4 m[4];
-#pragma unroll
-        for (int u = 0; u < 4; ++u) m[u] = __ldcs(M4 + (int64_t)(k + 8 * u) * s4);
-#pragma unroll
-        for (int u = 0; u < 4; ++u)
-#pragma unroll
-          for (int kb = 0; kb < KB; ++kb) {
-            const C rv = rj[kb * n + k + 8 * u];
-            acc[kb][0] = O::fmac(rv, Ops<C>::mk(m[u].x, m[u].y), acc[kb][0]);
-            acc[kb][1 % PER] = O::fmac(rv, Ops<C>::mk(m[u].z, m[u].w), acc[kb][1 % PER]);
-          }
-      }
-      for (; k < n; k += 8) {
-        const float4 m0 = __ldcs(M4 + (int64_t)k * s4);
+      int d = 0;
+      for (int k = w; k < n; k += 8) {
+        cp_async_wait<BLK_DEPTH - 1>();   // this thread's oldest group (row k) has landed
+        const float4 m0 = ring[d][threadIdx.x];
 #pragma unroll
         for (int kb = 0; kb < KB; ++kb) {
-          acc[kb][0] = O::fmac(rj[kb * n + k], Ops<C>::mk(m0.x, m0.y), acc[kb][0]);
-          acc[kb][1 % PER] = O::fmac(rj[kb * n + k], Ops<C>::mk(m0.z, m0.w), acc[kb][1 % PER]);
+          const C rv = rj[kb * n + k];
+          acc[kb][0] = O::fmac(rv, Ops<C>::mk(m0.x, m0.y), acc[kb][0]);
+          acc[kb][1 % PER] = O::fmac(rv, Ops<C>::mk(m0.z, m0.w), acc[kb][1 % PER]);
         }
+        // refill the slot with row k + 8 BLK_DEPTH (m0 has been consumed above)
+        const int kn = k + 8 * BLK_DEPTH;
+        if (kn < n) cp_async16(&ring[d][threadIdx.x], M4 + (int64_t)kn * s4);
+        cp_async_commit();
+        d = d + 1 == BLK_DEPTH ? 0 : d + 1;
       }
+      cp_async_wait<0>();
     } else {
+      int k = w;
       for (; k + 24 < n; k += 32) {
         C m[4];
 #pragma unroll

@@ -628,7 +628,7 @@ void patch_recompute_apply_blk(const Level& L, const float2* r, int64_t ldr, flo
   const size_t smi = (size_t)(NB * NB + 2 * TL * NB) * sizeof(float2) + 64;
   static std::once_flag once;
   std::call_once(once, []() {
-    const int mx = 200 * 1024;
+    const int mx = 160 * 1024;   // + the kernel's static shared memory (37 KiB) stays within 227 KiB
     DPG_CUDA(cudaFuncSetAttribute(k_patch_apply_blk<float2, float2, 2, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
     DPG_CUDA(cudaFuncSetAttribute(k_patch_apply_blk<float2, float2, 2, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
     DPG_CUDA(cudaFuncSetAttribute(k_patch_apply_blk<float2, float2, 2, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));

@@ -12,6 +12,7 @@
 #include <algorithm>
 #include <initializer_list>
 #include <map>
+#include <memory>
 #include <mutex>
 #include <tuple>
 #include <type_traits>
@@ -1010,6 +1011,88 @@ __global__ void k_cg_dir(double2* __restrict__ p, const TZ* __restrict__ z, cons
   }
 }
 
+// Block forms of the fused CG kernels for K columns (blockIdx.y = column k;
+// vectors at stride n; column k's scalars at sc + k SC_COUNT, its partials at
+// part + k RED_BLOCKS and its ticket at ticket[k]).  Columns whose bit in
+// `active` is clear return at once (all their blocks alike).
+template <class TU>
+__global__ void k_dot_fused_blk(const TU* __restrict__ u, const double2* __restrict__ v, int64_t n,
+                                double2* __restrict__ part, double2* sc, int which, unsigned* ticket,
+                                unsigned long long active) {
+  const int k = blockIdx.y;
+  if (!((active >> k) & 1ull)) return;
+  u += (int64_t)k * n;
+  v += (int64_t)k * n;
+  part += (int64_t)k * RED_BLOCKS;
+  sc += (int64_t)k * SC_COUNT;
+  __shared__ double2 sh[8];
+  double2 acc = make_double2(0, 0);
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    acc = Ops<double2>::fmac(v[i], to_c128(u[i]), acc);
+  acc = warp_sum(acc);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double2 s = make_double2(0, 0);
+    for (int q = 0; q < (int)(blockDim.x >> 5); ++q) s = Ops<double2>::add(s, sh[q]);
+    part[blockIdx.x] = s;
+  }
+  if (!last_block(ticket + k)) return;
+  block_finish(part, gridDim.x, sc, which);
+  if (threadIdx.x == 0) ticket[k] = 0u;
+}
+
+__global__ void k_cg_update_fused_blk(double2* __restrict__ x, double2* __restrict__ r, const double2* __restrict__ p,
+                                      const double2* __restrict__ q, double2* sc, int64_t n, double2* __restrict__ part,
+                                      unsigned* ticket, unsigned long long active) {
+  const int k = blockIdx.y;
+  if (!((active >> k) & 1ull)) return;
+  const int64_t o = (int64_t)k * n;
+  x += o;
+  r += o;
+  p += o;
+  q += o;
+  sc += (int64_t)k * SC_COUNT;
+  part += (int64_t)k * RED_BLOCKS;
+  __shared__ double2 sh[8];
+  const double2 al = sc[SC_ALPHA];
+  double acc = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    double2 pi = p[i], qi = q[i], xi = x[i], ri = r[i];
+    xi.x += al.x * pi.x - al.y * pi.y;
+    xi.y += al.x * pi.y + al.y * pi.x;
+    ri.x -= al.x * qi.x - al.y * qi.y;
+    ri.y -= al.x * qi.y + al.y * qi.x;
+    x[i] = xi;
+    r[i] = ri;
+    acc += ri.x * ri.x + ri.y * ri.y;
+  }
+  double2 a2 = warp_sum(make_double2(acc, 0.0));
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = a2;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double2 s = make_double2(0, 0);
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s = Ops<double2>::add(s, sh[w]);
+    part[blockIdx.x] = s;
+  }
+  if (!last_block(ticket + k)) return;
+  block_finish(part, gridDim.x, sc, 1);
+  if (threadIdx.x == 0) ticket[k] = 0u;
+}
+
+__global__ void k_cg_dir_blk(double2* __restrict__ p, const double2* __restrict__ z, const double2* __restrict__ sc,
+                             int64_t n, unsigned long long active) {
+  const int k = blockIdx.y;
+  if (!((active >> k) & 1ull)) return;
+  p += (int64_t)k * n;
+  z += (int64_t)k * n;
+  const double2 be = sc[(int64_t)k * SC_COUNT + SC_BETA];
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const double2 pi = p[i], zi = z[i];
+    p[i] = make_double2(zi.x + be.x * pi.x - be.y * pi.y, zi.y + be.x * pi.y + be.y * pi.x);
+  }
+}
+
 // ------------------------------------------------------------ workspace
 template <class C> struct LevelWS {
   C *r = nullptr, *rs = nullptr, *x = nullptr, *t = nullptr, *pbuf = nullptr, *cbuf = nullptr;
@@ -1225,7 +1308,7 @@ static void patch_apply_blk_launch(const PatchDev& P, int per, const C* inv, con
 
 // dynamic shared memory of the block products: the gathered right-hand sides
 // of one group (vectors x patch size), up to BLK_SMEM bytes
-constexpr int BLK_SMEM = 200 * 1024;
+constexpr int BLK_SMEM = 160 * 1024;   // + up to 37 KiB of static shared memory (the smoother ring)
 static void configure_block_kernels() {
   static std::once_flag once;
   std::call_once(once, []() {
@@ -1288,16 +1371,19 @@ static void smooth_blk(const Level& L, const C* r, C* y, double theta, int accum
   DPG_CHECK_LAUNCH();
 }
 
+// One row per warp (the entity-grouped form measured slower: fewer loads in
+// flight at its register count).
 template <class C>
-static void spmv_blk(const ECSRDev& A, const C* vals, const C* x, const C* b, C* y, int mode, int K, cudaStream_t st) {
+static void spmv_blk(const ECSRDev& A, const C* vals, const C* x, const C* b, C* y, int mode, int K,
+                     cudaStream_t st) {
   const int64_t n = A.nrows;
-  const unsigned blocks = (unsigned)std::min<int64_t>((A.nrows + 7) / 8, 152 * 16);
   for (int g = 0; g < K; g += BLK_MAX) {
     const int kb = std::min(BLK_MAX, K - g);
     const C* xg = x + g * n;
     const C* bg = b ? b + g * n : nullptr;
     C* yg = y + g * n;
-#define DPG_SPMV_BLK(KB)                                                                                          \
+    const unsigned blocks = (unsigned)std::min<int64_t>((A.nrows + 7) / 8, 152 * 16);
+#define DPG_SPMV_BLK(KB)                                                                                            \
   k_spmv_blk<C, KB><<<blocks, 256, 0, st>>>(A.row_ent, A.ent_start, A.col_ptr, A.col_idx, A.val_ptr, vals, xg, bg, yg, \
                                             n, A.nrows, mode)
     if (kb == 4) DPG_SPMV_BLK(4);
@@ -1827,8 +1913,11 @@ int pcg_solve(SystemImpl& S, cudaStream_t st, double2* xout, dpgmg_stats* stats,
 // K independent MG-PCG iterations (each with its own scalars and stopping
 // test, the recurrence of pcg_solve) that share every V-cycle: z_k = B r_k for
 // all k at once through vcycle_blk.  Right-hand sides B and solutions X are
-// device [K][n].  A right-hand side that has converged keeps its x and r; its
-// V-cycle column is still computed (the matrices are read once for all).
+// device [K][n].  A right-hand side that has converged keeps its x, r and p;
+// its V-cycle and operator columns are still computed (the matrices are read
+// once for all columns).  The steps after the first are replayed from a CUDA
+// graph captured for the current set of active columns (captured again when
+// a column converges).
 int pcg_solve_block(SystemImpl& S, cudaStream_t st, int K, const double2* B, double2* X, dpgmg_stats* stats) {
   ensure_workspace(S, st);
   WS& W = *reinterpret_cast<WS*>(S.ws);
@@ -1844,8 +1933,18 @@ int pcg_solve_block(SystemImpl& S, cudaStream_t st, int K, const double2* B, dou
   double2* Q = M.arr<double2>((size_t)n * K);
   double2* Z = M.arr<double2>((size_t)n * K);
   double2* sc = M.arr<double2>((size_t)SC_COUNT * K);
+  double2* part = M.arr<double2>((size_t)RED_BLOCKS * K);
+  unsigned* ticket = M.arr<unsigned>((size_t)K);
+  double2* sch = nullptr;   // pinned copy of the scalars
+  DPG_CUDA(cudaMallocHost(&sch, (size_t)SC_COUNT * K * sizeof(double2)));
+  struct HostFree {
+    double2* p;
+    ~HostFree() { cudaFreeHost(p); }
+  } hf{sch};
   float2* XH = cg_c128(S) ? nullptr : M.arr<float2>((size_t)n * K);
   float2* XL = cg_c128(S) ? nullptr : M.arr<float2>((size_t)n * K);
+  DPG_CUDA(cudaMemsetAsync(ticket, 0, (size_t)K * sizeof(unsigned), st));
+  DPG_CUDA(cudaMemsetAsync(sc, 0, (size_t)SC_COUNT * K * sizeof(double2), st));
   // Y = A X (mode 0) or B - A X (mode 1) for all K columns with the CG operator,
   // its stored values read once per group of BLK_MAX columns
   auto cg_apply_blk = [&](const double2* Xs, const double2* Bs, double2* Ys, int mode) {
@@ -1855,13 +1954,16 @@ int pcg_solve_block(SystemImpl& S, cudaStream_t st, int K, const double2* B, dou
     }
     k_split_vec<<<nblk(n * K), 256, 0, st>>>(Xs, XH, XL, n * K);
     DPG_CHECK_LAUNCH();
-    const unsigned blocks = (unsigned)std::min<int64_t>((n + 7) / 8, 152 * 16);
     for (int g = 0; g < K; g += BLK_MAX) {
       const int kb = std::min(BLK_MAX, K - g);
       const double2* bg = Bs ? Bs + (size_t)g * n : nullptr;
+      const float2* xh = XH + (size_t)g * n;
+      const float2* xl = XL + (size_t)g * n;
+      double2* yg = Ys + (size_t)g * n;
+      const unsigned blocks = (unsigned)std::min<int64_t>((n + 7) / 8, 152 * 16);
 #define DPG_DF_BLK(KB)                                                                                            \
   k_spmv_df_blk<KB><<<blocks, 256, 0, st>>>(A.row_ent, A.ent_start, A.col_ptr, A.col_idx, A.val_ptr, A.v32, A.vlo, \
-                                            XH + (size_t)g * n, XL + (size_t)g * n, bg, Ys + (size_t)g * n, n, n, mode)
+                                            xh, xl, bg, yg, n, n, mode)
       if (kb == 4) DPG_DF_BLK(4);
       else if (kb == 3) DPG_DF_BLK(3);
       else if (kb == 2) DPG_DF_BLK(2);
@@ -1874,12 +1976,6 @@ int pcg_solve_block(SystemImpl& S, cudaStream_t st, int K, const double2* B, dou
   std::vector<BlockLevel<double2>> V64;
   if (mixed) V32 = alloc_block_levels<float2>(M, S, K);
   else V64 = alloc_block_levels<double2>(M, S, K);
-  std::vector<double2> sch((size_t)SC_COUNT * K);
-  auto read_scalars = [&]() {
-    DPG_CUDA(cudaMemcpyAsync(sch.data(), sc, sch.size() * sizeof(double2), cudaMemcpyDeviceToHost, st));
-    DPG_CUDA(cudaStreamSynchronize(st));
-  };
-  auto rhs_of = [&](double2* base, int k) { return base + (size_t)k * n; };
   // z = B r for every column (complex128 result in Z)
   auto precondition_blk = [&]() {
     if (mixed) {
@@ -1892,6 +1988,15 @@ int pcg_solve_block(SystemImpl& S, cudaStream_t st, int K, const double2* B, dou
       vcycle_blk<double2>(S, W, V64, L, R, Z, K, st);
     }
   };
+  const dim3 rgrid(RED_BLOCKS, (unsigned)K);
+  auto dot_blk = [&](const double2* U, const double2* Vv, int which, unsigned long long mask) {
+    k_dot_fused_blk<double2><<<rgrid, 256, 0, st>>>(U, Vv, n, part, sc, which, ticket, mask);
+    DPG_CHECK_LAUNCH();
+  };
+  auto read_scalars = [&]() {
+    DPG_CUDA(cudaMemcpyAsync(sch, sc, (size_t)SC_COUNT * K * sizeof(double2), cudaMemcpyDeviceToHost, st));
+  };
+  const unsigned long long all = K == 64 ? ~0ull : ((1ull << K) - 1ull);
   cudaEvent_t e0, e1;
   DPG_CUDA(cudaEventCreate(&e0));
   DPG_CUDA(cudaEventCreate(&e1));
@@ -1899,61 +2004,67 @@ int pcg_solve_block(SystemImpl& S, cudaStream_t st, int K, const double2* B, dou
   DPG_CUDA(cudaMemcpyAsync(R, B, (size_t)n * K * sizeof(double2), cudaMemcpyDeviceToDevice, st));
   k_zero<double2><<<nblk(n * K), 256, 0, st>>>(X, n * K);
   DPG_CHECK_LAUNCH();
-  // column k's CG scalars: sc[k * SC_COUNT ..]
-  auto sck = [&](int k) { return sc + (size_t)k * SC_COUNT; };
-  auto dotk = [&](const double2* u, const double2* v, int which, int k) {
-    k_dot_fused<double2><<<RED_BLOCKS, 256, 0, st>>>(u, v, n, W.part, sck(k), which, W.ticket);
-    DPG_CHECK_LAUNCH();
-  };
-  DPG_CUDA(cudaMemsetAsync(sc, 0, (size_t)SC_COUNT * K * sizeof(double2), st));
-  for (int k = 0; k < K; ++k) dotk(rhs_of(R, k), rhs_of(R, k), 1, k);
+  dot_blk(R, R, 1, all);   // ||b_k||^2
   read_scalars();
+  DPG_CUDA(cudaStreamSynchronize(st));
   std::vector<double> nb(K), rel(K, 0.0);
-  std::vector<int> iters(K, 0), done(K, 0), status(K, DPGMG_OK);
-  int active = 0;
+  std::vector<int> iters(K, 0), status(K, DPGMG_OK);
+  unsigned long long active = 0;
   for (int k = 0; k < K; ++k) {
     nb[k] = std::sqrt(sch[(size_t)k * SC_COUNT + SC_RR].x);
-    done[k] = !(nb[k] > 0.0);
-    active += !done[k];
+    if (nb[k] > 0.0) active |= 1ull << k;
   }
+  // q = A p, alpha = rho / p^H q, x += alpha p, r -= alpha q, ||r||^2, scalars to the host
+  auto tail = [&](unsigned long long mask) {
+    cg_apply_blk(P, nullptr, Q, 0);
+    dot_blk(P, Q, 0, mask);
+    k_cg_update_fused_blk<<<rgrid, 256, 0, st>>>(X, R, P, Q, sc, n, part, ticket, mask);
+    DPG_CHECK_LAUNCH();
+    read_scalars();
+  };
+  // z = B r, rho_new = z^H r, beta = rho_new / rho, p = z + beta p
+  auto head = [&](unsigned long long mask) {
+    precondition_blk();
+    dot_blk(Z, R, 2, mask);
+    k_cg_dir_blk<<<rgrid, 256, 0, st>>>(P, Z, sc, n, mask);
+    DPG_CHECK_LAUNCH();
+  };
   int it = 0;
   if (active) {
     precondition_blk();
-    for (int k = 0; k < K; ++k) dotk(rhs_of(Z, k), rhs_of(R, k), 3, k);
+    dot_blk(Z, R, 3, active);   // rho = z^H r
     DPG_CUDA(cudaMemcpyAsync(P, Z, (size_t)n * K * sizeof(double2), cudaMemcpyDeviceToDevice, st));
+    tail(active);
+    std::unique_ptr<PcgGraph> G;
+    unsigned long long gmask = 0;
+    const bool graphs = !(S.op.flags & DPGMG_FLAG_EAGER);
     while (true) {
+      DPG_CUDA(cudaStreamSynchronize(st));
       ++it;
-      cg_apply_blk(P, nullptr, Q, 0);
       for (int k = 0; k < K; ++k) {
-        if (done[k]) continue;
-        dotk(rhs_of(P, k), rhs_of(Q, k), 0, k);
-        k_cg_update_fused<<<RED_BLOCKS, 256, 0, st>>>(rhs_of(X, k), rhs_of(R, k), rhs_of(P, k), rhs_of(Q, k), sck(k),
-                                                       n, W.part, W.ticket, nullptr);
-        DPG_CHECK_LAUNCH();
-      }
-      read_scalars();
-      active = 0;
-      for (int k = 0; k < K; ++k) {
-        if (done[k]) continue;
+        if (!((active >> k) & 1ull)) continue;
         const double2* c = &sch[(size_t)k * SC_COUNT];
         iters[k] = it;
         const double pq = c[SC_PQ].x;
         rel[k] = std::sqrt(c[SC_RR].x) / nb[k];
         if (!(pq > 0.0) || !std::isfinite(pq) || !std::isfinite(rel[k])) {
           status[k] = DPGMG_ERR_BREAKDOWN;
-          done[k] = 1;
+          active &= ~(1ull << k);
         } else if (rel[k] <= S.op.tol || it >= S.op.max_iter) {
-          done[k] = 1;
+          active &= ~(1ull << k);
         }
-        active += !done[k];
       }
       if (!active) break;
-      precondition_blk();
-      for (int k = 0; k < K; ++k) {
-        if (done[k]) continue;
-        dotk(rhs_of(Z, k), rhs_of(R, k), 2, k);
-        k_cg_dir<double2><<<RED_BLOCKS, 256, 0, st>>>(rhs_of(P, k), rhs_of(Z, k), sck(k), n, W.xh, W.xl);
-        DPG_CHECK_LAUNCH();
+      if (graphs && (!G || gmask != active)) {
+        G.reset(new PcgGraph());
+        gmask = active;
+      }
+      const unsigned long long mask = active;
+      if (graphs && G->ready(st, [&]() { head(mask); tail(mask); })) {
+        G->launch(st);
+      } else {
+        head(mask);
+        tail(mask);
       }
     }
   }
@@ -1963,11 +2074,12 @@ int pcg_solve_block(SystemImpl& S, cudaStream_t st, int K, const double2* B, dou
   DPG_CUDA(cudaEventElapsedTime(&ms, e0, e1));
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
-  int worst = DPGMG_OK;
   // true residuals ||b - A x|| / ||b|| in FP64
   cg_apply_blk(X, B, Q, 1);
-  for (int k = 0; k < K; ++k) dotk(rhs_of(Q, k), rhs_of(Q, k), 1, k);
+  dot_blk(Q, Q, 1, all);
   read_scalars();
+  DPG_CUDA(cudaStreamSynchronize(st));
+  int worst = DPGMG_OK;
   for (int k = 0; k < K; ++k) {
     if (status[k] == DPGMG_OK && nb[k] > 0.0 && rel[k] > S.op.tol) status[k] = DPGMG_ERR_NOT_CONVERGED;
     const double true_rel = nb[k] > 0.0 ? std::sqrt(sch[(size_t)k * SC_COUNT + SC_RR].x) / nb[k] : 0.0;
@@ -1984,7 +2096,6 @@ int pcg_solve_block(SystemImpl& S, cudaStream_t st, int K, const double2* B, dou
     }
     if (worst == DPGMG_OK && status[k] != DPGMG_OK) worst = status[k];
   }
-  DPG_CUDA(cudaStreamSynchronize(st));
   return worst;
 }
 
