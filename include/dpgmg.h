@@ -383,13 +383,16 @@ long long dpgmg_launch_count(void);
  * 8; the rows of an entity share their column list, so larger G loads each
  * column index and vector entry once for G rows), or (G = 16) by one warp
  * per row with the column indices loaded one step ahead of the gathers they
- * feed.  dpgmg_setup times every variant on each operator and keeps the
- * fastest; choices are cached per (product type, p, level kind, log2 of the
- * row count) for the life of the process.  level >= 1 addresses that level's
- * V-cycle operator, level == -1 the CG operator.  set = 1, 2, 4, 8 or 16
- * overrides the choice (0 leaves it); *group (may be NULL) receives the value
- * in force.  Returns DPGMG_ERR_ARG for an invalid level or size.  Results do
- * not depend on the variant beyond rounding order (G = 1 and 16: bitwise). */
+ * feed, or (G = 32) by one warp per row with the warp's stream of values and
+ * column indices copied 8 steps ahead into shared memory by asynchronous
+ * copies (cp.async).  dpgmg_setup times every variant on each operator and
+ * keeps the fastest; choices are cached per (product type, p, level kind,
+ * log2 of the row count) for the life of the process.  level >= 1 addresses
+ * that level's V-cycle operator, level == -1 the CG operator.  set = 1, 2, 4,
+ * 8, 16 or 32 overrides the choice (0 leaves it); *group (may be NULL)
+ * receives the value in force.  Returns DPGMG_ERR_ARG for an invalid level or
+ * size.  Results do not depend on the variant beyond rounding order (G = 1,
+ * 16 and 32: bitwise). */
 int dpgmg_spmv_group(dpgmg_handle h, dpgmg_system sys, int level, int set, int* group);
 
 /* DPG error indicator (Sec. 1.2: the residual that DPG minimises, in the

@@ -662,7 +662,7 @@ int dpgmg_setup_phases(dpgmg_handle h, dpgmg_system sys, double* ms, int n) {
 
 int dpgmg_spmv_group(dpgmg_handle h, dpgmg_system sys, int level, int set, int* group) {
   if (!h || !sys) return DPGMG_ERR_ARG;
-  if (set != 0 && set != 1 && set != 2 && set != 4 && set != 8 && set != 16) return DPGMG_ERR_ARG;
+  if (set != 0 && set != 1 && set != 2 && set != 4 && set != 8 && set != 16 && set != 32) return DPGMG_ERR_ARG;
   std::lock_guard<std::mutex> lk(h->mu);
   SystemImpl& S = sys->s;
   const int slot = S.op.precision == DPGMG_PREC_MIXED ? 0 : 1;

@@ -197,6 +197,113 @@ __global__ void __launch_bounds__(256) k_spmv_pf(const int32_t* __restrict__ row
   }
 }
 
+// The same product with the warp's whole stream of (value, column index)
+// pairs, across its rows, prefetched SPMV_DEPTH steps ahead by cp.async into
+// a per-thread shared-memory ring: the loads in flight hold no registers, so
+// a small kernel keeps enough bytes in flight to stream the values.  Same
+// accumulation order as k_spmv (two accumulators alternating by step):
+// bitwise the same results.
+constexpr int SPMV_DEPTH = 8;
+
+// Row descriptor of the ring kernels (steps = ceil(nnz / 32); 0 for a row of no entity).
+template <class T> struct RingRow {
+  int64_t row;
+  int nnz, steps;
+  const T* vals;
+  const int32_t* cols;
+  int64_t voff;
+};
+template <class T>
+__device__ __forceinline__ RingRow<T> ring_open(int64_t row, int64_t nrows, const int32_t* __restrict__ row_ent,
+                                                const int64_t* __restrict__ ent_start,
+                                                const int64_t* __restrict__ col_ptr,
+                                                const int32_t* __restrict__ col_idx,
+                                                const int64_t* __restrict__ val_ptr, const T* v) {
+  RingRow<T> c;
+  c.row = row;
+  c.nnz = 0;
+  c.steps = 0;
+  c.vals = nullptr;
+  c.cols = nullptr;
+  c.voff = 0;
+  if (row < nrows) {
+    const int32_t E = row_ent[row];
+    if (E >= 0) {
+      const int64_t c0 = col_ptr[E];
+      c.nnz = (int)(col_ptr[E + 1] - c0);
+      c.voff = val_ptr[E] + (row - ent_start[E]) * c.nnz;
+      c.vals = v + c.voff;
+      c.cols = col_idx + c0;
+      c.steps = (c.nnz + 31) >> 5;
+    }
+  }
+  return c;
+}
+
+template <class C>
+__device__ __forceinline__ void ring_copy(C* dst, const C* src) {
+  if constexpr (sizeof(C) == 16) cp_async16(dst, src);
+  else cp_async8(dst, src);
+}
+
+template <class C>
+__global__ void __launch_bounds__(256) k_spmv_ring(const int32_t* __restrict__ row_ent,
+                                                   const int64_t* __restrict__ ent_start,
+                                                   const int64_t* __restrict__ col_ptr,
+                                                   const int32_t* __restrict__ col_idx,
+                                                   const int64_t* __restrict__ val_ptr, const C* __restrict__ v,
+                                                   const C* __restrict__ x, const C* __restrict__ b, C* __restrict__ y,
+                                                   int64_t nrows, int mode) {
+  __shared__ C sv[SPMV_DEPTH][256];
+  __shared__ int32_t si[SPMV_DEPTH][256];
+  using O = Ops<C>;
+  const int lane = threadIdx.x & 31, t = threadIdx.x;
+  const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
+  const int64_t first = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5);
+  // prefetch cursor: the (row, step) whose pair is copied next
+  RingRow<C> p = ring_open<C>(first, nrows, row_ent, ent_start, col_ptr, col_idx, val_ptr, v);
+  int ps = 0;
+  while (p.row < nrows && p.steps == 0) p = ring_open<C>(p.row + nw, nrows, row_ent, ent_start, col_ptr, col_idx,
+                                                         val_ptr, v);
+  auto issue = [&](int slot) {
+    if (p.row < nrows) {
+      const int k = lane + 32 * ps;
+      if (k < p.nnz) {
+        ring_copy<C>(&sv[slot][t], p.vals + k);
+        cp_async4(&si[slot][t], p.cols + k);
+      }
+      if (++ps >= p.steps) {
+        ps = 0;
+        do {
+          p = ring_open<C>(p.row + nw, nrows, row_ent, ent_start, col_ptr, col_idx, val_ptr, v);
+        } while (p.row < nrows && p.steps == 0);
+      }
+    }
+    cp_async_commit();
+  };
+#pragma unroll
+  for (int d = 0; d < SPMV_DEPTH; ++d) issue(d);
+  int slot = 0;
+  for (int64_t row = first; row < nrows; row += nw) {
+    const RingRow<C> c = ring_open<C>(row, nrows, row_ent, ent_start, col_ptr, col_idx, val_ptr, v);
+    C acc = O::zero(), acc1 = O::zero();
+    for (int st = 0; st < c.steps; ++st) {
+      cp_async_wait<SPMV_DEPTH - 1>();
+      if (lane + 32 * st < c.nnz) {
+        const C val = sv[slot][t];
+        const C xv = x[si[slot][t]];
+        if (st & 1) acc1 = O::fma(val, xv, acc1);
+        else acc = O::fma(val, xv, acc);
+      }
+      issue(slot);
+      slot = slot + 1 == SPMV_DEPTH ? 0 : slot + 1;
+    }
+    acc = warp_sum(O::add(acc, acc1));
+    if (lane == 0) y[row] = mode ? O::sub(b[row], acc) : acc;
+  }
+  cp_async_wait<0>();
+}
+
 // Entity-blocked SpMV: one warp per task (entity E, rows r0 .. r0 + G - 1 of
 // E).  The G rows share E's column list, so each column index and x entry is
 // loaded once for G rows and G value streams are in flight per column.
@@ -256,10 +363,19 @@ template <> struct SpmvSlot<float2> { static constexpr int v = 0; };
 template <> struct SpmvSlot<double2> { static constexpr int v = 1; };
 
 // G: rows of one entity per warp (1, 2, 4, 8); SPMV_PF = one row per warp with
-// the column indices loaded one step ahead (k_spmv_pf)
+// the column indices loaded one step ahead (k_spmv_pf); SPMV_RING = one row
+// per warp with the (value, index) stream prefetched by cp.async (k_spmv_ring)
 constexpr int SPMV_PF = 16;
+constexpr int SPMV_RING = 32;   // one row per warp, (value, index) stream prefetched by cp.async
 template <class C>
 static void spmv_g(const ECSRDev& A, const C* vals, const C* x, const C* b, C* y, int mode, int G, cudaStream_t st) {
+  if (G == SPMV_RING) {
+    int64_t blocks = std::min<int64_t>((A.nrows + 7) / 8, 152 * 8);
+    k_spmv_ring<C><<<(unsigned)blocks, 256, 0, st>>>(A.row_ent, A.ent_start, A.col_ptr, A.col_idx, A.val_ptr, vals, x,
+                                                      b, y, A.nrows, mode);
+    DPG_CHECK_LAUNCH();
+    return;
+  }
   if (G == SPMV_PF) {
     int64_t blocks = std::min<int64_t>((A.nrows + 7) / 8, 152 * 16);
     k_spmv_pf<C><<<(unsigned)blocks, 256, 0, st>>>(A.row_ent, A.ent_start, A.col_ptr, A.col_idx, A.val_ptr, vals, x,
@@ -416,6 +532,81 @@ __global__ void __launch_bounds__(256) k_spmv_df(const int32_t* __restrict__ row
   }
 }
 
+// The double-float CG operator with the warp's stream of (high, low, column
+// index) triples prefetched SPMV_DEPTH steps ahead by cp.async (see
+// k_spmv_ring).  Per lane the sums run over k = lane, lane + 32, ... in order,
+// as in k_spmv_df: bitwise the same results.
+__global__ void __launch_bounds__(256) k_spmv_df_ring(const int32_t* __restrict__ row_ent,
+                                                      const int64_t* __restrict__ ent_start,
+                                                      const int64_t* __restrict__ col_ptr,
+                                                      const int32_t* __restrict__ col_idx,
+                                                      const int64_t* __restrict__ val_ptr,
+                                                      const float2* __restrict__ vh, const float2* __restrict__ vl,
+                                                      const float2* __restrict__ xh, const float2* __restrict__ xl,
+                                                      const double2* __restrict__ b, double2* __restrict__ y,
+                                                      int64_t nrows, int mode) {
+  __shared__ float2 sh[SPMV_DEPTH][256];
+  __shared__ float2 sl[SPMV_DEPTH][256];
+  __shared__ int32_t si[SPMV_DEPTH][256];
+  const int lane = threadIdx.x & 31, t = threadIdx.x;
+  const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
+  const int64_t first = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5);
+  RingRow<float2> p = ring_open<float2>(first, nrows, row_ent, ent_start, col_ptr, col_idx, val_ptr, vh);
+  int ps = 0;
+  while (p.row < nrows && p.steps == 0)
+    p = ring_open<float2>(p.row + nw, nrows, row_ent, ent_start, col_ptr, col_idx, val_ptr, vh);
+  auto issue = [&](int slot) {
+    if (p.row < nrows) {
+      const int k = lane + 32 * ps;
+      if (k < p.nnz) {
+        cp_async8(&sh[slot][t], vh + p.voff + k);
+        cp_async8(&sl[slot][t], vl + p.voff + k);
+        cp_async4(&si[slot][t], p.cols + k);
+      }
+      if (++ps >= p.steps) {
+        ps = 0;
+        do {
+          p = ring_open<float2>(p.row + nw, nrows, row_ent, ent_start, col_ptr, col_idx, val_ptr, vh);
+        } while (p.row < nrows && p.steps == 0);
+      }
+    }
+    cp_async_commit();
+  };
+#pragma unroll
+  for (int d = 0; d < SPMV_DEPTH; ++d) issue(d);
+  int slot = 0;
+  for (int64_t row = first; row < nrows; row += nw) {
+    const RingRow<float2> c = ring_open<float2>(row, nrows, row_ent, ent_start, col_ptr, col_idx, val_ptr, vh);
+    float rh = 0.f, rl = 0.f, ih = 0.f, il = 0.f;
+    for (int st = 0; st < c.steps; ++st) {
+      cp_async_wait<SPMV_DEPTH - 1>();
+      if (lane + 32 * st < c.nnz) {
+        const float2 ah = sh[slot][t], al = sl[slot][t];
+        const int col = si[slot][t];
+        const float2 uh = xh[col], ul = xl[col];
+        float pp, q;
+        df_mul(ah.x, al.x, uh.x, ul.x, pp, q);
+        df_add(rh, rl, pp, q);
+        df_mul(ah.y, al.y, uh.y, ul.y, pp, q);
+        df_add(rh, rl, -pp, -q);
+        df_mul(ah.x, al.x, uh.y, ul.y, pp, q);
+        df_add(ih, il, pp, q);
+        df_mul(ah.y, al.y, uh.x, ul.x, pp, q);
+        df_add(ih, il, pp, q);
+      }
+      issue(slot);
+      slot = slot + 1 == SPMV_DEPTH ? 0 : slot + 1;
+    }
+    df_warp_sum(rh, rl);
+    df_warp_sum(ih, il);
+    if (lane == 0) {
+      const double re = (double)rh + (double)rl, im = (double)ih + (double)il;
+      y[row] = mode ? make_double2(b[row].x - re, b[row].y - im) : make_double2(re, im);
+    }
+  }
+  cp_async_wait<0>();
+}
+
 // Entity-blocked double-float CG operator (same task lists as k_spmv_ent).
 template <int G>
 __global__ void __launch_bounds__(256) k_spmv_df_ent(const int2* __restrict__ tasks, int64_t ntasks,
@@ -498,6 +689,13 @@ __global__ void k_split_vals(const double2* __restrict__ v, float2* __restrict__
 static void spmv_df_g(const ECSRDev& A, const float2* xh, const float2* xl, const double2* b, double2* y, int mode,
                       int G, cudaStream_t st) {
   const int64_t n = A.nrows;
+  if (G == SPMV_RING) {
+    const int64_t blocks = std::min<int64_t>((n + 7) / 8, 152 * 5);
+    k_spmv_df_ring<<<(unsigned)blocks, 256, 0, st>>>(A.row_ent, A.ent_start, A.col_ptr, A.col_idx, A.val_ptr, A.v32,
+                                                     A.vlo, xh, xl, b, y, n, mode);
+    DPG_CHECK_LAUNCH();
+    return;
+  }
   if (G == SPMV_PF || G <= 1 || !A.tasks[1]) {
     const int64_t blocks = (n + DF_ROWS - 1) / DF_ROWS;
     if (G == SPMV_PF)
@@ -1611,7 +1809,7 @@ static int pick_variant(const TuneKey& key, const Evict& ev, cudaStream_t st, st
 
 template <class F>
 static int pick_group(const TuneKey& key, const Evict& ev, cudaStream_t st, F&& run) {
-  return pick_variant(key, ev, st, {1, SPMV_PF, 2, 4, 8}, run);
+  return pick_variant(key, ev, st, {1, SPMV_PF, SPMV_RING, 2, 4, 8}, run);
 }
 
 template <class F>

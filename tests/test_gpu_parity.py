@@ -310,9 +310,9 @@ def test_spmv_group_sizes(name, request):
     c = request.getfixturevalue(name)
     s = c.solver
     tuned = [D.dpgmg_spmv_group(s.h, s.s, l) for l in range(1, c.L + 1)] + [D.dpgmg_spmv_group(s.h, s.s, -1)]
-    assert all(g in (1, 2, 4, 8, 16) for g in tuned)
+    assert all(g in (1, 2, 4, 8, 16, 32) for g in tuned)
     try:
-        for G in (1, 2, 4, 8, 16):
+        for G in (1, 2, 4, 8, 16, 32):
             for l in range(1, c.L + 1):
                 D.dpgmg_spmv_group(s.h, s.s, l, G)
                 n = c.levels[l].mesh.n_dof
@@ -327,17 +327,18 @@ def test_spmv_group_sizes(name, request):
     finally:
         for l, g in zip(list(range(1, c.L + 1)) + [-1], tuned):
             D.dpgmg_spmv_group(s.h, s.s, l, g)
-    # one row per warp with and without the index prefetch: the same arithmetic, bitwise
+    # one row per warp with and without the index prefetch, and with the
+    # cp.async ring: the same arithmetic, bitwise
     for l in list(range(1, c.L + 1)) + [-1]:
         n = c.A.shape[0] if l == -1 else c.levels[l].mesh.n_dof
         op, lv = (D.OP_AFULL, c.L) if l == -1 else (D.OP_A, l)
         x = rand_vec(n, 80 + l)
         ys = []
-        for G in (1, 16):
+        for G in (1, 16, 32):
             D.dpgmg_spmv_group(s.h, s.s, l, G)
             ys.append(D.dpgmg_apply(s.h, s.s, op, lv, x, n))
         D.dpgmg_spmv_group(s.h, s.s, l, tuned[l - 1] if l > 0 else tuned[-1])
-        assert np.array_equal(ys[0], ys[1]), l
+        assert np.array_equal(ys[0], ys[1]) and np.array_equal(ys[0], ys[2]), l
     with pytest.raises(D.DpgmgError):
         D.dpgmg_spmv_group(s.h, s.s, 1, 3)
 
@@ -345,7 +346,7 @@ def test_spmv_group_sizes(name, request):
 def test_spmv_group_sizes_mixed(c1):
     """The complex64 V-cycle operators under every work decomposition."""
     with D.Solver(c1.pk, **dict(c1.ok, precision="mixed")) as s:
-        for G in (1, 2, 4, 8, 16):
+        for G in (1, 2, 4, 8, 16, 32):
             for l in range(1, c1.L + 1):
                 D.dpgmg_spmv_group(s.h, s.s, l, G)
                 n = c1.levels[l].mesh.n_dof
