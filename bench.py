@@ -393,6 +393,7 @@ def run_gb300(args, rank, world, local_rank):
 
     tuned = {}
     elem_acc = [0.0, 0.0, 0]   # element-stage ms, GFLOP, setups
+    phases = []                # device ms of each setup phase, per step
 
     def step(prof=D.PROF_OFF):
         s = D.dpgmg_setup(h, pb, op)
@@ -404,6 +405,7 @@ def run_gb300(args, rank, world, local_rank):
                     break
             tuned["cg"] = D.dpgmg_spmv_group(h, s, -1)
             em, eg, _ = D.dpgmg_setup_profile(h, s)
+            phases.append(D.dpgmg_setup_phases(h, s))
             elem_acc[0] += em
             elem_acc[1] += eg
             elem_acc[2] += 1
@@ -420,6 +422,7 @@ def run_gb300(args, rank, world, local_rank):
     for _ in range(args.warmup):
         step()
     elem_acc[:] = [0.0, 0.0, 0]
+    phases.clear()
     clocks = Clocks(local_rank)
     clocks.start()
     if dist:
@@ -560,6 +563,8 @@ def run_gb300(args, rank, world, local_rank):
         "precision_options": options,
         "kernels": [dict(k, frac=k["achieved"] / peak) for k in kernels],
         "spmv_group_tuned": tuned,
+        "setup_phases_ms": ({k: sum(p[i] for p in phases) / len(phases) for i, k in enumerate(D.SETUP_PHASES)}
+                            if phases else None),
         "element_stage": element_line(elem_acc_timed, full_pipeline_gflop(int(np.prod(w["problem"]["n"])),
                                                                           w["problem"]["p"])),
     }
