@@ -831,8 +831,8 @@ def stream_run(D, items, rate, slots, budget_gb):
             if e.code != D.DPGMG_ERR_NOMEM:
                 raise
             refused += 1
-    lat, di, fails = [], 0.0, 0
-    for tk, nt, nf in tickets:
+    lat, di, fails, codes = [], 0.0, 0, []
+    for q, (tk, nt, nf) in enumerate(tickets):
         while True:
             code, st, l = D.dpgmg_poll(h, tk, None, None)
             if code != D.DPGMG_ERR_PENDING:
@@ -840,12 +840,14 @@ def stream_run(D, items, rate, slots, budget_gb):
             time.sleep(0.0005)
         if code != D.DPGMG_OK:
             fails += 1
+            codes.append({"request": q, "status": D.strerror(code), "message": D.lib().dpgmg_last_error().decode(),
+                          "iters": st.iters, "relres": st.relres, "n_dof": nt})
             continue
         lat.append(l)
         di += nt * st.iters
     wall = time.perf_counter() - t0
     D.dpgmg_destroy(h)
-    return {"completed": len(lat), "failed": fails, "refused_nomem": refused, "wall_s": wall,
+    return {"completed": len(lat), "failed": fails, "failures": codes, "refused_nomem": refused, "wall_s": wall,
             "solves_per_s": len(lat) / wall, "dof_iters_per_s": di / wall,
             "p50_ms": float(np.percentile(lat, 50)) if lat else None,
             "p99_ms": float(np.percentile(lat, 99)) if lat else None}

@@ -154,12 +154,15 @@ __device__ int cta_potrf(T* A, int n, int lda, T* smem, Team<CL> tm = Team<CL>()
   __syncthreads();
   for (int k0 = 0; k0 < n; k0 += NB) {
     const int kb = min(NB, n - k0);
-    // diagonal block -> shared, unblocked factorisation
+    // diagonal block -> shared, unblocked factorisation.  With a cluster every
+    // CTA factors its own copy; the cluster barrier keeps the owner's write-back
+    // of the factored block (below) from reaching A before every CTA has read it.
     for (int e = tid; e < kb * kb; e += blockDim.x) {
       int i = e / kb, j = e % kb;
       D[i * NB + j] = tm.ld(&A[(size_t)(k0 + i) * lda + k0 + j]);
     }
-    __syncthreads();
+    if constexpr (CL) tm.sync();
+    else __syncthreads();
     for (int j = 0; j < kb; ++j) {
       if (tid == 0) {
         R d = O::re(D[j * NB + j]);

@@ -163,11 +163,23 @@ template <class T> __device__ __forceinline__ T to_path(double2 v, bool rot);
 template <> __device__ __forceinline__ double2 to_path<double2>(double2 v, bool) { return v; }
 template <> __device__ __forceinline__ double to_path<double>(double2 v, bool rot) { return rot ? -v.y : v.x; }
 
+// Shared memory of the load builder: the four source arrays at the nq^3
+// points and the first partial contraction (4 n1 nq^2 values).
+__host__ __device__ inline size_t build_load_smem(int nq, int n1) {
+  return ((size_t)4 * nq * nq * nq + (size_t)4 * n1 * nq * nq) * sizeof(double2) + 64;
+}
+
 // Volume load l' of one element (Sec. 2: (f, v) + (g, q); v rows scaled by
-// -i in the real form) into out[i * stride], i < nt.  sh2: 4 nq^3 complex.
+// -i in the real form) into out[i * stride], i < nt.  The test functions are
+// tensor products L_a(x) L_b(y) L_c(z) of the 1D functions tabulated at the
+// load rule's points, so the quadrature sums factor axis by axis (sum
+// factorisation): for each of the four source arrays S (f and the three
+// components of g) T[a][b][c] = sum_qc L_c sum_qb L_b sum_qa L_a S[qc][qb][qa],
+// 4 (n1 nq^3 + n1^2 nq^2 + n1^3 nq) products instead of nt nq^3; every test
+// function then reads its entry of T.  sh2: build_load_smem(nq, n1) bytes.
 template <class T>
 __device__ void build_load(const ElemArgs& a, const double corner[3], double c, double2* sh2, T* out, size_t stride) {
-  const int nq = a.nql, nq3 = nq * nq * nq, nt = a.nt;
+  const int nq = a.nql, nq2 = nq * nq, nq3 = nq2 * nq, nt = a.nt, n1 = a.tab.n1;
   double2* fv = sh2;                 // [nq3]
   double2* gv = sh2 + nq3;           // [3][nq3]
   const double J = a.h[0] * a.h[1] * a.h[2];
@@ -181,16 +193,56 @@ __device__ void build_load(const ElemArgs& a, const double corner[3], double c, 
     for (int d = 0; d < 3; ++d) gv[d * nq3 + q] = make_double2(g[d].x * w, g[d].y * w);
   }
   __syncthreads();
+  // T1[s][a][qc][qb] = sum_qa L_a(qa) S_s[qc][qb][qa]
+  double2* T1 = sh2 + 4 * nq3;
+  const int n1q2 = n1 * nq2;
+  for (int q = threadIdx.x; q < 4 * n1q2; q += blockDim.x) {
+    const int arr = q / n1q2, rem = q % n1q2, ia = rem / nq2, cb = rem % nq2;
+    const double2* S = sh2 + (size_t)arr * nq3 + (size_t)cb * nq;
+    const double* L = a.Lq + ia * nq;
+    double2 acc = make_double2(0, 0);
+    for (int qa = 0; qa < nq; ++qa) {
+      acc.x += S[qa].x * L[qa];
+      acc.y += S[qa].y * L[qa];
+    }
+    T1[q] = acc;
+  }
+  __syncthreads();
+  // T2[s][a][b][qc] = sum_qb L_b(qb) T1[s][a][qc][qb]   (over the source arrays' space)
+  double2* T2 = sh2;
+  const int n12q = n1 * n1 * nq;
+  for (int q = threadIdx.x; q < 4 * n12q; q += blockDim.x) {
+    const int arr = q / n12q, rem = q % n12q, ia = rem / (n1 * nq), rem2 = rem % (n1 * nq), ib = rem2 / nq,
+              qc = rem2 % nq;
+    const double2* S = T1 + (size_t)arr * n1q2 + (size_t)ia * nq2 + (size_t)qc * nq;
+    const double* L = a.Lq + ib * nq;
+    double2 acc = make_double2(0, 0);
+    for (int qb = 0; qb < nq; ++qb) {
+      acc.x += S[qb].x * L[qb];
+      acc.y += S[qb].y * L[qb];
+    }
+    T2[q] = acc;
+  }
+  __syncthreads();
+  // T3[s][a][b][c] = sum_qc L_c(qc) T2[s][a][b][qc]   (over T1's space)
+  double2* T3 = T1;
+  const int n13 = n1 * n1 * n1;
+  for (int q = threadIdx.x; q < 4 * n13; q += blockDim.x) {
+    const int arr = q / n13, rem = q % n13, ab = rem / n1, ic = rem % n1;
+    const double2* S = T2 + (size_t)arr * n12q + (size_t)ab * nq;
+    const double* L = a.Lq + ic * nq;
+    double2 acc = make_double2(0, 0);
+    for (int qc = 0; qc < nq; ++qc) {
+      acc.x += S[qc].x * L[qc];
+      acc.y += S[qc].y * L[qc];
+    }
+    T3[q] = acc;
+  }
+  __syncthreads();
   for (int i = threadIdx.x; i < nt; i += blockDim.x) {
     int4 t = a.tf[i];
-    double2 acc = make_double2(0, 0);
-    const double2* src = (t.x == 3) ? fv : gv + (size_t)t.x * nq3;
-    for (int q = 0; q < nq3; ++q) {
-      int qa = q % nq, qb = (q / nq) % nq, qc = q / (nq * nq);
-      double bv = a.Lq[t.y * nq + qa] * a.Lq[t.z * nq + qb] * a.Lq[t.w * nq + qc];
-      acc.x += src[q].x * bv;
-      acc.y += src[q].y * bv;
-    }
+    const int arr = t.x == 3 ? 0 : 1 + t.x;
+    double2 acc = T3[(size_t)arr * n13 + (t.y * n1 + t.z) * n1 + t.w];
     if (t.x != 3) acc = make_double2(acc.y, -acc.x);
     out[(size_t)i * stride] = to_path<T>(acc, false);
   }
@@ -672,10 +724,10 @@ static void element_core(SystemImpl& S, Level& L, const std::vector<double>& cva
   a.W = A.arr<double2>((size_t)chunk * a.nt * (a.m + 1));
   a.K = A.arr<double2>((size_t)chunk * (a.m + 1) * (a.m + 1));
 
-  const size_t sm_build = (size_t)4 * T.nql * T.nql * T.nql * sizeof(double2) + 64;
+  const size_t sm_build = build_load_smem(T.nql, p + 2);
   // Function attributes are process-wide and systems may be set up concurrently
   // (serving slots), so the limit is the largest any order p <= 5 needs.
-  const size_t sm_build_max = (size_t)4 * 10 * 10 * 10 * sizeof(double2) + 64;
+  const size_t sm_build_max = build_load_smem(10, 7);   // p = 5
   const size_t sm_real = smem_bytes_dense(8);
   const size_t sm_cplx = smem_bytes_dense(16);
   DPG_CUDA(cudaFuncSetAttribute(k_elem_build<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_build_max));
@@ -1018,7 +1070,7 @@ void error_indicator(SystemImpl& S, const double2* x, double* eta2, cudaStream_t
   a.elist = dall;
   a.info = A.arr<int>(1);
   DPG_CUDA(cudaMemsetAsync(a.info, 0, sizeof(int), st));
-  const size_t sm_build = (size_t)4 * a.nql * a.nql * a.nql * sizeof(double2) + 64;
+  const size_t sm_build = build_load_smem(a.nql, a.tab.n1);
   const size_t sm_real = smem_bytes_dense(8);
   const size_t sm_eta = (size_t)a.m * sizeof(double2) + smem_bytes_dense(16);
   DPG_CUDA(cudaFuncSetAttribute(k_elem_eta, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_eta));

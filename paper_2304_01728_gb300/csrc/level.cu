@@ -999,7 +999,11 @@ void build_hierarchy(SystemImpl& S, cudaStream_t st) {
     if (!(S.op.theta > 0.0)) S.levels[l].theta = theta_from_rayleigh(th[2 * l], th[2 * l + 1]);
   info |= info_main;
   if (info & 32) throw Err{DPGMG_ERR_TIMEOUT, "tensor-core update: a bounded wait for the MMAs ran out"};
-  if (info) throw Err{DPGMG_ERR_NOT_HPD, "a macro, patch or coarsest factorisation lost positive definiteness"};
+  if (info)
+    throw Err{DPGMG_ERR_NOT_HPD, std::string("lost positive definiteness in:") + ((info & 4) ? " macro condensation" : "") +
+                                     ((info & 8) ? " patch factorisation" : "") +
+                                     ((info & 16) ? " coarsest factorisation" : "") +
+                                     ((info & ~(4 | 8 | 16 | 32)) ? " other" : "")};
 }
 
 }  // namespace dpgmg
