@@ -182,3 +182,4 @@ def test_element_class_reuse_matches_full_pipeline(n, p, prec, layers, monkeypat
         # factored in FP32: the preconditioners may differ in a few entries
         assert abs(i1 - i0) <= 1
         assert rel(x1, x0) < 1e-7 and rel(f1, f0) < 1e-7
+

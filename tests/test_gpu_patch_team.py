@@ -27,6 +27,9 @@ CASES = [
      dict(n_levels=2, p_min=2, precision="fp64")),
     (dict(n=(4, 4, 4), p=3, omega=9.0, src_center=(0.45, 0.5, 0.55), src_width=0.2),
      dict(n_levels=3, p_min=2, precision="fp64")),
+    # complex64 blocks factored in FP32 (the mixed path), macro patches of two h-levels
+    (dict(n=(8, 8, 8), p=2, omega=6.0, src_center=(0.4, 0.5, 0.6), src_width=0.15),
+     dict(n_levels=3, p_min=2, precision="mixed")),
 ]
 
 
