@@ -394,6 +394,7 @@ def run_gb300(args, rank, world, local_rank):
     tuned = {}
     elem_acc = [0.0, 0.0, 0]   # element-stage ms, GFLOP, setups
     phases = []                # device ms of each setup phase, per step
+    patch_store = {}           # finest level: sum n_j^2, and over the real packed patches
 
     def step(prof=D.PROF_OFF):
         s = D.dpgmg_setup(h, pb, op)
@@ -404,6 +405,8 @@ def run_gb300(args, rank, world, local_rank):
                 except D.DpgmgError:
                     break
             tuned["cg"] = D.dpgmg_spmv_group(h, s, -1)
+            li = D.dpgmg_level_info(h, s, w["opts"]["n_levels"] - 1)
+            patch_store.update(sum_patch_sq=int(li.sum_patch_sq), real_sq=int(li.patch_real_sq))
             em, eg, _ = D.dpgmg_setup_profile(h, s)
             phases.append(D.dpgmg_setup_phases(h, s))
             elem_acc[0] += em
@@ -520,7 +523,8 @@ def run_gb300(args, rank, world, local_rank):
                        "fp64_cg_double_float": fp64,
                        "fp64_cg_c128": one(dict(precision="fp64", flags=D.FLAG_CG_C128)),
                        "mixed_patch_factors_fp64": one(dict(flags=D.FLAG_PATCH_FP64)),
-                       "mixed_coarsest_cuda_cores": one(dict(flags=D.FLAG_CUDA_CORES))}
+                       "mixed_coarsest_cuda_cores": one(dict(flags=D.FLAG_CUDA_CORES)),
+                       "mixed_patches_all_complex64": one(dict(flags=D.FLAG_PATCH_COMPLEX))}
     D.dpgmg_destroy(h)
 
 
@@ -546,6 +550,10 @@ def run_gb300(args, rank, world, local_rank):
         "roofline": {"kernel": "k_patch_apply (finest smoother)", "bound": "hbm", "achieved": achieved,
                      "peak": peak, "unit": "GB/s", "frac": achieved / peak, "peak_source": peak_kind,
                      "bytes_per_launch": prof_b, "launches": prof_n, "avg_launch_ms": per_launch_ms,
+                     "bytes_rule": "stored patch-inverse entries read once: 8 B per complex64 entry, 4 B per "
+                                   "entry of a real packed block",
+                     "real_packed_fraction_of_entries": (patch_store["real_sq"] / patch_store["sum_patch_sq"]
+                                                         if patch_store.get("sum_patch_sq") else None),
                      "traffic": traffic_for("k_patch_apply", prof_b),
                      "traffic_source": "not measured in this run: ncu dram__bytes_read.sum + dram__bytes_write.sum "
                                        "per algorithmic byte of the finest launches of one step of the "

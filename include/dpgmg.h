@@ -182,6 +182,15 @@ typedef struct dpgmg_opts {
    Mixed path only, without DPGMG_FLAG_PATCH_FP64 and DPGMG_FLAG_CG_C128
    (ARG otherwise); dpgmg_smooth_noalloc is not available (ARG). */
 #define DPGMG_FLAG_RECOMPUTE_PATCHES 128
+/* Mixed path: keep every stored patch inverse as a complex64 block.  By
+   default a patch whose block is real once the unit phases of the real form
+   are taken out (every element touching it has no impedance face and a real
+   source: Sec. 2, impedance condition) keeps its FP32-factored inverse as a
+   real matrix w, A_j^-1[r][c] = w[r][c] i^(s_r - s_c) with s = 1 on p-hat
+   DOFs, at half the bytes, and the smoother applies the phases exactly.  The
+   products then differ from the complex64 ones by FP32 rounding order only;
+   this flag is the comparison. */
+#define DPGMG_FLAG_PATCH_COMPLEX 256
 /* Host-made failures for testing the error paths (the paper has no
    counterpart; no GPU fault is involved):
    FAULT_NOT_HPD: the host overwrites the first diagonal entry of the dense
@@ -220,6 +229,8 @@ typedef struct dpgmg_level_desc {
   double theta;
   long long patch_stored;  /* stored patch-inverse entries (sum n_j^2, or sum n_j(n_j+1)/2 in
                               Hermitian half storage) */
+  long long patch_real_sq; /* sum of n_j^2 over the patches whose inverses are stored as real
+                              blocks (mixed path, see DPGMG_FLAG_PATCH_COMPLEX): half the bytes */
 } dpgmg_level_desc;
 
 typedef struct dpgmg_handle_s* dpgmg_handle;

@@ -86,7 +86,7 @@ int validate_problem(const dpgmg_problem* pb, const dpgmg_opts* op) {
        op->coarsest != DPGMG_COARSEST_AUTO && op->coarsest != DPGMG_COARSEST_SMOOTH) ||
       (op->flags & ~(DPGMG_FLAG_EAGER | DPGMG_FLAG_CUDA_CORES | DPGMG_FLAG_STORE_COARSE | DPGMG_FLAG_WARM_START |
                      DPGMG_FLAG_CG_C128 | DPGMG_FLAG_PATCH_FP64 | DPGMG_FLAG_PATCH_R2 |
-                     DPGMG_FLAG_RECOMPUTE_PATCHES | DPGMG_FLAG_FAULT_NOT_HPD |
+                     DPGMG_FLAG_RECOMPUTE_PATCHES | DPGMG_FLAG_PATCH_COMPLEX | DPGMG_FLAG_FAULT_NOT_HPD |
                      DPGMG_FLAG_FAULT_TC_WAIT)))
     return DPGMG_ERR_ARG;
   // recompute mode: the mixed path's FP32 patch factors and complex64 damping estimate only
@@ -203,7 +203,8 @@ static void fill_bytes_per_iter(SystemImpl& S) {
   const int nu = S.op.nu_pre + S.op.nu_post;
   for (size_t l = 1; l < S.levels.size(); ++l) {
     const Level& L = S.levels[l];
-    b += nu * (double)L.P.sum_sq * esz;                                          // smoother (n_j^2 per patch)
+    b += nu * ((double)(L.P.sum_sq - L.P.real_sq) + 0.5 * (double)L.P.real_sq) * esz;  // smoother (n_j^2 per
+                                                                                      // patch, real ones half)
     b += std::max(1, nu) * (double)L.A.nnz_alg * esz;                            // residual SpMVs
     if (L.kind == 2) b += (double)L.nK * (2.0 * L.nI * L.nS + L.nI * L.nI) * esz; // condense + backsub
   }
@@ -282,6 +283,17 @@ void setup_system(SystemImpl& S, const dpgmg_problem* pb, const dpgmg_opts* op, 
   S.t_phase[3] = S.ph_side ? span(5, 6) : 0.0;
   S.t_phase[4] = span(3, 4);
   S.t_phase[5] = span(4, 7);
+  // patches whose inverses are stored as real blocks (half the bytes per entry)
+  for (size_t l = 1; l < S.levels.size() && S.plan; ++l) {
+    PatchDev& P = S.levels[l].P;
+    P.real_sq = 0;
+    if (!P.rflag || P.np == 0) continue;
+    std::vector<uint8_t> fl((size_t)P.np);
+    DPG_CUDA(cudaMemcpy(fl.data(), P.rflag, (size_t)P.np, cudaMemcpyDeviceToHost));
+    const std::vector<int64_t>& pp = S.plan->lv[l].P.ptr;
+    for (int64_t j = 0; j < P.np; ++j)
+      if (fl[j]) P.real_sq += (pp[j + 1] - pp[j]) * (pp[j + 1] - pp[j]);
+  }
   fill_bytes_per_iter(S);
 }
 
@@ -696,6 +708,7 @@ int dpgmg_level_info(dpgmg_handle h, dpgmg_system sys, int level, dpgmg_level_de
   out->op_nnz = L.A.nnz_alg;
   out->theta = L.theta;
   out->patch_stored = L.P.recompute ? 0 : (L.P.half ? L.P.nhvals : L.P.nvals);
+  out->patch_real_sq = L.P.real_sq;
   return DPGMG_OK;
 }
 

@@ -20,25 +20,6 @@ constexpr int BLK_MAX = 4;   // vectors per launch of a block kernel
 // item (patch j, first column a0; PER columns per lane, warps split the rows
 // k = w, w + 8, ...), for kb < KB.  r_kb = r + kb * ldr.  Shared memory:
 // KB * n_j values of the gathered right-hand sides.
-// 16-byte asynchronous global -> shared copies (cp.async, L2 only); each thread
-// later reads back only what it copied itself, after waiting on its own groups.
-__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
-  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
-}
-__device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
-  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(gmem) : "memory");
-}
-__device__ __forceinline__ void cp_async4(void* smem, const void* gmem) {
-  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(gmem) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-template <int N> __device__ __forceinline__ void cp_async_wait() {
-  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
-}
-
 constexpr int BLK_DEPTH = 8;   // rows in flight per thread in the block smoother
 
 // pbuf[kb * ldp + slot] = A_jj^-1 (R_j r_kb) for the patch columns of one work
@@ -53,7 +34,8 @@ __global__ void __launch_bounds__(256) k_patch_apply_blk(const int64_t* __restri
                                                          const int64_t* __restrict__ vptr,
                                                          const int2* __restrict__ chunks, const C* __restrict__ inv,
                                                          const TIN* __restrict__ r, int64_t ldr,
-                                                         C* __restrict__ pbuf, int64_t ldp) {
+                                                         C* __restrict__ pbuf, int64_t ldp,
+                                                         const uint8_t* __restrict__ rflag, int64_t offU) {
   extern __shared__ unsigned char shraw[];
   __shared__ C part[8][32 * PER + 1];
   __shared__ float4 ring[PER == 2 ? BLK_DEPTH : 1][PER == 2 ? 256 : 1];
@@ -67,7 +49,8 @@ __global__ void __launch_bounds__(256) k_patch_apply_blk(const int64_t* __restri
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int a = ch.y + PER * lane;
   const C* M = inv + vptr[j] + a;
-  if (PER == 2 && a < n) {
+  const bool rp = rflag != nullptr && rflag[j] != 0;   // real packed block (k_patch_apply)
+  if (PER == 2 && a < n && !rp) {
     // start the first BLK_DEPTH rows of this thread (k = w + 8 d) before the gather
     const float4* M4 = reinterpret_cast<const float4*>(M);
     const int64_t s4 = ld / 2;
@@ -80,8 +63,9 @@ __global__ void __launch_bounds__(256) k_patch_apply_blk(const int64_t* __restri
   }
   for (int q = threadIdx.x; q < n; q += blockDim.x) {
     const int32_t g = dofs[b + q];
+    const int s = rp && g < offU ? -1 : 0;
 #pragma unroll
-    for (int kb = 0; kb < KB; ++kb) rj[kb * n + q] = cvt_in<C>(r[kb * ldr + g]);
+    for (int kb = 0; kb < KB; ++kb) rj[kb * n + q] = mul_i(cvt_in<C>(r[kb * ldr + g]), s);
   }
   __syncthreads();
   C acc[KB][PER];
@@ -89,7 +73,37 @@ __global__ void __launch_bounds__(256) k_patch_apply_blk(const int64_t* __restri
   for (int kb = 0; kb < KB; ++kb)
 #pragma unroll
     for (int u = 0; u < PER; ++u) acc[kb][u] = O::zero();
-  if (a < n) {
+  if (a < n && rp) {
+    // real rows (two columns of a lane in one load for PER = 2), four rows in flight
+    using R = typename Ops<C>::R;
+    const R* Wt = reinterpret_cast<const R*>(inv + vptr[j]) + a;
+    const int64_t ldw = patch_ldr(n);   // real rows
+    int k = w;
+    for (; k + 24 < n; k += 32) {
+      C m[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+        m[u] = PER == 2 ? __ldcs(reinterpret_cast<const C*>(Wt + (int64_t)(k + 8 * u) * ldw))
+                        : Ops<C>::mk(__ldcs(Wt + (int64_t)(k + 8 * u) * ldw), R(0));
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int kb = 0; kb < KB; ++kb) {
+          const C rv = rj[kb * n + k + 8 * u];
+          acc[kb][0] = rfma<C>(m[u].x, rv, acc[kb][0]);
+          if (PER == 2) acc[kb][1 % PER] = rfma<C>(m[u].y, rv, acc[kb][1 % PER]);
+        }
+    }
+    for (; k < n; k += 8) {
+      const C m0 = PER == 2 ? __ldcs(reinterpret_cast<const C*>(Wt + (int64_t)k * ldw))
+                            : Ops<C>::mk(__ldcs(Wt + (int64_t)k * ldw), R(0));
+#pragma unroll
+      for (int kb = 0; kb < KB; ++kb) {
+        acc[kb][0] = rfma<C>(m0.x, rj[kb * n + k], acc[kb][0]);
+        if (PER == 2) acc[kb][1 % PER] = rfma<C>(m0.y, rj[kb * n + k], acc[kb][1 % PER]);
+      }
+    }
+  } else if (a < n) {
     if (PER == 2) {
       const float4* M4 = reinterpret_cast<const float4*>(M);
       const int64_t s4 = ld / 2;
@@ -141,7 +155,7 @@ __global__ void __launch_bounds__(256) k_patch_apply_blk(const int64_t* __restri
           C s2 = part[0][PER * lane + u];
 #pragma unroll
           for (int q = 1; q < 8; ++q) s2 = O::add(s2, part[q][PER * lane + u]);
-          pbuf[kb * ldp + b + c] = s2;
+          pbuf[kb * ldp + b + c] = rp ? mul_i(s2, dofs[b + c] < offU ? 1 : 0) : s2;
         }
       }
     }

@@ -104,6 +104,14 @@ int patch_axis_span(int ctr, int H, int nco, bool r2, int W[2]);
 __host__ __device__
 #endif
 inline int64_t patch_ld(int64_t n) { return n + (n & 1); }
+// Row length of a patch block stored as real numbers (a real-path inverse of
+// the mixed path, in the first half of its complex64 block): n rounded up to
+// a multiple of 4, so that every row starts on a 16-byte boundary.  4 ld >= 2
+// ldr, so the real rows fit in the block.
+#if defined(__CUDACC__)
+__host__ __device__
+#endif
+inline int64_t patch_ldr(int64_t n) { return (n + 3) & ~(int64_t)3; }
 // Patch sizes only (same rule), for memory estimates: n_j per coarse vertex.
 // macro = true selects the h-level smoothing space (fine DOFs on the coarse skeleton).
 std::vector<int64_t> patch_sizes(const MeshL& m, bool macro, int H, const int nco[3], bool r2);

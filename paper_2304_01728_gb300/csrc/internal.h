@@ -94,6 +94,13 @@ struct PatchDev {
   int2* chunks64 = nullptr;    // the same for 64-column work items (complex64)
   int64_t nchunks64 = 0;
   int cols = 2;                // complex64 product: columns per lane (1 or 2), tuned at setup
+  int variant = 2;             // complex64 single-vector product variant (smoother.cuh), tuned at setup
+  // complex64 inverses of the mixed path: rflag[j] = 1 when patch j's block
+  // holds the real matrix w (A^-1[r][c] = w[r][c] i^(s_r - s_c), s = 1 on
+  // p-hat DOFs, global index < offU) as n rows of ld reals in its first half
+  uint8_t* rflag = nullptr;
+  int64_t offU = 0;
+  int64_t real_sq = 0;         // sum of n_j^2 over the real patches (host copy, after setup)
   // Hermitian half storage (lower triangles packed by rows), used for the
   // complex64 operators of the mixed path
   bool half = false;

@@ -312,14 +312,10 @@ __global__ void k_patch_gather(ECSRDev A, const int64_t* ptr, const int32_t* dof
   }
 }
 
-// Unit phases of the real form: p-hat DOFs (global index < offU) carry i,
-// u-hat DOFs carry 1.  rot(v, a, b) = conj(beta_a) v beta_b and its inverse
-// unrot(x, a, b) = beta_a x conj(beta_b); multiplying by +-i only swaps
-// components, so both are exact.
-template <class C>
-__device__ __forceinline__ C mul_i(C v, int s) {   // v * (i)^s, s in {-1, 0, 1}
-  return s == 0 ? v : (s > 0 ? Ops<C>::mk(-v.y, v.x) : Ops<C>::mk(v.y, -v.x));
-}
+// Unit phases of the real form (mul_i, smoother.cuh): p-hat DOFs (global
+// index < offU) carry i, u-hat DOFs carry 1.  rot(v, a, b) = conj(beta_a) v
+// beta_b and its inverse unrot(x, a, b) = beta_a x conj(beta_b); multiplying
+// by +-i only swaps components, so both are exact.
 
 // In place: M (n x n) -> M^-1 via Cholesky in the scratch copy W.
 // Real path: on a patch whose block is real after the unit phases are removed
@@ -329,6 +325,11 @@ __device__ __forceinline__ C mul_i(C v, int s) {   // v * (i)^s, s in {-1, 0, 1}
 // are put back on the inverse.  Other patches take the complex path.
 // CL: one patch per thread-block cluster; the cluster's CTAs share every
 // dense step (Team<true>), which spreads a large patch over several SMs.
+// rpack (optional, one byte per patch): a real-path patch then stores its
+// inverse as the real matrix w with A^-1[r][c] = w[r][c] i^(s_r - s_c) (s = 1
+// on p-hat DOFs), n rows of patch_ldr(n) reals at the start of its block, and
+// sets rpack[j] = 1; a complex patch stores the complex inverse and sets 0.
+// The smoother then streams half the bytes of a real patch (smoother.cuh).
 __device__ __forceinline__ unsigned cluster_rank() {
   unsigned r;
   asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
@@ -344,7 +345,7 @@ template <class C, bool CL>
 __global__ void __launch_bounds__(CTA_THREADS) k_patch_invert(const int64_t* ptr, const int32_t* pdofs,
                                                             const int64_t* vptr, C* vals, C* scratch,
                                                             const int64_t* soff, const int64_t* order, int64_t j0,
-                                                            int64_t offU, int* info) {
+                                                            int64_t offU, int* info, uint8_t* rpack) {
   extern __shared__ unsigned char shraw[];
   C* sh = reinterpret_cast<C*>(shraw);
   Team<CL> tm;
@@ -387,6 +388,15 @@ __global__ void __launch_bounds__(CTA_THREADS) k_patch_invert(const int64_t* ptr
     tm.sync();
     cta_herk_lower_tri<R, CL>(Mr, n, n, Wr, n, shr, tm);
     tm.sync();
+    if (rpack) {   // real rows of length ldr (padding columns 0) over the L^-1 copy, no longer read
+      const int ldr = (int)patch_ldr(n);
+      for (int q = threadIdx.x; q < n * ldr; q += blockDim.x) {
+        const int r = q / ldr, c = q % ldr;
+        if (tm.own_row(r / TL)) Mr[q] = c < n ? tm.ld(&Wr[(size_t)r * n + c]) : R(0);
+      }
+      if (threadIdx.x == 0 && tm.rank == 0) rpack[j] = 1;
+      return;
+    }
     for (int q = threadIdx.x; q < n * ld; q += blockDim.x) {
       const int r = q / ld, c = q % ld;
       if (!tm.own_row(r / TL)) continue;
@@ -395,6 +405,7 @@ __global__ void __launch_bounds__(CTA_THREADS) k_patch_invert(const int64_t* ptr
     }
     return;
   }
+  if (rpack && threadIdx.x == 0 && tm.rank == 0) rpack[j] = 0;
   for (int q = threadIdx.x; q < n * n; q += blockDim.x)
     if (tm.own_row((q / n) / TL)) W[q] = M[(size_t)(q / n) * ld + q % n];
   tm.sync();
@@ -486,7 +497,7 @@ static int patch_team(const Patches& P, int64_t max_n) {
 
 template <class C>
 static void invert_patches(Alloc& A, PatchDev& D, const LevelPlan& lp, C* vals, int64_t offU, int* dinfo,
-                           cudaStream_t st) {
+                           cudaStream_t st, uint8_t* rpack = nullptr) {
   const Patches& P = lp.P;
   const size_t sm = (size_t)(NB * NB + 2 * TL * NB) * sizeof(C) + 64;
   DPG_CUDA(cudaFuncSetAttribute(k_patch_invert<C, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
@@ -536,13 +547,13 @@ static void invert_patches(Alloc& A, PatchDev& D, const LevelPlan& lp, C* vals, 
     const int64_t j0 = starts[c], q = starts[c + 1];
     if (team == 1) {
       k_patch_invert<C, false><<<(unsigned)(q - j0), CTA_THREADS, sm, st>>>(D.ptr, D.dofs, D.val_ptr, vals, scratch,
-                                                                          soff, dorder, j0, offU, dinfo);
+                                                                          soff, dorder, j0, offU, dinfo, rpack);
       DPG_CHECK_LAUNCH();
     } else {
       cfg.gridDim = dim3((unsigned)((q - j0) * team));
       DPG_CUDA(cudaLaunchKernelEx(&cfg, k_patch_invert<C, true>, (const int64_t*)D.ptr, (const int32_t*)D.dofs,
                                   (const int64_t*)D.val_ptr, vals, scratch, (const int64_t*)soff,
-                                  (const int64_t*)dorder, j0, offU, dinfo));
+                                  (const int64_t*)dorder, j0, offU, dinfo, rpack));
       count_launch();
     }
   }
@@ -597,7 +608,7 @@ static void setup_recompute(Alloc& A, PatchDev& D, const LevelPlan& lp, int64_t 
     k_patch_gather<float2><<<(unsigned)(q1 - q0), 256, 0, st>>>(Aop, D.ptr, D.dofs, D.wvptr, D.wbuf, q0, D.worder);
     DPG_CHECK_LAUNCH();
     k_patch_invert<float2, false><<<(unsigned)(q1 - q0), CTA_THREADS, sm, st>>>(
-        D.ptr, D.dofs, D.wvptr, D.wbuf, D.wscratch, D.wsoff, D.worder, q0, offU, dinfo);
+        D.ptr, D.dofs, D.wvptr, D.wbuf, D.wscratch, D.wsoff, D.worder, q0, offU, dinfo, nullptr);
     DPG_CHECK_LAUNCH();
   }
 }
@@ -611,11 +622,11 @@ void patch_recompute_apply(const Level& L, const float2* r, float2* pbuf, cudaSt
     k_patch_gather<float2><<<(unsigned)(q1 - q0), 256, 0, st>>>(L.A, D.ptr, D.dofs, D.wvptr, D.wbuf, q0, D.worder);
     DPG_CHECK_LAUNCH();
     k_patch_invert<float2, false><<<(unsigned)(q1 - q0), CTA_THREADS, smi, st>>>(
-        D.ptr, D.dofs, D.wvptr, D.wbuf, D.wscratch, D.wsoff, D.worder, q0, L.mesh.offU, D.winfo);
+        D.ptr, D.dofs, D.wvptr, D.wbuf, D.wscratch, D.wsoff, D.worder, q0, L.mesh.offU, D.winfo, nullptr);
     DPG_CHECK_LAUNCH();
     const int64_t c0 = D.wch[w], c1 = D.wch[w + 1];
     k_patch_apply<float2, float2, 2><<<(unsigned)(c1 - c0), 256, sma, st>>>(D.ptr, D.dofs, D.wvptr, D.wchunks + c0,
-                                                                            D.wbuf, r, pbuf);
+                                                                            D.wbuf, r, pbuf, nullptr, 0);
     DPG_CHECK_LAUNCH();
   }
 }
@@ -639,7 +650,7 @@ void patch_recompute_apply_blk(const Level& L, const float2* r, int64_t ldr, flo
     k_patch_gather<float2><<<(unsigned)(q1 - q0), 256, 0, st>>>(L.A, D.ptr, D.dofs, D.wvptr, D.wbuf, q0, D.worder);
     DPG_CHECK_LAUNCH();
     k_patch_invert<float2, false><<<(unsigned)(q1 - q0), CTA_THREADS, smi, st>>>(
-        D.ptr, D.dofs, D.wvptr, D.wbuf, D.wscratch, D.wsoff, D.worder, q0, L.mesh.offU, D.winfo);
+        D.ptr, D.dofs, D.wvptr, D.wbuf, D.wscratch, D.wsoff, D.worder, q0, L.mesh.offU, D.winfo, nullptr);
     DPG_CHECK_LAUNCH();
     const int64_t c0 = D.wch[w], c1 = D.wch[w + 1];
     for (int g = 0; g < K; g += BLK_MAX) {
@@ -647,7 +658,8 @@ void patch_recompute_apply_blk(const Level& L, const float2* r, int64_t ldr, flo
       const size_t sm = (size_t)kb * D.max_n * sizeof(float2) + 16;
 #define DPG_RC_BLK(KB)                                                                                     \
   k_patch_apply_blk<float2, float2, 2, KB><<<(unsigned)(c1 - c0), 256, sm, st>>>(                          \
-      D.ptr, D.dofs, D.wvptr, D.wchunks + c0, D.wbuf, r + (int64_t)g * ldr, ldr, pbuf + (int64_t)g * ldp, ldp)
+      D.ptr, D.dofs, D.wvptr, D.wchunks + c0, D.wbuf, r + (int64_t)g * ldr, ldr, pbuf + (int64_t)g * ldp, ldp, \
+      nullptr, 0)
       if (kb == 4) DPG_RC_BLK(4);
       else if (kb == 3) DPG_RC_BLK(3);
       else if (kb == 2) DPG_RC_BLK(2);
@@ -667,6 +679,7 @@ static void setup_patches(SystemImpl& S, Level& F, const LevelPlan& lp, int* din
   D.nvals = P.val_ptr.back();
   D.max_n = lp.max_n;
   D.sum_sq = lp.sum_sq;
+  D.offU = F.mesh.offU;
   D.ptr = upload(A, P.ptr, st);
   D.dofs = upload(A, P.dofs, st);
   D.val_ptr = upload(A, P.val_ptr, st);
@@ -686,7 +699,12 @@ static void setup_patches(SystemImpl& S, Level& F, const LevelPlan& lp, int* din
     D.inv32 = A.arr<float2>((size_t)std::max<int64_t>(D.nvals, 1));
     k_patch_gather<float2><<<(unsigned)D.np, 256, 0, st>>>(F.A, D.ptr, D.dofs, D.val_ptr, D.inv32, 0);
     DPG_CHECK_LAUNCH();
-    invert_patches<float2>(A, D, lp, D.inv32, F.mesh.offU, dinfo, st);
+    // real-path patches keep real inverses (half the smoother's bytes for them)
+    if (!(S.op.flags & DPGMG_FLAG_PATCH_COMPLEX)) {
+      D.rflag = A.arr<uint8_t>((size_t)std::max<int64_t>(D.np, 1));
+      DPG_CUDA(cudaMemsetAsync(D.rflag, 0, (size_t)std::max<int64_t>(D.np, 1), st));
+    }
+    invert_patches<float2>(A, D, lp, D.inv32, F.mesh.offU, dinfo, st, D.rflag);
     return;
   }
   D.inv64 = A.arr<double2>((size_t)D.nvals);

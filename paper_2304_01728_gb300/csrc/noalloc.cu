@@ -16,6 +16,7 @@
 // every call (a cheap query), so a context the caller has reset and recreated
 // in between is never given a stale address.
 #include <cstdint>
+#include <type_traits>
 
 #include "common.cuh"
 #include "internal.h"
@@ -54,7 +55,9 @@ static void na_smooth(const Level& L, const C* inv_full, const C* inv_half, cons
     const size_t sm = (size_t)P.max_n * sizeof(C) + 16;
     int64_t nch = 0;
     const int2* chunks = patch_chunks(P, PatchCols<C>::per, &nch);
-    k_patch_apply<C, double2><<<(unsigned)nch, 256, sm, st>>>(P.ptr, P.dofs, P.val_ptr, chunks, inv_full, r, scratch);
+    const uint8_t* rflag = std::is_same<C, float2>::value ? P.rflag : nullptr;   // packed complex64 inverses only
+    k_patch_apply<C, double2><<<(unsigned)nch, 256, sm, st>>>(P.ptr, P.dofs, P.val_ptr, chunks, inv_full, r, scratch,
+                                                              rflag, P.offU);
   }
   DPG_CHECK_LAUNCH();
   k_slot_sum<C, double2><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(P.slot_ptr, P.slots, scratch, y, n, L.theta, 0);

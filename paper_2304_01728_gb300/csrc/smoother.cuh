@@ -13,6 +13,7 @@
 // column sum), see k_patch_apply_h.  Used for complex64 operators; patches
 // up to HALF_MAX_N DOFs (the shared-memory buffers scale with n_j).
 #pragma once
+#include <type_traits>
 #include "common.cuh"
 #include "host_mesh.h"
 #include "internal.h"
@@ -29,6 +30,12 @@ template <class C> __device__ __forceinline__ C warp_sum_s(C v) {
   return v;
 }
 
+// v * i^s for s in {-1, 0, 1}: a swap of the components and one sign, exact
+template <class C>
+__device__ __forceinline__ C mul_i(C v, int s) {
+  return s == 0 ? v : (s > 0 ? Ops<C>::mk(-v.y, v.x) : Ops<C>::mk(v.y, -v.x));
+}
+
 // conversions between the operator precision C and the vectors' type
 template <class C, class V> __device__ __forceinline__ C cvt_in(V v) {
   return Ops<C>::mk((typename Ops<C>::R)v.x, (typename Ops<C>::R)v.y);
@@ -37,6 +44,119 @@ template <class C, class V> __device__ __forceinline__ C cvt_in(V v) {
 // patch inverses are read once per application: streaming loads (evict first)
 template <class C> __device__ __forceinline__ C ld_stream(const C* p) { return __ldcs(p); }
 
+// 16-byte asynchronous global -> shared copies (cp.async, L2 only); each thread
+// later reads back only what it copied itself, after waiting on its own groups.
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async4(void* smem, const void* gmem) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N> __device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+// acc + w r for a real w: two real FMAs instead of a complex product
+template <class C>
+__device__ __forceinline__ C rfma(typename Ops<C>::R w, C r, C acc) {
+  if constexpr (std::is_same<C, float2>::value) return make_float2(fmaf(w, r.x, acc.x), fmaf(w, r.y, acc.y));
+  else return Ops<C>::mk(::fma(w, r.x, acc.x), ::fma(w, r.y, acc.y));
+}
+
+// The work item (patch with a real packed block, first column a0, 32 PER
+// columns) of k_patch_apply.  Rows have ldr = patch_ldr(n) reals (Wb = row 0);
+// a lane reads 4 columns with one 16-byte copy, 8 PER lanes cover a row and a
+// warp 4 / PER rows at a time (warp w: rows w 4/PER + lane / (8 PER) + 32 i).
+// Each thread streams its rows through a shared-memory ring of REAL_RING
+// cp.async copies, the first of them issued before the right-hand-side
+// gather, so that the gather's dependent loads overlap the stream and the
+// rows in flight hold no registers.  Then: shuffles combine the lanes that
+// share columns, the 8 warp partials are summed in a fixed order, and the
+// output phase is applied.  The start of the patch's slots passes through
+// shared memory (sb), so no 64-bit value stays live across the stream.
+constexpr int REAL_RING = 5;
+
+template <class TIN, int PER>
+__device__ __forceinline__ void patch_apply_real(const int32_t* __restrict__ dofs, const float* __restrict__ Wb,
+                                                 const TIN* __restrict__ r, float2* __restrict__ pbuf, int64_t b,
+                                                 int n, int a0, int64_t offU, float2* rj,
+                                                 float2 (*part)[32 * PER + 1], int64_t* sb) {
+  constexpr int LPR = 8 * PER, RPI = 4 / PER, STEP = 8 * RPI;
+  __shared__ float4 ring[REAL_RING][256];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int cg = lane % LPR, ro = lane / LPR;
+  const int a = a0 + 4 * cg;   // columns a .. a + 3 lie within the padded row when a < n
+  const bool act = a < n;
+  const float4* W4 = reinterpret_cast<const float4*>(Wb + a);
+  const int s4 = (int)(patch_ldr(n) / 4), ds = STEP * s4;   // offsets below n ldr / 4 < 2^31
+  const int k0 = w * RPI + ro;
+#pragma unroll
+  for (int d = 0; d < REAL_RING; ++d) {
+    if (act && k0 + d * STEP < n) cp_async16(&ring[d][threadIdx.x], W4 + (k0 * s4 + d * ds));
+    cp_async_commit();
+  }
+  if (threadIdx.x == 0) *sb = b;
+  for (int q = threadIdx.x; q < n; q += blockDim.x) {
+    const int32_t g = dofs[b + q];
+    rj[q] = mul_i(cvt_in<float2>(r[g]), g < offU ? -1 : 0);
+  }
+  __syncthreads();
+  float2 acc[4];
+#pragma unroll
+  for (int c = 0; c < 4; ++c) acc[c] = make_float2(0.f, 0.f);
+  if (act) {
+    const int nr = k0 < n ? (n - k0 + STEP - 1) / STEP : 0;   // this thread's rows
+    const float4* src = W4 + (k0 * s4 + REAL_RING * ds);      // the next row to copy
+    const float2* rp = rj + k0;
+    int d = 0;
+    for (int i = 0; i < nr; ++i, rp += STEP, src += ds) {
+      cp_async_wait<REAL_RING - 1>();   // this thread's oldest copy (its row i) has landed
+      const float4 m0 = ring[d][threadIdx.x];
+      const float2 rv = *rp;
+      acc[0] = rfma<float2>(m0.x, rv, acc[0]);
+      acc[1] = rfma<float2>(m0.y, rv, acc[1]);
+      acc[2] = rfma<float2>(m0.z, rv, acc[2]);
+      acc[3] = rfma<float2>(m0.w, rv, acc[3]);
+      // refill the slot with row i + REAL_RING (m0 has been read above)
+      if (i + REAL_RING < nr) cp_async16(&ring[d][threadIdx.x], src);
+      cp_async_commit();
+      d = d + 1 == REAL_RING ? 0 : d + 1;
+    }
+  }
+  cp_async_wait<0>();
+#pragma unroll
+  for (int o = LPR; o < 32; o <<= 1)
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      acc[c].x += __shfl_xor_sync(0xffffffffu, acc[c].x, o);
+      acc[c].y += __shfl_xor_sync(0xffffffffu, acc[c].y, o);
+    }
+  if (ro == 0)
+#pragma unroll
+    for (int c = 0; c < 4; ++c) part[w][4 * cg + c] = acc[c];
+  __syncthreads();
+  if (w == 0) {
+    const int64_t b2 = *sb;
+#pragma unroll
+    for (int u = 0; u < PER; ++u) {
+      const int c = a0 + PER * lane + u;
+      if (c < n) {
+        float2 s2 = part[0][PER * lane + u];
+#pragma unroll
+        for (int q = 1; q < 8; ++q) s2 = Ops<float2>::add(s2, part[q][PER * lane + u]);
+        pbuf[b2 + c] = mul_i(s2, dofs[b2 + c] < offU ? 1 : 0);
+      }
+    }
+  }
+}
+
 // Rows of a stored block have length ld = patch_ld(n) (even).  Work item
 // (patch j, first column a0) of COLS columns; lane `lane` of warp w handles
 // columns a0 + PER * lane .. + PER - 1 (PER = 1 for complex128, 2 for
@@ -44,11 +164,17 @@ template <class C> __device__ __forceinline__ C ld_stream(const C* p) { return _
 template <class C> struct PatchCols { static constexpr int per = 1; };
 template <> struct PatchCols<float2> { static constexpr int per = 2; };
 
-template <class C, class TIN, int PER = PatchCols<C>::per>
-__global__ void __launch_bounds__(256, PER == 2 ? 8 : 3) k_patch_apply(const int64_t* __restrict__ ptr, const int32_t* __restrict__ dofs,
+// A patch with rflag[j] set holds a real packed block w (A^-1[k][a] =
+// w[k][a] i^(s_k - s_a), s = 1 on p-hat DOFs, global index < offU):
+//   y_a = sum_k conj(A^-1[k][a]) r_k = i^(s_a) sum_k w[k][a] (i^(-s_k) r_k),
+// so the gathered r carries the phase i^(-s_k), the sum is real-times-complex
+// and the output the phase i^(s_a); all three phase steps are exact.
+template <class C, class TIN, int PER = PatchCols<C>::per, int MINB = (PER == 2 ? 8 : 3)>
+__global__ void __launch_bounds__(256, MINB) k_patch_apply(const int64_t* __restrict__ ptr, const int32_t* __restrict__ dofs,
                                                      const int64_t* __restrict__ vptr, const int2* __restrict__ chunks,
                                                      const C* __restrict__ inv, const TIN* __restrict__ r,
-                                                     C* __restrict__ pbuf) {
+                                                     C* __restrict__ pbuf, const uint8_t* __restrict__ rflag,
+                                                     int64_t offU) {
   extern __shared__ unsigned char shraw[];
   __shared__ C part[8][32 * PER + 1];
   C* rj = reinterpret_cast<C*>(shraw);
@@ -57,6 +183,14 @@ __global__ void __launch_bounds__(256, PER == 2 ? 8 : 3) k_patch_apply(const int
   const int64_t j = ch.x;
   const int64_t b = ptr[j];
   const int n = (int)(ptr[j + 1] - b);
+  if constexpr (std::is_same<C, float2>::value) {   // only complex64 inverses are packed
+    if (rflag != nullptr && rflag[j] != 0) {         // uniform over the CTA
+      __shared__ int64_t sb;
+      patch_apply_real<TIN, PER>(dofs, reinterpret_cast<const float*>(inv + vptr[j]), r, pbuf, b, n, ch.y, offU, rj,
+                                 part, &sb);
+      return;
+    }
+  }
   const int64_t ld = patch_ld(n);
   for (int q = threadIdx.x; q < n; q += blockDim.x) rj[q] = cvt_in<C>(r[dofs[b + q]]);
   __syncthreads();
@@ -128,17 +262,28 @@ inline const int2* patch_chunks(const PatchDev& P, int per, int64_t* n) {
   return per == 2 ? P.chunks64 : P.chunks;
 }
 
-// complex64 smoother product with the tuned columns per lane (1 or 2)
+// Variants of the complex64 smoother product, tuned per level at setup:
+// 1 = one column per lane (32-column work items), 2 = two columns per lane
+// (64-column work items, 8 CTAs per SM, 32 registers), 3 = two columns per
+// lane at 6 CTAs per SM (40 registers: the real packed path then keeps its
+// loads in registers).
+constexpr int SMOOTH_PER2_WIDE = 3;
+
 template <class TIN>
-inline void launch_patch_apply_c64(const PatchDev& P, int per, const float2* inv, const TIN* r, float2* pbuf,
+inline void launch_patch_apply_c64(const PatchDev& P, int variant, const float2* inv, const TIN* r, float2* pbuf,
                                    cudaStream_t st) {
   const size_t sm = (size_t)P.max_n * sizeof(float2) + 16;
   int64_t nch = 0;
-  const int2* chunks = patch_chunks(P, per, &nch);
-  if (per == 2)
-    k_patch_apply<float2, TIN, 2><<<(unsigned)nch, 256, sm, st>>>(P.ptr, P.dofs, P.val_ptr, chunks, inv, r, pbuf);
+  const int2* chunks = patch_chunks(P, variant == 1 ? 1 : 2, &nch);
+  if (variant == SMOOTH_PER2_WIDE)
+    k_patch_apply<float2, TIN, 2, 6><<<(unsigned)nch, 256, sm, st>>>(P.ptr, P.dofs, P.val_ptr, chunks, inv, r, pbuf,
+                                                                     P.rflag, P.offU);
+  else if (variant == 2)
+    k_patch_apply<float2, TIN, 2><<<(unsigned)nch, 256, sm, st>>>(P.ptr, P.dofs, P.val_ptr, chunks, inv, r, pbuf,
+                                                                  P.rflag, P.offU);
   else
-    k_patch_apply<float2, TIN, 1><<<(unsigned)nch, 256, sm, st>>>(P.ptr, P.dofs, P.val_ptr, chunks, inv, r, pbuf);
+    k_patch_apply<float2, TIN, 1><<<(unsigned)nch, 256, sm, st>>>(P.ptr, P.dofs, P.val_ptr, chunks, inv, r, pbuf,
+                                                                  P.rflag, P.offU);
   DPG_CHECK_LAUNCH();
 }
 

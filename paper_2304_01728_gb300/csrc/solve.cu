@@ -823,12 +823,15 @@ void split_df(const double2* v, float2* hi, float2* lo, int64_t n, cudaStream_t 
 // with the error-free products and sums of the CG operator.  One column per
 // lane (32-column work items), warp w takes rows k = w + 8 i with two
 // accumulator pairs; the 8 warp partials are combined in a fixed order and
-// written in complex128.
+// written in complex128.  LO = false also reads the real packed blocks of
+// k_patch_apply (rflag[j] set): phase i^(-s_k) on the gathered r, real
+// products, phase i^(s_a) on the output.
 template <bool LO>
 __global__ void __launch_bounds__(256) k_patch_apply_df(const int64_t* __restrict__ ptr, const int32_t* __restrict__ dofs,
                                                         const int64_t* __restrict__ vptr, const int2* __restrict__ chunks,
                                                         const float2* __restrict__ Mh, const float2* __restrict__ Ml,
-                                                        const double2* __restrict__ r, double2* __restrict__ pbuf) {
+                                                        const double2* __restrict__ r, double2* __restrict__ pbuf,
+                                                        const uint8_t* __restrict__ rflag, int64_t offU) {
   extern __shared__ unsigned char shraw[];
   float4* rj = reinterpret_cast<float4*>(shraw);   // (re_hi, re_lo, im_hi, im_lo) per patch DOF
   __shared__ float4 part[8][33];
@@ -837,8 +840,10 @@ __global__ void __launch_bounds__(256) k_patch_apply_df(const int64_t* __restric
   const int64_t b = ptr[j];
   const int n = (int)(ptr[j + 1] - b);
   const int64_t ld = patch_ld(n);
+  const bool rp = !LO && rflag != nullptr && rflag[j] != 0;
   for (int q = threadIdx.x; q < n; q += blockDim.x) {
-    const double2 v = r[dofs[b + q]];
+    const int32_t g = dofs[b + q];
+    const double2 v = mul_i(r[g], rp && g < offU ? -1 : 0);
     const float hx = (float)v.x, hy = (float)v.y;
     rj[q] = make_float4(hx, (float)(v.x - (double)hx), hy, (float)(v.y - (double)hy));
   }
@@ -846,7 +851,34 @@ __global__ void __launch_bounds__(256) k_patch_apply_df(const int64_t* __restric
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int a = ch.y + lane;
   float rh0 = 0.f, rl0 = 0.f, ih0 = 0.f, il0 = 0.f, rh1 = 0.f, rl1 = 0.f, ih1 = 0.f, il1 = 0.f;
-  if (a < n) {
+  if (a < n && rp) {
+    const float* Wt = reinterpret_cast<const float*>(Mh + vptr[j]) + a;
+    const int64_t ldr = patch_ldr(n);
+    int k = w;
+    float p, q;
+    for (; k + 8 < n; k += 16) {
+      const float w0 = __ldcs(Wt + (int64_t)k * ldr), w1 = __ldcs(Wt + (int64_t)(k + 8) * ldr);
+      const float4 x0 = rj[k], x1 = rj[k + 8];
+      df_mul(w0, 0.f, x0.x, x0.y, p, q);
+      df_add(rh0, rl0, p, q);
+      df_mul(w0, 0.f, x0.z, x0.w, p, q);
+      df_add(ih0, il0, p, q);
+      df_mul(w1, 0.f, x1.x, x1.y, p, q);
+      df_add(rh1, rl1, p, q);
+      df_mul(w1, 0.f, x1.z, x1.w, p, q);
+      df_add(ih1, il1, p, q);
+    }
+    if (k < n) {
+      const float w0 = __ldcs(Wt + (int64_t)k * ldr);
+      const float4 x0 = rj[k];
+      df_mul(w0, 0.f, x0.x, x0.y, p, q);
+      df_add(rh0, rl0, p, q);
+      df_mul(w0, 0.f, x0.z, x0.w, p, q);
+      df_add(ih0, il0, p, q);
+    }
+    df_add(rh0, rl0, rh1, rl1);
+    df_add(ih0, il0, ih1, il1);
+  } else if (a < n) {
     const float2* H = Mh + vptr[j] + a;
     const float2* Lo = LO ? Ml + vptr[j] + a : nullptr;
     int k = w;
@@ -898,7 +930,8 @@ __global__ void __launch_bounds__(256) k_patch_apply_df(const int64_t* __restric
       df_add(s4.x, s4.y, o.x, o.y);
       df_add(s4.z, s4.w, o.z, o.w);
     }
-    pbuf[b + a] = make_double2((double)s4.x + (double)s4.y, (double)s4.z + (double)s4.w);
+    const double2 o = make_double2((double)s4.x + (double)s4.y, (double)s4.z + (double)s4.w);
+    pbuf[b + a] = rp ? mul_i(o, dofs[b + a] < offU ? 1 : 0) : o;
   }
 }
 
@@ -911,10 +944,10 @@ static void smooth_df(const Level& F, const float2* plo, const double2* r, doubl
   const size_t sm = (size_t)P.max_n * sizeof(float4) + 16;
   if (plo)
     k_patch_apply_df<true><<<(unsigned)P.nchunks, 256, sm, st>>>(P.ptr, P.dofs, P.val_ptr, P.chunks, P.inv32, plo, r,
-                                                                  pbuf);
+                                                                  pbuf, nullptr, 0);
   else
     k_patch_apply_df<false><<<(unsigned)P.nchunks, 256, sm, st>>>(P.ptr, P.dofs, P.val_ptr, P.chunks, P.inv32,
-                                                                   nullptr, r, pbuf);
+                                                                   nullptr, r, pbuf, P.rflag, P.offU);
   DPG_CHECK_LAUNCH();
   k_slot_sum<double2, double2><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(P.slot_ptr, P.slots, pbuf, y, n, 1.0, 0);
   DPG_CHECK_LAUNCH();
@@ -936,14 +969,15 @@ static void configure_smoother_kernels() {
 template <class C> static void patch_product(const PatchDev& P, const C* inv, const C* r, C* pbuf, cudaStream_t st);
 template <>
 void patch_product<float2>(const PatchDev& P, const float2* inv, const float2* r, float2* pbuf, cudaStream_t st) {
-  launch_patch_apply_c64<float2>(P, P.cols, inv, r, pbuf, st);
+  launch_patch_apply_c64<float2>(P, P.variant, inv, r, pbuf, st);
 }
 template <>
 void patch_product<double2>(const PatchDev& P, const double2* inv, const double2* r, double2* pbuf, cudaStream_t st) {
   const size_t sm = (size_t)P.max_n * sizeof(double2) + 16;
   int64_t nch = 0;
   const int2* chunks = patch_chunks(P, 1, &nch);
-  k_patch_apply<double2, double2><<<(unsigned)nch, 256, sm, st>>>(P.ptr, P.dofs, P.val_ptr, chunks, inv, r, pbuf);
+  k_patch_apply<double2, double2><<<(unsigned)nch, 256, sm, st>>>(P.ptr, P.dofs, P.val_ptr, chunks, inv, r, pbuf,
+                                                                  nullptr, 0);
   DPG_CHECK_LAUNCH();
 }
 
@@ -1495,12 +1529,13 @@ static void patch_apply_blk_launch(const PatchDev& P, int per, const C* inv, con
   const size_t sm = (size_t)KB * P.max_n * sizeof(C) + 16;
   int64_t nch = 0;
   const int2* chunks = patch_chunks(P, per, &nch);
+  const uint8_t* rflag = std::is_same<C, float2>::value ? P.rflag : nullptr;   // packed complex64 inverses only
   if (per == 2)
     k_patch_apply_blk<C, C, 2, KB><<<(unsigned)nch, 256, sm, st>>>(P.ptr, P.dofs, P.val_ptr, chunks, inv, r, ldr,
-                                                                   pbuf, ldp);
+                                                                   pbuf, ldp, rflag, P.offU);
   else
     k_patch_apply_blk<C, C, 1, KB><<<(unsigned)nch, 256, sm, st>>>(P.ptr, P.dofs, P.val_ptr, chunks, inv, r, ldr,
-                                                                   pbuf, ldp);
+                                                                   pbuf, ldp, rflag, P.offU);
   DPG_CHECK_LAUNCH();
 }
 
@@ -1949,11 +1984,14 @@ void prepare_solve(SystemImpl& S, cudaStream_t st) {
       DPG_CUDA(cudaMemsetAsync(x, 0, (size_t)n * sizeof(float2), st));
       F.A.gsel[0] = pick_group(key, ev, st, [&](int G) { spmv_g<float2>(F.A, F.A.v32, x, nullptr, y, 0, G, st); });
       if (F.P.inv32 && F.P.np) {
-        // smoother product: 1 or 2 columns per lane (32- or 64-column work items)
-        const TuneKey skey{3, F.mesh.p, F.kind, log2i(F.P.np)};
-        F.P.cols = pick_variant(skey, ev, st, {2, 1}, [&](int c) {
-          launch_patch_apply_c64<float2>(F.P, c, F.P.inv32, x, W.w32[l].pbuf, st);
-        });
+        // smoother product: 1 or 2 columns per lane (32- or 64-column work
+        // items), the latter at 8 or 6 CTAs per SM; the block smoother takes
+        // the same columns per lane
+        const TuneKey skey{F.P.rflag ? 4 : 3, F.mesh.p, F.kind, log2i(F.P.np)};   // packed real blocks or not
+        auto run = [&](int c) { launch_patch_apply_c64<float2>(F.P, c, F.P.inv32, x, W.w32[l].pbuf, st); };
+        F.P.variant = F.P.rflag ? pick_variant(skey, ev, st, {SMOOTH_PER2_WIDE, 2, 1}, run)
+                                : pick_variant(skey, ev, st, {2, SMOOTH_PER2_WIDE, 1}, run);
+        F.P.cols = F.P.variant == 1 ? 1 : 2;
       }
     } else {
       double2 *x = W.w64[l].x, *y = W.w64[l].t;
@@ -1984,7 +2022,8 @@ int pcg_solve(SystemImpl& S, cudaStream_t st, double2* xout, dpgmg_stats* stats,
   {
     const Level& Ff = S.levels.back();
     const int64_t esz = S.op.precision == DPGMG_PREC_MIXED ? 8 : 16;
-    if (S.prof_which == DPGMG_PROF_SMOOTH_FINE) S.prof_bytes = Ff.P.sum_sq * esz;   // full-storage algorithmic bytes
+    if (S.prof_which == DPGMG_PROF_SMOOTH_FINE)   // stored entries read once: real packed blocks at half size
+      S.prof_bytes = (Ff.P.sum_sq - Ff.P.real_sq) * esz + Ff.P.real_sq * (esz / 2);
     else if (S.prof_which == DPGMG_PROF_SPMV_FINE) S.prof_bytes = Ff.A.nnz_alg * esz;
     else if (S.prof_which == DPGMG_PROF_SPMV_CG) S.prof_bytes = A.nnz_alg * 16;   // hi + lo complex64
   }
