@@ -524,7 +524,7 @@ def run_gb300(args, rank, world, local_rank):
                        "fp64_cg_c128": one(dict(precision="fp64", flags=D.FLAG_CG_C128)),
                        "mixed_patch_factors_fp64": one(dict(flags=D.FLAG_PATCH_FP64)),
                        "mixed_coarsest_cuda_cores": one(dict(flags=D.FLAG_CUDA_CORES)),
-                       "mixed_patches_all_complex64": one(dict(flags=D.FLAG_PATCH_COMPLEX))}
+                       "mixed_all_complex64_storage": one(dict(flags=D.FLAG_COMPLEX_STORAGE))}
     D.dpgmg_destroy(h)
 
 

@@ -182,15 +182,18 @@ typedef struct dpgmg_opts {
    Mixed path only, without DPGMG_FLAG_PATCH_FP64 and DPGMG_FLAG_CG_C128
    (ARG otherwise); dpgmg_smooth_noalloc is not available (ARG). */
 #define DPGMG_FLAG_RECOMPUTE_PATCHES 128
-/* Mixed path: keep every stored patch inverse as a complex64 block.  By
-   default a patch whose block is real once the unit phases of the real form
-   are taken out (every element touching it has no impedance face and a real
-   source: Sec. 2, impedance condition) keeps its FP32-factored inverse as a
-   real matrix w, A_j^-1[r][c] = w[r][c] i^(s_r - s_c) with s = 1 on p-hat
-   DOFs, at half the bytes, and the smoother applies the phases exactly.  The
-   products then differ from the complex64 ones by FP32 rounding order only;
-   this flag is the comparison. */
-#define DPGMG_FLAG_PATCH_COMPLEX 256
+/* Mixed path: keep every stored matrix of the solve in complex64 (the
+   comparison for the default real packing).  By default a block that is real
+   once the unit phases of the real form are taken out (p-hat DOFs carry i;
+   true of everything that only elements without an impedance face and with a
+   real source touch: Sec. 2, impedance condition) is stored as reals at half
+   the bytes:
+     patch inverses: A_j^-1[r][c] = w[r][c] i^(s_r - s_c), s = 1 on p-hat DOFs;
+     operators (V-cycle complex64 values, and the CG operator's high and low
+     parts): every row of an entity whose entries are all of that form.
+   The products apply the phases exactly; their results differ from the
+   complex64 ones by FP32 rounding order only. */
+#define DPGMG_FLAG_COMPLEX_STORAGE 256
 /* Host-made failures for testing the error paths (the paper has no
    counterpart; no GPU fault is involved):
    FAULT_NOT_HPD: the host overwrites the first diagonal entry of the dense
@@ -230,7 +233,8 @@ typedef struct dpgmg_level_desc {
   long long patch_stored;  /* stored patch-inverse entries (sum n_j^2, or sum n_j(n_j+1)/2 in
                               Hermitian half storage) */
   long long patch_real_sq; /* sum of n_j^2 over the patches whose inverses are stored as real
-                              blocks (mixed path, see DPGMG_FLAG_PATCH_COMPLEX): half the bytes */
+                              blocks (mixed path, see DPGMG_FLAG_COMPLEX_STORAGE): half the bytes */
+  long long op_real_nnz;   /* entries of the level's complex64 operator stored as reals (the same) */
 } dpgmg_level_desc;
 
 typedef struct dpgmg_handle_s* dpgmg_handle;
@@ -396,11 +400,13 @@ long long dpgmg_launch_count(void);
  * per row with the column indices loaded one step ahead of the gathers they
  * feed, or (G = 32) by one warp per row with the warp's stream of values and
  * column indices copied 8 steps ahead into shared memory by asynchronous
- * copies (cp.async).  dpgmg_setup times every variant on each operator and
+ * copies (cp.async), or (G = 64, V-cycle operators only) by one half-warp
+ * per row, two rows of a warp at a time.  dpgmg_setup times every variant on each operator and
  * keeps the fastest; choices are cached per (product type, p, level kind,
  * log2 of the row count) for the life of the process.  level >= 1 addresses
  * that level's V-cycle operator, level == -1 the CG operator.  set = 1, 2, 4,
- * 8, 16 or 32 overrides the choice (0 leaves it); *group (may be NULL)
+ * 8, 16, 32 or 64 overrides the choice (0 leaves it; 64 is refused for the CG
+ * operator); *group (may be NULL)
  * receives the value in force.  Returns DPGMG_ERR_ARG for an invalid level or
  * size.  Results do not depend on the variant beyond rounding order (G = 1,
  * 16 and 32: bitwise). */

@@ -86,7 +86,7 @@ int validate_problem(const dpgmg_problem* pb, const dpgmg_opts* op) {
        op->coarsest != DPGMG_COARSEST_AUTO && op->coarsest != DPGMG_COARSEST_SMOOTH) ||
       (op->flags & ~(DPGMG_FLAG_EAGER | DPGMG_FLAG_CUDA_CORES | DPGMG_FLAG_STORE_COARSE | DPGMG_FLAG_WARM_START |
                      DPGMG_FLAG_CG_C128 | DPGMG_FLAG_PATCH_FP64 | DPGMG_FLAG_PATCH_R2 |
-                     DPGMG_FLAG_RECOMPUTE_PATCHES | DPGMG_FLAG_PATCH_COMPLEX | DPGMG_FLAG_FAULT_NOT_HPD |
+                     DPGMG_FLAG_RECOMPUTE_PATCHES | DPGMG_FLAG_COMPLEX_STORAGE | DPGMG_FLAG_FAULT_NOT_HPD |
                      DPGMG_FLAG_FAULT_TC_WAIT)))
     return DPGMG_ERR_ARG;
   // recompute mode: the mixed path's FP32 patch factors and complex64 damping estimate only
@@ -195,17 +195,23 @@ static void fill_bytes_per_iter(SystemImpl& S) {
   const double esz = mixed ? 8.0 : 16.0;
   double b = 0;
   const Level& F = S.levels.back();
-  // CG operator (FP64)
-  int64_t cg_nnz = 0;
-  if (S.levels.size() > 1 && F.kind == 1) cg_nnz = F.A.nnz_alg;
-  else cg_nnz = (int64_t)(F.mesh.nelem * (double)F.nloc * F.nloc * 0.8);
-  b += cg_nnz * 16.0;
+  // CG operator (FP64 as complex64 high and low parts; packed real entities half)
+  int64_t cg_nnz = 0, cg_real = 0;
+  if (const ECSRDev* cg = cg_operator_of(S)) {
+    cg_nnz = cg->nnz_alg;
+    cg_real = cg->nnz_real;
+  } else if (S.levels.size() > 1 && F.kind == 1) {
+    cg_nnz = F.A.nnz_alg;
+  } else {
+    cg_nnz = (int64_t)(F.mesh.nelem * (double)F.nloc * F.nloc * 0.8);
+  }
+  b += (cg_nnz - cg_real) * 16.0 + cg_real * 8.0;
   const int nu = S.op.nu_pre + S.op.nu_post;
   for (size_t l = 1; l < S.levels.size(); ++l) {
     const Level& L = S.levels[l];
     b += nu * ((double)(L.P.sum_sq - L.P.real_sq) + 0.5 * (double)L.P.real_sq) * esz;  // smoother (n_j^2 per
                                                                                       // patch, real ones half)
-    b += std::max(1, nu) * (double)L.A.nnz_alg * esz;                            // residual SpMVs
+    b += std::max(1, nu) * ((double)(L.A.nnz_alg - L.A.nnz_real) + 0.5 * (double)L.A.nnz_real) * esz;  // SpMVs
     if (L.kind == 2) b += (double)L.nK * (2.0 * L.nI * L.nS + L.nI * L.nI) * esz; // condense + backsub
   }
   const Level& C0 = S.levels[0];
@@ -283,7 +289,9 @@ void setup_system(SystemImpl& S, const dpgmg_problem* pb, const dpgmg_opts* op, 
   S.t_phase[3] = S.ph_side ? span(5, 6) : 0.0;
   S.t_phase[4] = span(3, 4);
   S.t_phase[5] = span(4, 7);
-  // patches whose inverses are stored as real blocks (half the bytes per entry)
+  // operators and patches stored as reals (half the bytes per entry)
+  for (size_t l = 1; l < S.levels.size(); ++l) S.levels[l].A.nnz_real = packed_entries(S.levels[l].A);
+  if (ECSRDev* cg = cg_operator_of(S)) cg->nnz_real = packed_entries(*cg);
   for (size_t l = 1; l < S.levels.size() && S.plan; ++l) {
     PatchDev& P = S.levels[l].P;
     P.real_sq = 0;
@@ -674,7 +682,9 @@ int dpgmg_setup_phases(dpgmg_handle h, dpgmg_system sys, double* ms, int n) {
 
 int dpgmg_spmv_group(dpgmg_handle h, dpgmg_system sys, int level, int set, int* group) {
   if (!h || !sys) return DPGMG_ERR_ARG;
-  if (set != 0 && set != 1 && set != 2 && set != 4 && set != 8 && set != 16 && set != 32) return DPGMG_ERR_ARG;
+  if (set != 0 && set != 1 && set != 2 && set != 4 && set != 8 && set != 16 && set != 32 && set != 64)
+    return DPGMG_ERR_ARG;
+  if (level == -1 && set == 64) return DPGMG_ERR_ARG;   // no half-warp form of the CG operator
   std::lock_guard<std::mutex> lk(h->mu);
   SystemImpl& S = sys->s;
   const int slot = S.op.precision == DPGMG_PREC_MIXED ? 0 : 1;
@@ -709,6 +719,7 @@ int dpgmg_level_info(dpgmg_handle h, dpgmg_system sys, int level, dpgmg_level_de
   out->theta = L.theta;
   out->patch_stored = L.P.recompute ? 0 : (L.P.half ? L.P.nhvals : L.P.nvals);
   out->patch_real_sq = L.P.real_sq;
+  out->op_real_nnz = L.A.nnz_real;
   return DPGMG_OK;
 }
 

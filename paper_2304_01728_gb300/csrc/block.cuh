@@ -173,7 +173,8 @@ __global__ void __launch_bounds__(256) k_spmv_blk(const int32_t* __restrict__ ro
                                                   const int32_t* __restrict__ col_idx,
                                                   const int64_t* __restrict__ val_ptr, const C* __restrict__ v,
                                                   const C* __restrict__ x, const C* __restrict__ b, C* __restrict__ y,
-                                                  int64_t ld, int64_t nrows, int mode) {
+                                                  int64_t ld, int64_t nrows, int mode,
+                                                  const uint8_t* __restrict__ rent, int64_t offU) {
   using O = Ops<C>;
   const int lane = threadIdx.x & 31;
   const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
@@ -190,6 +191,36 @@ __global__ void __launch_bounds__(256) k_spmv_blk(const int32_t* __restrict__ ro
       int k = lane;
       int cA = k < nnz ? __ldg(cols + k) : 0;
       int cB = k + 32 < nnz ? __ldg(cols + k + 32) : 0;
+      const bool real = rent != nullptr && rent[E] != 0;   // packed real entity (complex64 values only)
+      if (real) {
+        using R = typename Ops<C>::R;
+        const R* a = reinterpret_cast<const R*>(v + val_ptr[E]) + (row - ent_start[E]) * nnz;
+        for (; k + 32 < nnz; k += 64) {
+          const R w0 = __ldcs(a + k), w1 = __ldcs(a + k + 32);
+          const int sA = cA < offU ? -1 : 0, sB = cB < offU ? -1 : 0;
+          C x0[KB], x1[KB];
+#pragma unroll
+          for (int kb = 0; kb < KB; ++kb) {
+            x0[kb] = mul_i(x[kb * ld + cA], sA);
+            x1[kb] = mul_i(x[kb * ld + cB], sB);
+          }
+          const int kn = k + 64;
+          cA = kn < nnz ? __ldg(cols + kn) : 0;
+          cB = kn + 32 < nnz ? __ldg(cols + kn + 32) : 0;
+#pragma unroll
+          for (int kb = 0; kb < KB; ++kb) {
+            acc[kb] = rfma<C>(w0, x0[kb], acc[kb]);
+            acc[kb] = rfma<C>(w1, x1[kb], acc[kb]);
+          }
+        }
+        if (k < nnz) {
+          const R w0 = __ldcs(a + k);
+          const int sA = cA < offU ? -1 : 0;
+#pragma unroll
+          for (int kb = 0; kb < KB; ++kb) acc[kb] = rfma<C>(w0, mul_i(x[kb * ld + cA], sA), acc[kb]);
+        }
+        k = nnz;   // the complex loop below has nothing left
+      }
       for (; k + 32 < nnz; k += 64) {   // two columns per lane per step, indices one step ahead
         const C v0 = __ldcs(vals + k), v1 = __ldcs(vals + k + 32);
         C x0[KB], x1[KB];
@@ -213,7 +244,10 @@ __global__ void __launch_bounds__(256) k_spmv_blk(const int32_t* __restrict__ ro
         for (int kb = 0; kb < KB; ++kb) acc[kb] = O::fma(v0, x[kb * ld + cA], acc[kb]);
       }
 #pragma unroll
-      for (int kb = 0; kb < KB; ++kb) acc[kb] = warp_sum_s(acc[kb]);
+      for (int kb = 0; kb < KB; ++kb) {
+        acc[kb] = warp_sum_s(acc[kb]);
+        if (real) acc[kb] = mul_i(acc[kb], row < offU ? 1 : 0);
+      }
     }
     if (lane < KB) {
       C mine = acc[0];

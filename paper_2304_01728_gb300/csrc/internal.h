@@ -69,6 +69,13 @@ struct ECSRDev {
   double2* v64 = nullptr;
   float2* v32 = nullptr;   // complex64 values (= high parts of the double-float split)
   float2* vlo = nullptr;   // low parts: v64 ~ v32 + vlo (CG operator only)
+  // rent[E] = 1: row entity E's rows are real once the unit phases are taken
+  // out (A[r][c] = a[r][c] i^(s_r - s_c), s = 1 on DOFs below offU), and v32
+  // (and vlo) hold the reals a: rows of nnz(E) reals from float offset
+  // 2 val_ptr[E] (k_pack_ops).  Null: every entity complex64.
+  uint8_t* rent = nullptr;
+  int64_t offU = 0;
+  int64_t nnz_real = 0;    // entries of the packed entities (host copy, after setup)
   // Entity-blocked SpMV work lists: tasks[i] = (entity, first row) groups of
   // G = 2^i rows of one entity (i = 1, 2, 3); rows with no entity are listed
   // in null_rows.  gsel[] is the group size chosen by the tuner for the
@@ -299,7 +306,13 @@ void spmv64(const ECSRDev& A, const double2* x, double2* y, cudaStream_t st);
 // inverses their high parts in P.inv32 and low parts in plo)
 void estimate_theta(SystemImpl& S, int level, double* rayleigh, const float2* plo, cudaStream_t st);
 // double-float split of an operator's values: v32 (kept if already set) + vlo
-void split_operator(Alloc& M, ECSRDev& A, cudaStream_t st);
+void split_operator(Alloc& M, ECSRDev& A, int64_t offU, bool pack, cudaStream_t st);
+void operator_c64(Alloc& M, ECSRDev& A, int64_t offU, bool pack, cudaStream_t st);
+int64_t packed_entries(const ECSRDev& A);
+// mixed path: real entities of operators and real patch inverses stored as reals
+inline bool pack_storage(const SystemImpl& S) {
+  return S.op.precision == DPGMG_PREC_MIXED && !(S.op.flags & DPGMG_FLAG_COMPLEX_STORAGE);
+}
 // hi + lo = v (complex64 parts of complex128 values)
 void split_df(const double2* v, float2* hi, float2* lo, int64_t n, cudaStream_t st);
 double theta_from_rayleigh(double num, double den);

@@ -700,7 +700,7 @@ static void setup_patches(SystemImpl& S, Level& F, const LevelPlan& lp, int* din
     k_patch_gather<float2><<<(unsigned)D.np, 256, 0, st>>>(F.A, D.ptr, D.dofs, D.val_ptr, D.inv32, 0);
     DPG_CHECK_LAUNCH();
     // real-path patches keep real inverses (half the smoother's bytes for them)
-    if (!(S.op.flags & DPGMG_FLAG_PATCH_COMPLEX)) {
+    if (pack_storage(S)) {
       D.rflag = A.arr<uint8_t>((size_t)std::max<int64_t>(D.np, 1));
       DPG_CUDA(cudaMemsetAsync(D.rflag, 0, (size_t)std::max<int64_t>(D.np, 1), st));
     }
@@ -943,12 +943,12 @@ void build_hierarchy(SystemImpl& S, cudaStream_t st) {
     const bool c128 = (S.op.flags & DPGMG_FLAG_CG_C128) != 0;
     if (!(S.op.theta > 0.0) && !c128 && patches_fp32(S)) {
       // estimate in the V-cycle's complex64 arithmetic (its operator and FP32-factored smoother)
-      if (!F.A.v32) F.A.v32 = to_c64(A, F.A.v64, F.A.nnz, st);
+      if (!F.A.v32) operator_c64(A, F.A, F.mesh.offU, pack_storage(S), st);
     } else if (!(S.op.theta > 0.0) && !c128) {   // double-float estimate
       Pd.inv32 = A.arr<float2>((size_t)std::max<int64_t>(Pd.nvals, 1));
       plo = A.arr<float2>((size_t)std::max<int64_t>(Pd.nvals, 1));
       split_df(Pd.inv64, Pd.inv32, plo, Pd.nvals, st);
-      if (!F.A.vlo) split_operator(A, F.A, st);
+      if (!F.A.vlo) split_operator(A, F.A, F.mesh.offU, pack_storage(S), st);
     }
     estimate_theta(S, l, dtheta + 2 * l, plo, st);
     if (plo) A.release(plo);
@@ -965,7 +965,7 @@ void build_hierarchy(SystemImpl& S, cudaStream_t st) {
       }
     }
     if (mixed) {
-      if (!F.A.v32) F.A.v32 = to_c64(A, F.A.v64, F.A.nnz, st);
+      if (!F.A.v32) operator_c64(A, F.A, F.mesh.offU, pack_storage(S), st);
       if (kHalfStorageSmoother && Pd.max_n <= HALF_MAX_N && Pd.inv64) {
         // complex64 Hermitian half storage: lower triangles packed by rows
         std::vector<int64_t> hp(Pd.np + 1, 0), pp(Pd.np + 1);

@@ -121,19 +121,82 @@ template <class C> __device__ __forceinline__ C warp_sum(C v) {
 }
 
 // ------------------------------------------------------------------ SpMV
-// mode 0: y = A x; mode 1: y = b - A x.  One warp per row.
+// A row of a packed real entity (k_pack_ops): the lane's part of
+// sum_c a[r][c] (i^(-s_c) x_c) over columns k = lane, lane + 32, ...: four
+// columns per lane per step (the 4-byte values leave room for more loads in
+// flight), then two, then one, with two accumulators alternating by column;
+// PF: each step's column indices loaded one step ahead.  The same order for
+// both PF forms (bitwise equal results).  The caller sums the lanes and
+// applies i^(s_r).
+template <bool PF>
+__device__ __forceinline__ float2 spmv_real_row(const float* __restrict__ a, const int32_t* __restrict__ cols,
+                                                int nnz, const float2* __restrict__ x, int64_t offU, int lane) {
+  float2 acc = make_float2(0.f, 0.f), acc1 = make_float2(0.f, 0.f);
+  auto xs = [&](int c) { return mul_i(x[c], c < offU ? -1 : 0); };
+  int k = lane;
+  int ci[4] = {0, 0, 0, 0};
+  if (PF)
+#pragma unroll
+    for (int u = 0; u < 4; ++u) ci[u] = k + 32 * u < nnz ? __ldg(cols + k + 32 * u) : 0;
+  for (; k + 96 < nnz; k += 128) {
+    float w[4];
+    float2 xv[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) w[u] = __ldcs(a + k + 32 * u);
+#pragma unroll
+    for (int u = 0; u < 4; ++u) xv[u] = xs(PF ? ci[u] : cols[k + 32 * u]);
+    if (PF) {
+      const int kn = k + 128;
+#pragma unroll
+      for (int u = 0; u < 4; ++u) ci[u] = kn + 32 * u < nnz ? __ldg(cols + kn + 32 * u) : 0;
+    }
+#pragma unroll
+    for (int u = 0; u < 4; u += 2) {
+      acc = rfma<float2>(w[u], xv[u], acc);
+      acc1 = rfma<float2>(w[u + 1], xv[u + 1], acc1);
+    }
+  }
+  // at most three columns left (k + 96 >= nnz); ci[] holds the indices of k, k + 32, k + 64
+  if (k + 32 < nnz) {
+    const float w0 = __ldcs(a + k), w1 = __ldcs(a + k + 32);
+    const float2 x0 = xs(PF ? ci[0] : cols[k]), x1 = xs(PF ? ci[1] : cols[k + 32]);
+    acc = rfma<float2>(w0, x0, acc);
+    acc1 = rfma<float2>(w1, x1, acc1);
+    if (PF) {
+      ci[0] = ci[2];
+      ci[1] = ci[3];
+    }
+    k += 64;
+  }
+  if (k < nnz) acc = rfma<float2>(__ldcs(a + k), xs(PF ? ci[0] : cols[k]), acc);
+  return make_float2(acc.x + acc1.x, acc.y + acc1.y);
+}
+
+// mode 0: y = A x; mode 1: y = b - A x.  One warp per row.  rent: packed
+// real entities (complex64 values only; null otherwise).
 template <class C>
 __global__ void __launch_bounds__(256) k_spmv(const int32_t* __restrict__ row_ent, const int64_t* __restrict__ ent_start,
                                               const int64_t* __restrict__ col_ptr, const int32_t* __restrict__ col_idx,
                                               const int64_t* __restrict__ val_ptr, const C* __restrict__ v,
                                               const C* __restrict__ x, const C* __restrict__ b, C* __restrict__ y,
-                                              int64_t nrows, int mode) {
+                                              int64_t nrows, int mode, const uint8_t* __restrict__ rent,
+                                              int64_t offU) {
   using O = Ops<C>;
   const int lane = threadIdx.x & 31;
   const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
   for (int64_t row = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); row < nrows; row += nw) {
     const int32_t E = row_ent[row];
     C acc = O::zero();
+    if constexpr (std::is_same<C, float2>::value) {
+      if (E >= 0 && rent != nullptr && rent[E] != 0) {
+        const int64_t c0 = col_ptr[E];
+        const int nnz = (int)(col_ptr[E + 1] - c0);
+        const float* a = reinterpret_cast<const float*>(v + val_ptr[E]) + (row - ent_start[E]) * nnz;
+        acc = mul_i(warp_sum(spmv_real_row<false>(a, col_idx + c0, nnz, x, offU, lane)), row < offU ? 1 : 0);
+        if (lane == 0) y[row] = mode ? O::sub(b[row], acc) : acc;
+        continue;
+      }
+    }
     if (E >= 0) {
       const int64_t c0 = col_ptr[E];
       const int nnz = (int)(col_ptr[E + 1] - c0);
@@ -154,6 +217,74 @@ __global__ void __launch_bounds__(256) k_spmv(const int32_t* __restrict__ row_en
   }
 }
 
+// The same product with one row per half-warp: two rows of a warp in flight
+// at once, so that twice the rows' dependent loads (entity tables, column
+// indices, gathered x) overlap.  16 lanes per row, columns k = h, h + 16, ...
+// (h = lane within the half) in two accumulators alternating by column;
+// packed real entities as in k_spmv.  A different summation order from
+// k_spmv: equal to rounding.
+template <class C>
+__global__ void __launch_bounds__(256) k_spmv_hw(const int32_t* __restrict__ row_ent,
+                                                 const int64_t* __restrict__ ent_start,
+                                                 const int64_t* __restrict__ col_ptr,
+                                                 const int32_t* __restrict__ col_idx,
+                                                 const int64_t* __restrict__ val_ptr, const C* __restrict__ v,
+                                                 const C* __restrict__ x, const C* __restrict__ b, C* __restrict__ y,
+                                                 int64_t nrows, int mode, const uint8_t* __restrict__ rent,
+                                                 int64_t offU) {
+  using O = Ops<C>;
+  const int lane = threadIdx.x & 31, h = lane & 15;
+  const int64_t nh = (int64_t)gridDim.x * (blockDim.x >> 4);   // half-warps of the grid
+  // the loop bound depends on the warp only: both halves run every trip (full-warp shuffles)
+  for (int64_t base = 2 * (blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5)); base < nrows; base += nh) {
+    const int64_t row = base + (lane >> 4);
+    C acc = O::zero(), acc1 = O::zero();
+    bool real = false;
+    const int32_t E = row < nrows ? row_ent[row] : -1;
+    if (E >= 0) {
+      const int64_t c0 = col_ptr[E];
+      const int nnz = (int)(col_ptr[E + 1] - c0);
+      const int32_t* cols = col_idx + c0;
+      const int64_t roff = (row - ent_start[E]) * nnz;
+      if constexpr (std::is_same<C, float2>::value) real = rent != nullptr && rent[E] != 0;
+      if (real) {
+        if constexpr (std::is_same<C, float2>::value) {
+          const float* a = reinterpret_cast<const float*>(v + val_ptr[E]) + roff;
+          int k = h;
+          for (; k + 16 < nnz; k += 32) {
+            const float w0 = __ldcs(a + k), w1 = __ldcs(a + k + 16);
+            const int cA = cols[k], cB = cols[k + 16];
+            acc = rfma<float2>(w0, mul_i(x[cA], cA < offU ? -1 : 0), acc);
+            acc1 = rfma<float2>(w1, mul_i(x[cB], cB < offU ? -1 : 0), acc1);
+          }
+          if (k < nnz) {
+            const int cA = cols[k];
+            acc = rfma<float2>(__ldcs(a + k), mul_i(x[cA], cA < offU ? -1 : 0), acc);
+          }
+        }
+      } else {
+        const C* vals = v + val_ptr[E] + roff;
+        int k = h;
+        for (; k + 16 < nnz; k += 32) {
+          const C v0 = __ldcs(vals + k), v1 = __ldcs(vals + k + 16);
+          const int cA = cols[k], cB = cols[k + 16];
+          acc = O::fma(v0, x[cA], acc);
+          acc1 = O::fma(v1, x[cB], acc1);
+        }
+        if (k < nnz) acc = O::fma(__ldcs(vals + k), x[cols[k]], acc);
+      }
+    }
+    acc = O::add(acc, acc1);
+#pragma unroll
+    for (int o = 8; o > 0; o >>= 1) {
+      acc.x += __shfl_xor_sync(0xffffffffu, acc.x, o);
+      acc.y += __shfl_xor_sync(0xffffffffu, acc.y, o);
+    }
+    if (real) acc = mul_i(acc, row < offU ? 1 : 0);
+    if (h == 0 && row < nrows) y[row] = mode ? O::sub(b[row], acc) : acc;
+  }
+}
+
 // The same product with the column indices of the next step loaded one step
 // ahead, so that each step waits on the gathered x entries only (the index ->
 // gather chain of k_spmv is the latency it is bound by).  Identical
@@ -165,13 +296,24 @@ __global__ void __launch_bounds__(256) k_spmv_pf(const int32_t* __restrict__ row
                                                  const int32_t* __restrict__ col_idx,
                                                  const int64_t* __restrict__ val_ptr, const C* __restrict__ v,
                                                  const C* __restrict__ x, const C* __restrict__ b, C* __restrict__ y,
-                                                 int64_t nrows, int mode) {
+                                                 int64_t nrows, int mode, const uint8_t* __restrict__ rent,
+                                                 int64_t offU) {
   using O = Ops<C>;
   const int lane = threadIdx.x & 31;
   const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
   for (int64_t row = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); row < nrows; row += nw) {
     const int32_t E = row_ent[row];
     C acc = O::zero();
+    if constexpr (std::is_same<C, float2>::value) {
+      if (E >= 0 && rent != nullptr && rent[E] != 0) {
+        const int64_t c0 = col_ptr[E];
+        const int nnz = (int)(col_ptr[E + 1] - c0);
+        const float* a = reinterpret_cast<const float*>(v + val_ptr[E]) + (row - ent_start[E]) * nnz;
+        acc = mul_i(warp_sum(spmv_real_row<true>(a, col_idx + c0, nnz, x, offU, lane)), row < offU ? 1 : 0);
+        if (lane == 0) y[row] = mode ? O::sub(b[row], acc) : acc;
+        continue;
+      }
+    }
     if (E >= 0) {
       const int64_t c0 = col_ptr[E];
       const int nnz = (int)(col_ptr[E + 1] - c0);
@@ -314,7 +456,7 @@ __global__ void __launch_bounds__(256) k_spmv_ent(const int2* __restrict__ tasks
                                                   const int32_t* __restrict__ col_idx,
                                                   const int64_t* __restrict__ val_ptr, const C* __restrict__ v,
                                                   const C* __restrict__ x, const C* __restrict__ b, C* __restrict__ y,
-                                                  int mode) {
+                                                  int mode, const uint8_t* __restrict__ rent, int64_t offU) {
   using O = Ops<C>;
   const int lane = threadIdx.x & 31;
   const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
@@ -329,7 +471,19 @@ __global__ void __launch_bounds__(256) k_spmv_ent(const int2* __restrict__ tasks
     C acc[G];
 #pragma unroll
     for (int r = 0; r < G; ++r) acc[r] = O::zero();
-    for (int k = lane; k < nnz; k += 32) {
+    const bool real = rent != nullptr && rent[E] != 0;   // packed real entity (complex64 values only)
+    if (real) {
+      using R = typename Ops<C>::R;
+      const R* a = reinterpret_cast<const R*>(v + val_ptr[E]) + (int64_t)r0 * nnz;
+      for (int k = lane; k < nnz; k += 32) {
+        const int c = cols[k];
+        const C xv = mul_i(x[c], c < offU ? -1 : 0);
+#pragma unroll
+        for (int r = 0; r < G; ++r)
+          if (r < g) acc[r] = rfma<C>(__ldcs(a + (int64_t)r * nnz + k), xv, acc[r]);
+      }
+    }
+    for (int k = real ? nnz : lane; k < nnz; k += 32) {
       const C xv = x[cols[k]];
 #pragma unroll
       for (int r = 0; r < G; ++r)
@@ -343,6 +497,7 @@ __global__ void __launch_bounds__(256) k_spmv_ent(const int2* __restrict__ tasks
     }
     if (lane < g) {
       const int64_t row = ent_start[E] + r0 + lane;
+      if (real) mine = mul_i(mine, row < offU ? 1 : 0);
       y[row] = mode ? O::sub(b[row], mine) : mine;
     }
   }
@@ -367,8 +522,24 @@ template <> struct SpmvSlot<double2> { static constexpr int v = 1; };
 // per warp with the (value, index) stream prefetched by cp.async (k_spmv_ring)
 constexpr int SPMV_PF = 16;
 constexpr int SPMV_RING = 32;   // one row per warp, (value, index) stream prefetched by cp.async
+constexpr int SPMV_HALF = 64;   // one row per half-warp (k_spmv_hw)
+// complex64 values with packed real entities: every SpMV but the cp.async
+// ring variant reads them
+template <class C> static const uint8_t* packed_rows(const ECSRDev& A) {
+  return std::is_same<C, float2>::value ? A.rent : nullptr;
+}
+
 template <class C>
 static void spmv_g(const ECSRDev& A, const C* vals, const C* x, const C* b, C* y, int mode, int G, cudaStream_t st) {
+  const uint8_t* rent = packed_rows<C>(A);
+  if (rent && G == SPMV_RING) G = SPMV_PF;   // the ring kernel reads complex64 values only
+  if (G == SPMV_HALF) {
+    int64_t blocks = std::min<int64_t>((A.nrows + 15) / 16, 152 * 16);
+    k_spmv_hw<C><<<(unsigned)blocks, 256, 0, st>>>(A.row_ent, A.ent_start, A.col_ptr, A.col_idx, A.val_ptr, vals, x,
+                                                    b, y, A.nrows, mode, rent, A.offU);
+    DPG_CHECK_LAUNCH();
+    return;
+  }
   if (G == SPMV_RING) {
     int64_t blocks = std::min<int64_t>((A.nrows + 7) / 8, 152 * 8);
     k_spmv_ring<C><<<(unsigned)blocks, 256, 0, st>>>(A.row_ent, A.ent_start, A.col_ptr, A.col_idx, A.val_ptr, vals, x,
@@ -379,14 +550,14 @@ static void spmv_g(const ECSRDev& A, const C* vals, const C* x, const C* b, C* y
   if (G == SPMV_PF) {
     int64_t blocks = std::min<int64_t>((A.nrows + 7) / 8, 152 * 16);
     k_spmv_pf<C><<<(unsigned)blocks, 256, 0, st>>>(A.row_ent, A.ent_start, A.col_ptr, A.col_idx, A.val_ptr, vals, x,
-                                                    b, y, A.nrows, mode);
+                                                    b, y, A.nrows, mode, rent, A.offU);
     DPG_CHECK_LAUNCH();
     return;
   }
   if (G <= 1 || !A.tasks[1]) {
     int64_t blocks = std::min<int64_t>((A.nrows + 7) / 8, 152 * 16);
     k_spmv<C><<<(unsigned)blocks, 256, 0, st>>>(A.row_ent, A.ent_start, A.col_ptr, A.col_idx, A.val_ptr, vals, x, b,
-                                                 y, A.nrows, mode);
+                                                 y, A.nrows, mode, rent, A.offU);
     DPG_CHECK_LAUNCH();
     return;
   }
@@ -395,13 +566,13 @@ static void spmv_g(const ECSRDev& A, const C* vals, const C* x, const C* b, C* y
   const unsigned blocks = (unsigned)std::min<int64_t>((nt + 7) / 8, 152 * 16);
   if (G == 2)
     k_spmv_ent<C, 2><<<blocks, 256, 0, st>>>(A.tasks[gi], nt, A.ent_start, A.ent_nd, A.col_ptr, A.col_idx, A.val_ptr,
-                                             vals, x, b, y, mode);
+                                             vals, x, b, y, mode, rent, A.offU);
   else if (G == 4)
     k_spmv_ent<C, 4><<<blocks, 256, 0, st>>>(A.tasks[gi], nt, A.ent_start, A.ent_nd, A.col_ptr, A.col_idx, A.val_ptr,
-                                             vals, x, b, y, mode);
+                                             vals, x, b, y, mode, rent, A.offU);
   else
     k_spmv_ent<C, 8><<<blocks, 256, 0, st>>>(A.tasks[gi], nt, A.ent_start, A.ent_nd, A.col_ptr, A.col_idx, A.val_ptr,
-                                             vals, x, b, y, mode);
+                                             vals, x, b, y, mode, rent, A.offU);
   DPG_CHECK_LAUNCH();
   if (A.n_null) {
     k_null_rows<C><<<(unsigned)((A.n_null + 255) / 256), 256, 0, st>>>(A.null_rows, A.n_null, b, y, mode);
@@ -465,7 +636,8 @@ __global__ void __launch_bounds__(256) k_spmv_df(const int32_t* __restrict__ row
                                                  const int64_t* __restrict__ val_ptr, const float2* __restrict__ vh,
                                                  const float2* __restrict__ vl, const float2* __restrict__ xh,
                                                  const float2* __restrict__ xl, const double2* __restrict__ b,
-                                                 double2* __restrict__ y, int64_t nrows, int mode) {
+                                                 double2* __restrict__ y, int64_t nrows, int mode,
+                                                 const uint8_t* __restrict__ rent, int64_t offU) {
   __shared__ float4 res[DF_ROWS];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int64_t base = (int64_t)blockIdx.x * DF_ROWS;
@@ -484,7 +656,36 @@ __global__ void __launch_bounds__(256) k_spmv_df(const int32_t* __restrict__ row
         pA = __ldg(cols + lane);
         pB = lane + 32 < nnz ? __ldg(cols + lane + 32) : pA;
       }
-      for (int k = lane; k < nnz; k += 64) {
+      const bool real = rent != nullptr && rent[E] != 0;
+      if (real) {   // packed real entity (k_pack_ops): a = ah + al, x_c carries i^(-s_c)
+        const float* ahr = reinterpret_cast<const float*>(vh + val_ptr[E]) + (row - ent_start[E]) * nnz;
+        const float* alr = reinterpret_cast<const float*>(vl + val_ptr[E]) + (row - ent_start[E]) * nnz;
+        for (int k = lane; k < nnz; k += 64) {
+          const bool two = k + 32 < nnz;
+          const float ah0 = __ldcs(ahr + k), al0 = __ldcs(alr + k);
+          const int cA = PF ? pA : cols[k];
+          const float ah1 = two ? __ldcs(ahr + k + 32) : 0.f, al1 = two ? __ldcs(alr + k + 32) : 0.f;
+          const int cB = PF ? pB : (two ? cols[k + 32] : cA);
+          const int sA = cA < offU ? -1 : 0, sB = cB < offU ? -1 : 0;
+          const float2 uh0 = mul_i(xh[cA], sA), ul0 = mul_i(xl[cA], sA);
+          const float2 uh1 = mul_i(xh[cB], sB), ul1 = mul_i(xl[cB], sB);
+          if (PF) {
+            const int kn = k + 64;
+            pA = kn < nnz ? __ldg(cols + kn) : 0;
+            pB = kn + 32 < nnz ? __ldg(cols + kn + 32) : pA;
+          }
+          float p, q;
+          df_mul(ah0, al0, uh0.x, ul0.x, p, q);
+          df_add(rh, rl, p, q);
+          df_mul(ah0, al0, uh0.y, ul0.y, p, q);
+          df_add(ih, il, p, q);
+          df_mul(ah1, al1, uh1.x, ul1.x, p, q);
+          df_add(rh, rl, p, q);
+          df_mul(ah1, al1, uh1.y, ul1.y, p, q);
+          df_add(ih, il, p, q);
+        }
+      }
+      for (int k = real ? nnz : lane; k < nnz; k += 64) {
         // two columns per lane per step, all loads issued before the arithmetic
         const bool two = k + 32 < nnz;
         const float2 ah0 = __ldcs(vh + off + k), al0 = __ldcs(vl + off + k);
@@ -518,6 +719,13 @@ __global__ void __launch_bounds__(256) k_spmv_df(const int32_t* __restrict__ row
       }
       df_warp_sum(rh, rl);
       df_warp_sum(ih, il);
+      if (real && row < offU) {   // output phase i^(s_r): (re, im) -> (-im, re), exact
+        const float th = rh, tl = rl;
+        rh = -ih;
+        rl = -il;
+        ih = th;
+        il = tl;
+      }
     }
     if (lane == 0) res[w * (DF_ROWS / 8) + i] = make_float4(rh, rl, ih, il);
   }
@@ -617,7 +825,8 @@ __global__ void __launch_bounds__(256) k_spmv_df_ent(const int2* __restrict__ ta
                                                      const int64_t* __restrict__ val_ptr, const float2* __restrict__ vh,
                                                      const float2* __restrict__ vl, const float2* __restrict__ xh,
                                                      const float2* __restrict__ xl, const double2* __restrict__ b,
-                                                     double2* __restrict__ y, int mode) {
+                                                     double2* __restrict__ y, int mode,
+                                                     const uint8_t* __restrict__ rent, int64_t offU) {
   const int lane = threadIdx.x & 31;
   const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
   for (int64_t t = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); t < ntasks; t += nw) {
@@ -631,7 +840,28 @@ __global__ void __launch_bounds__(256) k_spmv_df_ent(const int2* __restrict__ ta
     float rh[G], rl[G], ih[G], il[G];
 #pragma unroll
     for (int r = 0; r < G; ++r) rh[r] = rl[r] = ih[r] = il[r] = 0.f;
-    for (int k = lane; k < nnz; k += 32) {
+    const bool real = rent != nullptr && rent[E] != 0;   // packed real entity (k_pack_ops)
+    if (real) {
+      const float* ahr = reinterpret_cast<const float*>(vh + val_ptr[E]) + (int64_t)r0 * nnz;
+      const float* alr = reinterpret_cast<const float*>(vl + val_ptr[E]) + (int64_t)r0 * nnz;
+      for (int k = lane; k < nnz; k += 32) {
+        const int c = cols[k];
+        const int sc = c < offU ? -1 : 0;
+        const float2 uh = mul_i(xh[c], sc), ul = mul_i(xl[c], sc);
+#pragma unroll
+        for (int r = 0; r < G; ++r) {
+          if (r < g) {
+            const float ah = __ldcs(ahr + (int64_t)r * nnz + k), al = __ldcs(alr + (int64_t)r * nnz + k);
+            float p, q;
+            df_mul(ah, al, uh.x, ul.x, p, q);
+            df_add(rh[r], rl[r], p, q);
+            df_mul(ah, al, uh.y, ul.y, p, q);
+            df_add(ih[r], il[r], p, q);
+          }
+        }
+      }
+    }
+    for (int k = real ? nnz : lane; k < nnz; k += 32) {
       const int c = cols[k];
       const float2 uh = xh[c], ul = xl[c];
 #pragma unroll
@@ -659,6 +889,7 @@ __global__ void __launch_bounds__(256) k_spmv_df_ent(const int2* __restrict__ ta
     }
     if (lane < g) {
       const int64_t row = ent_start[E] + r0 + lane;
+      if (real && row < offU) mine = make_float4(-mine.z, -mine.w, mine.x, mine.y);   // i^(s_r), exact
       const double re = (double)mine.x + (double)mine.y, im = (double)mine.z + (double)mine.w;
       y[row] = mode ? make_double2(b[row].x - re, b[row].y - im) : make_double2(re, im);
     }
@@ -689,6 +920,7 @@ __global__ void k_split_vals(const double2* __restrict__ v, float2* __restrict__
 static void spmv_df_g(const ECSRDev& A, const float2* xh, const float2* xl, const double2* b, double2* y, int mode,
                       int G, cudaStream_t st) {
   const int64_t n = A.nrows;
+  if (A.rent && G == SPMV_RING) G = SPMV_PF;   // the ring kernel reads complex64 values only
   if (G == SPMV_RING) {
     const int64_t blocks = std::min<int64_t>((n + 7) / 8, 152 * 5);
     k_spmv_df_ring<<<(unsigned)blocks, 256, 0, st>>>(A.row_ent, A.ent_start, A.col_ptr, A.col_idx, A.val_ptr, A.v32,
@@ -700,10 +932,10 @@ static void spmv_df_g(const ECSRDev& A, const float2* xh, const float2* xl, cons
     const int64_t blocks = (n + DF_ROWS - 1) / DF_ROWS;
     if (G == SPMV_PF)
       k_spmv_df<true><<<(unsigned)blocks, 256, 0, st>>>(A.row_ent, A.ent_start, A.col_ptr, A.col_idx, A.val_ptr,
-                                                        A.v32, A.vlo, xh, xl, b, y, n, mode);
+                                                        A.v32, A.vlo, xh, xl, b, y, n, mode, A.rent, A.offU);
     else
       k_spmv_df<false><<<(unsigned)blocks, 256, 0, st>>>(A.row_ent, A.ent_start, A.col_ptr, A.col_idx, A.val_ptr,
-                                                         A.v32, A.vlo, xh, xl, b, y, n, mode);
+                                                         A.v32, A.vlo, xh, xl, b, y, n, mode, A.rent, A.offU);
     DPG_CHECK_LAUNCH();
     return;
   }
@@ -712,13 +944,13 @@ static void spmv_df_g(const ECSRDev& A, const float2* xh, const float2* xl, cons
   const unsigned blocks = (unsigned)std::min<int64_t>((nt + 7) / 8, 152 * 16);
   if (G == 2)
     k_spmv_df_ent<2><<<blocks, 256, 0, st>>>(A.tasks[gi], nt, A.ent_start, A.ent_nd, A.col_ptr, A.col_idx, A.val_ptr,
-                                             A.v32, A.vlo, xh, xl, b, y, mode);
+                                             A.v32, A.vlo, xh, xl, b, y, mode, A.rent, A.offU);
   else if (G == 4)
     k_spmv_df_ent<4><<<blocks, 256, 0, st>>>(A.tasks[gi], nt, A.ent_start, A.ent_nd, A.col_ptr, A.col_idx, A.val_ptr,
-                                             A.v32, A.vlo, xh, xl, b, y, mode);
+                                             A.v32, A.vlo, xh, xl, b, y, mode, A.rent, A.offU);
   else
     k_spmv_df_ent<8><<<blocks, 256, 0, st>>>(A.tasks[gi], nt, A.ent_start, A.ent_nd, A.col_ptr, A.col_idx, A.val_ptr,
-                                             A.v32, A.vlo, xh, xl, b, y, mode);
+                                             A.v32, A.vlo, xh, xl, b, y, mode, A.rent, A.offU);
   DPG_CHECK_LAUNCH();
   if (A.n_null) {
     k_null_rows<double2><<<(unsigned)((A.n_null + 255) / 256), 256, 0, st>>>(A.null_rows, A.n_null, b, y, mode);
@@ -739,7 +971,8 @@ __global__ void __launch_bounds__(256) k_spmv_df_blk(const int32_t* __restrict__
                                                      const int64_t* __restrict__ val_ptr, const float2* __restrict__ vh,
                                                      const float2* __restrict__ vl, const float2* __restrict__ xh,
                                                      const float2* __restrict__ xl, const double2* __restrict__ b,
-                                                     double2* __restrict__ y, int64_t ld, int64_t nrows, int mode) {
+                                                     double2* __restrict__ y, int64_t ld, int64_t nrows, int mode,
+                                                     const uint8_t* __restrict__ rent, int64_t offU) {
   const int lane = threadIdx.x & 31;
   const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
   for (int64_t row = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); row < nrows; row += nw) {
@@ -753,7 +986,32 @@ __global__ void __launch_bounds__(256) k_spmv_df_blk(const int32_t* __restrict__
       const int64_t off = val_ptr[E] + (row - ent_start[E]) * nnz;
       const int32_t* cols = col_idx + c0;
       int cA = lane < nnz ? __ldg(cols + lane) : 0;
-      for (int k = lane; k < nnz; k += 32) {
+      const bool real = rent != nullptr && rent[E] != 0;
+      if (real) {   // packed real entity (k_pack_ops): x_c carries i^(-s_c), a = ah + al
+        const float* ahr = reinterpret_cast<const float*>(vh + val_ptr[E]) + (row - ent_start[E]) * nnz;
+        const float* alr = reinterpret_cast<const float*>(vl + val_ptr[E]) + (row - ent_start[E]) * nnz;
+        for (int k = lane; k < nnz; k += 32) {
+          const float ah = __ldcs(ahr + k), al = __ldcs(alr + k);
+          const int sc = cA < offU ? -1 : 0;
+          float2 uh[KB], ul[KB];
+#pragma unroll
+          for (int kb = 0; kb < KB; ++kb) {
+            uh[kb] = mul_i(xh[kb * ld + cA], sc);
+            ul[kb] = mul_i(xl[kb * ld + cA], sc);
+          }
+          const int kn = k + 32;
+          cA = kn < nnz ? __ldg(cols + kn) : 0;
+#pragma unroll
+          for (int kb = 0; kb < KB; ++kb) {
+            float p, q;
+            df_mul(ah, al, uh[kb].x, ul[kb].x, p, q);
+            df_add(rh[kb], rl[kb], p, q);
+            df_mul(ah, al, uh[kb].y, ul[kb].y, p, q);
+            df_add(ih[kb], il[kb], p, q);
+          }
+        }
+      }
+      for (int k = real ? nnz : lane; k < nnz; k += 32) {
         const float2 ah = __ldcs(vh + off + k), al = __ldcs(vl + off + k);
         float2 uh[KB], ul[KB];
 #pragma unroll
@@ -780,6 +1038,13 @@ __global__ void __launch_bounds__(256) k_spmv_df_blk(const int32_t* __restrict__
       for (int kb = 0; kb < KB; ++kb) {
         df_warp_sum(rh[kb], rl[kb]);
         df_warp_sum(ih[kb], il[kb]);
+        if (real && row < offU) {   // output phase i^(s_r), exact
+          const float th = rh[kb], tl = rl[kb];
+          rh[kb] = -ih[kb];
+          rl[kb] = -il[kb];
+          ih[kb] = th;
+          il[kb] = tl;
+        }
       }
     }
     if (lane < KB) {
@@ -804,11 +1069,94 @@ static void spmv_df(const ECSRDev& A, const double2* x, const double2* b, double
   prof_end(prof, pe, st);
 }
 
-void split_operator(Alloc& M, ECSRDev& A, cudaStream_t st) {
+// Complex64 values of an operator (LO: the double-float split, high parts in
+// vh and low parts in vl), one CTA per row entity.  With rent, an entity whose
+// entries are all real once the unit phases are taken out,
+//   a[r][c] = A[r][c] i^(s_c - s_r) real (s = 1 on DOFs below offU; exact),
+// is stored packed: its rows as nnz reals from float offset 2 val_ptr[E]
+// (high and low parts alike), rent[E] = 1.  The SpMVs apply the phases
+// exactly: y_r = i^(s_r) sum_c a[r][c] (i^(-s_c) x_c).
+template <bool LO>
+__global__ void k_pack_ops(const int64_t* __restrict__ ent_start, const int32_t* __restrict__ ent_nd,
+                           const int64_t* __restrict__ col_ptr, const int32_t* __restrict__ col_idx,
+                           const int64_t* __restrict__ val_ptr, const double2* __restrict__ v, float2* __restrict__ vh,
+                           float2* __restrict__ vl, uint8_t* __restrict__ rent, int64_t offU) {
+  const int64_t E = blockIdx.x;
+  const int64_t r0 = ent_start[E];
+  const int64_t c0 = col_ptr[E];
+  const int nnz = (int)(col_ptr[E + 1] - c0);
+  const int total = ent_nd[E] * nnz;
+  const int64_t vo = val_ptr[E];
+  auto phase = [&](int q) {   // s_c - s_r of entry q of the entity's block
+    const int64_t row = r0 + q / nnz, col = col_idx[c0 + q % nnz];
+    return (col < offU ? 1 : 0) - (row < offU ? 1 : 0);
+  };
+  bool cplx = rent == nullptr;
+  if (!cplx)
+    for (int q = threadIdx.x; q < total; q += blockDim.x)
+      if (mul_i(v[vo + q], phase(q)).y != 0.0) cplx = true;
+  cplx = __syncthreads_or(cplx) != 0;
+  if (!cplx) {
+    float* h = reinterpret_cast<float*>(vh + vo);
+    float* l = LO ? reinterpret_cast<float*>(vl + vo) : nullptr;
+    for (int q = threadIdx.x; q < total; q += blockDim.x) {
+      const double a = mul_i(v[vo + q], phase(q)).x;
+      const float hx = (float)a;
+      h[q] = hx;
+      if (LO) l[q] = (float)(a - (double)hx);
+    }
+  } else {
+    for (int q = threadIdx.x; q < total; q += blockDim.x) {
+      const double2 a = v[vo + q];
+      const float hx = (float)a.x, hy = (float)a.y;
+      vh[vo + q] = make_float2(hx, hy);
+      if (LO) vl[vo + q] = make_float2((float)(a.x - (double)hx), (float)(a.y - (double)hy));
+    }
+  }
+  if (threadIdx.x == 0 && rent) rent[E] = cplx ? 0 : 1;
+}
+
+// complex64 (and, with lo, double-float) values of A from A.v64; pack: real
+// entities stored as reals (k_pack_ops).  Idempotent: a later call with lo
+// rewrites the high parts with the same values.
+static void pack_operator(Alloc& M, ECSRDev& A, bool lo, int64_t offU, bool pack, cudaStream_t st) {
   if (!A.v32) A.v32 = M.arr<float2>((size_t)std::max<int64_t>(A.nnz, 1));
-  A.vlo = M.arr<float2>((size_t)std::max<int64_t>(A.nnz, 1));
-  k_split_vals<<<1216, 256, 0, st>>>(A.v64, A.v32, A.vlo, A.nnz);
-  DPG_CHECK_LAUNCH();
+  if (lo && !A.vlo) A.vlo = M.arr<float2>((size_t)std::max<int64_t>(A.nnz, 1));
+  if (pack && !A.rent) A.rent = M.arr<uint8_t>((size_t)std::max<int64_t>(A.nent, 1));
+  if (!pack) A.rent = nullptr;
+  A.offU = offU;
+  if (A.nent > 0) {
+    if (lo)
+      k_pack_ops<true><<<(unsigned)A.nent, 128, 0, st>>>(A.ent_start, A.ent_nd, A.col_ptr, A.col_idx, A.val_ptr,
+                                                          A.v64, A.v32, A.vlo, A.rent, offU);
+    else
+      k_pack_ops<false><<<(unsigned)A.nent, 128, 0, st>>>(A.ent_start, A.ent_nd, A.col_ptr, A.col_idx, A.val_ptr,
+                                                           A.v64, A.v32, nullptr, A.rent, offU);
+    DPG_CHECK_LAUNCH();
+  }
+}
+
+// entries of the packed real entities of A (host count from the device tables)
+int64_t packed_entries(const ECSRDev& A) {
+  if (!A.rent || A.nent == 0) return 0;
+  std::vector<uint8_t> fl((size_t)A.nent);
+  std::vector<int32_t> nd((size_t)A.nent);
+  std::vector<int64_t> cp((size_t)A.nent + 1);
+  DPG_CUDA(cudaMemcpy(fl.data(), A.rent, (size_t)A.nent, cudaMemcpyDeviceToHost));
+  DPG_CUDA(cudaMemcpy(nd.data(), A.ent_nd, (size_t)A.nent * sizeof(int32_t), cudaMemcpyDeviceToHost));
+  DPG_CUDA(cudaMemcpy(cp.data(), A.col_ptr, ((size_t)A.nent + 1) * sizeof(int64_t), cudaMemcpyDeviceToHost));
+  int64_t t = 0;
+  for (int64_t E = 0; E < A.nent; ++E)
+    if (fl[E]) t += (int64_t)nd[E] * (cp[E + 1] - cp[E]);
+  return t;
+}
+
+void split_operator(Alloc& M, ECSRDev& A, int64_t offU, bool pack, cudaStream_t st) {
+  pack_operator(M, A, true, offU, pack, st);
+}
+
+void operator_c64(Alloc& M, ECSRDev& A, int64_t offU, bool pack, cudaStream_t st) {
+  pack_operator(M, A, false, offU, pack, st);
 }
 
 void split_df(const double2* v, float2* hi, float2* lo, int64_t n, cudaStream_t st) {
@@ -1618,7 +1966,7 @@ static void spmv_blk(const ECSRDev& A, const C* vals, const C* x, const C* b, C*
     const unsigned blocks = (unsigned)std::min<int64_t>((A.nrows + 7) / 8, 152 * 16);
 #define DPG_SPMV_BLK(KB)                                                                                            \
   k_spmv_blk<C, KB><<<blocks, 256, 0, st>>>(A.row_ent, A.ent_start, A.col_ptr, A.col_idx, A.val_ptr, vals, xg, bg, yg, \
-                                            n, A.nrows, mode)
+                                            n, A.nrows, mode, packed_rows<C>(A), A.offU)
     if (kb == 4) DPG_SPMV_BLK(4);
     else if (kb == 3) DPG_SPMV_BLK(3);
     else if (kb == 2) DPG_SPMV_BLK(2);
@@ -1769,7 +2117,7 @@ static bool cg_c128(const SystemImpl& S) { return (S.op.flags & DPGMG_FLAG_CG_C1
 static const ECSRDev& cg_operator(SystemImpl& S, WS& W, cudaStream_t st) {
   Level& F = S.levels.back();
   if (S.levels.size() > 1 && F.kind == 1) {
-    if (!F.A.vlo && !cg_c128(S)) split_operator(S.mem, F.A, st);
+    if (!F.A.vlo && !cg_c128(S)) split_operator(S.mem, F.A, F.mesh.offU, pack_storage(S), st);
     return F.A;
   }
   if (!W.acg_owned) {
@@ -1781,7 +2129,7 @@ static const ECSRDev& cg_operator(SystemImpl& S, WS& W, cudaStream_t st) {
       assemble_ecsr(S.mem, prep_ecsr(F.mesh, element_groups(F.mesh)), W.Acg, st);
     }
     ecsr_add_elements(W.Acg, F.E, F.dofs, F.mesh.nelem, F.nloc, 0, F.mesh.n, st);
-    if (!cg_c128(S)) split_operator(S.mem, W.Acg, st);
+    if (!cg_c128(S)) split_operator(S.mem, W.Acg, F.mesh.offU, pack_storage(S), st);
     DPG_CUDA(cudaStreamSynchronize(st));
     W.acg_owned = true;
   }
@@ -1843,8 +2191,14 @@ static int pick_variant(const TuneKey& key, const Evict& ev, cudaStream_t st, st
                         F&& run);
 
 template <class F>
-static int pick_group(const TuneKey& key, const Evict& ev, cudaStream_t st, F&& run) {
-  return pick_variant(key, ev, st, {1, SPMV_PF, SPMV_RING, 2, 4, 8}, run);
+static int pick_group(const TuneKey& key, const Evict& ev, cudaStream_t st, F&& run, bool packed = false,
+                      bool df = false) {
+  TuneKey k = key;
+  if (packed) k.kind += 8;   // packed real entities: every variant but the cp.async ring
+  if (df) return packed ? pick_variant(k, ev, st, {1, SPMV_PF, 2, 4, 8}, run)
+                        : pick_variant(k, ev, st, {1, SPMV_PF, SPMV_RING, 2, 4, 8}, run);
+  return packed ? pick_variant(k, ev, st, {1, SPMV_PF, SPMV_HALF, 2, 4, 8}, run)
+                : pick_variant(k, ev, st, {1, SPMV_PF, SPMV_RING, SPMV_HALF, 2, 4, 8}, run);
 }
 
 template <class F>
@@ -1982,7 +2336,8 @@ void prepare_solve(SystemImpl& S, cudaStream_t st) {
     if (mixed) {
       float2 *x = W.w32[l].x, *y = W.w32[l].t;
       DPG_CUDA(cudaMemsetAsync(x, 0, (size_t)n * sizeof(float2), st));
-      F.A.gsel[0] = pick_group(key, ev, st, [&](int G) { spmv_g<float2>(F.A, F.A.v32, x, nullptr, y, 0, G, st); });
+      F.A.gsel[0] = pick_group(key, ev, st, [&](int G) { spmv_g<float2>(F.A, F.A.v32, x, nullptr, y, 0, G, st); },
+                               F.A.rent != nullptr);
       if (F.P.inv32 && F.P.np) {
         // smoother product: 1 or 2 columns per lane (32- or 64-column work
         // items), the latter at 8 or 6 CTAs per SM; the block smoother takes
@@ -2010,7 +2365,8 @@ void prepare_solve(SystemImpl& S, cudaStream_t st) {
       Acg.gsel[1] = pick_group(key, ev, st, [&](int G) { spmv_g<double2>(Acg, Acg.v64, W.p, nullptr, W.q, 0, G, st); });
     } else {
       const TuneKey key{2, F.mesh.p, F.kind, log2i(n)};
-      Acg.gsel[2] = pick_group(key, ev, st, [&](int G) { spmv_df_g(Acg, W.xh, W.xl, nullptr, W.q, 0, G, st); });
+      Acg.gsel[2] = pick_group(key, ev, st, [&](int G) { spmv_df_g(Acg, W.xh, W.xl, nullptr, W.q, 0, G, st); },
+                               Acg.rent != nullptr, true);
     }
   }
 }
@@ -2024,8 +2380,10 @@ int pcg_solve(SystemImpl& S, cudaStream_t st, double2* xout, dpgmg_stats* stats,
     const int64_t esz = S.op.precision == DPGMG_PREC_MIXED ? 8 : 16;
     if (S.prof_which == DPGMG_PROF_SMOOTH_FINE)   // stored entries read once: real packed blocks at half size
       S.prof_bytes = (Ff.P.sum_sq - Ff.P.real_sq) * esz + Ff.P.real_sq * (esz / 2);
-    else if (S.prof_which == DPGMG_PROF_SPMV_FINE) S.prof_bytes = Ff.A.nnz_alg * esz;
-    else if (S.prof_which == DPGMG_PROF_SPMV_CG) S.prof_bytes = A.nnz_alg * 16;   // hi + lo complex64
+    else if (S.prof_which == DPGMG_PROF_SPMV_FINE)   // packed real entities at half size
+      S.prof_bytes = (Ff.A.nnz_alg - Ff.A.nnz_real) * esz + Ff.A.nnz_real * (esz / 2);
+    else if (S.prof_which == DPGMG_PROF_SPMV_CG)     // hi + lo complex64, or hi + lo reals
+      S.prof_bytes = (A.nnz_alg - A.nnz_real) * 16 + A.nnz_real * 8;
   }
   const int64_t n = S.levels.back().mesh.ndof;
   cudaEvent_t e0, e1;
@@ -2200,7 +2558,7 @@ int pcg_solve_block(SystemImpl& S, cudaStream_t st, int K, const double2* B, dou
       const unsigned blocks = (unsigned)std::min<int64_t>((n + 7) / 8, 152 * 16);
 #define DPG_DF_BLK(KB)                                                                                            \
   k_spmv_df_blk<KB><<<blocks, 256, 0, st>>>(A.row_ent, A.ent_start, A.col_ptr, A.col_idx, A.val_ptr, A.v32, A.vlo, \
-                                            xh, xl, bg, yg, n, n, mode)
+                                            xh, xl, bg, yg, n, n, mode, A.rent, A.offU)
       if (kb == 4) DPG_DF_BLK(4);
       else if (kb == 3) DPG_DF_BLK(3);
       else if (kb == 2) DPG_DF_BLK(2);

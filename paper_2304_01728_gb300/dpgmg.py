@@ -22,7 +22,7 @@ SRC_GAUSSIAN, SRC_PLANE_WAVE, SRC_MANUFACTURED = 0, 1, 2
 PREC_FP64, PREC_MIXED = 0, 1
 COARSEST_CHOLESKY, COARSEST_NONE, COARSEST_AUTO, COARSEST_SMOOTH = 0, 1, 2, 3
 FLAG_EAGER, FLAG_CUDA_CORES, FLAG_STORE_COARSE, FLAG_WARM_START, FLAG_CG_C128 = 1, 2, 4, 8, 16
-FLAG_PATCH_FP64, FLAG_PATCH_R2, FLAG_RECOMPUTE_PATCHES, FLAG_PATCH_COMPLEX = 32, 64, 128, 256
+FLAG_PATCH_FP64, FLAG_PATCH_R2, FLAG_RECOMPUTE_PATCHES, FLAG_COMPLEX_STORAGE = 32, 64, 128, 256
 FLAG_FAULT_NOT_HPD, FLAG_FAULT_TC_WAIT = 1 << 28, 1 << 29
 OP_A, OP_SMOOTH, OP_VCYCLE, OP_RESTRICT, OP_PROLONG, OP_CONDENSE, OP_COARSE, OP_AFULL = range(8)
 
@@ -62,7 +62,7 @@ class dpgmg_level_desc(ctypes.Structure):
                 ("n_smooth", ctypes.c_longlong), ("kind", ctypes.c_int), ("n_patches", ctypes.c_longlong),
                 ("patch_max", ctypes.c_longlong), ("sum_patch_sq", ctypes.c_longlong),
                 ("op_nnz", ctypes.c_longlong), ("theta", ctypes.c_double), ("patch_stored", ctypes.c_longlong),
-                ("patch_real_sq", ctypes.c_longlong)]
+                ("patch_real_sq", ctypes.c_longlong), ("op_real_nnz", ctypes.c_longlong)]
 
 
 _lib = None

@@ -310,7 +310,7 @@ def test_spmv_group_sizes(name, request):
     c = request.getfixturevalue(name)
     s = c.solver
     tuned = [D.dpgmg_spmv_group(s.h, s.s, l) for l in range(1, c.L + 1)] + [D.dpgmg_spmv_group(s.h, s.s, -1)]
-    assert all(g in (1, 2, 4, 8, 16, 32) for g in tuned)
+    assert all(g in (1, 2, 4, 8, 16, 32, 64) for g in tuned)
     try:
         for G in (1, 2, 4, 8, 16, 32):
             for l in range(1, c.L + 1):
@@ -341,12 +341,14 @@ def test_spmv_group_sizes(name, request):
         assert np.array_equal(ys[0], ys[1]) and np.array_equal(ys[0], ys[2]), l
     with pytest.raises(D.DpgmgError):
         D.dpgmg_spmv_group(s.h, s.s, 1, 3)
+    with pytest.raises(D.DpgmgError):   # no half-warp form of the CG operator
+        D.dpgmg_spmv_group(s.h, s.s, -1, 64)
 
 
 def test_spmv_group_sizes_mixed(c1):
     """The complex64 V-cycle operators under every work decomposition."""
     with D.Solver(c1.pk, **dict(c1.ok, precision="mixed")) as s:
-        for G in (1, 2, 4, 8, 16, 32):
+        for G in (1, 2, 4, 8, 16, 32, 64):
             for l in range(1, c1.L + 1):
                 D.dpgmg_spmv_group(s.h, s.s, l, G)
                 n = c1.levels[l].mesh.n_dof
