@@ -3,6 +3,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <functional>
 #include <map>
 #include <stdexcept>
 #include <thread>
@@ -364,19 +365,32 @@ std::vector<LevelSpec> plan_levels(const int n[3], int p, int n_levels, int p_mi
 }
 
 // ------------------------------------------------------------------- ECSR
-// Runs body(lo, hi) over [0, n) on up to 16 host threads (contiguous ranges).
-template <class F>
-static void parallel_ranges(int64_t n, F&& body) {
+// Number of host threads for a loop of n items: up to 16, at least 256 items each.
+static int64_t host_threads(int64_t n) {
   const int64_t hw = std::max<int64_t>(1, (int64_t)std::thread::hardware_concurrency());
-  const int64_t nt = std::min<int64_t>({hw, (int64_t)16, std::max<int64_t>(1, n / 256)});
+  return std::min<int64_t>({hw, (int64_t)16, std::max<int64_t>(1, n / 256)});
+}
+
+// Runs body(t, lo, hi) for t < nt over contiguous ranges of [0, n), one host
+// thread each (nt = host_threads(n), or the given count).
+template <class F>
+static void parallel_chunks(int64_t n, int64_t nt, F&& body) {
   if (nt <= 1) {
-    body((int64_t)0, n);
+    body((int64_t)0, (int64_t)0, n);
     return;
   }
   std::vector<std::thread> th;
-  for (int64_t t = 0; t < nt; ++t) th.emplace_back([&, t]() { body(n * t / nt, n * (t + 1) / nt); });
+  for (int64_t t = 0; t < nt; ++t) th.emplace_back([&, t]() { body(t, n * t / nt, n * (t + 1) / nt); });
   for (auto& x : th) x.join();
 }
+
+// Runs body(lo, hi) over [0, n) in contiguous ranges on host_threads(n) threads.
+template <class F>
+static void parallel_ranges(int64_t n, F&& body) {
+  parallel_chunks(n, host_threads(n), [&](int64_t, int64_t lo, int64_t hi) { body(lo, hi); });
+}
+
+void host_parallel(int64_t n, const std::function<void(int64_t, int64_t)>& body) { parallel_ranges(n, body); }
 
 ECSRHost build_ecsr(const MeshL& m, const std::vector<std::vector<int64_t>>& groups) {
   ECSRHost A;
@@ -402,26 +416,36 @@ ECSRHost build_ecsr(const MeshL& m, const std::vector<std::vector<int64_t>>& gro
     if (nd > 0) rows.push_back(E);
   }
   const int64_t R = (int64_t)rows.size();
-  // per row entity: sorted distinct column entities and their DOF count
-  std::vector<std::vector<int64_t>> nb(R);
+  // per row entity: sorted distinct column entities (a stamp per entity drops
+  // repeats before the sort), kept per thread in one flat buffer, and the
+  // row's column DOF count
+  const int64_t nt = host_threads(R);
+  std::vector<std::vector<int32_t>> buf((size_t)std::max<int64_t>(nt, 1));
+  std::vector<int32_t> nb_cnt(R);
   std::vector<int64_t> ncol(R);
-  parallel_ranges(R, [&](int64_t lo, int64_t hi) {
-    std::vector<int64_t> cols;
+  parallel_chunks(R, nt, [&](int64_t t, int64_t lo, int64_t hi) {
+    std::vector<int32_t> stamp(m.nent, -1);
+    std::vector<int32_t> cols;
+    std::vector<int32_t>& out = buf[t];
     for (int64_t r = lo; r < hi; ++r) {
       const int64_t E = rows[r];
       cols.clear();
       for (int64_t q = eg_ptr[E]; q < eg_ptr[E + 1]; ++q)
-        for (int64_t F : groups[eg[q]]) cols.push_back(F);
+        for (int64_t F : groups[eg[q]])
+          if (stamp[F] != (int32_t)r) {
+            stamp[F] = (int32_t)r;
+            cols.push_back((int32_t)F);
+          }
       std::sort(cols.begin(), cols.end());
-      cols.erase(std::unique(cols.begin(), cols.end()), cols.end());
       int64_t c = 0;
-      for (int64_t F : cols) {
+      for (int32_t F : cols) {
         int64_t fs;
         int fn;
         m.ent_range(F, &fs, &fn);
         c += fn;
       }
-      nb[r] = cols;
+      out.insert(out.end(), cols.begin(), cols.end());
+      nb_cnt[r] = (int32_t)cols.size();
       ncol[r] = c;
     }
   });
@@ -442,18 +466,14 @@ ECSRHost build_ecsr(const MeshL& m, const std::vector<std::vector<int64_t>>& gro
     A.nnz_alg += ncol[r] * nd;
     for (int k = 0; k < nd; ++k) A.row_ent[st + k] = (int32_t)r;
   }
-  A.col_idx.resize(A.col_ptr[R]);
-  parallel_ranges(R, [&](int64_t lo, int64_t hi) {
-    for (int64_t r = lo; r < hi; ++r) {
-      int32_t* out = A.col_idx.data() + A.col_ptr[r];
-      for (int64_t F : nb[r]) {
-        int64_t fs;
-        int fn;
-        m.ent_range(F, &fs, &fn);
-        for (int k = 0; k < fn; ++k) *out++ = (int32_t)(fs + k);
-      }
-    }
+  // column entity lists: the per-thread buffers in row order
+  A.cent_ptr.assign(R + 1, 0);
+  for (int64_t r = 0; r < R; ++r) A.cent_ptr[r + 1] = A.cent_ptr[r] + nb_cnt[r];
+  A.col_ent.resize(A.cent_ptr[R]);   // left uninitialised (NoInitAlloc): every entry is written below
+  parallel_chunks(R, nt, [&](int64_t t, int64_t lo, int64_t hi) {
+    if (lo < hi) std::copy(buf[t].begin(), buf[t].end(), A.col_ent.begin() + A.cent_ptr[lo]);
   });
+  A.er = EntRanges{m.entE, m.entF, m.entU, m.offE, m.offF, m.offU, m.p};
   return A;
 }
 
@@ -521,34 +541,50 @@ int patch_axis_span(int ctr, int H, int nco, bool r2, int W[2]) {
 
 Patches build_patches(const MeshL& m, const std::vector<char>& smask, int H, const int nco[3], bool r2) {
   Patches P;
-  int64_t npatch = (int64_t)(nco[0] + 1) * (nco[1] + 1) * (nco[2] + 1);
-  std::vector<int64_t> count(npatch + 1, 0);
-  auto sets = [&](int64_t g, int W[3][2], int cnt[3]) {
-    int ctr[3];
-    m.ent_center(m.dof_entity(g), ctr);
-    for (int d = 0; d < 3; ++d) cnt[d] = patch_axis_span(ctr[d], H, nco[d], r2, W[d]);
-  };
-  for (int pass = 0; pass < 2; ++pass) {
-    std::vector<int64_t> fill;
-    if (pass == 1) {
-      P.ptr.assign(npatch + 1, 0);
-      for (int64_t j = 0; j < npatch; ++j) P.ptr[j + 1] = P.ptr[j] + count[j];
-      P.dofs.assign(P.ptr[npatch], 0);
-      fill.assign(P.ptr.begin(), P.ptr.end() - 1);
-    }
-    for (int64_t g = 0; g < m.ndof; ++g) {
-      if (!smask[g]) continue;
-      int W[3][2], cnt[3];
-      sets(g, W, cnt);
-      for (int a = 0; a < cnt[0]; ++a)
-        for (int b = 0; b < cnt[1]; ++b)
-          for (int c = 0; c < cnt[2]; ++c) {
-            int64_t w = W[0][a] + (int64_t)(nco[0] + 1) * (W[1][b] + (int64_t)(nco[1] + 1) * W[2][c]);
-            if (pass == 0) ++count[w];
-            else P.dofs[fill[w]++] = (int32_t)g;
+  const int64_t npatch = (int64_t)(nco[0] + 1) * (nco[1] + 1) * (nco[2] + 1);
+  // Entities in order (their DOFs are consecutive and increasing with the
+  // entity), split into contiguous ranges over host threads: pass 0 counts per
+  // (thread, patch), pass 1 writes each thread's DOFs after those of the
+  // threads before it, so every patch lists its DOFs in increasing order.
+  const int64_t nt = host_threads(m.nent);
+  std::vector<int64_t> cnt((size_t)(nt * npatch), 0);
+  auto visit = [&](int64_t lo, int64_t hi, auto&& emit) {
+    for (int64_t E = lo; E < hi; ++E) {
+      int64_t st;
+      int nd;
+      m.ent_range(E, &st, &nd);
+      if (nd == 0) continue;
+      int ctr[3], W[3][2], c[3];
+      m.ent_center(E, ctr);
+      for (int d = 0; d < 3; ++d) c[d] = patch_axis_span(ctr[d], H, nco[d], r2, W[d]);
+      for (int a = 0; a < c[0]; ++a)
+        for (int b = 0; b < c[1]; ++b)
+          for (int q = 0; q < c[2]; ++q) {
+            const int64_t w = W[0][a] + (int64_t)(nco[0] + 1) * (W[1][b] + (int64_t)(nco[1] + 1) * W[2][q]);
+            for (int k = 0; k < nd; ++k)
+              if (smask[st + k]) emit(w, st + k);
           }
     }
+  };
+  parallel_chunks(m.nent, nt, [&](int64_t t, int64_t lo, int64_t hi) {
+    int64_t* ct = cnt.data() + t * npatch;
+    visit(lo, hi, [&](int64_t w, int64_t) { ++ct[w]; });
+  });
+  P.ptr.assign(npatch + 1, 0);
+  for (int64_t w = 0; w < npatch; ++w) {   // cnt becomes each thread's first position in patch w
+    int64_t acc = P.ptr[w];
+    for (int64_t t = 0; t < nt; ++t) {
+      const int64_t c = cnt[t * npatch + w];
+      cnt[t * npatch + w] = acc;
+      acc += c;
+    }
+    P.ptr[w + 1] = acc;
   }
+  P.dofs.resize(P.ptr[npatch]);
+  parallel_chunks(m.nent, nt, [&](int64_t t, int64_t lo, int64_t hi) {
+    int64_t* fill = cnt.data() + t * npatch;
+    visit(lo, hi, [&](int64_t w, int64_t g) { P.dofs[fill[w]++] = (int32_t)g; });
+  });
   P.val_ptr.assign(npatch + 1, 0);
   for (int64_t j = 0; j < npatch; ++j) {
     int64_t nj = P.ptr[j + 1] - P.ptr[j];

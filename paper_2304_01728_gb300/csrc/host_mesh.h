@@ -6,6 +6,10 @@
 // arithmetic of the method runs in the CUDA kernels.
 #pragma once
 #include <cstdint>
+#include <functional>
+#include <memory>
+#include <new>
+#include <utility>
 #include <vector>
 
 namespace dpgmg {
@@ -65,6 +69,38 @@ struct MeshL {
 struct LevelSpec { int n[3]; int p; int kind_below; };  // kind 0 none, 1 p, 2 h
 std::vector<LevelSpec> plan_levels(const int n[3], int p, int n_levels, int p_min);
 
+// std::allocator whose value-initialisation of trivial elements is left out
+// (resize leaves them uninitialised), for large arrays that are filled in
+// parallel right after their allocation.
+template <class T> struct NoInitAlloc : std::allocator<T> {
+  template <class U> struct rebind { using other = NoInitAlloc<U>; };
+  NoInitAlloc() = default;
+  template <class U> NoInitAlloc(const NoInitAlloc<U>&) noexcept {}
+  template <class U> void construct(U* p) noexcept { ::new ((void*)p) U; }
+  template <class U, class... Args> void construct(U* p, Args&&... args) {
+    ::new ((void*)p) U(std::forward<Args>(args)...);
+  }
+};
+
+// First DOF and DOF count of an entity from the mesh's counts alone (the same
+// rule as MeshL::ent_range), for device code that expands entity lists.
+struct EntRanges {
+  int64_t entE, entF, entU, offE, offF, offU;
+  int p;
+#if defined(__CUDACC__)
+  __host__ __device__
+#endif
+  void range(int64_t E, int64_t* start, int* nd) const {
+    if (E < entE) { *start = E; *nd = 1; }
+    else if (E < entF) { *start = offE + (E - entE) * (p - 1); *nd = p - 1; }
+    else if (E < entU) { *start = offF + (E - entF) * (int64_t)(p - 1) * (p - 1); *nd = (p - 1) * (p - 1); }
+    else { *start = offU + (E - entU) * (int64_t)p * p; *nd = p * p; }
+  }
+};
+
+// Runs body(lo, hi) over contiguous ranges of [0, n) on up to 16 host threads.
+void host_parallel(int64_t n, const std::function<void(int64_t, int64_t)>& body);
+
 // Entity-shared CSR ("ECSR"): rows are grouped by entity; all rows of one
 // entity share one sorted list of column DOFs.  Values of row r of entity E
 // start at val_ptr[E] + (r - start(E)) * nnz_row(E).
@@ -74,10 +110,15 @@ struct ECSRHost {
   std::vector<int64_t> ent_start;    // per row entity: first DOF
   std::vector<int32_t> ent_nd;       // per row entity: DOF count
   std::vector<int64_t> col_ptr;      // per row entity (+1): offset in col_idx
-  std::vector<int32_t> col_idx;      // expanded column DOFs, sorted per entity
+  // column entities per row entity (sorted, distinct): col_ent[cent_ptr[E] ..
+  // cent_ptr[E + 1]); the expanded column DOFs (col_ptr) are the DOF ranges of
+  // these entities in order, built on the device (assemble_ecsr)
+  std::vector<int64_t> cent_ptr;
+  std::vector<int32_t, NoInitAlloc<int32_t>> col_ent;
   std::vector<int64_t> val_ptr;      // per row entity (+1): value offset
   int64_t nnz() const { return val_ptr.empty() ? 0 : val_ptr.back(); }
   int64_t nnz_alg = 0;               // = nnz(): entries of the operator
+  EntRanges er{};                    // the mesh's entity -> DOF range rule
 };
 // groups: for each super-element, the list of entity ids it touches.
 ECSRHost build_ecsr(const MeshL& m, const std::vector<std::vector<int64_t>>& groups);

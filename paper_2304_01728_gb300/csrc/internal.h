@@ -50,7 +50,7 @@ struct Alloc {
   ~Alloc() { free_all(); }
 };
 
-template <class T> T* upload(Alloc& A, const std::vector<T>& h, cudaStream_t s) {
+template <class T, class AL> T* upload(Alloc& A, const std::vector<T, AL>& h, cudaStream_t s) {
   T* d = A.arr<T>(h.size() ? h.size() : 1);
   if (!h.empty()) DPG_CUDA(cudaMemcpyAsync(d, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice, s));
   return d;

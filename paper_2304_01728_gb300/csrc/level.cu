@@ -43,6 +43,33 @@ EcsrPrep prep_ecsr(const MeshL& m, const std::vector<std::vector<int64_t>>& grou
   return P;
 }
 
+// Expanded column DOFs of the ECSR operator: row entity r (one warp) lists the
+// DOF ranges of its column entities in order from col_ptr[r]; a warp-wide
+// exclusive scan of the entities' DOF counts places each range.
+__global__ void k_expand_cols(const int64_t* __restrict__ cent_ptr, const int32_t* __restrict__ col_ent,
+                              const int64_t* __restrict__ col_ptr, EntRanges er, int64_t nent,
+                              int32_t* __restrict__ col_idx) {
+  const int lane = threadIdx.x & 31;
+  const int64_t r = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (r >= nent) return;
+  int64_t base = col_ptr[r];
+  const int64_t q0 = cent_ptr[r], q1 = cent_ptr[r + 1];
+  for (int64_t q = q0; q < q1; q += 32) {
+    int64_t fs = 0;
+    int fn = 0;
+    if (q + lane < q1) er.range(col_ent[q + lane], &fs, &fn);
+    int incl = fn;   // inclusive scan of the DOF counts over the warp
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int v = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += v;
+    }
+    int32_t* out = col_idx + base + (incl - fn);
+    for (int k = 0; k < fn; ++k) out[k] = (int32_t)(fs + k);
+    base += __shfl_sync(0xffffffffu, incl, 31);
+  }
+}
+
 void assemble_ecsr(Alloc& A, const EcsrPrep& P, ECSRDev& D, cudaStream_t st) {
   const ECSRHost& H = P.H;
   D.nrows = H.nrows;
@@ -53,7 +80,18 @@ void assemble_ecsr(Alloc& A, const EcsrPrep& P, ECSRDev& D, cudaStream_t st) {
   D.ent_start = upload(A, H.ent_start, st);
   D.ent_nd = upload(A, H.ent_nd, st);
   D.col_ptr = upload(A, H.col_ptr, st);
-  D.col_idx = upload(A, H.col_idx, st);
+  {
+    const int64_t ncols = H.col_ptr.empty() ? 0 : H.col_ptr.back();
+    D.col_idx = A.arr<int32_t>((size_t)std::max<int64_t>(ncols, 1));
+    if (D.nent > 0) {
+      int64_t* cptr = upload(A, H.cent_ptr, st);
+      int32_t* cent = upload(A, H.col_ent, st);
+      k_expand_cols<<<(unsigned)((D.nent + 7) / 8), 256, 0, st>>>(cptr, cent, D.col_ptr, H.er, D.nent, D.col_idx);
+      DPG_CHECK_LAUNCH();
+      A.release(cent);   // stream-ordered frees: after the expansion
+      A.release(cptr);
+    }
+  }
   D.val_ptr = upload(A, H.val_ptr, st);
   D.max_nnz_row = P.max_nnz_row;
   for (int gi = 1; gi <= 3; ++gi) {
@@ -125,14 +163,16 @@ void ecsr_add_elements(ECSRDev& D, const double2* E, const int64_t* dofs, int64_
 
 std::vector<std::vector<int64_t>> element_groups(const MeshL& m) {
   std::vector<std::vector<int64_t>> g(m.nelem);
-  std::vector<int64_t> ent(m.loc.size());
-  for (int64_t e = 0; e < m.nelem; ++e) {
-    m.elem_entities(e, ent.data());
-    for (int64_t E : ent)
-      if (E >= 0) g[e].push_back(E);
-    std::sort(g[e].begin(), g[e].end());
-    g[e].erase(std::unique(g[e].begin(), g[e].end()), g[e].end());
-  }
+  host_parallel(m.nelem, [&](int64_t lo, int64_t hi) {
+    std::vector<int64_t> ent(m.loc.size());
+    for (int64_t e = lo; e < hi; ++e) {
+      m.elem_entities(e, ent.data());
+      for (int64_t E : ent)
+        if (E >= 0) g[e].push_back(E);
+      std::sort(g[e].begin(), g[e].end());
+      g[e].erase(std::unique(g[e].begin(), g[e].end()), g[e].end());
+    }
+  });
   return g;
 }
 
