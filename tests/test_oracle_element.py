@@ -204,3 +204,54 @@ def test_condensed_matrix_depends_only_on_impedance_faces_and_wavespeed():
     K3, _ = cond(idx(1, 1, 1), c=1.3)
     assert np.linalg.norm(K1 - K2) > 1e-3 * np.linalg.norm(K1)
     assert np.linalg.norm(K1 - K3) > 1e-3 * np.linalg.norm(K1)
+
+
+def test_interior_condensed_matrix_is_real_after_unit_phases():
+    # premise of storing such blocks as reals on the mixed path: in the real
+    # form the p-hat traces carry the unit phase i (Sec. 2, the first-order
+    # system's i w terms), so an element without an impedance face and with a
+    # real wavespeed has Kc[r][c] = a[r][c] i^(s_r - s_c) with a real (s = 1
+    # on p-hat traces); the impedance term makes a boundary element's complex
+    from oracle.mesh import local_trace_functions
+    p, om = 2, 6.0
+    m = Mesh((4, 4, 4), p)
+    ld = GaussianSource((0.35, 0.5, 0.6), 0.2)
+    s = np.array([1 if fn[0] == "p" else 0 for fn in local_trace_functions(p)])
+    unphase = (1j) ** (s[None, :] - s[:, None])   # i^(s_c - s_r)
+
+    def cond(e, c=1.0):
+        bf = boundary_faces(m, e)
+        corner = m.x0 + np.asarray(m.elem_coord(e)) * m.h
+        K, F = dpg_element(p, m.h, corner, c, om, bf, ld)
+        return condense(p, K, F, bf)[0]
+
+    idx = lambda i, j, k: i + 4 * (j + 4 * k)
+    for e, c in [(idx(1, 1, 1), 1.0), (idx(2, 1, 2), 0.7)]:
+        a = cond(e, c) * unphase
+        assert np.linalg.norm(a.imag) <= 1e-12 * np.linalg.norm(a.real)
+        assert np.linalg.norm(a - a.T) <= 1e-12 * np.linalg.norm(a)   # real symmetric
+    for e in (idx(0, 1, 1), idx(3, 3, 0)):
+        a = cond(e) * unphase
+        assert np.linalg.norm(a.imag) > 1e-3 * np.linalg.norm(a.real)
+
+
+def test_assembled_rows_of_interior_entities_are_real_after_unit_phases():
+    # the same on the assembled trace operator: every row whose DOF only
+    # interior elements touch is real after the phases, and rows touched by an
+    # impedance element are not all real
+    p, om = 2, 5.0
+    fs = build_fine((4, 4, 4), p, om)
+    A, _ = fs.assemble()
+    mesh = fs.mesh
+    s = (np.arange(mesh.n_dof) < mesh.off_U).astype(int)
+    touched = np.zeros(mesh.n_dof, dtype=bool)
+    for e in range(mesh.n_elem):
+        if any(fs.bflags[e]):
+            g = fs.dofs[e]
+            touched[g[g >= 0]] = True
+    A = A.tocoo()
+    a = A.data * (1j) ** (s[A.col] - s[A.row])
+    inner = ~touched[A.row]
+    assert inner.sum() > 0 and (~inner).sum() > 0
+    assert np.abs(a[inner].imag).max() <= 1e-12 * np.abs(a[inner]).max()
+    assert np.abs(a[~inner].imag).max() > 1e-3 * np.abs(a[~inner]).max()
