@@ -406,7 +406,8 @@ def run_gb300(args, rank, world, local_rank):
                     break
             tuned["cg"] = D.dpgmg_spmv_group(h, s, -1)
             li = D.dpgmg_level_info(h, s, w["opts"]["n_levels"] - 1)
-            patch_store.update(sum_patch_sq=int(li.sum_patch_sq), real_sq=int(li.patch_real_sq))
+            patch_store.update(sum_patch_sq=int(li.sum_patch_sq), real_sq=int(li.patch_real_sq),
+                               op_nnz=int(li.op_nnz), op_real_nnz=int(li.op_real_nnz))
             em, eg, _ = D.dpgmg_setup_profile(h, s)
             phases.append(D.dpgmg_setup_phases(h, s))
             elem_acc[0] += em
@@ -469,7 +470,11 @@ def run_gb300(args, rank, world, local_rank):
         ms = pr[0] / max(pr[1], 1)
         gbs = pr[2] / (ms / 1e3) / 1e9
         kernels.append({"kernel": name, "bytes_per_launch": pr[2], "launches": pr[1], "avg_launch_ms": ms,
-                        "achieved": gbs, "unit": "GB/s"})
+                        "achieved": gbs, "unit": "GB/s",
+                        "bytes_rule": "stored values read once: complex64 8 B per entry (CG operator: high + "
+                                      "low parts, 16 B), real packed rows half of that",
+                        "real_packed_fraction_of_entries": (patch_store["op_real_nnz"] / patch_store["op_nnz"]
+                                                            if patch_store.get("op_nnz") else None)})
 
     # ---- end to end through the public API with host buffers
     e2e = None
