@@ -149,3 +149,33 @@ def test_boundary_points_are_the_oracle_face_rule(libpath, n, p):
     ref = np.array(ref)
     assert pts.shape == ref.shape
     assert np.abs(pts - ref).max() < 1e-13
+
+
+def test_binding_struct_layouts_match_the_header(tmp_path):
+    """The ctypes mirrors of the public structs have the C compiler's size and
+    field offsets (a field added to one side only would shift every later one)."""
+    import shutil
+    import subprocess
+    from paper_2304_01728_gb300 import dpgmg
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    structs = [dpgmg.dpgmg_problem, dpgmg.dpgmg_opts, dpgmg.dpgmg_stats, dpgmg.dpgmg_level_desc]
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "dpgmg.h"', "int main(void) {"]
+    for S in structs:
+        t = S.__name__
+        lines.append('printf("%s sizeof %%zu\\n", sizeof(%s));' % (t, t))
+        for f in S._fields_:
+            lines.append('printf("%s %s %%zu\\n", offsetof(%s, %s));' % (t, f[0], t, f[0]))
+    lines += ["return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    got = {tuple(l.split()[:2]): int(l.split()[2]) for l in out if l.strip()}
+    for S in structs:
+        t = S.__name__
+        assert got[(t, "sizeof")] == ctypes.sizeof(S), t
+        for f in S._fields_:
+            assert got[(t, f[0])] == getattr(S, f[0]).offset, (t, f[0])
