@@ -1,0 +1,131 @@
+"""Host index structures of the library (csrc/host_mesh.cpp) against the
+oracle, on the CPU.
+
+A small C++ driver, compiled here against host_mesh.cpp, prints the vertex
+patches (rules R1 and R2) and the entity-shared CSR operator's column lists
+(column entities expanded to DOFs by the same range rule the device uses).
+The oracle gives the same objects from its own definitions: the patch rules of
+Sec. 3 ("V-cycle and smoother") from entity centres and adjacency, and the
+sparsity of the assembled condensed operator from the element DOF maps.
+"""
+import os
+import shutil
+import subprocess
+
+import numpy as np
+import pytest
+
+from oracle.assembly import build_fine
+from oracle.hierarchy import PATCH_RULES
+from oracle.mesh import Mesh
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+CSRC = os.path.join(ROOT, "paper_2304_01728_gb300", "csrc")
+
+DRIVER = r"""
+#include <algorithm>
+#include <cstdio>
+#include <cstdlib>
+#include "host_mesh.h"
+using namespace dpgmg;
+int main(int argc, char** argv) {
+  int n[3] = {atoi(argv[1]), atoi(argv[2]), atoi(argv[3])};
+  const int p = atoi(argv[4]);
+  double a[3] = {0, 0, 0}, b[3] = {1, 1, 1};
+  MeshL m;
+  m.init(n, p, a, b);
+  std::vector<std::vector<int64_t>> groups(m.nelem);
+  std::vector<int64_t> ent(m.loc.size());
+  for (int64_t e = 0; e < m.nelem; ++e) {
+    m.elem_entities(e, ent.data());
+    for (int64_t E : ent)
+      if (E >= 0) groups[e].push_back(E);
+    std::sort(groups[e].begin(), groups[e].end());
+    groups[e].erase(std::unique(groups[e].begin(), groups[e].end()), groups[e].end());
+  }
+  std::vector<char> sm(m.ndof, 1);
+  for (int r2 = 0; r2 < 2; ++r2) {
+    Patches P = build_patches(m, sm, 2, n, r2 != 0);
+    printf("patches %d %zu\n", r2, P.ptr.size() - 1);
+    for (size_t j = 0; j + 1 < P.ptr.size(); ++j) {
+      printf("%lld", (long long)(P.ptr[j + 1] - P.ptr[j]));
+      for (int64_t q = P.ptr[j]; q < P.ptr[j + 1]; ++q) printf(" %d", P.dofs[q]);
+      printf("\n");
+    }
+  }
+  ECSRHost H = build_ecsr(m, groups);
+  printf("ecsr %lld\n", (long long)m.ndof);
+  for (int64_t r = 0; r < m.ndof; ++r) {
+    const int32_t E = H.row_ent[r];
+    if (E < 0) { printf("0\n"); continue; }
+    std::vector<int64_t> cols;
+    for (int64_t q = H.cent_ptr[E]; q < H.cent_ptr[E + 1]; ++q) {
+      int64_t s;
+      int nd;
+      H.er.range(H.col_ent[q], &s, &nd);
+      for (int k = 0; k < nd; ++k) cols.push_back(s + k);
+    }
+    if ((int64_t)cols.size() != H.col_ptr[E + 1] - H.col_ptr[E]) return 3;
+    printf("%zu", cols.size());
+    for (int64_t c : cols) printf(" %lld", (long long)c);
+    printf("\n");
+  }
+  return 0;
+}
+"""
+
+
+@pytest.fixture(scope="module")
+def driver(tmp_path_factory):
+    cxx = shutil.which("g++") or shutil.which("c++")
+    if cxx is None:
+        pytest.skip("no C++ compiler")
+    d = tmp_path_factory.mktemp("hostidx")
+    src = d / "driver.cpp"
+    src.write_text(DRIVER)
+    exe = d / "driver"
+    subprocess.run([cxx, "-O1", "-std=c++17", "-pthread", "-I", CSRC, str(src),
+                    os.path.join(CSRC, "host_mesh.cpp"), "-o", str(exe)], check=True)
+    return str(exe)
+
+
+def run_driver(exe, n, p):
+    out = subprocess.run([exe, str(n[0]), str(n[1]), str(n[2]), str(p)], check=True, capture_output=True,
+                         text=True).stdout.split("\n")
+    res, i = {}, 0
+    while i < len(out):
+        head = out[i].split()
+        if not head:
+            i += 1
+            continue
+        cnt = int(head[-1])
+        rows = []
+        for line in out[i + 1:i + 1 + cnt]:
+            v = [int(x) for x in line.split()]
+            assert v[0] == len(v) - 1
+            rows.append(np.array(v[1:], dtype=np.int64))
+        res[tuple(head[:-1])] = rows
+        i += 1 + cnt
+    return res
+
+
+@pytest.mark.parametrize("n,p", [((4, 4, 4), 2), ((3, 2, 4), 3), ((2, 3, 2), 1)])
+def test_patches_and_operator_pattern_match_oracle(driver, n, p):
+    got = run_driver(driver, n, p)
+    mesh = Mesh(n, p)
+    table = mesh.dof_table()
+    smask = np.ones(mesh.n_dof, dtype=bool)
+    for r2, rule in ((0, "R1"), (1, "R2")):
+        ref = PATCH_RULES[rule](mesh, mesh, table, "p", smask)
+        mine = got[("patches", str(r2))]
+        assert len(mine) == len(ref)
+        for a, b in zip(mine, ref):
+            assert np.array_equal(a, b)
+    fs = build_fine(n, p, 3.0)
+    A, _ = fs.assemble()
+    A = A.tocsr()
+    rows = got[("ecsr",)]
+    assert len(rows) == mesh.n_dof
+    for r in range(mesh.n_dof):
+        ref = np.sort(A.indices[A.indptr[r]:A.indptr[r + 1]])
+        assert np.array_equal(rows[r], ref), r
