@@ -2,8 +2,9 @@
 oracle, on the CPU.
 
 A small C++ driver, compiled here against host_mesh.cpp, prints the vertex
-patches (rules R1 and R2) and the entity-shared CSR operator's column lists
-(column entities expanded to DOFs by the same range rule the device uses).
+patches (rules R1 and R2), on an h level the smoothed skeleton DOFs and the
+macro patches, and the entity-shared CSR operator's column lists (column
+entities expanded to DOFs by the same range rule the device uses).
 The oracle gives the same objects from its own definitions: the patch rules of
 Sec. 3 ("V-cycle and smoother") from entity centres and adjacency, and the
 sparsity of the assembled condensed operator from the element DOF maps.
@@ -16,7 +17,7 @@ import numpy as np
 import pytest
 
 from oracle.assembly import build_fine
-from oracle.hierarchy import PATCH_RULES
+from oracle.hierarchy import PATCH_RULES, build_hierarchy
 from oracle.mesh import Mesh
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
@@ -51,6 +52,25 @@ int main(int argc, char** argv) {
       printf("%lld", (long long)(P.ptr[j + 1] - P.ptr[j]));
       for (int64_t q = P.ptr[j]; q < P.ptr[j + 1]; ++q) printf(" %d", P.dofs[q]);
       printf("\n");
+    }
+  }
+  if (argc > 5 && n[0] % 2 == 0 && n[1] % 2 == 0 && n[2] % 2 == 0) {   // h transition to n / 2
+    int nc[3] = {n[0] / 2, n[1] / 2, n[2] / 2};
+    MeshL mc;
+    mc.init(nc, p, a, b);
+    MacroHost M = build_macro(m, mc);
+    printf("smask 1\n%lld", (long long)m.ndof);
+    for (int64_t g = 0; g < m.ndof; ++g) printf(" %d", (int)M.smask[g]);
+    printf("\n");
+    std::vector<char> s2(M.smask.begin(), M.smask.end());
+    for (int r2 = 0; r2 < 2; ++r2) {
+      Patches P = build_patches(m, s2, 4, nc, r2 != 0);
+      printf("macro %d %zu\n", r2, P.ptr.size() - 1);
+      for (size_t j = 0; j + 1 < P.ptr.size(); ++j) {
+        printf("%lld", (long long)(P.ptr[j + 1] - P.ptr[j]));
+        for (int64_t q = P.ptr[j]; q < P.ptr[j + 1]; ++q) printf(" %d", P.dofs[q]);
+        printf("\n");
+      }
     }
   }
   ECSRHost H = build_ecsr(m, groups);
@@ -89,9 +109,9 @@ def driver(tmp_path_factory):
     return str(exe)
 
 
-def run_driver(exe, n, p):
-    out = subprocess.run([exe, str(n[0]), str(n[1]), str(n[2]), str(p)], check=True, capture_output=True,
-                         text=True).stdout.split("\n")
+def run_driver(exe, n, p, macro=False):
+    args = [exe, str(n[0]), str(n[1]), str(n[2]), str(p)] + (["macro"] if macro else [])
+    out = subprocess.run(args, check=True, capture_output=True, text=True).stdout.split("\n")
     res, i = {}, 0
     while i < len(out):
         head = out[i].split()
@@ -129,3 +149,22 @@ def test_patches_and_operator_pattern_match_oracle(driver, n, p):
     for r in range(mesh.n_dof):
         ref = np.sort(A.indices[A.indptr[r]:A.indptr[r + 1]])
         assert np.array_equal(rows[r], ref), r
+
+
+@pytest.mark.parametrize("n,p", [((4, 4, 4), 2), ((4, 2, 4), 1)])
+def test_macro_smoothing_space_and_patches_match_oracle(driver, n, p):
+    """h level: the smoothed DOFs (the coarse elements' skeleton) and the macro
+    vertex patches (coarse element width 4 in doubled fine units) under both
+    rules, against the oracle's hierarchy on the same mesh."""
+    got = run_driver(driver, n, p, macro=True)
+    fs = build_fine(n, p, 3.0)
+    mask = got[("smask",)][0].astype(bool)
+    for r2, rule in ((0, "R1"), (1, "R2")):
+        levels = build_hierarchy(fs.mesh, fs.Kc, fs.dofs, n_levels=2, p_min=p, patch_rule=rule)
+        lev = levels[1]
+        assert lev.kind == "h"
+        assert np.array_equal(mask, lev.smask)
+        mine = got[("macro", str(r2))]
+        assert len(mine) == len(lev.patches)
+        for a, b in zip(mine, lev.patches):
+            assert np.array_equal(a, b)
