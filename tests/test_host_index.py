@@ -17,7 +17,7 @@ import numpy as np
 import pytest
 
 from oracle.assembly import build_fine
-from oracle.hierarchy import PATCH_RULES, build_hierarchy
+from oracle.hierarchy import PATCH_RULES, _p_injection, _p_selection, build_hierarchy
 from oracle.mesh import Mesh
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
@@ -26,6 +26,7 @@ CSRC = os.path.join(ROOT, "paper_2304_01728_gb300", "csrc")
 DRIVER = r"""
 #include <algorithm>
 #include <cstdio>
+#include <cmath>
 #include <cstdlib>
 #include "host_mesh.h"
 using namespace dpgmg;
@@ -43,6 +44,18 @@ int main(int argc, char** argv) {
       if (E >= 0) groups[e].push_back(E);
     std::sort(groups[e].begin(), groups[e].end());
     groups[e].erase(std::unique(groups[e].begin(), groups[e].end()), groups[e].end());
+  }
+  if (p > 1) {   // p transition to p - 1 on the same mesh
+    MeshL mc;
+    mc.init(n, p - 1, a, b);
+    std::vector<int32_t> sel, inj;
+    p_selection(p, sel);
+    p_injection(m, mc, inj);
+    printf("selection %d\n%zu", 1, sel.size());
+    for (int32_t v : sel) printf(" %d", v);
+    printf("\ninjection %d\n%zu", 1, inj.size());
+    for (int32_t v : inj) printf(" %d", v);
+    printf("\n");
   }
   std::vector<char> sm(m.ndof, 1);
   for (int r2 = 0; r2 < 2; ++r2) {
@@ -62,6 +75,13 @@ int main(int argc, char** argv) {
     printf("smask 1\n%lld", (long long)m.ndof);
     for (int64_t g = 0; g < m.ndof; ++g) printf(" %d", (int)M.smask[g]);
     printf("\n");
+    printf("inclusion %lld\n", (long long)m.ndof);   // rows of P: count, then (column, value) pairs
+    for (int64_t g = 0; g < m.ndof; ++g) {
+      printf("%lld", (long long)(2 * (M.P_ptr[g + 1] - M.P_ptr[g])));
+      for (int64_t q = M.P_ptr[g]; q < M.P_ptr[g + 1]; ++q)
+        printf(" %d %lld", M.P_col[q], (long long)llround(M.P_val[q] * 1099511627776.0));   // value x 2^40
+      printf("\n");
+    }
     std::vector<char> s2(M.smask.begin(), M.smask.end());
     for (int r2 = 0; r2 < 2; ++r2) {
       Patches P = build_patches(m, s2, 4, nc, r2 != 0);
@@ -141,6 +161,9 @@ def test_patches_and_operator_pattern_match_oracle(driver, n, p):
         assert len(mine) == len(ref)
         for a, b in zip(mine, ref):
             assert np.array_equal(a, b)
+    if p > 1:   # p transition: local selection and the coarse -> fine injection
+        assert np.array_equal(got[("selection",)][0], _p_selection(p))
+        assert np.array_equal(got[("injection",)][0], _p_injection(mesh, Mesh(n, p - 1)))
     fs = build_fine(n, p, 3.0)
     A, _ = fs.assemble()
     A = A.tocsr()
@@ -164,6 +187,18 @@ def test_macro_smoothing_space_and_patches_match_oracle(driver, n, p):
         lev = levels[1]
         assert lev.kind == "h"
         assert np.array_equal(mask, lev.smask)
+        if r2 == 0:   # natural inclusion P (fine x coarse): two-scale tables against the oracle's fit
+            Pref = lev.P.tocsr()
+            Pref.sort_indices()
+            rows = got[("inclusion",)]
+            assert len(rows) == Pref.shape[0]
+            for g, row in enumerate(rows):
+                cols, vals = row[0::2], row[1::2] / 2.0 ** 40
+                keep = np.abs(Pref.data[Pref.indptr[g]:Pref.indptr[g + 1]]) > 1e-12
+                rc = Pref.indices[Pref.indptr[g]:Pref.indptr[g + 1]][keep]
+                rv = Pref.data[Pref.indptr[g]:Pref.indptr[g + 1]][keep]
+                assert np.array_equal(cols, rc), g
+                assert np.allclose(vals, rv, rtol=0, atol=1e-11), g
         mine = got[("macro", str(r2))]
         assert len(mine) == len(lev.patches)
         for a, b in zip(mine, lev.patches):
