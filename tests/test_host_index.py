@@ -60,6 +60,10 @@ int main(int argc, char** argv) {
   std::vector<char> sm(m.ndof, 1);
   for (int r2 = 0; r2 < 2; ++r2) {
     Patches P = build_patches(m, sm, 2, n, r2 != 0);
+    std::vector<int64_t> ps = patch_sizes(m, false, 2, n, r2 != 0);   // the memory estimate's sizes
+    printf("psizes %d 1\n%zu", r2, ps.size());
+    for (int64_t v : ps) printf(" %lld", (long long)v);
+    printf("\n");
     printf("patches %d %zu\n", r2, P.ptr.size() - 1);
     for (size_t j = 0; j + 1 < P.ptr.size(); ++j) {
       printf("%lld", (long long)(P.ptr[j + 1] - P.ptr[j]));
@@ -85,6 +89,10 @@ int main(int argc, char** argv) {
     std::vector<char> s2(M.smask.begin(), M.smask.end());
     for (int r2 = 0; r2 < 2; ++r2) {
       Patches P = build_patches(m, s2, 4, nc, r2 != 0);
+      std::vector<int64_t> ps = patch_sizes(m, true, 4, nc, r2 != 0);
+      printf("msizes %d 1\n%zu", r2, ps.size());
+      for (int64_t v : ps) printf(" %lld", (long long)v);
+      printf("\n");
       printf("macro %d %zu\n", r2, P.ptr.size() - 1);
       for (size_t j = 0; j + 1 < P.ptr.size(); ++j) {
         printf("%lld", (long long)(P.ptr[j + 1] - P.ptr[j]));
@@ -159,6 +167,8 @@ def test_patches_and_operator_pattern_match_oracle(driver, n, p):
         ref = PATCH_RULES[rule](mesh, mesh, table, "p", smask)
         mine = got[("patches", str(r2))]
         assert len(mine) == len(ref)
+        # the sizes the memory estimate uses (dpgmg_query_sizes) are those of the built patches
+        assert np.array_equal(got[("psizes", str(r2))][0], [len(x) for x in ref])
         for a, b in zip(mine, ref):
             assert np.array_equal(a, b)
     if p > 1:   # p transition: local selection and the coarse -> fine injection
@@ -201,5 +211,6 @@ def test_macro_smoothing_space_and_patches_match_oracle(driver, n, p):
                 assert np.allclose(vals, rv, rtol=0, atol=1e-11), g
         mine = got[("macro", str(r2))]
         assert len(mine) == len(lev.patches)
+        assert np.array_equal(got[("msizes", str(r2))][0], [len(x) for x in lev.patches])
         for a, b in zip(mine, lev.patches):
             assert np.array_equal(a, b)
